@@ -1,0 +1,241 @@
+"""Energy, gradient and Gauss-Newton Hessian-vector product of BL PDE-LDDMM. FP64.
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+Two variants of Sec. 2.3, both with a stationary band-limited velocity v~ (one cube for all
+t) and SL-RK integration of every equation (Sec. 3.3, Table 1):
+
+  * IMAGE  -- original BL PDE-LDDMM (Sec. 2.3.1, Eqs. 15-20): spatial state m and adjoint
+    lambda, band-limited incremental state dm~ and incremental adjoint dlambda~;
+    g = L~v~ + int lambda~ * grad~ m~ dt, H dv~ = L~dv~ + int dlambda~ * grad~ m~ dt.
+  * DEFSTATE -- BL PDE-LDDMM based on the deformation state equation (Sec. 2.3.3,
+    Eqs. 31-37): displacement u~ with phi = id - iota(u~), m(1) = I0 o phi(1); adjoint rho~;
+    g = L~v~ + int (rho~ - D~u~ * rho~) dt, H dv~ = L~dv~ + int (drho~ - D~u~ * drho~) dt.
+
+Energy (Eq. 10): E = 1/2 <L~v~, v~> + (1/sigma^2) ||m(1) - I1||^2 with the L2 norm read as
+the mean over voxels (the same normalisation as pi, so that <iota c, f> = <c, pi f>).
+
+Readings fixed here (the paper is ambiguous, silent or has typos at these places):
+  * D~u~ * rho~ in the DEFSTATE gradient is (D iota(u~))^T iota(rho~) projected, i.e.
+    component b = sum_a d_b u_a rho_a (the adjoint of v -> (Du) v).
+  * The DEFSTATE Hessian of Eq. 33 prints D~ du~ * rho~; the Gauss-Newton operator
+    (J^T W J, which is symmetric) has D~u~ * drho~ there, and that is what is used.
+  * Table 1 row 6 prints lambda~ on the right-hand side of the dlambda~ equation; Eq. 20
+    has dlambda~, which is used.
+  * rho~(1) = pi(-(2/sigma^2) r G), drho~(1) = pi(-(2/sigma^2) dm(1) G) with r = m(1) - I1,
+    dm(1) = -G . iota(du~(1)) and G = (grad I0) o phi(1), the exact derivative of
+    m(1) = I0 o (id - iota(u~(1))) with respect to u~(1) (the paper writes grad m(1)).
+  * Time integrals: trapezoid rule over the nt + 1 nodes t_j = j / nt.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+
+import numpy as np
+
+from . import interp as I
+from . import sl as SL
+from . import spectral as S
+
+IMAGE = 1
+DEFSTATE = 3
+
+
+@dataclass
+class Params:
+    K: int = 16
+    nt: int = 10
+    alpha: float = 0.0025
+    s: int = 2
+    sigma2: float = 0.01
+    order: int = 1          # 1 trilinear, 3 cubic B-spline
+    variant: int = DEFSTATE
+
+
+def trapezoid_weights(nt):
+    w = np.full(nt + 1, 1.0 / nt)
+    w[0] = w[-1] = 0.5 / nt
+    return w
+
+
+class Problem:
+    """One registration problem: source I0 (moving), target I1 (fixed), parameters."""
+
+    def __init__(self, I0, I1, params: Params):
+        self.I0 = np.asarray(I0, dtype=np.float64)
+        self.I1 = np.asarray(I1, dtype=np.float64)
+        assert self.I0.shape == self.I1.shape and self.I0.ndim == 3
+        self.p = params
+        self.shape = self.I0.shape
+        nz, ny, nx = self.shape
+        # physical [0, 2 pi) -> voxel units, per component x, y, z
+        self.to_vox = np.array([nx, ny, nz], dtype=np.float64) / (2.0 * np.pi)
+        self.dt = 1.0 / params.nt
+        self.tw = trapezoid_weights(params.nt)
+
+    # ---------------------------------------------------------------- velocity (Sec. 3.2)
+    def velocity(self, vt):
+        """v = iota(v~) (physical), V = v in voxel units, d = iota(div~ v~) (Eq. 46, Table 1)."""
+        v = S.include(vt, self.shape)
+        V = v * self.to_vox[:, None, None, None]
+        d = S.include(S.div(vt), self.shape)
+        return v, V, d
+
+    def energy_reg(self, vt):
+        """1/2 <L~ v~, v~>_{l2} (Eq. 10, first term, stationary v~)."""
+        return 0.5 * S.inner(S.apply_L(vt, self.p.alpha, self.p.s), vt)
+
+    def energy_data(self, m1):
+        """(1/sigma^2) ||m(1) - I1||^2 as a voxel mean (Eq. 10, second term)."""
+        r = m1 - self.I1
+        return float(np.mean(r * r)) / self.p.sigma2
+
+    # ------------------------------------------------------------------ DEFSTATE (V3)
+    def _warp_I0(self, u1):
+        """m(1) = I0 o phi(1), phi = id - iota(u~(1)), and G = (grad I0) o phi(1) (physical)."""
+        offs = -S.include(u1, self.shape) * self.to_vox[:, None, None, None]
+        m1 = I.interpolate(self.I0, offs, self.p.order)
+        G = I.interpolate_grad(self.I0, offs, self.p.order) * self.to_vox[:, None, None, None]
+        return m1, G
+
+    def state_defstate(self, vt):
+        """u~ from D~_t u~ = v~, u~(0) = 0 (Eq. 34; Table 1 row 3), all nodes kept."""
+        p = self.p
+        v, V, d = self.velocity(vt)
+        D = SL.departure_offsets(V, self.dt, +1, p.order)
+        u = np.zeros((3, p.K, p.K, p.K), dtype=np.complex128)
+        us = [u]
+        for _ in range(p.nt):
+            u = SL.bl_heun_source_step(u, D, v, v, self.dt, p.order, self.shape, p.K)
+            us.append(u)
+        return us
+
+    def _jacobians(self, us):
+        """Spatial D iota(u~_j): [j][a][b] = d u_a / d x_b (physical)."""
+        return [S.include(S.jacobian(u), self.shape) for u in us]
+
+    def _adjoint_bl(self, rho_end, vt):
+        """Backward sweep of -D~_t rho~ = rho~ * div~ v~ (Eqs. 35/37; Table 1 rows 4/8)."""
+        p = self.p
+        v, V, d = self.velocity(vt)
+        Dp = SL.departure_offsets(V, self.dt, -1, p.order)
+        rhos = [None] * (p.nt + 1)
+        rhos[p.nt] = rho_end
+        rho = rho_end
+        for j in range(p.nt - 1, -1, -1):
+            rho = SL.bl_heun_divergence_step(rho, Dp, d, self.dt, p.order, self.shape, p.K)
+            rhos[j] = rho
+        return rhos
+
+    def _assemble_defstate(self, base, rhos, Jus):
+        """L~ base + sum_j w_j (rho~_j - pi((D iota u~_j)^T iota(rho~_j))) (Eqs. 32-33)."""
+        out = S.apply_L(base, self.p.alpha, self.p.s).astype(np.complex128)
+        for j, (rho, Ju) in enumerate(zip(rhos, Jus)):
+            r_sp = S.include(rho, self.shape)
+            JT = np.einsum("abzyx,azyx->bzyx", Ju, r_sp)
+            out = out + self.tw[j] * (rho - S.project(JT, self.p.K))
+        return out
+
+    # ------------------------------------------------------------------ IMAGE (V1)
+    def state_image(self, vt):
+        """m from D_t m = 0, m(0) = I0 (Eq. 17; Table 1 row 1), all nodes kept (spatial)."""
+        p = self.p
+        v, V, d = self.velocity(vt)
+        D = SL.departure_offsets(V, self.dt, +1, p.order)
+        m = self.I0.copy()
+        ms = [m]
+        for _ in range(p.nt):
+            m = SL.transport_step(m, D, p.order)
+            ms.append(m)
+        return ms
+
+    def _grad_mtilde(self, ms):
+        """iota(grad~ m~_j) with m~_j = pi(m_j) (Sec. 2.3.1), [j][3] spatial, physical."""
+        return [S.include(S.grad(S.project(m, self.p.K)), self.shape) for m in ms]
+
+    # ------------------------------------------------------------------ public API
+    def objective(self, vt):
+        """(E, E_reg, E_data, m(1)) at v~ (Eq. 10 with the variant's state equation)."""
+        if self.p.variant == DEFSTATE:
+            us = self.state_defstate(vt)
+            m1, _ = self._warp_I0(us[-1])
+        else:
+            m1 = self.state_image(vt)[-1]
+        er, ed = self.energy_reg(vt), self.energy_data(m1)
+        return er + ed, er, ed, m1
+
+    def gradient(self, vt):
+        """Returns (E, E_reg, E_data, g~) (Eq. 15 for IMAGE, Eq. 32 for DEFSTATE)."""
+        p = self.p
+        if p.variant == DEFSTATE:
+            us = self.state_defstate(vt)
+            m1, G = self._warp_I0(us[-1])
+            r = m1 - self.I1
+            rho1 = S.project(-(2.0 / p.sigma2) * r[None] * G, p.K)
+            rhos = self._adjoint_bl(rho1, vt)
+            g = self._assemble_defstate(vt, rhos, self._jacobians(us))
+        else:
+            ms = self.state_image(vt)
+            m1 = ms[-1]
+            v, V, d = self.velocity(vt)
+            Dp = SL.departure_offsets(V, self.dt, -1, p.order)
+            lam = -(2.0 / p.sigma2) * (m1 - self.I1)          # lambda(1)
+            lams = [None] * (p.nt + 1)
+            lams[p.nt] = lam
+            for j in range(p.nt - 1, -1, -1):                   # Eq. 18, Table 1 row 2
+                lam = SL.heun_divergence_step(lam, Dp, d, self.dt, p.order)
+                lams[j] = lam
+            gms = self._grad_mtilde(ms)
+            g = S.apply_L(vt, p.alpha, p.s).astype(np.complex128)
+            for j in range(p.nt + 1):                            # lambda~ * grad~ m~
+                lam_bl = S.include(S.project(lams[j], p.K), self.shape)
+                g = g + self.tw[j] * S.project(lam_bl[None] * gms[j], p.K)
+        er, ed = self.energy_reg(vt), self.energy_data(m1)
+        return er + ed, er, ed, g
+
+    def hessian_matvec(self, vt, dvt):
+        """Gauss-Newton H dv~ at v~ (Eq. 16 for IMAGE, Eq. 33 as read for DEFSTATE)."""
+        p = self.p
+        v, V, d = self.velocity(vt)
+        D = SL.departure_offsets(V, self.dt, +1, p.order)
+        dv = S.include(dvt, self.shape)
+        if p.variant == DEFSTATE:
+            us = self.state_defstate(vt)
+            Jus = self._jacobians(us)
+            _, G = self._warp_I0(us[-1])
+            # incremental state D~_t du~ = dv~ - D~u~ * dv~ (Eq. 36; Table 1 row 7)
+            F = [dv - np.einsum("abzyx,bzyx->azyx", Ju, dv) for Ju in Jus]
+            du = np.zeros_like(dvt, dtype=np.complex128)
+            for j in range(p.nt):
+                du = SL.bl_heun_source_step(du, D, F[j], F[j + 1], self.dt, p.order,
+                                            self.shape, p.K)
+            dm1 = -np.sum(G * S.include(du, self.shape), axis=0)
+            drho1 = S.project(-(2.0 / p.sigma2) * dm1[None] * G, p.K)
+            drhos = self._adjoint_bl(drho1, vt)
+            return self._assemble_defstate(dvt, drhos, Jus)
+        ms = self.state_image(vt)
+        gms = self._grad_mtilde(ms)
+        # incremental state D~_t dm~ = -grad~ m~ * dv~ (Eq. 19; Table 1 row 5)
+        F = [-np.sum(gm * dv, axis=0) for gm in gms]
+        dm = np.zeros((p.K, p.K, p.K), dtype=np.complex128)
+        for j in range(p.nt):
+            dm = SL.bl_heun_source_step(dm, D, F[j], F[j + 1], self.dt, p.order, self.shape, p.K)
+        dlam = -(2.0 / p.sigma2) * dm                             # dlambda~(1)
+        Dp = SL.departure_offsets(V, self.dt, -1, p.order)
+        out = S.apply_L(dvt, p.alpha, p.s).astype(np.complex128)
+        for j in range(p.nt, -1, -1):                             # Eq. 20; Table 1 row 6
+            out = out + self.tw[j] * S.project(S.include(dlam, self.shape)[None] * gms[j], p.K)
+            if j > 0:
+                dlam = SL.bl_heun_divergence_step(dlam, Dp, d, self.dt, p.order, self.shape, p.K)
+        return out
+
+    # ------------------------------------------------------------------ diagnostics
+    def mse_rel(self, m1):
+        """MSE_rel = ||m(1) - I1||^2 / ||I0 - I1||^2 (Sec. 5.1.1)."""
+        return float(np.sum((m1 - self.I1) ** 2) / np.sum((self.I0 - self.I1) ** 2))
+
+    def max_displacement_vox(self, vt):
+        """Max over voxels of |phi(1)(x) - x| in voxels (DEFSTATE: |iota(u~(1))|)."""
+        us = self.state_defstate(vt)
+        u = S.include(us[-1], self.shape) * self.to_vox[:, None, None, None]
+        return float(np.sqrt((u * u).sum(0)).max())

@@ -1,0 +1,121 @@
+"""Pins of the oracle's energy, gradient and GN Hessian (Sec. 2.3.1, 2.3.3).
+
+The gradient is derived optimise-then-discretise, so it matches finite differences of the
+discrete energy only up to discretisation error: the tolerances below are measured ones.
+"""
+import numpy as np
+import pytest
+
+from oracle import sl as SL
+from oracle import spectral as S
+from oracle import variants as Vn
+from paper_2006_06823_b300 import synth
+
+N = 16
+K = 8
+
+
+def _problem(variant, order, nt=10, zero_residual=False):
+    shape = (N, N, N)
+    I1 = synth.gaussian_blobs(shape, seed=0)
+    p = Vn.Params(K=K, nt=nt, order=order, variant=variant, sigma2=0.01)
+    vgen = synth.random_velocity_coeffs(K, 8, seed=1)
+    base = Vn.Problem(I1, I1, p)
+    _, V, _ = base.velocity(vgen)
+    sc = 2.0 / np.abs(V).max()
+    I0 = I1 if zero_residual else SL.sl_transport(I1, V * sc, 10, +1, order)
+    return Vn.Problem(I0, I1, p), vgen * sc
+
+
+def _fd(prob, vt, dvt, h=1e-3):
+    return (prob.objective(vt + h * dvt)[0] - prob.objective(vt - h * dvt)[0]) / (2 * h)
+
+
+def test_zero_velocity_and_equal_images_give_zero_energy():
+    prob, _ = _problem(Vn.DEFSTATE, 1, zero_residual=True)
+    E, Er, Ed, m1 = prob.objective(np.zeros((3, K, K, K), complex))
+    assert E == 0.0 and Er == 0.0 and Ed == 0.0
+
+
+def test_regularisation_energy_closed_form_single_mode():
+    prob, _ = _problem(Vn.DEFSTATE, 1, zero_residual=True)
+    vt = np.zeros((3, K, K, K), complex)
+    h = K // 2
+    vt[1, h + 2, h - 1, h + 3] = 0.4 + 0.1j
+    vt[1, h - 2, h + 1, h - 3] = 0.4 - 0.1j
+    w = (1 + 0.0025 * (4 + 1 + 9)) ** 2
+    assert prob.energy_reg(vt) == pytest.approx(0.5 * w * 2 * (0.16 + 0.01), rel=1e-14)
+
+
+def test_data_energy_at_zero_velocity_is_the_image_mse():
+    for variant in (Vn.IMAGE, Vn.DEFSTATE):
+        prob, _ = _problem(variant, 1)
+        E, Er, Ed, m1 = prob.objective(np.zeros((3, K, K, K), complex))
+        assert Ed == pytest.approx(np.mean((prob.I0 - prob.I1) ** 2) / 0.01, rel=1e-13)
+
+
+@pytest.mark.parametrize("variant", [Vn.IMAGE, Vn.DEFSTATE])
+def test_constant_images_reduce_gradient_and_hessian_to_L(variant):
+    shape = (N, N, N)
+    c = np.full(shape, 0.4)
+    prob = Vn.Problem(c, c, Vn.Params(K=K, nt=5, variant=variant))
+    vt = synth.random_coeffs(K, seed=2) * 0.05
+    E, Er, Ed, g = prob.gradient(vt)
+    assert Ed < 1e-28
+    np.testing.assert_allclose(g, S.apply_L(vt, 0.0025, 2), atol=1e-14)
+    dv = synth.random_coeffs(K, seed=3)
+    np.testing.assert_allclose(prob.hessian_matvec(vt, dv), S.apply_L(dv, 0.0025, 2), atol=1e-13)
+
+
+@pytest.mark.parametrize("order,tol", [(1, 1e-2), (3, 1e-3)])
+def test_defstate_gradient_matches_central_differences(order, tol):
+    prob, vt = _problem(Vn.DEFSTATE, order)
+    vt = vt * 0.3
+    g = prob.gradient(vt)[3]
+    for seed in (5, 6, 7):
+        dvt = synth.random_coeffs(K, seed) * 0.05
+        fd = _fd(prob, vt, dvt)
+        assert abs(fd - S.inner(g, dvt)) <= tol * abs(fd), (fd, S.inner(g, dvt))
+
+
+def test_image_variant_gradient_matches_central_differences_with_cubic():
+    prob, vt = _problem(Vn.IMAGE, 3)
+    vt = vt * 0.3
+    g = prob.gradient(vt)[3]
+    for seed in (5, 6):
+        dvt = synth.random_coeffs(K, seed) * 0.05
+        fd = _fd(prob, vt, dvt)
+        assert abs(fd - S.inner(g, dvt)) <= 5e-2 * abs(fd)
+
+
+@pytest.mark.parametrize("variant", [Vn.IMAGE, Vn.DEFSTATE])
+def test_negative_gradient_is_a_descent_direction(variant):
+    prob, vt = _problem(variant, 1)
+    vt = vt * 0.3
+    E, _, _, g = prob.gradient(vt)
+    step = 1e-3 / np.sqrt(S.inner(g, g))
+    assert prob.objective(vt - step * g)[0] < E
+
+
+@pytest.mark.parametrize("variant,order,tol", [(Vn.DEFSTATE, 1, 1e-2), (Vn.DEFSTATE, 3, 1e-3),
+                                               (Vn.IMAGE, 1, 3e-2), (Vn.IMAGE, 3, 1e-2)])
+def test_gauss_newton_hessian_is_symmetric_positive(variant, order, tol):
+    prob, vt = _problem(variant, order)
+    vt = vt * 0.3
+    x = synth.random_coeffs(K, 7) * 0.05
+    y = synth.random_coeffs(K, 8) * 0.05
+    Hx, Hy = prob.hessian_matvec(vt, x), prob.hessian_matvec(vt, y)
+    a, b = S.inner(y, Hx), S.inner(x, Hy)
+    assert abs(a - b) <= tol * max(abs(a), abs(b))
+    assert S.inner(x, Hx) > S.inner(x, S.apply_L(x, 0.0025, 2))
+    assert S.inner(y, Hy) > S.inner(y, S.apply_L(y, 0.0025, 2))
+
+
+def test_defstate_hessian_matches_gradient_differences_at_zero_residual():
+    prob, _ = _problem(Vn.DEFSTATE, 3, zero_residual=True)
+    vt = np.zeros((3, K, K, K), complex)
+    d = synth.random_coeffs(K, 9) * 0.05
+    h = 1e-3
+    fd = (prob.gradient(vt + h * d)[3] - prob.gradient(vt - h * d)[3]) / (2 * h)
+    Hd = prob.hessian_matvec(vt, d)
+    assert np.linalg.norm(fd - Hd) <= 1e-3 * np.linalg.norm(Hd)
