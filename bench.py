@@ -1,0 +1,359 @@
+#!/usr/bin/env python
+"""Benchmark: Gauss-Newton time-to-residual of BL PDE-LDDMM (deformation-state variant,
+SL-RK) on a paper-scale synthetic pair, plus SL voxel-steps/s, on one B300 per rank.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl b300|reference]
+
+One step = one full registration from a cold start (v~ = 0) of a 192 x 224 x 192 pair:
+velocity synthesis, characteristics, state / adjoint / incremental sweeps, projections,
+PCG, line search and the stopping test -- every row of the hot path. Inputs are resident
+in device memory before timing starts; the e2e figure repeats the step through the public
+API with host buffers (host->device images, device->host velocity) inside the timing.
+
+Under torchrun (N > 1) each rank registers its own pair (independent replicas: a pair
+does not shard); the value divides the slowest rank's time by all pairs processed.
+
+``--impl reference`` times the FP64 CPU oracle on a bounded sample of the same workload
+(one band-limited SL-RK step of the deformation state, extrapolated to a registration by
+the step count the GPU path performs on this workload).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+SHAPE = (192, 224, 192)        # nz, ny, nx
+K = 32
+NT = 10
+MAX_GN, MAX_PCG, GTOL = 10, 20, 1e-3
+SIGMA2, ALPHA, S_EXP = 0.01, 0.0025, 2
+METRIC = "GN time-to-residual 1e-3 (s/pair) + SL voxel-steps/s, plain FP32 vs chosen form"
+WORKLOAD = ("192x224x192 brain-like ellipsoid phantom pair (moving = phantom warped by a "
+            "random 32^3-mode stationary velocity, 8 vox max; N(0,0.01) noise), "
+            "deformation-state BL PDE-LDDMM, K=32, nt=10, trilinear SL-RK, "
+            "alpha=0.0025, s=2, sigma^2=0.01, <=10 GN x <=20 PCG, gtol=1e-3")
+# BL steps the GPU path performs in one registration of this workload (solves x nt), as
+# reported by lddmm_register on a B300; used only to extrapolate the oracle's sample.
+REF_STEPS_PER_PAIR = None
+
+# kernel -> roofline bound used for the dominant-kernel report
+HBM_KERNELS = {"sl_gather", "sl_gather_scale", "sl_gather_add", "sl_inc_defstate",
+               "sl_char", "sl_prep_adjoint", "sl_prep_source", "warp_image", "accum_JT",
+               "defstate_rhs", "defstate_drho1", "sum_sq_diff"}
+
+
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))), "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0, "bf16_tflops_sustained": 1400.0,
+                "sm_max_mhz": 2032.0}, "fallback"
+
+
+def _fp32_simt_peak_tflops(sm_mhz):
+    # 148 SMs x 128 FP32 lanes x 2 flop (FMA) per clock
+    return 148 * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs(L, torch, dev):
+    """Phantom pair on the device (float32 [nz, ny, nx] each) and pinned host copies."""
+    import numpy as np
+    from paper_2006_06823_b300 import synth
+    nz, ny, nx = SHAPE
+    fixed = synth.ellipsoid_phantom(SHAPE)
+    vt = synth.random_velocity_coeffs(K, K, seed=1)
+    vt_d = torch.as_tensor(vt.astype(np.complex64), device=dev)
+    v = L.bl_include(vt_d, SHAPE)
+    to_vox = torch.tensor([nx, ny, nz], dtype=torch.float32, device=dev).view(3, 1, 1, 1) / (2 * np.pi)
+    V = v * to_vox
+    V *= 8.0 / V.pow(2).sum(0).sqrt().max()
+    fixed_d = torch.as_tensor(fixed, dtype=torch.float32, device=dev)
+    moving_d = L.sl_transport(V, fixed_d, NT, L.FORWARD, L.INTERP_LINEAR)
+    moving = moving_d.cpu().numpy().astype(np.float64)
+    I0 = synth.add_noise(moving, seed=2).astype(np.float32)
+    I1 = synth.add_noise(fixed, seed=3).astype(np.float32)
+    I0h = torch.from_numpy(I0).pin_memory()
+    I1h = torch.from_numpy(I1).pin_memory()
+    return I0h.to(dev), I1h.to(dev), I0h, I1h, V, fixed_d
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_b300(args):
+    import torch
+    import paper_2006_06823_b300 as L
+    world, rank, local = dist_setup()
+    dev = torch.device("cuda", local if world > 1 else 0)
+    peaks, peak_src = _peaks()
+    nz, ny, nx = SHAPE
+    I0d, I1d, I0h, I1h, V, fixed_d = make_inputs(L, torch, dev)
+    ctx = L.Context(nx, ny, nz, K, nt=NT, variant=L.V_DEFSTATE, interp=L.INTERP_LINEAR,
+                    alpha=ALPHA, s=S_EXP, sigma2=SIGMA2, max_gn=MAX_GN, max_pcg=MAX_PCG,
+                    gtol=GTOL)
+    ctx.set_images(I0d, I1d)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream()
+
+    reports = []
+    for _ in range(args.warmup):
+        _, rep = ctx.register()
+        reports.append(rep)
+    torch.cuda.synchronize()
+
+    # ---- timed region: K registrations from a cold start, inputs resident on the device
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if sampler:
+        sampler.start()
+    L.trace_reset()
+    L.trace_enable(True)
+    launches0 = L.launch_count()
+    step_ms = []
+    barrier(world)
+    torch.cuda.synchronize()
+    for _ in range(args.steps):
+        flush.fill_(1.0)                       # evict L2 between steps (outside the timing)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, rep = ctx.register()
+        e1.record(stream)
+        e1.synchronize()
+        step_ms.append(e0.elapsed_time(e1))
+        reports.append(rep)
+    torch.cuda.synchronize()
+    barrier(world)
+    launches = L.launch_count() - launches0
+    trace = L.trace_read()
+    L.trace_enable(False)
+    clocks = sampler.stop() if sampler else None
+    total_s = max_over_ranks(sum(step_ms) / 1e3, world)
+
+    # ---- SL voxel-steps/s: nt-step scalar transport of the phantom (Table 1 row 1)
+    sl_ms = []
+    for i in range(args.warmup + args.steps):
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        L.sl_transport(V, fixed_d, NT, L.FORWARD, L.INTERP_LINEAR)
+        e1.record(stream)
+        e1.synchronize()
+        if i >= args.warmup:
+            sl_ms.append(e0.elapsed_time(e1))
+    ntot = nx * ny * nz
+    sl_vps = NT * ntot / (statistics.mean(sl_ms) / 1e3)
+
+    # ---- e2e: the public API with host buffers, copies inside the timing
+    e2e_s = []
+    v_host = torch.empty((3, K, K, K), dtype=torch.complex64).pin_memory()
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx.set_images(I0h, I1h)
+        v, _ = ctx.register()
+        v_host.copy_(v, non_blocking=True)
+        torch.cuda.synchronize()
+        e2e_s.append(time.perf_counter() - t0)
+    e2e_total = max_over_ranks(sum(e2e_s), world)
+    ctx.close()
+
+    if rank != 0:
+        return None
+    last = reports[-1]
+    per_pair = total_s / (args.steps * world)
+    # dominant kernel by total device time in the timed region
+    name, kt = max(trace.items(), key=lambda kv: kv[1]["ms"])
+    avg_ms = kt["ms"] / kt["launches"]
+    hbm = peaks["hbm_gbs"]
+    if name in HBM_KERNELS:
+        achieved = kt["bytes"] / kt["launches"] / (avg_ms * 1e-3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                "frac": achieved / hbm}
+    else:
+        achieved = kt["flops"] / kt["launches"] / (avg_ms * 1e-3) / 1e12
+        pk = _fp32_simt_peak_tflops(peaks.get("sm_max_mhz", 2032.0))
+        roof = {"bound": "alu", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
+                "frac": achieved / pk}
+    roof.update({"kernel": name, "traffic": None, "peak_source": peak_src,
+                 "avg_launch_us": avg_ms * 1e3, "launches": kt["launches"],
+                 "share": kt["ms"] / sum(v["ms"] for v in trace.values())})
+    out = {
+        "metric": METRIC, "value": per_pair, "unit": "s/pair", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_s * 1e3 / args.steps,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic", "impl": "b300",
+        "config": {"workload": WORKLOAD, "pairs_per_step": world,
+                   "l2": "flushed (256 MB write) between timed steps; working set ~5 GB"},
+        "residual_reached": last["grad_rel_l2"] <= GTOL,
+        "report": {k: last[k] for k in ("gn_iters", "pcg_iters_total", "stop_reason", "solves",
+                                        "E0", "E", "grad_rel_l2", "grad_rel_inf", "mse_rel")},
+        "sl_voxel_steps_per_s": sl_vps,
+        "e2e": {"value": e2e_total / (args.steps * world), "unit": "s/pair",
+                "h2d_bytes_per_step": 2 * ntot * 4, "d2h_bytes_per_step": 3 * K ** 3 * 8},
+        "gpu_launches": launches,
+        "clocks": clocks,
+        "roofline": roof,
+        "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3)} for k, v in
+                    sorted(trace.items(), key=lambda kv: -kv[1]["ms"])[:12]},
+    }
+    if not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(steps_per_pair=last["solves"] * NT, samples=1)
+    return out
+
+
+def cpu_baseline(steps_per_pair, samples=1):
+    """The FP64 oracle timed on one BL SL-RK step of the deformation state at full size
+    (iota of 3 components, trilinear gather, pi), extrapolated to a registration."""
+    import numpy as np
+    from oracle import sl as SL
+    from oracle import spectral as S
+    from paper_2006_06823_b300 import synth
+    nz, ny, nx = SHAPE
+    rng = synth.rng(7)
+    u = synth.random_velocity_coeffs(K, K, seed=8) * 0.05
+    D = synth.random_displacement(SHAPE, seed=9, max_vox=4.0, smooth=2.0)
+    W = rng.standard_normal((3,) + SHAPE) * 1e-3
+    ts = []
+    for _ in range(samples):
+        t0 = time.perf_counter()
+        SL.bl_heun_source_step(u, D, W, W, 0.1, 1, SHAPE, K)
+        ts.append(time.perf_counter() - t0)
+    step_s = min(ts)
+    return {"value": step_s * steps_per_pair, "unit": "s/pair", "cores": 1, "kind": "oracle",
+            "sample": (f"one BL SL-RK step (iota x3, trilinear gather, pi x3) at 192x224x192 "
+                       f"in FP64 numpy = {step_s:.2f} s, x {steps_per_pair} steps per "
+                       f"registration (the GPU path's count on this workload)"),
+            "voxel_steps_per_s": nx * ny * nz / step_s}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    steps_per_pair = REF_STEPS_PER_PAIR or (NT * 40)
+    t0 = time.perf_counter()
+    vals = []
+    for i in range(args.warmup + args.steps):
+        cb = cpu_baseline(steps_per_pair, samples=1)
+        if i >= args.warmup:
+            vals.append(cb["value"])
+    value = statistics.mean(vals)
+    cb["value"] = value
+    return {"metric": METRIC, "value": value, "unit": "s/pair", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": (time.perf_counter() - t0) * 1e3 / (args.steps + args.warmup),
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference", "config": {"workload": WORKLOAD},
+            "cpu_baseline": cb,
+            "e2e": {"value": value, "unit": "s/pair", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    out = run_reference(args) if args.impl == "reference" else run_b300(args)
+    if out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,188 @@
+/*
+ * lddmm.h -- C ABI of the B300 (sm_103a) library for band-limited PDE-constrained LDDMM
+ * with Gauss-Newton-Krylov optimisation and Semi-Lagrangian Runge-Kutta (SL-RK)
+ * integration (arxiv 2006.06823).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  Grid      nx, ny, nz voxels; scalar fields are float[nz][ny][nx] (x fastest); vector
+ *            fields are float[3][nz][ny][nx] with component 0 = x, 1 = y, 2 = z.
+ *  Domain    Omega = [0, 2 pi)^3, periodic; voxel j_a sits at x_a = 2 pi j_a / n_a.
+ *  Band      K even, 4 <= K <= min(nx, ny, nz). Coefficient cubes are interleaved complex
+ *            float[ncomp][K][K][K][2] indexed [comp][jz][jy][jx][re/im]; slot j holds
+ *            wavenumber k = j - K/2. Slot j = 0 (k = -K/2) is always zero, so the retained
+ *            set is S = {|k_a| <= K/2 - 1} (Sec. 2.2, truncated Fourier domain).
+ *            Cubes describing real fields are Hermitian (c_{-k} = conj c_k); the library
+ *            reads only the kx >= 0 half of an input cube and writes full, Hermitian cubes.
+ *  pi / iota pi(f)_k = (1/N_tot) sum_x f(x) e^{-i k.x};  iota(c)(x) = sum_{k in S} c_k e^{i k.x}.
+ *  Units     Band-limited velocities and displacements are physical (per [0, 2 pi)); spatial
+ *            velocities handed to the SL entry points are in voxels per unit time.
+ *  Pointers  Field and cube pointers are DEVICE pointers owned by the caller, unless a
+ *            parameter says "host". The library owns only a context's workspace and the
+ *            scratch of the stand-alone calls (taken from CUDA's stream-ordered pool).
+ *  Streams   `stream` is a cudaStream_t (NULL = legacy default stream). Calls are
+ *            asynchronous on it, except those returning host scalars or reports, which
+ *            synchronise that stream before returning.
+ *  Errors    Every call returns an lddmm_status; nothing is thrown across the ABI. The
+ *            message of the calling thread's most recent failure is in lddmm_last_error().
+ *            A context records its first error and refuses further work (sticky).
+ */
+#ifndef LDDMM_H
+#define LDDMM_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    LDDMM_OK = 0,
+    LDDMM_EINVAL = -1,      /* bad argument, shape or parameter */
+    LDDMM_ENOMEM = -2,      /* device allocation failed or workspace cap exceeded */
+    LDDMM_ECUDA = -3,       /* a CUDA runtime error (message kept) */
+    LDDMM_ENONFINITE = -4,  /* NaN/Inf met in an energy or inner product */
+    LDDMM_ETIMEOUT = -5,    /* a bounded device-side wait gave up */
+    LDDMM_ELINESEARCH = -6  /* no acceptable update length (returned in reports only) */
+} lddmm_status;
+
+enum { LDDMM_V_IMAGE = 1, LDDMM_V_DEFSTATE = 3 };          /* Sec. 2.3.1, Sec. 2.3.3 */
+enum { LDDMM_INTERP_LINEAR = 1, LDDMM_INTERP_CUBIC = 3 };  /* Sec. 3.1, Sec. 4.2 */
+enum { LDDMM_PREC_FP32 = 0, LDDMM_PREC_BF16X3 = 1 };       /* spectral path precision */
+enum { LDDMM_FORWARD = 1, LDDMM_BACKWARD = -1 };           /* SL time direction */
+enum { LDDMM_STOP_GTOL = 1, LDDMM_STOP_MAXIT = 2, LDDMM_STOP_LINESEARCH = 3 };
+
+/* Problem parameters. Paper values (Sec. 4.3): alpha = 0.0025, s = 2, at most 10 Gauss-
+ * Newton iterations with at most 5 PCG iterations, nt = 5 for SL-RK. */
+typedef struct {
+    int nx, ny, nz;    /* grid */
+    int K;             /* band (cube edge), even */
+    int nt;            /* time steps on [0, 1] */
+    int variant;       /* LDDMM_V_IMAGE or LDDMM_V_DEFSTATE */
+    int interp;        /* LDDMM_INTERP_LINEAR or LDDMM_INTERP_CUBIC */
+    double alpha;      /* L = (Id - alpha Laplacian)^s, Eq. 1 */
+    int s;
+    double sigma2;     /* data weight 1/sigma^2 of Eq. 10 */
+    int max_gn;        /* Gauss-Newton updates */
+    int max_pcg;       /* PCG iterations per update */
+    double gtol;       /* stop when ||g|| / ||g(v=0)|| <= gtol */
+    int precision;     /* LDDMM_PREC_FP32 or LDDMM_PREC_BF16X3 */
+} lddmm_params;
+
+/* Outcome of lddmm_register. */
+typedef struct {
+    int gn_iters;         /* accepted Gauss-Newton updates */
+    int pcg_iters_total;  /* Hessian-vector products spent in PCG */
+    int stop_reason;      /* LDDMM_STOP_* */
+    int solves;           /* PDE solves of nt steps (state, adjoint, incremental) */
+    double E0, E, E_reg, E_data;   /* energy at v0 and at the result (Eq. 10) */
+    double grad_rel_l2;   /* ||g(v)||_2 / ||g(0)||_2 at the result */
+    double grad_rel_inf;  /* ||g(v)||_inf / ||g(0)||_inf (Sec. 5.1.1) */
+    double mse_rel;       /* ||m(1) - I1||^2 / ||I0 - I1||^2 (Sec. 5.1.1) */
+    double seconds;       /* wall time inside the call */
+} lddmm_report;
+
+typedef struct lddmm_ctx lddmm_ctx;
+
+/* ---------------------------------------------------------------- context lifecycle */
+
+/* Validates *params, allocates the context's device workspace on the current device and
+ * binds the context to `stream`. *out receives the handle (NULL on failure).
+ * Errors: EINVAL (shape, band, variant, interp, nt, sigma2 <= 0), ENOMEM, ECUDA. */
+int lddmm_create(const lddmm_params* params, void* stream, lddmm_ctx** out);
+
+/* Frees the workspace (after synchronising the context's stream). NULL is accepted. */
+int lddmm_destroy(lddmm_ctx* ctx);
+
+/* Copies the source image I0 (moving, m(0) = I0) and the target I1 (fixed) into the
+ * context, device-to-device (float[nz][ny][nx] each). Eq. 10, Eq. 17. */
+int lddmm_set_images(lddmm_ctx* ctx, const float* I0, const float* I1);
+
+/* Same, from HOST buffers (pageable or pinned); the copies run on the context's stream. */
+int lddmm_set_images_host(lddmm_ctx* ctx, const float* I0_host, const float* I1_host);
+
+/* ------------------------------------------------------------------ the optimiser */
+
+/* Energy of Eq. 10 at the band-limited velocity v (cube float[3][K][K][K][2]) under the
+ * context's variant: solves the state equation (Eq. 17 or Eq. 34). Writes host doubles
+ * (any pointer may be NULL). Synchronises. */
+int lddmm_objective(lddmm_ctx* ctx, const float* v, double* E, double* E_reg, double* E_data);
+
+/* Gradient g~ at v (Eq. 15 for IMAGE, Eq. 32 for DEFSTATE) into g (device cube
+ * float[3][K][K][K][2]); also leaves the state trajectory of v cached for
+ * lddmm_hessian_matvec. Energies as in lddmm_objective (host, may be NULL). Synchronises. */
+int lddmm_gradient(lddmm_ctx* ctx, const float* v, float* g, double* E, double* E_reg,
+                   double* E_data);
+
+/* Gauss-Newton Hessian-vector product H(v) dv (Eq. 16 for IMAGE, Eq. 33 read as the
+ * Gauss-Newton operator for DEFSTATE) into Hdv (device cubes). Recomputes the state of
+ * v when it is not the cached one. Asynchronous. */
+int lddmm_hessian_matvec(lddmm_ctx* ctx, const float* v, const float* dv, float* Hdv);
+
+/* Gauss-Newton-Krylov registration (Eqs. 13-14): v_inout (device cube) holds the
+ * initial velocity (zeros for a cold start) and receives the result; PCG with
+ * preconditioner L~^{-1}, Armijo update length, stop on grad ratio or max_gn.
+ * g_ref_norms (host, may be NULL): {||g(0)||_2, ||g(0)||_inf} of the cold start, so that a
+ * warm start is judged against the cold-start reference; NULL computes them here.
+ * *report (host) receives the outcome. Synchronises. */
+int lddmm_register(lddmm_ctx* ctx, float* v_inout, const double* g_ref_norms,
+                   lddmm_report* report);
+
+/* Warp m(1) = I0 o phi(1) of the last state solved in the context into m1 (device,
+ * float[nz][ny][nx]). DEFSTATE: phi(1) = id - iota(u~(1)); IMAGE: m(nt). */
+int lddmm_get_warped(lddmm_ctx* ctx, float* m1);
+
+/* ----------------------------------------------- stand-alone operators of the hot path */
+
+/* pi: ncomp real fields f (float[ncomp][nz][ny][nx]) -> cubes c (float[ncomp][K][K][K][2]).
+ * Sec. 2.2. precision: LDDMM_PREC_FP32 (FP32 arithmetic) or LDDMM_PREC_BF16X3 (tensor-core
+ * split products, FP32 accumulation). Scratch from the stream-ordered pool.
+ * Errors: EINVAL (shape, K, ncomp < 1), ENOMEM, ECUDA. */
+int lddmm_bl_project(int nx, int ny, int nz, int K, const float* f, int ncomp, float* c,
+                     int precision, void* stream);
+
+/* iota: cubes c (float[ncomp][K][K][K][2], Hermitian) -> real fields f.
+ * deriv_axis = -1: iota(c); 0/1/2: iota(i k_axis c), the spectral derivative along x/y/z.
+ * bspline = 1: iota(c / B^(k)) with B^(k) = prod_a (2 + cos(2 pi k_a / n_a)) / 3, i.e. the
+ * periodic cubic B-spline coefficients of iota(c) (the prefilter of Sec. 4.2 done exactly in
+ * Fourier). Sec. 2.2. Errors as lddmm_bl_project. */
+int lddmm_bl_include(int nx, int ny, int nz, int K, const float* c, int ncomp, float* f,
+                     int deriv_axis, int bspline, int precision, void* stream);
+
+/* Departure-point offsets D = X - x (voxels, float[3][nz][ny][nx]) of one SL step of length
+ * dt for the stationary voxel-unit velocity vel (float[3][nz][ny][nx]) by Eqs. 40-42:
+ * direction FORWARD: X* = x - dt v, X = x - dt/2 (v(X*) + v); BACKWARD: the same along -v.
+ * interp LINEAR or CUBIC (cubic prefilters vel internally). Errors: EINVAL, ENOMEM, ECUDA. */
+int lddmm_sl_characteristics(int nx, int ny, int nz, const float* vel, double dt,
+                             int direction, int interp, float* offsets, void* stream);
+
+/* nt SL steps of D_t u = 0 (Table 1 row 1) for ncomp fields with the stationary voxel-unit
+ * velocity vel: characteristics once (as above, dt = 1/nt), then u^{j+1} = u^j o X.
+ * direction BACKWARD integrates -D_t u = 0 from t = 1 to 0. field and out are
+ * float[ncomp][nz][ny][nx] and may alias. This is the unit of the voxel-steps/s figure.
+ * Errors: EINVAL, ENOMEM, ECUDA. */
+int lddmm_sl_transport(int nx, int ny, int nz, int nt, int interp, const float* vel,
+                       const float* field, int ncomp, int direction, float* out,
+                       void* stream);
+
+/* ---------------------------------------------------------------------- diagnostics */
+
+/* Kernel tracing (no counterpart in the paper; profiling support). The library counts
+ * every kernel it launches (process-wide, always on). With tracing enabled it also records
+ * a CUDA event pair around each launch on the launch's stream, with the launch's
+ * algorithmic bytes and flops; lddmm_trace_read synchronises those events and returns a
+ * JSON object {kernel: {launches, ms, bytes, flops}} summed since the last reset into
+ * buf (len bytes). With buf == NULL it returns the size needed; EINVAL if len is short. */
+long lddmm_launch_count(void);
+int lddmm_trace_enable(int on);
+int lddmm_trace_reset(void);
+int lddmm_trace_read(char* buf, int len);
+
+/* Message of the calling thread's most recent failure ("" if none). Never NULL. */
+const char* lddmm_last_error(void);
+
+/* Library version string, e.g. "lddmm-b300 0.1 sm_103a". */
+const char* lddmm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LDDMM_H */

@@ -1,0 +1,309 @@
+"""B300 (sm_103a) band-limited PDE-constrained LDDMM with SL-RK integration.
+
+Thin Python binding of the C ABI declared in ``include/lddmm.h`` (``liblddmm.so``, built
+in-tree by ``python -m paper_2006_06823_b300.build``). Every function here only marshals
+arguments: tensors are passed as device pointers with the current torch CUDA stream, and
+all arithmetic runs in the library's CUDA kernels. There is no CPU fallback: if the
+library is missing, the first call raises.
+
+Names follow the C entry points without their ``lddmm_`` prefix:
+``bl_project``, ``bl_include``, ``sl_characteristics``, ``sl_transport`` and the context
+methods ``set_images``, ``objective``, ``gradient``, ``hessian_matvec``, ``register``,
+``get_warped``.
+
+Conventions (see the header): images float32 ``[nz, ny, nx]``; vector fields float32
+``[3, nz, ny, nx]`` (component 0 = x); band-limited cubes complex64 ``[C, K, K, K]``
+indexed ``[comp, jz, jy, jx]`` with wavenumber ``k = j - K/2``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import re
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblddmm.so")
+HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "lddmm.h")
+
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ELINESEARCH = 0, -1, -2, -3, -4, -5, -6
+V_IMAGE, V_DEFSTATE = 1, 3
+INTERP_LINEAR, INTERP_CUBIC = 1, 3
+PREC_FP32, PREC_BF16X3 = 0, 1
+FORWARD, BACKWARD = 1, -1
+STOP_GTOL, STOP_MAXIT, STOP_LINESEARCH = 1, 2, 3
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("K", ctypes.c_int), ("nt", ctypes.c_int), ("variant", ctypes.c_int),
+                ("interp", ctypes.c_int), ("alpha", ctypes.c_double), ("s", ctypes.c_int),
+                ("sigma2", ctypes.c_double), ("max_gn", ctypes.c_int),
+                ("max_pcg", ctypes.c_int), ("gtol", ctypes.c_double),
+                ("precision", ctypes.c_int)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("gn_iters", ctypes.c_int), ("pcg_iters_total", ctypes.c_int),
+                ("stop_reason", ctypes.c_int), ("solves", ctypes.c_int),
+                ("E0", ctypes.c_double), ("E", ctypes.c_double), ("E_reg", ctypes.c_double),
+                ("E_data", ctypes.c_double), ("grad_rel_l2", ctypes.c_double),
+                ("grad_rel_inf", ctypes.c_double), ("mse_rel", ctypes.c_double),
+                ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class LddmmError(RuntimeError):
+    def __init__(self, code, message):
+        super().__init__(f"lddmm error {code}: {message}")
+        self.code = code
+
+
+_lib = None
+_P, _I, _D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+
+
+def _declare(lib):
+    sig = {
+        "lddmm_create": (_I, [ctypes.POINTER(Params), _P, ctypes.POINTER(_P)]),
+        "lddmm_destroy": (_I, [_P]),
+        "lddmm_set_images": (_I, [_P, _P, _P]),
+        "lddmm_set_images_host": (_I, [_P, _P, _P]),
+        "lddmm_objective": (_I, [_P, _P, _P, _P, _P]),
+        "lddmm_gradient": (_I, [_P, _P, _P, _P, _P, _P]),
+        "lddmm_hessian_matvec": (_I, [_P, _P, _P, _P]),
+        "lddmm_register": (_I, [_P, _P, _P, ctypes.POINTER(Report)]),
+        "lddmm_get_warped": (_I, [_P, _P]),
+        "lddmm_bl_project": (_I, [_I, _I, _I, _I, _P, _I, _P, _I, _P]),
+        "lddmm_bl_include": (_I, [_I, _I, _I, _I, _P, _I, _P, _I, _I, _I, _P]),
+        "lddmm_sl_characteristics": (_I, [_I, _I, _I, _P, _D, _I, _I, _P, _P]),
+        "lddmm_sl_transport": (_I, [_I, _I, _I, _I, _I, _P, _P, _I, _I, _P, _P]),
+        "lddmm_launch_count": (ctypes.c_long, []),
+        "lddmm_trace_enable": (_I, [_I]),
+        "lddmm_trace_reset": (_I, []),
+        "lddmm_trace_read": (_I, [ctypes.c_char_p, _I]),
+        "lddmm_last_error": (ctypes.c_char_p, []),
+        "lddmm_version": (ctypes.c_char_p, []),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+
+
+def load():
+    """Loads ``liblddmm.so`` (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                               "`python -m paper_2006_06823_b300.build`")
+        lib = ctypes.CDLL(LIB_PATH)
+        _declare(lib)
+        _lib = lib
+    return _lib
+
+
+def header_functions():
+    """Names of the functions declared in include/lddmm.h."""
+    text = open(HEADER_PATH).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lddmm_[a-z_]+)\s*\(", text)))
+
+
+def _check(rc):
+    if rc != 0:
+        raise LddmmError(rc, load().lddmm_last_error().decode())
+
+
+def _stream():
+    import torch
+    return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _ptr(t, dtype):
+    import torch
+    if not t.is_cuda:
+        raise ValueError("expected a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError("expected a contiguous tensor")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _f32(t):
+    import torch
+    return _ptr(t, torch.float32)
+
+
+def _c64(t):
+    import torch
+    return _ptr(t, torch.complex64)
+
+
+# ------------------------------------------------------------------ stand-alone operators
+
+def bl_project(f, K, precision=PREC_FP32, out=None):
+    """pi (Sec. 2.2): real fields ``[C, nz, ny, nx]`` -> Hermitian cubes ``[C, K, K, K]``."""
+    import torch
+    if f.dim() == 3:
+        f = f.unsqueeze(0)
+    C, nz, ny, nx = f.shape
+    if out is None:
+        out = torch.empty((C, K, K, K), dtype=torch.complex64, device=f.device)
+    _check(load().lddmm_bl_project(nx, ny, nz, K, _f32(f), C, _c64(out), precision, _stream()))
+    return out
+
+
+def bl_include(c, shape, deriv_axis=-1, bspline=False, precision=PREC_FP32, out=None):
+    """iota (Sec. 2.2): cubes ``[C, K, K, K]`` -> real fields ``[C, nz, ny, nx]``.
+
+    deriv_axis 0/1/2 synthesises the spectral derivative along x/y/z; bspline=True the
+    periodic cubic B-spline coefficients of the field.
+    """
+    import torch
+    if c.dim() == 3:
+        c = c.unsqueeze(0)
+    C, K = c.shape[0], c.shape[-1]
+    nz, ny, nx = shape
+    if out is None:
+        out = torch.empty((C, nz, ny, nx), dtype=torch.float32, device=c.device)
+    _check(load().lddmm_bl_include(nx, ny, nz, K, _c64(c), C, _f32(out), deriv_axis,
+                                   1 if bspline else 0, precision, _stream()))
+    return out
+
+
+def sl_characteristics(vel, dt, direction=FORWARD, interp=INTERP_LINEAR, out=None):
+    """Departure offsets (voxels) of one SL step for a voxel-unit velocity (Eqs. 40-42)."""
+    import torch
+    _, nz, ny, nx = vel.shape
+    if out is None:
+        out = torch.empty_like(vel)
+    _check(load().lddmm_sl_characteristics(nx, ny, nz, _f32(vel), float(dt), direction, interp,
+                                           _f32(out), _stream()))
+    return out
+
+
+def sl_transport(vel, field, nt, direction=FORWARD, interp=INTERP_LINEAR, out=None):
+    """nt SL steps of D_t u = 0 (Table 1 row 1) for fields ``[C, nz, ny, nx]``."""
+    import torch
+    squeeze = field.dim() == 3
+    if squeeze:
+        field = field.unsqueeze(0)
+    C, nz, ny, nx = field.shape
+    if out is None:
+        out = torch.empty_like(field)
+    _check(load().lddmm_sl_transport(nx, ny, nz, nt, interp, _f32(vel), _f32(field), C,
+                                     direction, _f32(out), _stream()))
+    return out[0] if squeeze else out
+
+
+# ------------------------------------------------------------------ the optimiser
+
+class Context:
+    """One registration problem on the current CUDA device and stream (lddmm_create)."""
+
+    def __init__(self, nx, ny, nz, K, nt=10, variant=V_DEFSTATE, interp=INTERP_LINEAR,
+                 alpha=0.0025, s=2, sigma2=0.01, max_gn=10, max_pcg=20, gtol=1e-3,
+                 precision=PREC_FP32):
+        self.params = Params(nx, ny, nz, K, nt, variant, interp, alpha, s, sigma2, max_gn,
+                             max_pcg, gtol, precision)
+        self.shape = (nz, ny, nx)
+        self.K = K
+        self._h = ctypes.c_void_p()
+        _check(load().lddmm_create(ctypes.byref(self.params), _stream(), ctypes.byref(self._h)))
+
+    def close(self):
+        if self._h:
+            load().lddmm_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def zeros_cube(self):
+        import torch
+        return torch.zeros((3, self.K, self.K, self.K), dtype=torch.complex64, device="cuda")
+
+    def set_images(self, I0, I1):
+        if I0.is_cuda:
+            _check(load().lddmm_set_images(self._h, _f32(I0), _f32(I1)))
+        else:
+            import torch
+            a = I0.to(torch.float32).contiguous()
+            b = I1.to(torch.float32).contiguous()
+            _check(load().lddmm_set_images_host(self._h, ctypes.c_void_p(a.data_ptr()),
+                                                ctypes.c_void_p(b.data_ptr())))
+
+    def objective(self, v):
+        E, Er, Ed = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(load().lddmm_objective(self._h, _c64(v), ctypes.byref(E), ctypes.byref(Er),
+                                      ctypes.byref(Ed)))
+        return E.value, Er.value, Ed.value
+
+    def gradient(self, v, out=None):
+        import torch
+        g = torch.empty_like(v) if out is None else out
+        E, Er, Ed = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+        _check(load().lddmm_gradient(self._h, _c64(v), _c64(g), ctypes.byref(E),
+                                     ctypes.byref(Er), ctypes.byref(Ed)))
+        return (E.value, Er.value, Ed.value), g
+
+    def hessian_matvec(self, v, dv, out=None):
+        import torch
+        h = torch.empty_like(dv) if out is None else out
+        _check(load().lddmm_hessian_matvec(self._h, _c64(v), _c64(dv), _c64(h)))
+        return h
+
+    def register(self, v=None, g_ref_norms=None):
+        """GN-Krylov registration; v (complex64 [3,K,K,K], device) is updated in place."""
+        v = self.zeros_cube() if v is None else v
+        rep = Report()
+        ref = None
+        if g_ref_norms is not None:
+            ref = (ctypes.c_double * 2)(*g_ref_norms)
+        _check(load().lddmm_register(self._h, _c64(v), ref, ctypes.byref(rep)))
+        return v, rep.as_dict()
+
+    def get_warped(self, out=None):
+        import torch
+        m = torch.empty(self.shape, dtype=torch.float32, device="cuda") if out is None else out
+        _check(load().lddmm_get_warped(self._h, _f32(m)))
+        return m
+
+
+# ------------------------------------------------------------------ tracing
+
+def launch_count():
+    """Kernels launched by the library so far in this process."""
+    return int(load().lddmm_launch_count())
+
+
+def trace_enable(on=True):
+    _check(load().lddmm_trace_enable(1 if on else 0))
+
+
+def trace_reset():
+    _check(load().lddmm_trace_reset())
+
+
+def trace_read():
+    """Per-kernel {launches, ms, bytes, flops} since the last reset (synchronises)."""
+    import json
+    lib = load()
+    size = lib.lddmm_trace_read(None, 0)
+    buf = ctypes.create_string_buffer(size + 64)
+    _check(lib.lddmm_trace_read(buf, size + 64))
+    return json.loads(buf.value.decode())
+

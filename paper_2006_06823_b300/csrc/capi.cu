@@ -1,0 +1,917 @@
+// C ABI of the library: contexts, the Gauss-Newton-Krylov driver and the stand-alone
+// operators. The driver follows Sec. 2.2 (Eqs. 13-14): v~ <- v~ + eps dv~, dv~ from PCG on
+// H dv~ = -g~ with preconditioner L~^{-1}; the gradient and Hessian-vector products of the
+// image-transport variant (Sec. 2.3.1) and the deformation-state variant (Sec. 2.3.3) are
+// assembled from the SL-RK sweeps of Table 1.
+//
+// Readings fixed here (the cited stopping rules are not written out in the paper):
+// PCG from zero with forcing eta = min(0.5, sqrt(||g||/||g_ref||)); Armijo backtracking
+// from eps = 1 (halving, at most 10 times, constant 1e-4); stop on ||g||/||g_ref|| <= gtol
+// with g_ref the gradient at v~ = 0; time integrals by the trapezoid rule on the nt + 1
+// nodes. FP64 holds every inner product, energy, comparison and the stopping test.
+#include "common.cuh"
+#include "lddmm.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+namespace lddmm {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+}  // namespace lddmm
+
+using namespace lddmm;
+
+#define TRY(expr)                      \
+    do {                               \
+        int rc__ = (expr);             \
+        if (rc__ != LDDMM_OK) return rc__; \
+    } while (0)
+
+struct lddmm_ctx {
+    lddmm_params p;
+    Grid g;
+    long n = 0;       // voxels
+    long kc = 0;      // K^3
+    int K = 0;
+    cudaStream_t st = nullptr;
+    double dt = 0;
+    float to_vox[3];
+    int sticky = LDDMM_OK;
+    std::vector<void*> allocs;
+    Twiddles tw;
+    SLArgs sl;
+
+    // images
+    float *I0 = nullptr, *I1 = nullptr, *I0c = nullptr;
+    // velocity fields of the current v~ (stationary)
+    float *v = nullptr, *vc = nullptr, *d = nullptr, *dc = nullptr;
+    float *Df = nullptr, *Db = nullptr, *gam = nullptr, *W = nullptr;
+    // trajectories
+    float2* ut = nullptr;   // DEFSTATE: u~_j, (nt+1) x 3 x K^3
+    float* Du = nullptr;    // DEFSTATE: (nt+1) x 9 planes
+    float* ms = nullptr;    // IMAGE: m_j, (nt+1) planes
+    float* Gm = nullptr;    // IMAGE: iota(grad~ pi(m_j)), (nt+1) x 3 planes
+    float *G = nullptr, *m1 = nullptr;
+    // work fields
+    float *fa = nullptr, *fb = nullptr, *fc = nullptr, *fd = nullptr, *acc = nullptr,
+          *dvsp = nullptr;
+    // spectral scratch
+    float2 *s1 = nullptr, *s2 = nullptr;
+    // cube vectors (3 x K^3 each)
+    enum { C_V, C_VT, C_G, C_R, C_Z, C_P, C_HP, C_X, C_T0, C_T1, C_T2, C_CUR, C_DV, C_NUM };
+    float2* cv[C_NUM];
+    // reductions
+    double* partials = nullptr;
+    double* dsc = nullptr;     // device scalars
+    double* hsc = nullptr;     // pinned host mirror
+    // cache
+    bool vel_valid = false;    // velocity fields + state of cv[C_CUR]
+    bool traj_valid = false;   // + Jacobians / grad m~ for the Hessian
+    int solves = 0;
+};
+
+static int fail(lddmm_ctx* c, int rc) {
+    if (c && c->sticky == LDDMM_OK) c->sticky = rc;
+    return rc;
+}
+
+static int dalloc(lddmm_ctx* c, void** p, size_t bytes) {
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        set_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
+        *p = nullptr;
+        return LDDMM_ENOMEM;
+    }
+    c->allocs.push_back(*p);
+    return LDDMM_OK;
+}
+template <class T>
+static int dalloc_t(lddmm_ctx* c, T** p, size_t count) {
+    return dalloc(c, reinterpret_cast<void**>(p), count * sizeof(T));
+}
+
+static int validate(const lddmm_params* p) {
+    if (!p) { set_error("params is NULL"); return LDDMM_EINVAL; }
+    if (p->nx < 4 || p->ny < 4 || p->nz < 4 || p->nx > 1024 || p->ny > 1024 || p->nz > 4096) {
+        set_error("grid must be 4..1024 (x, y) and 4..4096 (z) voxels per axis");
+        return LDDMM_EINVAL;
+    }
+    if (p->K < 4 || (p->K & 1) || p->K > 64 || p->K > p->nx || p->K > p->ny || p->K > p->nz) {
+        set_error("band K must be even, 4 <= K <= min(64, nx, ny, nz)");
+        return LDDMM_EINVAL;
+    }
+    if (p->nt < 1 || p->nt > 1000) { set_error("nt must be 1..1000"); return LDDMM_EINVAL; }
+    if (p->variant != LDDMM_V_IMAGE && p->variant != LDDMM_V_DEFSTATE) {
+        set_error("variant must be LDDMM_V_IMAGE or LDDMM_V_DEFSTATE");
+        return LDDMM_EINVAL;
+    }
+    if (p->interp != LDDMM_INTERP_LINEAR && p->interp != LDDMM_INTERP_CUBIC) {
+        set_error("interp must be LDDMM_INTERP_LINEAR or LDDMM_INTERP_CUBIC");
+        return LDDMM_EINVAL;
+    }
+    if (!(p->sigma2 > 0) || !(p->alpha >= 0) || p->s < 0 || p->s > 8) {
+        set_error("need sigma2 > 0, alpha >= 0, 0 <= s <= 8");
+        return LDDMM_EINVAL;
+    }
+    if (p->max_gn < 0 || p->max_pcg < 1 || !(p->gtol >= 0)) {
+        set_error("need max_gn >= 0, max_pcg >= 1, gtol >= 0");
+        return LDDMM_EINVAL;
+    }
+    if (p->precision != LDDMM_PREC_FP32 && p->precision != LDDMM_PREC_BF16X3) {
+        set_error("precision must be LDDMM_PREC_FP32 or LDDMM_PREC_BF16X3");
+        return LDDMM_EINVAL;
+    }
+    return LDDMM_OK;
+}
+
+// ------------------------------------------------------------------ small helpers
+static int project(lddmm_ctx* c, const float* f, int ncomp, float2* out) {
+    return bl_project(c->g, c->tw, f, c->n, ncomp, out, c->s1, c->s2, c->p.precision, c->st);
+}
+static int include(lddmm_ctx* c, const float2* cube, int ncomp, float* f, long fstride,
+                   int deriv, int bspline) {
+    return bl_include(c->g, c->tw, cube, ncomp, f, fstride, deriv, bspline, c->s1, c->s2,
+                      c->p.precision, c->st);
+}
+static bool cubic(const lddmm_ctx* c) { return c->p.interp == LDDMM_INTERP_CUBIC; }
+
+// Reads `count` device doubles from c->dsc into c->hsc (synchronises the stream).
+static int read_scalars(lddmm_ctx* c, int count) {
+    LDDMM_CUDA(cudaMemcpyAsync(c->hsc, c->dsc, count * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    LDDMM_CUDA(cudaStreamSynchronize(c->st));
+    for (int i = 0; i < count; ++i)
+        if (!std::isfinite(c->hsc[i])) {
+            set_error("non-finite value in an energy or inner product");
+            return LDDMM_ENONFINITE;
+        }
+    return LDDMM_OK;
+}
+
+static double trap_w(const lddmm_ctx* c, int j) {
+    return (j == 0 || j == c->p.nt) ? 0.5 * c->dt : c->dt;
+}
+
+// ------------------------------------------------------------------ velocity (Sec. 3.2)
+// v = iota(v~), d = iota(div~ v~), departure offsets forward / backward (Eqs. 40-42, 46),
+// the adjoint factor gam and the deformation-state source W.
+static int prepare_velocity(lddmm_ctx* c, const float2* vt) {
+    const long n = c->n;
+    TRY(include(c, vt, 3, c->v, n, -1, 0));
+    TRY(include(c, vt, 3, c->d, n, 3, 0));
+    const float* vsrc = c->v;
+    const float* dsrc = c->d;
+    if (cubic(c)) {
+        TRY(include(c, vt, 3, c->vc, n, -1, 1));
+        TRY(include(c, vt, 3, c->dc, n, 3, 1));
+        vsrc = c->vc;
+        dsrc = c->dc;
+    }
+    TRY(sl_characteristics(c->sl, vsrc, c->v, c->to_vox, -c->dt, c->Df, c->st));
+    TRY(sl_characteristics(c->sl, vsrc, c->v, c->to_vox, +c->dt, c->Db, c->st));
+    TRY(sl_prep_adjoint(c->sl, dsrc, c->d, c->Db, c->dt, c->gam, c->st));
+    if (c->p.variant == LDDMM_V_DEFSTATE)
+        TRY(sl_prep_source(c->sl, vsrc, c->v, c->Df, c->dt, c->W, c->st));
+    return LDDMM_OK;
+}
+
+// ------------------------------------------------------------------ state equations
+// DEFSTATE: D~_t u~ = v~ (Eq. 34): u~_{j+1} = pi(iota(u~_j) o X + W), u~_0 = 0.
+static int state_defstate(lddmm_ctx* c) {
+    const long kc3 = 3 * c->kc;
+    LDDMM_CUDA(cudaMemsetAsync(c->ut, 0, kc3 * sizeof(float2), c->st));
+    for (int j = 0; j < c->p.nt; ++j) {
+        TRY(include(c, c->ut + j * kc3, 3, c->fa, c->n, -1, cubic(c)));
+        TRY(sl_gather_add(c->sl, c->fa, c->Df, c->W, 3, c->fb, c->st));
+        TRY(project(c, c->fb, 3, c->ut + (j + 1) * kc3));
+    }
+    c->solves++;
+    return LDDMM_OK;
+}
+
+// IMAGE: D_t m = 0 (Eq. 17): m_{j+1} = m_j o X, m_0 = I0 (spatial).
+static int state_image(lddmm_ctx* c) {
+    const long n = c->n;
+    LDDMM_CUDA(cudaMemcpyAsync(c->ms, c->I0, n * sizeof(float), cudaMemcpyDeviceToDevice, c->st));
+    for (int j = 0; j < c->p.nt; ++j) {
+        const float* src = c->ms + j * n;
+        if (cubic(c)) {
+            TRY(bspline_prefilter(c->g, src, 1, c->fa, c->st));
+            src = c->fa;
+        }
+        TRY(sl_gather(c->sl, src, c->Df, 1, c->ms + (j + 1) * n, c->st));
+    }
+    c->solves++;
+    return LDDMM_OK;
+}
+
+// E_data = (1/sigma2) mean (m1 - I1)^2 into dsc[0]; DEFSTATE also forms m1, G and
+// (optionally) rho(1) = -(2/sigma2) r G into `rho`.
+static int data_term(lddmm_ctx* c, float* rho) {
+    const long n = c->n;
+    if (c->p.variant == LDDMM_V_DEFSTATE) {
+        TRY(include(c, c->ut + (long)c->p.nt * 3 * c->kc, 3, c->fa, n, -1, 0));
+        const float* I0src = cubic(c) ? c->I0c : c->I0;
+        TRY(sl_warp_image(c->sl, I0src, c->fa, c->to_vox, c->I1, c->p.sigma2, c->m1, c->G, rho,
+                          c->partials, c->st));
+        TRY(finalize_sum(c->partials, kReduceBlocks, c->dsc, c->st));
+    } else {
+        TRY(sum_sq_diff(c->ms + (long)c->p.nt * n, c->I1, n, c->partials, c->dsc, c->st));
+    }
+    return LDDMM_OK;
+}
+
+// E_reg = 1/2 <L~ v~, v~> into dsc[1]
+static int reg_term(lddmm_ctx* c, const float2* vt) {
+    float2* t = c->cv[lddmm_ctx::C_T0];
+    TRY(cube_apply_L(t, vt, 1.f, 0.f, nullptr, c->K, 3, c->p.alpha, c->p.s, 1, c->st));
+    TRY(dot_f2(t, vt, 3 * c->kc, c->partials, c->dsc + 1, c->st));
+    return LDDMM_OK;
+}
+
+// Makes the velocity fields and the state of vt current (copied into cv[C_CUR]).
+static int ensure_state(lddmm_ctx* c, const float2* vt, bool known_same) {
+    if (known_same && c->vel_valid) return LDDMM_OK;
+    float2* cur = c->cv[lddmm_ctx::C_CUR];
+    if (vt != cur)
+        LDDMM_CUDA(cudaMemcpyAsync(cur, vt, 3 * c->kc * sizeof(float2), cudaMemcpyDeviceToDevice, c->st));
+    c->vel_valid = false;
+    c->traj_valid = false;
+    TRY(prepare_velocity(c, cur));
+    if (c->p.variant == LDDMM_V_DEFSTATE) TRY(state_defstate(c));
+    else TRY(state_image(c));
+    c->vel_valid = true;
+    return LDDMM_OK;
+}
+
+// Spatial derivatives of the stored trajectory needed by gradient and Hessian.
+static int ensure_traj(lddmm_ctx* c) {
+    if (c->traj_valid) return LDDMM_OK;
+    const long n = c->n;
+    if (c->p.variant == LDDMM_V_DEFSTATE) {
+        for (int j = 0; j <= c->p.nt; ++j)
+            for (int b = 0; b < 3; ++b)
+                TRY(include(c, c->ut + (long)j * 3 * c->kc, 3, c->Du + (long)j * 9 * n + b * n,
+                            3 * n, b, 0));
+    } else {
+        float2* mt = c->cv[lddmm_ctx::C_T1];
+        for (int j = 0; j <= c->p.nt; ++j) {
+            TRY(project(c, c->ms + (long)j * n, 1, mt));
+            for (int b = 0; b < 3; ++b)
+                TRY(include(c, mt, 1, c->Gm + (long)j * 3 * n + b * n, n, b, 0));
+        }
+    }
+    c->traj_valid = true;
+    return LDDMM_OK;
+}
+
+// ------------------------------------------------------------------ adjoint sweeps
+// DEFSTATE (Eqs. 35, 37; Table 1 rows 4, 8), backward from rho(1) given spatially in `rho1`:
+// out = wL L~ base + sum_j w_j (rho~_j - pi((D iota u~_j)^T iota(rho~_j))).
+static int adjoint_defstate(lddmm_ctx* c, const float* rho1, const float2* base, float2* out) {
+    const long n = c->n, kc3 = 3 * c->kc;
+    const int nt = c->p.nt;
+    float2* rt = c->cv[lddmm_ctx::C_T1];     // rho~_j
+    float2* rsum = c->cv[lddmm_ctx::C_T2];   // sum_j w_j rho~_j
+    TRY(project(c, rho1, 3, rt));
+    TRY(cube_axpby(rsum, (float)trap_w(c, nt), rt, 0.f, nullptr, kc3, c->st));
+    TRY(include(c, rt, 3, c->fc, n, -1, 0));  // iota(rho~_nt) values
+    TRY(accum_JT(c->g, c->Du + (long)nt * 9 * n, c->fc, (float)trap_w(c, nt), c->acc, 1, c->st));
+    for (int j = nt - 1; j >= 0; --j) {
+        const float* src = c->fc;
+        if (cubic(c)) {
+            TRY(include(c, rt, 3, c->fa, n, -1, 1));
+            src = c->fa;
+        }
+        TRY(sl_gather_scale(c->sl, src, c->Db, c->gam, 3, c->fd, c->st));
+        TRY(project(c, c->fd, 3, rt));
+        TRY(cube_axpby(rsum, 1.f, rsum, (float)trap_w(c, j), rt, kc3, c->st));
+        TRY(include(c, rt, 3, c->fc, n, -1, 0));
+        TRY(accum_JT(c->g, c->Du + (long)j * 9 * n, c->fc, (float)trap_w(c, j), c->acc, 0, c->st));
+    }
+    c->solves++;
+    float2* pacc = c->cv[lddmm_ctx::C_T0];
+    TRY(project(c, c->acc, 3, pacc));
+    TRY(cube_axpby(rsum, 1.f, rsum, -1.f, pacc, kc3, c->st));
+    TRY(cube_apply_L(out, base, 1.f, 1.f, rsum, c->K, 3, c->p.alpha, c->p.s, 1, c->st));
+    return LDDMM_OK;
+}
+
+// IMAGE, gradient (Eqs. 15, 18; Table 1 row 2): spatial adjoint lambda from
+// lambda(1) = -(2/sigma2)(m1 - I1); g = L~ v~ + sum_j w_j pi(iota(pi(lambda_j)) Gm_j).
+static int gradient_image_adjoint(lddmm_ctx* c, const float2* vt, float2* g) {
+    const long n = c->n;
+    const int nt = c->p.nt;
+    float2* lt = c->cv[lddmm_ctx::C_T1];
+    TRY(scaled_diff(c->g, c->ms + (long)nt * n, c->I1, (float)(-2.0 / c->p.sigma2), c->fb, c->st));
+    for (int j = nt; j >= 0; --j) {
+        // fb holds lambda_j (spatial)
+        TRY(project(c, c->fb, 1, lt));
+        TRY(include(c, lt, 1, c->fc, n, -1, 0));
+        TRY(accum_sv(c->g, c->fc, c->Gm + (long)j * 3 * n, (float)trap_w(c, j), c->acc, j == nt,
+                     c->st));
+        if (j > 0) {
+            const float* src = c->fb;
+            if (cubic(c)) {
+                TRY(bspline_prefilter(c->g, c->fb, 1, c->fa, c->st));
+                src = c->fa;
+            }
+            TRY(sl_gather_scale(c->sl, src, c->Db, c->gam, 1, c->fd, c->st));
+            std::swap(c->fb, c->fd);
+        }
+    }
+    c->solves++;
+    float2* pacc = c->cv[lddmm_ctx::C_T0];
+    TRY(project(c, c->acc, 3, pacc));
+    TRY(cube_apply_L(g, vt, 1.f, 1.f, pacc, c->K, 3, c->p.alpha, c->p.s, 1, c->st));
+    return LDDMM_OK;
+}
+
+// ------------------------------------------------------------------ objective / gradient
+static int objective_impl(lddmm_ctx* c, const float2* vt, bool known_same, double* E, double* Er,
+                          double* Ed) {
+    TRY(ensure_state(c, vt, known_same));
+    TRY(data_term(c, nullptr));
+    TRY(reg_term(c, vt));
+    TRY(read_scalars(c, 2));
+    double ed = c->hsc[0] / (double)c->n / c->p.sigma2, er = 0.5 * c->hsc[1];
+    if (E) *E = er + ed;
+    if (Er) *Er = er;
+    if (Ed) *Ed = ed;
+    return LDDMM_OK;
+}
+
+static int gradient_impl(lddmm_ctx* c, const float2* vt, bool known_same, float2* g, double* E,
+                         double* Er, double* Ed) {
+    TRY(ensure_state(c, vt, known_same));
+    TRY(ensure_traj(c));
+    float2* cur = c->cv[lddmm_ctx::C_CUR];
+    if (c->p.variant == LDDMM_V_DEFSTATE) {
+        TRY(data_term(c, c->fb));
+        TRY(adjoint_defstate(c, c->fb, cur, g));
+    } else {
+        TRY(data_term(c, nullptr));
+        TRY(gradient_image_adjoint(c, cur, g));
+    }
+    TRY(reg_term(c, cur));
+    TRY(read_scalars(c, 2));
+    double ed = c->hsc[0] / (double)c->n / c->p.sigma2, er = 0.5 * c->hsc[1];
+    if (E) *E = er + ed;
+    if (Er) *Er = er;
+    if (Ed) *Ed = ed;
+    return LDDMM_OK;
+}
+
+// Gauss-Newton H dv~ at the current velocity (state and trajectory must be current).
+static int hessian_impl(lddmm_ctx* c, const float2* dvt, float2* out) {
+    TRY(ensure_traj(c));
+    const long n = c->n, kc3 = 3 * c->kc;
+    const int nt = c->p.nt;
+    TRY(include(c, dvt, 3, c->dvsp, n, -1, 0));
+    if (c->p.variant == LDDMM_V_DEFSTATE) {
+        // incremental state D~_t du~ = dv~ - D~u~ * dv~ (Eq. 36; Table 1 row 7)
+        float2* dut = c->cv[lddmm_ctx::C_T1];
+        float* Fold = c->fa;
+        float* Fnew = c->fd;
+        TRY(defstate_rhs(c->g, c->Du, c->dvsp, Fold, c->st));
+        LDDMM_CUDA(cudaMemsetAsync(dut, 0, kc3 * sizeof(float2), c->st));
+        for (int j = 0; j < nt; ++j) {
+            TRY(include(c, dut, 3, c->fb, n, -1, cubic(c)));
+            const float* Fsrc = Fold;
+            if (cubic(c)) {
+                TRY(bspline_prefilter(c->g, Fold, 3, c->acc, c->st));
+                Fsrc = c->acc;
+            }
+            TRY(sl_inc_defstate(c->sl, c->fb, c->Df, Fsrc, c->Du + (long)(j + 1) * 9 * n, c->dvsp,
+                                c->dt, c->fc, Fnew, c->st));
+            TRY(project(c, c->fc, 3, dut));
+            std::swap(Fold, Fnew);
+        }
+        c->solves++;
+        // drho(1) = pi(-(2/sigma2) dm1 G), dm1 = -G . iota(du~(1))
+        TRY(include(c, dut, 3, c->fa, n, -1, 0));
+        TRY(defstate_drho1(c->g, c->G, c->fa, c->p.sigma2, c->fb, c->st));
+        return adjoint_defstate(c, c->fb, dvt, out);
+    }
+    // IMAGE: incremental state D~_t dm~ = -grad~ m~ * dv~ (Eq. 19; Table 1 row 5)
+    float2* dmt = c->cv[lddmm_ctx::C_T1];
+    float* Fold = c->fa;
+    float* Fnew = c->fd;
+    TRY(image_rhs(c->g, c->Gm, c->dvsp, Fold, c->st));
+    LDDMM_CUDA(cudaMemsetAsync(dmt, 0, c->kc * sizeof(float2), c->st));
+    for (int j = 0; j < nt; ++j) {
+        TRY(include(c, dmt, 1, c->fb, n, -1, cubic(c)));
+        const float* Fsrc = Fold;
+        if (cubic(c)) {
+            TRY(bspline_prefilter(c->g, Fold, 1, c->acc, c->st));
+            Fsrc = c->acc;
+        }
+        TRY(sl_inc_image(c->sl, c->fb, c->Df, Fsrc, c->Gm + (long)(j + 1) * 3 * n, c->dvsp, c->dt,
+                         c->fc, Fnew, c->st));
+        TRY(project(c, c->fc, 1, dmt));
+        std::swap(Fold, Fnew);
+    }
+    c->solves++;
+    // incremental adjoint -D~_t dlambda~ = dlambda~ * div~ v~ (Eq. 20), dlambda~(1) = -(2/s2) dm~(1)
+    TRY(cube_axpby(dmt, (float)(-2.0 / c->p.sigma2), dmt, 0.f, nullptr, c->kc, c->st));
+    for (int j = nt; j >= 0; --j) {
+        TRY(include(c, dmt, 1, c->fc, n, -1, 0));
+        TRY(accum_sv(c->g, c->fc, c->Gm + (long)j * 3 * n, (float)trap_w(c, j), c->acc, j == nt,
+                     c->st));
+        if (j > 0) {
+            const float* src = c->fc;
+            if (cubic(c)) {
+                TRY(include(c, dmt, 1, c->fa, n, -1, 1));
+                src = c->fa;
+            }
+            TRY(sl_gather_scale(c->sl, src, c->Db, c->gam, 1, c->fd, c->st));
+            TRY(project(c, c->fd, 1, dmt));
+        }
+    }
+    c->solves++;
+    float2* pacc = c->cv[lddmm_ctx::C_T0];
+    TRY(project(c, c->acc, 3, pacc));
+    TRY(cube_apply_L(out, dvt, 1.f, 1.f, pacc, c->K, 3, c->p.alpha, c->p.s, 1, c->st));
+    return LDDMM_OK;
+}
+
+// device comparison of vt against the cached velocity: true if bitwise equal
+__global__ void k_cube_neq(const float2* a, const float2* b, long n, int* flag) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        float2 x = a[i], y = b[i];
+        if (__float_as_uint(x.x) != __float_as_uint(y.x) || __float_as_uint(x.y) != __float_as_uint(y.y))
+            *flag = 1;
+    }
+}
+
+static int same_as_current(lddmm_ctx* c, const float2* vt, bool* same) {
+    *same = false;
+    if (!c->vel_valid) return LDDMM_OK;
+    int* flag = reinterpret_cast<int*>(c->dsc + 8);
+    LDDMM_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), c->st));
+    long n = 3 * c->kc;
+    {
+        KTRACE("cube_neq", c->st, 16.0 * n, 0);
+        k_cube_neq<<<(int)((n + 255) / 256), 256, 0, c->st>>>(vt, c->cv[lddmm_ctx::C_CUR], n, flag);
+    }
+    LDDMM_CHECK_LAUNCH();
+    int h = 1;
+    LDDMM_CUDA(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    LDDMM_CUDA(cudaStreamSynchronize(c->st));
+    *same = (h == 0);
+    return LDDMM_OK;
+}
+
+// ------------------------------------------------------------------ GN-Krylov driver
+static double dot_host(lddmm_ctx* c, const float2* a, const float2* b, int* rc) {
+    *rc = dot_f2(a, b, 3 * c->kc, c->partials, c->dsc, c->st);
+    if (*rc) return 0;
+    *rc = read_scalars(c, 1);
+    return c->hsc[0];
+}
+
+static int register_impl(lddmm_ctx* c, float2* v_io, const double* gref_in, lddmm_report* rep) {
+    auto t0 = std::chrono::steady_clock::now();
+    const long kc3 = 3 * c->kc;
+    const int K = c->K;
+    std::memset(rep, 0, sizeof(*rep));
+    c->solves = 0;
+    int rc = 0;
+    float2* v = c->cv[lddmm_ctx::C_V];
+    float2* vtr = c->cv[lddmm_ctx::C_VT];
+    float2* g = c->cv[lddmm_ctx::C_G];
+    float2 *r = c->cv[lddmm_ctx::C_R], *z = c->cv[lddmm_ctx::C_Z], *pp = c->cv[lddmm_ctx::C_P];
+    float2 *Hp = c->cv[lddmm_ctx::C_HP], *x = c->cv[lddmm_ctx::C_X];
+    LDDMM_CUDA(cudaMemcpyAsync(v, v_io, kc3 * sizeof(float2), cudaMemcpyDeviceToDevice, c->st));
+    TRY(cube_hermitian(v, K, 3, c->st));
+
+    double gref2, grefi;
+    double E, Er, Ed;
+    if (gref_in) {
+        gref2 = gref_in[0];
+        grefi = gref_in[1];
+    } else {
+        // reference: the gradient at v~ = 0 (cold start)
+        TRY(max_abs_f2(v, kc3, c->partials, c->dsc, c->st));
+        TRY(read_scalars(c, 1));
+        if (c->hsc[0] != 0.0) {
+            LDDMM_CUDA(cudaMemsetAsync(vtr, 0, kc3 * sizeof(float2), c->st));
+            TRY(gradient_impl(c, vtr, false, g, nullptr, nullptr, nullptr));
+            gref2 = std::sqrt(dot_host(c, g, g, &rc));
+            TRY(rc);
+            TRY(max_abs_f2(g, kc3, c->partials, c->dsc, c->st));
+            TRY(read_scalars(c, 1));
+            grefi = c->hsc[0];
+        } else {
+            gref2 = grefi = -1;  // filled from the first gradient below
+        }
+    }
+    TRY(gradient_impl(c, v, false, g, &E, &Er, &Ed));
+    double gn = std::sqrt(dot_host(c, g, g, &rc));
+    TRY(rc);
+    if (gref2 < 0) {
+        gref2 = gn;
+        TRY(max_abs_f2(g, kc3, c->partials, c->dsc, c->st));
+        TRY(read_scalars(c, 1));
+        grefi = c->hsc[0];
+    }
+    if (!(gref2 > 0)) gref2 = 1.0;
+    if (!(grefi > 0)) grefi = 1.0;
+    rep->E0 = E;
+    int stop = LDDMM_STOP_MAXIT;
+    int gn_iters = 0;
+    for (int it = 0; it < c->p.max_gn; ++it) {
+        if (gn / gref2 <= c->p.gtol) {
+            stop = LDDMM_STOP_GTOL;
+            break;
+        }
+        const double eta = std::min(0.5, std::sqrt(gn / gref2));
+        // PCG on H x = -g with preconditioner L~^{-1}, x0 = 0
+        LDDMM_CUDA(cudaMemsetAsync(x, 0, kc3 * sizeof(float2), c->st));
+        TRY(cube_axpby(r, -1.f, g, 0.f, nullptr, kc3, c->st));
+        TRY(cube_apply_L(z, r, 1.f, 0.f, nullptr, K, 3, c->p.alpha, c->p.s, -1, c->st));
+        TRY(cube_axpby(pp, 1.f, z, 0.f, nullptr, kc3, c->st));
+        double rz = dot_host(c, r, z, &rc);
+        TRY(rc);
+        for (int i = 0; i < c->p.max_pcg; ++i) {
+            TRY(hessian_impl(c, pp, Hp));
+            rep->pcg_iters_total++;
+            double pHp = dot_host(c, pp, Hp, &rc);
+            TRY(rc);
+            if (pHp <= 0.0) {
+                if (i == 0)  // preconditioned steepest descent
+                    TRY(cube_apply_L(x, r, 1.f, 0.f, nullptr, K, 3, c->p.alpha, c->p.s, -1, c->st));
+                break;
+            }
+            const double a = rz / pHp;
+            TRY(cube_axpby(x, 1.f, x, (float)a, pp, kc3, c->st));
+            TRY(cube_axpby(r, 1.f, r, (float)-a, Hp, kc3, c->st));
+            double rn = std::sqrt(dot_host(c, r, r, &rc));
+            TRY(rc);
+            if (rn <= eta * gn) break;
+            TRY(cube_apply_L(z, r, 1.f, 0.f, nullptr, K, 3, c->p.alpha, c->p.s, -1, c->st));
+            double rz2 = dot_host(c, r, z, &rc);
+            TRY(rc);
+            TRY(cube_axpby(pp, 1.f, z, (float)(rz2 / rz), pp, kc3, c->st));
+            rz = rz2;
+        }
+        // Armijo backtracking on eps
+        const double slope = dot_host(c, g, x, &rc);
+        TRY(rc);
+        double eps = 1.0, Et = 0;
+        bool ok = false;
+        for (int ls = 0; ls <= 10; ++ls) {
+            TRY(cube_axpby(vtr, 1.f, v, (float)eps, x, kc3, c->st));
+            TRY(objective_impl(c, vtr, false, &Et, nullptr, nullptr));
+            if (Et <= E + 1e-4 * eps * slope) {
+                ok = true;
+                break;
+            }
+            eps *= 0.5;
+        }
+        if (!ok) {
+            stop = LDDMM_STOP_LINESEARCH;
+            break;
+        }
+        LDDMM_CUDA(cudaMemcpyAsync(v, vtr, kc3 * sizeof(float2), cudaMemcpyDeviceToDevice, c->st));
+        gn_iters = it + 1;
+        // the accepted trial's state is current: the gradient reuses it
+        TRY(gradient_impl(c, vtr, true, g, &E, &Er, &Ed));
+        gn = std::sqrt(dot_host(c, g, g, &rc));
+        TRY(rc);
+    }
+    if (stop == LDDMM_STOP_MAXIT && gn / gref2 <= c->p.gtol) stop = LDDMM_STOP_GTOL;
+    // if the line search failed, the state in the buffers belongs to a rejected trial
+    if (stop == LDDMM_STOP_LINESEARCH) TRY(objective_impl(c, v, false, &E, &Er, &Ed));
+    // MSE_rel = ||m1 - I1||^2 / ||I0 - I1||^2
+    const float* m1 = c->p.variant == LDDMM_V_DEFSTATE ? c->m1 : c->ms + (long)c->p.nt * c->n;
+    TRY(sum_sq_diff(m1, c->I1, c->n, c->partials, c->dsc, c->st));
+    TRY(sum_sq_diff(c->I0, c->I1, c->n, c->partials, c->dsc + 1, c->st));
+    TRY(max_abs_f2(g, kc3, c->partials, c->dsc + 2, c->st));
+    TRY(read_scalars(c, 3));
+    rep->mse_rel = c->hsc[1] > 0 ? c->hsc[0] / c->hsc[1] : 0.0;
+    rep->grad_rel_inf = c->hsc[2] / grefi;
+    rep->grad_rel_l2 = gn / gref2;
+    rep->E = E;
+    rep->E_reg = Er;
+    rep->E_data = Ed;
+    rep->gn_iters = gn_iters;
+    rep->stop_reason = stop;
+    rep->solves = c->solves;
+    LDDMM_CUDA(cudaMemcpyAsync(v_io, v, kc3 * sizeof(float2), cudaMemcpyDeviceToDevice, c->st));
+    LDDMM_CUDA(cudaStreamSynchronize(c->st));
+    rep->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    return LDDMM_OK;
+}
+
+// ================================================================== the C ABI
+static int ctx_alloc(lddmm_ctx* c) {
+    const long n = c->n, kc3 = 3 * c->kc;
+    const int nt = c->p.nt;
+    const bool def = c->p.variant == LDDMM_V_DEFSTATE, cub = cubic(c);
+    float* twm = nullptr;
+    TRY(dalloc_t(c, &twm, twiddle_floats(c->g, c->K)));
+    TRY(twiddle_init(c->g, c->K, twm, c->tw, c->st));
+    TRY(dalloc_t(c, &c->I0, n));
+    TRY(dalloc_t(c, &c->I1, n));
+    if (cub) TRY(dalloc_t(c, &c->I0c, n));
+    TRY(dalloc_t(c, &c->v, 3 * n));
+    TRY(dalloc_t(c, &c->d, n));
+    if (cub) {
+        TRY(dalloc_t(c, &c->vc, 3 * n));
+        TRY(dalloc_t(c, &c->dc, n));
+    }
+    TRY(dalloc_t(c, &c->Df, 3 * n));
+    TRY(dalloc_t(c, &c->Db, 3 * n));
+    TRY(dalloc_t(c, &c->gam, n));
+    if (def) {
+        TRY(dalloc_t(c, &c->W, 3 * n));
+        TRY(dalloc_t(c, &c->ut, (size_t)(nt + 1) * kc3));
+        TRY(dalloc_t(c, &c->Du, (size_t)(nt + 1) * 9 * n));
+        TRY(dalloc_t(c, &c->G, 3 * n));
+        TRY(dalloc_t(c, &c->m1, n));
+    } else {
+        TRY(dalloc_t(c, &c->ms, (size_t)(nt + 1) * n));
+        TRY(dalloc_t(c, &c->Gm, (size_t)(nt + 1) * 3 * n));
+    }
+    for (float** f : {&c->fa, &c->fb, &c->fc, &c->fd, &c->acc, &c->dvsp}) TRY(dalloc_t(c, f, 3 * n));
+    long se = spectral_scratch_elems(c->g, c->K, 3);
+    TRY(dalloc_t(c, &c->s1, se));
+    TRY(dalloc_t(c, &c->s2, se));
+    for (int i = 0; i < lddmm_ctx::C_NUM; ++i) {
+        TRY(dalloc_t(c, &c->cv[i], kc3));
+        LDDMM_CUDA(cudaMemsetAsync(c->cv[i], 0, kc3 * sizeof(float2), c->st));
+    }
+    TRY(dalloc_t(c, &c->partials, kReduceBlocks));
+    TRY(dalloc_t(c, &c->dsc, 16));
+    LDDMM_CUDA(cudaMallocHost(reinterpret_cast<void**>(&c->hsc), 16 * sizeof(double)));
+    return LDDMM_OK;
+}
+
+static int check_ctx(lddmm_ctx* c) {
+    if (!c) { set_error("context is NULL"); return LDDMM_EINVAL; }
+    if (c->sticky != LDDMM_OK) {
+        set_error("context is in an error state (" + std::to_string(c->sticky) + ")");
+        return c->sticky;
+    }
+    return LDDMM_OK;
+}
+
+#define CTX_CALL(c, expr)                 \
+    do {                                  \
+        int rc0__ = check_ctx(c);         \
+        if (rc0__) return rc0__;          \
+        int rc1__ = (expr);               \
+        if (rc1__) return fail(c, rc1__); \
+        return LDDMM_OK;                  \
+    } while (0)
+
+static int after_images(lddmm_ctx* c) {
+    c->vel_valid = c->traj_valid = false;
+    if (cubic(c)) TRY(bspline_prefilter(c->g, c->I0, 1, c->I0c, c->st));
+    return LDDMM_OK;
+}
+
+extern "C" {
+
+const char* lddmm_last_error(void) { return g_last_error.c_str(); }
+
+const char* lddmm_version(void) { return "lddmm-b300 0.1 sm_103a"; }
+
+int lddmm_create(const lddmm_params* params, void* stream, lddmm_ctx** out) {
+    if (!out) { set_error("out is NULL"); return LDDMM_EINVAL; }
+    *out = nullptr;
+    TRY(validate(params));
+    lddmm_ctx* c = new lddmm_ctx();
+    c->p = *params;
+    c->g = Grid{params->nx, params->ny, params->nz};
+    c->n = c->g.ntot();
+    c->K = params->K;
+    c->kc = (long)c->K * c->K * c->K;
+    c->st = static_cast<cudaStream_t>(stream);
+    c->dt = 1.0 / params->nt;
+    c->to_vox[0] = (float)(params->nx / (2.0 * M_PI));
+    c->to_vox[1] = (float)(params->ny / (2.0 * M_PI));
+    c->to_vox[2] = (float)(params->nz / (2.0 * M_PI));
+    c->sl = SLArgs{c->g, params->interp};
+    int rc = ctx_alloc(c);
+    if (rc) {
+        std::string msg = g_last_error;
+        lddmm_destroy(c);
+        set_error(msg);
+        return rc;
+    }
+    *out = c;
+    return LDDMM_OK;
+}
+
+int lddmm_destroy(lddmm_ctx* c) {
+    if (!c) return LDDMM_OK;
+    if (c->st || true) cudaStreamSynchronize(c->st);
+    for (void* p : c->allocs) cudaFree(p);
+    if (c->hsc) cudaFreeHost(c->hsc);
+    delete c;
+    return LDDMM_OK;
+}
+
+int lddmm_set_images(lddmm_ctx* c, const float* I0, const float* I1) {
+    if (!I0 || !I1) { set_error("image pointer is NULL"); return LDDMM_EINVAL; }
+    CTX_CALL(c, ([&]() -> int {
+        LDDMM_CUDA(cudaMemcpyAsync(c->I0, I0, c->n * sizeof(float), cudaMemcpyDeviceToDevice, c->st));
+        LDDMM_CUDA(cudaMemcpyAsync(c->I1, I1, c->n * sizeof(float), cudaMemcpyDeviceToDevice, c->st));
+        return after_images(c);
+    })());
+}
+
+int lddmm_set_images_host(lddmm_ctx* c, const float* I0, const float* I1) {
+    if (!I0 || !I1) { set_error("image pointer is NULL"); return LDDMM_EINVAL; }
+    CTX_CALL(c, ([&]() -> int {
+        LDDMM_CUDA(cudaMemcpyAsync(c->I0, I0, c->n * sizeof(float), cudaMemcpyHostToDevice, c->st));
+        LDDMM_CUDA(cudaMemcpyAsync(c->I1, I1, c->n * sizeof(float), cudaMemcpyHostToDevice, c->st));
+        return after_images(c);
+    })());
+}
+
+int lddmm_objective(lddmm_ctx* c, const float* v, double* E, double* Er, double* Ed) {
+    if (!v) { set_error("v is NULL"); return LDDMM_EINVAL; }
+    CTX_CALL(c, objective_impl(c, reinterpret_cast<const float2*>(v), false, E, Er, Ed));
+}
+
+int lddmm_gradient(lddmm_ctx* c, const float* v, float* g, double* E, double* Er, double* Ed) {
+    if (!v || !g) { set_error("v or g is NULL"); return LDDMM_EINVAL; }
+    CTX_CALL(c, gradient_impl(c, reinterpret_cast<const float2*>(v), false,
+                              reinterpret_cast<float2*>(g), E, Er, Ed));
+}
+
+int lddmm_hessian_matvec(lddmm_ctx* c, const float* v, const float* dv, float* Hdv) {
+    if (!v || !dv || !Hdv) { set_error("v, dv or Hdv is NULL"); return LDDMM_EINVAL; }
+    CTX_CALL(c, ([&]() -> int {
+        const float2* vt = reinterpret_cast<const float2*>(v);
+        bool same = false;
+        TRY(same_as_current(c, vt, &same));
+        if (!same) TRY(ensure_state(c, vt, false));
+        return hessian_impl(c, reinterpret_cast<const float2*>(dv), reinterpret_cast<float2*>(Hdv));
+    })());
+}
+
+int lddmm_register(lddmm_ctx* c, float* v_inout, const double* g_ref_norms, lddmm_report* rep) {
+    if (!v_inout || !rep) { set_error("v_inout or report is NULL"); return LDDMM_EINVAL; }
+    CTX_CALL(c, register_impl(c, reinterpret_cast<float2*>(v_inout), g_ref_norms, rep));
+}
+
+int lddmm_get_warped(lddmm_ctx* c, float* m1) {
+    if (!m1) { set_error("m1 is NULL"); return LDDMM_EINVAL; }
+    CTX_CALL(c, ([&]() -> int {
+        if (!c->vel_valid) { set_error("no state solved yet"); return LDDMM_EINVAL; }
+        if (c->p.variant == LDDMM_V_DEFSTATE) TRY(data_term(c, nullptr));
+        const float* src = c->p.variant == LDDMM_V_DEFSTATE ? c->m1 : c->ms + (long)c->p.nt * c->n;
+        LDDMM_CUDA(cudaMemcpyAsync(m1, src, c->n * sizeof(float), cudaMemcpyDeviceToDevice, c->st));
+        return LDDMM_OK;
+    })());
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ stand-alone operators
+// Scratch comes from CUDA's stream-ordered pool and is released on the same stream.
+struct PoolScratch {
+    cudaStream_t st;
+    std::vector<void*> ptrs;
+    explicit PoolScratch(cudaStream_t s) : st(s) {}
+    ~PoolScratch() {
+        for (void* p : ptrs) cudaFreeAsync(p, st);
+    }
+    template <class T>
+    int get(T** p, size_t count) {
+        cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(p), count * sizeof(T), st);
+        if (e != cudaSuccess) {
+            set_error(std::string("cudaMallocAsync: ") + cudaGetErrorString(e));
+            *p = nullptr;
+            return LDDMM_ENOMEM;
+        }
+        ptrs.push_back(*p);
+        return LDDMM_OK;
+    }
+};
+
+static int check_grid(int nx, int ny, int nz) {
+    if (nx < 2 || ny < 2 || nz < 2 || nx > 1024 || ny > 1024 || nz > 4096) {
+        set_error("grid must be 2..1024 (x, y) and 2..4096 (z) voxels per axis");
+        return LDDMM_EINVAL;
+    }
+    return LDDMM_OK;
+}
+
+extern "C" {
+
+int lddmm_bl_project(int nx, int ny, int nz, int K, const float* f, int ncomp, float* c,
+                     int precision, void* stream) {
+    TRY(check_grid(nx, ny, nz));
+    if (!f || !c || ncomp < 1) { set_error("bl_project: null pointer or ncomp < 1"); return LDDMM_EINVAL; }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Grid g{nx, ny, nz};
+    PoolScratch ps(st);
+    float* twm;
+    float2 *s1, *s2;
+    TRY(ps.get(&twm, twiddle_floats(g, K)));
+    long se = spectral_scratch_elems(g, K, ncomp);
+    TRY(ps.get(&s1, se));
+    TRY(ps.get(&s2, se));
+    Twiddles tw;
+    TRY(twiddle_init(g, K, twm, tw, st));
+    return bl_project(g, tw, f, g.ntot(), ncomp, reinterpret_cast<float2*>(c), s1, s2, precision, st);
+}
+
+int lddmm_bl_include(int nx, int ny, int nz, int K, const float* c, int ncomp, float* f,
+                     int deriv_axis, int bspline, int precision, void* stream) {
+    TRY(check_grid(nx, ny, nz));
+    if (!f || !c || ncomp < 1) { set_error("bl_include: null pointer or ncomp < 1"); return LDDMM_EINVAL; }
+    if (deriv_axis < -1 || deriv_axis > 2) { set_error("bl_include: deriv_axis must be -1..2"); return LDDMM_EINVAL; }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Grid g{nx, ny, nz};
+    PoolScratch ps(st);
+    float* twm;
+    float2 *s1, *s2;
+    TRY(ps.get(&twm, twiddle_floats(g, K)));
+    long se = spectral_scratch_elems(g, K, ncomp);
+    TRY(ps.get(&s1, se));
+    TRY(ps.get(&s2, se));
+    Twiddles tw;
+    TRY(twiddle_init(g, K, twm, tw, st));
+    return bl_include(g, tw, reinterpret_cast<const float2*>(c), ncomp, f, g.ntot(), deriv_axis,
+                      bspline ? 1 : 0, s1, s2, precision, st);
+}
+
+int lddmm_sl_characteristics(int nx, int ny, int nz, const float* vel, double dt, int direction,
+                             int interp, float* offsets, void* stream) {
+    TRY(check_grid(nx, ny, nz));
+    if (!vel || !offsets) { set_error("sl_characteristics: null pointer"); return LDDMM_EINVAL; }
+    if (interp != 1 && interp != 3) { set_error("interp must be 1 or 3"); return LDDMM_EINVAL; }
+    if (direction != 1 && direction != -1) { set_error("direction must be +1 or -1"); return LDDMM_EINVAL; }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Grid g{nx, ny, nz};
+    SLArgs a{g, interp};
+    const float one[3] = {1.f, 1.f, 1.f};
+    const float* vsrc = vel;
+    PoolScratch ps(st);
+    if (interp == 3) {
+        float* vc;
+        TRY(ps.get(&vc, 3 * g.ntot()));
+        TRY(bspline_prefilter(g, vel, 3, vc, st));
+        vsrc = vc;
+    }
+    return sl_characteristics(a, vsrc, vel, one, direction > 0 ? -dt : dt, offsets, st);
+}
+
+int lddmm_sl_transport(int nx, int ny, int nz, int nt, int interp, const float* vel,
+                       const float* field, int ncomp, int direction, float* out, void* stream) {
+    TRY(check_grid(nx, ny, nz));
+    if (!vel || !field || !out || ncomp < 1) { set_error("sl_transport: null pointer or ncomp < 1"); return LDDMM_EINVAL; }
+    if (nt < 1) { set_error("sl_transport: nt must be >= 1"); return LDDMM_EINVAL; }
+    if (interp != 1 && interp != 3) { set_error("interp must be 1 or 3"); return LDDMM_EINVAL; }
+    if (direction != 1 && direction != -1) { set_error("direction must be +1 or -1"); return LDDMM_EINVAL; }
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    Grid g{nx, ny, nz};
+    const long n = g.ntot();
+    SLArgs a{g, interp};
+    PoolScratch ps(st);
+    float *D, *tmp, *coef = nullptr;
+    TRY(ps.get(&D, 3 * n));
+    TRY(ps.get(&tmp, (size_t)ncomp * n));
+    const float one[3] = {1.f, 1.f, 1.f};
+    const double dt = 1.0 / nt;
+    const float* vsrc = vel;
+    if (interp == 3) {
+        TRY(ps.get(&coef, (size_t)std::max(ncomp, 3) * n));
+        TRY(bspline_prefilter(g, vel, 3, coef, st));
+        vsrc = coef;
+    }
+    TRY(sl_characteristics(a, vsrc, vel, one, direction > 0 ? -dt : dt, D, st));
+    // ping-pong between out and tmp so that the last step lands in out
+    const float* cur = field;
+    for (int j = 0; j < nt; ++j) {
+        const bool last_to_out = ((nt - 1 - j) % 2) == 0;
+        float* dst = last_to_out ? out : tmp;
+        const float* src = cur;
+        if (interp == 3) {
+            TRY(bspline_prefilter(g, cur, ncomp, coef, st));
+            src = coef;
+        } else if (src == dst) {
+            LDDMM_CUDA(cudaMemcpyAsync(tmp == dst ? out : tmp, cur, (size_t)ncomp * n * sizeof(float),
+                                       cudaMemcpyDeviceToDevice, st));
+            src = tmp == dst ? out : tmp;
+        }
+        TRY(sl_gather(a, src, D, ncomp, dst, st));
+        cur = dst;
+    }
+    return LDDMM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,148 @@
+// Internal declarations shared by the library's translation units (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+
+#include "lddmm.h"
+
+namespace lddmm {
+
+// Records `msg` as the calling thread's last error (read through lddmm_last_error()).
+void set_error(const std::string& msg);
+
+#define LDDMM_CUDA(expr)                                                              \
+    do {                                                                              \
+        cudaError_t e__ = (expr);                                                     \
+        if (e__ != cudaSuccess) {                                                     \
+            ::lddmm::set_error(std::string(#expr) + ": " + cudaGetErrorString(e__)); \
+            return LDDMM_ECUDA;                                                       \
+        }                                                                             \
+    } while (0)
+
+#define LDDMM_CHECK_LAUNCH() LDDMM_CUDA(cudaGetLastError())
+
+// Scope around one kernel launch: counts it and, when tracing is on, brackets it with CUDA
+// events on `st`, recording the launch's algorithmic bytes and flops.
+class KTrace {
+  public:
+    KTrace(const char* name, cudaStream_t st, double bytes, double flops = 0.0);
+    ~KTrace();
+    KTrace(const KTrace&) = delete;
+    KTrace& operator=(const KTrace&) = delete;
+
+  private:
+    const char* name_;
+    cudaStream_t st_;
+    double bytes_, flops_;
+    void* a_;
+};
+#define KTRACE(name, st, bytes, flops) ::lddmm::KTrace ktrace__(name, st, (double)(bytes), (double)(flops))
+
+struct Grid {
+    int nx, ny, nz;
+    __host__ __device__ long ntot() const { return (long)nx * ny * nz; }
+};
+
+// Twiddle tables [K][n] per axis: cos/sin(2 pi k j / n) for k = slot - K/2, FP64-evaluated,
+// stored FP32. All six tables sit in one allocation of table_floats(grid, K) floats.
+struct Twiddles {
+    int K;
+    const float *cx, *sx, *cy, *sy, *cz, *sz;
+};
+long twiddle_floats(const Grid& g, int K);
+// Fills `mem` (twiddle_floats floats, device) and points `tw` into it.
+int twiddle_init(const Grid& g, int K, float* mem, Twiddles& tw, cudaStream_t st);
+
+// float2 elements of each of the two scratch buffers that bl_project / bl_include need
+// for `ncomp` components.
+long spectral_scratch_elems(const Grid& g, int K, int ncomp);
+
+// pi: ncomp fields (component stride fstride floats) -> ncomp cubes (stride K^3 float2).
+int bl_project(const Grid& g, const Twiddles& tw, const float* f, long fstride, int ncomp,
+               float2* c, float2* s1, float2* s2, int precision, cudaStream_t st);
+
+// iota: ncomp cubes -> ncomp fields (component stride fstride). deriv_axis -1 none,
+// 0..2 spectral derivative, 3 divergence of a 3-component cube (writes one field).
+int bl_include(const Grid& g, const Twiddles& tw, const float2* c, int ncomp, float* f,
+               long fstride, int deriv_axis, int bspline, float2* s1, float2* s2,
+               int precision, cudaStream_t st);
+
+// ---------------------------------------------------------------- K^3 cube kernels
+// out = a*x + b*y over n complex values (x or y may be null => treated as zero).
+int cube_axpby(float2* out, float a, const float2* x, float b, const float2* y, long n,
+               cudaStream_t st);
+// out = wL * L~ x + a * y  (y may be null); mode 1: L~, mode -1: L~^{-1} (y ignored).
+int cube_apply_L(float2* out, const float2* x, float wL, float a, const float2* y, int K,
+                 int ncomp, double alpha, int s, int mode, cudaStream_t st);
+// Hermitian symmetrisation of ncomp cubes in place: c <- (c + conj c_{-k}) / 2, slot-0
+// planes zeroed.
+int cube_hermitian(float2* c, int K, int ncomp, cudaStream_t st);
+
+// FP64 reductions into device doubles (deterministic two-pass).
+int dot_f2(const float2* a, const float2* b, long n, double* partials, double* out,
+           cudaStream_t st);
+int max_abs_f2(const float2* a, long n, double* partials, double* out, cudaStream_t st);
+constexpr int kReduceBlocks = 296;  // 2 x 148 SMs
+
+// ---------------------------------------------------------------- SL kernels (sl.cu)
+struct SLArgs {
+    Grid g;
+    int interp;  // 1 or 3
+};
+// D = offsets of departure points; vsrc = samples (linear) or spline coefficients (cubic)
+// of the velocity, vval its samples; scale[a] converts component a to voxels.
+int sl_characteristics(const SLArgs& a, const float* vsrc, const float* vval,
+                       const float scale[3], double dt_signed, float* D, cudaStream_t st);
+// out[c] = src[c] o (x + D), ncomp components of stride g.ntot().
+int sl_gather(const SLArgs& a, const float* src, const float* D, int ncomp, float* out,
+              cudaStream_t st);
+// out[c] = src[c] o (x + D) * gam(x)
+int sl_gather_scale(const SLArgs& a, const float* src, const float* D, const float* gam,
+                    int ncomp, float* out, cudaStream_t st);
+// out[c] = src[c] o (x + D) + add[c](x)
+int sl_gather_add(const SLArgs& a, const float* src, const float* D, const float* add,
+                  int ncomp, float* out, cudaStream_t st);
+// gam = 1 + dt/2 (d(X+) + (1 + dt d(X+)) d(x)),  W = dt/2 (v(X) + v(x))
+int sl_prep_adjoint(const SLArgs& a, const float* dsrc, const float* dval, const float* Dp,
+                    double dt, float* gam, cudaStream_t st);
+int sl_prep_source(const SLArgs& a, const float* vsrc, const float* vval, const float* D,
+                   double dt, float* W, cudaStream_t st);
+// m1 = I0 o (x - u1*to_vox), G = grad(I0 interpolant) there (physical units),
+// rho = -(2/sigma2) (m1 - I1) G, partial sums of (m1 - I1)^2 (kReduceBlocks doubles).
+int sl_warp_image(const SLArgs& a, const float* I0src, const float* u1, const float to_vox[3],
+                  const float* I1, double sigma2, float* m1, float* G, float* rho,
+                  double* partials, cudaStream_t st);
+// incremental deformation state step: Fnew_a = dv_a - sum_b Du[a*3+b] dv_b;
+// out = U o X + dt/2 (Fold o X + Fnew)
+int sl_inc_defstate(const SLArgs& a, const float* U, const float* D, const float* Fold,
+                    const float* Du, const float* dv, double dt, float* out, float* Fnew,
+                    cudaStream_t st);
+// Fnew_a = dv_a - sum_b Du[a*3+b] dv_b (the first node)
+int defstate_rhs(const Grid& g, const float* Du, const float* dv, float* F, cudaStream_t st);
+// drho = -(2/sigma2) dm1 G with dm1 = -G . du1
+int defstate_drho1(const Grid& g, const float* G, const float* du1, double sigma2, float* drho,
+                   cudaStream_t st);
+// acc_b (+)= w sum_a Du[a*3+b] R_a   (init != 0 overwrites)
+int accum_JT(const Grid& g, const float* Du, const float* R, float w, float* acc, int init,
+             cudaStream_t st);
+// x_out = a * x (n floats)
+int scale_field(float* out, const float* in, float a, long n, cudaStream_t st);
+// partial sums over (a - b)^2 into kReduceBlocks doubles, then final into out
+int sum_sq_diff(const float* a, const float* b, long n, double* partials, double* out,
+                cudaStream_t st);
+int finalize_sum(const double* partials, int n, double* out, cudaStream_t st);
+// periodic cubic B-spline coefficients of ncomp fields (out may alias in)
+int bspline_prefilter(const Grid& g, const float* in, int ncomp, float* out, cudaStream_t st);
+// image variant: incremental state step, its first right-hand side, accumulation, lambda(1)
+int sl_inc_image(const SLArgs& a, const float* U, const float* D, const float* Fold,
+                 const float* Gm, const float* dv, double dt, float* out, float* Fnew,
+                 cudaStream_t st);
+int image_rhs(const Grid& g, const float* Gm, const float* dv, float* F, cudaStream_t st);
+int accum_sv(const Grid& g, const float* s, const float* Gm, float w, float* acc, int init,
+             cudaStream_t st);
+int scaled_diff(const Grid& g, const float* a, const float* b, float coef, float* out,
+                cudaStream_t st);
+
+}  // namespace lddmm

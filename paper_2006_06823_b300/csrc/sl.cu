@@ -1,0 +1,734 @@
+// Semi-Lagrangian kernels (Sec. 3): departure points (Eqs. 40-42), transport along them
+// with trilinear or cubic B-spline interpolation, the Heun (SL-RK) step forms of Table 1,
+// the warped source image with its gradient, and the periodic B-spline prefilter.
+//
+// Offsets D = X - x are stored per voxel in voxels (three planes). A query point is the
+// grid index j plus D; the cell is j + floor(D) and the fraction D - floor(D), which keeps
+// the fraction at the precision of the (small) offset. Indices wrap periodically. Offsets
+// are clamped to +-2^20 voxels before use, so non-finite or huge inputs can never address
+// memory outside the field.
+#include "common.cuh"
+#include "lddmm.h"
+
+namespace lddmm {
+
+static inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
+
+__device__ __forceinline__ float clampD(float d) { return fminf(fmaxf(d, -1048576.f), 1048576.f); }
+
+__device__ __forceinline__ int wrapi(int i, int n) {
+    if ((unsigned)i >= (unsigned)n) {
+        i %= n;
+        if (i < 0) i += n;
+    }
+    return i;
+}
+
+// Trilinear cell: corner offsets and fractions.
+struct LinCell {
+    long x0, x1, y0, y1, z0, z1;
+    float tx, ty, tz;
+};
+
+__device__ __forceinline__ void lin_axis(int j, float D, int n, long mul, long& a0, long& a1,
+                                         float& t) {
+    D = clampD(D);
+    float fl = floorf(D);
+    t = D - fl;
+    int i = wrapi(j + (int)fl, n);
+    int i1 = i + 1 == n ? 0 : i + 1;
+    a0 = (long)i * mul;
+    a1 = (long)i1 * mul;
+}
+
+__device__ __forceinline__ LinCell lin_cell(const Grid& g, int x, int y, int z, float dx, float dy,
+                                            float dz) {
+    LinCell c;
+    lin_axis(x, dx, g.nx, 1, c.x0, c.x1, c.tx);
+    lin_axis(y, dy, g.ny, g.nx, c.y0, c.y1, c.ty);
+    lin_axis(z, dz, g.nz, (long)g.nx * g.ny, c.z0, c.z1, c.tz);
+    return c;
+}
+
+__device__ __forceinline__ float lin_eval(const float* __restrict__ f, const LinCell& c) {
+    float v000 = __ldg(f + c.z0 + c.y0 + c.x0), v001 = __ldg(f + c.z0 + c.y0 + c.x1);
+    float v010 = __ldg(f + c.z0 + c.y1 + c.x0), v011 = __ldg(f + c.z0 + c.y1 + c.x1);
+    float v100 = __ldg(f + c.z1 + c.y0 + c.x0), v101 = __ldg(f + c.z1 + c.y0 + c.x1);
+    float v110 = __ldg(f + c.z1 + c.y1 + c.x0), v111 = __ldg(f + c.z1 + c.y1 + c.x1);
+    float a00 = fmaf(c.tx, v001 - v000, v000), a01 = fmaf(c.tx, v011 - v010, v010);
+    float a10 = fmaf(c.tx, v101 - v100, v100), a11 = fmaf(c.tx, v111 - v110, v110);
+    float b0 = fmaf(c.ty, a01 - a00, a00), b1 = fmaf(c.ty, a11 - a10, a10);
+    return fmaf(c.tz, b1 - b0, b0);
+}
+
+// value and gradient (d/dx, d/dy, d/dz in voxel units) of the trilinear interpolant
+__device__ __forceinline__ float lin_eval_grad(const float* __restrict__ f, const LinCell& c,
+                                               float& gx, float& gy, float& gz) {
+    float v000 = __ldg(f + c.z0 + c.y0 + c.x0), v001 = __ldg(f + c.z0 + c.y0 + c.x1);
+    float v010 = __ldg(f + c.z0 + c.y1 + c.x0), v011 = __ldg(f + c.z0 + c.y1 + c.x1);
+    float v100 = __ldg(f + c.z1 + c.y0 + c.x0), v101 = __ldg(f + c.z1 + c.y0 + c.x1);
+    float v110 = __ldg(f + c.z1 + c.y1 + c.x0), v111 = __ldg(f + c.z1 + c.y1 + c.x1);
+    float a00 = fmaf(c.tx, v001 - v000, v000), a01 = fmaf(c.tx, v011 - v010, v010);
+    float a10 = fmaf(c.tx, v101 - v100, v100), a11 = fmaf(c.tx, v111 - v110, v110);
+    float b0 = fmaf(c.ty, a01 - a00, a00), b1 = fmaf(c.ty, a11 - a10, a10);
+    gz = b1 - b0;
+    gy = fmaf(c.tz, (a11 - a10) - (a01 - a00), a01 - a00);
+    float dx00 = v001 - v000, dx01 = v011 - v010, dx10 = v101 - v100, dx11 = v111 - v110;
+    float e0 = fmaf(c.ty, dx01 - dx00, dx00), e1 = fmaf(c.ty, dx11 - dx10, dx10);
+    gx = fmaf(c.tz, e1 - e0, e0);
+    return fmaf(c.tz, b1 - b0, b0);
+}
+
+// Cubic B-spline cell: 4 taps per axis (i-1 .. i+2) and their weights.
+struct CubCell {
+    long ox[4], oy[4], oz[4];
+    float wx[4], wy[4], wz[4];
+};
+
+__device__ __forceinline__ void cub_weights(float t, float w[4]) {
+    float s = 1.f - t, t2 = t * t, t3 = t2 * t;
+    w[0] = s * s * s * (1.f / 6.f);
+    w[1] = (3.f * t3 - 6.f * t2 + 4.f) * (1.f / 6.f);
+    w[2] = (-3.f * t3 + 3.f * t2 + 3.f * t + 1.f) * (1.f / 6.f);
+    w[3] = t3 * (1.f / 6.f);
+}
+__device__ __forceinline__ void cub_dweights(float t, float w[4]) {
+    float s = 1.f - t;
+    w[0] = -0.5f * s * s;
+    w[1] = (9.f * t * t - 12.f * t) * (1.f / 6.f);
+    w[2] = (-9.f * t * t + 6.f * t + 3.f) * (1.f / 6.f);
+    w[3] = 0.5f * t * t;
+}
+
+__device__ __forceinline__ void cub_axis(int j, float D, int n, long mul, long o[4], float& t) {
+    D = clampD(D);
+    float fl = floorf(D);
+    t = D - fl;
+    int i = wrapi(j + (int)fl - 1, n);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        o[q] = (long)i * mul;
+        i = i + 1 == n ? 0 : i + 1;
+    }
+}
+
+__device__ __forceinline__ CubCell cub_cell(const Grid& g, int x, int y, int z, float dx, float dy,
+                                            float dz, float tf[3]) {
+    CubCell c;
+    cub_axis(x, dx, g.nx, 1, c.ox, tf[0]);
+    cub_axis(y, dy, g.ny, g.nx, c.oy, tf[1]);
+    cub_axis(z, dz, g.nz, (long)g.nx * g.ny, c.oz, tf[2]);
+    cub_weights(tf[0], c.wx);
+    cub_weights(tf[1], c.wy);
+    cub_weights(tf[2], c.wz);
+    return c;
+}
+
+__device__ __forceinline__ float cub_eval(const float* __restrict__ f, const CubCell& c) {
+    float acc = 0.f;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        float accy = 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float* row = f + c.oz[r] + c.oy[q];
+            float ax = c.wx[0] * __ldg(row + c.ox[0]);
+            ax = fmaf(c.wx[1], __ldg(row + c.ox[1]), ax);
+            ax = fmaf(c.wx[2], __ldg(row + c.ox[2]), ax);
+            ax = fmaf(c.wx[3], __ldg(row + c.ox[3]), ax);
+            accy = fmaf(c.wy[q], ax, accy);
+        }
+        acc = fmaf(c.wz[r], accy, acc);
+    }
+    return acc;
+}
+
+__device__ __forceinline__ float cub_eval_grad(const float* __restrict__ f, const CubCell& c,
+                                               const float tf[3], float& gx, float& gy,
+                                               float& gz) {
+    float dwx[4], dwy[4], dwz[4];
+    cub_dweights(tf[0], dwx);
+    cub_dweights(tf[1], dwy);
+    cub_dweights(tf[2], dwz);
+    float v = 0.f;
+    gx = gy = gz = 0.f;
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+        float vy = 0.f, vyd = 0.f, vxd = 0.f;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float* row = f + c.oz[r] + c.oy[q];
+            float s0 = __ldg(row + c.ox[0]), s1 = __ldg(row + c.ox[1]);
+            float s2 = __ldg(row + c.ox[2]), s3 = __ldg(row + c.ox[3]);
+            float ax = c.wx[0] * s0 + c.wx[1] * s1 + c.wx[2] * s2 + c.wx[3] * s3;
+            float adx = dwx[0] * s0 + dwx[1] * s1 + dwx[2] * s2 + dwx[3] * s3;
+            vy = fmaf(c.wy[q], ax, vy);
+            vyd = fmaf(dwy[q], ax, vyd);
+            vxd = fmaf(c.wy[q], adx, vxd);
+        }
+        v = fmaf(c.wz[r], vy, v);
+        gz = fmaf(dwz[r], vy, gz);
+        gy = fmaf(c.wz[r], vyd, gy);
+        gx = fmaf(c.wz[r], vxd, gx);
+    }
+    return v;
+}
+
+// Interpolator front end: IP = 1 trilinear on samples, 3 cubic on spline coefficients.
+template <int IP>
+struct Interp;
+
+template <>
+struct Interp<1> {
+    LinCell c;
+    __device__ __forceinline__ Interp(const Grid& g, int x, int y, int z, float dx, float dy,
+                                      float dz)
+        : c(lin_cell(g, x, y, z, dx, dy, dz)) {}
+    __device__ __forceinline__ float operator()(const float* f) const { return lin_eval(f, c); }
+    __device__ __forceinline__ float grad(const float* f, float& gx, float& gy, float& gz) const {
+        return lin_eval_grad(f, c, gx, gy, gz);
+    }
+};
+
+template <>
+struct Interp<3> {
+    CubCell c;
+    float tf[3];
+    __device__ __forceinline__ Interp(const Grid& g, int x, int y, int z, float dx, float dy,
+                                      float dz) {
+        c = cub_cell(g, x, y, z, dx, dy, dz, tf);
+    }
+    __device__ __forceinline__ float operator()(const float* f) const { return cub_eval(f, c); }
+    __device__ __forceinline__ float grad(const float* f, float& gx, float& gy, float& gz) const {
+        return cub_eval_grad(f, c, tf, gx, gy, gz);
+    }
+};
+
+#define VOXEL_PROLOGUE                                          \
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;        \
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;        \
+    const int z = blockIdx.z;                                   \
+    if (x >= g.nx || y >= g.ny) return;                         \
+    const long n = g.ntot();                                    \
+    const long i = ((long)z * g.ny + y) * g.nx + x;
+
+static inline dim3 vox_grid(const Grid& g) { return dim3(cdiv(g.nx, 32), cdiv(g.ny, 8), g.nz); }
+static const dim3 kVoxBlock(32, 8, 1);
+
+// ---------------------------------------------------------------- characteristics
+template <int IP>
+__global__ void k_sl_char(Grid g, const float* __restrict__ vsrc, const float* __restrict__ vval,
+                          float s0, float s1, float s2, float dts, float* __restrict__ D) {
+    VOXEL_PROLOGUE
+    float V0 = vval[i] * s0, V1 = vval[n + i] * s1, V2 = vval[2 * n + i] * s2;
+    Interp<IP> it(g, x, y, z, dts * V0, dts * V1, dts * V2);  // X* = x + dts V
+    float W0 = it(vsrc) * s0, W1 = it(vsrc + n) * s1, W2 = it(vsrc + 2 * n) * s2;
+    const float h = 0.5f * dts;
+    D[i] = h * (W0 + V0);
+    D[n + i] = h * (W1 + V1);
+    D[2 * n + i] = h * (W2 + V2);
+}
+
+int sl_characteristics(const SLArgs& a, const float* vsrc, const float* vval, const float scale[3],
+                       double dt_signed, float* D, cudaStream_t st) {
+    KTRACE(a.interp == 3 ? "sl_char_cubic" : "sl_char", st, 36.0 * a.g.ntot(), 0);
+    if (a.interp == 3)
+        k_sl_char<3><<<vox_grid(a.g), kVoxBlock, 0, st>>>(a.g, vsrc, vval, scale[0], scale[1],
+                                                          scale[2], (float)dt_signed, D);
+    else
+        k_sl_char<1><<<vox_grid(a.g), kVoxBlock, 0, st>>>(a.g, vsrc, vval, scale[0], scale[1],
+                                                          scale[2], (float)dt_signed, D);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+// ---------------------------------------------------------------- gathers
+// MODE 0: out = src o X; 1: * aux(x) (one plane); 2: + aux[c](x)
+template <int IP, int MODE>
+__global__ void k_sl_gather(Grid g, const float* __restrict__ src, const float* __restrict__ D,
+                            const float* __restrict__ aux, int ncomp, float* __restrict__ out) {
+    VOXEL_PROLOGUE
+    Interp<IP> it(g, x, y, z, D[i], D[n + i], D[2 * n + i]);
+    float sc = MODE == 1 ? aux[i] : 1.f;
+    for (int c = 0; c < ncomp; ++c) {
+        float v = it(src + c * n);
+        if (MODE == 1) v *= sc;
+        if (MODE == 2) v += aux[c * n + i];
+        out[c * n + i] = v;
+    }
+}
+
+template <int MODE>
+static int launch_gather(const SLArgs& a, const float* src, const float* D, const float* aux,
+                         int ncomp, float* out, cudaStream_t st) {
+    static const char* names[2][3] = {{"sl_gather", "sl_gather_scale", "sl_gather_add"},
+                                      {"sl_gather_cubic", "sl_gather_scale_cubic", "sl_gather_add_cubic"}};
+    KTRACE(names[a.interp == 3][MODE], st,
+           (double)a.g.ntot() * (12.0 + 8.0 * ncomp + (MODE == 1 ? 4.0 : MODE == 2 ? 4.0 * ncomp : 0.0)), 0);
+    if (a.interp == 3)
+        k_sl_gather<3, MODE><<<vox_grid(a.g), kVoxBlock, 0, st>>>(a.g, src, D, aux, ncomp, out);
+    else
+        k_sl_gather<1, MODE><<<vox_grid(a.g), kVoxBlock, 0, st>>>(a.g, src, D, aux, ncomp, out);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+int sl_gather(const SLArgs& a, const float* src, const float* D, int ncomp, float* out,
+              cudaStream_t st) {
+    return launch_gather<0>(a, src, D, nullptr, ncomp, out, st);
+}
+int sl_gather_scale(const SLArgs& a, const float* src, const float* D, const float* gam,
+                    int ncomp, float* out, cudaStream_t st) {
+    return launch_gather<1>(a, src, D, gam, ncomp, out, st);
+}
+int sl_gather_add(const SLArgs& a, const float* src, const float* D, const float* add, int ncomp,
+                  float* out, cudaStream_t st) {
+    return launch_gather<2>(a, src, D, add, ncomp, out, st);
+}
+
+// ---------------------------------------------------------------- stationary factors
+// Backward Heun step of -D_t u = u d folds into u^j(x) = u^{j+1}(X+) gam(x).
+template <int IP>
+__global__ void k_prep_adjoint(Grid g, const float* __restrict__ dsrc,
+                               const float* __restrict__ dval, const float* __restrict__ Dp,
+                               float dt, float* __restrict__ gam) {
+    VOXEL_PROLOGUE
+    Interp<IP> it(g, x, y, z, Dp[i], Dp[n + i], Dp[2 * n + i]);
+    float dX = it(dsrc);
+    float d = dval[i];
+    gam[i] = 1.f + 0.5f * dt * (dX + (1.f + dt * dX) * d);
+}
+
+int sl_prep_adjoint(const SLArgs& a, const float* dsrc, const float* dval, const float* Dp,
+                    double dt, float* gam, cudaStream_t st) {
+    KTRACE("sl_prep_adjoint", st, 24.0 * a.g.ntot(), 0);
+    if (a.interp == 3)
+        k_prep_adjoint<3><<<vox_grid(a.g), kVoxBlock, 0, st>>>(a.g, dsrc, dval, Dp, (float)dt, gam);
+    else
+        k_prep_adjoint<1><<<vox_grid(a.g), kVoxBlock, 0, st>>>(a.g, dsrc, dval, Dp, (float)dt, gam);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+// Deformation state source term with stationary v: W = dt/2 (v(X) + v(x)).
+template <int IP>
+__global__ void k_prep_source(Grid g, const float* __restrict__ vsrc,
+                              const float* __restrict__ vval, const float* __restrict__ D,
+                              float dt, float* __restrict__ W) {
+    VOXEL_PROLOGUE
+    Interp<IP> it(g, x, y, z, D[i], D[n + i], D[2 * n + i]);
+    for (int c = 0; c < 3; ++c) W[c * n + i] = 0.5f * dt * (it(vsrc + c * n) + vval[c * n + i]);
+}
+
+int sl_prep_source(const SLArgs& a, const float* vsrc, const float* vval, const float* D,
+                   double dt, float* W, cudaStream_t st) {
+    KTRACE("sl_prep_source", st, 48.0 * a.g.ntot(), 0);
+    if (a.interp == 3)
+        k_prep_source<3><<<vox_grid(a.g), kVoxBlock, 0, st>>>(a.g, vsrc, vval, D, (float)dt, W);
+    else
+        k_prep_source<1><<<vox_grid(a.g), kVoxBlock, 0, st>>>(a.g, vsrc, vval, D, (float)dt, W);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+// ---------------------------------------------------------------- block reduction
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum of a double over a (possibly 2-D) block; thread 0 gets the result.
+__device__ double block_sum_d(double v) {
+    __shared__ double part[32];
+    const int t = threadIdx.y * blockDim.x + threadIdx.x;
+    const int nthreads = blockDim.x * blockDim.y;
+    v = warp_sum_d(v);
+    if ((t & 31) == 0) part[t >> 5] = v;
+    __syncthreads();
+    double r = 0.0;
+    if (t < 32) {
+        r = t < (nthreads >> 5) ? part[t] : 0.0;
+        r = warp_sum_d(r);
+    }
+    return r;
+}
+
+// ---------------------------------------------------------------- warped source image
+// m1 = I0 o (x - u1 to_vox); G = grad(I0 interpolant) there in physical units;
+// rho = -(2/sigma2) r G with r = m1 - I1. One partial sum of r^2 per block (grid-stride).
+template <int IP>
+__global__ void k_warp_image(Grid g, const float* __restrict__ I0src, const float* __restrict__ u1,
+                             float t0, float t1, float t2, const float* __restrict__ I1,
+                             float coef, float* __restrict__ m1, float* __restrict__ G,
+                             float* __restrict__ rho, double* __restrict__ partials) {
+    const long n = g.ntot();
+    double acc = 0.0;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long)gridDim.x * blockDim.x) {
+        int x = (int)(i % g.nx);
+        long r_ = i / g.nx;
+        int y = (int)(r_ % g.ny);
+        int z = (int)(r_ / g.ny);
+        Interp<IP> it(g, x, y, z, -u1[i] * t0, -u1[n + i] * t1, -u1[2 * n + i] * t2);
+        float gx, gy, gz;
+        float m = it.grad(I0src, gx, gy, gz);
+        gx *= t0;
+        gy *= t1;
+        gz *= t2;
+        float r = m - I1[i];
+        acc += (double)r * r;
+        if (m1) m1[i] = m;
+        if (G) {
+            G[i] = gx;
+            G[n + i] = gy;
+            G[2 * n + i] = gz;
+        }
+        if (rho) {
+            float s = coef * r;
+            rho[i] = s * gx;
+            rho[n + i] = s * gy;
+            rho[2 * n + i] = s * gz;
+        }
+    }
+    double s = block_sum_d(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+int sl_warp_image(const SLArgs& a, const float* I0src, const float* u1, const float to_vox[3],
+                  const float* I1, double sigma2, float* m1, float* G, float* rho,
+                  double* partials, cudaStream_t st) {
+    float coef = (float)(-2.0 / sigma2);
+    KTRACE("warp_image", st, a.g.ntot() * (24.0 + (m1 ? 4.0 : 0.0) + (G ? 12.0 : 0.0) + (rho ? 12.0 : 0.0)), 0);
+    if (a.interp == 3)
+        k_warp_image<3><<<kReduceBlocks, 256, 0, st>>>(a.g, I0src, u1, to_vox[0], to_vox[1],
+                                                       to_vox[2], I1, coef, m1, G, rho, partials);
+    else
+        k_warp_image<1><<<kReduceBlocks, 256, 0, st>>>(a.g, I0src, u1, to_vox[0], to_vox[1],
+                                                       to_vox[2], I1, coef, m1, G, rho, partials);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+// ---------------------------------------------------------------- incremental state
+// D~_t du~ = dv~ - D~u~ * dv~ (Table 1 row 7): F = dv - (Du) dv, Heun along X.
+template <int IP>
+__global__ void k_inc_defstate(Grid g, const float* __restrict__ U, const float* __restrict__ D,
+                               const float* __restrict__ Fold, const float* __restrict__ Du,
+                               const float* __restrict__ dv, float dt, float* __restrict__ out,
+                               float* __restrict__ Fnew) {
+    VOXEL_PROLOGUE
+    float w0 = dv[i], w1 = dv[n + i], w2 = dv[2 * n + i];
+    float F[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float j0 = Du[(3 * c + 0) * n + i], j1 = Du[(3 * c + 1) * n + i], j2 = Du[(3 * c + 2) * n + i];
+        F[c] = (c == 0 ? w0 : c == 1 ? w1 : w2) - (j0 * w0 + j1 * w1 + j2 * w2);
+    }
+    Interp<IP> it(g, x, y, z, D[i], D[n + i], D[2 * n + i]);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        out[c * n + i] = it(U + c * n) + 0.5f * dt * (it(Fold + c * n) + F[c]);
+        Fnew[c * n + i] = F[c];
+    }
+}
+
+int sl_inc_defstate(const SLArgs& a, const float* U, const float* D, const float* Fold,
+                    const float* Du, const float* dv, double dt, float* out, float* Fnew,
+                    cudaStream_t st) {
+    KTRACE(a.interp == 3 ? "sl_inc_defstate_cubic" : "sl_inc_defstate", st, 108.0 * a.g.ntot(), 0);
+    if (a.interp == 3)
+        k_inc_defstate<3><<<vox_grid(a.g), kVoxBlock, 0, st>>>(a.g, U, D, Fold, Du, dv, (float)dt,
+                                                               out, Fnew);
+    else
+        k_inc_defstate<1><<<vox_grid(a.g), kVoxBlock, 0, st>>>(a.g, U, D, Fold, Du, dv, (float)dt,
+                                                               out, Fnew);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+__global__ void k_defstate_rhs(long n, const float* __restrict__ Du, const float* __restrict__ dv,
+                               float* __restrict__ F) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float w0 = dv[i], w1 = dv[n + i], w2 = dv[2 * n + i];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        float j0 = Du[(3 * c + 0) * n + i], j1 = Du[(3 * c + 1) * n + i], j2 = Du[(3 * c + 2) * n + i];
+        F[c * n + i] = (c == 0 ? w0 : c == 1 ? w1 : w2) - (j0 * w0 + j1 * w1 + j2 * w2);
+    }
+}
+
+int defstate_rhs(const Grid& g, const float* Du, const float* dv, float* F, cudaStream_t st) {
+    long n = g.ntot();
+    KTRACE("defstate_rhs", st, 60.0 * n, 24.0 * n);
+    k_defstate_rhs<<<cdiv(n, 256), 256, 0, st>>>(n, Du, dv, F);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+__global__ void k_defstate_drho1(long n, const float* __restrict__ G, const float* __restrict__ du,
+                                 float coef, float* __restrict__ drho) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float g0 = G[i], g1 = G[n + i], g2 = G[2 * n + i];
+    float dm = -(g0 * du[i] + g1 * du[n + i] + g2 * du[2 * n + i]);
+    float s = coef * dm;
+    drho[i] = s * g0;
+    drho[n + i] = s * g1;
+    drho[2 * n + i] = s * g2;
+}
+
+int defstate_drho1(const Grid& g, const float* G, const float* du1, double sigma2, float* drho,
+                   cudaStream_t st) {
+    long n = g.ntot();
+    KTRACE("defstate_drho1", st, 36.0 * n, 10.0 * n);
+    k_defstate_drho1<<<cdiv(n, 256), 256, 0, st>>>(n, G, du1, (float)(-2.0 / sigma2), drho);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+// acc_b (+)= w sum_a Du[a*3+b] R_a   ((D u)^T R, the D~u~ * rho~ term before projection)
+__global__ void k_accum_JT(long n, const float* __restrict__ Du, const float* __restrict__ R,
+                           float w, float* __restrict__ acc, int init) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float r0 = R[i], r1 = R[n + i], r2 = R[2 * n + i];
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        float s = Du[(0 + b) * n + i] * r0 + Du[(3 + b) * n + i] * r1 + Du[(6 + b) * n + i] * r2;
+        acc[b * n + i] = init ? w * s : fmaf(w, s, acc[b * n + i]);
+    }
+}
+
+int accum_JT(const Grid& g, const float* Du, const float* R, float w, float* acc, int init,
+             cudaStream_t st) {
+    long n = g.ntot();
+    KTRACE("accum_JT", st, n * (60.0 + (init ? 0.0 : 12.0)), 21.0 * n);
+    k_accum_JT<<<cdiv(n, 256), 256, 0, st>>>(n, Du, R, w, acc, init);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+__global__ void k_scale_field(float* out, const float* in, float a, long n) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = a * in[i];
+}
+
+int scale_field(float* out, const float* in, float a, long n, cudaStream_t st) {
+    KTRACE("scale_field", st, 8.0 * n, n);
+    k_scale_field<<<cdiv(n, 256), 256, 0, st>>>(out, in, a, n);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+__global__ void k_sum_sq_diff(const float* a, const float* b, long n, double* partials) {
+    double acc = 0.0;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (long)gridDim.x * blockDim.x) {
+        double d = (double)a[i] - (double)b[i];
+        acc += d * d;
+    }
+    double s = block_sum_d(acc);
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+int sum_sq_diff(const float* a, const float* b, long n, double* partials, double* out,
+                cudaStream_t st) {
+    {
+        KTRACE("sum_sq_diff", st, 8.0 * n, 3.0 * n);
+        k_sum_sq_diff<<<kReduceBlocks, 256, 0, st>>>(a, b, n, partials);
+    }
+    LDDMM_CHECK_LAUNCH();
+    return finalize_sum(partials, kReduceBlocks, out, st);
+}
+
+// ---------------------------------------------------------------- B-spline prefilter
+// Periodic cubic B-spline coefficients along one axis: the cyclic system
+// (c_{j-1} + 4 c_j + c_{j+1}) / 6 = f_j is solved by the causal / anti-causal recursive
+// filter pair with pole zp = sqrt(3) - 2 (Unser, Aldroubi and Eden's B-spline transform),
+// each started from its exact periodic initial value (a full-period geometric sum).
+__device__ __forceinline__ void prefilter_line(float* f, long stride, int L) {
+    const float zp = -0.2679491924311228f;
+    float zk = 1.f, s = 0.f;
+    for (int k = 0; k < L; ++k) {
+        int j = k == 0 ? 0 : L - k;
+        s = fmaf(zk, f[(long)j * stride], s);
+        zk *= zp;
+    }
+    const float zL = zk;
+    float prev = s / (1.f - zL);
+    f[0] = prev;
+    for (int j = 1; j < L; ++j) {
+        prev = fmaf(zp, prev, f[(long)j * stride]);
+        f[(long)j * stride] = prev;
+    }
+    zk = 1.f;
+    s = 0.f;
+    for (int k = 0; k < L; ++k) {
+        int j = k == 0 ? L - 1 : k - 1;
+        s = fmaf(zk, f[(long)j * stride], s);
+        zk *= zp;
+    }
+    float cm = -zp / (1.f - zL) * s;
+    f[(long)(L - 1) * stride] = 6.f * cm;
+    for (int j = L - 2; j >= 0; --j) {
+        cm = zp * (cm - f[(long)j * stride]);
+        f[(long)j * stride] = 6.f * cm;
+    }
+}
+
+// x lines through shared memory: the CTA stages `rows` rows, one thread filters one row.
+__global__ void k_prefilter_x(const float* __restrict__ in, float* __restrict__ out, long nrows,
+                              int nx, int rows) {
+    extern __shared__ float sm[];
+    const int ld = nx + 1;
+    const long row0 = (long)blockIdx.x * rows;
+    for (int r = 0; r < rows; ++r) {
+        long row = row0 + r;
+        if (row >= nrows) break;
+        for (int x = threadIdx.x; x < nx; x += blockDim.x) sm[r * ld + x] = in[row * nx + x];
+    }
+    __syncthreads();
+    if (threadIdx.x < rows && row0 + threadIdx.x < nrows) prefilter_line(sm + threadIdx.x * ld, 1, nx);
+    __syncthreads();
+    for (int r = 0; r < rows; ++r) {
+        long row = row0 + r;
+        if (row >= nrows) break;
+        for (int x = threadIdx.x; x < nx; x += blockDim.x) out[row * nx + x] = sm[r * ld + x];
+    }
+}
+
+// y or z lines in place in global memory: thread per line, consecutive threads along x.
+__global__ void k_prefilter_strided(float* f, long nlines, int nx, long outer_stride, long stride,
+                                    int L) {
+    long t = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= nlines) return;
+    long x = t % nx, o = t / nx;
+    prefilter_line(f + o * outer_stride + x, stride, L);
+}
+
+// out = B-spline coefficients of ncomp fields `in` (out may alias in).
+int bspline_prefilter(const Grid& g, const float* in, int ncomp, float* out, cudaStream_t st) {
+    const long n = g.ntot();
+    int rows = 128;
+    while (rows > 32 && (long)rows * (g.nx + 1) * 4 > 200 * 1024) rows -= 32;
+    if ((long)rows * (g.nx + 1) * 4 > 220 * 1024) {
+        set_error("bspline_prefilter: nx too large");
+        return LDDMM_EINVAL;
+    }
+    size_t smem = (size_t)rows * (g.nx + 1) * 4;
+    static bool attr = false;
+    if (!attr) {
+        LDDMM_CUDA(cudaFuncSetAttribute(k_prefilter_x, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        227 * 1024));
+        attr = true;
+    }
+    for (int c = 0; c < ncomp; ++c) {
+        const float* src = in + c * n;
+        float* dst = out + c * n;
+        long nrows = (long)g.ny * g.nz;
+        {
+            KTRACE("prefilter_x", st, 8.0 * n, 8.0 * n);
+            k_prefilter_x<<<cdiv(nrows, rows), rows, smem, st>>>(src, dst, nrows, g.nx, rows);
+        }
+        LDDMM_CHECK_LAUNCH();
+        // y lines: for each z, x -> start z*nx*ny + x, stride nx
+        long ly = (long)g.nx * g.nz;
+        {
+            KTRACE("prefilter_yz", st, 8.0 * n, 8.0 * n);
+            k_prefilter_strided<<<cdiv(ly, 128), 128, 0, st>>>(dst, ly, g.nx, (long)g.nx * g.ny,
+                                                              g.nx, g.ny);
+        }
+        LDDMM_CHECK_LAUNCH();
+        // z lines: for each y, x -> start y*nx + x, stride nx*ny
+        long lz = (long)g.nx * g.ny;
+        {
+            KTRACE("prefilter_yz", st, 8.0 * n, 8.0 * n);
+            k_prefilter_strided<<<cdiv(lz, 128), 128, 0, st>>>(dst, lz, g.nx, g.nx,
+                                                              (long)g.nx * g.ny, g.nz);
+        }
+        LDDMM_CHECK_LAUNCH();
+    }
+    return LDDMM_OK;
+}
+
+// ---------------------------------------------------------------- image variant
+// Incremental state, D~_t dm~ = -grad~ m~ * dv~ (Table 1 row 5): F = -Gm . dv,
+// out = U o X + dt/2 (Fold o X + Fnew).
+template <int IP>
+__global__ void k_inc_image(Grid g, const float* __restrict__ U, const float* __restrict__ D,
+                            const float* __restrict__ Fold, const float* __restrict__ Gm,
+                            const float* __restrict__ dv, float dt, float* __restrict__ out,
+                            float* __restrict__ Fnew) {
+    VOXEL_PROLOGUE
+    float F = -(Gm[i] * dv[i] + Gm[n + i] * dv[n + i] + Gm[2 * n + i] * dv[2 * n + i]);
+    Interp<IP> it(g, x, y, z, D[i], D[n + i], D[2 * n + i]);
+    out[i] = it(U) + 0.5f * dt * (it(Fold) + F);
+    Fnew[i] = F;
+}
+
+int sl_inc_image(const SLArgs& a, const float* U, const float* D, const float* Fold,
+                 const float* Gm, const float* dv, double dt, float* out, float* Fnew,
+                 cudaStream_t st) {
+    KTRACE(a.interp == 3 ? "sl_inc_image_cubic" : "sl_inc_image", st, 52.0 * a.g.ntot(), 0);
+    if (a.interp == 3)
+        k_inc_image<3><<<vox_grid(a.g), kVoxBlock, 0, st>>>(a.g, U, D, Fold, Gm, dv, (float)dt, out,
+                                                            Fnew);
+    else
+        k_inc_image<1><<<vox_grid(a.g), kVoxBlock, 0, st>>>(a.g, U, D, Fold, Gm, dv, (float)dt, out,
+                                                            Fnew);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+__global__ void k_image_rhs(long n, const float* __restrict__ Gm, const float* __restrict__ dv,
+                            float* __restrict__ F) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) F[i] = -(Gm[i] * dv[i] + Gm[n + i] * dv[n + i] + Gm[2 * n + i] * dv[2 * n + i]);
+}
+
+int image_rhs(const Grid& g, const float* Gm, const float* dv, float* F, cudaStream_t st) {
+    long n = g.ntot();
+    KTRACE("image_rhs", st, 28.0 * n, 6.0 * n);
+    k_image_rhs<<<cdiv(n, 256), 256, 0, st>>>(n, Gm, dv, F);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+// acc_b (+)= w s(x) Gm_b(x)   (the lambda~ * grad~ m~ term before projection)
+__global__ void k_accum_sv(long n, const float* __restrict__ s, const float* __restrict__ Gm,
+                           float w, float* __restrict__ acc, int init) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float v = w * s[i];
+#pragma unroll
+    for (int b = 0; b < 3; ++b)
+        acc[b * n + i] = init ? v * Gm[b * n + i] : fmaf(v, Gm[b * n + i], acc[b * n + i]);
+}
+
+int accum_sv(const Grid& g, const float* s, const float* Gm, float w, float* acc, int init,
+             cudaStream_t st) {
+    long n = g.ntot();
+    KTRACE("accum_sv", st, n * (28.0 + (init ? 0.0 : 12.0)), 7.0 * n);
+    k_accum_sv<<<cdiv(n, 256), 256, 0, st>>>(n, s, Gm, w, acc, init);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+// lambda(1) = coef (m1 - I1)
+__global__ void k_axpy_diff(long n, const float* a, const float* b, float coef, float* out) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = coef * (a[i] - b[i]);
+}
+
+int scaled_diff(const Grid& g, const float* a, const float* b, float coef, float* out,
+                cudaStream_t st) {
+    long n = g.ntot();
+    KTRACE("scaled_diff", st, 12.0 * n, 2.0 * n);
+    k_axpy_diff<<<cdiv(n, 256), 256, 0, st>>>(n, a, b, coef, out);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+}  // namespace lddmm

@@ -1,0 +1,735 @@
+// Band-limited projection pi and inclusion iota (Sec. 2.2) as separable partial DFTs.
+//
+// pi(f)_k = (1/N) sum_x f(x) e^{-i k.x} is computed axis by axis:
+//   stage X  A[row][kx]    = sum_jx f[row][jx] e^{-i kx 2pi jx/nx},  kx = 0..K/2-1 only:
+//                            f is real, so the kx < 0 half is the conjugate mirror;
+//   stage Y  B[z][jy][kx]  = sum_y A[z][y][kx] e^{-i ky 2pi y/ny},   all retained ky;
+//   stage Z  c[jz][jy][jx] = (1/N) sum_z B[z][jy][kx] e^{-i kz 2pi z/nz}, plus the mirror.
+// iota runs the same three stages backwards (Z, Y on the kx >= 0 half, then X producing
+// the real field as Re(T[0]) + 2 Re sum_{kx>0} T[kx] e^{i kx x}).
+//
+// Stage X touches the full grid and carries almost all of the work: it is a GEMM with
+// M = rows (ncomp*nz*ny), N = K (cos and sin of K/2 modes), K-dim = nx. Here it runs as a
+// register-blocked FP32 SIMT contraction with the twiddles staged in shared memory; the
+// Y and Z stages operate on L2-resident intermediates.
+#include "common.cuh"
+#include "lddmm.h"
+
+#include <algorithm>
+
+namespace lddmm {
+
+static inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
+
+long twiddle_floats(const Grid& g, int K) { return 2L * K * ((long)g.nx + g.ny + g.nz); }
+
+__global__ void k_twiddle(float* cosT, float* sinT, int K, int n) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= K * n) return;
+    int slot = i / n, j = i - slot * n;
+    long k = slot - K / 2;
+    long r = ((k * j) % n + n) % n;  // exact phase reduction
+    double s, c;
+    sincospi(2.0 * (double)r / (double)n, &s, &c);
+    cosT[i] = (float)c;
+    sinT[i] = (float)s;
+}
+
+int twiddle_init(const Grid& g, int K, float* mem, Twiddles& tw, cudaStream_t st) {
+    const int ns[3] = {g.nx, g.ny, g.nz};
+    const float* ptrs[6];
+    float* p = mem;
+    for (int a = 0; a < 3; ++a) {
+        int n = ns[a];
+        {
+            KTRACE("twiddle", st, 8.0 * K * n, 0);
+            k_twiddle<<<cdiv((long)K * n, 256), 256, 0, st>>>(p, p + (long)K * n, K, n);
+        }
+        LDDMM_CHECK_LAUNCH();
+        ptrs[2 * a] = p;
+        ptrs[2 * a + 1] = p + (long)K * n;
+        p += 2L * K * n;
+    }
+    tw.K = K;
+    tw.cx = ptrs[0]; tw.sx = ptrs[1];
+    tw.cy = ptrs[2]; tw.sy = ptrs[3];
+    tw.cz = ptrs[4]; tw.sz = ptrs[5];
+    return LDDMM_OK;
+}
+
+long spectral_scratch_elems(const Grid& g, int K, int ncomp) {
+    long kh = K / 2;
+    long a = (long)ncomp * g.nz * g.ny * kh;      // stage X output / iota stage Y output
+    long b = (long)ncomp * g.nz * K * kh;         // stage Y output / iota stage Z output
+    long c = (long)ncomp * K * K * K;             // B-spline-divided input cube
+    return std::max(a, std::max(b, c));
+}
+
+// ------------------------------------------------------------------------ pi, stage X
+// CTA: ROWS rows x all KH modes. Thread (row group rg, mode pair p): rows rg + 16 i
+// (i = 0..3) and modes 2p, 2p+1 -> 16 accumulators. Shared memory: rows padded to
+// ldr = round4(nx) + 4 floats (conflict-free float4 reads across row groups), twiddles
+// as (cos, sin) pairs at [jx][kx] so a thread reads both of its modes with one float4.
+constexpr int PX_ROWS = 64;
+
+template <int KHP>
+__global__ void __launch_bounds__(KHP * 8)
+k_pi_x(const float* __restrict__ f, long fstride, long rows_per_comp, int ncomp, int nx,
+       int KH, int K, const float* __restrict__ cosT, const float* __restrict__ sinT,
+       float2* __restrict__ A) {
+    constexpr int NT = KHP * 8;
+    extern __shared__ float4 smem4[];
+    float* sm = reinterpret_cast<float*>(smem4);
+    const int nxp = (nx + 3) & ~3;
+    const int ldr = nxp + 4;
+    float* frow = sm;                                             // PX_ROWS * ldr
+    float2* tw = reinterpret_cast<float2*>(sm + PX_ROWS * ldr);  // nxp * KHP
+    const int tid = threadIdx.x;
+
+    for (int e = tid; e < nxp * KHP; e += NT) {
+        int jx = e / KHP, kx = e - jx * KHP;
+        float2 v = make_float2(0.f, 0.f);
+        if (jx < nx && kx < KH) {
+            long o = (long)(K / 2 + kx) * nx + jx;
+            v = make_float2(cosT[o], sinT[o]);
+        }
+        tw[e] = v;
+    }
+    const long rows = rows_per_comp * ncomp;
+    const long row0 = (long)blockIdx.x * PX_ROWS;
+    for (int r = 0; r < PX_ROWS; ++r) {
+        long row = row0 + r;
+        const float* src = nullptr;
+        if (row < rows) {
+            long comp = row / rows_per_comp;
+            src = f + comp * fstride + (row - comp * rows_per_comp) * nx;
+        }
+        for (int x = tid; x < nxp; x += NT)
+            frow[r * ldr + x] = (src && x < nx) ? __ldcs(src + x) : 0.f;
+    }
+    __syncthreads();
+
+    const int p = tid % (KHP / 2);
+    const int rg = tid / (KHP / 2);  // 0..15
+    float re[4][2], im[4][2];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int q = 0; q < 2; ++q) re[i][q] = im[i][q] = 0.f;
+
+    for (int jx = 0; jx < nxp; jx += 4) {
+        float4 fr[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+            fr[i] = *reinterpret_cast<const float4*>(&frow[(rg + 16 * i) * ldr + jx]);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            float4 t = *reinterpret_cast<const float4*>(&tw[(jx + q) * KHP + 2 * p]);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float v = q == 0 ? fr[i].x : q == 1 ? fr[i].y : q == 2 ? fr[i].z : fr[i].w;
+                re[i][0] = fmaf(v, t.x, re[i][0]);
+                im[i][0] = fmaf(-v, t.y, im[i][0]);
+                re[i][1] = fmaf(v, t.z, re[i][1]);
+                im[i][1] = fmaf(-v, t.w, im[i][1]);
+            }
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        long row = row0 + rg + 16 * i;
+        if (row >= rows) continue;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+            int kx = 2 * p + q;
+            if (kx < KH) A[row * KH + kx] = make_float2(re[i][q], im[i][q]);
+        }
+    }
+}
+
+// ------------------------------------------------------------------------ pi, stage Y
+// One CTA loops over (comp, z) slabs. Thread (ky pair jp, mode kx). Twiddles [y][jy] as
+// (cos, sin) float2 in shared memory, the slab A[y][kx] beside them.
+template <int KHP>
+__global__ void k_pi_y(const float2* __restrict__ A, int nslabs, int ny, int KH, int K,
+                       const float* __restrict__ cosT, const float* __restrict__ sinT,
+                       float2* __restrict__ B) {
+    extern __shared__ float4 smem4[];
+    float2* tw = reinterpret_cast<float2*>(smem4);   // ny * K
+    float2* sa = tw + (long)ny * K;                  // ny * KHP
+    const int nt = blockDim.x;
+    for (int e = threadIdx.x; e < ny * K; e += nt) {
+        int y = e / K, jy = e - y * K;
+        long o = (long)jy * ny + y;
+        tw[e] = make_float2(cosT[o], sinT[o]);
+    }
+    const int kx = threadIdx.x % KHP;
+    const int jp = threadIdx.x / KHP;  // ky pair: slots 2jp, 2jp+1
+    for (int slab = blockIdx.x; slab < nslabs; slab += gridDim.x) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < ny * KHP; e += nt) {
+            int y = e / KHP, k = e - y * KHP;
+            sa[e] = k < KH ? A[((long)slab * ny + y) * KH + k] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        if (2 * jp < K) {
+            float r0 = 0.f, i0 = 0.f, r1 = 0.f, i1 = 0.f;
+            for (int y = 0; y < ny; ++y) {
+                float2 a = sa[y * KHP + kx];
+                float4 t = *reinterpret_cast<const float4*>(&tw[y * K + 2 * jp]);
+                // a * (cos - i sin)
+                r0 = fmaf(a.x, t.x, fmaf(a.y, t.y, r0));
+                i0 = fmaf(a.y, t.x, fmaf(-a.x, t.y, i0));
+                r1 = fmaf(a.x, t.z, fmaf(a.y, t.w, r1));
+                i1 = fmaf(a.y, t.z, fmaf(-a.x, t.w, i1));
+            }
+            if (kx < KH) {
+                B[((long)slab * K + 2 * jp) * KH + kx] = make_float2(r0, i0);
+                B[((long)slab * K + 2 * jp + 1) * KH + kx] = make_float2(r1, i1);
+            }
+        }
+    }
+}
+
+// ------------------------------------------------------------------------ pi, stage Z
+// Thread per (comp, jz, jy, kx >= 0); also writes the Hermitian mirror and the zero slots.
+__global__ void k_pi_z(const float2* __restrict__ B, int ncomp, int nz, int K, int KH,
+                       const float* __restrict__ cosT, const float* __restrict__ sinT,
+                       float inv_n, float2* __restrict__ c) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    long total = (long)ncomp * K * K * KH;
+    if (i >= total) return;
+    int kx = (int)(i % KH);
+    long t = i / KH;
+    int jy = (int)(t % K);
+    t /= K;
+    int jz = (int)(t % K);
+    int comp = (int)(t / K);
+    float re = 0.f, im = 0.f;
+    if (jz >= 1 && jy >= 1) {
+        const float2* b = B + (long)comp * nz * K * KH + (long)jy * KH + kx;
+        const float* cz = cosT + (long)jz * nz;
+        const float* sz = sinT + (long)jz * nz;
+        for (int z = 0; z < nz; ++z) {
+            float2 v = b[(long)z * K * KH];
+            float cs = __ldg(cz + z), sn = __ldg(sz + z);
+            re = fmaf(v.x, cs, fmaf(v.y, sn, re));
+            im = fmaf(v.y, cs, fmaf(-v.x, sn, im));
+        }
+        re *= inv_n;
+        im *= inv_n;
+    }
+    float2* cc = c + (long)comp * K * K * K;
+    const int h = K / 2;
+    cc[((long)jz * K + jy) * K + h + kx] = make_float2(re, im);
+    if (kx >= 1) {
+        if (jz >= 1 && jy >= 1)
+            cc[((long)(K - jz) * K + (K - jy)) * K + h - kx] = make_float2(re, -im);
+        else
+            cc[((long)jz * K + jy) * K + h - kx] = make_float2(0.f, 0.f);
+    } else {
+        cc[((long)jz * K + jy) * K + 0] = make_float2(0.f, 0.f);
+    }
+}
+
+template <int KHP>
+static int launch_pi_x(const Grid& g, const Twiddles& tw, const float* f, long fstride, int ncomp,
+                       float2* A, cudaStream_t st) {
+    const int KH = tw.K / 2;
+    const int nxp = (g.nx + 3) & ~3;
+    size_t smem = (size_t)PX_ROWS * (nxp + 4) * 4 + (size_t)nxp * KHP * 8;
+    if (smem > 227 * 1024) {
+        set_error("bl_project: nx too large for the x stage");
+        return LDDMM_EINVAL;
+    }
+    static bool attr_set = false;
+    if (!attr_set) {
+        LDDMM_CUDA(cudaFuncSetAttribute(k_pi_x<KHP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        227 * 1024));
+        attr_set = true;
+    }
+    long rows = (long)g.nz * g.ny * ncomp;
+    KTRACE("pi_x", st, rows * g.nx * 4.0 + rows * KH * 8.0, rows * g.nx * KH * 4.0);
+    k_pi_x<KHP><<<cdiv(rows, PX_ROWS), KHP * 8, smem, st>>>(
+        f, fstride, (long)g.nz * g.ny, ncomp, g.nx, KH, tw.K, tw.cx, tw.sx, A);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+template <int KHP>
+static int launch_pi_y(const Grid& g, const Twiddles& tw, int ncomp, const float2* A, float2* B,
+                       cudaStream_t st) {
+    const int K = tw.K, KH = K / 2;
+    size_t smem = (size_t)g.ny * K * 8 + (size_t)g.ny * KHP * 8;
+    if (smem > 227 * 1024) {
+        set_error("bl_project: ny too large for the y stage");
+        return LDDMM_EINVAL;
+    }
+    static bool attr_set = false;
+    if (!attr_set) {
+        LDDMM_CUDA(cudaFuncSetAttribute(k_pi_y<KHP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        227 * 1024));
+        attr_set = true;
+    }
+    int nslabs = ncomp * g.nz;
+    int threads = KHP * ((K + 1) / 2);
+    KTRACE("pi_y", st, (double)nslabs * (g.ny + K) * KH * 8.0, (double)nslabs * K * KH * g.ny * 8.0);
+    k_pi_y<KHP><<<std::min(nslabs, 2 * 148), threads, smem, st>>>(A, nslabs, g.ny, KH, K, tw.cy,
+                                                                  tw.sy, B);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+static int check_spectral_shape(const Grid& g, int K) {
+    if (g.nx < 2 || g.ny < 2 || g.nz < 2 || K < 4 || (K & 1) || K > 64 || K > g.nx ||
+        K > g.ny || K > g.nz || g.nx > 1024 || g.ny > 1024) {
+        set_error("spectral: need even 4 <= K <= min(64, nx, ny, nz) and nx, ny <= 1024");
+        return LDDMM_EINVAL;
+    }
+    return LDDMM_OK;
+}
+
+#define KHP_DISPATCH(KH, FN, ...)                                   \
+    ((KH) <= 2 ? FN<2>(__VA_ARGS__) : (KH) <= 4 ? FN<4>(__VA_ARGS__) \
+     : (KH) <= 8 ? FN<8>(__VA_ARGS__) : (KH) <= 16 ? FN<16>(__VA_ARGS__) : FN<32>(__VA_ARGS__))
+
+int bl_project(const Grid& g, const Twiddles& tw, const float* f, long fstride, int ncomp,
+               float2* c, float2* s1, float2* s2, int precision, cudaStream_t st) {
+    (void)precision;
+    int rc = check_spectral_shape(g, tw.K);
+    if (rc) return rc;
+    const int K = tw.K, KH = K / 2;
+    rc = KHP_DISPATCH(KH, launch_pi_x, g, tw, f, fstride, ncomp, s1, st);
+    if (rc) return rc;
+    rc = KHP_DISPATCH(KH, launch_pi_y, g, tw, ncomp, s1, s2, st);
+    if (rc) return rc;
+    long total = (long)ncomp * K * K * KH;
+    KTRACE("pi_z", st, (double)ncomp * g.nz * K * KH * 8.0 + (double)ncomp * K * K * K * 8.0,
+           (double)total * g.nz * 8.0);
+    k_pi_z<<<cdiv(total, 256), 256, 0, st>>>(s2, ncomp, g.nz, K, KH, tw.cz, tw.sz,
+                                             (float)(1.0 / (double)g.ntot()), c);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+// ---------------------------------------------------------------------- iota, stage Z
+// T1[comp][z][jy][kx] = sum_{jz>=1} m(k) c[comp][jz][jy][K/2+kx] e^{+i kz 2pi z/nz}
+// m(k) = i k_axis (or 1 with deriv_axis = -1). Mode 3: one output, the divergence
+// sum_a i k_a c_a of a 3-component cube.
+__global__ void k_iota_z(const float2* __restrict__ c, int ncomp_out, int nz, int K, int KH,
+                         int deriv_axis, const float* __restrict__ cosT,
+                         const float* __restrict__ sinT, float2* __restrict__ T1) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    long total = (long)ncomp_out * nz * K * KH;
+    if (i >= total) return;
+    int kx = (int)(i % KH);
+    long t = i / KH;
+    int jy = (int)(t % K);
+    t /= K;
+    int z = (int)(t % nz);
+    int comp = (int)(t / nz);
+    const int h = K / 2;
+    float re = 0.f, im = 0.f;
+    if (jy >= 1) {
+        const float ky = (float)(jy - h);
+        for (int jz = 1; jz < K; ++jz) {
+            const float kz = (float)(jz - h);
+            float mre, mim;  // multiplier (complex) applied to the coefficient
+            float2 v;
+            if (deriv_axis == 3) {
+                // sum_a i k_a c_a
+                float2 a0 = c[(((long)0 * K + jz) * K + jy) * K + h + kx];
+                float2 a1 = c[(((long)1 * K + jz) * K + jy) * K + h + kx];
+                float2 a2 = c[(((long)2 * K + jz) * K + jy) * K + h + kx];
+                float sr = -((float)kx * a0.y + ky * a1.y + kz * a2.y);
+                float si = (float)kx * a0.x + ky * a1.x + kz * a2.x;
+                v = make_float2(sr, si);
+                mre = 1.f;
+                mim = 0.f;
+            } else {
+                v = c[(((long)comp * K + jz) * K + jy) * K + h + kx];
+                if (deriv_axis < 0) {
+                    mre = 1.f; mim = 0.f;
+                } else {
+                    float k = deriv_axis == 0 ? (float)kx : deriv_axis == 1 ? ky : kz;
+                    mre = 0.f; mim = k;
+                }
+            }
+            float vr = v.x * mre - v.y * mim;
+            float vi = v.x * mim + v.y * mre;
+            float cs = __ldg(cosT + (long)jz * nz + z), sn = __ldg(sinT + (long)jz * nz + z);
+            // (vr + i vi)(cs + i sn)
+            re = fmaf(vr, cs, fmaf(-vi, sn, re));
+            im = fmaf(vr, sn, fmaf(vi, cs, im));
+        }
+    }
+    T1[i] = make_float2(re, im);
+}
+
+// B-spline prefilter division on a cube copy: out = c / B^(k) (all three axes).
+__global__ void k_cube_bspline_div(const float2* __restrict__ c, int ncomp, int K, int nx, int ny,
+                                   int nz, float2* __restrict__ out) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    long n = (long)ncomp * K * K * K;
+    if (i >= n) return;
+    int jx = (int)(i % K);
+    int jy = (int)((i / K) % K);
+    int jz = (int)((i / ((long)K * K)) % K);
+    const int h = K / 2;
+    double bx = (2.0 + cospi(2.0 * (jx - h) / nx)) / 3.0;
+    double by = (2.0 + cospi(2.0 * (jy - h) / ny)) / 3.0;
+    double bz = (2.0 + cospi(2.0 * (jz - h) / nz)) / 3.0;
+    float inv = (float)(1.0 / (bx * by * bz));
+    float2 v = c[i];
+    out[i] = make_float2(v.x * inv, v.y * inv);
+}
+
+// ---------------------------------------------------------------------- iota, stage Y
+// T2[slab][y][kx] = sum_{jy>=1} T1[slab][jy][kx] e^{+i ky 2pi y/ny}
+__global__ void k_iota_y(const float2* __restrict__ T1, int nslabs, int ny, int K, int KH,
+                         const float* __restrict__ cosT, const float* __restrict__ sinT,
+                         float2* __restrict__ T2) {
+    extern __shared__ float4 smem4[];
+    float2* tw = reinterpret_cast<float2*>(smem4);  // K * ny  [jy][y]
+    float2* st1 = tw + (long)K * ny;                // K * KH
+    const int nt = blockDim.x;
+    for (int e = threadIdx.x; e < K * ny; e += nt) tw[e] = make_float2(cosT[e], sinT[e]);
+    for (int slab = blockIdx.x; slab < nslabs; slab += gridDim.x) {
+        __syncthreads();
+        for (int e = threadIdx.x; e < K * KH; e += nt) st1[e] = T1[(long)slab * K * KH + e];
+        __syncthreads();
+        for (int e = threadIdx.x; e < ny * KH; e += nt) {
+            int y = e / KH, kx = e - y * KH;
+            float re = 0.f, im = 0.f;
+            for (int jy = 1; jy < K; ++jy) {
+                float2 v = st1[jy * KH + kx];
+                float2 t = tw[jy * ny + y];
+                re = fmaf(v.x, t.x, fmaf(-v.y, t.y, re));
+                im = fmaf(v.x, t.y, fmaf(v.y, t.x, im));
+            }
+            T2[(long)slab * ny * KH + e] = make_float2(re, im);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------- iota, stage X
+// f[row][x] = Re T[row][0] + 2 sum_{kx>=1} Re(T[row][kx] e^{i kx 2pi x/nx}).
+// CTA: IX_ROWS rows x all x. Warp tile: 16 rows x 32 x; lane -> (row lane rl = lane/8,
+// x group xl = lane%8), thread rows {16 i + 4 wr + rl}, x = 4 (8 wx + xl) .. +3.
+constexpr int IX_ROWS = 64;
+
+template <int KHP>
+__global__ void __launch_bounds__(256)
+k_iota_x(const float2* __restrict__ T, long rows_per_comp, int ncomp, int nx, int KH, int K,
+         const float* __restrict__ cosT, const float* __restrict__ sinT, float* __restrict__ f,
+         long fstride) {
+    extern __shared__ float4 smem4[];
+    float* sm = reinterpret_cast<float*>(smem4);
+    const int nxp = (nx + 31) & ~31;
+    float* tc = sm;                       // KHP * nxp
+    float* ts = tc + KHP * nxp;           // KHP * nxp
+    float2* co = reinterpret_cast<float2*>(ts + KHP * nxp);  // IX_ROWS * (KHP + 1)
+    const int ldc = KHP + 1;
+    const int tid = threadIdx.x;
+    const long rows = rows_per_comp * ncomp;
+    const long row0 = (long)blockIdx.x * IX_ROWS;
+
+    for (int e = tid; e < KHP * nxp; e += 256) {
+        int kx = e / nxp, x = e - kx * nxp;
+        float c = 0.f, s = 0.f;
+        if (kx < KH && x < nx) {
+            long o = (long)(K / 2 + kx) * nx + x;
+            float w = kx == 0 ? 1.f : 2.f;
+            c = w * cosT[o];
+            s = w * sinT[o];
+        }
+        tc[e] = c;
+        ts[e] = s;
+    }
+    for (int e = tid; e < IX_ROWS * KHP; e += 256) {
+        int r = e / KHP, kx = e - r * KHP;
+        long row = row0 + r;
+        float2 v = make_float2(0.f, 0.f);
+        if (row < rows && kx < KH) {
+            v = T[row * KH + kx];
+            if (kx == 0) v.y = 0.f;
+        }
+        co[r * ldc + kx] = v;
+    }
+    __syncthreads();
+
+    const int warp = tid >> 5, lane = tid & 31;
+    const int rl = lane >> 3, xl = lane & 7;
+    const int wtiles_x = nxp / 32;
+    const int wtiles = 4 * wtiles_x;  // 4 row blocks of 16 rows
+    for (int wt = warp; wt < wtiles; wt += 8) {
+        const int wr = wt % 4, wx = wt / 4;
+        const int x0 = 4 * (8 * wx + xl);
+        float acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) acc[i][q] = 0.f;
+        for (int kx = 0; kx < KHP; ++kx) {
+            float4 c4 = *reinterpret_cast<const float4*>(&tc[kx * nxp + x0]);
+            float4 s4 = *reinterpret_cast<const float4*>(&ts[kx * nxp + x0]);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                float2 ab = co[(16 * i + 4 * wr + rl) * ldc + kx];
+                acc[i][0] = fmaf(ab.x, c4.x, fmaf(-ab.y, s4.x, acc[i][0]));
+                acc[i][1] = fmaf(ab.x, c4.y, fmaf(-ab.y, s4.y, acc[i][1]));
+                acc[i][2] = fmaf(ab.x, c4.z, fmaf(-ab.y, s4.z, acc[i][2]));
+                acc[i][3] = fmaf(ab.x, c4.w, fmaf(-ab.y, s4.w, acc[i][3]));
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            long row = row0 + 16 * i + 4 * wr + rl;
+            if (row >= rows) continue;
+            long comp = row / rows_per_comp;
+            float* dst = f + comp * fstride + (row - comp * rows_per_comp) * nx;
+            if (x0 + 3 < nx && (nx & 3) == 0 && (reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+                __stcs(reinterpret_cast<float4*>(dst + x0),
+                       make_float4(acc[i][0], acc[i][1], acc[i][2], acc[i][3]));
+            } else {
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (x0 + q < nx) dst[x0 + q] = acc[i][q];
+            }
+        }
+    }
+}
+
+template <int KHP>
+static int launch_iota_x(const Grid& g, const Twiddles& tw, const float2* T, int ncomp, float* f,
+                         long fstride, cudaStream_t st) {
+    const int nxp = (g.nx + 31) & ~31;
+    size_t smem = (size_t)2 * KHP * nxp * 4 + (size_t)IX_ROWS * (KHP + 1) * 8;
+    if (smem > 227 * 1024) {
+        set_error("bl_include: nx too large for the x stage");
+        return LDDMM_EINVAL;
+    }
+    static bool attr_set = false;
+    if (!attr_set) {
+        LDDMM_CUDA(cudaFuncSetAttribute(k_iota_x<KHP>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+        attr_set = true;
+    }
+    long rows = (long)g.nz * g.ny * ncomp;
+    KTRACE("iota_x", st, rows * (tw.K / 2) * 8.0 + rows * g.nx * 4.0, rows * g.nx * (tw.K / 2) * 4.0);
+    k_iota_x<KHP><<<cdiv(rows, IX_ROWS), 256, smem, st>>>(T, (long)g.nz * g.ny, ncomp, g.nx,
+                                                         tw.K / 2, tw.K, tw.cx, tw.sx, f, fstride);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+int bl_include(const Grid& g, const Twiddles& tw, const float2* c, int ncomp, float* f,
+               long fstride, int deriv_axis, int bspline, float2* s1, float2* s2,
+               int precision, cudaStream_t st) {
+    (void)precision;
+    int rc = check_spectral_shape(g, tw.K);
+    if (rc) return rc;
+    if (deriv_axis < -1 || deriv_axis > 3 || (deriv_axis == 3 && ncomp != 3)) {
+        set_error("bl_include: deriv_axis must be -1..2, or 3 (divergence) with ncomp = 3");
+        return LDDMM_EINVAL;
+    }
+    const int K = tw.K, KH = K / 2;
+    const int nout = deriv_axis == 3 ? 1 : ncomp;
+    const float2* src = c;
+    if (bspline) {
+        // s1 holds the divided cube first (ncomp*K^3 <= scratch size), then stage Y output
+        long n = (long)ncomp * K * K * K;
+        KTRACE("cube_bspline_div", st, 16.0 * n, 0);
+        k_cube_bspline_div<<<cdiv(n, 256), 256, 0, st>>>(c, ncomp, K, g.nx, g.ny, g.nz, s1);
+        LDDMM_CHECK_LAUNCH();
+        src = s1;
+    }
+    long total = (long)nout * g.nz * K * KH;
+    KTRACE("iota_z", st, (double)(deriv_axis == 3 ? 3 : nout) * K * K * K * 8.0 + total * 8.0,
+           (double)total * K * 8.0);
+    k_iota_z<<<cdiv(total, 256), 256, 0, st>>>(src, nout, g.nz, K, KH, deriv_axis, tw.cz,
+                                               tw.sz, s2);
+    LDDMM_CHECK_LAUNCH();
+    int nslabs = nout * g.nz;
+    size_t smem = (size_t)K * g.ny * 8 + (size_t)K * KH * 8;
+    if (smem > 227 * 1024) {
+        set_error("bl_include: ny too large for the y stage");
+        return LDDMM_EINVAL;
+    }
+    static bool attr_set = false;
+    if (!attr_set) {
+        LDDMM_CUDA(cudaFuncSetAttribute(k_iota_y, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        227 * 1024));
+        attr_set = true;
+    }
+    {
+        KTRACE("iota_y", st, (double)nslabs * (K + g.ny) * KH * 8.0, (double)nslabs * g.ny * KH * K * 8.0);
+        k_iota_y<<<std::min(nslabs, 2 * 148), 256, smem, st>>>(s2, nslabs, g.ny, K, KH, tw.cy, tw.sy,
+                                                              s1);
+    }
+    LDDMM_CHECK_LAUNCH();
+    return KHP_DISPATCH(KH, launch_iota_x, g, tw, s1, nout, f, fstride, st);
+}
+
+// ------------------------------------------------------------------------ cube kernels
+__global__ void k_cube_axpby(float2* out, float a, const float2* x, float b, const float2* y,
+                             long n) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float2 r = make_float2(0.f, 0.f);
+    if (x) { float2 v = x[i]; r.x = a * v.x; r.y = a * v.y; }
+    if (y) { float2 v = y[i]; r.x = fmaf(b, v.x, r.x); r.y = fmaf(b, v.y, r.y); }
+    out[i] = r;
+}
+
+int cube_axpby(float2* out, float a, const float2* x, float b, const float2* y, long n,
+               cudaStream_t st) {
+    KTRACE("cube_axpby", st, 24.0 * n, 4.0 * n);
+    k_cube_axpby<<<cdiv(n, 256), 256, 0, st>>>(out, a, x, b, y, n);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+__global__ void k_cube_L(float2* out, const float2* x, float wL, float a, const float2* y, int K,
+                         long n, double alpha, int s, int mode) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    int jx = (int)(i % K), jy = (int)((i / K) % K), jz = (int)((i / ((long)K * K)) % K);
+    const int h = K / 2;
+    float2 r = make_float2(0.f, 0.f);
+    if (jx >= 1 && jy >= 1 && jz >= 1) {
+        double k2 = (double)(jx - h) * (jx - h) + (double)(jy - h) * (jy - h) +
+                    (double)(jz - h) * (jz - h);
+        double base = 1.0 + alpha * k2, w = 1.0;
+        for (int e = 0; e < s; ++e) w *= base;
+        float f = (float)(mode > 0 ? w : 1.0 / w) * wL;
+        float2 v = x[i];
+        r = make_float2(f * v.x, f * v.y);
+        if (y && mode > 0) {
+            float2 u = y[i];
+            r.x = fmaf(a, u.x, r.x);
+            r.y = fmaf(a, u.y, r.y);
+        }
+    }
+    out[i] = r;
+}
+
+int cube_apply_L(float2* out, const float2* x, float wL, float a, const float2* y, int K,
+                 int ncomp, double alpha, int s, int mode, cudaStream_t st) {
+    long n = (long)ncomp * K * K * K;
+    KTRACE("cube_L", st, 24.0 * n, 4.0 * n);
+    k_cube_L<<<cdiv(n, 256), 256, 0, st>>>(out, x, wL, a, y, K, n, alpha, s, mode);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+__global__ void k_cube_hermitian(float2* c, int K, long n) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    long kk = (long)K * K * K;
+    long comp = i / kk;
+    long r = i - comp * kk;
+    int jx = (int)(r % K), jy = (int)((r / K) % K), jz = (int)(r / ((long)K * K));
+    if (jx == 0 || jy == 0 || jz == 0) { c[i] = make_float2(0.f, 0.f); return; }
+    long m = comp * kk + ((long)(K - jz) * K + (K - jy)) * K + (K - jx);
+    if (m < i) return;  // the lower index of each pair does the work
+    float2 a = c[i], b = c[m];
+    float2 h = make_float2(0.5f * (a.x + b.x), 0.5f * (a.y - b.y));
+    c[i] = h;
+    c[m] = make_float2(h.x, -h.y);
+}
+
+int cube_hermitian(float2* c, int K, int ncomp, cudaStream_t st) {
+    long n = (long)ncomp * K * K * K;
+    KTRACE("cube_hermitian", st, 16.0 * n, 0);
+    k_cube_hermitian<<<cdiv(n, 256), 256, 0, st>>>(c, K, n);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+// ------------------------------------------------------------------- FP64 reductions
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+template <bool MAX>
+__device__ void block_reduce_store(double v, double* out) {
+    __shared__ double part[32];
+    v = MAX ? warp_max(v) : warp_sum(v);
+    int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    if (lane == 0) part[w] = v;
+    __syncthreads();
+    if (w == 0) {
+        int nw = blockDim.x >> 5;
+        v = lane < nw ? part[lane] : 0.0;
+        v = MAX ? warp_max(v) : warp_sum(v);
+        if (lane == 0) *out = v;
+    }
+}
+
+__global__ void k_dot_f2(const float2* a, const float2* b, long n, double* partials) {
+    double s = 0.0;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        float2 x = a[i], y = b[i];
+        s += (double)x.x * y.x + (double)x.y * y.y;
+    }
+    block_reduce_store<false>(s, partials + blockIdx.x);
+}
+
+__global__ void k_maxabs_f2(const float2* a, long n, double* partials) {
+    double s = 0.0;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        float2 x = a[i];
+        s = fmax(s, sqrt((double)x.x * x.x + (double)x.y * x.y));
+    }
+    block_reduce_store<true>(s, partials + blockIdx.x);
+}
+
+__global__ void k_finalize(const double* partials, int n, double* out, int is_max) {
+    double s = 0.0;
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        s = is_max ? fmax(s, partials[i]) : s + partials[i];
+    if (is_max) block_reduce_store<true>(s, out);
+    else block_reduce_store<false>(s, out);
+}
+
+int dot_f2(const float2* a, const float2* b, long n, double* partials, double* out,
+           cudaStream_t st) {
+    {
+        KTRACE("dot_f2", st, 16.0 * n, 4.0 * n);
+        k_dot_f2<<<kReduceBlocks, 256, 0, st>>>(a, b, n, partials);
+    }
+    LDDMM_CHECK_LAUNCH();
+    KTRACE("finalize", st, 8.0 * kReduceBlocks, kReduceBlocks);
+    k_finalize<<<1, 256, 0, st>>>(partials, kReduceBlocks, out, 0);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+int max_abs_f2(const float2* a, long n, double* partials, double* out, cudaStream_t st) {
+    {
+        KTRACE("maxabs_f2", st, 8.0 * n, 3.0 * n);
+        k_maxabs_f2<<<kReduceBlocks, 256, 0, st>>>(a, n, partials);
+    }
+    LDDMM_CHECK_LAUNCH();
+    KTRACE("finalize", st, 8.0 * kReduceBlocks, kReduceBlocks);
+    k_finalize<<<1, 256, 0, st>>>(partials, kReduceBlocks, out, 1);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+int finalize_sum(const double* partials, int n, double* out, cudaStream_t st) {
+    KTRACE("finalize", st, 8.0 * n, n);
+    k_finalize<<<1, 256, 0, st>>>(partials, n, out, 0);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+}  // namespace lddmm

@@ -1,0 +1,54 @@
+"""The C-ABI library loads and exports every declared entry point; host-side argument
+validation answers without touching a GPU."""
+import ctypes
+
+import pytest
+
+import paper_2006_06823_b300 as L
+
+
+def test_library_exports_every_declared_function():
+    lib = L.load()
+    names = L.header_functions()
+    assert "lddmm_register" in names and "lddmm_bl_project" in names
+    missing = [n for n in names if not hasattr(lib, n)]
+    assert missing == []
+
+
+def test_version_and_empty_error():
+    lib = L.load()
+    assert b"sm_103a" in lib.lddmm_version()
+    assert isinstance(lib.lddmm_last_error(), bytes)
+
+
+@pytest.mark.parametrize("field,value", [("K", 7), ("K", 2), ("K", 40), ("nt", 0),
+                                         ("variant", 2), ("interp", 2), ("sigma2", 0.0),
+                                         ("nx", 3), ("precision", 5), ("max_pcg", 0)])
+def test_create_rejects_bad_parameters_before_any_device_work(field, value):
+    lib = L.load()
+    p = L.Params(32, 32, 32, 16, 10, L.V_DEFSTATE, L.INTERP_LINEAR, 0.0025, 2, 0.01, 5, 10,
+                 1e-3, L.PREC_FP32)
+    setattr(p, field, value)
+    h = ctypes.c_void_p(123)
+    rc = lib.lddmm_create(ctypes.byref(p), None, ctypes.byref(h))
+    assert rc == L.EINVAL
+    assert h.value is None
+    assert len(lib.lddmm_last_error()) > 0
+
+
+def test_standalone_calls_reject_bad_shapes_before_any_device_work():
+    lib = L.load()
+    assert lib.lddmm_bl_project(1, 8, 8, 4, ctypes.c_void_p(16), 1, ctypes.c_void_p(16), 0, None) == L.EINVAL
+    assert lib.lddmm_bl_include(8, 8, 8, 4, None, 1, None, -1, 0, 0, None) == L.EINVAL
+    assert lib.lddmm_sl_transport(8, 8, 8, 0, 1, ctypes.c_void_p(16), ctypes.c_void_p(16), 1, 1,
+                                  ctypes.c_void_p(16), None) == L.EINVAL
+    assert lib.lddmm_sl_characteristics(8, 8, 8, ctypes.c_void_p(16), 0.1, 2, 1,
+                                        ctypes.c_void_p(16), None) == L.EINVAL
+    assert lib.lddmm_destroy(None) == L.OK
+
+
+def test_null_context_is_rejected():
+    lib = L.load()
+    rep = L.Report()
+    assert lib.lddmm_register(None, ctypes.c_void_p(16), None, ctypes.byref(rep)) == L.EINVAL
+    assert lib.lddmm_objective(None, ctypes.c_void_p(16), None, None, None) == L.EINVAL

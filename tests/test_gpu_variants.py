@@ -1,0 +1,136 @@
+"""GPU parity of energies, gradients, GN Hessian-vector products and full registrations
+against the FP64 oracle, through the C ABI (lddmm_create / objective / gradient /
+hessian_matvec / register)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from oracle import gnk
+from oracle import spectral as S
+from oracle import variants as Vn
+from paper_2006_06823_b300 import synth
+from _problems import oracle_problem, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+import paper_2006_06823_b300 as L  # noqa: E402
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def devc(c):
+    return torch.as_tensor(np.ascontiguousarray(c).astype(np.complex64), device="cuda")
+
+
+def dev(a):
+    return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float32, device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy().astype(np.complex128)
+
+
+def gpu_context(prob, **kw):
+    nz, ny, nx = prob.shape
+    p = prob.p
+    ctx = L.Context(nx, ny, nz, p.K, nt=p.nt, variant=p.variant, interp=p.order, alpha=p.alpha,
+                    s=p.s, sigma2=p.sigma2, **kw)
+    ctx.set_images(dev(prob.I0), dev(prob.I1))
+    return ctx
+
+
+CASES = [((16, 16, 16), 8, Vn.DEFSTATE, 1), ((16, 16, 16), 8, Vn.DEFSTATE, 3),
+         ((16, 16, 16), 8, Vn.IMAGE, 1), ((16, 16, 16), 8, Vn.IMAGE, 3),
+         ((20, 24, 28), 10, Vn.DEFSTATE, 1), ((20, 24, 28), 10, Vn.IMAGE, 1)]
+
+
+@pytest.mark.parametrize("shape,K,variant,order", CASES)
+def test_objective_gradient_hessian_match_oracle(shape, K, variant, order):
+    prob = oracle_problem(shape, K, variant, order, nt=5)
+    vt = synth.random_velocity_coeffs(K, K, seed=3) * 0.5
+    E, Er, Ed, g = prob.gradient(vt)
+    dv = synth.random_coeffs(K, seed=4) * 0.1
+    Hdv = prob.hessian_matvec(vt, dv)
+    with gpu_context(prob) as ctx:
+        Eg, Erg, Edg = ctx.objective(devc(vt))
+        assert Eg == pytest.approx(E, rel=1e-5)
+        assert Erg == pytest.approx(Er, rel=1e-6)
+        (E2, _, _), gg = ctx.gradient(devc(vt))
+        assert E2 == pytest.approx(E, rel=1e-5)
+        assert rel_l2(host(gg), g) < 1e-4
+        Hg = ctx.hessian_matvec(devc(vt), devc(dv))
+        assert rel_l2(host(Hg), Hdv) < 1e-4
+
+
+def test_hessian_recomputes_state_for_a_new_velocity():
+    prob = oracle_problem((16, 16, 16), 8, Vn.DEFSTATE, 1, nt=4)
+    v1 = synth.random_velocity_coeffs(8, 8, seed=5) * 0.5
+    v2 = synth.random_velocity_coeffs(8, 8, seed=6) * 0.5
+    dv = synth.random_coeffs(8, seed=7) * 0.1
+    with gpu_context(prob) as ctx:
+        ctx.gradient(devc(v1))
+        H = ctx.hessian_matvec(devc(v2), devc(dv))
+    assert rel_l2(host(H), prob.hessian_matvec(v2, dv)) < 1e-4
+
+
+def test_small_registration_matches_stored_oracle_result():
+    ref = json.load(open(os.path.join(HERE, "golden", "config1_seed0.json")))
+    v_ref = np.load(os.path.join(HERE, "golden", "config1_seed0.npz"))["v"]
+    c = ref["config"]
+    prob = oracle_problem(tuple(c["shape"]), c["K"], c["variant"], c["order"], nt=c["nt"],
+                          seed=c["seed"])
+    with gpu_context(prob, max_gn=c["max_gn"], max_pcg=c["max_pcg"], gtol=c["gtol"]) as ctx:
+        v, rep = ctx.register()
+    v = host(v)
+    assert rep["gn_iters"] == ref["gn_iters"]
+    assert rep["pcg_iters_total"] == ref["pcg_iters_total"]
+    assert rep["stop_reason"] == ref["stop_reason"]
+    assert rep["E"] == pytest.approx(ref["E"], rel=1e-3)
+    assert rep["E0"] == pytest.approx(ref["E0"], rel=1e-5)
+    # displacement of phi(1) from both velocities, by the oracle
+    nz, ny, nx = prob.shape
+    uo = S.include(prob.state_defstate(v_ref)[-1], prob.shape)
+    ug = S.include(prob.state_defstate(v)[-1], prob.shape)
+    scale = (np.array([nx, ny, nz]) / (2 * np.pi))[:, None, None, None]
+    assert np.abs((uo - ug) * scale).max() < 1e-2
+
+
+@pytest.mark.parametrize("variant,order", [(Vn.DEFSTATE, 3), (Vn.IMAGE, 1)])
+def test_live_registration_matches_oracle(variant, order):
+    prob = oracle_problem((16, 16, 16), 8, variant, order, nt=5)
+    v_o, rep_o = gnk.register(prob, max_gn=3, max_pcg=5)
+    with gpu_context(prob, max_gn=3, max_pcg=5) as ctx:
+        v, rep = ctx.register()
+    assert rep["gn_iters"] == rep_o.gn_iters
+    assert rep["pcg_iters_total"] == rep_o.pcg_iters_total
+    assert rep["E"] == pytest.approx(rep_o.E, rel=1e-3)
+    assert rep["mse_rel"] == pytest.approx(rep_o.mse_rel, rel=1e-3)
+
+
+def test_warm_start_uses_reference_norms():
+    prob = oracle_problem((16, 16, 16), 8, Vn.DEFSTATE, 1, nt=4)
+    with gpu_context(prob, max_gn=2, max_pcg=5) as ctx:
+        v, rep = ctx.register()
+        g0 = host(ctx.gradient(ctx.zeros_cube())[1])
+        norms = (float(np.sqrt(S.inner(g0, g0))), float(np.abs(g0).max()))
+        v2, rep2 = ctx.register(v.clone(), g_ref_norms=norms)
+    assert rep2["E0"] == pytest.approx(rep["E"], rel=1e-4)
+    assert rep2["E"] <= rep["E"] * (1 + 1e-6)
+
+
+def test_nonfinite_image_is_reported_and_sticky():
+    prob = oracle_problem((16, 16, 16), 8, Vn.DEFSTATE, 1, nt=4)
+    I0 = prob.I0.copy()
+    I0[3, 4, 5] = np.nan
+    nz, ny, nx = prob.shape
+    ctx = L.Context(nx, ny, nz, 8, nt=4)
+    ctx.set_images(dev(I0), dev(prob.I1))
+    with pytest.raises(L.LddmmError) as e:
+        ctx.objective(ctx.zeros_cube())
+    assert e.value.code == L.ENONFINITE
+    with pytest.raises(L.LddmmError):
+        ctx.objective(ctx.zeros_cube())
+    ctx.close()
