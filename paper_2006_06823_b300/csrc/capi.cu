@@ -74,6 +74,7 @@ struct lddmm_ctx {
     // cache
     bool vel_valid = false;    // velocity fields + state of cv[C_CUR]
     bool traj_valid = false;   // + Jacobians / grad m~ for the Hessian
+    bool warp_valid = false;   // DEFSTATE: m1 and G of the current state
     int solves = 0;
 };
 
@@ -101,6 +102,10 @@ static int validate(const lddmm_params* p) {
     if (!p) { set_error("params is NULL"); return LDDMM_EINVAL; }
     if (p->nx < 4 || p->ny < 4 || p->nz < 4 || p->nx > 1024 || p->ny > 1024 || p->nz > 4096) {
         set_error("grid must be 4..1024 (x, y) and 4..4096 (z) voxels per axis");
+        return LDDMM_EINVAL;
+    }
+    if ((long)p->nx * p->ny * p->nz > 0x7fffffffL / 3) {
+        set_error("grid too large: nx*ny*nz must stay below 2^31/3 voxels");
         return LDDMM_EINVAL;
     }
     if (p->K < 4 || (p->K & 1) || p->K > 64 || p->K > p->nx || p->K > p->ny || p->K > p->nz) {
@@ -221,6 +226,7 @@ static int data_term(lddmm_ctx* c, float* rho) {
         TRY(sl_warp_image(c->sl, I0src, c->fa, c->to_vox, c->I1, c->p.sigma2, c->m1, c->G, rho,
                           c->partials, c->st));
         TRY(finalize_sum(c->partials, kReduceBlocks, c->dsc, c->st));
+        c->warp_valid = true;
     } else {
         TRY(sum_sq_diff(c->ms + (long)c->p.nt * n, c->I1, n, c->partials, c->dsc, c->st));
     }
@@ -243,6 +249,7 @@ static int ensure_state(lddmm_ctx* c, const float2* vt, bool known_same) {
         LDDMM_CUDA(cudaMemcpyAsync(cur, vt, 3 * c->kc * sizeof(float2), cudaMemcpyDeviceToDevice, c->st));
     c->vel_valid = false;
     c->traj_valid = false;
+    c->warp_valid = false;
     TRY(prepare_velocity(c, cur));
     if (c->p.variant == LDDMM_V_DEFSTATE) TRY(state_defstate(c));
     else TRY(state_image(c));
@@ -371,6 +378,7 @@ static int gradient_impl(lddmm_ctx* c, const float2* vt, bool known_same, float2
 // Gauss-Newton H dv~ at the current velocity (state and trajectory must be current).
 static int hessian_impl(lddmm_ctx* c, const float2* dvt, float2* out) {
     TRY(ensure_traj(c));
+    if (c->p.variant == LDDMM_V_DEFSTATE && !c->warp_valid) TRY(data_term(c, nullptr));
     const long n = c->n, kc3 = 3 * c->kc;
     const int nt = c->p.nt;
     TRY(include(c, dvt, 3, c->dvsp, n, -1, 0));
@@ -674,7 +682,7 @@ static int check_ctx(lddmm_ctx* c) {
     } while (0)
 
 static int after_images(lddmm_ctx* c) {
-    c->vel_valid = c->traj_valid = false;
+    c->vel_valid = c->traj_valid = c->warp_valid = false;
     if (cubic(c)) TRY(bspline_prefilter(c->g, c->I0, 1, c->I0c, c->st));
     return LDDMM_OK;
 }
@@ -804,6 +812,10 @@ struct PoolScratch {
 static int check_grid(int nx, int ny, int nz) {
     if (nx < 2 || ny < 2 || nz < 2 || nx > 1024 || ny > 1024 || nz > 4096) {
         set_error("grid must be 2..1024 (x, y) and 2..4096 (z) voxels per axis");
+        return LDDMM_EINVAL;
+    }
+    if ((long)nx * ny * nz > 0x7fffffffL / 3) {
+        set_error("grid too large: nx*ny*nz must stay below 2^31/3 voxels");
         return LDDMM_EINVAL;
     }
     return LDDMM_OK;

@@ -26,19 +26,19 @@ __device__ __forceinline__ int wrapi(int i, int n) {
 
 // Trilinear cell: corner offsets and fractions.
 struct LinCell {
-    long x0, x1, y0, y1, z0, z1;
+    int x0, x1, y0, y1, z0, z1;   // offsets within one component (< 2^31 voxels)
     float tx, ty, tz;
 };
 
-__device__ __forceinline__ void lin_axis(int j, float D, int n, long mul, long& a0, long& a1,
+__device__ __forceinline__ void lin_axis(int j, float D, int n, int mul, int& a0, int& a1,
                                          float& t) {
     D = clampD(D);
     float fl = floorf(D);
     t = D - fl;
     int i = wrapi(j + (int)fl, n);
     int i1 = i + 1 == n ? 0 : i + 1;
-    a0 = (long)i * mul;
-    a1 = (long)i1 * mul;
+    a0 = i * mul;
+    a1 = i1 * mul;
 }
 
 __device__ __forceinline__ LinCell lin_cell(const Grid& g, int x, int y, int z, float dx, float dy,
@@ -46,7 +46,7 @@ __device__ __forceinline__ LinCell lin_cell(const Grid& g, int x, int y, int z, 
     LinCell c;
     lin_axis(x, dx, g.nx, 1, c.x0, c.x1, c.tx);
     lin_axis(y, dy, g.ny, g.nx, c.y0, c.y1, c.ty);
-    lin_axis(z, dz, g.nz, (long)g.nx * g.ny, c.z0, c.z1, c.tz);
+    lin_axis(z, dz, g.nz, g.nx * g.ny, c.z0, c.z1, c.tz);
     return c;
 }
 
@@ -81,7 +81,7 @@ __device__ __forceinline__ float lin_eval_grad(const float* __restrict__ f, cons
 
 // Cubic B-spline cell: 4 taps per axis (i-1 .. i+2) and their weights.
 struct CubCell {
-    long ox[4], oy[4], oz[4];
+    int ox[4], oy[4], oz[4];
     float wx[4], wy[4], wz[4];
 };
 
@@ -100,14 +100,14 @@ __device__ __forceinline__ void cub_dweights(float t, float w[4]) {
     w[3] = 0.5f * t * t;
 }
 
-__device__ __forceinline__ void cub_axis(int j, float D, int n, long mul, long o[4], float& t) {
+__device__ __forceinline__ void cub_axis(int j, float D, int n, int mul, int o[4], float& t) {
     D = clampD(D);
     float fl = floorf(D);
     t = D - fl;
     int i = wrapi(j + (int)fl - 1, n);
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
-        o[q] = (long)i * mul;
+        o[q] = i * mul;
         i = i + 1 == n ? 0 : i + 1;
     }
 }
@@ -117,7 +117,7 @@ __device__ __forceinline__ CubCell cub_cell(const Grid& g, int x, int y, int z, 
     CubCell c;
     cub_axis(x, dx, g.nx, 1, c.ox, tf[0]);
     cub_axis(y, dy, g.ny, g.nx, c.oy, tf[1]);
-    cub_axis(z, dz, g.nz, (long)g.nx * g.ny, c.oz, tf[2]);
+    cub_axis(z, dz, g.nz, g.nx * g.ny, c.oz, tf[2]);
     cub_weights(tf[0], c.wx);
     cub_weights(tf[1], c.wy);
     cub_weights(tf[2], c.wz);
@@ -210,14 +210,15 @@ struct Interp<3> {
     const int z = blockIdx.z;                                   \
     if (x >= g.nx || y >= g.ny) return;                         \
     const long n = g.ntot();                                    \
-    const long i = ((long)z * g.ny + y) * g.nx + x;
+    const int i = (z * g.ny + y) * g.nx + x;
 
 static inline dim3 vox_grid(const Grid& g) { return dim3(cdiv(g.nx, 32), cdiv(g.ny, 8), g.nz); }
 static const dim3 kVoxBlock(32, 8, 1);
 
 // ---------------------------------------------------------------- characteristics
 template <int IP>
-__global__ void k_sl_char(Grid g, const float* __restrict__ vsrc, const float* __restrict__ vval,
+__global__ void __launch_bounds__(256, IP == 3 ? 2 : 3)
+k_sl_char(Grid g, const float* __restrict__ vsrc, const float* __restrict__ vval,
                           float s0, float s1, float s2, float dts, float* __restrict__ D) {
     VOXEL_PROLOGUE
     float V0 = vval[i] * s0, V1 = vval[n + i] * s1, V2 = vval[2 * n + i] * s2;
@@ -243,18 +244,40 @@ int sl_characteristics(const SLArgs& a, const float* vsrc, const float* vval, co
 }
 
 // ---------------------------------------------------------------- gathers
-// MODE 0: out = src o X; 1: * aux(x) (one plane); 2: + aux[c](x)
-template <int IP, int MODE>
-__global__ void k_sl_gather(Grid g, const float* __restrict__ src, const float* __restrict__ D,
-                            const float* __restrict__ aux, int ncomp, float* __restrict__ out) {
+// MODE 0: out = src o X; 1: * aux(x) (one plane); 2: + aux[c](x). NC components;
+// launch bounds keep the kernel at <= 64 registers (8 warps x 4 CTAs per SM).
+template <int IP, int MODE, int NC>
+__global__ void __launch_bounds__(256, IP == 3 ? 2 : 4)
+k_sl_gather(Grid g, const float* __restrict__ src, const float* __restrict__ D,
+            const float* __restrict__ aux, float* __restrict__ out) {
     VOXEL_PROLOGUE
-    Interp<IP> it(g, x, y, z, D[i], D[n + i], D[2 * n + i]);
-    float sc = MODE == 1 ? aux[i] : 1.f;
-    for (int c = 0; c < ncomp; ++c) {
+    Interp<IP> it(g, x, y, z, __ldcs(D + i), __ldcs(D + n + i), __ldcs(D + 2 * n + i));
+    float sc = MODE == 1 ? __ldcs(aux + i) : 1.f;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
         float v = it(src + c * n);
         if (MODE == 1) v *= sc;
-        if (MODE == 2) v += aux[c * n + i];
-        out[c * n + i] = v;
+        if (MODE == 2) v += __ldcs(aux + c * n + i);
+        __stcs(out + c * n + i, v);
+    }
+}
+
+template <int IP, int MODE>
+static void launch_gather_nc(const SLArgs& a, const float* src, const float* D, const float* aux,
+                             int ncomp, float* out, cudaStream_t st) {
+    const long n = a.g.ntot();
+    for (int c0 = 0; c0 < ncomp;) {
+        int left = ncomp - c0;
+        const float* s = src + c0 * n;
+        const float* x = MODE == 2 ? aux + c0 * n : aux;
+        float* o = out + c0 * n;
+        if (left >= 3) {
+            k_sl_gather<IP, MODE, 3><<<vox_grid(a.g), kVoxBlock, 0, st>>>(a.g, s, D, x, o);
+            c0 += 3;
+        } else {
+            k_sl_gather<IP, MODE, 1><<<vox_grid(a.g), kVoxBlock, 0, st>>>(a.g, s, D, x, o);
+            c0 += 1;
+        }
     }
 }
 
@@ -266,9 +289,9 @@ static int launch_gather(const SLArgs& a, const float* src, const float* D, cons
     KTRACE(names[a.interp == 3][MODE], st,
            (double)a.g.ntot() * (12.0 + 8.0 * ncomp + (MODE == 1 ? 4.0 : MODE == 2 ? 4.0 * ncomp : 0.0)), 0);
     if (a.interp == 3)
-        k_sl_gather<3, MODE><<<vox_grid(a.g), kVoxBlock, 0, st>>>(a.g, src, D, aux, ncomp, out);
+        launch_gather_nc<3, MODE>(a, src, D, aux, ncomp, out, st);
     else
-        k_sl_gather<1, MODE><<<vox_grid(a.g), kVoxBlock, 0, st>>>(a.g, src, D, aux, ncomp, out);
+        launch_gather_nc<1, MODE>(a, src, D, aux, ncomp, out, st);
     LDDMM_CHECK_LAUNCH();
     return LDDMM_OK;
 }
@@ -289,7 +312,8 @@ int sl_gather_add(const SLArgs& a, const float* src, const float* D, const float
 // ---------------------------------------------------------------- stationary factors
 // Backward Heun step of -D_t u = u d folds into u^j(x) = u^{j+1}(X+) gam(x).
 template <int IP>
-__global__ void k_prep_adjoint(Grid g, const float* __restrict__ dsrc,
+__global__ void __launch_bounds__(256, IP == 3 ? 2 : 3)
+k_prep_adjoint(Grid g, const float* __restrict__ dsrc,
                                const float* __restrict__ dval, const float* __restrict__ Dp,
                                float dt, float* __restrict__ gam) {
     VOXEL_PROLOGUE
@@ -312,7 +336,8 @@ int sl_prep_adjoint(const SLArgs& a, const float* dsrc, const float* dval, const
 
 // Deformation state source term with stationary v: W = dt/2 (v(X) + v(x)).
 template <int IP>
-__global__ void k_prep_source(Grid g, const float* __restrict__ vsrc,
+__global__ void __launch_bounds__(256, IP == 3 ? 2 : 3)
+k_prep_source(Grid g, const float* __restrict__ vsrc,
                               const float* __restrict__ vval, const float* __restrict__ D,
                               float dt, float* __restrict__ W) {
     VOXEL_PROLOGUE
@@ -413,7 +438,8 @@ int sl_warp_image(const SLArgs& a, const float* I0src, const float* u1, const fl
 // ---------------------------------------------------------------- incremental state
 // D~_t du~ = dv~ - D~u~ * dv~ (Table 1 row 7): F = dv - (Du) dv, Heun along X.
 template <int IP>
-__global__ void k_inc_defstate(Grid g, const float* __restrict__ U, const float* __restrict__ D,
+__global__ void __launch_bounds__(256, IP == 3 ? 2 : 3)
+k_inc_defstate(Grid g, const float* __restrict__ U, const float* __restrict__ D,
                                const float* __restrict__ Fold, const float* __restrict__ Du,
                                const float* __restrict__ dv, float dt, float* __restrict__ out,
                                float* __restrict__ Fnew) {
@@ -657,7 +683,8 @@ int bspline_prefilter(const Grid& g, const float* in, int ncomp, float* out, cud
 // Incremental state, D~_t dm~ = -grad~ m~ * dv~ (Table 1 row 5): F = -Gm . dv,
 // out = U o X + dt/2 (Fold o X + Fnew).
 template <int IP>
-__global__ void k_inc_image(Grid g, const float* __restrict__ U, const float* __restrict__ D,
+__global__ void __launch_bounds__(256, IP == 3 ? 2 : 3)
+k_inc_image(Grid g, const float* __restrict__ U, const float* __restrict__ D,
                             const float* __restrict__ Fold, const float* __restrict__ Gm,
                             const float* __restrict__ dv, float dt, float* __restrict__ out,
                             float* __restrict__ Fnew) {

@@ -97,15 +97,34 @@ k_pi_x(const float* __restrict__ f, long fstride, long rows_per_comp, int ncomp,
     }
     const long rows = rows_per_comp * ncomp;
     const long row0 = (long)blockIdx.x * PX_ROWS;
-    for (int r = 0; r < PX_ROWS; ++r) {
-        long row = row0 + r;
-        const float* src = nullptr;
-        if (row < rows) {
-            long comp = row / rows_per_comp;
-            src = f + comp * fstride + (row - comp * rows_per_comp) * nx;
+    const bool contiguous = fstride == rows_per_comp * nx;
+    if (contiguous && (nx & 3) == 0 && (reinterpret_cast<uintptr_t>(f) & 15) == 0) {
+        // the CTA's rows are one contiguous chunk: every 16-byte copy in flight at once
+        const int q4 = nx >> 2;
+        const float* base = f + row0 * nx;
+        for (int e = tid; e < PX_ROWS * q4; e += NT) {
+            int r = e / q4, qq = e - r * q4;
+            float* dst = &frow[r * ldr + 4 * qq];
+            if (row0 + r < rows) {
+                unsigned sa = (unsigned)__cvta_generic_to_shared(dst);
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa),
+                             "l"(base + (long)e * 4));
+            } else {
+                *reinterpret_cast<float4*>(dst) = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
         }
-        for (int x = tid; x < nxp; x += NT)
-            frow[r * ldr + x] = (src && x < nx) ? __ldcs(src + x) : 0.f;
+        asm volatile("cp.async.wait_all;\n" ::: "memory");
+    } else {
+        for (int r = 0; r < PX_ROWS; ++r) {
+            long row = row0 + r;
+            const float* src = nullptr;
+            if (row < rows) {
+                long comp = row / rows_per_comp;
+                src = f + comp * fstride + (row - comp * rows_per_comp) * nx;
+            }
+            for (int x = tid; x < nxp; x += NT)
+                frow[r * ldr + x] = (src && x < nx) ? __ldcs(src + x) : 0.f;
+        }
     }
     __syncthreads();
 
@@ -192,10 +211,59 @@ __global__ void k_pi_y(const float2* __restrict__ A, int nslabs, int ny, int KH,
 }
 
 // ------------------------------------------------------------------------ pi, stage Z
-// Thread per (comp, jz, jy, kx >= 0); also writes the Hermitian mirror and the zero slots.
-__global__ void k_pi_z(const float2* __restrict__ B, int ncomp, int nz, int K, int KH,
-                       const float* __restrict__ cosT, const float* __restrict__ sinT,
-                       float inv_n, float2* __restrict__ c) {
+// Partial sums over a block of z planes: CTA (comp, 64 (jy, kx) columns, z block), thread
+// (column, jz residue class mod 4). part[split][comp][jz][col] = sum_z B[z][col] e^{-i kz z}.
+constexpr int PZ_COLS = 64;
+
+__global__ void __launch_bounds__(256)
+k_pi_z_part(const float2* __restrict__ B, int ncomp, int nz, int K, int KH, int zsplit,
+            const float* __restrict__ cosT, const float* __restrict__ sinT,
+            float2* __restrict__ part) {
+    extern __shared__ float4 smem4[];
+    float2* tw = reinterpret_cast<float2*>(smem4);  // [zl][jz]
+    const int ncol = K * KH;
+    const int colblocks = (ncol + PZ_COLS - 1) / PZ_COLS;
+    const int comp = blockIdx.x / colblocks;
+    const int col = (blockIdx.x - comp * colblocks) * PZ_COLS + (threadIdx.x & (PZ_COLS - 1));
+    const int jzg = threadIdx.x / PZ_COLS;  // 0..3
+    const int split = blockIdx.y;
+    const int zb = (nz + zsplit - 1) / zsplit;
+    const int z0 = split * zb, z1 = min(nz, z0 + zb);
+    for (int e = threadIdx.x; e < (z1 - z0) * K; e += blockDim.x) {
+        int zl = e / K, jz = e - zl * K;
+        long o = (long)jz * nz + z0 + zl;
+        tw[e] = make_float2(cosT[o], sinT[o]);
+    }
+    __syncthreads();
+    if (col >= ncol) return;
+    float re[16], im[16];
+#pragma unroll
+    for (int q = 0; q < 16; ++q) re[q] = im[q] = 0.f;
+    const float2* b = B + (long)comp * nz * ncol + col;
+    for (int z = z0; z < z1; ++z) {
+        const float2 v = b[(long)z * ncol];
+        const float2* t = tw + (z - z0) * K + jzg;
+#pragma unroll
+        for (int q = 0; q < 16; ++q) {
+            if (jzg + 4 * q < K) {
+                const float2 w = t[4 * q];
+                // v * (cos - i sin)
+                re[q] = fmaf(v.x, w.x, fmaf(v.y, w.y, re[q]));
+                im[q] = fmaf(v.y, w.x, fmaf(-v.x, w.y, im[q]));
+            }
+        }
+    }
+    float2* out = part + ((long)split * ncomp + comp) * K * ncol + col;
+#pragma unroll
+    for (int q = 0; q < 16; ++q) {
+        const int jz = jzg + 4 * q;
+        if (jz < K) out[(long)jz * ncol] = make_float2(re[q], im[q]);
+    }
+}
+
+// Sum of the z-block partials, 1/N normalisation, Hermitian mirror and zero slots.
+__global__ void k_pi_z_fin(const float2* __restrict__ part, int ncomp, int K, int KH, int zsplit,
+                           float inv_n, float2* __restrict__ c) {
     long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
     long total = (long)ncomp * K * K * KH;
     if (i >= total) return;
@@ -207,14 +275,12 @@ __global__ void k_pi_z(const float2* __restrict__ B, int ncomp, int nz, int K, i
     int comp = (int)(t / K);
     float re = 0.f, im = 0.f;
     if (jz >= 1 && jy >= 1) {
-        const float2* b = B + (long)comp * nz * K * KH + (long)jy * KH + kx;
-        const float* cz = cosT + (long)jz * nz;
-        const float* sz = sinT + (long)jz * nz;
-        for (int z = 0; z < nz; ++z) {
-            float2 v = b[(long)z * K * KH];
-            float cs = __ldg(cz + z), sn = __ldg(sz + z);
-            re = fmaf(v.x, cs, fmaf(v.y, sn, re));
-            im = fmaf(v.y, cs, fmaf(-v.x, sn, im));
+        const long stride = (long)ncomp * K * K * KH;
+        const float2* p = part + (((long)comp * K + jz) * K + jy) * KH + kx;
+        for (int sp = 0; sp < zsplit; ++sp) {
+            float2 v = p[sp * stride];
+            re += v.x;
+            im += v.y;
         }
         re *= inv_n;
         im *= inv_n;
@@ -303,113 +369,140 @@ int bl_project(const Grid& g, const Twiddles& tw, const float* f, long fstride, 
     if (rc) return rc;
     rc = KHP_DISPATCH(KH, launch_pi_y, g, tw, ncomp, s1, s2, st);
     if (rc) return rc;
+    // stage Z: z-block partial sums into s1 (free once stage Y has consumed it)
+    const int zsplit = std::max(1, std::min(8, g.nz / K));
+    const int colblocks = (K * KH + PZ_COLS - 1) / PZ_COLS;
+    {
+        size_t smem = (size_t)((g.nz + zsplit - 1) / zsplit) * K * 8;
+        KTRACE("pi_z", st, (double)ncomp * g.nz * K * KH * 8.0 + (double)zsplit * ncomp * K * K * KH * 8.0,
+               (double)ncomp * K * K * KH * g.nz * 8.0);
+        k_pi_z_part<<<dim3(ncomp * colblocks, zsplit), 256, smem, st>>>(s2, ncomp, g.nz, K, KH, zsplit,
+                                                                       tw.cz, tw.sz, s1);
+    }
+    LDDMM_CHECK_LAUNCH();
     long total = (long)ncomp * K * K * KH;
-    KTRACE("pi_z", st, (double)ncomp * g.nz * K * KH * 8.0 + (double)ncomp * K * K * K * 8.0,
-           (double)total * g.nz * 8.0);
-    k_pi_z<<<cdiv(total, 256), 256, 0, st>>>(s2, ncomp, g.nz, K, KH, tw.cz, tw.sz,
-                                             (float)(1.0 / (double)g.ntot()), c);
+    {
+        KTRACE("pi_z_fin", st, (double)zsplit * total * 8.0 + (double)ncomp * K * K * K * 8.0, 0);
+        k_pi_z_fin<<<cdiv(total, 256), 256, 0, st>>>(s1, ncomp, K, KH, zsplit,
+                                                     (float)(1.0 / (double)g.ntot()), c);
+    }
     LDDMM_CHECK_LAUNCH();
     return LDDMM_OK;
 }
 
-// ---------------------------------------------------------------------- iota, stage Z
-// T1[comp][z][jy][kx] = sum_{jz>=1} m(k) c[comp][jz][jy][K/2+kx] e^{+i kz 2pi z/nz}
-// m(k) = i k_axis (or 1 with deriv_axis = -1). Mode 3: one output, the divergence
-// sum_a i k_a c_a of a 3-component cube.
-__global__ void k_iota_z(const float2* __restrict__ c, int ncomp_out, int nz, int K, int KH,
-                         int deriv_axis, const float* __restrict__ cosT,
-                         const float* __restrict__ sinT, float2* __restrict__ T1) {
-    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    long total = (long)ncomp_out * nz * K * KH;
-    if (i >= total) return;
-    int kx = (int)(i % KH);
-    long t = i / KH;
-    int jy = (int)(t % K);
-    t /= K;
-    int z = (int)(t % nz);
-    int comp = (int)(t / nz);
-    const int h = K / 2;
-    float re = 0.f, im = 0.f;
-    if (jy >= 1) {
-        const float ky = (float)(jy - h);
-        for (int jz = 1; jz < K; ++jz) {
-            const float kz = (float)(jz - h);
-            float mre, mim;  // multiplier (complex) applied to the coefficient
-            float2 v;
-            if (deriv_axis == 3) {
-                // sum_a i k_a c_a
-                float2 a0 = c[(((long)0 * K + jz) * K + jy) * K + h + kx];
-                float2 a1 = c[(((long)1 * K + jz) * K + jy) * K + h + kx];
-                float2 a2 = c[(((long)2 * K + jz) * K + jy) * K + h + kx];
-                float sr = -((float)kx * a0.y + ky * a1.y + kz * a2.y);
-                float si = (float)kx * a0.x + ky * a1.x + kz * a2.x;
-                v = make_float2(sr, si);
-                mre = 1.f;
-                mim = 0.f;
-            } else {
-                v = c[(((long)comp * K + jz) * K + jy) * K + h + kx];
-                if (deriv_axis < 0) {
-                    mre = 1.f; mim = 0.f;
-                } else {
-                    float k = deriv_axis == 0 ? (float)kx : deriv_axis == 1 ? ky : kz;
-                    mre = 0.f; mim = k;
-                }
-            }
-            float vr = v.x * mre - v.y * mim;
-            float vi = v.x * mim + v.y * mre;
-            float cs = __ldg(cosT + (long)jz * nz + z), sn = __ldg(sinT + (long)jz * nz + z);
-            // (vr + i vi)(cs + i sn)
-            re = fmaf(vr, cs, fmaf(-vi, sn, re));
-            im = fmaf(vr, sn, fmaf(vi, cs, im));
-        }
-    }
-    T1[i] = make_float2(re, im);
-}
-
-// B-spline prefilter division on a cube copy: out = c / B^(k) (all three axes).
-__global__ void k_cube_bspline_div(const float2* __restrict__ c, int ncomp, int K, int nx, int ny,
-                                   int nz, float2* __restrict__ out) {
-    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
-    long n = (long)ncomp * K * K * K;
-    if (i >= n) return;
-    int jx = (int)(i % K);
-    int jy = (int)((i / K) % K);
-    int jz = (int)((i / ((long)K * K)) % K);
-    const int h = K / 2;
-    double bx = (2.0 + cospi(2.0 * (jx - h) / nx)) / 3.0;
-    double by = (2.0 + cospi(2.0 * (jy - h) / ny)) / 3.0;
-    double bz = (2.0 + cospi(2.0 * (jz - h) / nz)) / 3.0;
-    float inv = (float)(1.0 / (bx * by * bz));
-    float2 v = c[i];
-    out[i] = make_float2(v.x * inv, v.y * inv);
-}
-
-// ---------------------------------------------------------------------- iota, stage Y
-// T2[slab][y][kx] = sum_{jy>=1} T1[slab][jy][kx] e^{+i ky 2pi y/ny}
-__global__ void k_iota_y(const float2* __restrict__ T1, int nslabs, int ny, int K, int KH,
-                         const float* __restrict__ cosT, const float* __restrict__ sinT,
-                         float2* __restrict__ T2) {
+// ------------------------------------------------------------------- iota, stages Z+Y
+// One CTA per (comp, z) plane:
+//   T1[jy][kx] = sum_{jz>=1} m(k) c[comp][jz][jy][K/2+kx] e^{+i kz 2pi z/nz}    (smem)
+//   T2[y][kx]  = sum_{jy>=1} T1[jy][kx] e^{+i ky 2pi y/ny}                        (global)
+// m(k) = i k_axis (deriv_axis 0..2), the divergence sum_a i k_a c_a (deriv_axis 3), or 1;
+// divided by B^(k) = prod_a (2 + cos(2 pi k_a / n_a)) / 3 when bspline is set.
+template <int KHP>
+__global__ void __launch_bounds__(256)
+k_iota_zy(const float2* __restrict__ c, int nz, int ny, int nx, int K, int KH, int deriv_axis,
+          int bspline, const float* __restrict__ cxT, const float* __restrict__ cyT,
+          const float* __restrict__ czT, const float* __restrict__ szT,
+          const float* __restrict__ cyTab, const float* __restrict__ syTab,
+          float2* __restrict__ T2) {
     extern __shared__ float4 smem4[];
-    float2* tw = reinterpret_cast<float2*>(smem4);  // K * ny  [jy][y]
-    float2* st1 = tw + (long)K * ny;                // K * KH
-    const int nt = blockDim.x;
-    for (int e = threadIdx.x; e < K * ny; e += nt) tw[e] = make_float2(cosT[e], sinT[e]);
-    for (int slab = blockIdx.x; slab < nslabs; slab += gridDim.x) {
-        __syncthreads();
-        for (int e = threadIdx.x; e < K * KH; e += nt) st1[e] = T1[(long)slab * K * KH + e];
-        __syncthreads();
-        for (int e = threadIdx.x; e < ny * KH; e += nt) {
-            int y = e / KH, kx = e - y * KH;
-            float re = 0.f, im = 0.f;
-            for (int jy = 1; jy < K; ++jy) {
-                float2 v = st1[jy * KH + kx];
-                float2 t = tw[jy * ny + y];
-                re = fmaf(v.x, t.x, fmaf(-v.y, t.y, re));
-                im = fmaf(v.x, t.y, fmaf(v.y, t.x, im));
-            }
-            T2[(long)slab * ny * KH + e] = make_float2(re, im);
-        }
+    float2* twy = reinterpret_cast<float2*>(smem4);        // K * ny   [jy][y]
+    float2* t1 = twy + (long)K * ny;                        // K * KHP  [jy][kx]
+    float2* twz = t1 + (long)K * KHP;                       // K        e^{i kz z}
+    float* bx = reinterpret_cast<float*>(twz + K);          // KHP      1/B^_x(kx)
+    float* by = bx + KHP;                                   // K        1/B^_y(ky)
+    float* bz = by + K;                                     // K        1/B^_z(kz)
+    const int comp = blockIdx.x / nz, z = blockIdx.x - comp * nz;
+    const int h = K / 2;
+    const int tid = threadIdx.x, nt = blockDim.x;
+    for (int e = tid; e < K * ny; e += nt) twy[e] = make_float2(cyTab[e], syTab[e]);
+    for (int e = tid; e < K; e += nt) {
+        twz[e] = make_float2(czT[(long)e * nz + z], szT[(long)e * nz + z]);
+        by[e] = bspline ? 3.f / (2.f + cyT[(long)e * ny + 1]) : 1.f;
+        bz[e] = bspline ? 3.f / (2.f + czT[(long)e * nz + 1]) : 1.f;
     }
+    for (int e = tid; e < KHP; e += nt) bx[e] = (bspline && e < KH) ? 3.f / (2.f + cxT[(long)(h + e) * nx + 1]) : 1.f;
+    __syncthreads();
+    // stage Z
+    for (int e = tid; e < K * KHP; e += nt) {
+        const int jy = e / KHP, kx = e - jy * KHP;
+        float re = 0.f, im = 0.f;
+        if (jy >= 1 && kx < KH) {
+            const float ky = (float)(jy - h);
+#pragma unroll 4
+            for (int jz = 1; jz < K; ++jz) {
+                const float kz = (float)(jz - h);
+                float vr, vi;
+                if (deriv_axis == 3) {
+                    const long o = ((long)jz * K + jy) * K + h + kx;
+                    const long kk = (long)K * K * K;
+                    float2 a0 = c[o], a1 = c[kk + o], a2 = c[2 * kk + o];
+                    vr = -((float)kx * a0.y + ky * a1.y + kz * a2.y);
+                    vi = (float)kx * a0.x + ky * a1.x + kz * a2.x;
+                } else {
+                    float2 v = c[(((long)comp * K + jz) * K + jy) * K + h + kx];
+                    if (deriv_axis < 0) {
+                        vr = v.x;
+                        vi = v.y;
+                    } else {
+                        const float k = deriv_axis == 0 ? (float)kx : deriv_axis == 1 ? ky : kz;
+                        vr = -k * v.y;
+                        vi = k * v.x;
+                    }
+                }
+                const float b = bz[jz];
+                const float2 t = twz[jz];
+                re = fmaf(b * vr, t.x, fmaf(-b * vi, t.y, re));
+                im = fmaf(b * vr, t.y, fmaf(b * vi, t.x, im));
+            }
+            const float s = bx[kx] * by[jy];
+            re *= s;
+            im *= s;
+        }
+        t1[e] = make_float2(re, im);
+    }
+    __syncthreads();
+    // stage Y
+    float2* out = T2 + (long)blockIdx.x * ny * KH;
+    for (int e = tid; e < ny * KHP; e += nt) {
+        const int y = e / KHP, kx = e - y * KHP;
+        if (kx >= KH) continue;
+        float re = 0.f, im = 0.f;
+#pragma unroll 4
+        for (int jy = 1; jy < K; ++jy) {
+            const float2 v = t1[jy * KHP + kx];
+            const float2 t = twy[jy * ny + y];
+            re = fmaf(v.x, t.x, fmaf(-v.y, t.y, re));
+            im = fmaf(v.x, t.y, fmaf(v.y, t.x, im));
+        }
+        out[y * KH + kx] = make_float2(re, im);
+    }
+}
+
+template <int KHP>
+static int launch_iota_zy(const Grid& g, const Twiddles& tw, const float2* c, int nout,
+                          int deriv_axis, int bspline, float2* T2, cudaStream_t st) {
+    const int K = tw.K, KH = K / 2;
+    size_t smem = (size_t)K * g.ny * 8 + (size_t)K * KHP * 8 + (size_t)K * 8 +
+                  (size_t)(KHP + 2 * K) * 4;
+    if (smem > 227 * 1024) {
+        set_error("bl_include: ny too large for the y stage");
+        return LDDMM_EINVAL;
+    }
+    static bool attr_set = false;
+    if (!attr_set) {
+        LDDMM_CUDA(cudaFuncSetAttribute(k_iota_zy<KHP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        227 * 1024));
+        attr_set = true;
+    }
+    const int nslabs = nout * g.nz;
+    {
+        KTRACE("iota_zy", st, (double)(deriv_axis == 3 ? 3 : nout) * K * K * KH * 8.0 * g.nz / 8.0 +
+                                  (double)nslabs * g.ny * KH * 8.0,
+               (double)nslabs * (K * KH * K + g.ny * KH * K) * 8.0);
+        k_iota_zy<KHP><<<nslabs, 256, smem, st>>>(c, g.nz, g.ny, g.nx, K, KH, deriv_axis, bspline,
+                                                   tw.cx, tw.cy, tw.cz, tw.sz, tw.cy, tw.sy, T2);
+    }
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
 }
 
 // ---------------------------------------------------------------------- iota, stage X
@@ -535,39 +628,9 @@ int bl_include(const Grid& g, const Twiddles& tw, const float2* c, int ncomp, fl
     }
     const int K = tw.K, KH = K / 2;
     const int nout = deriv_axis == 3 ? 1 : ncomp;
-    const float2* src = c;
-    if (bspline) {
-        // s1 holds the divided cube first (ncomp*K^3 <= scratch size), then stage Y output
-        long n = (long)ncomp * K * K * K;
-        KTRACE("cube_bspline_div", st, 16.0 * n, 0);
-        k_cube_bspline_div<<<cdiv(n, 256), 256, 0, st>>>(c, ncomp, K, g.nx, g.ny, g.nz, s1);
-        LDDMM_CHECK_LAUNCH();
-        src = s1;
-    }
-    long total = (long)nout * g.nz * K * KH;
-    KTRACE("iota_z", st, (double)(deriv_axis == 3 ? 3 : nout) * K * K * K * 8.0 + total * 8.0,
-           (double)total * K * 8.0);
-    k_iota_z<<<cdiv(total, 256), 256, 0, st>>>(src, nout, g.nz, K, KH, deriv_axis, tw.cz,
-                                               tw.sz, s2);
-    LDDMM_CHECK_LAUNCH();
-    int nslabs = nout * g.nz;
-    size_t smem = (size_t)K * g.ny * 8 + (size_t)K * KH * 8;
-    if (smem > 227 * 1024) {
-        set_error("bl_include: ny too large for the y stage");
-        return LDDMM_EINVAL;
-    }
-    static bool attr_set = false;
-    if (!attr_set) {
-        LDDMM_CUDA(cudaFuncSetAttribute(k_iota_y, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        227 * 1024));
-        attr_set = true;
-    }
-    {
-        KTRACE("iota_y", st, (double)nslabs * (K + g.ny) * KH * 8.0, (double)nslabs * g.ny * KH * K * 8.0);
-        k_iota_y<<<std::min(nslabs, 2 * 148), 256, smem, st>>>(s2, nslabs, g.ny, K, KH, tw.cy, tw.sy,
-                                                              s1);
-    }
-    LDDMM_CHECK_LAUNCH();
+    (void)s2;
+    int rc2 = KHP_DISPATCH(KH, launch_iota_zy, g, tw, c, nout, deriv_axis, bspline ? 1 : 0, s1, st);
+    if (rc2) return rc2;
     return KHP_DISPATCH(KH, launch_iota_x, g, tw, s1, nout, f, fstride, st);
 }
 
