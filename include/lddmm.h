@@ -139,6 +139,26 @@ int lddmm_get_warped(lddmm_ctx* ctx, float* m1);
 int lddmm_bl_project(int nx, int ny, int nz, int K, const float* f, int ncomp, float* c,
                      int precision, void* stream);
 
+/* lddmm_bl_project without any allocation. The paper has no counterpart: this exists for
+ * callers that cannot let a library allocate device memory -- a host framework that owns
+ * all device memory through its own pool, a service held to a memory budget reserved up
+ * front, or a latency-critical loop that cannot afford the allocator. It computes what
+ * lddmm_bl_project computes, with the same kernels, but its scratch is one fixed 24 MiB
+ * device array inside the library (held by every GPU that loads the library until the
+ * process exits) instead of the stream-ordered pool. It calls no cudaMalloc, cudaFree or
+ * other allocating routine.
+ * Limit: the scratch needed, about ncomp * nz * max(ny, K) * K * 4 bytes plus the twiddle
+ * tables, must fit in 24 MiB (3 components of 192 x 224 x 192 at K = 32 take about 19 MiB);
+ * larger problems return EINVAL and should use lddmm_bl_project.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
+ * with that device current) and caches it; make that first call before any stream
+ * capture. All calls on a device share the one array, which keeps the last call's
+ * contents: calls that overlap on the GPU (different streams, or different host threads)
+ * race on it and must be serialised by the caller. Arguments and errors as
+ * lddmm_bl_project. */
+int lddmm_bl_project_noalloc(int nx, int ny, int nz, int K, const float* f, int ncomp, float* c,
+                             int precision, void* stream);
+
 /* iota: cubes c (float[ncomp][K][K][K][2], Hermitian) -> real fields f.
  * deriv_axis = -1: iota(c); 0/1/2: iota(i k_axis c), the spectral derivative along x/y/z.
  * bspline = 1: iota(c / B^(k)) with B^(k) = prod_a (2 + cos(2 pi k_a / n_a)) / 3, i.e. the

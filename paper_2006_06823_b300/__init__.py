@@ -76,6 +76,7 @@ def _declare(lib):
         "lddmm_register": (_I, [_P, _P, _P, ctypes.POINTER(Report)]),
         "lddmm_get_warped": (_I, [_P, _P]),
         "lddmm_bl_project": (_I, [_I, _I, _I, _I, _P, _I, _P, _I, _P]),
+        "lddmm_bl_project_noalloc": (_I, [_I, _I, _I, _I, _P, _I, _P, _I, _P]),
         "lddmm_bl_include": (_I, [_I, _I, _I, _I, _P, _I, _P, _I, _I, _I, _P]),
         "lddmm_sl_characteristics": (_I, [_I, _I, _I, _P, _D, _I, _I, _P, _P]),
         "lddmm_sl_transport": (_I, [_I, _I, _I, _I, _I, _P, _P, _I, _I, _P, _P]),
@@ -154,6 +155,18 @@ def bl_project(f, K, precision=PREC_FP32, out=None):
     if out is None:
         out = torch.empty((C, K, K, K), dtype=torch.complex64, device=f.device)
     _check(load().lddmm_bl_project(nx, ny, nz, K, _f32(f), C, _c64(out), precision, _stream()))
+    return out
+
+
+def bl_project_noalloc(f, K, out, precision=PREC_FP32):
+    """pi without allocations inside the library (lddmm_bl_project_noalloc): for callers
+    that cannot let the library allocate device memory. ``out`` must be given; the
+    library's fixed 24 MiB scratch bounds the problem size, and concurrent calls race."""
+    if f.dim() == 3:
+        f = f.unsqueeze(0)
+    C, nz, ny, nx = f.shape
+    _check(load().lddmm_bl_project_noalloc(nx, ny, nz, K, _f32(f), C, _c64(out), precision,
+                                           _stream()))
     return out
 
 
