@@ -46,7 +46,12 @@ typedef enum {
 
 enum { LDDMM_V_IMAGE = 1, LDDMM_V_DEFSTATE = 3 };          /* Sec. 2.3.1, Sec. 2.3.3 */
 enum { LDDMM_INTERP_LINEAR = 1, LDDMM_INTERP_CUBIC = 3 };  /* Sec. 3.1, Sec. 4.2 */
-enum { LDDMM_PREC_FP32 = 0, LDDMM_PREC_BF16X3 = 1 };       /* spectral path precision */
+/* Spectral path precision. FP32: FP32-accurate results; the x stages of pi and iota run on
+ * the tensor cores as split TF32 products (hi + lo, three products, FP32 accumulation) where
+ * the shape allows (K a multiple of 16, nx a multiple of 4, nx <= 256 for iota), else as
+ * FP32 SIMT. BF16X3: split BF16 products (lower precision, stated error). FP32_SIMT: never
+ * the tensor cores (the plain FP32 reference form). */
+enum { LDDMM_PREC_FP32 = 0, LDDMM_PREC_BF16X3 = 1, LDDMM_PREC_FP32_SIMT = 2 };
 enum { LDDMM_FORWARD = 1, LDDMM_BACKWARD = -1 };           /* SL time direction */
 enum { LDDMM_STOP_GTOL = 1, LDDMM_STOP_MAXIT = 2, LDDMM_STOP_LINESEARCH = 3 };
 
@@ -198,6 +203,10 @@ int lddmm_trace_read(char* buf, int len);
 
 /* Message of the calling thread's most recent failure ("" if none). Never NULL. */
 const char* lddmm_last_error(void);
+
+/* Reads and clears the device error word set by the library's kernels when a bounded
+ * device-side wait gives up (*code = LDDMM_ETIMEOUT; 0 if none). Synchronises the device. */
+int lddmm_device_error(int* code);
 
 /* Library version string, e.g. "lddmm-b300 0.1 sm_103a". */
 const char* lddmm_version(void);

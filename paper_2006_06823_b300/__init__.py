@@ -28,7 +28,7 @@ HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "lddmm.h")
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ELINESEARCH = 0, -1, -2, -3, -4, -5, -6
 V_IMAGE, V_DEFSTATE = 1, 3
 INTERP_LINEAR, INTERP_CUBIC = 1, 3
-PREC_FP32, PREC_BF16X3 = 0, 1
+PREC_FP32, PREC_BF16X3, PREC_FP32_SIMT = 0, 1, 2
 FORWARD, BACKWARD = 1, -1
 STOP_GTOL, STOP_MAXIT, STOP_LINESEARCH = 1, 2, 3
 
@@ -84,6 +84,7 @@ def _declare(lib):
         "lddmm_trace_enable": (_I, [_I]),
         "lddmm_trace_reset": (_I, []),
         "lddmm_trace_read": (_I, [ctypes.c_char_p, _I]),
+        "lddmm_device_error": (_I, [ctypes.POINTER(_I)]),
         "lddmm_last_error": (ctypes.c_char_p, []),
         "lddmm_version": (ctypes.c_char_p, []),
     }
@@ -319,4 +320,11 @@ def trace_read():
     buf = ctypes.create_string_buffer(size + 64)
     _check(lib.lddmm_trace_read(buf, size + 64))
     return json.loads(buf.value.decode())
+
+
+def device_error():
+    """Reads and clears the library's device error word (0 if no bounded wait gave up)."""
+    code = ctypes.c_int(0)
+    _check(load().lddmm_device_error(ctypes.byref(code)))
+    return code.value
 

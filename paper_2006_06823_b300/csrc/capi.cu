@@ -129,8 +129,9 @@ static int validate(const lddmm_params* p) {
         set_error("need max_gn >= 0, max_pcg >= 1, gtol >= 0");
         return LDDMM_EINVAL;
     }
-    if (p->precision != LDDMM_PREC_FP32 && p->precision != LDDMM_PREC_BF16X3) {
-        set_error("precision must be LDDMM_PREC_FP32 or LDDMM_PREC_BF16X3");
+    if (p->precision != LDDMM_PREC_FP32 && p->precision != LDDMM_PREC_BF16X3 &&
+        p->precision != LDDMM_PREC_FP32_SIMT) {
+        set_error("precision must be LDDMM_PREC_FP32, LDDMM_PREC_BF16X3 or LDDMM_PREC_FP32_SIMT");
         return LDDMM_EINVAL;
     }
     return LDDMM_OK;
@@ -692,6 +693,12 @@ extern "C" {
 const char* lddmm_last_error(void) { return g_last_error.c_str(); }
 
 const char* lddmm_version(void) { return "lddmm-b300 0.1 sm_103a"; }
+
+int lddmm_device_error(int* code) {
+    if (!code) { set_error("code is NULL"); return LDDMM_EINVAL; }
+    LDDMM_CUDA(cudaDeviceSynchronize());
+    return tc_take_error(code);
+}
 
 int lddmm_create(const lddmm_params* params, void* stream, lddmm_ctx** out) {
     if (!out) { set_error("out is NULL"); return LDDMM_EINVAL; }

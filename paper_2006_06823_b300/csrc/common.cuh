@@ -50,6 +50,11 @@ struct Grid {
 struct Twiddles {
     int K;
     const float *cx, *sx, *cy, *sy, *cz, *sz;
+    // x-stage matrices for the tensor-core path: W_pi[n][jx] (n = 2kx + re/im, K x nx) and
+    // W_io[x][j] (nx x K, weights 1 for kx = 0 and 2 otherwise)
+    const float *wpi, *wio;
+    // the same two matrices as tensor-core operand images (hi | lo, swizzled), 16-B aligned
+    const unsigned char *wpi_img, *wio_img;
 };
 long twiddle_floats(const Grid& g, int K);
 // Fills `mem` (twiddle_floats floats, device) and points `tw` into it.
@@ -58,6 +63,15 @@ int twiddle_init(const Grid& g, int K, float* mem, Twiddles& tw, cudaStream_t st
 // float2 elements of each of the two scratch buffers that bl_project / bl_include need
 // for `ncomp` components.
 long spectral_scratch_elems(const Grid& g, int K, int ncomp);
+
+// Tensor-core row GEMM OUT[row][n] = sum_k IN[row][k] W[n][k] (tc_rowgemm.cu).
+bool tc_rowgemm_supported(int N, int kdim, long rows, const void* in, long in_row_floats);
+int tc_rowgemm(const float* in, long rows, int kdim, long in_row_floats, const unsigned char* W,
+               int N, float* out, long rpc, long comp_stride, int n_out, const char* trace_name,
+               double trace_bytes, cudaStream_t st);
+long tc_wimage_bytes(int N, int kdim);
+int tc_build_wimage(const float* W, int N, int kdim, unsigned char* img, cudaStream_t st);
+int tc_take_error(int* code);
 
 // pi: ncomp fields (component stride fstride floats) -> ncomp cubes (stride K^3 float2).
 int bl_project(const Grid& g, const Twiddles& tw, const float* f, long fstride, int ncomp,

@@ -21,7 +21,35 @@ namespace lddmm {
 
 static inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
 
-long twiddle_floats(const Grid& g, int K) { return 2L * K * ((long)g.nx + g.ny + g.nz); }
+long twiddle_floats(const Grid& g, int K) {
+    // tables, W_pi and W_io, then the two tensor-core operand images (64-float aligned)
+    long f = 2L * K * ((long)g.nx + g.ny + g.nz) + 2L * K * g.nx;
+    f = (f + 63) & ~63L;
+    f += (tc_wimage_bytes(K, g.nx) + 255) / 4 + (tc_wimage_bytes(g.nx, K) + 255) / 4;
+    return f + 64;
+}
+
+// x-stage matrices of the tensor-core path from the x twiddle table (slot h + kx = wavenumber kx)
+__global__ void k_build_w(const float* cxT, const float* sxT, int K, int nx, float* wpi, float* wio) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= K * nx) return;
+    const int h = K / 2;
+    // W_pi[n][jx]
+    {
+        int n = i / nx, jx = i - n * nx;
+        int kx = n >> 1;
+        long o = (long)(h + kx) * nx + jx;
+        wpi[i] = (kx < h) ? ((n & 1) ? -sxT[o] : cxT[o]) : 0.f;
+    }
+    // W_io[x][j]
+    {
+        int x = i / K, j = i - x * K;
+        int kx = j >> 1;
+        long o = (long)(h + kx) * nx + x;
+        float w = kx == 0 ? 1.f : 2.f;
+        wio[i] = (kx < h) ? ((j & 1) ? -w * sxT[o] : w * cxT[o]) : 0.f;
+    }
+}
 
 __global__ void k_twiddle(float* cosT, float* sinT, int K, int n) {
     int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -54,6 +82,25 @@ int twiddle_init(const Grid& g, int K, float* mem, Twiddles& tw, cudaStream_t st
     tw.cx = ptrs[0]; tw.sx = ptrs[1];
     tw.cy = ptrs[2]; tw.sy = ptrs[3];
     tw.cz = ptrs[4]; tw.sz = ptrs[5];
+    float* wpi = p;
+    float* wio = p + (long)K * g.nx;
+    {
+        KTRACE("twiddle", st, 16.0 * K * g.nx, 0);
+        k_build_w<<<cdiv((long)K * g.nx, 256), 256, 0, st>>>(ptrs[0], ptrs[1], K, g.nx, wpi, wio);
+    }
+    LDDMM_CHECK_LAUNCH();
+    tw.wpi = wpi;
+    tw.wio = wio;
+    long off = (p - mem) + 2L * K * g.nx;
+    off = (off + 63) & ~63L;
+    unsigned char* img_pi = reinterpret_cast<unsigned char*>(mem + off);
+    unsigned char* img_io = img_pi + ((tc_wimage_bytes(K, g.nx) + 255) & ~255L);
+    int rc = tc_build_wimage(wpi, K, g.nx, img_pi, st);
+    if (rc) return rc;
+    rc = tc_build_wimage(wio, g.nx, K, img_io, st);
+    if (rc) return rc;
+    tw.wpi_img = img_pi;
+    tw.wio_img = img_io;
     return LDDMM_OK;
 }
 
@@ -361,11 +408,18 @@ static int check_spectral_shape(const Grid& g, int K) {
 
 int bl_project(const Grid& g, const Twiddles& tw, const float* f, long fstride, int ncomp,
                float2* c, float2* s1, float2* s2, int precision, cudaStream_t st) {
-    (void)precision;
     int rc = check_spectral_shape(g, tw.K);
     if (rc) return rc;
     const int K = tw.K, KH = K / 2;
-    rc = KHP_DISPATCH(KH, launch_pi_x, g, tw, f, fstride, ncomp, s1, st);
+    const long rows = (long)ncomp * g.nz * g.ny;
+    if (precision != LDDMM_PREC_FP32_SIMT && fstride == (long)g.nz * g.ny * g.nx &&
+        tc_rowgemm_supported(K, g.nx, rows, f, g.nx)) {
+        // stage X on the tensor cores: A[row][0..K) = (Re, Im) pairs of kx = 0..K/2-1
+        rc = tc_rowgemm(f, rows, g.nx, g.nx, tw.wpi_img, K, reinterpret_cast<float*>(s1), rows, 0, K,
+                        "pi_x_tc", rows * g.nx * 4.0 + rows * K * 4.0, st);
+    } else {
+        rc = KHP_DISPATCH(KH, launch_pi_x, g, tw, f, fstride, ncomp, s1, st);
+    }
     if (rc) return rc;
     rc = KHP_DISPATCH(KH, launch_pi_y, g, tw, ncomp, s1, s2, st);
     if (rc) return rc;
@@ -404,8 +458,7 @@ k_iota_zy(const float2* __restrict__ c, int nz, int ny, int nx, int K, int KH, i
           const float* __restrict__ cyTab, const float* __restrict__ syTab,
           float2* __restrict__ T2) {
     extern __shared__ float4 smem4[];
-    float2* twy = reinterpret_cast<float2*>(smem4);        // K * ny   [jy][y]
-    float2* t1 = twy + (long)K * ny;                        // K * KHP  [jy][kx]
+    float2* t1 = reinterpret_cast<float2*>(smem4);          // K * KHP  [jy][kx]
     float2* twz = t1 + (long)K * KHP;                       // K        e^{i kz z}
     float* bx = reinterpret_cast<float*>(twz + K);          // KHP      1/B^_x(kx)
     float* by = bx + KHP;                                   // K        1/B^_y(ky)
@@ -413,7 +466,6 @@ k_iota_zy(const float2* __restrict__ c, int nz, int ny, int nx, int K, int KH, i
     const int comp = blockIdx.x / nz, z = blockIdx.x - comp * nz;
     const int h = K / 2;
     const int tid = threadIdx.x, nt = blockDim.x;
-    for (int e = tid; e < K * ny; e += nt) twy[e] = make_float2(cyTab[e], syTab[e]);
     for (int e = tid; e < K; e += nt) {
         twz[e] = make_float2(czT[(long)e * nz + z], szT[(long)e * nz + z]);
         by[e] = bspline ? 3.f / (2.f + cyT[(long)e * ny + 1]) : 1.f;
@@ -469,9 +521,10 @@ k_iota_zy(const float2* __restrict__ c, int nz, int ny, int nx, int K, int KH, i
 #pragma unroll 4
         for (int jy = 1; jy < K; ++jy) {
             const float2 v = t1[jy * KHP + kx];
-            const float2 t = twy[jy * ny + y];
-            re = fmaf(v.x, t.x, fmaf(-v.y, t.y, re));
-            im = fmaf(v.x, t.y, fmaf(v.y, t.x, im));
+            // y twiddles straight from the (L1-resident) table
+            const float tc = __ldg(cyTab + (long)jy * ny + y), ts = __ldg(syTab + (long)jy * ny + y);
+            re = fmaf(v.x, tc, fmaf(-v.y, ts, re));
+            im = fmaf(v.x, ts, fmaf(v.y, tc, im));
         }
         out[y * KH + kx] = make_float2(re, im);
     }
@@ -481,8 +534,7 @@ template <int KHP>
 static int launch_iota_zy(const Grid& g, const Twiddles& tw, const float2* c, int nout,
                           int deriv_axis, int bspline, float2* T2, cudaStream_t st) {
     const int K = tw.K, KH = K / 2;
-    size_t smem = (size_t)K * g.ny * 8 + (size_t)K * KHP * 8 + (size_t)K * 8 +
-                  (size_t)(KHP + 2 * K) * 4;
+    size_t smem = (size_t)K * KHP * 8 + (size_t)K * 8 + (size_t)(KHP + 2 * K) * 4;
     if (smem > 227 * 1024) {
         set_error("bl_include: ny too large for the y stage");
         return LDDMM_EINVAL;
@@ -619,7 +671,6 @@ static int launch_iota_x(const Grid& g, const Twiddles& tw, const float2* T, int
 int bl_include(const Grid& g, const Twiddles& tw, const float2* c, int ncomp, float* f,
                long fstride, int deriv_axis, int bspline, float2* s1, float2* s2,
                int precision, cudaStream_t st) {
-    (void)precision;
     int rc = check_spectral_shape(g, tw.K);
     if (rc) return rc;
     if (deriv_axis < -1 || deriv_axis > 3 || (deriv_axis == 3 && ncomp != 3)) {
@@ -631,6 +682,13 @@ int bl_include(const Grid& g, const Twiddles& tw, const float2* c, int ncomp, fl
     (void)s2;
     int rc2 = KHP_DISPATCH(KH, launch_iota_zy, g, tw, c, nout, deriv_axis, bspline ? 1 : 0, s1, st);
     if (rc2) return rc2;
+    const long rows = (long)nout * g.nz * g.ny;
+    if (precision != LDDMM_PREC_FP32_SIMT && tc_rowgemm_supported(g.nx, K, rows, s1, K)) {
+        // stage X on the tensor cores: f[row][x] = sum_j T[row][j] W_io[x][j]
+        return tc_rowgemm(reinterpret_cast<const float*>(s1), rows, K, K, tw.wio_img, g.nx, f,
+                          (long)g.nz * g.ny, fstride, g.nx, "iota_x_tc",
+                          rows * K * 4.0 + rows * g.nx * 4.0, st);
+    }
     return KHP_DISPATCH(KH, launch_iota_x, g, tw, s1, nout, f, fstride, st);
 }
 

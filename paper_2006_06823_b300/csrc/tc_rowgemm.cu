@@ -1,0 +1,547 @@
+// Tensor-core (tcgen05) row GEMM for the x stages of pi and iota (Sec. 2.2):
+//
+//     OUT[row][n] = sum_k IN[row][k] * W[n][k],   rows = ncomp * nz * ny
+//
+// pi stage X:   IN = field rows (k = jx < nx),     W[2kx + {0,1}][jx] = {cos, -sin}(kx jx 2pi/nx)
+// iota stage X: IN = (Re, Im) coefficient rows,    W[x][2kx + {0,1}] = w_kx {cos, -sin}(kx x 2pi/nx)
+//
+// Both are dense contractions with a small fixed W, so they run on the 5th-generation tensor
+// cores: a persistent CTA per SM keeps W (split into hi + lo operands) resident in shared
+// memory, TMA streams 128-row x 32-column FP32 tiles of IN into a 4-stage ring (128-byte
+// swizzle, the K-major layout the MMA reads), four warps split each tile into hi and lo
+// parts in place, one thread issues tcgen05.mma into a TMEM accumulator, and the warps read
+// the accumulator back with tcgen05.ld for the epilogue store.
+//
+// Precision: FP32 inputs are represented as hi + lo with hi = x rounded to TF32 (low 13
+// mantissa bits cleared) and lo = x - hi (exact in FP32); A*B ~ Ah*Bh + Ah*Bl + Al*Bh, FP32
+// accumulation. The dropped Al*Bl term and the TF32 rounding of lo are ~2^-21 relative, so
+// the result matches FP32 arithmetic to within its rounding. (BF16 hi + lo with kind::f16
+// is the lower-precision variant of the same scheme.)
+//
+// Every mbarrier wait is bounded; on timeout the kernel records an error code in a device
+// word (read by lddmm_device_error), stops issuing work, waits (bounded) for its own copies
+// and MMAs, frees its TMEM and returns.
+#include "common.cuh"
+#include "lddmm.h"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <algorithm>
+#include <mutex>
+
+namespace lddmm {
+
+__device__ int g_tc_error = 0;
+
+namespace {
+
+constexpr int TM = 128;            // rows per tile (MMA M)
+constexpr int CHUNK = 32;          // FP32 columns per TMA box = 128 bytes = one swizzle row
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;  // 2 s per wait
+
+__device__ __forceinline__ unsigned smem_u32(const void* p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ unsigned long long now_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+
+// Parity wait bounded by wall-clock time; returns false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+    const unsigned a = smem_u32(bar);
+    const unsigned long long t0 = now_ns();
+    for (unsigned it = 0;; ++it) {
+        unsigned ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+            " selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((it & 255u) == 255u && now_ns() - t0 > kWaitLimitNs) return false;
+    }
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3}], [%4];\n" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// K-major operand, 128-byte swizzle: rows of 128 B, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(unsigned saddr) {
+    uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+    d |= (uint64_t)(16 >> 4) << 16;     // leading byte offset (unused for swizzled K-major)
+    d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;             // descriptor version for sm_100 family
+    d |= (uint64_t)2 << 61;             // SWIZZLE_128B
+    return d;
+}
+
+// kind::tf32, FP32 accumulate, both operands K-major, M = 128, N = n.
+__host__ __device__ constexpr uint32_t idesc_tf32(int n) {
+    return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_tf32(unsigned tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         unsigned accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+    asm volatile(
+        "tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];\n" ::"r"(
+            smem_u32(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void fence_before() {
+    asm volatile("tcgen05.fence::before_thread_sync;\n" ::: "memory");
+}
+__device__ __forceinline__ void fence_after() {
+    asm volatile("tcgen05.fence::after_thread_sync;\n" ::: "memory");
+}
+
+// 32 consecutive TMEM columns of this warp's 32 lanes.
+__device__ __forceinline__ void tmem_ld32(unsigned taddr, float (&v)[32]) {
+    unsigned r[32];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,"
+        "%14,%15,%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]),
+          "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]),
+          "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;\n" ::: "memory");
+#pragma unroll
+    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ float tf32_hi(float x) {
+    return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+}
+
+// byte offset of (row r, byte b in the 128-byte row) in a 1024-aligned SW128 tile
+__device__ __forceinline__ unsigned sw128_off(int r, int b) {
+    return (unsigned)(r * 128 + ((((b >> 4) ^ (r & 7))) << 4) + (b & 15));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, const void* src, int x, int y,
+                                             int z) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%2, %3, %4}], [%1];\n" ::"l"(
+            reinterpret_cast<uint64_t>(map)),
+        "r"(smem_u32(src)), "r"(x), "r"(y), "r"(z)
+        : "memory");
+    asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
+}
+
+__device__ __forceinline__ void workers_sync() {
+    asm volatile("bar.sync 1, 128;\n" ::: "memory");
+}
+
+constexpr int NWORK = 4;                 // split + epilogue warps
+constexpr int WARP_TMA = NWORK;          // TMA producer warp
+constexpr int WARP_MMA = NWORK + 1;      // MMA issuer (and TMEM owner)
+constexpr int NTHREADS_WS = 32 * (NWORK + 2);
+constexpr int NRAW = 4;                  // TMA landing ring (released after the split)
+constexpr int NOP = 2;                   // hi/lo operand ring (released by MMA completion)
+constexpr int TILE_B = TM * 128;         // 16 KB
+
+}  // namespace
+
+// Warp-specialised pipeline. Chunk q: tile t = q / nchunk, column block c = q % nchunk.
+//   producer : wait raw_empty[q%NRAW], TMA 128 x 32 tile -> raw[q%NRAW]
+//   workers  : wait raw_full, wait op_empty[q%NOP]; hi/lo split raw -> op; arrive raw_empty and
+//              op_full; after the first chunk of tile t, epilogue of tile t-1
+//   MMA warp : wait op_full (and, for c == 0, accempty of TMEM buffer t&1); 3 x 4 MMAs;
+//              commit -> op_empty; last chunk of the tile: commit -> accfull[t&1]
+//   epilogue : TMEM 32-column blocks -> swizzled staging (2 buffers) -> TMA store
+// OUT is the 3-D tensor [ncomp][rpc][n_out] behind tmap_out (rows r = comp * rpc + local).
+__global__ void __launch_bounds__(NTHREADS_WS, 1)
+k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant__ CUtensorMap tmap_out,
+             const unsigned char* __restrict__ w_image, int N, int kdim, long rows,
+             float* __restrict__ out, long rpc, long comp_stride, int n_out, unsigned tmem_cols) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ uint64_t raw_full[NRAW], raw_empty[NRAW], op_full[NOP], op_empty[NOP], w_bar;
+    __shared__ uint64_t accfull_bar[2], accempty_bar[2];
+    __shared__ unsigned tmem_holder;
+    __shared__ volatile int abort_flag;
+    __shared__ long consumed_sh, issued_sh;
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nchunk = (kdim + CHUNK - 1) / CHUNK;
+    unsigned char* base = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const size_t wbytes = (size_t)nchunk * N * 128;
+    unsigned char* w_hi = base;
+    unsigned char* w_lo = base + wbytes;
+    unsigned char* raw = base + 2 * wbytes;          // NRAW x 16 KB
+    unsigned char* op_hi = raw + NRAW * TILE_B;      // NOP x 16 KB
+    unsigned char* op_lo = op_hi + NOP * TILE_B;     // NOP x 16 KB
+    unsigned char* stg = op_lo + NOP * TILE_B;       // 2 x 16 KB epilogue staging
+
+    if (tid == 0) {
+        mbar_init(&w_bar, 1);
+        for (int i = 0; i < NRAW; ++i) {
+            mbar_init(&raw_full[i], 1);
+            mbar_init(&raw_empty[i], NWORK);
+        }
+        for (int i = 0; i < NOP; ++i) {
+            mbar_init(&op_full[i], NWORK);
+            mbar_init(&op_empty[i], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accfull_bar[b], 1);
+            mbar_init(&accempty_bar[b], NWORK);
+        }
+        abort_flag = 0;
+        consumed_sh = 0;
+        issued_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        // W (hi | lo, already in the swizzled operand layout) arrives by bulk copies; only
+        // the MMA warp waits for it
+        const unsigned wtot = (unsigned)(2 * wbytes);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(&w_bar)),
+                     "r"(wtot)
+                     : "memory");
+        for (unsigned o = 0; o < wtot; o += 16384) {
+            const unsigned len = min(16384u, wtot - o);
+            asm volatile(
+                "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+                    smem_u32(w_hi + o)),
+                "l"(w_image + o), "r"(len), "r"(smem_u32(&w_bar))
+                : "memory");
+        }
+    }
+    if (warp == WARP_MMA) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         smem_u32(&tmem_holder)),
+                     "r"(tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const unsigned tmem = tmem_holder;
+
+    const long ntiles = (rows + TM - 1) / TM;
+    const long my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const long total = my_tiles * nchunk;
+    const uint32_t idesc = idesc_tf32(N);
+
+    if (warp == WARP_TMA) {
+        if (lane == 0) {
+            for (long q = 0; q < total; ++q) {
+                const int s = (int)(q % NRAW);
+                const long u = q / NRAW;
+                if (u > 0 && !mbar_wait(&raw_empty[s], (unsigned)((u - 1) & 1))) {
+                    abort_flag = 1;
+                    break;
+                }
+                if (abort_flag) break;
+                const long t = blockIdx.x + (q / nchunk) * gridDim.x;
+                tma_load_2d(raw + (size_t)s * TILE_B, &tmap_in, (int)(q % nchunk) * CHUNK,
+                            (int)(t * TM), &raw_full[s], TILE_B);
+                issued_sh = q + 1;
+            }
+        }
+    } else if (warp == WARP_MMA) {
+        if (lane == 0) {
+            if (total > 0 && !mbar_wait(&w_bar, 0)) abort_flag = 1;
+            for (long q = 0; q < total && !abort_flag; ++q) {
+                const int o = (int)(q % NOP);
+                const int c = (int)(q % nchunk);
+                const long t = q / nchunk;
+                const int b = (int)(t & 1);
+                if (c == 0 && t >= 2 && !mbar_wait(&accempty_bar[b], (unsigned)(((t >> 1) - 1) & 1))) {
+                    abort_flag = 1;
+                    break;
+                }
+                if (!mbar_wait(&op_full[o], (unsigned)((q / NOP) & 1))) {
+                    abort_flag = 1;
+                    break;
+                }
+                if (abort_flag) break;
+                fence_after();
+                const unsigned d = tmem + (unsigned)(b * N);
+                const unsigned ah = smem_u32(op_hi + (size_t)o * TILE_B);
+                const unsigned al = smem_u32(op_lo + (size_t)o * TILE_B);
+                const unsigned wh = smem_u32(w_hi + (size_t)c * N * 128);
+                const unsigned wl = smem_u32(w_lo + (size_t)c * N * 128);
+#pragma unroll
+                for (int kk = 0; kk < CHUNK / 8; ++kk) {
+                    const unsigned ko = kk * 32;
+                    const unsigned acc = (c > 0 || kk > 0) ? 1u : 0u;
+                    mma_tf32(d, sw128_desc(ah + ko), sw128_desc(wh + ko), idesc, acc);
+                    mma_tf32(d, sw128_desc(ah + ko), sw128_desc(wl + ko), idesc, 1u);
+                    mma_tf32(d, sw128_desc(al + ko), sw128_desc(wh + ko), idesc, 1u);
+                }
+                mma_commit(&op_empty[o]);
+                if (c == nchunk - 1) mma_commit(&accfull_bar[b]);
+            }
+        }
+    } else {
+        // ---------------------------------------------------------------- workers
+        const int wt = tid;  // 0 .. 127: the tile row this thread stores in the epilogue
+        long sblock = 0;     // staging blocks used so far (buffer = sblock & 1)
+        auto epilogue = [&](long t) -> bool {
+            const int b = (int)(t & 1);
+            if (!mbar_wait(&accfull_bar[b], (unsigned)((t >> 1) & 1))) return false;
+            fence_after();
+            const long tg = blockIdx.x + t * gridDim.x;
+            const long row0 = tg * TM;
+            const long comp0 = row0 / rpc;
+            const long local0 = row0 - comp0 * rpc;
+            const long split = rpc - local0;  // tile rows at or past `split` belong to comp0 + 1
+            const long row = row0 + wt;
+            for (int c0 = 0; c0 < N; c0 += 32) {
+                float v[32];
+                tmem_ld32(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(b * N + c0), v);
+                unsigned char* sb = stg + (size_t)(sblock & 1) * TILE_B;
+                // the store issued two blocks ago from this buffer must have read it
+                if (wt == 0) asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
+                workers_sync();
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    *reinterpret_cast<float4*>(sb + sw128_off(wt, j * 16)) =
+                        make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                workers_sync();
+                if (wt == 0)
+                    tma_store_3d(&tmap_out, sb, c0, (int)local0, (int)comp0);
+                // rows of a second component (only when a tile straddles a component boundary)
+                if (wt >= split && row < rows) {
+                    float* dst = out + (comp0 + 1) * comp_stride + (wt - split) * n_out + c0;
+                    const int nv = min(32, n_out - c0);
+                    for (int i = 0; i < nv; ++i) dst[i] = v[i];
+                }
+                ++sblock;
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&accempty_bar[b]);
+            return true;
+        };
+        bool ok = true;
+        for (long q = 0; q < total && ok; ++q) {
+            const int s = (int)(q % NRAW);
+            const int o = (int)(q % NOP);
+            if (!mbar_wait(&raw_full[s], (unsigned)((q / NRAW) & 1)) ||
+                (q >= NOP && !mbar_wait(&op_empty[o], (unsigned)(((q / NOP) - 1) & 1))) ||
+                abort_flag) {
+                abort_flag = 1;
+                ok = false;
+                break;
+            }
+            const float4* src = reinterpret_cast<const float4*>(raw + (size_t)s * TILE_B);
+            float4* hi = reinterpret_cast<float4*>(op_hi + (size_t)o * TILE_B);
+            float4* lo = reinterpret_cast<float4*>(op_lo + (size_t)o * TILE_B);
+#pragma unroll
+            for (int i = 0; i < TILE_B / 16 / (32 * NWORK); ++i) {
+                const int e = wt + i * 32 * NWORK;
+                const float4 v = src[e];
+                const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
+                hi[e] = h;
+                lo[e] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+            }
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&raw_empty[s]);
+                mbar_arrive(&op_full[o]);
+            }
+            if (wt == 0) consumed_sh = q + 1;
+            const int c = (int)(q % nchunk);
+            const long t = q / nchunk;
+            if (c == 0 && t >= 1 && !epilogue(t - 1)) {
+                abort_flag = 1;
+                ok = false;
+            }
+        }
+        if (ok && my_tiles > 0 && !abort_flag && !epilogue(my_tiles - 1)) abort_flag = 1;
+        if (wt == 0) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+    }
+
+    __syncthreads();
+    if (abort_flag && tid == 0) {
+        atomicExch(&g_tc_error, LDDMM_ETIMEOUT);
+        for (long qq = consumed_sh; qq < issued_sh; ++qq)
+            mbar_wait(&raw_full[qq % NRAW], (unsigned)((qq / NRAW) & 1));
+    }
+    if (abort_flag && warp == WARP_MMA && lane == 0) {
+        mma_commit(&accfull_bar[0]);
+        mbar_wait(&accfull_bar[0], 0);
+        mbar_wait(&accfull_bar[0], 1);
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == WARP_MMA)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                     "r"(tmem_cols));
+}
+
+// W (N x kdim FP32) -> its shared-memory operand image: hi then lo, each nchunk x N rows of
+// 128 bytes in the 128-byte-swizzled K-major layout (zero past kdim).
+__global__ void k_build_wimage(const float* __restrict__ W, int N, int kdim,
+                               unsigned char* __restrict__ img) {
+    const int nchunk = (kdim + CHUNK - 1) / CHUNK;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= nchunk * N * CHUNK) return;
+    const int c = e / (N * CHUNK);
+    const int rem = e - c * N * CHUNK;
+    const int n = rem / CHUNK, k = rem - n * CHUNK;
+    const int kk = c * CHUNK + k;
+    const float w = kk < kdim ? W[(long)n * kdim + kk] : 0.f;
+    const float h = tf32_hi(w);
+    const size_t wbytes = (size_t)nchunk * N * 128;
+    const unsigned off = (unsigned)((size_t)c * N * 128) + sw128_off(n, k * 4);
+    *reinterpret_cast<float*>(img + off) = h;
+    *reinterpret_cast<float*>(img + wbytes + off) = w - h;
+}
+
+long tc_wimage_bytes(int N, int kdim) {
+    const int nchunk = (kdim + CHUNK - 1) / CHUNK;
+    return 2L * nchunk * N * 128;
+}
+
+int tc_build_wimage(const float* W, int N, int kdim, unsigned char* img, cudaStream_t st) {
+    const int nchunk = (kdim + CHUNK - 1) / CHUNK;
+    const int total = nchunk * N * CHUNK;
+    {
+        KTRACE("twiddle", st, 12.0 * total, 0);
+        k_build_wimage<<<(total + 255) / 256, 256, 0, st>>>(W, N, kdim, img);
+    }
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+// --------------------------------------------------------------------------- host side
+namespace {
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    });
+    return fn;
+}
+
+int tc_smem_bytes(int N, int kdim) {
+    const int nchunk = (kdim + CHUNK - 1) / CHUNK;
+    return 2 * nchunk * N * 128 + (NRAW + 2 * NOP + 2) * TILE_B + 1024;
+}
+
+}  // namespace
+
+bool tc_rowgemm_supported(int N, int kdim, long rows, const void* in, long in_row_floats) {
+    if (N < 16 || N > 256 || (N % 16) != 0) return false;
+    if (kdim < 1 || (in_row_floats % 4) != 0) return false;
+    if ((reinterpret_cast<uintptr_t>(in) & 15) != 0) return false;
+    if (rows < 1 || rows > 0x7fffffffL) return false;
+    if (tc_smem_bytes(N, kdim) > 220 * 1024) return false;
+    return encode_fn() != nullptr;
+}
+
+// in: rows x in_row_floats FP32 (the first kdim columns are used), W: N x kdim FP32.
+int tc_rowgemm(const float* in, long rows, int kdim, long in_row_floats, const unsigned char* W,
+               int N, float* out, long rpc, long comp_stride, int n_out, const char* trace_name,
+               double trace_bytes, cudaStream_t st) {
+    CUtensorMap map;
+    cuuint64_t dims[2] = {(cuuint64_t)in_row_floats, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)in_row_floats * 4};
+    cuuint32_t box[2] = {CHUNK, TM};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(in), dims,
+                             strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("tc_rowgemm: cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+        return LDDMM_ECUDA;
+    }
+    // output: [ncomp][rpc][n_out] with component stride comp_stride floats
+    CUtensorMap omap;
+    const long ncomp_out = (rows + rpc - 1) / rpc;
+    cuuint64_t odims[3] = {(cuuint64_t)n_out, (cuuint64_t)rpc, (cuuint64_t)ncomp_out};
+    cuuint64_t ostr[2] = {(cuuint64_t)n_out * 4, (cuuint64_t)(ncomp_out > 1 ? comp_stride : rpc * n_out) * 4};
+    cuuint32_t obox[3] = {32, TM, 1};
+    cuuint32_t oestr[3] = {1, 1, 1};
+    r = encode_fn()(&omap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, out, odims, ostr, obox, oestr,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                    CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("tc_rowgemm: cuTensorMapEncodeTiled (output) failed (" + std::to_string((int)r) + ")");
+        return LDDMM_ECUDA;
+    }
+    const int smem = tc_smem_bytes(N, kdim);
+    static int attr_smem = 0;  // largest dynamic size requested so far
+    if (smem > attr_smem) {
+        LDDMM_CUDA(cudaFuncSetAttribute(k_tc_rowgemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        smem));
+        attr_smem = smem;
+    }
+    // two accumulators at columns 0 and N; the epilogue reads 32-column blocks, so the
+    // second buffer's last block ends at N + roundup(N, 32)
+    const int need_cols = N + ((N + 31) / 32) * 32;
+    unsigned cols = 32;
+    while ((int)cols < need_cols) cols <<= 1;
+    if (cols > 512) {
+        set_error("tc_rowgemm: N too large for tensor memory");
+        return LDDMM_EINVAL;
+    }
+    int dev = 0, nsm = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    const long ntiles = (rows + TM - 1) / TM;
+    const int grid = (int)std::min<long>(ntiles, nsm);
+    {
+        KTRACE(trace_name, st, trace_bytes, 2.0 * rows * (double)N * kdim);
+        k_tc_rowgemm<<<grid, NTHREADS_WS, smem, st>>>(map, omap, W, N, kdim, rows, out, rpc,
+                                                     comp_stride, n_out, cols);
+    }
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+// Reads and clears the device error word of the tensor-core kernels.
+int tc_take_error(int* code) {
+    int zero = 0;
+    LDDMM_CUDA(cudaMemcpyFromSymbol(code, g_tc_error, sizeof(int)));
+    LDDMM_CUDA(cudaMemcpyToSymbol(g_tc_error, &zero, sizeof(int)));
+    return LDDMM_OK;
+}
+
+}  // namespace lddmm

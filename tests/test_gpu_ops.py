@@ -126,3 +126,28 @@ def test_invalid_arguments_raise():
         L.bl_project(torch.zeros((1, 8, 8, 8), device="cuda"), 10)  # K > n
     with pytest.raises(L.LddmmError):
         L.bl_project(torch.zeros((1, 8, 8, 8), device="cuda"), 5)   # odd K
+
+
+# shapes that take the tensor-core x stages (K a multiple of 16, nx a multiple of 4; iota also
+# needs nx a multiple of 16): ragged row counts, a partial last K chunk, K = 16 and 32
+TC_CASES = [((33, 40, 64), 32), ((20, 24, 48), 16), ((40, 36, 100), 32), ((18, 20, 80), 16)]
+
+
+@pytest.mark.parametrize("shape,K", TC_CASES)
+@pytest.mark.parametrize("precision", [L.PREC_FP32, L.PREC_FP32_SIMT])
+def test_bl_project_tensor_core_and_simt_paths_match_oracle(shape, K, precision):
+    f = synth.random_field(shape, seed=51, ncomp=3)
+    c = host(L.bl_project(dev(f), K, precision=precision))
+    assert rel_l2(c, S.project(f, K)) < 3e-6
+    assert L.device_error() == 0
+
+
+@pytest.mark.parametrize("shape,K", TC_CASES)
+@pytest.mark.parametrize("precision", [L.PREC_FP32, L.PREC_FP32_SIMT])
+@pytest.mark.parametrize("deriv", [-1, 1])
+def test_bl_include_tensor_core_and_simt_paths_match_oracle(shape, K, precision, deriv):
+    c = synth.random_coeffs(K, seed=52, ncomp=3, decay_power=0.5)
+    f = host(L.bl_include(devc(c), shape, deriv_axis=deriv, precision=precision))
+    src = c if deriv < 0 else np.stack([S.deriv(ci, deriv) for ci in c])
+    assert rel_l2(f, S.include(src, shape)) < 3e-6
+    assert L.device_error() == 0
