@@ -53,8 +53,9 @@ struct Twiddles {
     // x-stage matrices for the tensor-core path: W_pi[n][jx] (n = 2kx + re/im, K x nx) and
     // W_io[x][j] (nx x K, weights 1 for kx = 0 and 2 otherwise)
     const float *wpi, *wio;
-    // the same two matrices as tensor-core operand images (hi | lo, swizzled), 16-B aligned
-    const unsigned char *wpi_img, *wio_img;
+    // the same two matrices as tensor-core operand images (hi | lo, swizzled), 16-B aligned:
+    // [0] TF32 split, [1] BF16 split
+    const unsigned char *wpi_img[2], *wio_img[2];
 };
 long twiddle_floats(const Grid& g, int K);
 // Fills `mem` (twiddle_floats floats, device) and points `tw` into it.
@@ -67,10 +68,11 @@ long spectral_scratch_elems(const Grid& g, int K, int ncomp);
 // Tensor-core row GEMM OUT[row][n] = sum_k IN[row][k] W[n][k] (tc_rowgemm.cu).
 bool tc_rowgemm_supported(int N, int kdim, long rows, const void* in, long in_row_floats);
 int tc_rowgemm(const float* in, long rows, int kdim, long in_row_floats, const unsigned char* W,
-               int N, float* out, long rpc, long comp_stride, int n_out, const char* trace_name,
-               double trace_bytes, cudaStream_t st);
+               int N, int prec, float* out, long rpc, long comp_stride, int n_out,
+               const char* trace_name, double trace_bytes, cudaStream_t st);
 long tc_wimage_bytes(int N, int kdim);
-int tc_build_wimage(const float* W, int N, int kdim, unsigned char* img, cudaStream_t st);
+int tc_build_wimage(const float* W, int N, int kdim, int prec, unsigned char* img,
+                    cudaStream_t st);
 int tc_take_error(int* code);
 
 // pi: ncomp fields (component stride fstride floats) -> ncomp cubes (stride K^3 float2).

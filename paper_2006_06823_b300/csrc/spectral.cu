@@ -25,7 +25,7 @@ long twiddle_floats(const Grid& g, int K) {
     // tables, W_pi and W_io, then the two tensor-core operand images (64-float aligned)
     long f = 2L * K * ((long)g.nx + g.ny + g.nz) + 2L * K * g.nx;
     f = (f + 63) & ~63L;
-    f += (tc_wimage_bytes(K, g.nx) + 255) / 4 + (tc_wimage_bytes(g.nx, K) + 255) / 4;
+    f += 2 * ((tc_wimage_bytes(K, g.nx) + 255) / 4 + (tc_wimage_bytes(g.nx, K) + 255) / 4);
     return f + 64;
 }
 
@@ -93,14 +93,19 @@ int twiddle_init(const Grid& g, int K, float* mem, Twiddles& tw, cudaStream_t st
     tw.wio = wio;
     long off = (p - mem) + 2L * K * g.nx;
     off = (off + 63) & ~63L;
-    unsigned char* img_pi = reinterpret_cast<unsigned char*>(mem + off);
-    unsigned char* img_io = img_pi + ((tc_wimage_bytes(K, g.nx) + 255) & ~255L);
-    int rc = tc_build_wimage(wpi, K, g.nx, img_pi, st);
-    if (rc) return rc;
-    rc = tc_build_wimage(wio, g.nx, K, img_io, st);
-    if (rc) return rc;
-    tw.wpi_img = img_pi;
-    tw.wio_img = img_io;
+    unsigned char* img = reinterpret_cast<unsigned char*>(mem + off);
+    const long bpi = (tc_wimage_bytes(K, g.nx) + 255) & ~255L;
+    const long bio = (tc_wimage_bytes(g.nx, K) + 255) & ~255L;
+    for (int prec = 0; prec < 2; ++prec) {
+        unsigned char* img_pi = img + prec * (bpi + bio);
+        unsigned char* img_io = img_pi + bpi;
+        int rc = tc_build_wimage(wpi, K, g.nx, prec, img_pi, st);
+        if (rc) return rc;
+        rc = tc_build_wimage(wio, g.nx, K, prec, img_io, st);
+        if (rc) return rc;
+        tw.wpi_img[prec] = img_pi;
+        tw.wio_img[prec] = img_io;
+    }
     return LDDMM_OK;
 }
 
@@ -415,7 +420,8 @@ int bl_project(const Grid& g, const Twiddles& tw, const float* f, long fstride, 
     if (precision != LDDMM_PREC_FP32_SIMT && fstride == (long)g.nz * g.ny * g.nx &&
         tc_rowgemm_supported(K, g.nx, rows, f, g.nx)) {
         // stage X on the tensor cores: A[row][0..K) = (Re, Im) pairs of kx = 0..K/2-1
-        rc = tc_rowgemm(f, rows, g.nx, g.nx, tw.wpi_img, K, reinterpret_cast<float*>(s1), rows, 0, K,
+        const int tp = precision == LDDMM_PREC_BF16X3 ? 1 : 0;
+        rc = tc_rowgemm(f, rows, g.nx, g.nx, tw.wpi_img[tp], K, tp, reinterpret_cast<float*>(s1), rows, 0, K,
                         "pi_x_tc", rows * g.nx * 4.0 + rows * K * 4.0, st);
     } else {
         rc = KHP_DISPATCH(KH, launch_pi_x, g, tw, f, fstride, ncomp, s1, st);
@@ -685,7 +691,8 @@ int bl_include(const Grid& g, const Twiddles& tw, const float2* c, int ncomp, fl
     const long rows = (long)nout * g.nz * g.ny;
     if (precision != LDDMM_PREC_FP32_SIMT && tc_rowgemm_supported(g.nx, K, rows, s1, K)) {
         // stage X on the tensor cores: f[row][x] = sum_j T[row][j] W_io[x][j]
-        return tc_rowgemm(reinterpret_cast<const float*>(s1), rows, K, K, tw.wio_img, g.nx, f,
+        const int tp = precision == LDDMM_PREC_BF16X3 ? 1 : 0;
+        return tc_rowgemm(reinterpret_cast<const float*>(s1), rows, K, K, tw.wio_img[tp], g.nx, tp, f,
                           (long)g.nz * g.ny, fstride, g.nx, "iota_x_tc",
                           rows * K * 4.0 + rows * g.nx * 4.0, st);
     }

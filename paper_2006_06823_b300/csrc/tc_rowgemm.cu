@@ -25,6 +25,7 @@
 #include "lddmm.h"
 
 #include <cuda.h>
+#include <cuda_bf16.h>
 #include <cudaTypedefs.h>
 
 #include <algorithm>
@@ -98,12 +99,40 @@ __host__ __device__ constexpr uint32_t idesc_tf32(int n) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
 }
 
+// kind::f16 with BF16 A and B, FP32 accumulate, K-major, M = 128, N = n.
+__host__ __device__ constexpr uint32_t idesc_bf16(int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
+}
+
 __device__ __forceinline__ void mma_tf32(unsigned tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
                                          unsigned accumulate) {
     asm volatile(
         "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
         " tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
         "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+__device__ __forceinline__ void mma_bf16(unsigned tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         unsigned accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+        "l"(a), "l"(b), "r"(idesc), "r"(accumulate));
+}
+
+// BF16 split: hi = RN(x), lo = RN(x - hi); returns the packed bits of four elements
+__device__ __forceinline__ void bf16_split4(float4 v, uint2& hi, uint2& lo) {
+    __nv_bfloat16 h[4], l[4];
+    const float x[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        h[i] = __float2bfloat16_rn(x[i]);
+        l[i] = __float2bfloat16_rn(x[i] - __bfloat162float(h[i]));
+    }
+    hi.x = (unsigned)__bfloat16_as_ushort(h[0]) | ((unsigned)__bfloat16_as_ushort(h[1]) << 16);
+    hi.y = (unsigned)__bfloat16_as_ushort(h[2]) | ((unsigned)__bfloat16_as_ushort(h[3]) << 16);
+    lo.x = (unsigned)__bfloat16_as_ushort(l[0]) | ((unsigned)__bfloat16_as_ushort(l[1]) << 16);
+    lo.y = (unsigned)__bfloat16_as_ushort(l[2]) | ((unsigned)__bfloat16_as_ushort(l[3]) << 16);
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -182,6 +211,9 @@ constexpr int TILE_B = TM * 128;         // 16 KB
 //              commit -> op_empty; last chunk of the tile: commit -> accfull[t&1]
 //   epilogue : TMEM 32-column blocks -> swizzled staging (2 buffers) -> TMA store
 // OUT is the 3-D tensor [ncomp][rpc][n_out] behind tmap_out (rows r = comp * rpc + local).
+// PREC 0: TF32 hi + lo (4 k-steps of 8 per 32-column chunk). PREC 1: BF16 hi + lo, the 32
+// elements of a chunk in the first 64 bytes of each 128-byte operand row (2 k-steps of 16).
+template <int PREC>
 __global__ void __launch_bounds__(NTHREADS_WS, 1)
 k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant__ CUtensorMap tmap_out,
              const unsigned char* __restrict__ w_image, int N, int kdim, long rows,
@@ -253,7 +285,7 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
     const long ntiles = (rows + TM - 1) / TM;
     const long my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const long total = my_tiles * nchunk;
-    const uint32_t idesc = idesc_tf32(N);
+    const uint32_t idesc = PREC == 0 ? idesc_tf32(N) : idesc_bf16(N);
 
     if (warp == WARP_TMA) {
         if (lane == 0) {
@@ -294,13 +326,24 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
                 const unsigned al = smem_u32(op_lo + (size_t)o * TILE_B);
                 const unsigned wh = smem_u32(w_hi + (size_t)c * N * 128);
                 const unsigned wl = smem_u32(w_lo + (size_t)c * N * 128);
+                if (PREC == 0) {
 #pragma unroll
-                for (int kk = 0; kk < CHUNK / 8; ++kk) {
-                    const unsigned ko = kk * 32;
-                    const unsigned acc = (c > 0 || kk > 0) ? 1u : 0u;
-                    mma_tf32(d, sw128_desc(ah + ko), sw128_desc(wh + ko), idesc, acc);
-                    mma_tf32(d, sw128_desc(ah + ko), sw128_desc(wl + ko), idesc, 1u);
-                    mma_tf32(d, sw128_desc(al + ko), sw128_desc(wh + ko), idesc, 1u);
+                    for (int kk = 0; kk < CHUNK / 8; ++kk) {
+                        const unsigned ko = kk * 32;
+                        const unsigned acc = (c > 0 || kk > 0) ? 1u : 0u;
+                        mma_tf32(d, sw128_desc(ah + ko), sw128_desc(wh + ko), idesc, acc);
+                        mma_tf32(d, sw128_desc(ah + ko), sw128_desc(wl + ko), idesc, 1u);
+                        mma_tf32(d, sw128_desc(al + ko), sw128_desc(wh + ko), idesc, 1u);
+                    }
+                } else {
+#pragma unroll
+                    for (int kk = 0; kk < CHUNK / 16; ++kk) {
+                        const unsigned ko = kk * 32;
+                        const unsigned acc = (c > 0 || kk > 0) ? 1u : 0u;
+                        mma_bf16(d, sw128_desc(ah + ko), sw128_desc(wh + ko), idesc, acc);
+                        mma_bf16(d, sw128_desc(ah + ko), sw128_desc(wl + ko), idesc, 1u);
+                        mma_bf16(d, sw128_desc(al + ko), sw128_desc(wh + ko), idesc, 1u);
+                    }
                 }
                 mma_commit(&op_empty[o]);
                 if (c == nchunk - 1) mma_commit(&accfull_bar[b]);
@@ -366,9 +409,20 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
             for (int i = 0; i < TILE_B / 16 / (32 * NWORK); ++i) {
                 const int e = wt + i * 32 * NWORK;
                 const float4 v = src[e];
-                const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
-                hi[e] = h;
-                lo[e] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+                if (PREC == 0) {
+                    const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
+                    hi[e] = h;
+                    lo[e] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
+                } else {
+                    // raw 16-byte chunk e = (row r, physical chunk p) holds logical chunk
+                    // j = p ^ (r & 7), i.e. elements 4j..4j+3 -> bf16 bytes 8j..8j+7
+                    const int r = e >> 3, pch = e & 7, j = pch ^ (r & 7);
+                    const unsigned off = sw128_off(r, 8 * j);
+                    uint2 h2, l2;
+                    bf16_split4(v, h2, l2);
+                    *reinterpret_cast<uint2*>(reinterpret_cast<unsigned char*>(hi) + off) = h2;
+                    *reinterpret_cast<uint2*>(reinterpret_cast<unsigned char*>(lo) + off) = l2;
+                }
             }
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             __syncwarp();
@@ -409,6 +463,7 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
 
 // W (N x kdim FP32) -> its shared-memory operand image: hi then lo, each nchunk x N rows of
 // 128 bytes in the 128-byte-swizzled K-major layout (zero past kdim).
+template <int PREC>
 __global__ void k_build_wimage(const float* __restrict__ W, int N, int kdim,
                                unsigned char* __restrict__ img) {
     const int nchunk = (kdim + CHUNK - 1) / CHUNK;
@@ -419,11 +474,19 @@ __global__ void k_build_wimage(const float* __restrict__ W, int N, int kdim,
     const int n = rem / CHUNK, k = rem - n * CHUNK;
     const int kk = c * CHUNK + k;
     const float w = kk < kdim ? W[(long)n * kdim + kk] : 0.f;
-    const float h = tf32_hi(w);
     const size_t wbytes = (size_t)nchunk * N * 128;
-    const unsigned off = (unsigned)((size_t)c * N * 128) + sw128_off(n, k * 4);
-    *reinterpret_cast<float*>(img + off) = h;
-    *reinterpret_cast<float*>(img + wbytes + off) = w - h;
+    if (PREC == 0) {
+        const float h = tf32_hi(w);
+        const unsigned off = (unsigned)((size_t)c * N * 128) + sw128_off(n, k * 4);
+        *reinterpret_cast<float*>(img + off) = h;
+        *reinterpret_cast<float*>(img + wbytes + off) = w - h;
+    } else {
+        const __nv_bfloat16 h = __float2bfloat16_rn(w);
+        const __nv_bfloat16 l = __float2bfloat16_rn(w - __bfloat162float(h));
+        const unsigned off = (unsigned)((size_t)c * N * 128) + sw128_off(n, k * 2);
+        *reinterpret_cast<__nv_bfloat16*>(img + off) = h;
+        *reinterpret_cast<__nv_bfloat16*>(img + wbytes + off) = l;
+    }
 }
 
 long tc_wimage_bytes(int N, int kdim) {
@@ -431,12 +494,18 @@ long tc_wimage_bytes(int N, int kdim) {
     return 2L * nchunk * N * 128;
 }
 
-int tc_build_wimage(const float* W, int N, int kdim, unsigned char* img, cudaStream_t st) {
+int tc_build_wimage(const float* W, int N, int kdim, int prec, unsigned char* img,
+                    cudaStream_t st) {
     const int nchunk = (kdim + CHUNK - 1) / CHUNK;
     const int total = nchunk * N * CHUNK;
+    // BF16 images leave the upper 64 bytes of each operand row unused: clear them
+    LDDMM_CUDA(cudaMemsetAsync(img, 0, tc_wimage_bytes(N, kdim), st));
     {
         KTRACE("twiddle", st, 12.0 * total, 0);
-        k_build_wimage<<<(total + 255) / 256, 256, 0, st>>>(W, N, kdim, img);
+        if (prec == 0)
+            k_build_wimage<0><<<(total + 255) / 256, 256, 0, st>>>(W, N, kdim, img);
+        else
+            k_build_wimage<1><<<(total + 255) / 256, 256, 0, st>>>(W, N, kdim, img);
     }
     LDDMM_CHECK_LAUNCH();
     return LDDMM_OK;
@@ -477,8 +546,8 @@ bool tc_rowgemm_supported(int N, int kdim, long rows, const void* in, long in_ro
 
 // in: rows x in_row_floats FP32 (the first kdim columns are used), W: N x kdim FP32.
 int tc_rowgemm(const float* in, long rows, int kdim, long in_row_floats, const unsigned char* W,
-               int N, float* out, long rpc, long comp_stride, int n_out, const char* trace_name,
-               double trace_bytes, cudaStream_t st) {
+               int N, int prec, float* out, long rpc, long comp_stride, int n_out,
+               const char* trace_name, double trace_bytes, cudaStream_t st) {
     CUtensorMap map;
     cuuint64_t dims[2] = {(cuuint64_t)in_row_floats, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)in_row_floats * 4};
@@ -507,11 +576,15 @@ int tc_rowgemm(const float* in, long rows, int kdim, long in_row_floats, const u
         return LDDMM_ECUDA;
     }
     const int smem = tc_smem_bytes(N, kdim);
-    static int attr_smem = 0;  // largest dynamic size requested so far
-    if (smem > attr_smem) {
-        LDDMM_CUDA(cudaFuncSetAttribute(k_tc_rowgemm, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        smem));
-        attr_smem = smem;
+    static int attr_smem[2] = {0, 0};  // largest dynamic size requested so far
+    if (smem > attr_smem[prec]) {
+        if (prec == 0)
+            LDDMM_CUDA(cudaFuncSetAttribute(k_tc_rowgemm<0>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        else
+            LDDMM_CUDA(cudaFuncSetAttribute(k_tc_rowgemm<1>,
+                                            cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        attr_smem[prec] = smem;
     }
     // two accumulators at columns 0 and N; the epilogue reads 32-column blocks, so the
     // second buffer's last block ends at N + roundup(N, 32)
@@ -529,8 +602,12 @@ int tc_rowgemm(const float* in, long rows, int kdim, long in_row_floats, const u
     const int grid = (int)std::min<long>(ntiles, nsm);
     {
         KTRACE(trace_name, st, trace_bytes, 2.0 * rows * (double)N * kdim);
-        k_tc_rowgemm<<<grid, NTHREADS_WS, smem, st>>>(map, omap, W, N, kdim, rows, out, rpc,
-                                                     comp_stride, n_out, cols);
+        if (prec == 0)
+            k_tc_rowgemm<0><<<grid, NTHREADS_WS, smem, st>>>(map, omap, W, N, kdim, rows, out, rpc,
+                                                            comp_stride, n_out, cols);
+        else
+            k_tc_rowgemm<1><<<grid, NTHREADS_WS, smem, st>>>(map, omap, W, N, kdim, rows, out, rpc,
+                                                            comp_stride, n_out, cols);
     }
     LDDMM_CHECK_LAUNCH();
     return LDDMM_OK;

@@ -151,3 +151,18 @@ def test_bl_include_tensor_core_and_simt_paths_match_oracle(shape, K, precision,
     src = c if deriv < 0 else np.stack([S.deriv(ci, deriv) for ci in c])
     assert rel_l2(f, S.include(src, shape)) < 3e-6
     assert L.device_error() == 0
+
+
+@pytest.mark.parametrize("shape,K", TC_CASES + [((96, 112, 96), 32)])
+def test_bf16x3_projection_and_inclusion_error_is_bounded(shape, K):
+    """Mixed-precision spectral path: BF16 hi + lo split products with FP32 accumulation.
+    hi and lo each carry 8 mantissa bits, so the represented operands are exact to ~2^-17
+    and the dropped lo*lo product is ~2^-18 relative: results stay within ~1e-5 of FP64."""
+    f = synth.random_field(shape, seed=53, ncomp=3)
+    c = host(L.bl_project(dev(f), K, precision=L.PREC_BF16X3))
+    e_pi = rel_l2(c, S.project(f, K))
+    cc = synth.random_coeffs(K, seed=54, ncomp=3, decay_power=0.5)
+    g = host(L.bl_include(devc(cc), shape, precision=L.PREC_BF16X3))
+    e_io = rel_l2(g, S.include(cc, shape))
+    assert e_pi < 5e-5 and e_io < 5e-5, (e_pi, e_io)
+    assert L.device_error() == 0

@@ -134,3 +134,39 @@ def test_nonfinite_image_is_reported_and_sticky():
     with pytest.raises(L.LddmmError):
         ctx.objective(ctx.zeros_cube())
     ctx.close()
+
+
+def test_mixed_precision_registration_against_oracle_and_fp32_form():
+    """Small workload in three precision forms against the stored FP64 oracle result:
+    final energy, GN / PCG counts and max displacement difference. With LDDMM_REPORT_DIR set
+    the measured numbers are written there as mixed_precision.json."""
+    ref = json.load(open(os.path.join(HERE, "golden", "config1_seed0.json")))
+    v_ref = np.load(os.path.join(HERE, "golden", "config1_seed0.npz"))["v"]
+    c = ref["config"]
+    prob = oracle_problem(tuple(c["shape"]), c["K"], c["variant"], c["order"], nt=c["nt"],
+                          seed=c["seed"])
+    nz, ny, nx = prob.shape
+    scale = (np.array([nx, ny, nz]) / (2 * np.pi))[:, None, None, None]
+    uo = S.include(prob.state_defstate(v_ref)[-1], prob.shape) * scale
+    out = {}
+    for name, prec in (("fp32_tensor", L.PREC_FP32), ("fp32_simt", L.PREC_FP32_SIMT),
+                       ("bf16x3", L.PREC_BF16X3)):
+        with gpu_context(prob, max_gn=c["max_gn"], max_pcg=c["max_pcg"], gtol=c["gtol"],
+                         precision=prec) as ctx:
+            v, rep = ctx.register()
+        v = host(v)
+        ug = S.include(prob.state_defstate(v)[-1], prob.shape) * scale
+        out[name] = {"E_rel_err": abs(rep["E"] - ref["E"]) / ref["E"],
+                     "v_rel_l2": rel_l2(v, v_ref),
+                     "max_disp_diff_vox": float(np.abs(ug - uo).max()),
+                     "gn_iters": rep["gn_iters"], "pcg_iters": rep["pcg_iters_total"],
+                     "oracle_gn_iters": ref["gn_iters"], "oracle_pcg_iters": ref["pcg_iters_total"]}
+    rd = os.environ.get("LDDMM_REPORT_DIR")
+    if rd:
+        os.makedirs(rd, exist_ok=True)
+        json.dump(out, open(os.path.join(rd, "mixed_precision.json"), "w"), indent=1)
+    for name, r in out.items():
+        assert r["E_rel_err"] < 1e-3, (name, r)
+        assert r["max_disp_diff_vox"] < 1e-2, (name, r)
+    assert out["fp32_tensor"]["gn_iters"] == ref["gn_iters"]
+    assert out["fp32_tensor"]["pcg_iters"] == ref["pcg_iters_total"]
