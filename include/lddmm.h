@@ -131,6 +131,30 @@ int lddmm_hessian_matvec(lddmm_ctx* ctx, const float* v, const float* dv, float*
 int lddmm_register(lddmm_ctx* ctx, float* v_inout, const double* g_ref_norms,
                    lddmm_report* report);
 
+/* Batched form (no counterpart in the paper's text; it serves many independent pairs).
+ * Registers n pairs, each with its own context (created on the current device, ideally each
+ * bound to its own stream so that their kernels overlap), from up to max_threads host
+ * threads (<= 0: 8). Each pair runs lddmm_register with its Hessian-vector product captured
+ * once into a CUDA graph and replayed for every PCG iteration. g_ref_norms: NULL or n pairs
+ * of {||g(0)||_2, ||g(0)||_inf}. reports[i] receives pair i's outcome. Returns the first
+ * failure (message names the pair); the other pairs still complete. Synchronises. */
+int lddmm_register_batch(lddmm_ctx* const* ctxs, float* const* v_inout, int n,
+                         const double* g_ref_norms, lddmm_report* reports, int max_threads);
+
+enum { LDDMM_OPT_GRAPHS = 1, LDDMM_OPT_BLOCK_X = 2 };
+
+/* Context options: LDDMM_OPT_GRAPHS (0/1) captures the PCG Hessian-vector product into a
+ * CUDA graph on its second use and replays it (lddmm_register); LDDMM_OPT_BLOCK_X sets the
+ * x extent of the 256-thread blocks of the SL voxel kernels (must divide 256). */
+int lddmm_set_option(lddmm_ctx* ctx, int option, long value);
+
+/* Autotuner: times the SL voxel kernels of the context's grid for block shapes
+ * 16x16, 32x8, 64x4, 128x2 and 256x1 and keeps the fastest (written to *block_x_out if not
+ * NULL). cache_path (may be NULL): JSON object {"<nx>x<ny>x<nz>/i<interp>": block_x}; an
+ * existing entry is used without timing, a new one is added. Overwrites the context's
+ * departure offsets (the next objective/gradient recomputes them). Synchronises. */
+int lddmm_autotune(lddmm_ctx* ctx, const char* cache_path, int* block_x_out);
+
 /* Warp m(1) = I0 o phi(1) of the last state solved in the context into m1 (device,
  * float[nz][ny][nx]). DEFSTATE: phi(1) = id - iota(u~(1)); IMAGE: m(nt). */
 int lddmm_get_warped(lddmm_ctx* ctx, float* m1);

@@ -31,6 +31,7 @@ INTERP_LINEAR, INTERP_CUBIC = 1, 3
 PREC_FP32, PREC_BF16X3, PREC_FP32_SIMT = 0, 1, 2
 FORWARD, BACKWARD = 1, -1
 STOP_GTOL, STOP_MAXIT, STOP_LINESEARCH = 1, 2, 3
+OPT_GRAPHS, OPT_BLOCK_X = 1, 2
 
 
 class Params(ctypes.Structure):
@@ -80,6 +81,10 @@ def _declare(lib):
         "lddmm_bl_include": (_I, [_I, _I, _I, _I, _P, _I, _P, _I, _I, _I, _P]),
         "lddmm_sl_characteristics": (_I, [_I, _I, _I, _P, _D, _I, _I, _P, _P]),
         "lddmm_sl_transport": (_I, [_I, _I, _I, _I, _I, _P, _P, _I, _I, _P, _P]),
+        "lddmm_register_batch": (_I, [ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _P,
+                                      ctypes.POINTER(Report), _I]),
+        "lddmm_set_option": (_I, [_P, _I, ctypes.c_long]),
+        "lddmm_autotune": (_I, [_P, ctypes.c_char_p, ctypes.POINTER(_I)]),
         "lddmm_launch_count": (ctypes.c_long, []),
         "lddmm_trace_enable": (_I, [_I]),
         "lddmm_trace_reset": (_I, []),
@@ -290,6 +295,16 @@ class Context:
         _check(load().lddmm_register(self._h, _c64(v), ref, ctypes.byref(rep)))
         return v, rep.as_dict()
 
+    def set_option(self, option, value):
+        _check(load().lddmm_set_option(self._h, option, int(value)))
+
+    def autotune(self, cache_path=None):
+        """Picks the fastest SL voxel-kernel block shape for this grid (lddmm_autotune)."""
+        bx = ctypes.c_int(0)
+        path = cache_path.encode() if cache_path else None
+        _check(load().lddmm_autotune(self._h, path, ctypes.byref(bx)))
+        return bx.value
+
     def get_warped(self, out=None):
         import torch
         m = torch.empty(self.shape, dtype=torch.float32, device="cuda") if out is None else out
@@ -327,4 +342,20 @@ def device_error():
     code = ctypes.c_int(0)
     _check(load().lddmm_device_error(ctypes.byref(code)))
     return code.value
+
+
+def register_batch(contexts, velocities, g_ref_norms=None, max_threads=8):
+    """Registers many pairs concurrently (lddmm_register_batch). ``contexts``: Context objects
+    (each best created under its own torch CUDA stream); ``velocities``: complex64
+    [3, K, K, K] device cubes updated in place. Returns the list of report dicts."""
+    n = len(contexts)
+    hs = (_P * n)(*[c._h for c in contexts])
+    vs = (_P * n)(*[ctypes.c_void_p(_c64(v).value) for v in velocities])
+    reps = (Report * n)()
+    ref = None
+    if g_ref_norms is not None:
+        flat = [float(x) for pair in g_ref_norms for x in pair]
+        ref = (ctypes.c_double * (2 * n))(*flat)
+    _check(load().lddmm_register_batch(hs, vs, n, ref, reps, max_threads))
+    return [r.as_dict() for r in reps]
 

@@ -13,7 +13,10 @@
 #include "lddmm.h"
 
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <mutex>
+#include <thread>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -76,6 +79,12 @@ struct lddmm_ctx {
     bool traj_valid = false;   // + Jacobians / grad m~ for the Hessian
     bool warp_valid = false;   // DEFSTATE: m1 and G of the current state
     int solves = 0;
+    // CUDA graph of the PCG Hessian-vector product (cv[C_P] -> cv[C_HP])
+    bool use_graphs = false;
+    bool graph_failed = false;
+    int hv_eager_runs = 0;
+    cudaGraphExec_t hv_exec = nullptr;
+    long hv_graph_launches = 0;
 };
 
 static int fail(lddmm_ctx* c, int rc) {
@@ -478,6 +487,53 @@ static int same_as_current(lddmm_ctx* c, const float2* vt, bool* same) {
     return LDDMM_OK;
 }
 
+// ------------------------------------------------------------------ graph-captured Hv
+// H cv[C_P] -> cv[C_HP] at the current state. With graphs enabled, the first product runs
+// eagerly (it settles kernel attributes), the second is captured into a CUDA graph and every
+// later product (all PCG iterations of all Gauss-Newton updates: the buffers never move)
+// replays it. Tracing forces the eager path so that kernels can be timed.
+static int hessian_pcg(lddmm_ctx* c) {
+    float2* pp = c->cv[lddmm_ctx::C_P];
+    float2* Hp = c->cv[lddmm_ctx::C_HP];
+    TRY(ensure_traj(c));
+    if (c->p.variant == LDDMM_V_DEFSTATE && !c->warp_valid) TRY(data_term(c, nullptr));
+    if (!c->use_graphs || c->graph_failed || tracing()) return hessian_impl(c, pp, Hp);
+    if (c->hv_exec) {
+        LDDMM_CUDA(cudaGraphLaunch(c->hv_exec, c->st));
+        count_launches(c->hv_graph_launches);
+        return LDDMM_OK;
+    }
+    if (c->hv_eager_runs++ == 0) return hessian_impl(c, pp, Hp);
+    cudaGraph_t graph = nullptr;
+    if (cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        c->graph_failed = true;
+        return hessian_impl(c, pp, Hp);
+    }
+    capture_begin();
+    int rc = hessian_impl(c, pp, Hp);
+    long nl = capture_end();
+    cudaError_t e = cudaStreamEndCapture(c->st, &graph);
+    if (rc != LDDMM_OK || e != cudaSuccess || !graph) {
+        cudaGetLastError();
+        if (graph) cudaGraphDestroy(graph);
+        c->graph_failed = true;
+        return hessian_impl(c, pp, Hp);
+    }
+    e = cudaGraphInstantiate(&c->hv_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->hv_exec = nullptr;
+        c->graph_failed = true;
+        return hessian_impl(c, pp, Hp);
+    }
+    c->hv_graph_launches = nl;
+    LDDMM_CUDA(cudaGraphLaunch(c->hv_exec, c->st));
+    count_launches(nl);
+    return LDDMM_OK;
+}
+
 // ------------------------------------------------------------------ GN-Krylov driver
 static double dot_host(lddmm_ctx* c, const float2* a, const float2* b, int* rc) {
     *rc = dot_f2(a, b, 3 * c->kc, c->partials, c->dsc, c->st);
@@ -550,7 +606,7 @@ static int register_impl(lddmm_ctx* c, float2* v_io, const double* gref_in, lddm
         double rz = dot_host(c, r, z, &rc);
         TRY(rc);
         for (int i = 0; i < c->p.max_pcg; ++i) {
-            TRY(hessian_impl(c, pp, Hp));
+            TRY(hessian_pcg(c));
             rep->pcg_iters_total++;
             double pHp = dot_host(c, pp, Hp, &rc);
             TRY(rc);
@@ -730,6 +786,7 @@ int lddmm_create(const lddmm_params* params, void* stream, lddmm_ctx** out) {
 int lddmm_destroy(lddmm_ctx* c) {
     if (!c) return LDDMM_OK;
     if (c->st || true) cudaStreamSynchronize(c->st);
+    if (c->hv_exec) cudaGraphExecDestroy(c->hv_exec);
     for (void* p : c->allocs) cudaFree(p);
     if (c->hsc) cudaFreeHost(c->hsc);
     delete c;
@@ -931,6 +988,188 @@ int lddmm_sl_transport(int nx, int ny, int nz, int nt, int interp, const float* 
         cur = dst;
     }
     return LDDMM_OK;
+}
+
+
+// ------------------------------------------------------------------ options, autotuning
+int lddmm_set_option(lddmm_ctx* c, int option, long value) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    switch (option) {
+        case LDDMM_OPT_GRAPHS:
+            c->use_graphs = value != 0;
+            return LDDMM_OK;
+        case LDDMM_OPT_BLOCK_X: {
+            if (value < 1 || value > 256 || 256 % value != 0) {
+                set_error("block x must divide 256");
+                return LDDMM_EINVAL;
+            }
+            c->sl.bx = (int)value;
+            c->sl.by = 256 / (int)value;
+            return LDDMM_OK;
+        }
+        default:
+            set_error("unknown option");
+            return LDDMM_EINVAL;
+    }
+}
+
+}  // extern "C"
+
+namespace {
+
+std::string tune_key(const lddmm_ctx* c) {
+    return std::to_string(c->g.nx) + "x" + std::to_string(c->g.ny) + "x" + std::to_string(c->g.nz) +
+           "/i" + std::to_string(c->p.interp);
+}
+
+// The cache is a flat JSON object {"<nx>x<ny>x<nz>/i<interp>": <block x>, ...}.
+std::vector<std::pair<std::string, int>> read_tune_cache(const char* path) {
+    std::vector<std::pair<std::string, int>> out;
+    FILE* f = path ? fopen(path, "r") : nullptr;
+    if (!f) return out;
+    std::string text;
+    char buf[4096];
+    size_t n;
+    while ((n = fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, n);
+    fclose(f);
+    size_t pos = 0;
+    while ((pos = text.find('"', pos)) != std::string::npos) {
+        size_t end = text.find('"', pos + 1);
+        if (end == std::string::npos) break;
+        std::string key = text.substr(pos + 1, end - pos - 1);
+        size_t colon = text.find(':', end);
+        if (colon == std::string::npos) break;
+        int v = atoi(text.c_str() + colon + 1);
+        out.emplace_back(key, v);
+        pos = colon + 1;
+    }
+    return out;
+}
+
+void write_tune_cache(const char* path, const std::vector<std::pair<std::string, int>>& kv) {
+    FILE* f = fopen(path, "w");
+    if (!f) return;
+    fprintf(f, "{");
+    for (size_t i = 0; i < kv.size(); ++i)
+        fprintf(f, "%s\n \"%s\": %d", i ? "," : "", kv[i].first.c_str(), kv[i].second);
+    fprintf(f, "\n}\n");
+    fclose(f);
+}
+
+}  // namespace
+
+extern "C" {
+
+// Times the SL voxel kernels of this context's grid for each 256-thread block shape and
+// keeps the fastest; with cache_path, reuses / records the choice there.
+int lddmm_autotune(lddmm_ctx* c, const char* cache_path, int* block_x_out) {
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    const std::string key = tune_key(c);
+    auto kv = read_tune_cache(cache_path);
+    for (auto& e : kv)
+        if (e.first == key && e.second > 0 && 256 % e.second == 0) {
+            c->sl.bx = e.second;
+            c->sl.by = 256 / e.second;
+            if (block_x_out) *block_x_out = e.second;
+            return LDDMM_OK;
+        }
+    // candidates; inputs are the context's own buffers (zeroed offsets: no data dependence
+    // of the timing beyond the access pattern of a zero displacement)
+    const int cand[] = {32, 64, 128, 256, 16};
+    const long n = c->n;
+    LDDMM_CUDA(cudaMemsetAsync(c->Df, 0, 3 * n * sizeof(float), c->st));
+    cudaEvent_t e0, e1;
+    LDDMM_CUDA(cudaEventCreate(&e0));
+    LDDMM_CUDA(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int best_bx = c->sl.bx;
+    for (int bx : cand) {
+        SLArgs a = c->sl;
+        a.bx = bx;
+        a.by = 256 / bx;
+        float tot = 0.f;
+        for (int rep = 0; rep < 4; ++rep) {
+            LDDMM_CUDA(cudaEventRecord(e0, c->st));
+            rc = sl_gather_scale(a, c->fa, c->Df, c->gam, 3, c->fb, c->st);
+            if (rc == LDDMM_OK && c->p.variant == LDDMM_V_DEFSTATE && c->Du)
+                rc = sl_inc_defstate(a, c->fa, c->Df, c->fb, c->Du, c->dvsp, c->dt, c->fc, c->fd, c->st);
+            LDDMM_CUDA(cudaEventRecord(e1, c->st));
+            LDDMM_CUDA(cudaEventSynchronize(e1));
+            if (rc) break;
+            float ms = 0.f;
+            LDDMM_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+            if (rep > 0) tot += ms;  // first repetition warms up
+        }
+        if (rc) break;
+        if (tot < best) {
+            best = tot;
+            best_bx = bx;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (rc) return fail(c, rc);
+    c->sl.bx = best_bx;
+    c->sl.by = 256 / best_bx;
+    c->vel_valid = c->traj_valid = c->warp_valid = false;  // the offsets were overwritten
+    if (block_x_out) *block_x_out = best_bx;
+    if (cache_path) {
+        kv.emplace_back(key, best_bx);
+        write_tune_cache(cache_path, kv);
+    }
+    return LDDMM_OK;
+}
+
+// ------------------------------------------------------------------ batched registration
+int lddmm_register_batch(lddmm_ctx* const* ctxs, float* const* v_inout, int n,
+                         const double* g_ref_norms, lddmm_report* reports, int max_threads) {
+    if (n < 0 || (n > 0 && (!ctxs || !v_inout || !reports))) {
+        set_error("register_batch: null arrays or n < 0");
+        return LDDMM_EINVAL;
+    }
+    for (int i = 0; i < n; ++i) {
+        int rc = check_ctx(ctxs[i]);
+        if (rc) return rc;
+        if (!v_inout[i]) {
+            set_error("register_batch: null velocity");
+            return LDDMM_EINVAL;
+        }
+    }
+    int dev = 0;
+    LDDMM_CUDA(cudaGetDevice(&dev));
+    const int nthreads = std::max(1, std::min(n, max_threads > 0 ? max_threads : 8));
+    std::atomic<int> next{0};
+    std::atomic<int> first_rc{LDDMM_OK};
+    std::string first_msg;
+    std::mutex msg_mu;
+    auto worker = [&]() {
+        cudaSetDevice(dev);
+        for (;;) {
+            const int i = next.fetch_add(1);
+            if (i >= n) break;
+            lddmm_ctx* c = ctxs[i];
+            const bool g = c->use_graphs;
+            c->use_graphs = true;
+            int rc = register_impl(c, reinterpret_cast<float2*>(v_inout[i]),
+                                   g_ref_norms ? g_ref_norms + 2 * i : nullptr, &reports[i]);
+            c->use_graphs = g;
+            if (rc != LDDMM_OK) {
+                fail(c, rc);
+                int expect = LDDMM_OK;
+                if (first_rc.compare_exchange_strong(expect, rc)) {
+                    std::lock_guard<std::mutex> lk(msg_mu);
+                    first_msg = "pair " + std::to_string(i) + ": " + g_last_error;
+                }
+            }
+        }
+    };
+    std::vector<std::thread> pool;
+    for (int t = 0; t < nthreads; ++t) pool.emplace_back(worker);
+    for (auto& t : pool) t.join();
+    if (first_rc.load() != LDDMM_OK) set_error(first_msg);
+    return first_rc.load();
 }
 
 }  // extern "C"

@@ -38,6 +38,13 @@ class KTrace {
     double bytes_, flops_;
     void* a_;
 };
+// Graph capture bookkeeping: launches made while capturing are counted into the graph and
+// added to the process count each time the graph is launched.
+void capture_begin();
+long capture_end();
+void count_launches(long n);
+bool tracing();
+
 #define KTRACE(name, st, bytes, flops) ::lddmm::KTrace ktrace__(name, st, (double)(bytes), (double)(flops))
 
 struct Grid {
@@ -105,7 +112,9 @@ constexpr int kReduceBlocks = 296;  // 2 x 148 SMs
 // ---------------------------------------------------------------- SL kernels (sl.cu)
 struct SLArgs {
     Grid g;
-    int interp;  // 1 or 3
+    int interp;      // 1 or 3
+    int bx = 32;     // block shape of the one-voxel-per-thread kernels (bx * by = 256)
+    int by = 8;
 };
 // D = offsets of departure points; vsrc = samples (linear) or spline coefficients (cubic)
 // of the velocity, vval its samples; scale[a] converts component a to voxels.

@@ -214,6 +214,8 @@ struct Interp<3> {
 
 static inline dim3 vox_grid(const Grid& g) { return dim3(cdiv(g.nx, 32), cdiv(g.ny, 8), g.nz); }
 static const dim3 kVoxBlock(32, 8, 1);
+// launch shape of a voxel kernel for SLArgs (autotuned block, 256 threads)
+#define VOX_LAUNCH(a) dim3(cdiv((a).g.nx, (a).bx), cdiv((a).g.ny, (a).by), (a).g.nz), dim3((a).bx, (a).by, 1)
 
 // ---------------------------------------------------------------- characteristics
 template <int IP>
@@ -234,10 +236,10 @@ int sl_characteristics(const SLArgs& a, const float* vsrc, const float* vval, co
                        double dt_signed, float* D, cudaStream_t st) {
     KTRACE(a.interp == 3 ? "sl_char_cubic" : "sl_char", st, 36.0 * a.g.ntot(), 0);
     if (a.interp == 3)
-        k_sl_char<3><<<vox_grid(a.g), kVoxBlock, 0, st>>>(a.g, vsrc, vval, scale[0], scale[1],
+        k_sl_char<3><<<VOX_LAUNCH(a), 0, st>>>(a.g, vsrc, vval, scale[0], scale[1],
                                                           scale[2], (float)dt_signed, D);
     else
-        k_sl_char<1><<<vox_grid(a.g), kVoxBlock, 0, st>>>(a.g, vsrc, vval, scale[0], scale[1],
+        k_sl_char<1><<<VOX_LAUNCH(a), 0, st>>>(a.g, vsrc, vval, scale[0], scale[1],
                                                           scale[2], (float)dt_signed, D);
     LDDMM_CHECK_LAUNCH();
     return LDDMM_OK;
@@ -320,10 +322,10 @@ static void launch_gather_nc(const SLArgs& a, const float* src, const float* D, 
             k_sl_gather4<MODE, 1><<<g4, b4, 0, st>>>(a.g, s, D, x, o);
             c0 += 1;
         } else if (left >= 3) {
-            k_sl_gather<IP, MODE, 3><<<vox_grid(a.g), kVoxBlock, 0, st>>>(a.g, s, D, x, o);
+            k_sl_gather<IP, MODE, 3><<<VOX_LAUNCH(a), 0, st>>>(a.g, s, D, x, o);
             c0 += 3;
         } else {
-            k_sl_gather<IP, MODE, 1><<<vox_grid(a.g), kVoxBlock, 0, st>>>(a.g, s, D, x, o);
+            k_sl_gather<IP, MODE, 1><<<VOX_LAUNCH(a), 0, st>>>(a.g, s, D, x, o);
             c0 += 1;
         }
     }
@@ -378,9 +380,9 @@ int sl_prep_adjoint(const SLArgs& a, const float* dsrc, const float* dval, const
                     double dt, float* gam, cudaStream_t st) {
     KTRACE("sl_prep_adjoint", st, 24.0 * a.g.ntot(), 0);
     if (a.interp == 3)
-        k_prep_adjoint<3><<<vox_grid(a.g), kVoxBlock, 0, st>>>(a.g, dsrc, dval, Dp, (float)dt, gam);
+        k_prep_adjoint<3><<<VOX_LAUNCH(a), 0, st>>>(a.g, dsrc, dval, Dp, (float)dt, gam);
     else
-        k_prep_adjoint<1><<<vox_grid(a.g), kVoxBlock, 0, st>>>(a.g, dsrc, dval, Dp, (float)dt, gam);
+        k_prep_adjoint<1><<<VOX_LAUNCH(a), 0, st>>>(a.g, dsrc, dval, Dp, (float)dt, gam);
     LDDMM_CHECK_LAUNCH();
     return LDDMM_OK;
 }
@@ -400,9 +402,9 @@ int sl_prep_source(const SLArgs& a, const float* vsrc, const float* vval, const 
                    double dt, float* W, cudaStream_t st) {
     KTRACE("sl_prep_source", st, 48.0 * a.g.ntot(), 0);
     if (a.interp == 3)
-        k_prep_source<3><<<vox_grid(a.g), kVoxBlock, 0, st>>>(a.g, vsrc, vval, D, (float)dt, W);
+        k_prep_source<3><<<VOX_LAUNCH(a), 0, st>>>(a.g, vsrc, vval, D, (float)dt, W);
     else
-        k_prep_source<1><<<vox_grid(a.g), kVoxBlock, 0, st>>>(a.g, vsrc, vval, D, (float)dt, W);
+        k_prep_source<1><<<VOX_LAUNCH(a), 0, st>>>(a.g, vsrc, vval, D, (float)dt, W);
     LDDMM_CHECK_LAUNCH();
     return LDDMM_OK;
 }
@@ -515,10 +517,10 @@ int sl_inc_defstate(const SLArgs& a, const float* U, const float* D, const float
                     cudaStream_t st) {
     KTRACE(a.interp == 3 ? "sl_inc_defstate_cubic" : "sl_inc_defstate", st, 108.0 * a.g.ntot(), 0);
     if (a.interp == 3)
-        k_inc_defstate<3><<<vox_grid(a.g), kVoxBlock, 0, st>>>(a.g, U, D, Fold, Du, dv, (float)dt,
+        k_inc_defstate<3><<<VOX_LAUNCH(a), 0, st>>>(a.g, U, D, Fold, Du, dv, (float)dt,
                                                                out, Fnew);
     else
-        k_inc_defstate<1><<<vox_grid(a.g), kVoxBlock, 0, st>>>(a.g, U, D, Fold, Du, dv, (float)dt,
+        k_inc_defstate<1><<<VOX_LAUNCH(a), 0, st>>>(a.g, U, D, Fold, Du, dv, (float)dt,
                                                                out, Fnew);
     LDDMM_CHECK_LAUNCH();
     return LDDMM_OK;
@@ -751,10 +753,10 @@ int sl_inc_image(const SLArgs& a, const float* U, const float* D, const float* F
                  cudaStream_t st) {
     KTRACE(a.interp == 3 ? "sl_inc_image_cubic" : "sl_inc_image", st, 52.0 * a.g.ntot(), 0);
     if (a.interp == 3)
-        k_inc_image<3><<<vox_grid(a.g), kVoxBlock, 0, st>>>(a.g, U, D, Fold, Gm, dv, (float)dt, out,
+        k_inc_image<3><<<VOX_LAUNCH(a), 0, st>>>(a.g, U, D, Fold, Gm, dv, (float)dt, out,
                                                             Fnew);
     else
-        k_inc_image<1><<<vox_grid(a.g), kVoxBlock, 0, st>>>(a.g, U, D, Fold, Gm, dv, (float)dt, out,
+        k_inc_image<1><<<VOX_LAUNCH(a), 0, st>>>(a.g, U, D, Fold, Gm, dv, (float)dt, out,
                                                             Fnew);
     LDDMM_CHECK_LAUNCH();
     return LDDMM_OK;

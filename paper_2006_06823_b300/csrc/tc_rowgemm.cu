@@ -595,9 +595,13 @@ int tc_rowgemm(const float* in, long rows, int kdim, long in_row_floats, const u
         set_error("tc_rowgemm: N too large for tensor memory");
         return LDDMM_EINVAL;
     }
-    int dev = 0, nsm = 148;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0, v = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        nsm = v;
+    }
     const long ntiles = (rows + TM - 1) / TM;
     const int grid = (int)std::min<long>(ntiles, nsm);
     {

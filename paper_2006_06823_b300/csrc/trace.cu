@@ -19,6 +19,8 @@ struct Rec {
     double bytes, flops;
 };
 std::atomic<long> g_launches{0};
+thread_local bool t_capturing = false;   // this thread is capturing a CUDA graph
+thread_local long t_captured = 0;        // launches recorded into the graph so far
 std::atomic<bool> g_enabled{false};
 std::mutex g_mu;
 std::vector<Rec> g_recs;
@@ -59,6 +61,10 @@ void drain_locked() {
 
 KTrace::KTrace(const char* name, cudaStream_t st, double bytes, double flops)
     : name_(name), st_(st), bytes_(bytes), flops_(flops), a_(nullptr) {
+    if (t_capturing) {  // counted when the graph is launched; no events inside a graph
+        ++t_captured;
+        return;
+    }
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if (g_enabled.load(std::memory_order_relaxed)) {
         std::lock_guard<std::mutex> lk(g_mu);
@@ -75,6 +81,17 @@ KTrace::~KTrace() {
     g_recs.push_back(Rec{name_, static_cast<cudaEvent_t>(a_), b, bytes_, flops_});
     if (g_recs.size() > 4096) drain_locked();
 }
+
+void capture_begin() {
+    t_capturing = true;
+    t_captured = 0;
+}
+long capture_end() {
+    t_capturing = false;
+    return t_captured;
+}
+void count_launches(long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+bool tracing() { return g_enabled.load(std::memory_order_relaxed); }
 
 }  // namespace lddmm
 
