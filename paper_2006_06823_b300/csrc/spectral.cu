@@ -450,114 +450,199 @@ int bl_project(const Grid& g, const Twiddles& tw, const float* f, long fstride, 
     return LDDMM_OK;
 }
 
-// ------------------------------------------------------------------- iota, stages Z+Y
-// One CTA per (comp, z) plane:
-//   T1[jy][kx] = sum_{jz>=1} m(k) c[comp][jz][jy][K/2+kx] e^{+i kz 2pi z/nz}    (smem)
-//   T2[y][kx]  = sum_{jy>=1} T1[jy][kx] e^{+i ky 2pi y/ny}                        (global)
-// m(k) = i k_axis (deriv_axis 0..2), the divergence sum_a i k_a c_a (deriv_axis 3), or 1;
-// divided by B^(k) = prod_a (2 + cos(2 pi k_a / n_a)) / 3 when bspline is set.
-template <int KHP>
+// ------------------------------------------------- iota stage Z (GEMM over all planes)
+// T1[comp][z][j] = sum_{jz>=1} Ez[z][jz] * m(k) c[comp][jz][jy][K/2+kx],  j = jy*KH + kx,
+// with m(k) the derivative / divergence multiplier and 1/B^(k) for B-spline coefficients.
+// CTA tile: 32 planes x 64 columns; thread: 4 planes x 2 columns (8 complex accumulators).
+constexpr int Z2_ZT = 32, Z2_JT = 64;
+
 __global__ void __launch_bounds__(256)
-k_iota_zy(const float2* __restrict__ c, int nz, int ny, int nx, int K, int KH, int deriv_axis,
+k_iota_z2(const float2* __restrict__ c, int nz, int ny, int nx, int K, int KH, int deriv_axis,
           int bspline, const float* __restrict__ cxT, const float* __restrict__ cyT,
-          const float* __restrict__ czT, const float* __restrict__ szT,
-          const float* __restrict__ cyTab, const float* __restrict__ syTab,
-          float2* __restrict__ T2) {
-    extern __shared__ float4 smem4[];
-    float2* t1 = reinterpret_cast<float2*>(smem4);          // K * KHP  [jy][kx]
-    float2* twz = t1 + (long)K * KHP;                       // K        e^{i kz z}
-    float* bx = reinterpret_cast<float*>(twz + K);          // KHP      1/B^_x(kx)
-    float* by = bx + KHP;                                   // K        1/B^_y(ky)
-    float* bz = by + K;                                     // K        1/B^_z(kz)
-    const int comp = blockIdx.x / nz, z = blockIdx.x - comp * nz;
-    const int h = K / 2;
-    const int tid = threadIdx.x, nt = blockDim.x;
-    for (int e = tid; e < K; e += nt) {
-        twz[e] = make_float2(czT[(long)e * nz + z], szT[(long)e * nz + z]);
-        by[e] = bspline ? 3.f / (2.f + cyT[(long)e * ny + 1]) : 1.f;
-        bz[e] = bspline ? 3.f / (2.f + czT[(long)e * nz + 1]) : 1.f;
-    }
-    for (int e = tid; e < KHP; e += nt) bx[e] = (bspline && e < KH) ? 3.f / (2.f + cxT[(long)(h + e) * nx + 1]) : 1.f;
-    __syncthreads();
-    // stage Z
-    for (int e = tid; e < K * KHP; e += nt) {
-        const int jy = e / KHP, kx = e - jy * KHP;
-        float re = 0.f, im = 0.f;
-        if (jy >= 1 && kx < KH) {
-            const float ky = (float)(jy - h);
-#pragma unroll 4
-            for (int jz = 1; jz < K; ++jz) {
-                const float kz = (float)(jz - h);
-                float vr, vi;
-                if (deriv_axis == 3) {
+          const float* __restrict__ czT, const float* __restrict__ szT, float2* __restrict__ T1) {
+    __shared__ float4 cs4[32 * Z2_JT / 2];   // [jz][64] float2 (K <= 64 -> 2 passes if K > 32)
+    __shared__ float4 es4[32 * Z2_ZT / 2];   // [jz][32] float2
+    float2* cs = reinterpret_cast<float2*>(cs4);
+    float2* es = reinterpret_cast<float2*>(es4);
+    const int comp = blockIdx.z;
+    const int z0 = blockIdx.x * Z2_ZT, j0 = blockIdx.y * Z2_JT;
+    const int KK = K * KH, h = K / 2;
+    const int tid = threadIdx.x, jq = tid & 31, zq = tid >> 5;   // 32 x 8
+    float ar[4][2], ai[4][2];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b) ar[a][b] = ai[a][b] = 0.f;
+    const long kk3 = (long)K * K * K;
+    for (int jzb = 0; jzb < K; jzb += 32) {
+        const int nj = min(32, K - jzb);
+        __syncthreads();
+        for (int e = tid; e < 32 * Z2_JT; e += 256) {
+            const int jzl = e / Z2_JT, jj = e - jzl * Z2_JT;
+            const int jz = jzb + jzl, j = j0 + jj;
+            float2 v = make_float2(0.f, 0.f);
+            if (jzl < nj && jz >= 1 && j < KK) {
+                const int jy = j / KH, kx = j - jy * KH;
+                if (jy >= 1) {
                     const long o = ((long)jz * K + jy) * K + h + kx;
-                    const long kk = (long)K * K * K;
-                    float2 a0 = c[o], a1 = c[kk + o], a2 = c[2 * kk + o];
-                    vr = -((float)kx * a0.y + ky * a1.y + kz * a2.y);
-                    vi = (float)kx * a0.x + ky * a1.x + kz * a2.x;
-                } else {
-                    float2 v = c[(((long)comp * K + jz) * K + jy) * K + h + kx];
-                    if (deriv_axis < 0) {
-                        vr = v.x;
-                        vi = v.y;
+                    const float kxf = (float)kx, kyf = (float)(jy - h), kzf = (float)(jz - h);
+                    float vr, vi;
+                    if (deriv_axis == 3) {
+                        const float2 a0 = c[o], a1 = c[kk3 + o], a2 = c[2 * kk3 + o];
+                        vr = -(kxf * a0.y + kyf * a1.y + kzf * a2.y);
+                        vi = kxf * a0.x + kyf * a1.x + kzf * a2.x;
                     } else {
-                        const float k = deriv_axis == 0 ? (float)kx : deriv_axis == 1 ? ky : kz;
-                        vr = -k * v.y;
-                        vi = k * v.x;
+                        const float2 w = c[comp * kk3 + o];
+                        if (deriv_axis < 0) {
+                            vr = w.x;
+                            vi = w.y;
+                        } else {
+                            const float k = deriv_axis == 0 ? kxf : deriv_axis == 1 ? kyf : kzf;
+                            vr = -k * w.y;
+                            vi = k * w.x;
+                        }
                     }
+                    if (bspline) {
+                        const float b = 27.f / ((2.f + cxT[(long)(h + kx) * nx + 1]) *
+                                                (2.f + cyT[(long)jy * ny + 1]) *
+                                                (2.f + czT[(long)jz * nz + 1]));
+                        vr *= b;
+                        vi *= b;
+                    }
+                    v = make_float2(vr, vi);
                 }
-                const float b = bz[jz];
-                const float2 t = twz[jz];
-                re = fmaf(b * vr, t.x, fmaf(-b * vi, t.y, re));
-                im = fmaf(b * vr, t.y, fmaf(b * vi, t.x, im));
             }
-            const float s = bx[kx] * by[jy];
-            re *= s;
-            im *= s;
+            cs[e] = v;
         }
-        t1[e] = make_float2(re, im);
+        for (int e = tid; e < 32 * Z2_ZT; e += 256) {
+            const int jzl = e / Z2_ZT, zz = e - jzl * Z2_ZT;
+            const int jz = jzb + jzl, z = z0 + zz;
+            es[e] = (jzl < nj && z < nz) ? make_float2(czT[(long)jz * nz + z], szT[(long)jz * nz + z])
+                                         : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        for (int jzl = 0; jzl < nj; ++jzl) {
+            const float4 cv = *reinterpret_cast<const float4*>(&cs[jzl * Z2_JT + 2 * jq]);
+            const float4 e01 = *reinterpret_cast<const float4*>(&es[jzl * Z2_ZT + 4 * zq]);
+            const float4 e23 = *reinterpret_cast<const float4*>(&es[jzl * Z2_ZT + 4 * zq + 2]);
+            const float2 ev[4] = {make_float2(e01.x, e01.y), make_float2(e01.z, e01.w),
+                                  make_float2(e23.x, e23.y), make_float2(e23.z, e23.w)};
+            const float2 cw[2] = {make_float2(cv.x, cv.y), make_float2(cv.z, cv.w)};
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 2; ++b) {
+                    // (e.x + i e.y)(c.x + i c.y)
+                    ar[a][b] = fmaf(ev[a].x, cw[b].x, fmaf(-ev[a].y, cw[b].y, ar[a][b]));
+                    ai[a][b] = fmaf(ev[a].x, cw[b].y, fmaf(ev[a].y, cw[b].x, ai[a][b]));
+                }
+        }
     }
-    __syncthreads();
-    // stage Y
-    float2* out = T2 + (long)blockIdx.x * ny * KH;
-    for (int e = tid; e < ny * KHP; e += nt) {
-        const int y = e / KHP, kx = e - y * KHP;
-        if (kx >= KH) continue;
-        float re = 0.f, im = 0.f;
-#pragma unroll 4
-        for (int jy = 1; jy < K; ++jy) {
-            const float2 v = t1[jy * KHP + kx];
-            // y twiddles straight from the (L1-resident) table
-            const float tc = __ldg(cyTab + (long)jy * ny + y), ts = __ldg(syTab + (long)jy * ny + y);
-            re = fmaf(v.x, tc, fmaf(-v.y, ts, re));
-            im = fmaf(v.x, ts, fmaf(v.y, tc, im));
-        }
-        out[y * KH + kx] = make_float2(re, im);
+#pragma unroll
+    for (int a = 0; a < 4; ++a) {
+        const int z = z0 + 4 * zq + a;
+        if (z >= nz) continue;
+        float2* dst = T1 + ((long)comp * nz + z) * KK + j0 + 2 * jq;
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+            if (j0 + 2 * jq + b < KK) dst[b] = make_float2(ar[a][b], ai[a][b]);
     }
 }
 
-template <int KHP>
-static int launch_iota_zy(const Grid& g, const Twiddles& tw, const float2* c, int nout,
-                          int deriv_axis, int bspline, float2* T2, cudaStream_t st) {
-    const int K = tw.K, KH = K / 2;
-    size_t smem = (size_t)K * KHP * 8 + (size_t)K * 8 + (size_t)(KHP + 2 * K) * 4;
-    if (smem > 227 * 1024) {
+// ---------------------------------------------------------- iota stage Y (register-tiled)
+// T2[plane][y][kx] = sum_{jy>=1} Ey[y][jy] T1[plane][jy][kx]; persistent CTA over planes,
+// twiddles [jy][y] in shared memory once; thread tile 4 y x 4 kx.
+__global__ void __launch_bounds__(256)
+k_iota_y2(const float2* __restrict__ T1, int nplanes, int ny, int K, int KH,
+          const float* __restrict__ cyT, const float* __restrict__ syT, float2* __restrict__ T2) {
+    extern __shared__ float4 smem4[];
+    const int nyp = (ny + 3) & ~3, KHP = (KH + 3) & ~3;
+    float2* tw = reinterpret_cast<float2*>(smem4);   // K x nyp
+    float2* t1 = tw + (long)K * nyp;                 // K x KHP
+    const int tid = threadIdx.x;
+    for (int e = tid; e < K * nyp; e += blockDim.x) {
+        const int jy = e / nyp, y = e - jy * nyp;
+        tw[e] = (jy >= 1 && y < ny) ? make_float2(cyT[(long)jy * ny + y], syT[(long)jy * ny + y])
+                                    : make_float2(0.f, 0.f);
+    }
+    const int kgroups = KHP / 4, ygroups = nyp / 4;
+    const int tiles = kgroups * ygroups;
+    for (int plane = blockIdx.x; plane < nplanes; plane += gridDim.x) {
+        __syncthreads();
+        for (int e = tid; e < K * KHP; e += blockDim.x) {
+            const int jy = e / KHP, kx = e - jy * KHP;
+            t1[e] = kx < KH ? T1[((long)plane * K + jy) * KH + kx] : make_float2(0.f, 0.f);
+        }
+        __syncthreads();
+        float2* out = T2 + (long)plane * ny * KH;
+        for (int tile = tid; tile < tiles; tile += blockDim.x) {
+            const int kg = tile % kgroups, yg = tile / kgroups;
+            float ar[4][4], ai[4][4];
+#pragma unroll
+            for (int a = 0; a < 4; ++a)
+#pragma unroll
+                for (int b = 0; b < 4; ++b) ar[a][b] = ai[a][b] = 0.f;
+            for (int jy = 1; jy < K; ++jy) {
+                const float4 e01 = *reinterpret_cast<const float4*>(&tw[jy * nyp + 4 * yg]);
+                const float4 e23 = *reinterpret_cast<const float4*>(&tw[jy * nyp + 4 * yg + 2]);
+                const float4 t01 = *reinterpret_cast<const float4*>(&t1[jy * KHP + 4 * kg]);
+                const float4 t23 = *reinterpret_cast<const float4*>(&t1[jy * KHP + 4 * kg + 2]);
+                const float2 ev[4] = {make_float2(e01.x, e01.y), make_float2(e01.z, e01.w),
+                                      make_float2(e23.x, e23.y), make_float2(e23.z, e23.w)};
+                const float2 tv[4] = {make_float2(t01.x, t01.y), make_float2(t01.z, t01.w),
+                                      make_float2(t23.x, t23.y), make_float2(t23.z, t23.w)};
+#pragma unroll
+                for (int a = 0; a < 4; ++a)
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        ar[a][b] = fmaf(ev[a].x, tv[b].x, fmaf(-ev[a].y, tv[b].y, ar[a][b]));
+                        ai[a][b] = fmaf(ev[a].x, tv[b].y, fmaf(ev[a].y, tv[b].x, ai[a][b]));
+                    }
+            }
+#pragma unroll
+            for (int a = 0; a < 4; ++a) {
+                const int y = 4 * yg + a;
+                if (y >= ny) continue;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const int kx = 4 * kg + b;
+                    if (kx < KH) out[(long)y * KH + kx] = make_float2(ar[a][b], ai[a][b]);
+                }
+            }
+        }
+    }
+}
+
+static int launch_iota_zy2(const Grid& g, const Twiddles& tw, const float2* c, int nout,
+                           int deriv_axis, int bspline, float2* T1, float2* T2, cudaStream_t st) {
+    const int K = tw.K, KH = K / 2, KK = K * KH;
+    {
+        dim3 grid(cdiv(g.nz, Z2_ZT), cdiv(KK, Z2_JT), nout);
+        KTRACE("iota_z", st, (double)(deriv_axis == 3 ? 3 : nout) * K * K * KH * 8.0 +
+                                 (double)nout * g.nz * KK * 8.0,
+               (double)nout * g.nz * KK * K * 8.0);
+        k_iota_z2<<<grid, 256, 0, st>>>(c, g.nz, g.ny, g.nx, K, KH, deriv_axis, bspline, tw.cx,
+                                        tw.cy, tw.cz, tw.sz, T1);
+    }
+    LDDMM_CHECK_LAUNCH();
+    const int nyp = (g.ny + 3) & ~3, KHP = (KH + 3) & ~3;
+    const size_t smem = (size_t)K * nyp * 8 + (size_t)K * KHP * 8;
+    if (smem > 200 * 1024) {
         set_error("bl_include: ny too large for the y stage");
         return LDDMM_EINVAL;
     }
-    static bool attr_set = false;
-    if (!attr_set) {
-        LDDMM_CUDA(cudaFuncSetAttribute(k_iota_zy<KHP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        227 * 1024));
-        attr_set = true;
+    static bool attr = false;
+    if (!attr) {
+        LDDMM_CUDA(cudaFuncSetAttribute(k_iota_y2, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        200 * 1024));
+        attr = true;
     }
-    const int nslabs = nout * g.nz;
+    const int nplanes = nout * g.nz;
     {
-        KTRACE("iota_zy", st, (double)(deriv_axis == 3 ? 3 : nout) * K * K * KH * 8.0 * g.nz / 8.0 +
-                                  (double)nslabs * g.ny * KH * 8.0,
-               (double)nslabs * (K * KH * K + g.ny * KH * K) * 8.0);
-        k_iota_zy<KHP><<<nslabs, 256, smem, st>>>(c, g.nz, g.ny, g.nx, K, KH, deriv_axis, bspline,
-                                                   tw.cx, tw.cy, tw.cz, tw.sz, tw.cy, tw.sy, T2);
+        KTRACE("iota_y", st, (double)nplanes * (K + g.ny) * KH * 8.0,
+               (double)nplanes * g.ny * KH * K * 8.0);
+        k_iota_y2<<<std::min(nplanes, 3 * 148), 256, smem, st>>>(T1, nplanes, g.ny, K, KH, tw.cy,
+                                                                tw.sy, T2);
     }
     LDDMM_CHECK_LAUNCH();
     return LDDMM_OK;
@@ -686,7 +771,8 @@ int bl_include(const Grid& g, const Twiddles& tw, const float2* c, int ncomp, fl
     const int K = tw.K, KH = K / 2;
     const int nout = deriv_axis == 3 ? 1 : ncomp;
     (void)s2;
-    int rc2 = KHP_DISPATCH(KH, launch_iota_zy, g, tw, c, nout, deriv_axis, bspline ? 1 : 0, s1, st);
+    // stage Z into s2, stage Y into s1
+    int rc2 = launch_iota_zy2(g, tw, c, nout, deriv_axis, bspline ? 1 : 0, s2, s1, st);
     if (rc2) return rc2;
     const long rows = (long)nout * g.nz * g.ny;
     if (precision != LDDMM_PREC_FP32_SIMT && tc_rowgemm_supported(g.nx, K, rows, s1, K)) {
