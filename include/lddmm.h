@@ -212,6 +212,66 @@ int lddmm_sl_transport(int nx, int ny, int nz, int nt, int interp, const float* 
                        const float* field, int ncomp, int direction, float* out,
                        void* stream);
 
+/* ------------------------------------------------------- learned Gauss-Newton warm start */
+/* No counterpart in the paper (its solver always starts from v = 0). A 3-D convolutional
+ * encoder-decoder maps the image pair, band-limited and resampled to D^3, to a velocity on
+ * the (D/2)^3 grid; its band-limited projection is an initial velocity for lddmm_register,
+ * which then finishes the registration and judges the prediction by its own residual.
+ * Architecture (base c channels): D^3: conv 2->c, c->c; pool; (D/2)^3: c->2c, 2c->2c;
+ * pool; (D/4)^3: 2c->4c, 4c->4c; pool; (D/8)^3: 4c->8c, 8c->8c; upsample; (D/4)^3:
+ * [8c up | 4c skip] -> 4c, 4c->4c; upsample; (D/2)^3: [4c up | 2c skip] -> 2c, 2c->2c,
+ * 2c->3. Convolutions 3x3x3 (zero padding, stride 1) with ReLU except the last; pooling is
+ * the 2x2x2 mean; upsampling repeats each voxel 2x2x2. Weights and activations are stored
+ * BF16 (LDDMM_NET_FP32: FP32), master weights, gradients and Adam moments FP32, all sums
+ * accumulate in FP32.
+ * Network tensors are device float arrays: input x [B][2][D][D][D] (channel 0 = I0, the
+ * template, channel 1 = I1, the reference), output y [B][3][D/2][D/2][D/2] (physical
+ * velocity components x, y, z). Parameters: one flat float vector, per convolution in
+ * forward order its weights W[cout][cin][27] (tap t = (dz+1)*9 + (dy+1)*3 + (dx+1)) then
+ * its biases b[cout]. The network object owns all its device memory; calls run on its
+ * stream, are not thread-safe on one object, and are asynchronous unless stated. */
+typedef struct lddmm_net lddmm_net;
+
+/* Storage of the network's weights and activations: BF16 (the default form) or FP32 (the
+ * same kernels with FP32 storage; the reference form for checking the BF16 one). */
+enum { LDDMM_NET_BF16 = 0, LDDMM_NET_FP32 = 1 };
+
+/* D a power of two in 8..128, base_channels 1..64, batch_max 1..64 (largest B of later
+ * calls), storage LDDMM_NET_BF16 or LDDMM_NET_FP32. Weights He-initialised (normal, std
+ * sqrt(2 / (27 cin))) from `seed`, biases 0. Synchronises. Errors: EINVAL, ENOMEM, ECUDA. */
+int lddmm_net_create(int D, int base_channels, int batch_max, int storage,
+                     unsigned long long seed, void* stream, lddmm_net** out);
+int lddmm_net_destroy(lddmm_net* net);
+/* Length of the flat parameter vector (0 for NULL). */
+long lddmm_net_num_params(const lddmm_net* net);
+/* Copy the FP32 parameters to / from dst / src (host or device, num_params floats).
+ * set_params also resets the Adam state. Both synchronise. */
+int lddmm_net_get_params(lddmm_net* net, float* dst);
+int lddmm_net_set_params(lddmm_net* net, const float* src);
+/* y = net(x) for B samples (device pointers). Errors: EINVAL (B outside 1..batch_max,
+ * NULL), ECUDA. */
+int lddmm_net_forward(lddmm_net* net, const float* x, int B, float* y);
+/* grads (device, num_params floats) = gradient of sum(dy * net(x)) over the parameters,
+ * layout as the parameter vector. Errors as lddmm_net_forward. */
+int lddmm_net_gradients(lddmm_net* net, const float* x, const float* dy, int B, float* grads);
+/* One Adam step (beta1 0.9, beta2 0.999, eps 1e-8, learning rate lr > 0) on the mean squared
+ * error mean((net(x) - target)^2) of B samples (target [B][3][D/2]^3, device). The loss of
+ * the step's forward pass goes to *loss (host, FP64) if loss is not NULL, which
+ * synchronises. Errors as lddmm_net_forward, EINVAL for lr <= 0. */
+int lddmm_net_train_step(lddmm_net* net, const float* x, const float* target, int B, float lr,
+                         double* loss);
+/* Network input of one pair: x[c] = iota_{D^3}(pi_D(I_c)), each image (device,
+ * float[nz][ny][nx], nx, ny, nz >= D) band-limited to D^3 modes and evaluated on the D^3
+ * grid of the same domain (spectral resampling, Sec. 2.2 operators). x: device
+ * float[2][D][D][D]. Errors: EINVAL, ENOMEM, ECUDA. */
+int lddmm_net_input(lddmm_net* net, int nx, int ny, int nz, const float* I0, const float* I1,
+                    float* x);
+/* Warm start: vtilde (device cube float[3][K][K][K][2]) = pi_K(net(input(I0, I1))), the
+ * exact band-limited projection of the predicted (D/2)^3 velocity (K <= D/2). Pass it as
+ * the initial velocity of lddmm_register. Errors: EINVAL, ENOMEM, ECUDA. */
+int lddmm_net_warm_start(lddmm_net* net, int nx, int ny, int nz, const float* I0,
+                         const float* I1, int K, float* vtilde);
+
 /* ---------------------------------------------------------------------- diagnostics */
 
 /* Kernel tracing (no counterpart in the paper; profiling support). The library counts

@@ -40,7 +40,7 @@ def conv3d(x, w, b=None):
     out = np.zeros((cout,) + x.shape[1:])
     for t, (dz, dy, dx) in enumerate(TAPS):
         xs = _shift(x, dz, dy, dx)
-        out += np.einsum("oc,czyx->ozyx", w[:, :, t], xs)
+        out += np.tensordot(w[:, :, t], xs, axes=(1, 0))
     if b is not None:
         out += b[:, None, None, None]
     return out
@@ -50,7 +50,7 @@ def conv3d_dgrad(dout, w):
     """Gradient of sum(dout * conv3d(x, w)) with respect to x."""
     din = np.zeros((w.shape[1],) + dout.shape[1:])
     for t, (dz, dy, dx) in enumerate(TAPS):
-        din += _shift(np.einsum("oc,ozyx->czyx", w[:, :, t], dout), -dz, -dy, -dx)
+        din += _shift(np.tensordot(w[:, :, t].T, dout, axes=(1, 0)), -dz, -dy, -dx)
     return din
 
 
@@ -58,7 +58,7 @@ def conv3d_wgrad(dout, x):
     """Gradient of sum(dout * conv3d(x, w)) with respect to w ([Cout][Cin][27]) and b."""
     dw = np.zeros((dout.shape[0], x.shape[0], 27))
     for t, (dz, dy, dx) in enumerate(TAPS):
-        dw[:, :, t] = np.einsum("ozyx,czyx->oc", dout, _shift(x, dz, dy, dx))
+        dw[:, :, t] = np.tensordot(dout, _shift(x, dz, dy, dx), axes=([1, 2, 3], [1, 2, 3]))
     return dw, dout.sum(axis=(1, 2, 3))
 
 
@@ -111,21 +111,37 @@ def layer_specs(base_channels=16):
             ("d1a", 6 * c, 2 * c), ("d1b", 2 * c, 2 * c), ("out", 2 * c, 3)]
 
 
-def forward(params, x):
+def round_bf16(a):
+    """Round to the nearest bfloat16 value (8 significant bits, ties to even), returned as
+    float64. Written from the format's definition: keep the top 16 bits of the IEEE float32
+    pattern after adding 0x7FFF plus the lowest kept bit."""
+    f = np.ascontiguousarray(np.asarray(a, dtype=np.float32))
+    u = f.view(np.uint32).astype(np.uint64)
+    u = (u + 0x7FFF + ((u >> 16) & 1)) & 0xFFFF0000
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward(params, x, storage=None):
     """Network forward for one sample x [2][D^3] (D divisible by 8). Returns (y, cache):
-    y [3][(D/2)^3], the velocity on the half-resolution grid (no activation on the output)."""
+    y [3][(D/2)^3], the velocity on the half-resolution grid (no activation on the output).
+
+    storage="bf16" models a network that stores its input and every activation it keeps
+    (ReLU outputs, pooled maps; upsampling copies) in bfloat16, each rounded once from the
+    exact value; the output stays unrounded. storage=None is the FP64 network."""
     P = params
     cache = {}
+    R = round_bf16 if storage == "bf16" else (lambda a: a)
 
     def cv(name, inp, act=True):
         pre = conv3d(inp, P[name + ".w"], P[name + ".b"])
         cache[name] = (inp, pre)
-        return relu(pre) if act else pre
+        return R(relu(pre)) if act else pre
 
-    e0 = cv("e0b", cv("e0a", x))                 # D
-    e1 = cv("e1b", cv("e1a", avgpool2(e0)))      # D/2
-    e2 = cv("e2b", cv("e2a", avgpool2(e1)))      # D/4
-    e3 = cv("e3b", cv("e3a", avgpool2(e2)))      # D/8
+    x = R(x)
+    e0 = cv("e0b", cv("e0a", x))                    # D
+    e1 = cv("e1b", cv("e1a", R(avgpool2(e0))))      # D/2
+    e2 = cv("e2b", cv("e2a", R(avgpool2(e1))))      # D/4
+    e3 = cv("e3b", cv("e3a", R(avgpool2(e2))))      # D/8
     d2 = cv("d2b", cv("d2a", np.concatenate([upsample2(e3), e2])))   # D/4
     d1 = cv("d1b", cv("d1a", np.concatenate([upsample2(d2), e1])))   # D/2
     y = cv("out", d1, act=False)

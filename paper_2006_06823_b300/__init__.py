@@ -32,6 +32,7 @@ PREC_FP32, PREC_BF16X3, PREC_FP32_SIMT = 0, 1, 2
 FORWARD, BACKWARD = 1, -1
 STOP_GTOL, STOP_MAXIT, STOP_LINESEARCH = 1, 2, 3
 OPT_GRAPHS, OPT_BLOCK_X = 1, 2
+NET_BF16, NET_FP32 = 0, 1
 
 
 class Params(ctypes.Structure):
@@ -85,6 +86,17 @@ def _declare(lib):
                                       ctypes.POINTER(Report), _I]),
         "lddmm_set_option": (_I, [_P, _I, ctypes.c_long]),
         "lddmm_autotune": (_I, [_P, ctypes.c_char_p, ctypes.POINTER(_I)]),
+        "lddmm_net_create": (_I, [_I, _I, _I, _I, ctypes.c_ulonglong, _P, ctypes.POINTER(_P)]),
+        "lddmm_net_destroy": (_I, [_P]),
+        "lddmm_net_num_params": (ctypes.c_long, [_P]),
+        "lddmm_net_get_params": (_I, [_P, _P]),
+        "lddmm_net_set_params": (_I, [_P, _P]),
+        "lddmm_net_forward": (_I, [_P, _P, _I, _P]),
+        "lddmm_net_gradients": (_I, [_P, _P, _P, _I, _P]),
+        "lddmm_net_train_step": (_I, [_P, _P, _P, _I, ctypes.c_float,
+                                      ctypes.POINTER(_D)]),
+        "lddmm_net_input": (_I, [_P, _I, _I, _I, _P, _P, _P]),
+        "lddmm_net_warm_start": (_I, [_P, _I, _I, _I, _P, _P, _I, _P]),
         "lddmm_launch_count": (ctypes.c_long, []),
         "lddmm_trace_enable": (_I, [_I]),
         "lddmm_trace_reset": (_I, []),
@@ -310,6 +322,83 @@ class Context:
         m = torch.empty(self.shape, dtype=torch.float32, device="cuda") if out is None else out
         _check(load().lddmm_get_warped(self._h, _f32(m)))
         return m
+
+
+# ------------------------------------------------------------------ learned warm start
+
+class Net:
+    """The warm-start encoder-decoder (lddmm_net_*): input ``[B, 2, D, D, D]`` float32
+    (template, reference), output ``[B, 3, D/2, D/2, D/2]`` float32 velocity. Runs on the
+    torch CUDA stream current at construction."""
+
+    def __init__(self, D=64, base_channels=16, batch_max=8, seed=0, storage=NET_BF16):
+        import torch
+        self.D, self.c, self.batch_max, self.storage = D, base_channels, batch_max, storage
+        self._stream = torch.cuda.current_stream()
+        self._h = ctypes.c_void_p()
+        _check(load().lddmm_net_create(D, base_channels, batch_max, storage, seed,
+                                       ctypes.c_void_p(self._stream.cuda_stream),
+                                       ctypes.byref(self._h)))
+        self.num_params = int(load().lddmm_net_num_params(self._h))
+
+    def close(self):
+        if self._h:
+            load().lddmm_net_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        import torch
+        p = torch.empty(self.num_params, dtype=torch.float32, device="cuda")
+        _check(load().lddmm_net_get_params(self._h, _f32(p)))
+        return p
+
+    def set_params(self, p):
+        import torch
+        p = torch.as_tensor(p, dtype=torch.float32).contiguous()
+        if p.numel() != self.num_params:
+            raise ValueError(f"expected {self.num_params} parameters, got {p.numel()}")
+        _check(load().lddmm_net_set_params(self._h, ctypes.c_void_p(p.data_ptr())))
+
+    def forward(self, x, out=None):
+        import torch
+        B, d = x.shape[0], self.D // 2
+        y = torch.empty((B, 3, d, d, d), dtype=torch.float32, device=x.device) if out is None else out
+        _check(load().lddmm_net_forward(self._h, _f32(x), B, _f32(y)))
+        return y
+
+    def gradients(self, x, dy, out=None):
+        import torch
+        g = torch.empty(self.num_params, dtype=torch.float32, device=x.device) if out is None else out
+        _check(load().lddmm_net_gradients(self._h, _f32(x), _f32(dy), x.shape[0], _f32(g)))
+        return g
+
+    def train_step(self, x, target, lr, want_loss=True):
+        loss = ctypes.c_double(0.0)
+        _check(load().lddmm_net_train_step(self._h, _f32(x), _f32(target), x.shape[0],
+                                           float(lr), ctypes.byref(loss) if want_loss else None))
+        return loss.value if want_loss else None
+
+    def input(self, I0, I1, out=None):
+        import torch
+        nz, ny, nx = I0.shape
+        x = torch.empty((2, self.D, self.D, self.D), dtype=torch.float32, device=I0.device) \
+            if out is None else out
+        _check(load().lddmm_net_input(self._h, nx, ny, nz, _f32(I0), _f32(I1), _f32(x)))
+        return x
+
+    def warm_start(self, I0, I1, K, out=None):
+        import torch
+        nz, ny, nx = I0.shape
+        v = torch.empty((3, K, K, K), dtype=torch.complex64, device=I0.device) \
+            if out is None else out
+        _check(load().lddmm_net_warm_start(self._h, nx, ny, nz, _f32(I0), _f32(I1), K, _c64(v)))
+        return v
 
 
 # ------------------------------------------------------------------ tracing

@@ -30,24 +30,47 @@ def _grid(shape):
     return x, y, z
 
 
-def gaussian_blobs(shape=(32, 32, 32), seed=0, n_blobs=8):
-    """Fixed image of the small workload: a clipped sum of isotropic Gaussians.
+def blob_params(shape=(32, 32, 32), seed=0, n_blobs=8):
+    """Random draws of ``gaussian_blobs``: a list of (centre (x, y, z), width, amplitude).
 
     Centres ~ U[8, 24] voxels per axis, widths ~ U[3, 6] voxels, amplitudes ~ U[0.3, 1],
-    all scaled by N/32 on grids other than 32^3. Values clipped to [0, 1]. float64.
-    """
+    scaled by N/32 on grids other than 32^3."""
     g = rng(seed)
     nz, ny, nx = shape
     scale = np.array([nx, ny, nz], dtype=np.float64) / 32.0
-    x, y, z = _grid(shape)
-    img = np.zeros(shape)
+    out = []
     for _ in range(n_blobs):
         c = g.uniform(8.0, 24.0, size=3) * scale
         s = g.uniform(3.0, 6.0) * scale.mean()
         a = g.uniform(0.3, 1.0)
+        out.append((c, s, a))
+    return out
+
+
+def gaussian_blobs(shape=(32, 32, 32), seed=0, n_blobs=8):
+    """Fixed image of the small workload: the sum of the ``blob_params`` Gaussians, clipped
+    to [0, 1]. float64."""
+    x, y, z = _grid(shape)
+    img = np.zeros(shape)
+    for c, s, a in blob_params(shape, seed, n_blobs):
         r2 = (x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2
         img += a * np.exp(-r2 / (2.0 * s * s))
     return np.clip(img, 0.0, 1.0)
+
+
+def gaussian_blobs_device(shape, seed, device, n_blobs=8):
+    """``gaussian_blobs`` evaluated on a torch device in float32 (same random draws), for
+    generating many large phantoms without host work."""
+    import torch
+    nz, ny, nx = shape
+    z = torch.arange(nz, dtype=torch.float32, device=device).view(nz, 1, 1)
+    y = torch.arange(ny, dtype=torch.float32, device=device).view(1, ny, 1)
+    x = torch.arange(nx, dtype=torch.float32, device=device).view(1, 1, nx)
+    img = torch.zeros(shape, dtype=torch.float32, device=device)
+    for c, s, a in blob_params(shape, seed, n_blobs):
+        r2 = (x - float(c[0])) ** 2 + (y - float(c[1])) ** 2 + (z - float(c[2])) ** 2
+        img += float(a) * torch.exp(r2 * float(-1.0 / (2.0 * s * s)))
+    return img.clamp_(0.0, 1.0)
 
 
 ELLIPSOID_SEMI_AXES = (0.42, 0.45, 0.40)          # fractions of (nx, ny, nz)

@@ -52,3 +52,24 @@ def test_null_context_is_rejected():
     rep = L.Report()
     assert lib.lddmm_register(None, ctypes.c_void_p(16), None, ctypes.byref(rep)) == L.EINVAL
     assert lib.lddmm_objective(None, ctypes.c_void_p(16), None, None, None) == L.EINVAL
+
+
+@pytest.mark.parametrize("D,c,B,st", [(48, 4, 1, 0), (4, 4, 1, 0), (256, 4, 1, 0), (64, 0, 1, 0),
+                                      (64, 65, 1, 0), (64, 16, 0, 0), (64, 16, 65, 0),
+                                      (64, 16, 8, 2), (64, 16, 8, -1)])
+def test_net_create_rejects_bad_shapes_before_any_device_work(D, c, B, st):
+    lib = L.load()
+    h = ctypes.c_void_p(123)
+    rc = lib.lddmm_net_create(D, c, B, st, 0, None, ctypes.byref(h))
+    assert rc == L.EINVAL
+    assert h.value is None
+    assert b"net_create" in lib.lddmm_last_error()
+
+
+def test_net_calls_reject_null_network():
+    lib = L.load()
+    assert lib.lddmm_net_forward(None, None, 1, None) == L.EINVAL
+    assert lib.lddmm_net_train_step(None, None, None, 1, 1e-3, None) == L.EINVAL
+    assert lib.lddmm_net_warm_start(None, 64, 64, 64, None, None, 32, None) == L.EINVAL
+    assert lib.lddmm_net_num_params(None) == 0
+    assert lib.lddmm_net_destroy(None) == L.OK

@@ -61,3 +61,38 @@ def test_network_backward_matches_central_differences():
         fd = (np.sum(cnn.forward(Pp, x)[0] * dy) - np.sum(cnn.forward(Pm, x)[0] * dy)) / (2 * h)
         an = np.sum(grads[name] * d)
         assert abs(fd - an) <= 1e-6 * max(1.0, abs(an)), (name, fd, an)
+
+
+def test_round_bf16_exact_values():
+    """bfloat16 keeps 8 significant bits: 1 + 2^-7 is representable, 1 + 2^-8 is the tie
+    between 1 and 1 + 2^-7 and rounds to the even one (1), 1 + 3 * 2^-9 rounds up."""
+    x = np.array([1.0, 1 + 2.0 ** -7, 1 + 2.0 ** -8, 1 + 3 * 2.0 ** -9, 1 + 3 * 2.0 ** -8,
+                  -2.5, 0.0, 3.0e38, 1e-40])
+    want = np.array([1.0, 1 + 2.0 ** -7, 1.0, 1 + 2.0 ** -7, 1 + 2.0 ** -6, -2.5, 0.0,
+                     2.99e38, 1e-40])
+    got = cnn.round_bf16(x)
+    np.testing.assert_array_equal(got[:7], want[:7])
+    assert abs(got[7] - 3.0e38) <= 3.0e38 * 2.0 ** -8          # nearest, not truncated
+    assert abs(got[8] - 1e-40) <= 2.0 ** -133                  # subnormal spacing
+    # rounding error bound u = 2^-8 on random normal values
+    r = np.random.default_rng(0).standard_normal(10000) * 100
+    assert np.max(np.abs(cnn.round_bf16(r) - r) / np.abs(r)) <= 2.0 ** -8
+
+
+def test_bf16_storage_network_is_close_to_exact():
+    """The bf16-storage model differs from the FP64 network by roundings alone; with no
+    roundings possible (every activation already a bfloat16 number) the two agree."""
+    g = np.random.default_rng(6)
+    P = cnn.init_params(g, 2)
+    x = g.random((2, 8, 8, 8))
+    y, _ = cnn.forward(P, x)
+    yb, _ = cnn.forward(P, x, storage="bf16")
+    assert 0 < np.linalg.norm(yb - y) / np.linalg.norm(y) < 0.05
+    # zero weights except biases that are bfloat16 numbers: every activation is exact
+    Z = {k: np.zeros_like(v) for k, v in P.items()}
+    for k in Z:
+        if k.endswith(".b"):
+            Z[k] = cnn.round_bf16(g.random(Z[k].shape))
+    y0, _ = cnn.forward(Z, x)
+    y0b, _ = cnn.forward(Z, x, storage="bf16")
+    np.testing.assert_array_equal(y0, y0b)
