@@ -46,12 +46,15 @@ typedef enum {
 
 enum { LDDMM_V_IMAGE = 1, LDDMM_V_DEFSTATE = 3 };          /* Sec. 2.3.1, Sec. 2.3.3 */
 enum { LDDMM_INTERP_LINEAR = 1, LDDMM_INTERP_CUBIC = 3 };  /* Sec. 3.1, Sec. 4.2 */
-/* Spectral path precision. FP32: FP32-accurate results; the x stages of pi and iota run on
- * the tensor cores as split TF32 products (hi + lo, three products, FP32 accumulation) where
- * the shape allows (K a multiple of 16, nx a multiple of 4, nx <= 256 for iota), else as
- * FP32 SIMT. BF16X3: split BF16 products (lower precision, stated error). FP32_SIMT: never
- * the tensor cores (the plain FP32 reference form). */
-enum { LDDMM_PREC_FP32 = 0, LDDMM_PREC_BF16X3 = 1, LDDMM_PREC_FP32_SIMT = 2 };
+/* Precision form. FP32: FP32-accurate results; the x stages of pi and iota run on the
+ * tensor cores as split TF32 products (hi + lo, three products, FP32 accumulation) where the
+ * shape allows (K a multiple of 16, nx a multiple of 4, nx <= 256 for iota), else as FP32
+ * SIMT. BF16X3: split BF16 products (lower precision, stated error). FP32_SIMT: never the
+ * tensor cores (the plain FP32 reference form). BF16X3_JBF16 (contexts only): BF16X3 plus
+ * BF16 storage of the trajectory Jacobians D iota(u~_j) that the Gauss-Newton Hessian-vector
+ * products read (halving their largest stream); the gradient keeps FP32 Jacobians. */
+enum { LDDMM_PREC_FP32 = 0, LDDMM_PREC_BF16X3 = 1, LDDMM_PREC_FP32_SIMT = 2,
+       LDDMM_PREC_BF16X3_JBF16 = 3 };
 enum { LDDMM_FORWARD = 1, LDDMM_BACKWARD = -1 };           /* SL time direction */
 enum { LDDMM_STOP_GTOL = 1, LDDMM_STOP_MAXIT = 2, LDDMM_STOP_LINESEARCH = 3 };
 
@@ -69,7 +72,7 @@ typedef struct {
     int max_gn;        /* Gauss-Newton updates */
     int max_pcg;       /* PCG iterations per update */
     double gtol;       /* stop when ||g|| / ||g(v=0)|| <= gtol */
-    int precision;     /* LDDMM_PREC_FP32 or LDDMM_PREC_BF16X3 */
+    int precision;     /* LDDMM_PREC_* form */
 } lddmm_params;
 
 /* Outcome of lddmm_register. */

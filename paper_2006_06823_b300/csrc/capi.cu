@@ -59,6 +59,7 @@ struct lddmm_ctx {
     // trajectories
     float2* ut = nullptr;   // DEFSTATE: u~_j, (nt+1) x 3 x K^3
     float* Du = nullptr;    // DEFSTATE: (nt+1) x 9 planes
+    void* Du16 = nullptr;   // DEFSTATE, LDDMM_PREC_BF16X3_JBF16: BF16 copy read by the Hessian
     float* ms = nullptr;    // IMAGE: m_j, (nt+1) planes
     float* Gm = nullptr;    // IMAGE: iota(grad~ pi(m_j)), (nt+1) x 3 planes
     float *G = nullptr, *m1 = nullptr;
@@ -139,21 +140,32 @@ static int validate(const lddmm_params* p) {
         return LDDMM_EINVAL;
     }
     if (p->precision != LDDMM_PREC_FP32 && p->precision != LDDMM_PREC_BF16X3 &&
-        p->precision != LDDMM_PREC_FP32_SIMT) {
-        set_error("precision must be LDDMM_PREC_FP32, LDDMM_PREC_BF16X3 or LDDMM_PREC_FP32_SIMT");
+        p->precision != LDDMM_PREC_FP32_SIMT && p->precision != LDDMM_PREC_BF16X3_JBF16) {
+        set_error("precision must be LDDMM_PREC_FP32, LDDMM_PREC_BF16X3, LDDMM_PREC_FP32_SIMT or "
+                  "LDDMM_PREC_BF16X3_JBF16");
         return LDDMM_EINVAL;
     }
     return LDDMM_OK;
 }
 
 // ------------------------------------------------------------------ small helpers
+// precision of the spectral stages (the JBF16 form uses the BF16 split there)
+static int spec_prec(const lddmm_ctx* c) {
+    return c->p.precision == LDDMM_PREC_BF16X3_JBF16 ? LDDMM_PREC_BF16X3 : c->p.precision;
+}
+static bool jac_bf16(const lddmm_ctx* c) { return c->p.precision == LDDMM_PREC_BF16X3_JBF16; }
 static int project(lddmm_ctx* c, const float* f, int ncomp, float2* out) {
-    return bl_project(c->g, c->tw, f, c->n, ncomp, out, c->s1, c->s2, c->p.precision, c->st);
+    return bl_project(c->g, c->tw, f, c->n, ncomp, out, c->s1, c->s2, spec_prec(c), c->st);
 }
 static int include(lddmm_ctx* c, const float2* cube, int ncomp, float* f, long fstride,
                    int deriv, int bspline) {
     return bl_include(c->g, c->tw, cube, ncomp, f, fstride, deriv, bspline, c->s1, c->s2,
-                      c->p.precision, c->st);
+                      spec_prec(c), c->st);
+}
+// the Jacobian planes of node j, as the Hessian (hess) or the gradient reads them
+static const void* jac(const lddmm_ctx* c, int j, bool hess) {
+    if (hess && jac_bf16(c)) return static_cast<const uint16_t*>(c->Du16) + (long)j * 9 * c->n;
+    return c->Du + (long)j * 9 * c->n;
 }
 static bool cubic(const lddmm_ctx* c) { return c->p.interp == LDDMM_INTERP_CUBIC; }
 
@@ -276,6 +288,7 @@ static int ensure_traj(lddmm_ctx* c) {
             for (int b = 0; b < 3; ++b)
                 TRY(include(c, c->ut + (long)j * 3 * c->kc, 3, c->Du + (long)j * 9 * n + b * n,
                             3 * n, b, 0));
+        if (jac_bf16(c)) TRY(to_bf16(c->Du, c->Du16, (long)(c->p.nt + 1) * 9 * n, c->st));
     } else {
         float2* mt = c->cv[lddmm_ctx::C_T1];
         for (int j = 0; j <= c->p.nt; ++j) {
@@ -291,7 +304,8 @@ static int ensure_traj(lddmm_ctx* c) {
 // ------------------------------------------------------------------ adjoint sweeps
 // DEFSTATE (Eqs. 35, 37; Table 1 rows 4, 8), backward from rho(1) given spatially in `rho1`:
 // out = wL L~ base + sum_j w_j (rho~_j - pi((D iota u~_j)^T iota(rho~_j))).
-static int adjoint_defstate(lddmm_ctx* c, const float* rho1, const float2* base, float2* out) {
+static int adjoint_defstate(lddmm_ctx* c, const float* rho1, const float2* base, float2* out,
+                            bool hess) {
     const long n = c->n, kc3 = 3 * c->kc;
     const int nt = c->p.nt;
     float2* rt = c->cv[lddmm_ctx::C_T1];     // rho~_j
@@ -299,7 +313,8 @@ static int adjoint_defstate(lddmm_ctx* c, const float* rho1, const float2* base,
     TRY(project(c, rho1, 3, rt));
     TRY(cube_axpby(rsum, (float)trap_w(c, nt), rt, 0.f, nullptr, kc3, c->st));
     TRY(include(c, rt, 3, c->fc, n, -1, 0));  // iota(rho~_nt) values
-    TRY(accum_JT(c->g, c->Du + (long)nt * 9 * n, c->fc, (float)trap_w(c, nt), c->acc, 1, c->st));
+    TRY(accum_JT(c->g, jac(c, nt, hess), jac_bf16(c) && hess, c->fc, (float)trap_w(c, nt), c->acc, 1,
+                 c->st));
     for (int j = nt - 1; j >= 0; --j) {
         const float* src = c->fc;
         if (cubic(c)) {
@@ -310,7 +325,8 @@ static int adjoint_defstate(lddmm_ctx* c, const float* rho1, const float2* base,
         TRY(project(c, c->fd, 3, rt));
         TRY(cube_axpby(rsum, 1.f, rsum, (float)trap_w(c, j), rt, kc3, c->st));
         TRY(include(c, rt, 3, c->fc, n, -1, 0));
-        TRY(accum_JT(c->g, c->Du + (long)j * 9 * n, c->fc, (float)trap_w(c, j), c->acc, 0, c->st));
+        TRY(accum_JT(c->g, jac(c, j, hess), jac_bf16(c) && hess, c->fc, (float)trap_w(c, j), c->acc, 0,
+                     c->st));
     }
     c->solves++;
     float2* pacc = c->cv[lddmm_ctx::C_T0];
@@ -371,7 +387,7 @@ static int gradient_impl(lddmm_ctx* c, const float2* vt, bool known_same, float2
     float2* cur = c->cv[lddmm_ctx::C_CUR];
     if (c->p.variant == LDDMM_V_DEFSTATE) {
         TRY(data_term(c, c->fb));
-        TRY(adjoint_defstate(c, c->fb, cur, g));
+        TRY(adjoint_defstate(c, c->fb, cur, g, false));
     } else {
         TRY(data_term(c, nullptr));
         TRY(gradient_image_adjoint(c, cur, g));
@@ -397,7 +413,7 @@ static int hessian_impl(lddmm_ctx* c, const float2* dvt, float2* out) {
         float2* dut = c->cv[lddmm_ctx::C_T1];
         float* Fold = c->fa;
         float* Fnew = c->fd;
-        TRY(defstate_rhs(c->g, c->Du, c->dvsp, Fold, c->st));
+        TRY(defstate_rhs(c->g, jac(c, 0, true), jac_bf16(c), c->dvsp, Fold, c->st));
         LDDMM_CUDA(cudaMemsetAsync(dut, 0, kc3 * sizeof(float2), c->st));
         for (int j = 0; j < nt; ++j) {
             TRY(include(c, dut, 3, c->fb, n, -1, cubic(c)));
@@ -406,7 +422,7 @@ static int hessian_impl(lddmm_ctx* c, const float2* dvt, float2* out) {
                 TRY(bspline_prefilter(c->g, Fold, 3, c->acc, c->st));
                 Fsrc = c->acc;
             }
-            TRY(sl_inc_defstate(c->sl, c->fb, c->Df, Fsrc, c->Du + (long)(j + 1) * 9 * n, c->dvsp,
+            TRY(sl_inc_defstate(c->sl, c->fb, c->Df, Fsrc, jac(c, j + 1, true), jac_bf16(c), c->dvsp,
                                 c->dt, c->fc, Fnew, c->st));
             TRY(project(c, c->fc, 3, dut));
             std::swap(Fold, Fnew);
@@ -415,7 +431,7 @@ static int hessian_impl(lddmm_ctx* c, const float2* dvt, float2* out) {
         // drho(1) = pi(-(2/sigma2) dm1 G), dm1 = -G . iota(du~(1))
         TRY(include(c, dut, 3, c->fa, n, -1, 0));
         TRY(defstate_drho1(c->g, c->G, c->fa, c->p.sigma2, c->fb, c->st));
-        return adjoint_defstate(c, c->fb, dvt, out);
+        return adjoint_defstate(c, c->fb, dvt, out, true);
     }
     // IMAGE: incremental state D~_t dm~ = -grad~ m~ * dv~ (Eq. 19; Table 1 row 5)
     float2* dmt = c->cv[lddmm_ctx::C_T1];
@@ -700,6 +716,7 @@ static int ctx_alloc(lddmm_ctx* c) {
         TRY(dalloc_t(c, &c->W, 3 * n));
         TRY(dalloc_t(c, &c->ut, (size_t)(nt + 1) * kc3));
         TRY(dalloc_t(c, &c->Du, (size_t)(nt + 1) * 9 * n));
+        if (jac_bf16(c)) TRY(dalloc_t(c, reinterpret_cast<uint16_t**>(&c->Du16), (size_t)(nt + 1) * 9 * n));
         TRY(dalloc_t(c, &c->G, 3 * n));
         TRY(dalloc_t(c, &c->m1, n));
     } else {
@@ -885,11 +902,22 @@ static int check_grid(int nx, int ny, int nz) {
     return LDDMM_OK;
 }
 
+// precision forms accepted by the stand-alone spectral operators
+static int check_spectral_precision(int precision) {
+    if (precision != LDDMM_PREC_FP32 && precision != LDDMM_PREC_BF16X3 &&
+        precision != LDDMM_PREC_FP32_SIMT) {
+        set_error("spectral precision must be LDDMM_PREC_FP32, LDDMM_PREC_BF16X3 or LDDMM_PREC_FP32_SIMT");
+        return LDDMM_EINVAL;
+    }
+    return LDDMM_OK;
+}
+
 extern "C" {
 
 int lddmm_bl_project(int nx, int ny, int nz, int K, const float* f, int ncomp, float* c,
                      int precision, void* stream) {
     TRY(check_grid(nx, ny, nz));
+    TRY(check_spectral_precision(precision));
     if (!f || !c || ncomp < 1) { set_error("bl_project: null pointer or ncomp < 1"); return LDDMM_EINVAL; }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     Grid g{nx, ny, nz};
@@ -908,6 +936,7 @@ int lddmm_bl_project(int nx, int ny, int nz, int K, const float* f, int ncomp, f
 int lddmm_bl_include(int nx, int ny, int nz, int K, const float* c, int ncomp, float* f,
                      int deriv_axis, int bspline, int precision, void* stream) {
     TRY(check_grid(nx, ny, nz));
+    TRY(check_spectral_precision(precision));
     if (!f || !c || ncomp < 1) { set_error("bl_include: null pointer or ncomp < 1"); return LDDMM_EINVAL; }
     if (deriv_axis < -1 || deriv_axis > 2) { set_error("bl_include: deriv_axis must be -1..2"); return LDDMM_EINVAL; }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1094,7 +1123,8 @@ int lddmm_autotune(lddmm_ctx* c, const char* cache_path, int* block_x_out) {
             LDDMM_CUDA(cudaEventRecord(e0, c->st));
             rc = sl_gather_scale(a, c->fa, c->Df, c->gam, 3, c->fb, c->st);
             if (rc == LDDMM_OK && c->p.variant == LDDMM_V_DEFSTATE && c->Du)
-                rc = sl_inc_defstate(a, c->fa, c->Df, c->fb, c->Du, c->dvsp, c->dt, c->fc, c->fd, c->st);
+                rc = sl_inc_defstate(a, c->fa, c->Df, c->fb, jac(c, 0, true), jac_bf16(c), c->dvsp, c->dt,
+                                     c->fc, c->fd, c->st);
             LDDMM_CUDA(cudaEventRecord(e1, c->st));
             LDDMM_CUDA(cudaEventSynchronize(e1));
             if (rc) break;

@@ -186,14 +186,17 @@ k_conv_wgrad(const float* __restrict__ dout, int cout, long dout_bstride,
     }
 }
 
-// db[co] += sum over b, v of dout[b][co][v]   (one CTA per channel)
+// db[co] += sum over b, v of dout[b][co][v]; grid (cout, slices), one FP32 atomic per CTA
 __global__ void __launch_bounds__(256)
 k_bias_grad(const float* __restrict__ dout, long nv, int B, long bstride, float* __restrict__ db) {
     const int co = blockIdx.x;
+    const long total = nv * B;
+    const long chunk = (total + gridDim.y - 1) / gridDim.y;
+    const long s0 = (long)blockIdx.y * chunk, s1 = min(total, s0 + chunk);
     float s = 0.f;
-    for (int b = 0; b < B; ++b) {
-        const float* p = dout + (long)b * bstride + (long)co * nv;
-        for (long i = threadIdx.x; i < nv; i += blockDim.x) s += p[i];
+    for (long i = s0 + threadIdx.x; i < s1; i += blockDim.x) {
+        const long b = i / nv;
+        s += dout[b * bstride + (long)co * nv + (i - b * nv)];
     }
     __shared__ float red[256];
     red[threadIdx.x] = s;
@@ -202,7 +205,7 @@ k_bias_grad(const float* __restrict__ dout, long nv, int B, long bstride, float*
         if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
         __syncthreads();
     }
-    if (threadIdx.x == 0) db[co] += red[0];
+    if (threadIdx.x == 0) atomicAdd(db + co, red[0]);
 }
 
 // storage copies of a layer's weights: Wb = W, Wt = transposed and tap-flipped W
@@ -439,7 +442,8 @@ struct Net {
         LDDMM_CHECK_LAUNCH();
         {
             KTRACE("cnn_bias_grad", n->st, (double)B * cout * vol(D) * 4.0, (double)B * cout * vol(D));
-            k_bias_grad<<<cout, 256, 0, n->st>>>(dout, vol(D), B, dout_bs, db);
+            const int slices = (int)std::max(1L, std::min((long)cdiv_i(2 * 148, cout), total / 4096));
+            k_bias_grad<<<dim3(cout, slices), 256, 0, n->st>>>(dout, vol(D), B, dout_bs, db);
         }
         LDDMM_CHECK_LAUNCH();
         return LDDMM_OK;

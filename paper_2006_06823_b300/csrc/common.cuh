@@ -141,17 +141,21 @@ int sl_warp_image(const SLArgs& a, const float* I0src, const float* u1, const fl
                   double* partials, cudaStream_t st);
 // incremental deformation state step: Fnew_a = dv_a - sum_b Du[a*3+b] dv_b;
 // out = U o X + dt/2 (Fold o X + Fnew)
+// Du: the 9 Jacobian planes of one node, FP32 or (du_bf16) BF16
 int sl_inc_defstate(const SLArgs& a, const float* U, const float* D, const float* Fold,
-                    const float* Du, const float* dv, double dt, float* out, float* Fnew,
-                    cudaStream_t st);
+                    const void* Du, bool du_bf16, const float* dv, double dt, float* out,
+                    float* Fnew, cudaStream_t st);
 // Fnew_a = dv_a - sum_b Du[a*3+b] dv_b (the first node)
-int defstate_rhs(const Grid& g, const float* Du, const float* dv, float* F, cudaStream_t st);
+int defstate_rhs(const Grid& g, const void* Du, bool du_bf16, const float* dv, float* F,
+                 cudaStream_t st);
 // drho = -(2/sigma2) dm1 G with dm1 = -G . du1
 int defstate_drho1(const Grid& g, const float* G, const float* du1, double sigma2, float* drho,
                    cudaStream_t st);
 // acc_b (+)= w sum_a Du[a*3+b] R_a   (init != 0 overwrites)
-int accum_JT(const Grid& g, const float* Du, const float* R, float w, float* acc, int init,
-             cudaStream_t st);
+int accum_JT(const Grid& g, const void* Du, bool du_bf16, const float* R, float w, float* acc,
+             int init, cudaStream_t st);
+// out[i] = bf16(in[i]), i < n (round to nearest even)
+int to_bf16(const float* in, void* out, long n, cudaStream_t st);
 // x_out = a * x (n floats)
 int scale_field(float* out, const float* in, float a, long n, cudaStream_t st);
 // partial sums over (a - b)^2 into kReduceBlocks doubles, then final into out

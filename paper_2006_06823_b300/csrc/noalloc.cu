@@ -72,6 +72,12 @@ extern "C" int lddmm_bl_project_noalloc(int nx, int ny, int nz, int K, const flo
         set_error("bl_project_noalloc: need even 4 <= K <= min(64, nx, ny, nz)");
         return LDDMM_EINVAL;
     }
+    if (precision != LDDMM_PREC_FP32 && precision != LDDMM_PREC_BF16X3 &&
+        precision != LDDMM_PREC_FP32_SIMT) {
+        set_error("bl_project_noalloc: precision must be LDDMM_PREC_FP32, LDDMM_PREC_BF16X3 or "
+                  "LDDMM_PREC_FP32_SIMT");
+        return LDDMM_EINVAL;
+    }
     const Grid g{nx, ny, nz};
     const long kh = K / 2;
     // stage X output and z-block partials share s1; stage Y output in s2

@@ -8,6 +8,8 @@
 // are clamped to +-2^20 voxels before use, so non-finite or huge inputs can never address
 // memory outside the field.
 #include "common.cuh"
+
+#include <cuda_bf16.h>
 #include "lddmm.h"
 
 namespace lddmm {
@@ -489,11 +491,14 @@ int sl_warp_image(const SLArgs& a, const float* I0src, const float* u1, const fl
 }
 
 // ---------------------------------------------------------------- incremental state
+__device__ __forceinline__ float ldj(const float* p) { return *p; }
+__device__ __forceinline__ float ldj(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+
 // D~_t du~ = dv~ - D~u~ * dv~ (Table 1 row 7): F = dv - (Du) dv, Heun along X.
-template <int IP>
+template <int IP, typename TJ>
 __global__ void __launch_bounds__(256, IP == 3 ? 2 : 3)
 k_inc_defstate(Grid g, const float* __restrict__ U, const float* __restrict__ D,
-                               const float* __restrict__ Fold, const float* __restrict__ Du,
+                               const float* __restrict__ Fold, const TJ* __restrict__ Du,
                                const float* __restrict__ dv, float dt, float* __restrict__ out,
                                float* __restrict__ Fnew) {
     VOXEL_PROLOGUE
@@ -501,7 +506,8 @@ k_inc_defstate(Grid g, const float* __restrict__ U, const float* __restrict__ D,
     float F[3];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        float j0 = Du[(3 * c + 0) * n + i], j1 = Du[(3 * c + 1) * n + i], j2 = Du[(3 * c + 2) * n + i];
+        float j0 = ldj(Du + (3 * c + 0) * n + i), j1 = ldj(Du + (3 * c + 1) * n + i),
+              j2 = ldj(Du + (3 * c + 2) * n + i);
         F[c] = (c == 0 ? w0 : c == 1 ? w1 : w2) - (j0 * w0 + j1 * w1 + j2 * w2);
     }
     Interp<IP> it(g, x, y, z, D[i], D[n + i], D[2 * n + i]);
@@ -513,35 +519,63 @@ k_inc_defstate(Grid g, const float* __restrict__ U, const float* __restrict__ D,
 }
 
 int sl_inc_defstate(const SLArgs& a, const float* U, const float* D, const float* Fold,
-                    const float* Du, const float* dv, double dt, float* out, float* Fnew,
-                    cudaStream_t st) {
-    KTRACE(a.interp == 3 ? "sl_inc_defstate_cubic" : "sl_inc_defstate", st, 108.0 * a.g.ntot(), 0);
-    if (a.interp == 3)
-        k_inc_defstate<3><<<VOX_LAUNCH(a), 0, st>>>(a.g, U, D, Fold, Du, dv, (float)dt,
-                                                               out, Fnew);
-    else
-        k_inc_defstate<1><<<VOX_LAUNCH(a), 0, st>>>(a.g, U, D, Fold, Du, dv, (float)dt,
-                                                               out, Fnew);
+                    const void* Du, bool du_bf16, const float* dv, double dt, float* out,
+                    float* Fnew, cudaStream_t st) {
+    const double bytes = (du_bf16 ? 90.0 : 108.0) * a.g.ntot();
+    const char* name = a.interp == 3 ? (du_bf16 ? "sl_inc_defstate_cubic_jbf16" : "sl_inc_defstate_cubic")
+                                     : (du_bf16 ? "sl_inc_defstate_jbf16" : "sl_inc_defstate");
+    KTRACE(name, st, bytes, 0);
+    const auto* j32 = static_cast<const float*>(Du);
+    const auto* j16 = static_cast<const __nv_bfloat16*>(Du);
+    if (a.interp == 3) {
+        if (du_bf16)
+            k_inc_defstate<3, __nv_bfloat16><<<VOX_LAUNCH(a), 0, st>>>(a.g, U, D, Fold, j16, dv, (float)dt, out, Fnew);
+        else
+            k_inc_defstate<3, float><<<VOX_LAUNCH(a), 0, st>>>(a.g, U, D, Fold, j32, dv, (float)dt, out, Fnew);
+    } else {
+        if (du_bf16)
+            k_inc_defstate<1, __nv_bfloat16><<<VOX_LAUNCH(a), 0, st>>>(a.g, U, D, Fold, j16, dv, (float)dt, out, Fnew);
+        else
+            k_inc_defstate<1, float><<<VOX_LAUNCH(a), 0, st>>>(a.g, U, D, Fold, j32, dv, (float)dt, out, Fnew);
+    }
     LDDMM_CHECK_LAUNCH();
     return LDDMM_OK;
 }
 
-__global__ void k_defstate_rhs(long n, const float* __restrict__ Du, const float* __restrict__ dv,
+template <typename TJ>
+__global__ void k_defstate_rhs(long n, const TJ* __restrict__ Du, const float* __restrict__ dv,
                                float* __restrict__ F) {
     long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float w0 = dv[i], w1 = dv[n + i], w2 = dv[2 * n + i];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        float j0 = Du[(3 * c + 0) * n + i], j1 = Du[(3 * c + 1) * n + i], j2 = Du[(3 * c + 2) * n + i];
+        float j0 = ldj(Du + (3 * c + 0) * n + i), j1 = ldj(Du + (3 * c + 1) * n + i),
+              j2 = ldj(Du + (3 * c + 2) * n + i);
         F[c * n + i] = (c == 0 ? w0 : c == 1 ? w1 : w2) - (j0 * w0 + j1 * w1 + j2 * w2);
     }
 }
 
-int defstate_rhs(const Grid& g, const float* Du, const float* dv, float* F, cudaStream_t st) {
+int defstate_rhs(const Grid& g, const void* Du, bool du_bf16, const float* dv, float* F,
+                 cudaStream_t st) {
     long n = g.ntot();
-    KTRACE("defstate_rhs", st, 60.0 * n, 24.0 * n);
-    k_defstate_rhs<<<cdiv(n, 256), 256, 0, st>>>(n, Du, dv, F);
+    KTRACE("defstate_rhs", st, (du_bf16 ? 42.0 : 60.0) * n, 24.0 * n);
+    if (du_bf16)
+        k_defstate_rhs<<<cdiv(n, 256), 256, 0, st>>>(n, static_cast<const __nv_bfloat16*>(Du), dv, F);
+    else
+        k_defstate_rhs<<<cdiv(n, 256), 256, 0, st>>>(n, static_cast<const float*>(Du), dv, F);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+__global__ void k_to_bf16(const float* __restrict__ in, __nv_bfloat16* __restrict__ out, long n) {
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
+        out[i] = __float2bfloat16_rn(in[i]);
+}
+
+int to_bf16(const float* in, void* out, long n, cudaStream_t st) {
+    KTRACE("to_bf16", st, 6.0 * n, 0);
+    k_to_bf16<<<(int)std::min<long>(cdiv(n, 256), 16 * 148), 256, 0, st>>>(in, static_cast<__nv_bfloat16*>(out), n);
     LDDMM_CHECK_LAUNCH();
     return LDDMM_OK;
 }
@@ -568,23 +602,28 @@ int defstate_drho1(const Grid& g, const float* G, const float* du1, double sigma
 }
 
 // acc_b (+)= w sum_a Du[a*3+b] R_a   ((D u)^T R, the D~u~ * rho~ term before projection)
-__global__ void k_accum_JT(long n, const float* __restrict__ Du, const float* __restrict__ R,
+template <typename TJ>
+__global__ void k_accum_JT(long n, const TJ* __restrict__ Du, const float* __restrict__ R,
                            float w, float* __restrict__ acc, int init) {
     long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float r0 = R[i], r1 = R[n + i], r2 = R[2 * n + i];
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-        float s = Du[(0 + b) * n + i] * r0 + Du[(3 + b) * n + i] * r1 + Du[(6 + b) * n + i] * r2;
+        float s = ldj(Du + (0 + b) * n + i) * r0 + ldj(Du + (3 + b) * n + i) * r1 +
+                  ldj(Du + (6 + b) * n + i) * r2;
         acc[b * n + i] = init ? w * s : fmaf(w, s, acc[b * n + i]);
     }
 }
 
-int accum_JT(const Grid& g, const float* Du, const float* R, float w, float* acc, int init,
-             cudaStream_t st) {
+int accum_JT(const Grid& g, const void* Du, bool du_bf16, const float* R, float w, float* acc,
+             int init, cudaStream_t st) {
     long n = g.ntot();
-    KTRACE("accum_JT", st, n * (60.0 + (init ? 0.0 : 12.0)), 21.0 * n);
-    k_accum_JT<<<cdiv(n, 256), 256, 0, st>>>(n, Du, R, w, acc, init);
+    KTRACE("accum_JT", st, n * ((du_bf16 ? 42.0 : 60.0) + (init ? 0.0 : 12.0)), 21.0 * n);
+    if (du_bf16)
+        k_accum_JT<<<cdiv(n, 256), 256, 0, st>>>(n, static_cast<const __nv_bfloat16*>(Du), R, w, acc, init);
+    else
+        k_accum_JT<<<cdiv(n, 256), 256, 0, st>>>(n, static_cast<const float*>(Du), R, w, acc, init);
     LDDMM_CHECK_LAUNCH();
     return LDDMM_OK;
 }

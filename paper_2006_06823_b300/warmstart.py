@@ -11,8 +11,8 @@ Workload (the small workload's recipe scaled to the paper-scale grid): the fixed
 the Gaussian-blob phantom (``synth.gaussian_blobs`` scaled to the grid), the moving image
 is the fixed one transported by the library for nt steps along a random stationary
 band-limited velocity (8^3 generated modes, decay (1 + |k|^2)^-2) scaled to a maximum
-displacement of 3 * n / 32 voxels (n the smallest extent). Every pair comes from one
-seed. Targets are iota_{(D/2)^3}(v~_GN), the solver's solution on the network's output
+displacement of 8 voxels (the paper-scale workload's displacement). Every pair comes from
+one seed. Targets are iota_{(D/2)^3}(v~_GN), the solver's solution on the network's output
 grid (exact: the band K <= D/2 fits that grid), inputs the band-limited resampling of the
 pair to D^3.
 
@@ -40,6 +40,8 @@ NT = 10
 SOLVER = dict(nt=NT, variant=L.V_DEFSTATE, interp=L.INTERP_LINEAR, alpha=0.0025, s=2,
               sigma2=0.01, max_gn=10, max_pcg=20, gtol=1e-3)
 NET_D, NET_C = 64, 16
+MAX_VOX = 8.0          # maximum displacement of the generating velocity, voxels
+EVAL_MAX_GN = 30       # GN cap of the evaluation (both arms), so both can reach gtol
 TRAIN_SEED0, EVAL_SEED0 = 100_000, 900_000
 WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights",
                        "warmstart_d64_c16.npz")
@@ -47,11 +49,12 @@ WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights",
 
 def make_pair(seed, shape=SHAPE, K=K, nt=NT, max_vox=None):
     """(I0, I1) float32 device images of one seed: I1 = blobs, I0 = I1 transported along
-    the seed's random band-limited velocity (library kernels)."""
+    the seed's random band-limited velocity (library kernels), scaled to a maximum
+    displacement of max_vox voxels (default MAX_VOX)."""
     import torch
     nz, ny, nx = shape
     if max_vox is None:
-        max_vox = 3.0 * min(shape) / 32.0
+        max_vox = MAX_VOX
     I1 = synth.gaussian_blobs_device(shape, seed, "cuda")
     vt = synth.random_velocity_coeffs(K, 8, seed + 1)
     vt_d = torch.as_tensor(vt.astype(np.complex64), device="cuda")
@@ -97,34 +100,64 @@ def _bias_mask(net):
     return m
 
 
-def generate(seeds, net, log=print):
-    """Registers every seed's pair from a cold start; returns (X, T, reports) with X the
-    network inputs [N, 2, D^3] and T the targets [N, 3, (D/2)^3] on the device."""
+def generate(seeds, net, max_vox=None, contexts=4, log=print):
+    """Registers every seed's pair from a cold start (``contexts`` pairs at a time through
+    lddmm_register_batch, one stream each); returns (X, T, reports) with X the network
+    inputs [N, 2, D^3] and T the targets [N, 3, (D/2)^3] on the device."""
     import torch
     nz, ny, nx = SHAPE
     D, d = net.D, net.D // 2
     X = torch.empty((len(seeds), 2, D, D, D), dtype=torch.float32, device="cuda")
     T = torch.empty((len(seeds), 3, d, d, d), dtype=torch.float32, device="cuda")
-    ctx = L.Context(nx, ny, nz, K, **SOLVER)
+    streams = [torch.cuda.Stream() for _ in range(contexts)]
+    ctxs = []
+    for st in streams:
+        with torch.cuda.stream(st):
+            ctxs.append(L.Context(nx, ny, nz, K, **SOLVER))
     reps = []
     t0 = time.time()
-    for i, s in enumerate(seeds):
-        I0, I1 = make_pair(s)
-        ctx.set_images(I0, I1)
-        v, rep = ctx.register()
-        net.input(I0, I1, out=X[i])
-        L.bl_include(v, (d, d, d), out=T[i])
-        reps.append(rep)
-        if (i + 1) % 50 == 0 or i + 1 == len(seeds):
-            log(f"  generated {i + 1}/{len(seeds)} pairs, {time.time() - t0:.0f} s, "
-                f"mean GN {np.mean([r['gn_iters'] for r in reps]):.2f}")
-    ctx.close()
+    for a in range(0, len(seeds), contexts):
+        chunk = seeds[a:a + contexts]
+        pairs = [make_pair(s, max_vox=max_vox) for s in chunk]
+        torch.cuda.synchronize()
+        for c, (I0, I1) in zip(ctxs, pairs):
+            c.set_images(I0, I1)
+        vs = [c.zeros_cube() for c in ctxs[:len(chunk)]]
+        torch.cuda.synchronize()
+        reps += L.register_batch(ctxs[:len(chunk)], vs, max_threads=contexts)
+        for j, ((I0, I1), v) in enumerate(zip(pairs, vs)):
+            net.input(I0, I1, out=X[a + j])
+            L.bl_include(v, (d, d, d), out=T[a + j])
+        done = a + len(chunk)
+        if done % 100 < contexts or done == len(seeds):
+            log(f"  generated {done}/{len(seeds)} pairs, {time.time() - t0:.0f} s, "
+                f"mean GN {np.mean([r['gn_iters'] for r in reps]):.2f}, reached gtol "
+                f"{np.mean([r['grad_rel_l2'] <= SOLVER['gtol'] for r in reps]):.2f}")
+    torch.cuda.synchronize()
+    for c in ctxs:
+        c.close()
     return X, T, reps
 
 
-def train(net, X, T, epochs=30, batch=8, lr=1e-3, lr_min=1e-5, seed=0, log=print):
+def reflect(X, T, axes):
+    """The pairs and targets mirrored through the periodic domain's origin along the given
+    axes (0 = x, 1 = y, 2 = z): f(x) -> f(-x mod n), and the mirrored velocity component
+    changes sign. The registration problem is invariant under these reflections (isotropic
+    regulariser, symmetric band, reflection-symmetric interpolation), so a mirrored pair's
+    solution is the mirrored solution."""
+    import torch
+    for a in axes:
+        dim = X.dim() - 1 - a
+        X = torch.roll(torch.flip(X, [dim]), 1, dim)
+        T = torch.roll(torch.flip(T, [dim]), 1, dim)
+        T[:, a] = -T[:, a]
+    return X.contiguous(), T.contiguous()
+
+
+def train(net, X, T, epochs=30, batch=8, lr=1e-3, lr_min=1e-5, seed=0, augment=True, log=print):
     """Adam on contiguous mini-batches of (X, T) with a cosine learning-rate decay; the
-    batch windows move by a random offset each epoch."""
+    batch windows move by a random offset each epoch, and each batch is mirrored along a
+    random subset of the axes (augment)."""
     N = X.shape[0]
     g = synth.rng(seed)
     nb = N // batch
@@ -133,13 +166,17 @@ def train(net, X, T, epochs=30, batch=8, lr=1e-3, lr_min=1e-5, seed=0, log=print
     step = 0
     t0 = time.time()
     for ep in range(epochs):
-        shift = int(g.integers(0, batch)) if N > nb * batch else 0
+        shift = int(g.integers(0, N - nb * batch + 1))
         order = g.permutation(nb)
         losses = []
         for j in order:
             a = shift + j * batch
             cur = lr_min + 0.5 * (lr - lr_min) * (1 + math.cos(math.pi * step / max(total, 1)))
-            losses.append(net.train_step(X[a:a + batch], T[a:a + batch], cur))
+            xb, tb = X[a:a + batch], T[a:a + batch]
+            if augment:
+                r = int(g.integers(0, 8))
+                xb, tb = reflect(xb, tb, [ax for ax in range(3) if r >> ax & 1])
+            losses.append(net.train_step(xb, tb, cur))
             step += 1
         curve.append(float(np.mean(losses)))
         log(f"  epoch {ep + 1}/{epochs}: loss {curve[-1]:.4e} ({time.time() - t0:.0f} s)")
@@ -158,19 +195,20 @@ def prediction_error(net, X, T, batch=8):
     return errs
 
 
-def evaluate(net, seeds, log=print):
-    """Cold vs warm registrations of the seeds' pairs (wall time with device sync)."""
+def evaluate(net, seeds, max_vox=None, max_gn=None, log=print):
+    """Cold vs warm registrations of the seeds' pairs (wall time with device sync); both
+    arms stop at the same relative residual gtol or after max_gn GN iterations."""
     import torch
     nz, ny, nx = SHAPE
-    ctx = L.Context(nx, ny, nz, K, **SOLVER)
+    ctx = L.Context(nx, ny, nz, K, **dict(SOLVER, max_gn=max_gn or SOLVER["max_gn"]))
     # one untimed warm-up of both paths
-    I0, I1 = make_pair(seeds[0])
+    I0, I1 = make_pair(seeds[0], max_vox=max_vox)
     ctx.set_images(I0, I1)
     ctx.register()
     ctx.register(net.warm_start(I0, I1, K))
     rows = []
     for i, s in enumerate(seeds):
-        I0, I1 = make_pair(s)
+        I0, I1 = make_pair(s, max_vox=max_vox)
         ctx.set_images(I0, I1)
         torch.cuda.synchronize()
         t = time.perf_counter()
@@ -230,6 +268,10 @@ def main(argv=None):
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--out", default=".")
     ap.add_argument("--init", default=None, help="start from saved weights")
+    ap.add_argument("--max-vox", type=float, default=MAX_VOX,
+                    help="maximum displacement of the generating velocity (voxels)")
+    ap.add_argument("--eval-max-gn", type=int, default=EVAL_MAX_GN)
+    ap.add_argument("--contexts", type=int, default=4)
     args = ap.parse_args(argv)
     import torch
     torch.cuda.set_device(0)
@@ -242,7 +284,7 @@ def main(argv=None):
     train_seeds = [TRAIN_SEED0 + 2 * i for i in range(args.train_pairs)]
     eval_seeds = [EVAL_SEED0 + 2 * i for i in range(args.eval_pairs)]
     t = time.time()
-    X, T, reps = generate(train_seeds, net, log)
+    X, T, reps = generate(train_seeds, net, max_vox=args.max_vox, contexts=args.contexts, log=log)
     t_gen = time.time() - t
     n_val = max(1, len(train_seeds) // 20)
     t = time.time()
@@ -258,7 +300,9 @@ def main(argv=None):
                    "train_reached_gtol": float(np.mean([r["grad_rel_l2"] <= SOLVER["gtol"] for r in reps]))},
                   f, indent=1)
     del X, T
-    rows, summary = evaluate(net, eval_seeds, log)
+    rows, summary = evaluate(net, eval_seeds, max_vox=args.max_vox, max_gn=args.eval_max_gn, log=log)
+    summary.update({"max_vox": args.max_vox, "eval_max_gn": args.eval_max_gn,
+                    "train_pairs": len(train_seeds) - n_val, "epochs": args.epochs})
     with open(os.path.join(args.out, "warmstart_eval.json"), "w") as f:
         json.dump({"summary": summary, "pairs": rows}, f, indent=1)
     log(json.dumps(summary, indent=1))

@@ -47,6 +47,18 @@ def test_standalone_calls_reject_bad_shapes_before_any_device_work():
     assert lib.lddmm_destroy(None) == L.OK
 
 
+@pytest.mark.parametrize("prec", [3, 7, -1])
+def test_standalone_spectral_calls_reject_unknown_precision(prec):
+    """The stand-alone operators take FP32, BF16X3 or FP32_SIMT (BF16X3_JBF16 is a context
+    form); anything else is EINVAL before any device work."""
+    lib = L.load()
+    p = ctypes.c_void_p(256)
+    assert lib.lddmm_bl_project(16, 16, 16, 8, p, 1, p, prec, None) == L.EINVAL
+    assert lib.lddmm_bl_include(16, 16, 16, 8, p, 1, p, -1, 0, prec, None) == L.EINVAL
+    assert lib.lddmm_bl_project_noalloc(16, 16, 16, 8, p, 1, p, prec, None) == L.EINVAL
+    assert b"precision" in lib.lddmm_last_error()
+
+
 def test_null_context_is_rejected():
     lib = L.load()
     rep = L.Report()

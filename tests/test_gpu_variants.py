@@ -65,6 +65,26 @@ def test_objective_gradient_hessian_match_oracle(shape, K, variant, order):
         assert rel_l2(host(Hg), Hdv) < 1e-4
 
 
+@pytest.mark.parametrize("shape,K,order", [((16, 16, 16), 8, 1), ((20, 24, 28), 10, 1),
+                                           ((16, 16, 16), 8, 3)])
+def test_bf16_jacobian_form_against_oracle(shape, K, order):
+    """LDDMM_PREC_BF16X3_JBF16: the gradient reads FP32 Jacobians and BF16X3 spectral stages
+    (relative error ~1e-5 per pi/iota); the Hessian-vector product reads the Jacobians
+    D iota(u~_j) rounded to BF16 (relative error <= 2^-9 per entry), so its bound is 1e-2."""
+    prob = oracle_problem(shape, K, Vn.DEFSTATE, order, nt=5)
+    vt = synth.random_velocity_coeffs(K, K, seed=3) * 0.5
+    E, Er, Ed, g = prob.gradient(vt)
+    dv = synth.random_coeffs(K, seed=4) * 0.1
+    Hdv = prob.hessian_matvec(vt, dv)
+    with gpu_context(prob, precision=L.PREC_BF16X3_JBF16) as ctx:
+        (E2, _, _), gg = ctx.gradient(devc(vt))
+        assert E2 == pytest.approx(E, rel=1e-4)
+        assert rel_l2(host(gg), g) < 1e-3
+        Hg = ctx.hessian_matvec(devc(vt), devc(dv))
+        err = rel_l2(host(Hg), Hdv)
+        assert 0 < err < 1e-2, err
+
+
 def test_hessian_recomputes_state_for_a_new_velocity():
     prob = oracle_problem((16, 16, 16), 8, Vn.DEFSTATE, 1, nt=4)
     v1 = synth.random_velocity_coeffs(8, 8, seed=5) * 0.5
@@ -150,7 +170,7 @@ def test_mixed_precision_registration_against_oracle_and_fp32_form():
     uo = S.include(prob.state_defstate(v_ref)[-1], prob.shape) * scale
     out = {}
     for name, prec in (("fp32_tensor", L.PREC_FP32), ("fp32_simt", L.PREC_FP32_SIMT),
-                       ("bf16x3", L.PREC_BF16X3)):
+                       ("bf16x3", L.PREC_BF16X3), ("bf16x3_jbf16", L.PREC_BF16X3_JBF16)):
         with gpu_context(prob, max_gn=c["max_gn"], max_pcg=c["max_pcg"], gtol=c["gtol"],
                          precision=prec) as ctx:
             v, rep = ctx.register()
