@@ -261,6 +261,8 @@ def run_b300(args):
         e2e_s.append(time.perf_counter() - t0)
     e2e_total = max_over_ranks(sum(e2e_s), world)
     ctx.close()
+    forms = measure_forms(L, torch, I0d, I1d, stream, flush) if args.forms and rank == 0 else None
+    warm = measure_warm_start(L, torch) if args.forms and rank == 0 else None
 
     if rank != 0:
         return None
@@ -304,9 +306,114 @@ def run_b300(args):
         "kernels": {k: {"launches": v["launches"], "ms": round(v["ms"], 3)} for k, v in
                     sorted(trace.items(), key=lambda kv: -kv[1]["ms"])[:12]},
     }
+    if forms is not None:
+        out["forms"] = forms
+    if warm is not None:
+        out["chosen_form"] = warm
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(steps_per_pair=last["solves"] * NT, samples=1)
     return out
+
+
+FORMS = [("defstate/linear/bf16x3_jbf16", "V_DEFSTATE", "INTERP_LINEAR", "PREC_BF16X3_JBF16"),
+         ("image/linear/fp32", "V_IMAGE", "INTERP_LINEAR", "PREC_FP32"),
+         ("defstate/cubic/fp32", "V_DEFSTATE", "INTERP_CUBIC", "PREC_FP32"),
+         ("image/cubic/fp32", "V_IMAGE", "INTERP_CUBIC", "PREC_FP32")]
+
+
+def measure_forms(L, torch, I0d, I1d, stream, flush):
+    """The bench pair in the other forms of the workload (variant x interpolation, and the
+    mixed-precision form): one untimed and one event-timed registration each."""
+    nz, ny, nx = SHAPE
+    res = {}
+    for name, var, interp, prec in FORMS:
+        ctx = L.Context(nx, ny, nz, K, nt=NT, variant=getattr(L, var), interp=getattr(L, interp),
+                        alpha=ALPHA, s=S_EXP, sigma2=SIGMA2, max_gn=MAX_GN, max_pcg=MAX_PCG,
+                        gtol=GTOL, precision=getattr(L, prec))
+        ctx.set_images(I0d, I1d)
+        ctx.register()
+        flush.fill_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        _, rep = ctx.register()
+        e1.record(stream)
+        e1.synchronize()
+        ctx.close()
+        res[name] = {"s_per_pair": e0.elapsed_time(e1) / 1e3, "gn_iters": rep["gn_iters"],
+                     "pcg_iters": rep["pcg_iters_total"], "E": rep["E"],
+                     "grad_rel_l2": rep["grad_rel_l2"],
+                     "residual_reached": rep["grad_rel_l2"] <= GTOL}
+    return res
+
+
+WARM_PAIRS = 4
+
+
+def measure_warm_start(L, torch):
+    """Time to the relative residual 1e-3 on held-out warm-start workload pairs
+    (192x224x192 Gaussian-blob pairs, 8-voxel deformations): the plain FP32 method (cold start,
+    one pair after another) against the chosen form (network warm start + BF16X3 spectral
+    stages with BF16 Hessian Jacobians + all pairs batched), both capped at 30 GN."""
+    import os as _os
+    from paper_2006_06823_b300 import warmstart as WS
+    if not _os.path.exists(WS.WEIGHTS):
+        return {"unavailable": "no trained warm-start weights in the package"}
+    nz, ny, nx = WS.SHAPE
+    solver = dict(WS.SOLVER, max_gn=WS.EVAL_MAX_GN)
+    seeds = [WS.EVAL_SEED0 + 2 * i for i in range(WARM_PAIRS)]
+    pairs = [WS.make_pair(sd) for sd in seeds]
+    net = L.Net(WS.NET_D, WS.NET_C, batch_max=1, seed=0)
+    WS.load_params(net, WS.WEIGHTS)
+    torch.cuda.synchronize()
+    # plain FP32, cold, sequential
+    ctx = L.Context(nx, ny, nz, WS.K, **solver)
+    ctx.set_images(*pairs[0])
+    ctx.register()                       # warm-up
+    plain = []
+    for I0, I1 in pairs:
+        ctx.set_images(I0, I1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, rep = ctx.register()
+        torch.cuda.synchronize()
+        rep["wall_s"] = time.perf_counter() - t0
+        plain.append(rep)
+    ctx.close()
+    # chosen form: warm start + BF16X3_JBF16 + batched
+    streams = [torch.cuda.Stream() for _ in pairs]
+    ctxs = []
+    for st in streams:
+        with torch.cuda.stream(st):
+            ctxs.append(L.Context(nx, ny, nz, WS.K, **dict(solver, precision=L.PREC_BF16X3_JBF16)))
+    for c, (I0, I1) in zip(ctxs, pairs):
+        c.set_images(I0, I1)
+    torch.cuda.synchronize()
+    L.register_batch(ctxs[:1], [net.warm_start(*pairs[0], WS.K)])   # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    vs = [net.warm_start(I0, I1, WS.K) for I0, I1 in pairs]
+    torch.cuda.synchronize()
+    reps = L.register_batch(ctxs, vs)
+    torch.cuda.synchronize()
+    t_chosen = time.perf_counter() - t0
+    for c in ctxs:
+        c.close()
+    net.close()
+    t_plain = sum(r["wall_s"] for r in plain)
+    gap = max(abs(b["E"] - a["E"]) / abs(a["E"]) for a, b in zip(plain, reps))
+    return {"workload": (f"{WARM_PAIRS} held-out warm-start pairs (192x224x192 Gaussian blobs, "
+                         "8-voxel stationary deformation), deformation state, K=32, nt=10, "
+                         "trilinear, gtol 1e-3, <=30 GN x <=20 PCG"),
+            "plain_fp32_s_per_pair": t_plain / WARM_PAIRS,
+            "chosen_s_per_pair": t_chosen / WARM_PAIRS,
+            "speedup": t_plain / t_chosen,
+            "plain_reached": sum(r["grad_rel_l2"] <= GTOL for r in plain),
+            "chosen_reached": sum(r["grad_rel_l2"] <= GTOL for r in reps),
+            "plain_gn_iters": [r["gn_iters"] for r in plain],
+            "chosen_gn_iters": [r["gn_iters"] for r in reps],
+            "energy_gap_rel_max": gap,
+            "chosen": "network warm start + LDDMM_PREC_BF16X3_JBF16 + lddmm_register_batch"}
 
 
 def cpu_baseline(steps_per_pair, samples=1):
@@ -450,6 +557,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="b300", choices=["b300", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", dest="forms", action="store_false",
+                    help="skip the other forms of the workload and the warm-start comparison")
     ap.add_argument("--config", default="paper", choices=["paper", "batch"])
     ap.add_argument("--pairs", type=int, default=64)
     ap.add_argument("--batch-threads", type=int, default=16)

@@ -218,99 +218,119 @@ k_pi_x(const float* __restrict__ f, long fstride, long rows_per_comp, int ncomp,
     }
 }
 
-// ------------------------------------------------------------------------ pi, stage Y
-// One CTA loops over (comp, z) slabs. Thread (ky pair jp, mode kx). Twiddles [y][jy] as
-// (cos, sin) float2 in shared memory, the slab A[y][kx] beside them.
-template <int KHP>
-__global__ void k_pi_y(const float2* __restrict__ A, int nslabs, int ny, int KH, int K,
-                       const float* __restrict__ cosT, const float* __restrict__ sinT,
-                       float2* __restrict__ B) {
-    extern __shared__ float4 smem4[];
-    float2* tw = reinterpret_cast<float2*>(smem4);   // ny * K
-    float2* sa = tw + (long)ny * K;                  // ny * KHP
-    const int nt = blockDim.x;
-    for (int e = threadIdx.x; e < ny * K; e += nt) {
-        int y = e / K, jy = e - y * K;
-        long o = (long)jy * ny + y;
-        tw[e] = make_float2(cosT[o], sinT[o]);
-    }
-    const int kx = threadIdx.x % KHP;
-    const int jp = threadIdx.x / KHP;  // ky pair: slots 2jp, 2jp+1
-    for (int slab = blockIdx.x; slab < nslabs; slab += gridDim.x) {
+// ------------------------------------------- Y and Z stages: batched twiddle contractions
+// Out[split][s][p][col] = sum_{q in split's range} M[p][q] In[s][q][col] for every slab s and
+// column col < C, where M is a twiddle matrix read from the FP64-evaluated tables:
+// M[p][q] = cos(.) + i sgn sin(.) at (mode, position) = (p, q) (mode_is_p) or (q, p), and 0
+// for mode slot 0 when zero_mode0. The columns of all slabs form one GEMM dimension
+// N = nslab * C. CTA tile: 32 rows p x NT columns, q in chunks of 32 through shared memory;
+// thread tile 2 rows x NT/16 columns of complex FP32 accumulators.
+struct TwMat {
+    const float *cosT, *sinT;
+    int len;          // table row length (positions per mode)
+    float sgn;        // +1: e^{+i theta}; -1: e^{-i theta}
+    bool mode_is_p;   // the mode index is the row p (else the column q)
+    bool zero_mode0;  // mode slot 0 contributes zero
+};
+
+constexpr int CG_PT = 32, CG_QT = 32;
+
+template <int NT>
+__global__ void __launch_bounds__(256)
+k_cgemm_tw(TwMat M, int P, int Q, int C, long N, const float2* __restrict__ In, long inS, long inQ,
+           float2* __restrict__ Out, long outS, long outP, long outSplit) {
+    constexpr int CPT = NT / 16;  // columns per thread
+    __shared__ __align__(16) float2 Ms[CG_QT][CG_PT];
+    __shared__ __align__(16) float2 Is[CG_QT][NT];
+    const int tid = threadIdx.x, rg = tid >> 4, cg = tid & 15;
+    const long n0 = (long)blockIdx.x * NT;
+    const int p0 = blockIdx.y * CG_PT;
+    const int qsplit = gridDim.z;
+    const int qlen = (Q + qsplit - 1) / qsplit;
+    const int qb = blockIdx.z * qlen, qe = min(Q, qb + qlen);
+    float ar[2][CPT], ai[2][CPT];
+#pragma unroll
+    for (int i = 0; i < 2; ++i)
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) ar[i][j] = ai[i][j] = 0.f;
+    for (int q0 = qb; q0 < qe; q0 += CG_QT) {
         __syncthreads();
-        for (int e = threadIdx.x; e < ny * KHP; e += nt) {
-            int y = e / KHP, k = e - y * KHP;
-            sa[e] = k < KH ? A[((long)slab * ny + y) * KH + k] : make_float2(0.f, 0.f);
+        for (int e = tid; e < CG_QT * CG_PT; e += 256) {
+            const int ql = e / CG_PT, pl = e - ql * CG_PT;
+            const int p = p0 + pl, q = q0 + ql;
+            float2 v = make_float2(0.f, 0.f);
+            if (p < P && q < qe) {
+                const int m = M.mode_is_p ? p : q, x = M.mode_is_p ? q : p;
+                if (!(M.zero_mode0 && m == 0)) {
+                    const long o = (long)m * M.len + x;
+                    v = make_float2(M.cosT[o], M.sgn * M.sinT[o]);
+                }
+            }
+            Ms[ql][pl] = v;
+        }
+        for (int e = tid; e < CG_QT * NT; e += 256) {
+            const int ql = e / NT, nl = e - ql * NT;
+            const long n = n0 + nl;
+            const int q = q0 + ql;
+            float2 v = make_float2(0.f, 0.f);
+            if (n < N && q < qe) {
+                const long sl = n / C;
+                v = In[sl * inS + (long)q * inQ + (n - sl * C)];
+            }
+            Is[ql][nl] = v;
         }
         __syncthreads();
-        if (2 * jp < K) {
-            float r0 = 0.f, i0 = 0.f, r1 = 0.f, i1 = 0.f;
-            for (int y = 0; y < ny; ++y) {
-                float2 a = sa[y * KHP + kx];
-                float4 t = *reinterpret_cast<const float4*>(&tw[y * K + 2 * jp]);
-                // a * (cos - i sin)
-                r0 = fmaf(a.x, t.x, fmaf(a.y, t.y, r0));
-                i0 = fmaf(a.y, t.x, fmaf(-a.x, t.y, i0));
-                r1 = fmaf(a.x, t.z, fmaf(a.y, t.w, r1));
-                i1 = fmaf(a.y, t.z, fmaf(-a.x, t.w, i1));
+        const int qn = min(CG_QT, qe - q0);
+        for (int ql = 0; ql < qn; ++ql) {
+            const float4 m4 = *reinterpret_cast<const float4*>(&Ms[ql][2 * rg]);
+            const float2 mv[2] = {make_float2(m4.x, m4.y), make_float2(m4.z, m4.w)};
+            float2 iv[CPT];
+#pragma unroll
+            for (int j = 0; j < CPT; j += 2) {
+                const float4 t = *reinterpret_cast<const float4*>(&Is[ql][cg * CPT + j]);
+                iv[j] = make_float2(t.x, t.y);
+                iv[j + 1] = make_float2(t.z, t.w);
             }
-            if (kx < KH) {
-                B[((long)slab * K + 2 * jp) * KH + kx] = make_float2(r0, i0);
-                B[((long)slab * K + 2 * jp + 1) * KH + kx] = make_float2(r1, i1);
-            }
+#pragma unroll
+            for (int i = 0; i < 2; ++i)
+#pragma unroll
+                for (int j = 0; j < CPT; ++j) {
+                    ar[i][j] = fmaf(mv[i].x, iv[j].x, fmaf(-mv[i].y, iv[j].y, ar[i][j]));
+                    ai[i][j] = fmaf(mv[i].x, iv[j].y, fmaf(mv[i].y, iv[j].x, ai[i][j]));
+                }
+        }
+    }
+    float2* out = Out + (long)blockIdx.z * outSplit;
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        const int p = p0 + 2 * rg + i;
+        if (p >= P) continue;
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) {
+            const long n = n0 + cg * CPT + j;
+            if (n >= N) continue;
+            const long sl = n / C;
+            out[sl * outS + (long)p * outP + (n - sl * C)] = make_float2(ar[i][j], ai[i][j]);
         }
     }
 }
 
-// ------------------------------------------------------------------------ pi, stage Z
-// Partial sums over a block of z planes: CTA (comp, 64 (jy, kx) columns, z block), thread
-// (column, jz residue class mod 4). part[split][comp][jz][col] = sum_z B[z][col] e^{-i kz z}.
-constexpr int PZ_COLS = 64;
-
-__global__ void __launch_bounds__(256)
-k_pi_z_part(const float2* __restrict__ B, int ncomp, int nz, int K, int KH, int zsplit,
-            const float* __restrict__ cosT, const float* __restrict__ sinT,
-            float2* __restrict__ part) {
-    extern __shared__ float4 smem4[];
-    float2* tw = reinterpret_cast<float2*>(smem4);  // [zl][jz]
-    const int ncol = K * KH;
-    const int colblocks = (ncol + PZ_COLS - 1) / PZ_COLS;
-    const int comp = blockIdx.x / colblocks;
-    const int col = (blockIdx.x - comp * colblocks) * PZ_COLS + (threadIdx.x & (PZ_COLS - 1));
-    const int jzg = threadIdx.x / PZ_COLS;  // 0..3
-    const int split = blockIdx.y;
-    const int zb = (nz + zsplit - 1) / zsplit;
-    const int z0 = split * zb, z1 = min(nz, z0 + zb);
-    for (int e = threadIdx.x; e < (z1 - z0) * K; e += blockDim.x) {
-        int zl = e / K, jz = e - zl * K;
-        long o = (long)jz * nz + z0 + zl;
-        tw[e] = make_float2(cosT[o], sinT[o]);
+// Launches k_cgemm_tw: NT = 32 when the column count alone would leave SMs idle.
+static int cgemm_tw(const TwMat& M, int P, int Q, int C, long nslab, const float2* In, long inS,
+                    long inQ, float2* Out, long outS, long outP, int qsplit, long outSplit,
+                    const char* name, double bytes, cudaStream_t st) {
+    const long N = nslab * C;
+    const long tiles64 = ((N + 63) / 64) * ((P + CG_PT - 1) / CG_PT) * qsplit;
+    KTRACE(name, st, bytes, 8.0 * P * (double)Q * N);
+    if (tiles64 < 2 * 148) {
+        dim3 grid((unsigned)((N + 31) / 32), (P + CG_PT - 1) / CG_PT, qsplit);
+        k_cgemm_tw<32><<<grid, 256, 0, st>>>(M, P, Q, C, N, In, inS, inQ, Out, outS, outP, outSplit);
+    } else {
+        dim3 grid((unsigned)((N + 63) / 64), (P + CG_PT - 1) / CG_PT, qsplit);
+        k_cgemm_tw<64><<<grid, 256, 0, st>>>(M, P, Q, C, N, In, inS, inQ, Out, outS, outP, outSplit);
     }
-    __syncthreads();
-    if (col >= ncol) return;
-    float re[16], im[16];
-#pragma unroll
-    for (int q = 0; q < 16; ++q) re[q] = im[q] = 0.f;
-    const float2* b = B + (long)comp * nz * ncol + col;
-    for (int z = z0; z < z1; ++z) {
-        const float2 v = b[(long)z * ncol];
-        const float2* t = tw + (z - z0) * K + jzg;
-#pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            if (jzg + 4 * q < K) {
-                const float2 w = t[4 * q];
-                // v * (cos - i sin)
-                re[q] = fmaf(v.x, w.x, fmaf(v.y, w.y, re[q]));
-                im[q] = fmaf(v.y, w.x, fmaf(-v.x, w.y, im[q]));
-            }
-        }
-    }
-    float2* out = part + ((long)split * ncomp + comp) * K * ncol + col;
-#pragma unroll
-    for (int q = 0; q < 16; ++q) {
-        const int jz = jzg + 4 * q;
-        if (jz < K) out[(long)jz * ncol] = make_float2(re[q], im[q]);
-    }
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
 }
 
 // Sum of the z-block partials, 1/N normalisation, Hermitian mirror and zero slots.
@@ -374,30 +394,6 @@ static int launch_pi_x(const Grid& g, const Twiddles& tw, const float* f, long f
     return LDDMM_OK;
 }
 
-template <int KHP>
-static int launch_pi_y(const Grid& g, const Twiddles& tw, int ncomp, const float2* A, float2* B,
-                       cudaStream_t st) {
-    const int K = tw.K, KH = K / 2;
-    size_t smem = (size_t)g.ny * K * 8 + (size_t)g.ny * KHP * 8;
-    if (smem > 227 * 1024) {
-        set_error("bl_project: ny too large for the y stage");
-        return LDDMM_EINVAL;
-    }
-    static bool attr_set = false;
-    if (!attr_set) {
-        LDDMM_CUDA(cudaFuncSetAttribute(k_pi_y<KHP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        227 * 1024));
-        attr_set = true;
-    }
-    int nslabs = ncomp * g.nz;
-    int threads = KHP * ((K + 1) / 2);
-    KTRACE("pi_y", st, (double)nslabs * (g.ny + K) * KH * 8.0, (double)nslabs * K * KH * g.ny * 8.0);
-    k_pi_y<KHP><<<std::min(nslabs, 2 * 148), threads, smem, st>>>(A, nslabs, g.ny, KH, K, tw.cy,
-                                                                  tw.sy, B);
-    LDDMM_CHECK_LAUNCH();
-    return LDDMM_OK;
-}
-
 static int check_spectral_shape(const Grid& g, int K) {
     if (g.nx < 2 || g.ny < 2 || g.nz < 2 || K < 4 || (K & 1) || K > 64 || K > g.nx ||
         K > g.ny || K > g.nz || g.nx > 1024 || g.ny > 1024) {
@@ -427,19 +423,24 @@ int bl_project(const Grid& g, const Twiddles& tw, const float* f, long fstride, 
         rc = KHP_DISPATCH(KH, launch_pi_x, g, tw, f, fstride, ncomp, s1, st);
     }
     if (rc) return rc;
-    rc = KHP_DISPATCH(KH, launch_pi_y, g, tw, ncomp, s1, s2, st);
-    if (rc) return rc;
-    // stage Z: z-block partial sums into s1 (free once stage Y has consumed it)
-    const int zsplit = std::max(1, std::min(8, g.nz / K));
-    const int colblocks = (K * KH + PZ_COLS - 1) / PZ_COLS;
+    // stage Y: B[comp, z][jy][kx] = sum_y e^{-i ky y} A[comp, z][y][kx]
     {
-        size_t smem = (size_t)((g.nz + zsplit - 1) / zsplit) * K * 8;
-        KTRACE("pi_z", st, (double)ncomp * g.nz * K * KH * 8.0 + (double)zsplit * ncomp * K * K * KH * 8.0,
-               (double)ncomp * K * K * KH * g.nz * 8.0);
-        k_pi_z_part<<<dim3(ncomp * colblocks, zsplit), 256, smem, st>>>(s2, ncomp, g.nz, K, KH, zsplit,
-                                                                       tw.cz, tw.sz, s1);
+        const TwMat My{tw.cy, tw.sy, g.ny, -1.f, true, false};
+        const long nslab = (long)ncomp * g.nz;
+        rc = cgemm_tw(My, K, g.ny, KH, nslab, s1, (long)g.ny * KH, KH, s2, (long)K * KH, KH, 1, 0,
+                      "pi_y", (double)nslab * (g.ny + K) * KH * 8.0, st);
+        if (rc) return rc;
     }
-    LDDMM_CHECK_LAUNCH();
+    // stage Z: z-block partial sums part[split][comp][jz][col] into s1 (free after stage Y)
+    const int zsplit = std::max(1, std::min(8, g.nz / K));
+    {
+        const TwMat Mz{tw.cz, tw.sz, g.nz, -1.f, true, false};
+        const long ncol = (long)K * KH;
+        rc = cgemm_tw(Mz, K, g.nz, (int)ncol, ncomp, s2, g.nz * ncol, ncol, s1, K * ncol, ncol, zsplit,
+                      (long)ncomp * K * ncol, "pi_z",
+                      (double)ncomp * g.nz * ncol * 8.0 + (double)zsplit * ncomp * K * ncol * 8.0, st);
+        if (rc) return rc;
+    }
     long total = (long)ncomp * K * K * KH;
     {
         KTRACE("pi_z_fin", st, (double)zsplit * total * 8.0 + (double)ncomp * K * K * K * 8.0, 0);
@@ -549,70 +550,6 @@ k_iota_z2(const float2* __restrict__ c, int nz, int ny, int nx, int K, int KH, i
     }
 }
 
-// ---------------------------------------------------------- iota stage Y (register-tiled)
-// T2[plane][y][kx] = sum_{jy>=1} Ey[y][jy] T1[plane][jy][kx]; persistent CTA over planes,
-// twiddles [jy][y] in shared memory once; thread tile 4 y x 4 kx.
-__global__ void __launch_bounds__(256)
-k_iota_y2(const float2* __restrict__ T1, int nplanes, int ny, int K, int KH,
-          const float* __restrict__ cyT, const float* __restrict__ syT, float2* __restrict__ T2) {
-    extern __shared__ float4 smem4[];
-    const int nyp = (ny + 3) & ~3, KHP = (KH + 3) & ~3;
-    float2* tw = reinterpret_cast<float2*>(smem4);   // K x nyp
-    float2* t1 = tw + (long)K * nyp;                 // K x KHP
-    const int tid = threadIdx.x;
-    for (int e = tid; e < K * nyp; e += blockDim.x) {
-        const int jy = e / nyp, y = e - jy * nyp;
-        tw[e] = (jy >= 1 && y < ny) ? make_float2(cyT[(long)jy * ny + y], syT[(long)jy * ny + y])
-                                    : make_float2(0.f, 0.f);
-    }
-    const int kgroups = KHP / 4, ygroups = nyp / 4;
-    const int tiles = kgroups * ygroups;
-    for (int plane = blockIdx.x; plane < nplanes; plane += gridDim.x) {
-        __syncthreads();
-        for (int e = tid; e < K * KHP; e += blockDim.x) {
-            const int jy = e / KHP, kx = e - jy * KHP;
-            t1[e] = kx < KH ? T1[((long)plane * K + jy) * KH + kx] : make_float2(0.f, 0.f);
-        }
-        __syncthreads();
-        float2* out = T2 + (long)plane * ny * KH;
-        for (int tile = tid; tile < tiles; tile += blockDim.x) {
-            const int kg = tile % kgroups, yg = tile / kgroups;
-            float ar[4][4], ai[4][4];
-#pragma unroll
-            for (int a = 0; a < 4; ++a)
-#pragma unroll
-                for (int b = 0; b < 4; ++b) ar[a][b] = ai[a][b] = 0.f;
-            for (int jy = 1; jy < K; ++jy) {
-                const float4 e01 = *reinterpret_cast<const float4*>(&tw[jy * nyp + 4 * yg]);
-                const float4 e23 = *reinterpret_cast<const float4*>(&tw[jy * nyp + 4 * yg + 2]);
-                const float4 t01 = *reinterpret_cast<const float4*>(&t1[jy * KHP + 4 * kg]);
-                const float4 t23 = *reinterpret_cast<const float4*>(&t1[jy * KHP + 4 * kg + 2]);
-                const float2 ev[4] = {make_float2(e01.x, e01.y), make_float2(e01.z, e01.w),
-                                      make_float2(e23.x, e23.y), make_float2(e23.z, e23.w)};
-                const float2 tv[4] = {make_float2(t01.x, t01.y), make_float2(t01.z, t01.w),
-                                      make_float2(t23.x, t23.y), make_float2(t23.z, t23.w)};
-#pragma unroll
-                for (int a = 0; a < 4; ++a)
-#pragma unroll
-                    for (int b = 0; b < 4; ++b) {
-                        ar[a][b] = fmaf(ev[a].x, tv[b].x, fmaf(-ev[a].y, tv[b].y, ar[a][b]));
-                        ai[a][b] = fmaf(ev[a].x, tv[b].y, fmaf(ev[a].y, tv[b].x, ai[a][b]));
-                    }
-            }
-#pragma unroll
-            for (int a = 0; a < 4; ++a) {
-                const int y = 4 * yg + a;
-                if (y >= ny) continue;
-#pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const int kx = 4 * kg + b;
-                    if (kx < KH) out[(long)y * KH + kx] = make_float2(ar[a][b], ai[a][b]);
-                }
-            }
-        }
-    }
-}
-
 static int launch_iota_zy2(const Grid& g, const Twiddles& tw, const float2* c, int nout,
                            int deriv_axis, int bspline, float2* T1, float2* T2, cudaStream_t st) {
     const int K = tw.K, KH = K / 2, KK = K * KH;
@@ -625,27 +562,11 @@ static int launch_iota_zy2(const Grid& g, const Twiddles& tw, const float2* c, i
                                         tw.cy, tw.cz, tw.sz, T1);
     }
     LDDMM_CHECK_LAUNCH();
-    const int nyp = (g.ny + 3) & ~3, KHP = (KH + 3) & ~3;
-    const size_t smem = (size_t)K * nyp * 8 + (size_t)K * KHP * 8;
-    if (smem > 200 * 1024) {
-        set_error("bl_include: ny too large for the y stage");
-        return LDDMM_EINVAL;
-    }
-    static bool attr = false;
-    if (!attr) {
-        LDDMM_CUDA(cudaFuncSetAttribute(k_iota_y2, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        200 * 1024));
-        attr = true;
-    }
-    const int nplanes = nout * g.nz;
-    {
-        KTRACE("iota_y", st, (double)nplanes * (K + g.ny) * KH * 8.0,
-               (double)nplanes * g.ny * KH * K * 8.0);
-        k_iota_y2<<<std::min(nplanes, 3 * 148), 256, smem, st>>>(T1, nplanes, g.ny, K, KH, tw.cy,
-                                                                tw.sy, T2);
-    }
-    LDDMM_CHECK_LAUNCH();
-    return LDDMM_OK;
+    // stage Y: T2[plane][y][kx] = sum_{jy >= 1} e^{+i ky y} T1[plane][jy][kx]
+    const long nplanes = (long)nout * g.nz;
+    const TwMat My{tw.cy, tw.sy, g.ny, 1.f, false, true};
+    return cgemm_tw(My, g.ny, K, KH, nplanes, T1, (long)K * KH, KH, T2, (long)g.ny * KH, KH, 1, 0,
+                    "iota_y", (double)nplanes * (K + g.ny) * KH * 8.0, st);
 }
 
 // ---------------------------------------------------------------------- iota, stage X

@@ -197,18 +197,27 @@ constexpr int NWORK = 4;                 // split + epilogue warps
 constexpr int WARP_TMA = NWORK;          // TMA producer warp
 constexpr int WARP_MMA = NWORK + 1;      // MMA issuer (and TMEM owner)
 constexpr int NTHREADS_WS = 32 * (NWORK + 2);
-constexpr int NRAW = 4;                  // TMA landing ring (released after the split)
-constexpr int NOP = 2;                   // hi/lo operand ring (released by MMA completion)
+constexpr int NRAW_MAX = 6;
+constexpr int NOP = 2;                   // split-operand ring (released by MMA completion)
 constexpr int TILE_B = TM * 128;         // 16 KB
+// TMA landing ring depth. TF32: the landed FP32 tile is itself the hi operand (the tensor core
+// reads only the upper 19 bits of a TF32 operand, i.e. the truncation hi = x with its low 13
+// mantissa bits cleared), so only lo = x - hi is materialised and a raw slot is released by
+// MMA completion; the smem freed by not storing hi deepens the ring from 4 to 6 tiles.
+// BF16: hi and lo are both materialised and the raw slot is released after the split.
+__host__ __device__ constexpr int nraw(int prec) { return prec == 0 ? 6 : 4; }
+__host__ __device__ constexpr int nop_planes(int prec) { return prec == 0 ? 1 : 2; }
 
 }  // namespace
 
 // Warp-specialised pipeline. Chunk q: tile t = q / nchunk, column block c = q % nchunk.
 //   producer : wait raw_empty[q%NRAW], TMA 128 x 32 tile -> raw[q%NRAW]
-//   workers  : wait raw_full, wait op_empty[q%NOP]; hi/lo split raw -> op; arrive raw_empty and
-//              op_full; after the first chunk of tile t, epilogue of tile t-1
-//   MMA warp : wait op_full (and, for c == 0, accempty of TMEM buffer t&1); 3 x 4 MMAs;
-//              commit -> op_empty; last chunk of the tile: commit -> accfull[t&1]
+//   workers  : wait raw_full, wait op_empty[q%NOP]; split raw -> op (TF32: lo only; BF16: hi
+//              and lo, then arrive raw_empty); arrive op_full; after the first chunk of tile
+//              t, epilogue of tile t-1
+//   MMA warp : wait op_full (and, for c == 0, accempty of TMEM buffer t&1); 3 x k-step MMAs
+//              (TF32: A hi read straight from raw); commit -> op_empty (TF32: and raw_empty);
+//              last chunk of the tile: commit -> accfull[t&1]
 //   epilogue : TMEM 32-column blocks -> swizzled staging (2 buffers) -> TMA store
 // OUT is the 3-D tensor [ncomp][rpc][n_out] behind tmap_out (rows r = comp * rpc + local).
 // PREC 0: TF32 hi + lo (4 k-steps of 8 per 32-column chunk). PREC 1: BF16 hi + lo, the 32
@@ -219,7 +228,8 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
              const unsigned char* __restrict__ w_image, int N, int kdim, long rows,
              float* __restrict__ out, long rpc, long comp_stride, int n_out, unsigned tmem_cols) {
     extern __shared__ unsigned char smem_raw[];
-    __shared__ uint64_t raw_full[NRAW], raw_empty[NRAW], op_full[NOP], op_empty[NOP], w_bar;
+    constexpr int NRAW = nraw(PREC);
+    __shared__ uint64_t raw_full[NRAW_MAX], raw_empty[NRAW_MAX], op_full[NOP], op_empty[NOP], w_bar;
     __shared__ uint64_t accfull_bar[2], accempty_bar[2];
     __shared__ unsigned tmem_holder;
     __shared__ volatile int abort_flag;
@@ -233,15 +243,15 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
     unsigned char* w_hi = base;
     unsigned char* w_lo = base + wbytes;
     unsigned char* raw = base + 2 * wbytes;          // NRAW x 16 KB
-    unsigned char* op_hi = raw + NRAW * TILE_B;      // NOP x 16 KB
-    unsigned char* op_lo = op_hi + NOP * TILE_B;     // NOP x 16 KB
-    unsigned char* stg = op_lo + NOP * TILE_B;       // 2 x 16 KB epilogue staging
+    unsigned char* op_lo = raw + NRAW * TILE_B;      // NOP x 16 KB
+    unsigned char* op_hi = op_lo + NOP * TILE_B;     // NOP x 16 KB (BF16 only)
+    unsigned char* stg = op_lo + nop_planes(PREC) * NOP * TILE_B;  // 2 x 16 KB epilogue staging
 
     if (tid == 0) {
         mbar_init(&w_bar, 1);
         for (int i = 0; i < NRAW; ++i) {
             mbar_init(&raw_full[i], 1);
-            mbar_init(&raw_empty[i], NWORK);
+            mbar_init(&raw_empty[i], PREC == 0 ? 1 : NWORK);
         }
         for (int i = 0; i < NOP; ++i) {
             mbar_init(&op_full[i], NWORK);
@@ -322,7 +332,9 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
                 if (abort_flag) break;
                 fence_after();
                 const unsigned d = tmem + (unsigned)(b * N);
-                const unsigned ah = smem_u32(op_hi + (size_t)o * TILE_B);
+                const int s = (int)(q % NRAW);
+                const unsigned ah = PREC == 0 ? smem_u32(raw + (size_t)s * TILE_B)
+                                              : smem_u32(op_hi + (size_t)o * TILE_B);
                 const unsigned al = smem_u32(op_lo + (size_t)o * TILE_B);
                 const unsigned wh = smem_u32(w_hi + (size_t)c * N * 128);
                 const unsigned wl = smem_u32(w_lo + (size_t)c * N * 128);
@@ -346,6 +358,7 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
                     }
                 }
                 mma_commit(&op_empty[o]);
+                if (PREC == 0) mma_commit(&raw_empty[s]);
                 if (c == nchunk - 1) mma_commit(&accfull_bar[b]);
             }
         }
@@ -411,7 +424,6 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
                 const float4 v = src[e];
                 if (PREC == 0) {
                     const float4 h = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
-                    hi[e] = h;
                     lo[e] = make_float4(v.x - h.x, v.y - h.y, v.z - h.z, v.w - h.w);
                 } else {
                     // raw 16-byte chunk e = (row r, physical chunk p) holds logical chunk
@@ -427,7 +439,7 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             __syncwarp();
             if (lane == 0) {
-                mbar_arrive(&raw_empty[s]);
+                if (PREC != 0) mbar_arrive(&raw_empty[s]);
                 mbar_arrive(&op_full[o]);
             }
             if (wt == 0) consumed_sh = q + 1;
@@ -528,9 +540,12 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
+// W hi + lo, the raw ring, the split operands and two staging tiles (+ alignment slack);
+// both precisions come to 10 tiles besides W
 int tc_smem_bytes(int N, int kdim) {
     const int nchunk = (kdim + CHUNK - 1) / CHUNK;
-    return 2 * nchunk * N * 128 + (NRAW + 2 * NOP + 2) * TILE_B + 1024;
+    static_assert(nraw(0) + nop_planes(0) * NOP == nraw(1) + nop_planes(1) * NOP, "ring sizes");
+    return 2 * nchunk * N * 128 + (nraw(1) + nop_planes(1) * NOP + 2) * TILE_B + 1024;
 }
 
 }  // namespace

@@ -66,3 +66,53 @@ def test_transport_one_full_grid_step():
     out = L.sl_transport(Vt, ft, 1, L.FORWARD, L.INTERP_LINEAR).cpu().numpy()
     ref = SL.sl_transport(f, V, 1, +1, 1)
     assert rel_l2(out, ref) < 1e-5
+
+
+def test_mixed_precision_256_phantom():
+    """Mixed-precision forms on a 256^3 phantom (the paper-scale recipe on a cubic grid):
+    pi and iota in each spectral precision against the FP64 oracle's (numpy-FFT) pi/iota, and
+    one registration per form with its GN / PCG counts and final energy against the plain
+    FP32 form. With LDDMM_REPORT_DIR set the numbers go to mixed_precision_256.json."""
+    import json
+    import os
+    from oracle import spectral as S
+    shape = (256, 256, 256)
+    nz, ny, nx = shape
+    fixed = synth.ellipsoid_phantom(shape)
+    fd = torch.as_tensor(fixed, dtype=torch.float32, device="cuda")
+    ref_c = S.project(fixed, K)
+    ref_f = S.include(ref_c, shape)
+    out = {"operators": {}, "registration": {}}
+    for name, prec in (("fp32_tensor", L.PREC_FP32), ("fp32_simt", L.PREC_FP32_SIMT),
+                       ("bf16x3", L.PREC_BF16X3)):
+        c = L.bl_project(fd, K, precision=prec)[0].cpu().numpy().astype(np.complex128)
+        f = L.bl_include(torch.as_tensor(ref_c.astype(np.complex64), device="cuda")[None], shape,
+                         precision=prec)[0].cpu().numpy().astype(np.float64)
+        out["operators"][name] = {"pi_rel_l2": rel_l2(c, ref_c), "iota_rel_l2": rel_l2(f, ref_f)}
+    for name, r in out["operators"].items():
+        bound = 5e-5 if name == "bf16x3" else 3e-6
+        assert r["pi_rel_l2"] < bound and r["iota_rel_l2"] < bound, (name, r)
+    # moving = phantom transported along a random band-limited velocity (8 voxels max)
+    vt = synth.random_velocity_coeffs(K, K, seed=1)
+    v = L.bl_include(torch.as_tensor(vt.astype(np.complex64), device="cuda"), shape)
+    V = v * (torch.tensor([nx, ny, nz], dtype=torch.float32, device="cuda").view(3, 1, 1, 1)
+             / (2 * np.pi))
+    V *= 8.0 / V.pow(2).sum(0).sqrt().max()
+    moving = L.sl_transport(V, fd, 10, L.FORWARD, L.INTERP_LINEAR)
+    for name, prec in (("fp32_simt", L.PREC_FP32_SIMT), ("fp32_tensor", L.PREC_FP32),
+                       ("bf16x3", L.PREC_BF16X3), ("bf16x3_jbf16", L.PREC_BF16X3_JBF16)):
+        with L.Context(nx, ny, nz, K, nt=10, variant=L.V_DEFSTATE, interp=L.INTERP_LINEAR,
+                       max_gn=10, max_pcg=20, gtol=1e-3, precision=prec) as ctx:
+            ctx.set_images(moving, fd)
+            _, rep = ctx.register()
+        out["registration"][name] = {k: rep[k] for k in ("gn_iters", "pcg_iters_total", "E",
+                                                         "grad_rel_l2", "seconds")}
+    base = out["registration"]["fp32_simt"]
+    for name, r in out["registration"].items():
+        r["E_rel_diff_vs_fp32_simt"] = abs(r["E"] - base["E"]) / abs(base["E"])
+    rd = os.environ.get("LDDMM_REPORT_DIR")
+    if rd:
+        os.makedirs(rd, exist_ok=True)
+        json.dump(out, open(os.path.join(rd, "mixed_precision_256.json"), "w"), indent=1)
+    for name, r in out["registration"].items():
+        assert r["E_rel_diff_vs_fp32_simt"] < 1e-3, (name, r)
