@@ -63,6 +63,9 @@ struct Twiddles {
     // the same two matrices as tensor-core operand images (hi | lo, swizzled), 16-B aligned:
     // [0] TF32 split, [1] BF16 split
     const unsigned char *wpi_img[2], *wio_img[2];
+    // Y/Z-stage contraction matrices, complex [q][p] (p fastest): mpy[y][jy] = e^{-i ky y},
+    // miy[jy][y] = e^{+i ky y} (0 for jy = 0), mpz[z][jz] = e^{-i kz z}
+    const float2 *mpy, *miy, *mpz;
 };
 long twiddle_floats(const Grid& g, int K);
 // Fills `mem` (twiddle_floats floats, device) and points `tw` into it.

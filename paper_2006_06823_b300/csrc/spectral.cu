@@ -26,7 +26,21 @@ long twiddle_floats(const Grid& g, int K) {
     long f = 2L * K * ((long)g.nx + g.ny + g.nz) + 2L * K * g.nx;
     f = (f + 63) & ~63L;
     f += 2 * ((tc_wimage_bytes(K, g.nx) + 255) / 4 + (tc_wimage_bytes(g.nx, K) + 255) / 4);
+    f = (f + 63) & ~63L;
+    f += 2L * K * (2L * g.ny + g.nz);  // mpy, miy, mpz (float2)
     return f + 64;
+}
+
+// [q][p] complex contraction matrix from a twiddle table: M[q][p] = cos + i sgn sin at
+// (mode, position) = (p, q) (mode_is_p) or (q, p); mode slot 0 zero when zero_mode0.
+__global__ void k_build_cmat(const float* cosT, const float* sinT, int len, int P, int Q,
+                             float sgn, int mode_is_p, int zero_mode0, float2* M) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= P * Q) return;
+    const int q = i / P, pp = i - q * P;
+    const int m = mode_is_p ? pp : q, x = mode_is_p ? q : pp;
+    const long o = (long)m * len + x;
+    M[i] = (zero_mode0 && m == 0) ? make_float2(0.f, 0.f) : make_float2(cosT[o], sgn * sinT[o]);
 }
 
 // x-stage matrices of the tensor-core path from the x twiddle table (slot h + kx = wavenumber kx)
@@ -105,6 +119,23 @@ int twiddle_init(const Grid& g, int K, float* mem, Twiddles& tw, cudaStream_t st
         if (rc) return rc;
         tw.wpi_img[prec] = img_pi;
         tw.wio_img[prec] = img_io;
+    }
+    {
+        long moff = (long)(img + 2 * (bpi + bio) - reinterpret_cast<unsigned char*>(mem)) / 4;
+        moff = (moff + 63) & ~63L;
+        float2* m = reinterpret_cast<float2*>(mem + moff);
+        float2* mpy = m;
+        float2* miy = mpy + (long)K * g.ny;
+        float2* mpz = miy + (long)K * g.ny;
+        KTRACE("twiddle", st, 24.0 * K * (2.0 * g.ny + g.nz), 0);
+        k_build_cmat<<<cdiv((long)K * g.ny, 256), 256, 0, st>>>(tw.cy, tw.sy, g.ny, K, g.ny, -1.f, 1, 0, mpy);
+        k_build_cmat<<<cdiv((long)K * g.ny, 256), 256, 0, st>>>(tw.cy, tw.sy, g.ny, g.ny, K, 1.f, 0, 1, miy);
+        k_build_cmat<<<cdiv((long)K * g.nz, 256), 256, 0, st>>>(tw.cz, tw.sz, g.nz, K, g.nz, -1.f, 1, 0, mpz);
+        LDDMM_CHECK_LAUNCH();
+        count_launches(2);
+        tw.mpy = mpy;
+        tw.miy = miy;
+        tw.mpz = mpz;
     }
     return LDDMM_OK;
 }
@@ -218,116 +249,146 @@ k_pi_x(const float* __restrict__ f, long fstride, long rows_per_comp, int ncomp,
     }
 }
 
+// 8-byte asynchronous global -> shared copy; zero fill when !ok (source size 0)
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool ok) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(ok ? 8 : 0)
+                 : "memory");
+}
+
 // ------------------------------------------- Y and Z stages: batched twiddle contractions
-// Out[split][s][p][col] = sum_{q in split's range} M[p][q] In[s][q][col] for every slab s and
-// column col < C, where M is a twiddle matrix read from the FP64-evaluated tables:
-// M[p][q] = cos(.) + i sgn sin(.) at (mode, position) = (p, q) (mode_is_p) or (q, p), and 0
-// for mode slot 0 when zero_mode0. The columns of all slabs form one GEMM dimension
-// N = nslab * C. CTA tile: 32 rows p x NT columns, q in chunks of 32 through shared memory;
-// thread tile 2 rows x NT/16 columns of complex FP32 accumulators.
-struct TwMat {
-    const float *cosT, *sinT;
-    int len;          // table row length (positions per mode)
-    float sgn;        // +1: e^{+i theta}; -1: e^{-i theta}
-    bool mode_is_p;   // the mode index is the row p (else the column q)
-    bool zero_mode0;  // mode slot 0 contributes zero
-};
+// Out[split][s][p][col] = sum_{q in split's range} M[q][p] In[s][q][col] for every slab s and
+// column col < C, with M a prebuilt complex matrix (Twiddles::mpy / miy / mpz). The columns of
+// all slabs form one GEMM dimension N = nslab * C. CTA tile: PT = 16 RPT rows p x NT columns,
+// q in chunks of 32 through double-buffered shared memory (cp.async prefetch of the next
+// chunk during the current one). Thread (rg, cg): rows RPT rg .. RPT rg + RPT - 1 and columns
+// cg + 16 j (j < NT/16), so that for each j the 16 threads of a row group touch 16
+// consecutive columns: one shared-memory wavefront per read and 128-byte global stores. The
+// per-thread load positions do not change with q, so the index arithmetic (including the
+// slab division) is done once.
+constexpr int CG_QT = 32;
 
-constexpr int CG_PT = 32, CG_QT = 32;
-
-template <int NT>
+template <int RPT, int NT>
 __global__ void __launch_bounds__(256)
-k_cgemm_tw(TwMat M, int P, int Q, int C, long N, const float2* __restrict__ In, long inS, long inQ,
-           float2* __restrict__ Out, long outS, long outP, long outSplit) {
-    constexpr int CPT = NT / 16;  // columns per thread
-    __shared__ __align__(16) float2 Ms[CG_QT][CG_PT];
-    __shared__ __align__(16) float2 Is[CG_QT][NT];
+k_cgemm_tw(const float2* __restrict__ M, int P, int Q, int C, int N, const float2* __restrict__ In,
+           long inS, long inQ, float2* __restrict__ Out, long outS, long outP, long outSplit) {
+    constexpr int PT = 16 * RPT;
+    constexpr int CPT = NT / 16;         // columns per thread
+    constexpr int IROWS = 256 / NT;      // q rows of the input tile loaded per pass
+    constexpr int MROWS = 256 / PT;      // q rows of the matrix tile loaded per pass
+    __shared__ __align__(16) float2 Ms[2][CG_QT][PT];
+    __shared__ __align__(16) float2 Is[2][CG_QT][NT];
     const int tid = threadIdx.x, rg = tid >> 4, cg = tid & 15;
-    const long n0 = (long)blockIdx.x * NT;
-    const int p0 = blockIdx.y * CG_PT;
+    const int n0 = blockIdx.x * NT;
+    const int p0 = blockIdx.y * PT;
     const int qsplit = gridDim.z;
     const int qlen = (Q + qsplit - 1) / qsplit;
     const int qb = blockIdx.z * qlen, qe = min(Q, qb + qlen);
-    float ar[2][CPT], ai[2][CPT];
+    // load positions: matrix tile column pl (rows ql0 + MROWS r), input tile column nl (rows
+    // qi0 + IROWS r)
+    const int pl = tid % PT, ql0 = tid / PT;
+    const bool pok = p0 + pl < P;
+    const int nl = tid % NT, qi0 = tid / NT;
+    const int nload = n0 + nl;
+    const bool nok = nload < N;
+    const int sl = nok ? nload / C : 0;
+    const float2* inp = In + (long)sl * inS + (nload - sl * C);
+    // asynchronous copy of the chunk starting at q0 into buffer b (zero fill outside)
+    auto issue = [&](int b, int q0) {
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+        for (int r = 0; r < CG_QT / MROWS; ++r) {
+            const int ql = ql0 + MROWS * r, q = q0 + ql;
+            const bool ok = pok && q < qe;
+            cp_async8(&Ms[b][ql][pl], ok ? M + (long)q * P + p0 + pl : M, ok);
+        }
+#pragma unroll
+        for (int r = 0; r < CG_QT / IROWS; ++r) {
+            const int ql = qi0 + IROWS * r, q = q0 + ql;
+            const bool ok = nok && q < qe;
+            cp_async8(&Is[b][ql][nl], ok ? inp + (long)q * inQ : In, ok);
+        }
+        asm volatile("cp.async.commit_group;\n" ::: "memory");
+    };
+    float ar[RPT][CPT], ai[RPT][CPT];
+#pragma unroll
+    for (int i = 0; i < RPT; ++i)
 #pragma unroll
         for (int j = 0; j < CPT; ++j) ar[i][j] = ai[i][j] = 0.f;
-    for (int q0 = qb; q0 < qe; q0 += CG_QT) {
-        __syncthreads();
-        for (int e = tid; e < CG_QT * CG_PT; e += 256) {
-            const int ql = e / CG_PT, pl = e - ql * CG_PT;
-            const int p = p0 + pl, q = q0 + ql;
-            float2 v = make_float2(0.f, 0.f);
-            if (p < P && q < qe) {
-                const int m = M.mode_is_p ? p : q, x = M.mode_is_p ? q : p;
-                if (!(M.zero_mode0 && m == 0)) {
-                    const long o = (long)m * M.len + x;
-                    v = make_float2(M.cosT[o], M.sgn * M.sinT[o]);
-                }
-            }
-            Ms[ql][pl] = v;
+    // one q step: the thread's RPT matrix entries (broadcast reads) times its CPT inputs
+    auto step = [&](int b, int ql) {
+        float2 mv[RPT];
+#pragma unroll
+        for (int i = 0; i < RPT; i += 2) {
+            const float4 m4 = *reinterpret_cast<const float4*>(&Ms[b][ql][RPT * rg + i]);
+            mv[i] = make_float2(m4.x, m4.y);
+            mv[i + 1] = make_float2(m4.z, m4.w);
         }
-        for (int e = tid; e < CG_QT * NT; e += 256) {
-            const int ql = e / NT, nl = e - ql * NT;
-            const long n = n0 + nl;
-            const int q = q0 + ql;
-            float2 v = make_float2(0.f, 0.f);
-            if (n < N && q < qe) {
-                const long sl = n / C;
-                v = In[sl * inS + (long)q * inQ + (n - sl * C)];
+        float2 iv[CPT];
+#pragma unroll
+        for (int j = 0; j < CPT; ++j) iv[j] = Is[b][ql][cg + 16 * j];
+#pragma unroll
+        for (int i = 0; i < RPT; ++i)
+#pragma unroll
+            for (int j = 0; j < CPT; ++j) {
+                ar[i][j] = fmaf(mv[i].x, iv[j].x, fmaf(-mv[i].y, iv[j].y, ar[i][j]));
+                ai[i][j] = fmaf(mv[i].x, iv[j].y, fmaf(mv[i].y, iv[j].x, ai[i][j]));
             }
-            Is[ql][nl] = v;
+    };
+    if (qb < qe) issue(0, qb);
+    for (int q0 = qb, b = 0; q0 < qe; q0 += CG_QT, b ^= 1) {
+        if (q0 + CG_QT < qe) {
+            issue(b ^ 1, q0 + CG_QT);   // buffer b ^ 1 was last read before the previous barrier
+            asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+        } else {
+            asm volatile("cp.async.wait_group 0;\n" ::: "memory");
         }
         __syncthreads();
         const int qn = min(CG_QT, qe - q0);
-        for (int ql = 0; ql < qn; ++ql) {
-            const float4 m4 = *reinterpret_cast<const float4*>(&Ms[ql][2 * rg]);
-            const float2 mv[2] = {make_float2(m4.x, m4.y), make_float2(m4.z, m4.w)};
-            float2 iv[CPT];
+        if (qn == CG_QT) {
 #pragma unroll
-            for (int j = 0; j < CPT; j += 2) {
-                const float4 t = *reinterpret_cast<const float4*>(&Is[ql][cg * CPT + j]);
-                iv[j] = make_float2(t.x, t.y);
-                iv[j + 1] = make_float2(t.z, t.w);
-            }
-#pragma unroll
-            for (int i = 0; i < 2; ++i)
-#pragma unroll
-                for (int j = 0; j < CPT; ++j) {
-                    ar[i][j] = fmaf(mv[i].x, iv[j].x, fmaf(-mv[i].y, iv[j].y, ar[i][j]));
-                    ai[i][j] = fmaf(mv[i].x, iv[j].y, fmaf(mv[i].y, iv[j].x, ai[i][j]));
-                }
+            for (int ql = 0; ql < CG_QT; ++ql) step(b, ql);
+        } else {
+            for (int ql = 0; ql < qn; ++ql) step(b, ql);
         }
+        __syncthreads();
     }
     float2* out = Out + (long)blockIdx.z * outSplit;
 #pragma unroll
-    for (int i = 0; i < 2; ++i) {
-        const int p = p0 + 2 * rg + i;
-        if (p >= P) continue;
+    for (int j = 0; j < CPT; ++j) {
+        const int n = n0 + cg + 16 * j;
+        if (n >= N) continue;
+        const int s = n / C;
+        float2* o = out + (long)s * outS + (n - s * C);
 #pragma unroll
-        for (int j = 0; j < CPT; ++j) {
-            const long n = n0 + cg * CPT + j;
-            if (n >= N) continue;
-            const long sl = n / C;
-            out[sl * outS + (long)p * outP + (n - sl * C)] = make_float2(ar[i][j], ai[i][j]);
+        for (int i = 0; i < RPT; ++i) {
+            const int p = p0 + RPT * rg + i;
+            if (p < P) o[(long)p * outP] = make_float2(ar[i][j], ai[i][j]);
         }
     }
 }
 
-// Launches k_cgemm_tw: NT = 32 when the column count alone would leave SMs idle.
-static int cgemm_tw(const TwMat& M, int P, int Q, int C, long nslab, const float2* In, long inS,
+// Launches k_cgemm_tw: 64 x 32 CTA tiles (4 x 2 per thread) when P fills 64-row tiles, else
+// 32 x 64 (2 x 4), or 32 x 32 when 64-column tiles would leave SMs idle. Static shared memory
+// stays within 48 KB (two buffers of (PT + NT) x 32 complex).
+static int cgemm_tw(const float2* M, int P, int Q, int C, long nslab, const float2* In, long inS,
                     long inQ, float2* Out, long outS, long outP, int qsplit, long outSplit,
                     const char* name, double bytes, cudaStream_t st) {
     const long N = nslab * C;
-    const long tiles64 = ((N + 63) / 64) * ((P + CG_PT - 1) / CG_PT) * qsplit;
+    if (N > 0x7fffffffL) {
+        set_error("spectral: too many columns in a Y/Z stage");
+        return LDDMM_EINVAL;
+    }
     KTRACE(name, st, bytes, 8.0 * P * (double)Q * N);
-    if (tiles64 < 2 * 148) {
-        dim3 grid((unsigned)((N + 31) / 32), (P + CG_PT - 1) / CG_PT, qsplit);
-        k_cgemm_tw<32><<<grid, 256, 0, st>>>(M, P, Q, C, N, In, inS, inQ, Out, outS, outP, outSplit);
+    const unsigned nt64 = (unsigned)((N + 63) / 64), nt32 = (unsigned)((N + 31) / 32);
+    if (P > 48) {
+        dim3 grid(nt32, (P + 63) / 64, qsplit);
+        k_cgemm_tw<4, 32><<<grid, 256, 0, st>>>(M, P, Q, C, (int)N, In, inS, inQ, Out, outS, outP, outSplit);
+    } else if ((long)nt64 * ((P + 31) / 32) * qsplit >= 2 * 148) {
+        dim3 grid(nt64, (P + 31) / 32, qsplit);
+        k_cgemm_tw<2, 64><<<grid, 256, 0, st>>>(M, P, Q, C, (int)N, In, inS, inQ, Out, outS, outP, outSplit);
     } else {
-        dim3 grid((unsigned)((N + 63) / 64), (P + CG_PT - 1) / CG_PT, qsplit);
-        k_cgemm_tw<64><<<grid, 256, 0, st>>>(M, P, Q, C, N, In, inS, inQ, Out, outS, outP, outSplit);
+        dim3 grid(nt32, (P + 31) / 32, qsplit);
+        k_cgemm_tw<2, 32><<<grid, 256, 0, st>>>(M, P, Q, C, (int)N, In, inS, inQ, Out, outS, outP, outSplit);
     }
     LDDMM_CHECK_LAUNCH();
     return LDDMM_OK;
@@ -425,18 +486,16 @@ int bl_project(const Grid& g, const Twiddles& tw, const float* f, long fstride, 
     if (rc) return rc;
     // stage Y: B[comp, z][jy][kx] = sum_y e^{-i ky y} A[comp, z][y][kx]
     {
-        const TwMat My{tw.cy, tw.sy, g.ny, -1.f, true, false};
         const long nslab = (long)ncomp * g.nz;
-        rc = cgemm_tw(My, K, g.ny, KH, nslab, s1, (long)g.ny * KH, KH, s2, (long)K * KH, KH, 1, 0,
+        rc = cgemm_tw(tw.mpy, K, g.ny, KH, nslab, s1, (long)g.ny * KH, KH, s2, (long)K * KH, KH, 1, 0,
                       "pi_y", (double)nslab * (g.ny + K) * KH * 8.0, st);
         if (rc) return rc;
     }
     // stage Z: z-block partial sums part[split][comp][jz][col] into s1 (free after stage Y)
     const int zsplit = std::max(1, std::min(8, g.nz / K));
     {
-        const TwMat Mz{tw.cz, tw.sz, g.nz, -1.f, true, false};
         const long ncol = (long)K * KH;
-        rc = cgemm_tw(Mz, K, g.nz, (int)ncol, ncomp, s2, g.nz * ncol, ncol, s1, K * ncol, ncol, zsplit,
+        rc = cgemm_tw(tw.mpz, K, g.nz, (int)ncol, ncomp, s2, g.nz * ncol, ncol, s1, K * ncol, ncol, zsplit,
                       (long)ncomp * K * ncol, "pi_z",
                       (double)ncomp * g.nz * ncol * 8.0 + (double)zsplit * ncomp * K * ncol * 8.0, st);
         if (rc) return rc;
@@ -564,8 +623,7 @@ static int launch_iota_zy2(const Grid& g, const Twiddles& tw, const float2* c, i
     LDDMM_CHECK_LAUNCH();
     // stage Y: T2[plane][y][kx] = sum_{jy >= 1} e^{+i ky y} T1[plane][jy][kx]
     const long nplanes = (long)nout * g.nz;
-    const TwMat My{tw.cy, tw.sy, g.ny, 1.f, false, true};
-    return cgemm_tw(My, g.ny, K, KH, nplanes, T1, (long)K * KH, KH, T2, (long)g.ny * KH, KH, 1, 0,
+    return cgemm_tw(tw.miy, g.ny, K, KH, nplanes, T1, (long)K * KH, KH, T2, (long)g.ny * KH, KH, 1, 0,
                     "iota_y", (double)nplanes * (K + g.ny) * KH * 8.0, st);
 }
 
