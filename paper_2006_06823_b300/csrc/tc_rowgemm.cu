@@ -7,10 +7,10 @@
 //
 // Both are dense contractions with a small fixed W, so they run on the 5th-generation tensor
 // cores: a persistent CTA per SM keeps W (split into hi + lo operands) resident in shared
-// memory, TMA streams 128-row x 32-column FP32 tiles of IN into a 4-stage ring (128-byte
-// swizzle, the K-major layout the MMA reads), four warps split each tile into hi and lo
-// parts in place, one thread issues tcgen05.mma into a TMEM accumulator, and the warps read
-// the accumulator back with tcgen05.ld for the epilogue store.
+// memory, TMA streams 128-row x 32-column FP32 tiles of IN into a 4-stage ring (128-byte swizzle, the K-major layout the MMA reads), four warps split each
+// tile into hi and lo parts, one thread issues tcgen05.mma into a double-buffered TMEM
+// accumulator, and four further warps read the accumulator back with tcgen05.ld and store it
+// through TMA while the next tile is being split.
 //
 // Precision: FP32 inputs are represented as hi + lo with hi = x rounded to TF32 (low 13
 // mantissa bits cleared) and lo = x - hi (exact in FP32); A*B ~ Ah*Bh + Ah*Bl + Al*Bh, FP32
@@ -189,36 +189,40 @@ __device__ __forceinline__ void tma_store_3d(const CUtensorMap* map, const void*
     asm volatile("cp.async.bulk.commit_group;\n" ::: "memory");
 }
 
-__device__ __forceinline__ void workers_sync() {
+// named barrier of the four epilogue warps
+__device__ __forceinline__ void epi_sync() {
     asm volatile("bar.sync 1, 128;\n" ::: "memory");
 }
 
-constexpr int NWORK = 4;                 // split + epilogue warps
-constexpr int WARP_TMA = NWORK;          // TMA producer warp
-constexpr int WARP_MMA = NWORK + 1;      // MMA issuer (and TMEM owner)
-constexpr int NTHREADS_WS = 32 * (NWORK + 2);
+constexpr int NWORK = 4;                 // split warps 0..3
+constexpr int NEPI = 4;                  // epilogue warps 4..7 (TMEM lane quarters 0..3)
+constexpr int WARP_TMA = NWORK + NEPI;   // TMA producer warp
+constexpr int WARP_MMA = WARP_TMA + 1;   // MMA issuer (and TMEM owner)
+constexpr int NTHREADS_WS = 32 * (NWORK + NEPI + 2);
 constexpr int NRAW_MAX = 6;
-constexpr int NOP = 2;                   // split-operand ring (released by MMA completion)
+constexpr int NOP_MAX = 4;               // split-operand ring (released by MMA completion)
 constexpr int TILE_B = TM * 128;         // 16 KB
-// TMA landing ring depth. TF32: the landed FP32 tile is itself the hi operand (the tensor core
-// reads only the upper 19 bits of a TF32 operand, i.e. the truncation hi = x with its low 13
-// mantissa bits cleared), so only lo = x - hi is materialised and a raw slot is released by
-// MMA completion; the smem freed by not storing hi deepens the ring from 4 to 6 tiles.
-// BF16: hi and lo are both materialised and the raw slot is released after the split.
-__host__ __device__ constexpr int nraw(int prec) { return prec == 0 ? 6 : 4; }
+// Ring depths. TF32: the landed FP32 tile is itself the hi operand (the tensor core reads
+// only the upper 19 bits of a TF32 operand, i.e. the truncation hi = x with its low 13
+// mantissa bits cleared), so only lo = x - hi is materialised (4 raw + 4 lo tiles) and a
+// raw slot is released by MMA completion. BF16: hi and lo are both materialised (4 raw + 2 x
+// 2 operand tiles) and the raw slot is released after the split.
+__host__ __device__ constexpr int nraw(int prec) { return 4; }
+__host__ __device__ constexpr int nop(int prec) { return prec == 0 ? 4 : 2; }
 __host__ __device__ constexpr int nop_planes(int prec) { return prec == 0 ? 1 : 2; }
 
 }  // namespace
 
 // Warp-specialised pipeline. Chunk q: tile t = q / nchunk, column block c = q % nchunk.
 //   producer : wait raw_empty[q%NRAW], TMA 128 x 32 tile -> raw[q%NRAW]
-//   workers  : wait raw_full, wait op_empty[q%NOP]; split raw -> op (TF32: lo only; BF16: hi
-//              and lo, then arrive raw_empty); arrive op_full; after the first chunk of tile
-//              t, epilogue of tile t-1
+//   split    : (warps 0-3) wait raw_full, wait op_empty[q%NOP]; split raw -> op (TF32: lo
+//              only; BF16: hi and lo, then arrive raw_empty); arrive op_full
 //   MMA warp : wait op_full (and, for c == 0, accempty of TMEM buffer t&1); 3 x k-step MMAs
 //              (TF32: A hi read straight from raw); commit -> op_empty (TF32: and raw_empty);
 //              last chunk of the tile: commit -> accfull[t&1]
-//   epilogue : TMEM 32-column blocks -> swizzled staging (2 buffers) -> TMA store
+//   epilogue : (warps 4-7, concurrent with the split of the next tile) wait accfull[t&1];
+//              TMEM 32-column blocks -> swizzled staging (2 buffers) -> TMA store; arrive
+//              accempty[t&1]
 // OUT is the 3-D tensor [ncomp][rpc][n_out] behind tmap_out (rows r = comp * rpc + local).
 // PREC 0: TF32 hi + lo (4 k-steps of 8 per 32-column chunk). PREC 1: BF16 hi + lo, the 32
 // elements of a chunk in the first 64 bytes of each 128-byte operand row (2 k-steps of 16).
@@ -229,7 +233,8 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
              float* __restrict__ out, long rpc, long comp_stride, int n_out, unsigned tmem_cols) {
     extern __shared__ unsigned char smem_raw[];
     constexpr int NRAW = nraw(PREC);
-    __shared__ uint64_t raw_full[NRAW_MAX], raw_empty[NRAW_MAX], op_full[NOP], op_empty[NOP], w_bar;
+    constexpr int NOP = nop(PREC);
+    __shared__ uint64_t raw_full[NRAW_MAX], raw_empty[NRAW_MAX], op_full[NOP_MAX], op_empty[NOP_MAX], w_bar;
     __shared__ uint64_t accfull_bar[2], accempty_bar[2];
     __shared__ unsigned tmem_holder;
     __shared__ volatile int abort_flag;
@@ -259,7 +264,7 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
         }
         for (int b = 0; b < 2; ++b) {
             mbar_init(&accfull_bar[b], 1);
-            mbar_init(&accempty_bar[b], NWORK);
+            mbar_init(&accempty_bar[b], NEPI);
         }
         abort_flag = 0;
         consumed_sh = 0;
@@ -362,57 +367,64 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
                 if (c == nchunk - 1) mma_commit(&accfull_bar[b]);
             }
         }
-    } else {
-        // ---------------------------------------------------------------- workers
-        const int wt = tid;  // 0 .. 127: the tile row this thread stores in the epilogue
-        long sblock = 0;     // staging blocks used so far (buffer = sblock & 1)
-        auto epilogue = [&](long t) -> bool {
+    } else if (warp >= NWORK) {
+        // ---------------------------------------------------------------- epilogue warps
+        const int et = tid - 32 * NWORK;   // 0 .. 127: the tile row this thread stores
+        const int quarter = warp - NWORK;  // TMEM lanes 32 quarter .. 32 quarter + 31
+        long sblock = 0;                   // staging blocks used so far (buffer = sblock & 1)
+        for (long t = 0; t < my_tiles && !abort_flag; ++t) {
             const int b = (int)(t & 1);
-            if (!mbar_wait(&accfull_bar[b], (unsigned)((t >> 1) & 1))) return false;
+            if (!mbar_wait(&accfull_bar[b], (unsigned)((t >> 1) & 1))) {
+                abort_flag = 1;
+                break;
+            }
             fence_after();
             const long tg = blockIdx.x + t * gridDim.x;
             const long row0 = tg * TM;
             const long comp0 = row0 / rpc;
             const long local0 = row0 - comp0 * rpc;
             const long split = rpc - local0;  // tile rows at or past `split` belong to comp0 + 1
-            const long row = row0 + wt;
+            const long row = row0 + et;
             for (int c0 = 0; c0 < N; c0 += 32) {
                 float v[32];
-                tmem_ld32(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)(b * N + c0), v);
+                tmem_ld32(tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)(b * N + c0), v);
                 unsigned char* sb = stg + (size_t)(sblock & 1) * TILE_B;
                 // the store issued two blocks ago from this buffer must have read it
-                if (wt == 0) asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
-                workers_sync();
+                if (et == 0) asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
+                epi_sync();
 #pragma unroll
                 for (int j = 0; j < 8; ++j)
-                    *reinterpret_cast<float4*>(sb + sw128_off(wt, j * 16)) =
+                    *reinterpret_cast<float4*>(sb + sw128_off(et, j * 16)) =
                         make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-                workers_sync();
-                if (wt == 0)
+                epi_sync();
+                if (et == 0)
                     tma_store_3d(&tmap_out, sb, c0, (int)local0, (int)comp0);
                 // rows of a second component (only when a tile straddles a component boundary)
-                if (wt >= split && row < rows) {
-                    float* dst = out + (comp0 + 1) * comp_stride + (wt - split) * n_out + c0;
+                if (et >= split && row < rows) {
+                    float* dst = out + (comp0 + 1) * comp_stride + (et - split) * n_out + c0;
                     const int nv = min(32, n_out - c0);
-                    for (int i = 0; i < nv; ++i) dst[i] = v[i];
+#pragma unroll
+                    for (int i = 0; i < 32; ++i)
+                        if (i < nv) dst[i] = v[i];
                 }
                 ++sblock;
             }
             fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&accempty_bar[b]);
-            return true;
-        };
-        bool ok = true;
-        for (long q = 0; q < total && ok; ++q) {
+        }
+        if (et == 0) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
+    } else {
+        // ---------------------------------------------------------------- split warps
+        const int wt = tid;  // 0 .. 127
+        for (long q = 0; q < total; ++q) {
             const int s = (int)(q % NRAW);
             const int o = (int)(q % NOP);
             if (!mbar_wait(&raw_full[s], (unsigned)((q / NRAW) & 1)) ||
                 (q >= NOP && !mbar_wait(&op_empty[o], (unsigned)(((q / NOP) - 1) & 1))) ||
                 abort_flag) {
                 abort_flag = 1;
-                ok = false;
                 break;
             }
             const float4* src = reinterpret_cast<const float4*>(raw + (size_t)s * TILE_B);
@@ -443,15 +455,7 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
                 mbar_arrive(&op_full[o]);
             }
             if (wt == 0) consumed_sh = q + 1;
-            const int c = (int)(q % nchunk);
-            const long t = q / nchunk;
-            if (c == 0 && t >= 1 && !epilogue(t - 1)) {
-                abort_flag = 1;
-                ok = false;
-            }
         }
-        if (ok && my_tiles > 0 && !abort_flag && !epilogue(my_tiles - 1)) abort_flag = 1;
-        if (wt == 0) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
     }
 
     __syncthreads();
@@ -544,8 +548,8 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 // both precisions come to 10 tiles besides W
 int tc_smem_bytes(int N, int kdim) {
     const int nchunk = (kdim + CHUNK - 1) / CHUNK;
-    static_assert(nraw(0) + nop_planes(0) * NOP == nraw(1) + nop_planes(1) * NOP, "ring sizes");
-    return 2 * nchunk * N * 128 + (nraw(1) + nop_planes(1) * NOP + 2) * TILE_B + 1024;
+    static_assert(nraw(0) + nop_planes(0) * nop(0) == nraw(1) + nop_planes(1) * nop(1), "ring sizes");
+    return 2 * nchunk * N * 128 + (nraw(1) + nop_planes(1) * nop(1) + 2) * TILE_B + 1024;
 }
 
 }  // namespace
