@@ -550,6 +550,40 @@ def run_batch(args):
             "identical_to_sequential": same, "gpu_launches": launches}
 
 
+def run_spectral(args):
+    """Operator throughput of the band-limited projection and inclusion (three components at
+    the paper-scale grid, K = 32) in the FP32 and BF16X3 forms, per kernel from the library's
+    trace; not a bench line of the headline metric."""
+    import torch
+    import paper_2006_06823_b300 as L
+    torch.cuda.set_device(0)
+    nz, ny, nx = SHAPE
+    f = torch.rand((3, nz, ny, nx), device="cuda")
+    c = L.bl_project(f, K)
+    out = torch.empty_like(f)
+    res = {}
+    for name, prec in (("fp32", L.PREC_FP32), ("bf16x3", L.PREC_BF16X3)):
+        for _ in range(args.warmup):
+            L.bl_project(f, K, precision=prec, out=c)
+            L.bl_include(c, SHAPE, precision=prec, out=out)
+        torch.cuda.synchronize()
+        L.trace_reset()
+        L.trace_enable(True)
+        for _ in range(args.steps):
+            L.bl_project(f, K, precision=prec, out=c)
+            L.bl_include(c, SHAPE, precision=prec, out=out)
+        tr = L.trace_read()
+        L.trace_enable(False)
+        res[name] = {k: {"us_per_launch": v["ms"] / v["launches"] * 1e3,
+                         "GB_s": v["bytes"] / (v["ms"] * 1e-3) / 1e9,
+                         "TFLOP_s": v["flops"] / (v["ms"] * 1e-3) / 1e12}
+                     for k, v in tr.items() if k != "twiddle"}
+    return {"metric": "band-limited projection + inclusion, 3 components (per-kernel us)",
+            "unit": "us", "impl": "b300", "steps": args.steps, "warmup": args.warmup,
+            "config": {"workload": f"pi and iota of 3 random fields, {nx}x{ny}x{nz}, K={K}"},
+            "kernels": res}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -559,7 +593,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", dest="forms", action="store_false",
                     help="skip the other forms of the workload and the warm-start comparison")
-    ap.add_argument("--config", default="paper", choices=["paper", "batch"])
+    ap.add_argument("--config", default="paper", choices=["paper", "batch", "spectral"])
     ap.add_argument("--pairs", type=int, default=64)
     ap.add_argument("--batch-threads", type=int, default=16)
     ap.add_argument("--grid", type=int, nargs=3, metavar=("NZ", "NY", "NX"), default=None,
@@ -570,6 +604,8 @@ def main():
         SHAPE = tuple(args.grid)
     if args.config == "batch" and args.impl == "b300":
         out = run_batch(args)
+    elif args.config == "spectral" and args.impl == "b300":
+        out = run_spectral(args)
     else:
         out = run_reference(args) if args.impl == "reference" else run_b300(args)
     if out is not None:

@@ -513,21 +513,22 @@ int bl_project(const Grid& g, const Twiddles& tw, const float* f, long fstride, 
 // ------------------------------------------------- iota stage Z (GEMM over all planes)
 // T1[comp][z][j] = sum_{jz>=1} Ez[z][jz] * m(k) c[comp][jz][jy][K/2+kx],  j = jy*KH + kx,
 // with m(k) the derivative / divergence multiplier and 1/B^(k) for B-spline coefficients.
-// CTA tile: 32 planes x 64 columns; thread: 4 planes x 2 columns (8 complex accumulators).
-constexpr int Z2_ZT = 32, Z2_JT = 64;
+// CTA tile: 32 planes x 32 columns (128 threads, so that 192-plane grids still fill the SMs);
+// thread: 4 planes x 2 columns (8 complex accumulators).
+constexpr int Z2_ZT = 32, Z2_JT = 32, Z2_THREADS = (Z2_JT / 2) * (Z2_ZT / 4);
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(Z2_THREADS)
 k_iota_z2(const float2* __restrict__ c, int nz, int ny, int nx, int K, int KH, int deriv_axis,
           int bspline, const float* __restrict__ cxT, const float* __restrict__ cyT,
           const float* __restrict__ czT, const float* __restrict__ szT, float2* __restrict__ T1) {
-    __shared__ float4 cs4[32 * Z2_JT / 2];   // [jz][64] float2 (K <= 64 -> 2 passes if K > 32)
-    __shared__ float4 es4[32 * Z2_ZT / 2];   // [jz][32] float2
+    __shared__ float4 cs4[32 * Z2_JT / 2];   // [jz][Z2_JT] float2 (K <= 64 -> 2 passes if K > 32)
+    __shared__ float4 es4[32 * Z2_ZT / 2];   // [jz][Z2_ZT] float2
     float2* cs = reinterpret_cast<float2*>(cs4);
     float2* es = reinterpret_cast<float2*>(es4);
     const int comp = blockIdx.z;
     const int z0 = blockIdx.x * Z2_ZT, j0 = blockIdx.y * Z2_JT;
     const int KK = K * KH, h = K / 2;
-    const int tid = threadIdx.x, jq = tid & 31, zq = tid >> 5;   // 32 x 8
+    const int tid = threadIdx.x, jq = tid % (Z2_JT / 2), zq = tid / (Z2_JT / 2);
     float ar[4][2], ai[4][2];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
@@ -537,7 +538,7 @@ k_iota_z2(const float2* __restrict__ c, int nz, int ny, int nx, int K, int KH, i
     for (int jzb = 0; jzb < K; jzb += 32) {
         const int nj = min(32, K - jzb);
         __syncthreads();
-        for (int e = tid; e < 32 * Z2_JT; e += 256) {
+        for (int e = tid; e < 32 * Z2_JT; e += Z2_THREADS) {
             const int jzl = e / Z2_JT, jj = e - jzl * Z2_JT;
             const int jz = jzb + jzl, j = j0 + jj;
             float2 v = make_float2(0.f, 0.f);
@@ -574,7 +575,7 @@ k_iota_z2(const float2* __restrict__ c, int nz, int ny, int nx, int K, int KH, i
             }
             cs[e] = v;
         }
-        for (int e = tid; e < 32 * Z2_ZT; e += 256) {
+        for (int e = tid; e < 32 * Z2_ZT; e += Z2_THREADS) {
             const int jzl = e / Z2_ZT, zz = e - jzl * Z2_ZT;
             const int jz = jzb + jzl, z = z0 + zz;
             es[e] = (jzl < nj && z < nz) ? make_float2(czT[(long)jz * nz + z], szT[(long)jz * nz + z])
@@ -617,7 +618,7 @@ static int launch_iota_zy2(const Grid& g, const Twiddles& tw, const float2* c, i
         KTRACE("iota_z", st, (double)(deriv_axis == 3 ? 3 : nout) * K * K * KH * 8.0 +
                                  (double)nout * g.nz * KK * 8.0,
                (double)nout * g.nz * KK * K * 8.0);
-        k_iota_z2<<<grid, 256, 0, st>>>(c, g.nz, g.ny, g.nx, K, KH, deriv_axis, bspline, tw.cx,
+        k_iota_z2<<<grid, Z2_THREADS, 0, st>>>(c, g.nz, g.ny, g.nx, K, KH, deriv_axis, bspline, tw.cx,
                                         tw.cy, tw.cz, tw.sz, T1);
     }
     LDDMM_CHECK_LAUNCH();

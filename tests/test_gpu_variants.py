@@ -44,7 +44,10 @@ def gpu_context(prob, **kw):
 
 CASES = [((16, 16, 16), 8, Vn.DEFSTATE, 1), ((16, 16, 16), 8, Vn.DEFSTATE, 3),
          ((16, 16, 16), 8, Vn.IMAGE, 1), ((16, 16, 16), 8, Vn.IMAGE, 3),
-         ((20, 24, 28), 10, Vn.DEFSTATE, 1), ((20, 24, 28), 10, Vn.IMAGE, 1)]
+         ((20, 24, 28), 10, Vn.DEFSTATE, 1), ((20, 24, 28), 10, Vn.IMAGE, 1),
+         # K = 16 with nx = 32: the x stages of pi and iota run on the tensor cores
+         ((24, 20, 32), 16, Vn.DEFSTATE, 1), ((24, 20, 32), 16, Vn.DEFSTATE, 3),
+         ((24, 20, 32), 16, Vn.IMAGE, 3)]
 
 
 @pytest.mark.parametrize("shape,K,variant,order", CASES)
