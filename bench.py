@@ -58,8 +58,10 @@ def is_hbm_kernel(name):
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
-# the kernel on this workload; None where no capture of the current kernel exists.
-NCU_TRAFFIC_PER_LAUNCH = {}
+# the kernel, scaled by voxels to the 192x224x192 launch where the capture ran a smaller grid
+# (profiles/k_inc_defstate_128x160x128.md: 268.2 MB at 128x160x128 -> 844.8 MB); kernels
+# without a capture of their current code are absent (reported as null).
+NCU_TRAFFIC_PER_LAUNCH = {"sl_inc_defstate": 844.8e6}
 
 
 def _peaks():
