@@ -207,8 +207,9 @@ constexpr int TILE_B = TM * 128;         // 16 KB
 // mantissa bits cleared), so only lo = x - hi is materialised (4 raw + 4 lo tiles) and a
 // raw slot is released by MMA completion. BF16: hi and lo are both materialised (4 raw + 2 x
 // 2 operand tiles) and the raw slot is released after the split.
-__host__ __device__ constexpr int nraw(int prec) { return 4; }
-__host__ __device__ constexpr int nop(int prec) { return prec == 0 ? 4 : 2; }
+// DEPTH 4, or 3 when the stage's W (hi + lo) is too large for the deeper rings (nx = 256).
+__host__ __device__ constexpr int nraw(int prec, int depth) { return depth; }
+__host__ __device__ constexpr int nop(int prec, int depth) { return prec == 0 ? depth : 2; }
 __host__ __device__ constexpr int nop_planes(int prec) { return prec == 0 ? 1 : 2; }
 
 }  // namespace
@@ -226,14 +227,14 @@ __host__ __device__ constexpr int nop_planes(int prec) { return prec == 0 ? 1 : 
 // OUT is the 3-D tensor [ncomp][rpc][n_out] behind tmap_out (rows r = comp * rpc + local).
 // PREC 0: TF32 hi + lo (4 k-steps of 8 per 32-column chunk). PREC 1: BF16 hi + lo, the 32
 // elements of a chunk in the first 64 bytes of each 128-byte operand row (2 k-steps of 16).
-template <int PREC>
+template <int PREC, int DEPTH>
 __global__ void __launch_bounds__(NTHREADS_WS, 1)
 k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant__ CUtensorMap tmap_out,
              const unsigned char* __restrict__ w_image, int N, int kdim, long rows,
              float* __restrict__ out, long rpc, long comp_stride, int n_out, unsigned tmem_cols) {
     extern __shared__ unsigned char smem_raw[];
-    constexpr int NRAW = nraw(PREC);
-    constexpr int NOP = nop(PREC);
+    constexpr int NRAW = nraw(PREC, DEPTH);
+    constexpr int NOP = nop(PREC, DEPTH);
     __shared__ uint64_t raw_full[NRAW_MAX], raw_empty[NRAW_MAX], op_full[NOP_MAX], op_empty[NOP_MAX], w_bar;
     __shared__ uint64_t accfull_bar[2], accempty_bar[2];
     __shared__ unsigned tmem_holder;
@@ -546,10 +547,18 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // W hi + lo, the raw ring, the split operands and two staging tiles (+ alignment slack);
 // both precisions come to 10 tiles besides W
-int tc_smem_bytes(int N, int kdim) {
+int tc_smem_bytes(int N, int kdim, int prec, int depth) {
     const int nchunk = (kdim + CHUNK - 1) / CHUNK;
-    static_assert(nraw(0) + nop_planes(0) * nop(0) == nraw(1) + nop_planes(1) * nop(1), "ring sizes");
-    return 2 * nchunk * N * 128 + (nraw(1) + nop_planes(1) * nop(1) + 2) * TILE_B + 1024;
+    return 2 * nchunk * N * 128 + (nraw(prec, depth) + nop_planes(prec) * nop(prec, depth) + 2) * TILE_B + 1024;
+}
+
+constexpr int kTcSmemLimit = 220 * 1024;
+
+// the deepest ring that fits (4, else 3); 0 if none
+int tc_depth(int N, int kdim, int prec) {
+    if (tc_smem_bytes(N, kdim, prec, 4) <= kTcSmemLimit) return 4;
+    if (tc_smem_bytes(N, kdim, prec, 3) <= kTcSmemLimit) return 3;
+    return 0;
 }
 
 }  // namespace
@@ -559,7 +568,7 @@ bool tc_rowgemm_supported(int N, int kdim, long rows, const void* in, long in_ro
     if (kdim < 1 || (in_row_floats % 4) != 0) return false;
     if ((reinterpret_cast<uintptr_t>(in) & 15) != 0) return false;
     if (rows < 1 || rows > 0x7fffffffL) return false;
-    if (tc_smem_bytes(N, kdim) > 220 * 1024) return false;
+    if (tc_depth(N, kdim, 0) == 0 || tc_depth(N, kdim, 1) == 0) return false;
     return encode_fn() != nullptr;
 }
 
@@ -594,16 +603,29 @@ int tc_rowgemm(const float* in, long rows, int kdim, long in_row_floats, const u
         set_error("tc_rowgemm: cuTensorMapEncodeTiled (output) failed (" + std::to_string((int)r) + ")");
         return LDDMM_ECUDA;
     }
-    const int smem = tc_smem_bytes(N, kdim);
-    static int attr_smem[2] = {0, 0};  // largest dynamic size requested so far
-    if (smem > attr_smem[prec]) {
-        if (prec == 0)
-            LDDMM_CUDA(cudaFuncSetAttribute(k_tc_rowgemm<0>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        else
-            LDDMM_CUDA(cudaFuncSetAttribute(k_tc_rowgemm<1>,
-                                            cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
-        attr_smem[prec] = smem;
+    const int depth = tc_depth(N, kdim, prec);
+    if (depth == 0) {
+        set_error("tc_rowgemm: W too large for shared memory");
+        return LDDMM_EINVAL;
+    }
+    const int smem = tc_smem_bytes(N, kdim, prec, depth);
+    {
+        // largest dynamic size requested so far per instantiation
+        static std::mutex mu;
+        static int attr_smem[2][2] = {{0, 0}, {0, 0}};
+        std::lock_guard<std::mutex> lock(mu);
+        int& cur = attr_smem[prec][depth == 4];
+        if (smem > cur) {
+            cudaError_t e;
+            if (prec == 0)
+                e = depth == 4 ? cudaFuncSetAttribute(k_tc_rowgemm<0, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
+                               : cudaFuncSetAttribute(k_tc_rowgemm<0, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            else
+                e = depth == 4 ? cudaFuncSetAttribute(k_tc_rowgemm<1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
+                               : cudaFuncSetAttribute(k_tc_rowgemm<1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+            LDDMM_CUDA(e);
+            cur = smem;
+        }
     }
     // two accumulators at columns 0 and N; the epilogue reads 32-column blocks, so the
     // second buffer's last block ends at N + roundup(N, 32)
@@ -625,12 +647,18 @@ int tc_rowgemm(const float* in, long rows, int kdim, long in_row_floats, const u
     const int grid = (int)std::min<long>(ntiles, nsm);
     {
         KTRACE(trace_name, st, trace_bytes, 2.0 * rows * (double)N * kdim);
-        if (prec == 0)
-            k_tc_rowgemm<0><<<grid, NTHREADS_WS, smem, st>>>(map, omap, W, N, kdim, rows, out, rpc,
-                                                            comp_stride, n_out, cols);
+        if (prec == 0 && depth == 4)
+            k_tc_rowgemm<0, 4><<<grid, NTHREADS_WS, smem, st>>>(map, omap, W, N, kdim, rows, out, rpc,
+                                                               comp_stride, n_out, cols);
+        else if (prec == 0)
+            k_tc_rowgemm<0, 3><<<grid, NTHREADS_WS, smem, st>>>(map, omap, W, N, kdim, rows, out, rpc,
+                                                               comp_stride, n_out, cols);
+        else if (depth == 4)
+            k_tc_rowgemm<1, 4><<<grid, NTHREADS_WS, smem, st>>>(map, omap, W, N, kdim, rows, out, rpc,
+                                                               comp_stride, n_out, cols);
         else
-            k_tc_rowgemm<1><<<grid, NTHREADS_WS, smem, st>>>(map, omap, W, N, kdim, rows, out, rpc,
-                                                            comp_stride, n_out, cols);
+            k_tc_rowgemm<1, 3><<<grid, NTHREADS_WS, smem, st>>>(map, omap, W, N, kdim, rows, out, rpc,
+                                                               comp_stride, n_out, cols);
     }
     LDDMM_CHECK_LAUNCH();
     return LDDMM_OK;

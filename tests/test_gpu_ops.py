@@ -130,7 +130,8 @@ def test_invalid_arguments_raise():
 
 # shapes that take the tensor-core x stages (K a multiple of 16, nx a multiple of 4; iota also
 # needs nx a multiple of 16): ragged row counts, a partial last K chunk, K = 16 and 32
-TC_CASES = [((33, 40, 64), 32), ((20, 24, 48), 16), ((40, 36, 100), 32), ((18, 20, 80), 16)]
+TC_CASES = [((33, 40, 64), 32), ((20, 24, 48), 16), ((40, 36, 100), 32), ((18, 20, 80), 16),
+            ((34, 36, 256), 32)]   # nx = 256: the shallower (3-deep) tensor-core rings
 
 
 @pytest.mark.parametrize("shape,K", TC_CASES)
