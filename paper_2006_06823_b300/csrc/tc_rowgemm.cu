@@ -94,6 +94,11 @@ __device__ __forceinline__ uint64_t sw128_desc(unsigned saddr) {
     return d;
 }
 
+// W images with 2N <= 256 keep each chunk's hi rows and lo rows adjacent ([hi N rows | lo N
+// rows]), so that A_hi * [B_hi | B_lo] is one MMA of width 2N and only A_lo * B_hi needs a
+// second (2 instead of 3 MMAs per k-step; the epilogue adds the two column halves).
+__host__ __device__ constexpr bool wcat(int N) { return 2 * N <= 256; }
+
 // kind::tf32, FP32 accumulate, both operands K-major, M = 128, N = n.
 __host__ __device__ constexpr uint32_t idesc_tf32(int n) {
     return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(TM >> 4) << 24);
@@ -194,8 +199,8 @@ __device__ __forceinline__ void epi_sync() {
     asm volatile("bar.sync 1, 128;\n" ::: "memory");
 }
 
-constexpr int NWORK = 4;                 // split warps 0..3
-constexpr int NEPI = 4;                  // epilogue warps 4..7 (TMEM lane quarters 0..3)
+constexpr int NWORK = 8;                 // split warps 0..7
+constexpr int NEPI = 4;                  // epilogue warps 8..11 (TMEM lane quarters 0..3)
 constexpr int WARP_TMA = NWORK + NEPI;   // TMA producer warp
 constexpr int WARP_MMA = WARP_TMA + 1;   // MMA issuer (and TMEM owner)
 constexpr int NTHREADS_WS = 32 * (NWORK + NEPI + 2);
@@ -302,6 +307,9 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
     const long my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const long total = my_tiles * nchunk;
     const uint32_t idesc = PREC == 0 ? idesc_tf32(N) : idesc_bf16(N);
+    const bool cat = wcat(N);
+    const int accw = cat ? 2 * N : N;    // accumulator columns per TMEM buffer
+    const uint32_t idesc_cat = PREC == 0 ? idesc_tf32(accw) : idesc_bf16(accw);
 
     if (warp == WARP_TMA) {
         if (lane == 0) {
@@ -337,20 +345,24 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
                 }
                 if (abort_flag) break;
                 fence_after();
-                const unsigned d = tmem + (unsigned)(b * N);
+                const unsigned d = tmem + (unsigned)(b * accw);
                 const int s = (int)(q % NRAW);
                 const unsigned ah = PREC == 0 ? smem_u32(raw + (size_t)s * TILE_B)
                                               : smem_u32(op_hi + (size_t)o * TILE_B);
                 const unsigned al = smem_u32(op_lo + (size_t)o * TILE_B);
-                const unsigned wh = smem_u32(w_hi + (size_t)c * N * 128);
-                const unsigned wl = smem_u32(w_lo + (size_t)c * N * 128);
+                const unsigned wh = smem_u32(w_hi + (size_t)c * (cat ? 2 * N : N) * 128);
+                const unsigned wl = cat ? wh + (unsigned)(N * 128) : smem_u32(w_lo + (size_t)c * N * 128);
                 if (PREC == 0) {
 #pragma unroll
                     for (int kk = 0; kk < CHUNK / 8; ++kk) {
                         const unsigned ko = kk * 32;
                         const unsigned acc = (c > 0 || kk > 0) ? 1u : 0u;
-                        mma_tf32(d, sw128_desc(ah + ko), sw128_desc(wh + ko), idesc, acc);
-                        mma_tf32(d, sw128_desc(ah + ko), sw128_desc(wl + ko), idesc, 1u);
+                        if (cat) {
+                            mma_tf32(d, sw128_desc(ah + ko), sw128_desc(wh + ko), idesc_cat, acc);
+                        } else {
+                            mma_tf32(d, sw128_desc(ah + ko), sw128_desc(wh + ko), idesc, acc);
+                            mma_tf32(d, sw128_desc(ah + ko), sw128_desc(wl + ko), idesc, 1u);
+                        }
                         mma_tf32(d, sw128_desc(al + ko), sw128_desc(wh + ko), idesc, 1u);
                     }
                 } else {
@@ -358,8 +370,12 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
                     for (int kk = 0; kk < CHUNK / 16; ++kk) {
                         const unsigned ko = kk * 32;
                         const unsigned acc = (c > 0 || kk > 0) ? 1u : 0u;
-                        mma_bf16(d, sw128_desc(ah + ko), sw128_desc(wh + ko), idesc, acc);
-                        mma_bf16(d, sw128_desc(ah + ko), sw128_desc(wl + ko), idesc, 1u);
+                        if (cat) {
+                            mma_bf16(d, sw128_desc(ah + ko), sw128_desc(wh + ko), idesc_cat, acc);
+                        } else {
+                            mma_bf16(d, sw128_desc(ah + ko), sw128_desc(wh + ko), idesc, acc);
+                            mma_bf16(d, sw128_desc(ah + ko), sw128_desc(wl + ko), idesc, 1u);
+                        }
                         mma_bf16(d, sw128_desc(al + ko), sw128_desc(wh + ko), idesc, 1u);
                     }
                 }
@@ -371,7 +387,7 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
     } else if (warp >= NWORK) {
         // ---------------------------------------------------------------- epilogue warps
         const int et = tid - 32 * NWORK;   // 0 .. 127: the tile row this thread stores
-        const int quarter = warp - NWORK;  // TMEM lanes 32 quarter .. 32 quarter + 31
+        const int quarter = (warp - NWORK) & 3;  // TMEM lanes 32 quarter .. 32 quarter + 31
         long sblock = 0;                   // staging blocks used so far (buffer = sblock & 1)
         for (long t = 0; t < my_tiles && !abort_flag; ++t) {
             const int b = (int)(t & 1);
@@ -388,7 +404,14 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
             const long row = row0 + et;
             for (int c0 = 0; c0 < N; c0 += 32) {
                 float v[32];
-                tmem_ld32(tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)(b * N + c0), v);
+                const unsigned trow = tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)(b * accw + c0);
+                tmem_ld32(trow, v);
+                if (cat) {   // + the A_hi * B_lo half
+                    float v2[32];
+                    tmem_ld32(trow + (unsigned)N, v2);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) v[i] += v2[i];
+                }
                 unsigned char* sb = stg + (size_t)(sblock & 1) * TILE_B;
                 // the store issued two blocks ago from this buffer must have read it
                 if (et == 0) asm volatile("cp.async.bulk.wait_group.read 1;\n" ::: "memory");
@@ -418,7 +441,7 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
         if (et == 0) asm volatile("cp.async.bulk.wait_group 0;\n" ::: "memory");
     } else {
         // ---------------------------------------------------------------- split warps
-        const int wt = tid;  // 0 .. 127
+        const int wt = tid;  // 0 .. 32 NWORK - 1
         for (long q = 0; q < total; ++q) {
             const int s = (int)(q % NRAW);
             const int o = (int)(q % NOP);
@@ -478,8 +501,9 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
                      "r"(tmem_cols));
 }
 
-// W (N x kdim FP32) -> its shared-memory operand image: hi then lo, each nchunk x N rows of
-// 128 bytes in the 128-byte-swizzled K-major layout (zero past kdim).
+// W (N x kdim FP32) -> its shared-memory operand image: hi and lo parts, each nchunk x N rows
+// of 128 bytes in the 128-byte-swizzled K-major layout (zero past kdim); per chunk [hi | lo]
+// when wcat(N), else all hi chunks then all lo chunks.
 template <int PREC>
 __global__ void k_build_wimage(const float* __restrict__ W, int N, int kdim,
                                unsigned char* __restrict__ img) {
@@ -492,17 +516,20 @@ __global__ void k_build_wimage(const float* __restrict__ W, int N, int kdim,
     const int kk = c * CHUNK + k;
     const float w = kk < kdim ? W[(long)n * kdim + kk] : 0.f;
     const size_t wbytes = (size_t)nchunk * N * 128;
+    // hi and lo blocks: adjacent per chunk (wcat) or two separate halves of the image
+    const size_t hbase = wcat(N) ? (size_t)c * 2 * N * 128 : (size_t)c * N * 128;
+    const size_t lbase = wcat(N) ? hbase + (size_t)N * 128 : wbytes + hbase;
     if (PREC == 0) {
         const float h = tf32_hi(w);
-        const unsigned off = (unsigned)((size_t)c * N * 128) + sw128_off(n, k * 4);
-        *reinterpret_cast<float*>(img + off) = h;
-        *reinterpret_cast<float*>(img + wbytes + off) = w - h;
+        const unsigned off = sw128_off(n, k * 4);
+        *reinterpret_cast<float*>(img + hbase + off) = h;
+        *reinterpret_cast<float*>(img + lbase + off) = w - h;
     } else {
         const __nv_bfloat16 h = __float2bfloat16_rn(w);
         const __nv_bfloat16 l = __float2bfloat16_rn(w - __bfloat162float(h));
-        const unsigned off = (unsigned)((size_t)c * N * 128) + sw128_off(n, k * 2);
-        *reinterpret_cast<__nv_bfloat16*>(img + off) = h;
-        *reinterpret_cast<__nv_bfloat16*>(img + wbytes + off) = l;
+        const unsigned off = sw128_off(n, k * 2);
+        *reinterpret_cast<__nv_bfloat16*>(img + hbase + off) = h;
+        *reinterpret_cast<__nv_bfloat16*>(img + lbase + off) = l;
     }
 }
 
@@ -629,7 +656,8 @@ int tc_rowgemm(const float* in, long rows, int kdim, long in_row_floats, const u
     }
     // two accumulators at columns 0 and N; the epilogue reads 32-column blocks, so the
     // second buffer's last block ends at N + roundup(N, 32)
-    const int need_cols = N + ((N + 31) / 32) * 32;
+    const int accw = wcat(N) ? 2 * N : N;
+    const int need_cols = accw + (wcat(N) ? N : 0) + ((N + 31) / 32) * 32;
     unsigned cols = 32;
     while ((int)cols < need_cols) cols <<= 1;
     if (cols > 512) {
