@@ -55,19 +55,26 @@ __device__ __forceinline__ unsigned long long now_ns() {
     return t;
 }
 
-// Parity wait bounded by wall-clock time; returns false on timeout.
+__device__ __forceinline__ bool mbar_try(unsigned a, unsigned parity) {
+    unsigned ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(a), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Parity wait bounded by wall-clock time; returns false on timeout. The clock is read only
+// once the phase has been found incomplete (a %globaltimer read is slow next to a
+// completed try_wait).
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
     const unsigned a = smem_u32(bar);
+    if (mbar_try(a, parity)) return true;
     const unsigned long long t0 = now_ns();
     for (unsigned it = 0;; ++it) {
-        unsigned ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-            " selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (ok) return true;
+        if (mbar_try(a, parity)) return true;
         if ((it & 255u) == 255u && now_ns() - t0 > kWaitLimitNs) return false;
     }
 }
@@ -215,6 +222,7 @@ constexpr int TILE_B = TM * 128;         // 16 KB
 // DEPTH 4, or 3 when the stage's W (hi + lo) is too large for the deeper rings (nx = 256).
 __host__ __device__ constexpr int nraw(int prec, int depth) { return depth; }
 __host__ __device__ constexpr int nop(int prec, int depth) { return prec == 0 ? depth : 2; }
+static_assert(nraw(0, 4) == nop(0, 4) && nraw(0, 3) == nop(0, 3), "TF32 rings share release barriers");
 __host__ __device__ constexpr int nop_planes(int prec) { return prec == 0 ? 1 : 2; }
 
 }  // namespace
@@ -224,7 +232,8 @@ __host__ __device__ constexpr int nop_planes(int prec) { return prec == 0 ? 1 : 
 //   split    : (warps 0-3) wait raw_full, wait op_empty[q%NOP]; split raw -> op (TF32: lo
 //              only; BF16: hi and lo, then arrive raw_empty); arrive op_full
 //   MMA warp : wait op_full (and, for c == 0, accempty of TMEM buffer t&1); 3 x k-step MMAs
-//              (TF32: A hi read straight from raw); commit -> op_empty (TF32: and raw_empty);
+//              (TF32: A hi read straight from raw); commit -> op_empty (TF32: which also frees
+//              raw slot q%NRAW, the two rings having equal depth);
 //              last chunk of the tile: commit -> accfull[t&1]
 //   epilogue : (warps 4-7, concurrent with the split of the next tile) wait accfull[t&1];
 //              TMEM 32-column blocks -> swizzled staging (2 buffers) -> TMA store; arrive
@@ -313,40 +322,52 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
 
     if (warp == WARP_TMA) {
         if (lane == 0) {
+            // ring slot s, its use count u, column block c and global tile t advance
+            // incrementally (no divisions in the issue loop)
+            int s = 0, c = 0;
+            unsigned u = 0;
+            long t = blockIdx.x;
             for (long q = 0; q < total; ++q) {
-                const int s = (int)(q % NRAW);
-                const long u = q / NRAW;
-                if (u > 0 && !mbar_wait(&raw_empty[s], (unsigned)((u - 1) & 1))) {
+                // TF32: raw slot s is operand slot s (equal ring depths), released by the same
+                // MMA commit as the lo tile
+                uint64_t* freed = PREC == 0 ? &op_empty[s] : &raw_empty[s];
+                if (u > 0 && !mbar_wait(freed, (u - 1) & 1)) {
                     abort_flag = 1;
                     break;
                 }
                 if (abort_flag) break;
-                const long t = blockIdx.x + (q / nchunk) * gridDim.x;
-                tma_load_2d(raw + (size_t)s * TILE_B, &tmap_in, (int)(q % nchunk) * CHUNK,
-                            (int)(t * TM), &raw_full[s], TILE_B);
+                tma_load_2d(raw + (size_t)s * TILE_B, &tmap_in, c * CHUNK, (int)(t * TM), &raw_full[s],
+                            TILE_B);
                 issued_sh = q + 1;
+                if (++s == NRAW) {
+                    s = 0;
+                    ++u;
+                }
+                if (++c == nchunk) {
+                    c = 0;
+                    t += gridDim.x;
+                }
             }
         }
     } else if (warp == WARP_MMA) {
         if (lane == 0) {
             if (total > 0 && !mbar_wait(&w_bar, 0)) abort_flag = 1;
+            int o = 0, c = 0, s = 0;
+            unsigned uo = 0;   // use count of operand slot o
+            long t = 0;        // local tile index
             for (long q = 0; q < total && !abort_flag; ++q) {
-                const int o = (int)(q % NOP);
-                const int c = (int)(q % nchunk);
-                const long t = q / nchunk;
                 const int b = (int)(t & 1);
                 if (c == 0 && t >= 2 && !mbar_wait(&accempty_bar[b], (unsigned)(((t >> 1) - 1) & 1))) {
                     abort_flag = 1;
                     break;
                 }
-                if (!mbar_wait(&op_full[o], (unsigned)((q / NOP) & 1))) {
+                if (!mbar_wait(&op_full[o], uo & 1)) {
                     abort_flag = 1;
                     break;
                 }
                 if (abort_flag) break;
                 fence_after();
                 const unsigned d = tmem + (unsigned)(b * accw);
-                const int s = (int)(q % NRAW);
                 const unsigned ah = PREC == 0 ? smem_u32(raw + (size_t)s * TILE_B)
                                               : smem_u32(op_hi + (size_t)o * TILE_B);
                 const unsigned al = smem_u32(op_lo + (size_t)o * TILE_B);
@@ -380,8 +401,16 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
                     }
                 }
                 mma_commit(&op_empty[o]);
-                if (PREC == 0) mma_commit(&raw_empty[s]);
                 if (c == nchunk - 1) mma_commit(&accfull_bar[b]);
+                if (++o == NOP) {
+                    o = 0;
+                    ++uo;
+                }
+                if (++s == NRAW) s = 0;
+                if (++c == nchunk) {
+                    c = 0;
+                    ++t;
+                }
             }
         }
     } else if (warp >= NWORK) {
@@ -442,11 +471,10 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
     } else {
         // ---------------------------------------------------------------- split warps
         const int wt = tid;  // 0 .. 32 NWORK - 1
+        int s = 0, o = 0;
+        unsigned us = 0, uo = 0;   // use counts of raw slot s and operand slot o
         for (long q = 0; q < total; ++q) {
-            const int s = (int)(q % NRAW);
-            const int o = (int)(q % NOP);
-            if (!mbar_wait(&raw_full[s], (unsigned)((q / NRAW) & 1)) ||
-                (q >= NOP && !mbar_wait(&op_empty[o], (unsigned)(((q / NOP) - 1) & 1))) ||
+            if (!mbar_wait(&raw_full[s], us & 1) || (uo > 0 && !mbar_wait(&op_empty[o], (uo - 1) & 1)) ||
                 abort_flag) {
                 abort_flag = 1;
                 break;
@@ -479,6 +507,14 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
                 mbar_arrive(&op_full[o]);
             }
             if (wt == 0) consumed_sh = q + 1;
+            if (++s == NRAW) {
+                s = 0;
+                ++us;
+            }
+            if (++o == NOP) {
+                o = 0;
+                ++uo;
+            }
         }
     }
 
