@@ -496,7 +496,7 @@ __device__ __forceinline__ float ldj(const __nv_bfloat16* p) { return __bfloat16
 
 // D~_t du~ = dv~ - D~u~ * dv~ (Table 1 row 7): F = dv - (Du) dv, Heun along X.
 template <int IP, typename TJ>
-__global__ void __launch_bounds__(256, IP == 3 ? 2 : 3)
+__global__ void __launch_bounds__(256, IP == 3 ? 2 : 4)
 k_inc_defstate(Grid g, const float* __restrict__ U, const float* __restrict__ D,
                                const float* __restrict__ Fold, const TJ* __restrict__ Du,
                                const float* __restrict__ dv, float dt, float* __restrict__ out,
