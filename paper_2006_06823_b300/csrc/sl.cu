@@ -249,9 +249,10 @@ int sl_characteristics(const SLArgs& a, const float* vsrc, const float* vval, co
 
 // ---------------------------------------------------------------- gathers
 // MODE 0: out = src o X; 1: * aux(x) (one plane); 2: + aux[c](x). NC components;
-// launch bounds keep the kernel at <= 64 registers (8 warps x 4 CTAs per SM).
+// launch bounds keep the trilinear kernel at <= 40 registers (8 warps x 6 CTAs per SM: the
+// gathers are latency-bound, so resident warps matter more than registers).
 template <int IP, int MODE, int NC>
-__global__ void __launch_bounds__(256, IP == 3 ? 2 : 4)
+__global__ void __launch_bounds__(256, IP == 3 ? 2 : 6)
 k_sl_gather(Grid g, const float* __restrict__ src, const float* __restrict__ D,
             const float* __restrict__ aux, float* __restrict__ out) {
     VOXEL_PROLOGUE
