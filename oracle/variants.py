@@ -234,6 +234,18 @@ class Problem:
         """MSE_rel = ||m(1) - I1||^2 / ||I0 - I1||^2 (Sec. 5.1.1)."""
         return float(np.sum((m1 - self.I1) ** 2) / np.sum((self.I0 - self.I1) ** 2))
 
+    @staticmethod
+    def jacobian_determinant_of(u1, shape):
+        """det D phi per voxel for phi = id - iota(u~) (physical units): det(I - D iota(u~)).
+        The paper reports its minimum and maximum over the volume (Sec. 5.1.1, Table 3)."""
+        Du = S.include(S.jacobian(u1), shape)   # [a][b][z][y][x] = d u_a / d x_b
+        A = np.eye(3)[:, :, None, None, None] - Du
+        return np.linalg.det(np.moveaxis(A, (0, 1), (-2, -1)))
+
+    def jacobian_determinant(self, vt):
+        """det D phi(1) of the deformation-state solution for vt (DEFSTATE)."""
+        return self.jacobian_determinant_of(self.state_defstate(vt)[-1], self.shape)
+
     def max_displacement_vox(self, vt):
         """Max over voxels of |phi(1)(x) - x| in voxels (DEFSTATE: |iota(u~(1))|)."""
         us = self.state_defstate(vt)

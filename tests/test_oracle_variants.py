@@ -10,6 +10,7 @@ from oracle import sl as SL
 from oracle import spectral as S
 from oracle import variants as Vn
 from paper_2006_06823_b300 import synth
+from _problems import oracle_problem
 
 N = 16
 K = 8
@@ -119,3 +120,36 @@ def test_defstate_hessian_matches_gradient_differences_at_zero_residual():
     fd = (prob.gradient(vt + h * d)[3] - prob.gradient(vt - h * d)[3]) / (2 * h)
     Hd = prob.hessian_matvec(vt, d)
     assert np.linalg.norm(fd - Hd) <= 1e-3 * np.linalg.norm(Hd)
+
+
+def _single_mode(K, comp, axis, amp):
+    """Cube of u with u_comp = amp sin(x_axis) (wavenumber 1 along axis), other comps zero."""
+    c = np.zeros((3, K, K, K), dtype=np.complex128)
+    idx_p = [K // 2] * 3
+    idx_m = [K // 2] * 3
+    ax = 2 - axis                      # cube index order [jz][jy][jx]
+    idx_p[ax] += 1
+    idx_m[ax] -= 1
+    c[(comp,) + tuple(idx_p)] = -0.5j * amp      # sin = (e^{ix} - e^{-ix}) / 2i
+    c[(comp,) + tuple(idx_m)] = 0.5j * amp
+    return c
+
+
+def test_jacobian_determinant_closed_forms():
+    """det(I - Du): u = (a sin x, 0, 0) gives 1 - a cos x; u = (a sin y, 0, 0) is a shear,
+    det 1; zero velocity gives the identity map, det 1 exactly."""
+    shape, K, a = (8, 10, 12), 6, 0.3
+    nz, ny, nx = shape
+    x = 2 * np.pi * np.arange(nx) / nx
+    J = Vn.Problem.jacobian_determinant_of(_single_mode(K, 0, 0, a), shape)
+    np.testing.assert_allclose(J, np.broadcast_to(1 - a * np.cos(x), shape), atol=1e-12)
+    J = Vn.Problem.jacobian_determinant_of(_single_mode(K, 0, 1, a), shape)
+    np.testing.assert_allclose(J, 1.0, atol=1e-12)
+    # two components: u = (a sin x, b sin y, 0) -> (1 - a cos x)(1 - b cos y)
+    c = _single_mode(K, 0, 0, a) + _single_mode(K, 1, 1, 0.2)
+    y = 2 * np.pi * np.arange(ny) / ny
+    J = Vn.Problem.jacobian_determinant_of(c, shape)
+    ref = (1 - a * np.cos(x))[None, None, :] * (1 - 0.2 * np.cos(y))[None, :, None]
+    np.testing.assert_allclose(J, np.broadcast_to(ref, shape), atol=1e-12)
+    prob = oracle_problem((8, 8, 8), 4, Vn.DEFSTATE, 1, nt=3)
+    assert np.array_equal(prob.jacobian_determinant(np.zeros((3, 4, 4, 4), complex)), np.ones((8, 8, 8)))
