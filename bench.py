@@ -240,7 +240,7 @@ def run_b300(args):
     torch.cuda.synchronize()
     L.trace_reset()
     L.trace_enable(True)
-    ctx.register()
+    v_sol, _ = ctx.register()
     trace = L.trace_read()
     L.trace_enable(False)
 
@@ -260,6 +260,9 @@ def run_b300(args):
     sl_vps = NT * ntot / (statistics.mean(sl_ms) / 1e3)
 
     # ---- e2e: the public API with host buffers, copies inside the timing
+    # diagnostics of the solution (Sec. 5.1.1): range of det D phi(1)
+    jac_range, _ = ctx.jacobian_det(v_sol)
+
     e2e_s = []
     v_host = torch.empty((3, K, K, K), dtype=torch.complex64).pin_memory()
     for _ in range(args.steps):
@@ -306,8 +309,9 @@ def run_b300(args):
                    "pairs_per_step": world,
                    "l2": "flushed (256 MB write) between timed steps; working set ~5 GB"},
         "residual_reached": last["grad_rel_l2"] <= GTOL,
-        "report": {k: last[k] for k in ("gn_iters", "pcg_iters_total", "stop_reason", "solves",
-                                        "E0", "E", "grad_rel_l2", "grad_rel_inf", "mse_rel")},
+        "report": dict({k: last[k] for k in ("gn_iters", "pcg_iters_total", "stop_reason", "solves",
+                                             "E0", "E", "grad_rel_l2", "grad_rel_inf", "mse_rel")},
+                       jacobian_det_min=jac_range[0], jacobian_det_max=jac_range[1]),
         "sl_voxel_steps_per_s": sl_vps,
         "e2e": {"value": e2e_total / (args.steps * world), "unit": "s/pair",
                 "h2d_bytes_per_step": 2 * ntot * 4, "d2h_bytes_per_step": 3 * K ** 3 * 8},

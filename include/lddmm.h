@@ -158,6 +158,13 @@ int lddmm_set_option(lddmm_ctx* ctx, int option, long value);
  * departure offsets (the next objective/gradient recomputes them). Synchronises. */
 int lddmm_autotune(lddmm_ctx* ctx, const char* cache_path, int* block_x_out);
 
+/* Jacobian determinant of the deformation phi(1) = id - iota(u~(1)) for the velocity v
+ * (device cube): J = det(I - D iota(u~(1))) per voxel (Sec. 5.1.1 reports its minimum and
+ * maximum; J < 0 flags a fold). J: device float[nz][ny][nx] or NULL; range (host): {min J,
+ * max J} over the volume. Solves the state for v unless it is the context's current one.
+ * Deformation-state contexts only (EINVAL otherwise). Synchronises. */
+int lddmm_jacobian_det(lddmm_ctx* ctx, const float* v, float* J, double* range);
+
 /* Warp m(1) = I0 o phi(1) of the last state solved in the context into m1 (device,
  * float[nz][ny][nx]). DEFSTATE: phi(1) = id - iota(u~(1)); IMAGE: m(nt). */
 int lddmm_get_warped(lddmm_ctx* ctx, float* m1);

@@ -77,6 +77,7 @@ def _declare(lib):
         "lddmm_hessian_matvec": (_I, [_P, _P, _P, _P]),
         "lddmm_register": (_I, [_P, _P, _P, ctypes.POINTER(Report)]),
         "lddmm_get_warped": (_I, [_P, _P]),
+        "lddmm_jacobian_det": (_I, [_P, _P, _P, ctypes.POINTER(_D)]),
         "lddmm_bl_project": (_I, [_I, _I, _I, _I, _P, _I, _P, _I, _P]),
         "lddmm_bl_project_noalloc": (_I, [_I, _I, _I, _I, _P, _I, _P, _I, _P]),
         "lddmm_bl_include": (_I, [_I, _I, _I, _I, _P, _I, _P, _I, _I, _I, _P]),
@@ -316,6 +317,17 @@ class Context:
         path = cache_path.encode() if cache_path else None
         _check(load().lddmm_autotune(self._h, path, ctypes.byref(bx)))
         return bx.value
+
+    def jacobian_det(self, v, out=None, field=False):
+        """(min J, max J) of J = det D phi(1) for velocity v (lddmm_jacobian_det); with
+        field=True also the per-voxel J (float32 [nz, ny, nx])."""
+        import torch
+        J = None
+        if field:
+            J = torch.empty(self.shape, dtype=torch.float32, device="cuda") if out is None else out
+        rng = (ctypes.c_double * 2)()
+        _check(load().lddmm_jacobian_det(self._h, _c64(v), _f32(J) if J is not None else None, rng))
+        return (rng[0], rng[1]), J
 
     def get_warped(self, out=None):
         import torch

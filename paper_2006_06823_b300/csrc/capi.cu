@@ -731,7 +731,7 @@ static int ctx_alloc(lddmm_ctx* c) {
         TRY(dalloc_t(c, &c->cv[i], kc3));
         LDDMM_CUDA(cudaMemsetAsync(c->cv[i], 0, kc3 * sizeof(float2), c->st));
     }
-    TRY(dalloc_t(c, &c->partials, kReduceBlocks));
+    TRY(dalloc_t(c, &c->partials, 2 * kReduceBlocks));   // the Jacobian range uses two rows
     TRY(dalloc_t(c, &c->dsc, 16));
     LDDMM_CUDA(cudaMallocHost(reinterpret_cast<void**>(&c->hsc), 16 * sizeof(double)));
     return LDDMM_OK;
@@ -853,6 +853,31 @@ int lddmm_hessian_matvec(lddmm_ctx* c, const float* v, const float* dv, float* H
 int lddmm_register(lddmm_ctx* c, float* v_inout, const double* g_ref_norms, lddmm_report* rep) {
     if (!v_inout || !rep) { set_error("v_inout or report is NULL"); return LDDMM_EINVAL; }
     CTX_CALL(c, register_impl(c, reinterpret_cast<float2*>(v_inout), g_ref_norms, rep));
+}
+
+int lddmm_jacobian_det(lddmm_ctx* c, const float* v, float* J, double* range) {
+    if (!v || !range) { set_error("jacobian_det: v or range is NULL"); return LDDMM_EINVAL; }
+    CTX_CALL(c, ([&]() -> int {
+        if (c->p.variant != LDDMM_V_DEFSTATE) {
+            set_error("jacobian_det: deformation-state contexts only");
+            return LDDMM_EINVAL;
+        }
+        const float2* vt = reinterpret_cast<const float2*>(v);
+        bool same = false;
+        TRY(same_as_current(c, vt, &same));
+        TRY(ensure_state(c, vt, same));
+        TRY(ensure_traj(c));
+        double* pmin = c->partials;
+        double* pmax = c->partials + kReduceBlocks;
+        TRY(jacobian_det(c->g, c->Du + (long)c->p.nt * 9 * c->n, J, pmin, pmax, c->st));
+        std::vector<double> h(2 * kReduceBlocks);
+        LDDMM_CUDA(cudaMemcpyAsync(h.data(), c->partials, h.size() * sizeof(double),
+                                   cudaMemcpyDeviceToHost, c->st));
+        LDDMM_CUDA(cudaStreamSynchronize(c->st));
+        range[0] = *std::min_element(h.begin(), h.begin() + kReduceBlocks);
+        range[1] = *std::max_element(h.begin() + kReduceBlocks, h.end());
+        return LDDMM_OK;
+    })());
 }
 
 int lddmm_get_warped(lddmm_ctx* c, float* m1) {

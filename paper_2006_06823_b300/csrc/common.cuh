@@ -157,6 +157,8 @@ int defstate_drho1(const Grid& g, const float* G, const float* du1, double sigma
 // acc_b (+)= w sum_a Du[a*3+b] R_a   (init != 0 overwrites)
 int accum_JT(const Grid& g, const void* Du, bool du_bf16, const float* R, float w, float* acc,
              int init, cudaStream_t st);
+// J = det(I - Du) per voxel (J may be NULL) and kReduceBlocks per-block minima / maxima
+int jacobian_det(const Grid& g, const float* Du, float* J, double* pmin, double* pmax, cudaStream_t st);
 // out[i] = bf16(in[i]), i < n (round to nearest even)
 int to_bf16(const float* in, void* out, long n, cudaStream_t st);
 // x_out = a * x (n floats)

@@ -629,6 +629,50 @@ int accum_JT(const Grid& g, const void* Du, bool du_bf16, const float* R, float 
     return LDDMM_OK;
 }
 
+// J = det(I - Du) per voxel from the nine planes Du[3a + b] = d u_a / d x_b (physical), with
+// per-block minimum and maximum (FP64) into pmin / pmax (kReduceBlocks each).
+__global__ void __launch_bounds__(256)
+k_jacdet(long n, const float* __restrict__ Du, float* __restrict__ J, double* __restrict__ pmin,
+         double* __restrict__ pmax) {
+    double mn = 1e300, mx = -1e300;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        double a[3][3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) a[r][c] = (r == c ? 1.0 : 0.0) - (double)Du[(3 * r + c) * n + i];
+        const double det = a[0][0] * (a[1][1] * a[2][2] - a[1][2] * a[2][1]) -
+                           a[0][1] * (a[1][0] * a[2][2] - a[1][2] * a[2][0]) +
+                           a[0][2] * (a[1][0] * a[2][1] - a[1][1] * a[2][0]);
+        if (J) J[i] = (float)det;
+        mn = fmin(mn, det);
+        mx = fmax(mx, det);
+    }
+    __shared__ double smin[256], smax[256];
+    smin[threadIdx.x] = mn;
+    smax[threadIdx.x] = mx;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + o]);
+            smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        pmin[blockIdx.x] = smin[0];
+        pmax[blockIdx.x] = smax[0];
+    }
+}
+
+int jacobian_det(const Grid& g, const float* Du, float* J, double* pmin, double* pmax, cudaStream_t st) {
+    const long n = g.ntot();
+    KTRACE("jacobian_det", st, n * (36.0 + (J ? 4.0 : 0.0)), n * 40.0);
+    k_jacdet<<<kReduceBlocks, 256, 0, st>>>(n, Du, J, pmin, pmax);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
 __global__ void k_scale_field(float* out, const float* in, float a, long n) {
     long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) out[i] = a * in[i];

@@ -193,3 +193,26 @@ def test_mixed_precision_registration_against_oracle_and_fp32_form():
         assert r["max_disp_diff_vox"] < 1e-2, (name, r)
     assert out["fp32_tensor"]["gn_iters"] == ref["gn_iters"]
     assert out["fp32_tensor"]["pcg_iters"] == ref["pcg_iters_total"]
+
+
+@pytest.mark.parametrize("shape,K,order", [((16, 16, 16), 8, 1), ((24, 20, 32), 16, 3)])
+def test_jacobian_determinant_matches_oracle(shape, K, order):
+    """det D phi(1) per voxel and its range against the oracle (FP32 Jacobians, FP64 det)."""
+    prob = oracle_problem(shape, K, Vn.DEFSTATE, order, nt=5)
+    vt = synth.random_velocity_coeffs(K, K, seed=9) * 2.0
+    Jo = prob.jacobian_determinant(vt)
+    with gpu_context(prob) as ctx:
+        (jmin, jmax), J = ctx.jacobian_det(devc(vt), field=True)
+        J = J.cpu().numpy().astype(np.float64)
+        (zmin, zmax), _ = ctx.jacobian_det(ctx.zeros_cube())
+    assert np.abs(J - Jo).max() < 1e-4 * np.abs(Jo).max()
+    assert jmin == pytest.approx(Jo.min(), abs=1e-4) and jmax == pytest.approx(Jo.max(), abs=1e-4)
+    assert Jo.min() < 0.99 < 1.01 < Jo.max()          # a real deformation
+    assert zmin == 1.0 and zmax == 1.0                 # identity map
+
+
+def test_jacobian_determinant_needs_the_deformation_state():
+    prob = oracle_problem((16, 16, 16), 8, Vn.IMAGE, 1, nt=3)
+    with gpu_context(prob) as ctx:
+        with pytest.raises(L.LddmmError):
+            ctx.jacobian_det(ctx.zeros_cube())
