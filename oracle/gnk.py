@@ -30,18 +30,18 @@ STOP_MAXIT = 2
 STOP_LINESEARCH = 3
 
 
-def pcg(hv, b, prec, eta, maxit):
+def pcg(hv, b, prec, eta, maxit, inner=S.inner):
     """Preconditioned CG for H x = b from x = 0. Returns (x, iterations, negative_curvature)."""
     x = np.zeros_like(b)
     r = b.copy()
     z = prec(r)
     p = z.copy()
-    rz = S.inner(r, z)
-    bnorm = np.sqrt(S.inner(b, b))
+    rz = inner(r, z)
+    bnorm = np.sqrt(inner(b, b))
     its = 0
     for i in range(maxit):
         Hp = hv(p)
-        pHp = S.inner(p, Hp)
+        pHp = inner(p, Hp)
         its = i + 1
         if pHp <= 0.0:
             if i == 0:
@@ -50,10 +50,10 @@ def pcg(hv, b, prec, eta, maxit):
         a = rz / pHp
         x = x + a * p
         r = r - a * Hp
-        if np.sqrt(S.inner(r, r)) <= eta * bnorm:
+        if np.sqrt(inner(r, r)) <= eta * bnorm:
             break
         z = prec(r)
-        rz_new = S.inner(r, z)
+        rz_new = inner(r, z)
         p = z + (rz_new / rz) * p
         rz = rz_new
     return x, its, False
@@ -78,27 +78,33 @@ def register(problem, v0=None, max_gn=5, max_pcg=10, gtol=1e-3, g_ref=None):
     """Gauss-Newton-Krylov registration from v0 (zero by default). Returns (v~, Report)."""
     p = problem.p
     K = p.K
-    v = np.zeros((3, K, K, K), dtype=np.complex128) if v0 is None else np.array(v0, np.complex128)
-    prec = lambda c: S.apply_Linv(c, p.alpha, p.s)
+    # the problem may define its own unknown (a stack of cubes), product and preconditioner
+    inner = getattr(problem, "inner", S.inner)
+    if hasattr(problem, "zeros"):
+        v = problem.zeros() if v0 is None else np.array(v0, np.complex128)
+        prec = problem.precond
+    else:
+        v = np.zeros((3, K, K, K), dtype=np.complex128) if v0 is None else np.array(v0, np.complex128)
+        prec = lambda c: S.apply_Linv(c, p.alpha, p.s)
     if g_ref is None:
         g_ref = problem.gradient(np.zeros_like(v))[3] if v0 is not None else None
     rep = Report()
     E, Er, Ed, g = problem.gradient(v)
     if g_ref is None:
         g_ref = g
-    gref_l2 = np.sqrt(S.inner(g_ref, g_ref))
+    gref_l2 = np.sqrt(inner(g_ref, g_ref))
     gref_inf = np.abs(g_ref).max()
     rep.E0 = E
     for n in range(max_gn):
-        gn = np.sqrt(S.inner(g, g))
+        gn = np.sqrt(inner(g, g))
         rep.history.append((E, gn / gref_l2))
         if gn / gref_l2 <= gtol:
             rep.stop_reason = STOP_GTOL
             break
         eta = min(0.5, np.sqrt(gn / gref_l2))
-        dv, its, _ = pcg(lambda c: problem.hessian_matvec(v, c), -g, prec, eta, max_pcg)
+        dv, its, _ = pcg(lambda c: problem.hessian_matvec(v, c), -g, prec, eta, max_pcg, inner)
         rep.pcg_iters_total += its
-        slope = S.inner(g, dv)
+        slope = inner(g, dv)
         eps, accepted = 1.0, False
         for _ in range(11):
             Et = problem.objective(v + eps * dv)[0]
@@ -114,7 +120,7 @@ def register(problem, v0=None, max_gn=5, max_pcg=10, gtol=1e-3, g_ref=None):
         E, Er, Ed, g = problem.gradient(v)
     else:
         rep.stop_reason = STOP_MAXIT
-    gn = np.sqrt(S.inner(g, g))
+    gn = np.sqrt(inner(g, g))
     if rep.stop_reason == STOP_MAXIT and gn / gref_l2 <= gtol:
         rep.stop_reason = STOP_GTOL
     m1 = problem.objective(v)[3]

@@ -46,6 +46,20 @@ def departure_offsets(V, dt, direction, order):
     return sgn * 0.5 * dt * (Vstar + V)        # X - x
 
 
+def departure_offsets_ns(V_here, V_other, dt, direction, order):
+    """Offsets of one step between two nodes with different velocities (non-stationary v).
+
+    direction = +1 (state, arrival node t_{j+1}): X* = x - dt V_{j+1}(x),
+    X = x - dt/2 (V_{j+1}(x) + V_j(X*)), i.e. V_here = V_{j+1}, V_other = V_j.
+    direction = -1 (adjoint, arrival node t_j of the backward sweep): X+* = x + dt V_j(x),
+    X+ = x + dt/2 (V_j(x) + V_{j+1}(X+*)), i.e. V_here = V_j, V_other = V_{j+1}.
+    With V_here = V_other this is departure_offsets."""
+    sgn = -1.0 if direction > 0 else 1.0
+    Dstar = sgn * dt * V_here
+    Vstar = I.interpolate(V_other, Dstar, order)
+    return sgn * 0.5 * dt * (Vstar + V_here)
+
+
 def transport_step(u, D, order):
     """D_t u = 0 (Table 1 row 1, state equation in SL form): u^{j+1}(x) = u^j(X)."""
     return I.interpolate(u, D, order)
@@ -68,6 +82,15 @@ def heun_divergence_step(u, Dplus, d, dt, order):
     f_old = a * d_dep
     u_star = a + dt * f_old
     return a + 0.5 * dt * (f_old + u_star * d)
+
+
+def heun_divergence_step_ns(u, Dplus, d_next, d_here, dt, order):
+    """-D_t u = u div v_t between nodes t_j and t_{j+1} (non-stationary v): as
+    heun_divergence_step with d(X+) taken from d_{j+1} and d(x) from d_j."""
+    a = I.interpolate(u, Dplus, order)
+    f_old = a * I.interpolate(d_next, Dplus, order)
+    u_star = a + dt * f_old
+    return a + 0.5 * dt * (f_old + u_star * d_here)
 
 
 def sl_transport(field, V, nt, direction, order):
@@ -93,6 +116,11 @@ def bl_transport_step(c, D, order, shape, K):
 def bl_heun_source_step(c, D, F_old, F_new, dt, order, shape, K):
     """One BL step of D~_t u~ = F with spatial right-hand sides F_j, F_{j+1} on the grid."""
     return S.project(heun_source_step(S.include(c, shape), D, F_old, F_new, dt, order), K)
+
+
+def bl_heun_divergence_step_ns(c, Dplus, d_next, d_here, dt, order, shape, K):
+    """One backward BL step of -D~_t u~ = u~ * div~ v~_t with node-dependent divergence."""
+    return S.project(heun_divergence_step_ns(S.include(c, shape), Dplus, d_next, d_here, dt, order), K)
 
 
 def bl_heun_divergence_step(c, Dplus, d, dt, order, shape, K):

@@ -251,3 +251,114 @@ class Problem:
         us = self.state_defstate(vt)
         u = S.include(us[-1], self.shape) * self.to_vox[:, None, None, None]
         return float(np.sqrt((u * u).sum(0)).max())
+
+
+class ProblemNS(Problem):
+    """Non-stationary deformation-state variant (Sec. 2.3.3 with a time-dependent v~_t; the
+    paper's NSt rows): the unknown is v~ = [v~_0 .. v~_nt], one cube per node t_j = j/nt
+    ([nt+1][3][K][K][K]). Equations as in Problem with v~ replaced by v~(t_j) at node j:
+      state   u~_{j+1} = pi[iota(u~_j) o X_j + dt/2 (v_j(X_j) + v_{j+1}(x))],
+              X_j from departure_offsets_ns(V_{j+1}, V_j) (R10);
+      adjoint rho~_j = pi[Heun step of -D_t rho = rho div v_t along X+_j],
+              X+_j from departure_offsets_ns(V_j, V_{j+1}), d(X+) from d_{j+1}, d(x) from d_j;
+      energy  E = 1/2 sum_j w_j <L~v~_j, v~_j> + (1/sigma^2) mean r^2 (trapezoid weights w_j);
+      gradient at node j (the integrand of Eq. 32 at t_j, the Riesz representative for the
+              weighted product <a, b>_w = sum_j w_j <a_j, b_j>):
+              g_j = L~v~_j + rho~_j - pi((D iota u~_j)^T iota rho~_j);
+      Gauss-Newton Hessian likewise with drho~ and the incremental state
+              D~_t du~ = dv~_t - D~u~ * dv~_t.
+    With all nodes equal it reduces to Problem (the weighted sum of g_j is the stationary
+    gradient)."""
+
+    def __init__(self, I0, I1, params: Params):
+        assert params.variant == DEFSTATE
+        super().__init__(I0, I1, params)
+
+    def inner(self, a, b):
+        return float(sum(w * S.inner(x, y) for w, x, y in zip(self.tw, a, b)))
+
+    def precond(self, c):
+        return np.stack([S.apply_Linv(cj, self.p.alpha, self.p.s) for cj in c])
+
+    def zeros(self):
+        K = self.p.K
+        return np.zeros((self.p.nt + 1, 3, K, K, K), dtype=np.complex128)
+
+    def velocities(self, vts):
+        return [self.velocity(vt) for vt in vts]
+
+    def _offsets(self, vel):
+        p = self.p
+        Df = [SL.departure_offsets_ns(vel[j + 1][1], vel[j][1], self.dt, +1, p.order)
+              for j in range(p.nt)]
+        Db = [SL.departure_offsets_ns(vel[j][1], vel[j + 1][1], self.dt, -1, p.order)
+              for j in range(p.nt)]
+        return Df, Db
+
+    def energy_reg(self, vts):
+        return float(sum(w * 0.5 * S.inner(S.apply_L(vt, self.p.alpha, self.p.s), vt)
+                         for w, vt in zip(self.tw, vts)))
+
+    def state_defstate(self, vts):
+        p = self.p
+        vel = self.velocities(vts)
+        Df, _ = self._offsets(vel)
+        u = np.zeros((3, p.K, p.K, p.K), dtype=np.complex128)
+        us = [u]
+        for j in range(p.nt):
+            u = SL.bl_heun_source_step(u, Df[j], vel[j][0], vel[j + 1][0], self.dt, p.order,
+                                       self.shape, p.K)
+            us.append(u)
+        return us
+
+    def _adjoint_ns(self, rho_end, vel, Db):
+        p = self.p
+        rhos = [None] * (p.nt + 1)
+        rhos[p.nt] = rho = rho_end
+        for j in range(p.nt - 1, -1, -1):
+            rho = SL.bl_heun_divergence_step_ns(rho, Db[j], vel[j + 1][2], vel[j][2], self.dt,
+                                                p.order, self.shape, p.K)
+            rhos[j] = rho
+        return rhos
+
+    def _assemble_ns(self, base, rhos, Jus):
+        out = []
+        for bj, rho, Ju in zip(base, rhos, Jus):
+            JT = np.einsum("abzyx,azyx->bzyx", Ju, S.include(rho, self.shape))
+            out.append(S.apply_L(bj, self.p.alpha, self.p.s) + rho - S.project(JT, self.p.K))
+        return np.stack(out)
+
+    def objective(self, vts):
+        us = self.state_defstate(vts)
+        m1, _ = self._warp_I0(us[-1])
+        er, ed = self.energy_reg(vts), self.energy_data(m1)
+        return er + ed, er, ed, m1
+
+    def gradient(self, vts):
+        p = self.p
+        vel = self.velocities(vts)
+        _, Db = self._offsets(vel)
+        us = self.state_defstate(vts)
+        m1, G = self._warp_I0(us[-1])
+        rho1 = S.project(-(2.0 / p.sigma2) * (m1 - self.I1)[None] * G, p.K)
+        rhos = self._adjoint_ns(rho1, vel, Db)
+        g = self._assemble_ns(vts, rhos, self._jacobians(us))
+        er, ed = self.energy_reg(vts), self.energy_data(m1)
+        return er + ed, er, ed, g
+
+    def hessian_matvec(self, vts, dvts):
+        p = self.p
+        vel = self.velocities(vts)
+        Df, Db = self._offsets(vel)
+        us = self.state_defstate(vts)
+        Jus = self._jacobians(us)
+        _, G = self._warp_I0(us[-1])
+        dvs = [S.include(dv, self.shape) for dv in dvts]
+        F = [dv - np.einsum("abzyx,bzyx->azyx", Ju, dv) for Ju, dv in zip(Jus, dvs)]
+        du = np.zeros((3, p.K, p.K, p.K), dtype=np.complex128)
+        for j in range(p.nt):
+            du = SL.bl_heun_source_step(du, Df[j], F[j], F[j + 1], self.dt, p.order, self.shape, p.K)
+        dm1 = -np.sum(G * S.include(du, self.shape), axis=0)
+        drho1 = S.project(-(2.0 / p.sigma2) * dm1[None] * G, p.K)
+        drhos = self._adjoint_ns(drho1, vel, Db)
+        return self._assemble_ns(dvts, drhos, Jus)
