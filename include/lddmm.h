@@ -73,6 +73,12 @@ typedef struct {
     int max_pcg;       /* PCG iterations per update */
     double gtol;       /* stop when ||g|| / ||g(v=0)|| <= gtol */
     int precision;     /* LDDMM_PREC_* form */
+    int nonstationary; /* 0: one cube v~ for all t (the default); 1: v~_j at every node t_j =
+                          j/nt (deformation state only). Every velocity argument of a
+                          non-stationary context is then the stack float[nt+1][3][K][K][K][2];
+                          norms and inner products of such stacks weight node j by the
+                          trapezoid weight w_j (R11), and the gradient / Hessian at node j is
+                          the integrand of Eq. 32 / 33 at t_j. */
 } lddmm_params;
 
 /* Outcome of lddmm_register. */

@@ -41,7 +41,7 @@ class Params(ctypes.Structure):
                 ("interp", ctypes.c_int), ("alpha", ctypes.c_double), ("s", ctypes.c_int),
                 ("sigma2", ctypes.c_double), ("max_gn", ctypes.c_int),
                 ("max_pcg", ctypes.c_int), ("gtol", ctypes.c_double),
-                ("precision", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("nonstationary", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -239,11 +239,13 @@ class Context:
 
     def __init__(self, nx, ny, nz, K, nt=10, variant=V_DEFSTATE, interp=INTERP_LINEAR,
                  alpha=0.0025, s=2, sigma2=0.01, max_gn=10, max_pcg=20, gtol=1e-3,
-                 precision=PREC_FP32):
+                 precision=PREC_FP32, nonstationary=False):
         self.params = Params(nx, ny, nz, K, nt, variant, interp, alpha, s, sigma2, max_gn,
-                             max_pcg, gtol, precision)
+                             max_pcg, gtol, precision, 1 if nonstationary else 0)
         self.shape = (nz, ny, nx)
         self.K = K
+        self.nt = nt
+        self.nonstationary = bool(nonstationary)
         self._h = ctypes.c_void_p()
         _check(load().lddmm_create(ctypes.byref(self.params), _stream(), ctypes.byref(self._h)))
 
@@ -265,8 +267,10 @@ class Context:
         self.close()
 
     def zeros_cube(self):
+        """A zero velocity: [3, K, K, K], or [nt + 1, 3, K, K, K] for a non-stationary context."""
         import torch
-        return torch.zeros((3, self.K, self.K, self.K), dtype=torch.complex64, device="cuda")
+        lead = (self.nt + 1, 3) if self.nonstationary else (3,)
+        return torch.zeros(lead + (self.K, self.K, self.K), dtype=torch.complex64, device="cuda")
 
     def set_images(self, I0, I1):
         if I0.is_cuda:

@@ -53,7 +53,9 @@ struct lddmm_ctx {
 
     // images
     float *I0 = nullptr, *I1 = nullptr, *I0c = nullptr;
-    // velocity fields of the current v~ (stationary)
+    // velocity fields of the current v~: one node (stationary) or nt + 1 nodes (v, vc: 3
+    // planes each, d, dc: 1), and one step (stationary) or nt steps of offsets Df, Db,
+    // source W (3 planes each) and adjoint factor gam (1)
     float *v = nullptr, *vc = nullptr, *d = nullptr, *dc = nullptr;
     float *Df = nullptr, *Db = nullptr, *gam = nullptr, *W = nullptr;
     // trajectories
@@ -68,7 +70,7 @@ struct lddmm_ctx {
           *dvsp = nullptr;
     // spectral scratch
     float2 *s1 = nullptr, *s2 = nullptr;
-    // cube vectors (3 x K^3 each)
+    // cube vectors (3 x K^3 each, x (nt + 1) nodes in a non-stationary context)
     enum { C_V, C_VT, C_G, C_R, C_Z, C_P, C_HP, C_X, C_T0, C_T1, C_T2, C_CUR, C_DV, C_NUM };
     float2* cv[C_NUM];
     // reductions
@@ -127,6 +129,14 @@ static int validate(const lddmm_params* p) {
         set_error("variant must be LDDMM_V_IMAGE or LDDMM_V_DEFSTATE");
         return LDDMM_EINVAL;
     }
+    if (p->nonstationary != 0 && p->nonstationary != 1) {
+        set_error("nonstationary must be 0 or 1");
+        return LDDMM_EINVAL;
+    }
+    if (p->nonstationary && p->variant != LDDMM_V_DEFSTATE) {
+        set_error("the non-stationary form is implemented for the deformation-state variant");
+        return LDDMM_EINVAL;
+    }
     if (p->interp != LDDMM_INTERP_LINEAR && p->interp != LDDMM_INTERP_CUBIC) {
         set_error("interp must be LDDMM_INTERP_LINEAR or LDDMM_INTERP_CUBIC");
         return LDDMM_EINVAL;
@@ -169,6 +179,28 @@ static const void* jac(const lddmm_ctx* c, int j, bool hess) {
 }
 static bool cubic(const lddmm_ctx* c) { return c->p.interp == LDDMM_INTERP_CUBIC; }
 
+// Non-stationary form: nt + 1 velocity nodes and nt distinct steps; the stationary form has
+// one node and one step that serve every time.
+static bool ns(const lddmm_ctx* c) { return c->p.nonstationary != 0; }
+static int nodes(const lddmm_ctx* c) { return ns(c) ? c->p.nt + 1 : 1; }
+static long nvec(const lddmm_ctx* c) { return (long)nodes(c) * 3 * c->kc; }   // float2 per velocity
+static long node_off(const lddmm_ctx* c, int j, long planes) { return ns(c) ? (long)j * planes * c->n : 0; }
+static float* vnode(lddmm_ctx* c, int j) { return c->v + node_off(c, j, 3); }
+static float* vcnode(lddmm_ctx* c, int j) { return c->vc + node_off(c, j, 3); }
+static float* dnode(lddmm_ctx* c, int j) { return c->d + node_off(c, j, 1); }
+static float* dcnode(lddmm_ctx* c, int j) { return c->dc + node_off(c, j, 1); }
+static float* Dfstep(lddmm_ctx* c, int j) { return c->Df + node_off(c, j, 3); }
+static float* Dbstep(lddmm_ctx* c, int j) { return c->Db + node_off(c, j, 3); }
+static float* Wstep(lddmm_ctx* c, int j) { return c->W + node_off(c, j, 3); }
+static float* gamstep(lddmm_ctx* c, int j) { return c->gam + node_off(c, j, 1); }
+// cube j of a velocity-shaped vector (node j; the one cube when stationary)
+static const float2* vcube(const lddmm_ctx* c, const float2* vt, int j) {
+    return vt + (ns(c) ? (long)j * 3 * c->kc : 0);
+}
+static float2* vcube(const lddmm_ctx* c, float2* vt, int j) {
+    return vt + (ns(c) ? (long)j * 3 * c->kc : 0);
+}
+
 // Reads `count` device doubles from c->dsc into c->hsc (synchronises the stream).
 static int read_scalars(lddmm_ctx* c, int count) {
     LDDMM_CUDA(cudaMemcpyAsync(c->hsc, c->dsc, count * sizeof(double), cudaMemcpyDeviceToHost, c->st));
@@ -190,21 +222,32 @@ static double trap_w(const lddmm_ctx* c, int j) {
 // the adjoint factor gam and the deformation-state source W.
 static int prepare_velocity(lddmm_ctx* c, const float2* vt) {
     const long n = c->n;
-    TRY(include(c, vt, 3, c->v, n, -1, 0));
-    TRY(include(c, vt, 3, c->d, n, 3, 0));
-    const float* vsrc = c->v;
-    const float* dsrc = c->d;
-    if (cubic(c)) {
-        TRY(include(c, vt, 3, c->vc, n, -1, 1));
-        TRY(include(c, vt, 3, c->dc, n, 3, 1));
-        vsrc = c->vc;
-        dsrc = c->dc;
+    for (int j = 0; j < nodes(c); ++j) {
+        const float2* vj = vcube(c, vt, j);
+        TRY(include(c, vj, 3, vnode(c, j), n, -1, 0));
+        TRY(include(c, vj, 3, dnode(c, j), n, 3, 0));
+        if (cubic(c)) {
+            TRY(include(c, vj, 3, vcnode(c, j), n, -1, 1));
+            TRY(include(c, vj, 3, dcnode(c, j), n, 3, 1));
+        }
     }
-    TRY(sl_characteristics(c->sl, vsrc, c->v, c->to_vox, -c->dt, c->Df, c->st));
-    TRY(sl_characteristics(c->sl, vsrc, c->v, c->to_vox, +c->dt, c->Db, c->st));
-    TRY(sl_prep_adjoint(c->sl, dsrc, c->d, c->Db, c->dt, c->gam, c->st));
-    if (c->p.variant == LDDMM_V_DEFSTATE)
-        TRY(sl_prep_source(c->sl, vsrc, c->v, c->Df, c->dt, c->W, c->st));
+    // step j runs from node a = j to node b = j + 1 (stationary: both node 0)
+    const int steps = ns(c) ? c->p.nt : 1;
+    for (int j = 0; j < steps; ++j) {
+        const int a = j, b = ns(c) ? j + 1 : j;
+        const float* vsrc_a = cubic(c) ? vcnode(c, a) : vnode(c, a);   // interpolated fields
+        const float* vsrc_b = cubic(c) ? vcnode(c, b) : vnode(c, b);
+        const float* dsrc_b = cubic(c) ? dcnode(c, b) : dnode(c, b);
+        // state: X* = x - dt v_b(x), X = x - dt/2 (v_b(x) + v_a(X*))
+        TRY(sl_characteristics(c->sl, vsrc_a, vnode(c, b), c->to_vox, -c->dt, Dfstep(c, j), c->st));
+        // adjoint: X+* = x + dt v_a(x), X+ = x + dt/2 (v_a(x) + v_b(X+*))
+        TRY(sl_characteristics(c->sl, vsrc_b, vnode(c, a), c->to_vox, +c->dt, Dbstep(c, j), c->st));
+        // gamma = 1 + dt/2 (d_b(X+) + (1 + dt d_b(X+)) d_a(x))
+        TRY(sl_prep_adjoint(c->sl, dsrc_b, dnode(c, a), Dbstep(c, j), c->dt, gamstep(c, j), c->st));
+        // W = dt/2 (v_a(X) + v_b(x))
+        if (c->p.variant == LDDMM_V_DEFSTATE)
+            TRY(sl_prep_source(c->sl, vsrc_a, vnode(c, b), Dfstep(c, j), c->dt, Wstep(c, j), c->st));
+    }
     return LDDMM_OK;
 }
 
@@ -215,7 +258,7 @@ static int state_defstate(lddmm_ctx* c) {
     LDDMM_CUDA(cudaMemsetAsync(c->ut, 0, kc3 * sizeof(float2), c->st));
     for (int j = 0; j < c->p.nt; ++j) {
         TRY(include(c, c->ut + j * kc3, 3, c->fa, c->n, -1, cubic(c)));
-        TRY(sl_gather_add(c->sl, c->fa, c->Df, c->W, 3, c->fb, c->st));
+        TRY(sl_gather_add(c->sl, c->fa, Dfstep(c, j), Wstep(c, j), 3, c->fb, c->st));
         TRY(project(c, c->fb, 3, c->ut + (j + 1) * kc3));
     }
     c->solves++;
@@ -255,11 +298,11 @@ static int data_term(lddmm_ctx* c, float* rho) {
     return LDDMM_OK;
 }
 
-// E_reg = 1/2 <L~ v~, v~> into dsc[1]
+// E_reg = 1/2 <L~ v~, v~> into dsc[1] (non-stationary: sum_j w_j <L~ v~_j, v~_j>)
 static int reg_term(lddmm_ctx* c, const float2* vt) {
     float2* t = c->cv[lddmm_ctx::C_T0];
-    TRY(cube_apply_L(t, vt, 1.f, 0.f, nullptr, c->K, 3, c->p.alpha, c->p.s, 1, c->st));
-    TRY(dot_f2(t, vt, 3 * c->kc, c->partials, c->dsc + 1, c->st));
+    TRY(cube_apply_L(t, vt, 1.f, 0.f, nullptr, c->K, 3 * nodes(c), c->p.alpha, c->p.s, 1, c->st));
+    TRY(dot_f2_nodes(t, vt, 3 * c->kc, nodes(c), c->dt, c->partials, c->dsc + 1, c->st));
     return LDDMM_OK;
 }
 
@@ -268,7 +311,7 @@ static int ensure_state(lddmm_ctx* c, const float2* vt, bool known_same) {
     if (known_same && c->vel_valid) return LDDMM_OK;
     float2* cur = c->cv[lddmm_ctx::C_CUR];
     if (vt != cur)
-        LDDMM_CUDA(cudaMemcpyAsync(cur, vt, 3 * c->kc * sizeof(float2), cudaMemcpyDeviceToDevice, c->st));
+        LDDMM_CUDA(cudaMemcpyAsync(cur, vt, nvec(c) * sizeof(float2), cudaMemcpyDeviceToDevice, c->st));
     c->vel_valid = false;
     c->traj_valid = false;
     c->warp_valid = false;
@@ -336,6 +379,37 @@ static int adjoint_defstate(lddmm_ctx* c, const float* rho1, const float2* base,
     return LDDMM_OK;
 }
 
+// Non-stationary DEFSTATE adjoint, backward from rho(1): at every node j
+// out_j = L~ base_j + rho~_j - pi((D iota u~_j)^T iota(rho~_j)) (the integrand of Eqs. 32-33
+// at t_j), step j along X+_j with the factor gamma_j of nodes j and j + 1.
+static int adjoint_defstate_ns(lddmm_ctx* c, const float* rho1, const float2* base, float2* out,
+                               bool hess) {
+    const long n = c->n, kc3 = 3 * c->kc;
+    const int nt = c->p.nt;
+    float2* rt = c->cv[lddmm_ctx::C_T1];     // rho~_j
+    float2* pj = c->cv[lddmm_ctx::C_T0];     // node j's assembled data term
+    TRY(project(c, rho1, 3, rt));
+    for (int j = nt; j >= 0; --j) {
+        if (j < nt) {
+            const float* src = c->fc;        // iota(rho~_{j+1})
+            if (cubic(c)) {
+                TRY(include(c, rt, 3, c->fa, n, -1, 1));
+                src = c->fa;
+            }
+            TRY(sl_gather_scale(c->sl, src, Dbstep(c, j), gamstep(c, j), 3, c->fd, c->st));
+            TRY(project(c, c->fd, 3, rt));
+        }
+        TRY(include(c, rt, 3, c->fc, n, -1, 0));
+        TRY(accum_JT(c->g, jac(c, j, hess), jac_bf16(c) && hess, c->fc, 1.f, c->acc, 1, c->st));
+        TRY(project(c, c->acc, 3, pj));
+        TRY(cube_axpby(pj, 1.f, rt, -1.f, pj, kc3, c->st));
+        TRY(cube_apply_L(vcube(c, out, j), vcube(c, base, j), 1.f, 1.f, pj, c->K, 3, c->p.alpha,
+                         c->p.s, 1, c->st));
+    }
+    c->solves++;
+    return LDDMM_OK;
+}
+
 // IMAGE, gradient (Eqs. 15, 18; Table 1 row 2): spatial adjoint lambda from
 // lambda(1) = -(2/sigma2)(m1 - I1); g = L~ v~ + sum_j w_j pi(iota(pi(lambda_j)) Gm_j).
 static int gradient_image_adjoint(lddmm_ctx* c, const float2* vt, float2* g) {
@@ -387,7 +461,8 @@ static int gradient_impl(lddmm_ctx* c, const float2* vt, bool known_same, float2
     float2* cur = c->cv[lddmm_ctx::C_CUR];
     if (c->p.variant == LDDMM_V_DEFSTATE) {
         TRY(data_term(c, c->fb));
-        TRY(adjoint_defstate(c, c->fb, cur, g, false));
+        if (ns(c)) TRY(adjoint_defstate_ns(c, c->fb, cur, g, false));
+        else TRY(adjoint_defstate(c, c->fb, cur, g, false));
     } else {
         TRY(data_term(c, nullptr));
         TRY(gradient_image_adjoint(c, cur, g));
@@ -422,8 +497,10 @@ static int hessian_impl(lddmm_ctx* c, const float2* dvt, float2* out) {
                 TRY(bspline_prefilter(c->g, Fold, 3, c->acc, c->st));
                 Fsrc = c->acc;
             }
-            TRY(sl_inc_defstate(c->sl, c->fb, c->Df, Fsrc, jac(c, j + 1, true), jac_bf16(c), c->dvsp,
-                                c->dt, c->fc, Fnew, c->st));
+            // non-stationary: the right-hand side at node j + 1 uses dv~_{j+1}
+            if (ns(c)) TRY(include(c, vcube(c, dvt, j + 1), 3, c->dvsp, n, -1, 0));
+            TRY(sl_inc_defstate(c->sl, c->fb, Dfstep(c, j), Fsrc, jac(c, j + 1, true), jac_bf16(c),
+                                c->dvsp, c->dt, c->fc, Fnew, c->st));
             TRY(project(c, c->fc, 3, dut));
             std::swap(Fold, Fnew);
         }
@@ -431,6 +508,7 @@ static int hessian_impl(lddmm_ctx* c, const float2* dvt, float2* out) {
         // drho(1) = pi(-(2/sigma2) dm1 G), dm1 = -G . iota(du~(1))
         TRY(include(c, dut, 3, c->fa, n, -1, 0));
         TRY(defstate_drho1(c->g, c->G, c->fa, c->p.sigma2, c->fb, c->st));
+        if (ns(c)) return adjoint_defstate_ns(c, c->fb, dvt, out, true);
         return adjoint_defstate(c, c->fb, dvt, out, true);
     }
     // IMAGE: incremental state D~_t dm~ = -grad~ m~ * dv~ (Eq. 19; Table 1 row 5)
@@ -490,7 +568,7 @@ static int same_as_current(lddmm_ctx* c, const float2* vt, bool* same) {
     if (!c->vel_valid) return LDDMM_OK;
     int* flag = reinterpret_cast<int*>(c->dsc + 8);
     LDDMM_CUDA(cudaMemsetAsync(flag, 0, sizeof(int), c->st));
-    long n = 3 * c->kc;
+    long n = nvec(c);
     {
         KTRACE("cube_neq", c->st, 16.0 * n, 0);
         k_cube_neq<<<(int)((n + 255) / 256), 256, 0, c->st>>>(vt, c->cv[lddmm_ctx::C_CUR], n, flag);
@@ -551,8 +629,9 @@ static int hessian_pcg(lddmm_ctx* c) {
 }
 
 // ------------------------------------------------------------------ GN-Krylov driver
+// <a, b> of velocity-shaped vectors (non-stationary: trapezoid-weighted over the nodes)
 static double dot_host(lddmm_ctx* c, const float2* a, const float2* b, int* rc) {
-    *rc = dot_f2(a, b, 3 * c->kc, c->partials, c->dsc, c->st);
+    *rc = dot_f2_nodes(a, b, 3 * c->kc, nodes(c), c->dt, c->partials, c->dsc, c->st);
     if (*rc) return 0;
     *rc = read_scalars(c, 1);
     return c->hsc[0];
@@ -560,8 +639,9 @@ static double dot_host(lddmm_ctx* c, const float2* a, const float2* b, int* rc) 
 
 static int register_impl(lddmm_ctx* c, float2* v_io, const double* gref_in, lddmm_report* rep) {
     auto t0 = std::chrono::steady_clock::now();
-    const long kc3 = 3 * c->kc;
+    const long kc3 = nvec(c);             // float2 per velocity-shaped vector
     const int K = c->K;
+    const int ncube = 3 * nodes(c);       // K^3 cubes per vector
     std::memset(rep, 0, sizeof(*rep));
     c->solves = 0;
     int rc = 0;
@@ -571,7 +651,7 @@ static int register_impl(lddmm_ctx* c, float2* v_io, const double* gref_in, lddm
     float2 *r = c->cv[lddmm_ctx::C_R], *z = c->cv[lddmm_ctx::C_Z], *pp = c->cv[lddmm_ctx::C_P];
     float2 *Hp = c->cv[lddmm_ctx::C_HP], *x = c->cv[lddmm_ctx::C_X];
     LDDMM_CUDA(cudaMemcpyAsync(v, v_io, kc3 * sizeof(float2), cudaMemcpyDeviceToDevice, c->st));
-    TRY(cube_hermitian(v, K, 3, c->st));
+    TRY(cube_hermitian(v, K, ncube, c->st));
 
     double gref2, grefi;
     double E, Er, Ed;
@@ -617,7 +697,7 @@ static int register_impl(lddmm_ctx* c, float2* v_io, const double* gref_in, lddm
         // PCG on H x = -g with preconditioner L~^{-1}, x0 = 0
         LDDMM_CUDA(cudaMemsetAsync(x, 0, kc3 * sizeof(float2), c->st));
         TRY(cube_axpby(r, -1.f, g, 0.f, nullptr, kc3, c->st));
-        TRY(cube_apply_L(z, r, 1.f, 0.f, nullptr, K, 3, c->p.alpha, c->p.s, -1, c->st));
+        TRY(cube_apply_L(z, r, 1.f, 0.f, nullptr, K, ncube, c->p.alpha, c->p.s, -1, c->st));
         TRY(cube_axpby(pp, 1.f, z, 0.f, nullptr, kc3, c->st));
         double rz = dot_host(c, r, z, &rc);
         TRY(rc);
@@ -628,7 +708,7 @@ static int register_impl(lddmm_ctx* c, float2* v_io, const double* gref_in, lddm
             TRY(rc);
             if (pHp <= 0.0) {
                 if (i == 0)  // preconditioned steepest descent
-                    TRY(cube_apply_L(x, r, 1.f, 0.f, nullptr, K, 3, c->p.alpha, c->p.s, -1, c->st));
+                    TRY(cube_apply_L(x, r, 1.f, 0.f, nullptr, K, ncube, c->p.alpha, c->p.s, -1, c->st));
                 break;
             }
             const double a = rz / pHp;
@@ -637,7 +717,7 @@ static int register_impl(lddmm_ctx* c, float2* v_io, const double* gref_in, lddm
             double rn = std::sqrt(dot_host(c, r, r, &rc));
             TRY(rc);
             if (rn <= eta * gn) break;
-            TRY(cube_apply_L(z, r, 1.f, 0.f, nullptr, K, 3, c->p.alpha, c->p.s, -1, c->st));
+            TRY(cube_apply_L(z, r, 1.f, 0.f, nullptr, K, ncube, c->p.alpha, c->p.s, -1, c->st));
             double rz2 = dot_host(c, r, z, &rc);
             TRY(rc);
             TRY(cube_axpby(pp, 1.f, z, (float)(rz2 / rz), pp, kc3, c->st));
@@ -703,17 +783,18 @@ static int ctx_alloc(lddmm_ctx* c) {
     TRY(dalloc_t(c, &c->I0, n));
     TRY(dalloc_t(c, &c->I1, n));
     if (cub) TRY(dalloc_t(c, &c->I0c, n));
-    TRY(dalloc_t(c, &c->v, 3 * n));
-    TRY(dalloc_t(c, &c->d, n));
+    const size_t nodes_ = (size_t)nodes(c), steps = ns(c) ? (size_t)nt : 1;
+    TRY(dalloc_t(c, &c->v, nodes_ * 3 * n));
+    TRY(dalloc_t(c, &c->d, nodes_ * n));
     if (cub) {
-        TRY(dalloc_t(c, &c->vc, 3 * n));
-        TRY(dalloc_t(c, &c->dc, n));
+        TRY(dalloc_t(c, &c->vc, nodes_ * 3 * n));
+        TRY(dalloc_t(c, &c->dc, nodes_ * n));
     }
-    TRY(dalloc_t(c, &c->Df, 3 * n));
-    TRY(dalloc_t(c, &c->Db, 3 * n));
-    TRY(dalloc_t(c, &c->gam, n));
+    TRY(dalloc_t(c, &c->Df, steps * 3 * n));
+    TRY(dalloc_t(c, &c->Db, steps * 3 * n));
+    TRY(dalloc_t(c, &c->gam, steps * n));
     if (def) {
-        TRY(dalloc_t(c, &c->W, 3 * n));
+        TRY(dalloc_t(c, &c->W, steps * 3 * n));
         TRY(dalloc_t(c, &c->ut, (size_t)(nt + 1) * kc3));
         TRY(dalloc_t(c, &c->Du, (size_t)(nt + 1) * 9 * n));
         if (jac_bf16(c)) TRY(dalloc_t(c, reinterpret_cast<uint16_t**>(&c->Du16), (size_t)(nt + 1) * 9 * n));
@@ -728,8 +809,8 @@ static int ctx_alloc(lddmm_ctx* c) {
     TRY(dalloc_t(c, &c->s1, se));
     TRY(dalloc_t(c, &c->s2, se));
     for (int i = 0; i < lddmm_ctx::C_NUM; ++i) {
-        TRY(dalloc_t(c, &c->cv[i], kc3));
-        LDDMM_CUDA(cudaMemsetAsync(c->cv[i], 0, kc3 * sizeof(float2), c->st));
+        TRY(dalloc_t(c, &c->cv[i], nvec(c)));
+        LDDMM_CUDA(cudaMemsetAsync(c->cv[i], 0, nvec(c) * sizeof(float2), c->st));
     }
     TRY(dalloc_t(c, &c->partials, 2 * kReduceBlocks));   // the Jacobian range uses two rows
     TRY(dalloc_t(c, &c->dsc, 16));

@@ -110,6 +110,10 @@ int cube_hermitian(float2* c, int K, int ncomp, cudaStream_t st);
 int dot_f2(const float2* a, const float2* b, long n, double* partials, double* out,
            cudaStream_t st);
 int max_abs_f2(const float2* a, long n, double* partials, double* out, cudaStream_t st);
+// sum_j w_j <a_j, b_j> over `nodes` blocks of npn elements, w_j trapezoid weights of step dt
+// (nodes == 1: plain dot)
+int dot_f2_nodes(const float2* a, const float2* b, long npn, int nodes, double dt,
+                 double* partials, double* out, cudaStream_t st);
 constexpr int kReduceBlocks = 296;  // 2 x 148 SMs
 
 // ---------------------------------------------------------------- SL kernels (sl.cu)

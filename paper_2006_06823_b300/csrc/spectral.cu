@@ -877,6 +877,21 @@ __global__ void k_dot_f2(const float2* a, const float2* b, long n, double* parti
     block_reduce_store<false>(s, partials + blockIdx.x);
 }
 
+// sum over nodes j of w_j <a_j, b_j>, a_j the j-th block of npn elements; w_j the trapezoid
+// weights of nodes 0..nodes-1 with step dt (nodes == 1: weight 1)
+__global__ void k_dot_f2_nodes(const float2* a, const float2* b, long npn, int nodes, double dt,
+                               double* partials) {
+    double s = 0.0;
+    const long n = npn * nodes;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const int j = (int)(i / npn);
+        const double w = nodes == 1 ? 1.0 : (j == 0 || j == nodes - 1) ? 0.5 * dt : dt;
+        float2 x = a[i], y = b[i];
+        s += w * ((double)x.x * y.x + (double)x.y * y.y);
+    }
+    block_reduce_store<false>(s, partials + blockIdx.x);
+}
+
 __global__ void k_maxabs_f2(const float2* a, long n, double* partials) {
     double s = 0.0;
     for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
@@ -899,6 +914,19 @@ int dot_f2(const float2* a, const float2* b, long n, double* partials, double* o
     {
         KTRACE("dot_f2", st, 16.0 * n, 4.0 * n);
         k_dot_f2<<<kReduceBlocks, 256, 0, st>>>(a, b, n, partials);
+    }
+    LDDMM_CHECK_LAUNCH();
+    KTRACE("finalize", st, 8.0 * kReduceBlocks, kReduceBlocks);
+    k_finalize<<<1, 256, 0, st>>>(partials, kReduceBlocks, out, 0);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+int dot_f2_nodes(const float2* a, const float2* b, long npn, int nodes, double dt,
+                 double* partials, double* out, cudaStream_t st) {
+    {
+        KTRACE("dot_f2", st, 16.0 * npn * nodes, 5.0 * npn * nodes);
+        k_dot_f2_nodes<<<kReduceBlocks, 256, 0, st>>>(a, b, npn, nodes, dt, partials);
     }
     LDDMM_CHECK_LAUNCH();
     KTRACE("finalize", st, 8.0 * kReduceBlocks, kReduceBlocks);

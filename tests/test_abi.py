@@ -85,3 +85,13 @@ def test_net_calls_reject_null_network():
     assert lib.lddmm_net_warm_start(None, 64, 64, 64, None, None, 32, None) == L.EINVAL
     assert lib.lddmm_net_num_params(None) == 0
     assert lib.lddmm_net_destroy(None) == L.OK
+
+
+def test_nonstationary_flag_is_validated_before_any_device_work():
+    lib = L.load()
+    for variant, flag in ((L.V_IMAGE, 1), (L.V_DEFSTATE, 2)):
+        p = L.Params(32, 32, 32, 16, 10, variant, L.INTERP_LINEAR, 0.0025, 2, 0.01, 5, 10,
+                     1e-3, L.PREC_FP32, flag)
+        h = ctypes.c_void_p(123)
+        assert lib.lddmm_create(ctypes.byref(p), None, ctypes.byref(h)) == L.EINVAL
+        assert b"nonstationary" in lib.lddmm_last_error() or b"non-stationary" in lib.lddmm_last_error()
