@@ -10,7 +10,7 @@ Modules
   spectral  band-limited projection pi, inclusion iota, spectral derivatives, L~ (Sec. 2.2)
   interp    trilinear and periodic cubic B-spline interpolation (Sec. 3.1, Sec. 4.2)
   sl        SL characteristics and the Table 1 transport equations, Heun (SL-RK) steps (Sec. 3)
-  variants  energy, gradient and Gauss-Newton Hessian-vector products (Sec. 2.3.1, 2.3.3)
+  variants  energy, gradient and Gauss-Newton Hessian-vector products (Sec. 2.3.1-2.3.3)
   gnk       PCG with preconditioner L~^-1, Gauss-Newton update, line search (Sec. 2.1-2.2)
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test against a closed

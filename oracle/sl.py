@@ -84,6 +84,19 @@ def heun_divergence_step(u, Dplus, d, dt, order):
     return a + 0.5 * dt * (f_old + u_star * d)
 
 
+def heun_jacobian_step(U, Dplus, d, dt, order):
+    """-D_t U = -div v + U div v (the Jacobian equation of the state-equation variant,
+    Sec. 2.3.2), one step backward in time.
+
+    Along the backward characteristic D_tau U = d (U - 1) with d = div v, so
+    a = U^{j+1}(X+); f_old = d(X+) (a - 1); U* = a + dt f_old;
+    U^j(x) = a + dt/2 (f_old + d(x) (U* - 1))."""
+    a = I.interpolate(U, Dplus, order)
+    f_old = I.interpolate(d, Dplus, order) * (a - 1.0)
+    u_star = a + dt * f_old
+    return a + 0.5 * dt * (f_old + d * (u_star - 1.0))
+
+
 def heun_divergence_step_ns(u, Dplus, d_next, d_here, dt, order):
     """-D_t u = u div v_t between nodes t_j and t_{j+1} (non-stationary v): as
     heun_divergence_step with d(X+) taken from d_{j+1} and d(x) from d_j."""
@@ -121,6 +134,11 @@ def bl_heun_source_step(c, D, F_old, F_new, dt, order, shape, K):
 def bl_heun_divergence_step_ns(c, Dplus, d_next, d_here, dt, order, shape, K):
     """One backward BL step of -D~_t u~ = u~ * div~ v~_t with node-dependent divergence."""
     return S.project(heun_divergence_step_ns(S.include(c, shape), Dplus, d_next, d_here, dt, order), K)
+
+
+def bl_heun_jacobian_step(c, Dplus, d, dt, order, shape, K):
+    """One backward BL step of -D~_t U~ = -div~ v~ + U~ * div~ v~ (Sec. 2.3.2)."""
+    return S.project(heun_jacobian_step(S.include(c, shape), Dplus, d, dt, order), K)
 
 
 def bl_heun_divergence_step(c, Dplus, d, dt, order, shape, K):

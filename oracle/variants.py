@@ -2,12 +2,16 @@
 
 TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 
-Two variants of Sec. 2.3, both with a stationary band-limited velocity v~ (one cube for all
-t) and SL-RK integration of every equation (Sec. 3.3, Table 1):
+The three variants of Sec. 2.3, each with a stationary band-limited velocity v~ (one cube
+for all t) and SL-RK integration of every equation (Sec. 3.3, Table 1):
 
   * IMAGE  -- original BL PDE-LDDMM (Sec. 2.3.1, Eqs. 15-20): spatial state m and adjoint
     lambda, band-limited incremental state dm~ and incremental adjoint dlambda~;
     g = L~v~ + int lambda~ * grad~ m~ dt, H dv~ = L~dv~ + int dlambda~ * grad~ m~ dt.
+  * STATE -- BL PDE-LDDMM based on the state equation (Sec. 2.3.2): m(t) = I0 o phi(t),
+    lambda(t) = J(t) lambda(1) o psi(t), with phi = id - iota(u~) from the deformation state
+    equation, psi = id - iota(nu~) and J = 1 - iota(U~) from two backward equations; the
+    gradient and Hessian are those of IMAGE (Eqs. 15-16) with these m and lambda.
   * DEFSTATE -- BL PDE-LDDMM based on the deformation state equation (Sec. 2.3.3,
     Eqs. 31-37): displacement u~ with phi = id - iota(u~), m(1) = I0 o phi(1); adjoint rho~;
     g = L~v~ + int (rho~ - D~u~ * rho~) dt, H dv~ = L~dv~ + int (drho~ - D~u~ * drho~) dt.
@@ -26,6 +30,17 @@ Readings fixed here (the paper is ambiguous, silent or has typos at these places
     dm(1) = -G . iota(du~(1)) and G = (grad I0) o phi(1), the exact derivative of
     m(1) = I0 o (id - iota(u~(1))) with respect to u~(1) (the paper writes grad m(1)).
   * Time integrals: trapezoid rule over the nt + 1 nodes t_j = j / nt.
+  * STATE: the nu~ equation of Sec. 2.3.2 prints -nu~_t as its right-hand side; psi(t) maps
+    the point at time t to its position at time 1, psi = id - iota(nu~), which makes the
+    right-hand side -v~ (psi(t) = id + int_t^1 v), and that is used.
+  * STATE, Gauss-Newton Hessian: lambda(t) = J(t) lambda(1) o psi(t) varies with dv through
+    lambda(1), psi and J; the Sec. 2.3.2 formula for dlambda keeps the psi term, which is
+    proportional to grad lambda(1), i.e. to the residual. Gauss-Newton drops every term
+    proportional to the residual (as IMAGE drops lambda grad dm), which leaves
+    dlambda(t) = J(t) dlambda(1) o psi(t) with dlambda(1) = -(2/sigma^2) dm(1) and
+    dm(1) = -G . iota(du~(1)) (the sign of the exact derivative of I0 o (id - iota(u~)));
+    du~ solves the incremental deformation state equation (Eq. 36), and that is what is
+    used. dnu~ is then not needed.
 """
 from __future__ import annotations
 
@@ -38,6 +53,7 @@ from . import sl as SL
 from . import spectral as S
 
 IMAGE = 1
+STATE = 2
 DEFSTATE = 3
 
 
@@ -153,10 +169,71 @@ class Problem:
         """iota(grad~ m~_j) with m~_j = pi(m_j) (Sec. 2.3.1), [j][3] spatial, physical."""
         return [S.include(S.grad(S.project(m, self.p.K)), self.shape) for m in ms]
 
+    def _assemble_image(self, base, lams, gms, project_lam=True):
+        """L~ base + sum_j w_j pi(iota(lambda~_j) iota(grad~ m~_j)) (Eqs. 15-16); lams are
+        spatial fields (projected first, lambda~ = pi(lambda)) or, project_lam=False, cubes."""
+        p = self.p
+        out = S.apply_L(base, p.alpha, p.s).astype(np.complex128)
+        for j in range(p.nt + 1):
+            lt = S.project(lams[j], p.K) if project_lam else lams[j]
+            out = out + self.tw[j] * S.project(S.include(lt, self.shape)[None] * gms[j], p.K)
+        return out
+
+    # ------------------------------------------------------------------ STATE (V2)
+    def _compose_I0(self, us):
+        """m_j = I0 o phi_j, phi_j = id - iota(u~_j) (Sec. 2.3.2), every node."""
+        return [I.interpolate(self.I0, -S.include(u, self.shape) * self.to_vox[:, None, None, None],
+                              self.p.order) for u in us]
+
+    def inverse_maps(self, vt):
+        """nu~_j and U~_j at every node (Sec. 2.3.2), backward from nu~(1) = 0, U~(1) = 0:
+        -D~_t nu~ = -v~ and -D~_t U~ = -div~ v~ + U~ * div~ v~ in SL form (Sec. 3.3).
+        psi_j = id - iota(nu~_j) (physical), J_j = 1 - iota(U~_j)."""
+        p = self.p
+        v, V, d = self.velocity(vt)
+        Dp = SL.departure_offsets(V, self.dt, -1, p.order)
+        nu = np.zeros((3, p.K, p.K, p.K), dtype=np.complex128)
+        U = np.zeros((p.K, p.K, p.K), dtype=np.complex128)
+        nus, Us = [None] * (p.nt + 1), [None] * (p.nt + 1)
+        nus[p.nt], Us[p.nt] = nu, U
+        for j in range(p.nt - 1, -1, -1):
+            # backward in time: D_tau nu = -v along X+
+            nu = SL.bl_heun_source_step(nu, Dp, -v, -v, self.dt, p.order, self.shape, p.K)
+            U = SL.bl_heun_jacobian_step(U, Dp, d, self.dt, p.order, self.shape, p.K)
+            nus[j], Us[j] = nu, U
+        return nus, Us
+
+    def _pull_back(self, f, nus, Us):
+        """f_j = J_j (f o psi_j) at every node (lambda(t) = J(t) lambda(1) o psi(t))."""
+        out = []
+        for nu, U in zip(nus, Us):
+            offs = -S.include(nu, self.shape) * self.to_vox[:, None, None, None]
+            out.append((1.0 - S.include(U, self.shape)) * I.interpolate(f, offs, self.p.order))
+        return out
+
+    def _grads_state(self, vt):
+        """u~_j, m_j, iota(grad~ m~_j) and the inverse maps of the STATE variant."""
+        us = self.state_defstate(vt)
+        ms = self._compose_I0(us)
+        nus, Us = self.inverse_maps(vt)
+        return us, ms, self._grad_mtilde(ms), nus, Us
+
+    def _inc_defstate(self, vt, dvt, us):
+        """du~(1) from D~_t du~ = dv~ - D~u~ * dv~, du~(0) = 0 (Eq. 36; Table 1 row 7)."""
+        p = self.p
+        v, V, d = self.velocity(vt)
+        D = SL.departure_offsets(V, self.dt, +1, p.order)
+        dv = S.include(dvt, self.shape)
+        F = [dv - np.einsum("abzyx,bzyx->azyx", Ju, dv) for Ju in self._jacobians(us)]
+        du = np.zeros_like(dvt, dtype=np.complex128)
+        for j in range(p.nt):
+            du = SL.bl_heun_source_step(du, D, F[j], F[j + 1], self.dt, p.order, self.shape, p.K)
+        return du
+
     # ------------------------------------------------------------------ public API
     def objective(self, vt):
         """(E, E_reg, E_data, m(1)) at v~ (Eq. 10 with the variant's state equation)."""
-        if self.p.variant == DEFSTATE:
+        if self.p.variant in (DEFSTATE, STATE):
             us = self.state_defstate(vt)
             m1, _ = self._warp_I0(us[-1])
         else:
@@ -165,9 +242,14 @@ class Problem:
         return er + ed, er, ed, m1
 
     def gradient(self, vt):
-        """Returns (E, E_reg, E_data, g~) (Eq. 15 for IMAGE, Eq. 32 for DEFSTATE)."""
+        """Returns (E, E_reg, E_data, g~) (Eq. 15 for IMAGE and STATE, Eq. 32 for DEFSTATE)."""
         p = self.p
-        if p.variant == DEFSTATE:
+        if p.variant == STATE:
+            us, ms, gms, nus, Us = self._grads_state(vt)
+            m1, _ = self._warp_I0(us[-1])
+            lams = self._pull_back(-(2.0 / p.sigma2) * (m1 - self.I1), nus, Us)
+            g = self._assemble_image(vt, lams, gms)
+        elif p.variant == DEFSTATE:
             us = self.state_defstate(vt)
             m1, G = self._warp_I0(us[-1])
             r = m1 - self.I1
@@ -185,34 +267,30 @@ class Problem:
             for j in range(p.nt - 1, -1, -1):                   # Eq. 18, Table 1 row 2
                 lam = SL.heun_divergence_step(lam, Dp, d, self.dt, p.order)
                 lams[j] = lam
-            gms = self._grad_mtilde(ms)
-            g = S.apply_L(vt, p.alpha, p.s).astype(np.complex128)
-            for j in range(p.nt + 1):                            # lambda~ * grad~ m~
-                lam_bl = S.include(S.project(lams[j], p.K), self.shape)
-                g = g + self.tw[j] * S.project(lam_bl[None] * gms[j], p.K)
+            g = self._assemble_image(vt, lams, self._grad_mtilde(ms))   # lambda~ * grad~ m~
         er, ed = self.energy_reg(vt), self.energy_data(m1)
         return er + ed, er, ed, g
 
     def hessian_matvec(self, vt, dvt):
-        """Gauss-Newton H dv~ at v~ (Eq. 16 for IMAGE, Eq. 33 as read for DEFSTATE)."""
+        """Gauss-Newton H dv~ at v~ (Eq. 16 for IMAGE and, as read, STATE; Eq. 33 as read
+        for DEFSTATE)."""
         p = self.p
         v, V, d = self.velocity(vt)
         D = SL.departure_offsets(V, self.dt, +1, p.order)
         dv = S.include(dvt, self.shape)
+        if p.variant == STATE:
+            us, ms, gms, nus, Us = self._grads_state(vt)
+            _, G = self._warp_I0(us[-1])
+            dm1 = -np.sum(G * S.include(self._inc_defstate(vt, dvt, us), self.shape), axis=0)
+            dlams = self._pull_back(-(2.0 / p.sigma2) * dm1, nus, Us)
+            return self._assemble_image(dvt, dlams, gms)
         if p.variant == DEFSTATE:
             us = self.state_defstate(vt)
-            Jus = self._jacobians(us)
             _, G = self._warp_I0(us[-1])
-            # incremental state D~_t du~ = dv~ - D~u~ * dv~ (Eq. 36; Table 1 row 7)
-            F = [dv - np.einsum("abzyx,bzyx->azyx", Ju, dv) for Ju in Jus]
-            du = np.zeros_like(dvt, dtype=np.complex128)
-            for j in range(p.nt):
-                du = SL.bl_heun_source_step(du, D, F[j], F[j + 1], self.dt, p.order,
-                                            self.shape, p.K)
-            dm1 = -np.sum(G * S.include(du, self.shape), axis=0)
+            dm1 = -np.sum(G * S.include(self._inc_defstate(vt, dvt, us), self.shape), axis=0)
             drho1 = S.project(-(2.0 / p.sigma2) * dm1[None] * G, p.K)
             drhos = self._adjoint_bl(drho1, vt)
-            return self._assemble_defstate(dvt, drhos, Jus)
+            return self._assemble_defstate(dvt, drhos, self._jacobians(us))
         ms = self.state_image(vt)
         gms = self._grad_mtilde(ms)
         # incremental state D~_t dm~ = -grad~ m~ * dv~ (Eq. 19; Table 1 row 5)
