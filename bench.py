@@ -335,7 +335,8 @@ FORMS = [("defstate/linear/bf16x3_jbf16", "V_DEFSTATE", "INTERP_LINEAR", "PREC_B
          ("image/linear/fp32", "V_IMAGE", "INTERP_LINEAR", "PREC_FP32", False),
          ("defstate/cubic/fp32", "V_DEFSTATE", "INTERP_CUBIC", "PREC_FP32", False),
          ("image/cubic/fp32", "V_IMAGE", "INTERP_CUBIC", "PREC_FP32", False),
-         ("defstate/linear/fp32/nonstationary", "V_DEFSTATE", "INTERP_LINEAR", "PREC_FP32", True)]
+         ("defstate/linear/fp32/nonstationary", "V_DEFSTATE", "INTERP_LINEAR", "PREC_FP32", True),
+         ("state/linear/fp32", "V_STATE", "INTERP_LINEAR", "PREC_FP32", False)]
 
 
 def measure_forms(L, torch, I0d, I1d, stream, flush):

@@ -44,7 +44,13 @@ typedef enum {
     LDDMM_ELINESEARCH = -6  /* no acceptable update length (returned in reports only) */
 } lddmm_status;
 
-enum { LDDMM_V_IMAGE = 1, LDDMM_V_DEFSTATE = 3 };          /* Sec. 2.3.1, Sec. 2.3.3 */
+/* Variant (Sec. 2.3). IMAGE: transported image m and adjoint lambda (Sec. 2.3.1).
+ * STATE: m(t) = I0 o phi(t), lambda(t) = J(t) lambda(1) o psi(t) with phi = id - iota(u~)
+ * from the deformation state equation and psi = id - iota(nu~), J = 1 - iota(U~) from two
+ * backward equations (Sec. 2.3.2); gradient and Gauss-Newton Hessian of Eqs. 15-16 with
+ * dlambda(t) = J(t) dlambda(1) o psi(t) (stationary velocity only). DEFSTATE: displacement
+ * u~ and adjoint rho~ (Sec. 2.3.3). STATE and DEFSTATE share the energy (the same phi(1)). */
+enum { LDDMM_V_IMAGE = 1, LDDMM_V_STATE = 2, LDDMM_V_DEFSTATE = 3 };
 enum { LDDMM_INTERP_LINEAR = 1, LDDMM_INTERP_CUBIC = 3 };  /* Sec. 3.1, Sec. 4.2 */
 /* Precision form. FP32: FP32-accurate results; the x stages of pi and iota run on the
  * tensor cores as split TF32 products (hi + lo, three products, FP32 accumulation) where the
@@ -64,7 +70,7 @@ typedef struct {
     int nx, ny, nz;    /* grid */
     int K;             /* band (cube edge), even */
     int nt;            /* time steps on [0, 1] */
-    int variant;       /* LDDMM_V_IMAGE or LDDMM_V_DEFSTATE */
+    int variant;       /* LDDMM_V_IMAGE, LDDMM_V_STATE or LDDMM_V_DEFSTATE */
     int interp;        /* LDDMM_INTERP_LINEAR or LDDMM_INTERP_CUBIC */
     double alpha;      /* L = (Id - alpha Laplacian)^s, Eq. 1 */
     int s;
@@ -116,18 +122,18 @@ int lddmm_set_images_host(lddmm_ctx* ctx, const float* I0_host, const float* I1_
 /* ------------------------------------------------------------------ the optimiser */
 
 /* Energy of Eq. 10 at the band-limited velocity v (cube float[3][K][K][K][2]) under the
- * context's variant: solves the state equation (Eq. 17 or Eq. 34). Writes host doubles
+ * context's variant: solves the state equation (Eq. 17, or Eq. 34 for STATE and DEFSTATE). Writes host doubles
  * (any pointer may be NULL). Synchronises. */
 int lddmm_objective(lddmm_ctx* ctx, const float* v, double* E, double* E_reg, double* E_data);
 
-/* Gradient g~ at v (Eq. 15 for IMAGE, Eq. 32 for DEFSTATE) into g (device cube
+/* Gradient g~ at v (Eq. 15 for IMAGE and STATE, Eq. 32 for DEFSTATE) into g (device cube
  * float[3][K][K][K][2]); also leaves the state trajectory of v cached for
  * lddmm_hessian_matvec. Energies as in lddmm_objective (host, may be NULL). Synchronises. */
 int lddmm_gradient(lddmm_ctx* ctx, const float* v, float* g, double* E, double* E_reg,
                    double* E_data);
 
-/* Gauss-Newton Hessian-vector product H(v) dv (Eq. 16 for IMAGE, Eq. 33 read as the
- * Gauss-Newton operator for DEFSTATE) into Hdv (device cubes). Recomputes the state of
+/* Gauss-Newton Hessian-vector product H(v) dv (Eq. 16 for IMAGE and STATE, Eq. 33 read as
+ * the Gauss-Newton operator for DEFSTATE) into Hdv (device cubes). Recomputes the state of
  * v when it is not the cached one. Asynchronous. */
 int lddmm_hessian_matvec(lddmm_ctx* ctx, const float* v, const float* dv, float* Hdv);
 
@@ -168,11 +174,11 @@ int lddmm_autotune(lddmm_ctx* ctx, const char* cache_path, int* block_x_out);
  * (device cube): J = det(I - D iota(u~(1))) per voxel (Sec. 5.1.1 reports its minimum and
  * maximum; J < 0 flags a fold). J: device float[nz][ny][nx] or NULL; range (host): {min J,
  * max J} over the volume. Solves the state for v unless it is the context's current one.
- * Deformation-state contexts only (EINVAL otherwise). Synchronises. */
+ * DEFSTATE and STATE contexts only (EINVAL for IMAGE). Synchronises. */
 int lddmm_jacobian_det(lddmm_ctx* ctx, const float* v, float* J, double* range);
 
 /* Warp m(1) = I0 o phi(1) of the last state solved in the context into m1 (device,
- * float[nz][ny][nx]). DEFSTATE: phi(1) = id - iota(u~(1)); IMAGE: m(nt). */
+ * float[nz][ny][nx]). DEFSTATE, STATE: phi(1) = id - iota(u~(1)); IMAGE: m(nt). */
 int lddmm_get_warped(lddmm_ctx* ctx, float* m1);
 
 /* ----------------------------------------------- stand-alone operators of the hot path */

@@ -26,7 +26,7 @@ LIB_PATH = os.path.join(_HERE, "liblddmm.so")
 HEADER_PATH = os.path.join(os.path.dirname(_HERE), "include", "lddmm.h")
 
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, ELINESEARCH = 0, -1, -2, -3, -4, -5, -6
-V_IMAGE, V_DEFSTATE = 1, 3
+V_IMAGE, V_STATE, V_DEFSTATE = 1, 2, 3
 INTERP_LINEAR, INTERP_CUBIC = 1, 3
 PREC_FP32, PREC_BF16X3, PREC_FP32_SIMT, PREC_BF16X3_JBF16 = 0, 1, 2, 3
 FORWARD, BACKWARD = 1, -1

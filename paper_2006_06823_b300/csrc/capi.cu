@@ -59,11 +59,13 @@ struct lddmm_ctx {
     float *v = nullptr, *vc = nullptr, *d = nullptr, *dc = nullptr;
     float *Df = nullptr, *Db = nullptr, *gam = nullptr, *W = nullptr;
     // trajectories
-    float2* ut = nullptr;   // DEFSTATE: u~_j, (nt+1) x 3 x K^3
-    float* Du = nullptr;    // DEFSTATE: (nt+1) x 9 planes
-    void* Du16 = nullptr;   // DEFSTATE, LDDMM_PREC_BF16X3_JBF16: BF16 copy read by the Hessian
+    float2* ut = nullptr;   // DEFSTATE, STATE: u~_j, (nt+1) x 3 x K^3
+    float* Du = nullptr;    // DEFSTATE, STATE: (nt+1) x 9 planes
+    void* Du16 = nullptr;   // the same, LDDMM_PREC_BF16X3_JBF16: BF16 copy read by the Hessian
     float* ms = nullptr;    // IMAGE: m_j, (nt+1) planes
-    float* Gm = nullptr;    // IMAGE: iota(grad~ pi(m_j)), (nt+1) x 3 planes
+    float* Gm = nullptr;    // IMAGE, STATE: iota(grad~ pi(m_j)), (nt+1) x 3 planes
+    float* Wb = nullptr;    // STATE: source of the nu~ step, -dt/2 (v(X+) + v(x)), 3 planes
+    float* PJ = nullptr;    // STATE: per node iota(nu~_j) (3 planes, physical) and J_j (1 plane)
     float *G = nullptr, *m1 = nullptr;
     // work fields
     float *fa = nullptr, *fb = nullptr, *fc = nullptr, *fd = nullptr, *acc = nullptr,
@@ -80,7 +82,7 @@ struct lddmm_ctx {
     // cache
     bool vel_valid = false;    // velocity fields + state of cv[C_CUR]
     bool traj_valid = false;   // + Jacobians / grad m~ for the Hessian
-    bool warp_valid = false;   // DEFSTATE: m1 and G of the current state
+    bool warp_valid = false;   // DEFSTATE, STATE: m1 and G of the current state
     int solves = 0;
     // CUDA graph of the PCG Hessian-vector product (cv[C_P] -> cv[C_HP])
     bool use_graphs = false;
@@ -125,8 +127,9 @@ static int validate(const lddmm_params* p) {
         return LDDMM_EINVAL;
     }
     if (p->nt < 1 || p->nt > 1000) { set_error("nt must be 1..1000"); return LDDMM_EINVAL; }
-    if (p->variant != LDDMM_V_IMAGE && p->variant != LDDMM_V_DEFSTATE) {
-        set_error("variant must be LDDMM_V_IMAGE or LDDMM_V_DEFSTATE");
+    if (p->variant != LDDMM_V_IMAGE && p->variant != LDDMM_V_STATE &&
+        p->variant != LDDMM_V_DEFSTATE) {
+        set_error("variant must be LDDMM_V_IMAGE, LDDMM_V_STATE or LDDMM_V_DEFSTATE");
         return LDDMM_EINVAL;
     }
     if (p->nonstationary != 0 && p->nonstationary != 1) {
@@ -178,6 +181,9 @@ static const void* jac(const lddmm_ctx* c, int j, bool hess) {
     return c->Du + (long)j * 9 * c->n;
 }
 static bool cubic(const lddmm_ctx* c) { return c->p.interp == LDDMM_INTERP_CUBIC; }
+// the forward state is the displacement u~ (phi = id - iota(u~)): DEFSTATE and STATE
+static bool has_u(const lddmm_ctx* c) { return c->p.variant != LDDMM_V_IMAGE; }
+static bool state_eq(const lddmm_ctx* c) { return c->p.variant == LDDMM_V_STATE; }
 
 // Non-stationary form: nt + 1 velocity nodes and nt distinct steps; the stationary form has
 // one node and one step that serve every time.
@@ -245,8 +251,11 @@ static int prepare_velocity(lddmm_ctx* c, const float2* vt) {
         // gamma = 1 + dt/2 (d_b(X+) + (1 + dt d_b(X+)) d_a(x))
         TRY(sl_prep_adjoint(c->sl, dsrc_b, dnode(c, a), Dbstep(c, j), c->dt, gamstep(c, j), c->st));
         // W = dt/2 (v_a(X) + v_b(x))
-        if (c->p.variant == LDDMM_V_DEFSTATE)
+        if (has_u(c))
             TRY(sl_prep_source(c->sl, vsrc_a, vnode(c, b), Dfstep(c, j), c->dt, Wstep(c, j), c->st));
+        // STATE (stationary): Wb = -dt/2 (v(X+) + v(x)), the source of the nu~ step
+        if (state_eq(c))
+            TRY(sl_prep_source(c->sl, vsrc_b, vnode(c, a), Dbstep(c, j), -c->dt, c->Wb, c->st));
     }
     return LDDMM_OK;
 }
@@ -281,11 +290,11 @@ static int state_image(lddmm_ctx* c) {
     return LDDMM_OK;
 }
 
-// E_data = (1/sigma2) mean (m1 - I1)^2 into dsc[0]; DEFSTATE also forms m1, G and
+// E_data = (1/sigma2) mean (m1 - I1)^2 into dsc[0]; DEFSTATE and STATE also form m1, G and
 // (optionally) rho(1) = -(2/sigma2) r G into `rho`.
 static int data_term(lddmm_ctx* c, float* rho) {
     const long n = c->n;
-    if (c->p.variant == LDDMM_V_DEFSTATE) {
+    if (has_u(c)) {
         TRY(include(c, c->ut + (long)c->p.nt * 3 * c->kc, 3, c->fa, n, -1, 0));
         const float* I0src = cubic(c) ? c->I0c : c->I0;
         TRY(sl_warp_image(c->sl, I0src, c->fa, c->to_vox, c->I1, c->p.sigma2, c->m1, c->G, rho,
@@ -316,9 +325,54 @@ static int ensure_state(lddmm_ctx* c, const float2* vt, bool known_same) {
     c->traj_valid = false;
     c->warp_valid = false;
     TRY(prepare_velocity(c, cur));
-    if (c->p.variant == LDDMM_V_DEFSTATE) TRY(state_defstate(c));
+    if (has_u(c)) TRY(state_defstate(c));
     else TRY(state_image(c));
     c->vel_valid = true;
+    return LDDMM_OK;
+}
+
+// STATE (Sec. 2.3.2): iota(grad~ pi(m_j)) of m_j = I0 o phi_j, phi_j = id - iota(u~_j), and the
+// backward maps of every node: nu~ from -D~_t nu~ = -v~, nu~(1) = 0, stored as iota(nu~_j), and
+// J_j = 1 - iota(U~_j) from -D~_t U~ = -div~ v~ + U~ * div~ v~, U~(1) = 0. J~ = pi(1) - U~ obeys
+// -D~_t J~ = J~ * div~ v~, the adjoint step of Table 1 row 2 (the same SL-Heun arithmetic), so
+// J~ is what is stepped; iota(J~_j) = 1 - iota(U~_j).
+static int state_traj(lddmm_ctx* c) {
+    const long n = c->n, kc3 = 3 * c->kc;
+    const int nt = c->p.nt;
+    float2* mt = c->cv[lddmm_ctx::C_T1];
+    const float* I0src = cubic(c) ? c->I0c : c->I0;
+    for (int j = 0; j <= nt; ++j) {
+        TRY(include(c, c->ut + (long)j * kc3, 3, c->fa, n, -1, 0));
+        TRY(sl_compose(c->sl, I0src, c->fa, c->to_vox, nullptr, c->fb, c->st));
+        TRY(project(c, c->fb, 1, mt));
+        for (int b = 0; b < 3; ++b)
+            TRY(include(c, mt, 1, c->Gm + (long)j * 3 * n + b * n, n, b, 0));
+    }
+    float2* nut = c->cv[lddmm_ctx::C_T1];   // nu~_j
+    float2* Jt = c->cv[lddmm_ctx::C_T2];    // J~_j (first K^3)
+    float* pj = c->PJ + (long)nt * 4 * n;
+    LDDMM_CUDA(cudaMemsetAsync(pj, 0, 3 * n * sizeof(float), c->st));
+    TRY(fill_field(pj + 3 * n, 1.f, n, c->st));
+    LDDMM_CUDA(cudaMemsetAsync(nut, 0, kc3 * sizeof(float2), c->st));
+    TRY(project(c, pj + 3 * n, 1, Jt));
+    for (int j = nt - 1; j >= 0; --j) {
+        const float* src_nu = pj;          // iota(nu~_{j+1}), iota(J~_{j+1})
+        const float* src_J = pj + 3 * n;
+        if (cubic(c)) {
+            TRY(include(c, nut, 3, c->fa, n, -1, 1));
+            TRY(include(c, Jt, 1, c->fd, n, -1, 1));
+            src_nu = c->fa;
+            src_J = c->fd;
+        }
+        TRY(sl_gather_add(c->sl, src_nu, c->Db, c->Wb, 3, c->fb, c->st));
+        TRY(sl_gather_scale(c->sl, src_J, c->Db, c->gam, 1, c->fc, c->st));
+        TRY(project(c, c->fb, 3, nut));
+        TRY(project(c, c->fc, 1, Jt));
+        pj = c->PJ + (long)j * 4 * n;
+        TRY(include(c, nut, 3, pj, n, -1, 0));
+        TRY(include(c, Jt, 1, pj + 3 * n, n, -1, 0));
+    }
+    c->solves++;
     return LDDMM_OK;
 }
 
@@ -326,12 +380,13 @@ static int ensure_state(lddmm_ctx* c, const float2* vt, bool known_same) {
 static int ensure_traj(lddmm_ctx* c) {
     if (c->traj_valid) return LDDMM_OK;
     const long n = c->n;
-    if (c->p.variant == LDDMM_V_DEFSTATE) {
+    if (has_u(c)) {
         for (int j = 0; j <= c->p.nt; ++j)
             for (int b = 0; b < 3; ++b)
                 TRY(include(c, c->ut + (long)j * 3 * c->kc, 3, c->Du + (long)j * 9 * n + b * n,
                             3 * n, b, 0));
         if (jac_bf16(c)) TRY(to_bf16(c->Du, c->Du16, (long)(c->p.nt + 1) * 9 * n, c->st));
+        if (state_eq(c)) TRY(state_traj(c));
     } else {
         float2* mt = c->cv[lddmm_ctx::C_T1];
         for (int j = 0; j <= c->p.nt; ++j) {
@@ -410,6 +465,33 @@ static int adjoint_defstate_ns(lddmm_ctx* c, const float* rho1, const float2* ba
     return LDDMM_OK;
 }
 
+// STATE, gradient and Hessian (Eqs. 15-16 with lambda(t) = J(t) lambda(1) o psi(t)):
+// out = L~ base + sum_j w_j pi(iota(pi(f_j)) Gm_j), f_j = J_j f1 o psi_j, with f1 = lambda(1) for the
+// gradient and dlambda(1) for the Gauss-Newton Hessian. No recurrence: every node reads f1.
+static int pullback_assemble(lddmm_ctx* c, const float* f1, const float2* base, float2* out) {
+    const long n = c->n;
+    const int nt = c->p.nt;
+    const float* src = f1;
+    if (cubic(c)) {
+        TRY(bspline_prefilter(c->g, f1, 1, c->fa, c->st));
+        src = c->fa;
+    }
+    float2* lt = c->cv[lddmm_ctx::C_T1];
+    for (int j = nt; j >= 0; --j) {
+        const float* pj = c->PJ + (long)j * 4 * n;
+        TRY(sl_compose(c->sl, src, pj, c->to_vox, pj + 3 * n, c->fd, c->st));
+        TRY(project(c, c->fd, 1, lt));
+        TRY(include(c, lt, 1, c->fc, n, -1, 0));
+        TRY(accum_sv(c->g, c->fc, c->Gm + (long)j * 3 * n, (float)trap_w(c, j), c->acc, j == nt,
+                     c->st));
+    }
+    c->solves++;
+    float2* pacc = c->cv[lddmm_ctx::C_T0];
+    TRY(project(c, c->acc, 3, pacc));
+    TRY(cube_apply_L(out, base, 1.f, 1.f, pacc, c->K, 3, c->p.alpha, c->p.s, 1, c->st));
+    return LDDMM_OK;
+}
+
 // IMAGE, gradient (Eqs. 15, 18; Table 1 row 2): spatial adjoint lambda from
 // lambda(1) = -(2/sigma2)(m1 - I1); g = L~ v~ + sum_j w_j pi(iota(pi(lambda_j)) Gm_j).
 static int gradient_image_adjoint(lddmm_ctx* c, const float2* vt, float2* g) {
@@ -459,7 +541,11 @@ static int gradient_impl(lddmm_ctx* c, const float2* vt, bool known_same, float2
     TRY(ensure_state(c, vt, known_same));
     TRY(ensure_traj(c));
     float2* cur = c->cv[lddmm_ctx::C_CUR];
-    if (c->p.variant == LDDMM_V_DEFSTATE) {
+    if (state_eq(c)) {
+        TRY(data_term(c, nullptr));
+        TRY(scaled_diff(c->g, c->m1, c->I1, (float)(-2.0 / c->p.sigma2), c->fb, c->st));
+        TRY(pullback_assemble(c, c->fb, cur, g));
+    } else if (c->p.variant == LDDMM_V_DEFSTATE) {
         TRY(data_term(c, c->fb));
         if (ns(c)) TRY(adjoint_defstate_ns(c, c->fb, cur, g, false));
         else TRY(adjoint_defstate(c, c->fb, cur, g, false));
@@ -479,11 +565,11 @@ static int gradient_impl(lddmm_ctx* c, const float2* vt, bool known_same, float2
 // Gauss-Newton H dv~ at the current velocity (state and trajectory must be current).
 static int hessian_impl(lddmm_ctx* c, const float2* dvt, float2* out) {
     TRY(ensure_traj(c));
-    if (c->p.variant == LDDMM_V_DEFSTATE && !c->warp_valid) TRY(data_term(c, nullptr));
+    if (has_u(c) && !c->warp_valid) TRY(data_term(c, nullptr));
     const long n = c->n, kc3 = 3 * c->kc;
     const int nt = c->p.nt;
     TRY(include(c, dvt, 3, c->dvsp, n, -1, 0));
-    if (c->p.variant == LDDMM_V_DEFSTATE) {
+    if (has_u(c)) {
         // incremental state D~_t du~ = dv~ - D~u~ * dv~ (Eq. 36; Table 1 row 7)
         float2* dut = c->cv[lddmm_ctx::C_T1];
         float* Fold = c->fa;
@@ -505,8 +591,14 @@ static int hessian_impl(lddmm_ctx* c, const float2* dvt, float2* out) {
             std::swap(Fold, Fnew);
         }
         c->solves++;
-        // drho(1) = pi(-(2/sigma2) dm1 G), dm1 = -G . iota(du~(1))
         TRY(include(c, dut, 3, c->fa, n, -1, 0));
+        if (state_eq(c)) {
+            // Gauss-Newton: dlambda(t) = J(t) dlambda(1) o psi(t), dlambda(1) = -(2/sigma2) dm1,
+            // dm1 = -G . iota(du~(1))
+            TRY(state_dlam1(c->g, c->G, c->fa, c->p.sigma2, c->fb, c->st));
+            return pullback_assemble(c, c->fb, dvt, out);
+        }
+        // drho(1) = pi(-(2/sigma2) dm1 G), dm1 = -G . iota(du~(1))
         TRY(defstate_drho1(c->g, c->G, c->fa, c->p.sigma2, c->fb, c->st));
         if (ns(c)) return adjoint_defstate_ns(c, c->fb, dvt, out, true);
         return adjoint_defstate(c, c->fb, dvt, out, true);
@@ -590,7 +682,7 @@ static int hessian_pcg(lddmm_ctx* c) {
     float2* pp = c->cv[lddmm_ctx::C_P];
     float2* Hp = c->cv[lddmm_ctx::C_HP];
     TRY(ensure_traj(c));
-    if (c->p.variant == LDDMM_V_DEFSTATE && !c->warp_valid) TRY(data_term(c, nullptr));
+    if (has_u(c) && !c->warp_valid) TRY(data_term(c, nullptr));
     if (!c->use_graphs || c->graph_failed || tracing()) return hessian_impl(c, pp, Hp);
     if (c->hv_exec) {
         LDDMM_CUDA(cudaGraphLaunch(c->hv_exec, c->st));
@@ -752,7 +844,7 @@ static int register_impl(lddmm_ctx* c, float2* v_io, const double* gref_in, lddm
     // if the line search failed, the state in the buffers belongs to a rejected trial
     if (stop == LDDMM_STOP_LINESEARCH) TRY(objective_impl(c, v, false, &E, &Er, &Ed));
     // MSE_rel = ||m1 - I1||^2 / ||I0 - I1||^2
-    const float* m1 = c->p.variant == LDDMM_V_DEFSTATE ? c->m1 : c->ms + (long)c->p.nt * c->n;
+    const float* m1 = has_u(c) ? c->m1 : c->ms + (long)c->p.nt * c->n;
     TRY(sum_sq_diff(m1, c->I1, c->n, c->partials, c->dsc, c->st));
     TRY(sum_sq_diff(c->I0, c->I1, c->n, c->partials, c->dsc + 1, c->st));
     TRY(max_abs_f2(g, kc3, c->partials, c->dsc + 2, c->st));
@@ -776,7 +868,7 @@ static int register_impl(lddmm_ctx* c, float2* v_io, const double* gref_in, lddm
 static int ctx_alloc(lddmm_ctx* c) {
     const long n = c->n, kc3 = 3 * c->kc;
     const int nt = c->p.nt;
-    const bool def = c->p.variant == LDDMM_V_DEFSTATE, cub = cubic(c);
+    const bool def = has_u(c), cub = cubic(c);
     float* twm = nullptr;
     TRY(dalloc_t(c, &twm, twiddle_floats(c->g, c->K)));
     TRY(twiddle_init(c->g, c->K, twm, c->tw, c->st));
@@ -802,7 +894,11 @@ static int ctx_alloc(lddmm_ctx* c) {
         TRY(dalloc_t(c, &c->m1, n));
     } else {
         TRY(dalloc_t(c, &c->ms, (size_t)(nt + 1) * n));
-        TRY(dalloc_t(c, &c->Gm, (size_t)(nt + 1) * 3 * n));
+    }
+    if (!def || state_eq(c)) TRY(dalloc_t(c, &c->Gm, (size_t)(nt + 1) * 3 * n));
+    if (state_eq(c)) {
+        TRY(dalloc_t(c, &c->Wb, 3 * n));
+        TRY(dalloc_t(c, &c->PJ, (size_t)(nt + 1) * 4 * n));
     }
     for (float** f : {&c->fa, &c->fb, &c->fc, &c->fd, &c->acc, &c->dvsp}) TRY(dalloc_t(c, f, 3 * n));
     long se = spectral_scratch_elems(c->g, c->K, 3);
@@ -939,8 +1035,8 @@ int lddmm_register(lddmm_ctx* c, float* v_inout, const double* g_ref_norms, lddm
 int lddmm_jacobian_det(lddmm_ctx* c, const float* v, float* J, double* range) {
     if (!v || !range) { set_error("jacobian_det: v or range is NULL"); return LDDMM_EINVAL; }
     CTX_CALL(c, ([&]() -> int {
-        if (c->p.variant != LDDMM_V_DEFSTATE) {
-            set_error("jacobian_det: deformation-state contexts only");
+        if (!has_u(c)) {
+            set_error("jacobian_det: deformation-state or state-equation contexts only");
             return LDDMM_EINVAL;
         }
         const float2* vt = reinterpret_cast<const float2*>(v);
@@ -965,8 +1061,8 @@ int lddmm_get_warped(lddmm_ctx* c, float* m1) {
     if (!m1) { set_error("m1 is NULL"); return LDDMM_EINVAL; }
     CTX_CALL(c, ([&]() -> int {
         if (!c->vel_valid) { set_error("no state solved yet"); return LDDMM_EINVAL; }
-        if (c->p.variant == LDDMM_V_DEFSTATE) TRY(data_term(c, nullptr));
-        const float* src = c->p.variant == LDDMM_V_DEFSTATE ? c->m1 : c->ms + (long)c->p.nt * c->n;
+        if (has_u(c)) TRY(data_term(c, nullptr));
+        const float* src = has_u(c) ? c->m1 : c->ms + (long)c->p.nt * c->n;
         LDDMM_CUDA(cudaMemcpyAsync(m1, src, c->n * sizeof(float), cudaMemcpyDeviceToDevice, c->st));
         return LDDMM_OK;
     })());
@@ -1228,7 +1324,7 @@ int lddmm_autotune(lddmm_ctx* c, const char* cache_path, int* block_x_out) {
         for (int rep = 0; rep < 4; ++rep) {
             LDDMM_CUDA(cudaEventRecord(e0, c->st));
             rc = sl_gather_scale(a, c->fa, c->Df, c->gam, 3, c->fb, c->st);
-            if (rc == LDDMM_OK && c->p.variant == LDDMM_V_DEFSTATE && c->Du)
+            if (rc == LDDMM_OK && has_u(c) && c->Du)
                 rc = sl_inc_defstate(a, c->fa, c->Df, c->fb, jac(c, 0, true), jac_bf16(c), c->dvsp, c->dt,
                                      c->fc, c->fd, c->st);
             LDDMM_CUDA(cudaEventRecord(e1, c->st));

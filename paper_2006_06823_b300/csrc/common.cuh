@@ -155,6 +155,12 @@ int sl_inc_defstate(const SLArgs& a, const float* U, const float* D, const float
 // Fnew_a = dv_a - sum_b Du[a*3+b] dv_b (the first node)
 int defstate_rhs(const Grid& g, const void* Du, bool du_bf16, const float* dv, float* F,
                  cudaStream_t st);
+// out = mul * src o (x - U to_vox) (mul may be null; U: 3 physical planes)
+int sl_compose(const SLArgs& a, const float* src, const float* U, const float to_vox[3],
+               const float* mul, float* out, cudaStream_t st);
+// dlambda(1) = -(2/sigma2) dm1 with dm1 = -G . du1
+int state_dlam1(const Grid& g, const float* G, const float* du1, double sigma2, float* out,
+                cudaStream_t st);
 // drho = -(2/sigma2) dm1 G with dm1 = -G . du1
 int defstate_drho1(const Grid& g, const float* G, const float* du1, double sigma2, float* drho,
                    cudaStream_t st);
@@ -165,6 +171,8 @@ int accum_JT(const Grid& g, const void* Du, bool du_bf16, const float* R, float 
 int jacobian_det(const Grid& g, const float* Du, float* J, double* pmin, double* pmax, cudaStream_t st);
 // out[i] = bf16(in[i]), i < n (round to nearest even)
 int to_bf16(const float* in, void* out, long n, cudaStream_t st);
+// out[i] = v, i < n
+int fill_field(float* out, float v, long n, cudaStream_t st);
 // x_out = a * x (n floats)
 int scale_field(float* out, const float* in, float a, long n, cudaStream_t st);
 // partial sums over (a - b)^2 into kReduceBlocks doubles, then final into out

@@ -491,6 +491,47 @@ int sl_warp_image(const SLArgs& a, const float* I0src, const float* u1, const fl
     return LDDMM_OK;
 }
 
+// ---------------------------------------------------------------- compositions (state-eq. variant)
+// out = mul(x) * src o (x - U(x) to_vox): m_j = I0 o phi_j and lambda_j = J_j lambda(1) o psi_j
+// with phi_j = id - iota(u~_j), psi_j = id - iota(nu~_j) (U physical, mul may be null).
+template <int IP>
+__global__ void __launch_bounds__(256, IP == 3 ? 2 : 4)
+k_compose(Grid g, const float* __restrict__ src, const float* __restrict__ U, float t0, float t1,
+          float t2, const float* __restrict__ mul, float* __restrict__ out) {
+    VOXEL_PROLOGUE
+    Interp<IP> it(g, x, y, z, -U[i] * t0, -U[n + i] * t1, -U[2 * n + i] * t2);
+    const float f = it(src);
+    out[i] = mul ? mul[i] * f : f;
+}
+
+int sl_compose(const SLArgs& a, const float* src, const float* U, const float to_vox[3],
+               const float* mul, float* out, cudaStream_t st) {
+    KTRACE("sl_compose", st, a.g.ntot() * (20.0 + (mul ? 4.0 : 0.0)), 0);
+    if (a.interp == 3)
+        k_compose<3><<<VOX_LAUNCH(a), 0, st>>>(a.g, src, U, to_vox[0], to_vox[1], to_vox[2], mul, out);
+    else
+        k_compose<1><<<VOX_LAUNCH(a), 0, st>>>(a.g, src, U, to_vox[0], to_vox[1], to_vox[2], mul, out);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+// dlambda(1) = -(2/sigma2) dm1 with dm1 = -G . du1
+__global__ void k_state_dlam1(long n, const float* __restrict__ G, const float* __restrict__ du,
+                              float coef, float* __restrict__ out) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    out[i] = coef * (G[i] * du[i] + G[n + i] * du[n + i] + G[2 * n + i] * du[2 * n + i]);
+}
+
+int state_dlam1(const Grid& g, const float* G, const float* du1, double sigma2, float* out,
+                cudaStream_t st) {
+    long n = g.ntot();
+    KTRACE("state_dlam1", st, 28.0 * n, 6.0 * n);
+    k_state_dlam1<<<cdiv(n, 256), 256, 0, st>>>(n, G, du1, (float)(2.0 / sigma2), out);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
 // ---------------------------------------------------------------- incremental state
 __device__ __forceinline__ float ldj(const float* p) { return *p; }
 __device__ __forceinline__ float ldj(const __nv_bfloat16* p) { return __bfloat162float(*p); }
@@ -669,6 +710,18 @@ int jacobian_det(const Grid& g, const float* Du, float* J, double* pmin, double*
     const long n = g.ntot();
     KTRACE("jacobian_det", st, n * (36.0 + (J ? 4.0 : 0.0)), n * 40.0);
     k_jacdet<<<kReduceBlocks, 256, 0, st>>>(n, Du, J, pmin, pmax);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+__global__ void k_fill_field(float* out, float v, long n) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = v;
+}
+
+int fill_field(float* out, float v, long n, cudaStream_t st) {
+    KTRACE("fill_field", st, 4.0 * n, 0);
+    k_fill_field<<<cdiv(n, 256), 256, 0, st>>>(out, v, n);
     LDDMM_CHECK_LAUNCH();
     return LDDMM_OK;
 }

@@ -22,7 +22,7 @@ def test_version_and_empty_error():
 
 
 @pytest.mark.parametrize("field,value", [("K", 7), ("K", 2), ("K", 40), ("nt", 0),
-                                         ("variant", 2), ("interp", 2), ("sigma2", 0.0),
+                                         ("variant", 4), ("interp", 2), ("sigma2", 0.0),
                                          ("nx", 3), ("precision", 5), ("max_pcg", 0)])
 def test_create_rejects_bad_parameters_before_any_device_work(field, value):
     lib = L.load()
@@ -89,7 +89,7 @@ def test_net_calls_reject_null_network():
 
 def test_nonstationary_flag_is_validated_before_any_device_work():
     lib = L.load()
-    for variant, flag in ((L.V_IMAGE, 1), (L.V_DEFSTATE, 2)):
+    for variant, flag in ((L.V_IMAGE, 1), (L.V_STATE, 1), (L.V_DEFSTATE, 2)):
         p = L.Params(32, 32, 32, 16, 10, variant, L.INTERP_LINEAR, 0.0025, 2, 0.01, 5, 10,
                      1e-3, L.PREC_FP32, flag)
         h = ctypes.c_void_p(123)
