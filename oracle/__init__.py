@@ -11,6 +11,8 @@ Modules
   interp    trilinear and periodic cubic B-spline interpolation (Sec. 3.1, Sec. 4.2)
   sl        SL characteristics and the Table 1 transport equations, Heun (SL-RK) steps (Sec. 3)
   variants  energy, gradient and Gauss-Newton Hessian-vector products (Sec. 2.3.1-2.3.3)
+  spatial   the three variants in the spatial domain (Sec. 2.1, SL-RK in Omega): velocity on
+            the grid, spectral derivatives and L by numpy's FFT, voxel-mean L2 product
   gnk       PCG with preconditioner L~^-1, Gauss-Newton update, line search (Sec. 2.1-2.2)
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test against a closed

@@ -81,7 +81,7 @@ def register(problem, v0=None, max_gn=5, max_pcg=10, gtol=1e-3, g_ref=None):
     # the problem may define its own unknown (a stack of cubes), product and preconditioner
     inner = getattr(problem, "inner", S.inner)
     if hasattr(problem, "zeros"):
-        v = problem.zeros() if v0 is None else np.array(v0, np.complex128)
+        v = problem.zeros() if v0 is None else np.array(v0, problem.zeros().dtype)
         prec = problem.precond
     else:
         v = np.zeros((3, K, K, K), dtype=np.complex128) if v0 is None else np.array(v0, np.complex128)
