@@ -331,24 +331,27 @@ def run_b300(args):
     return out
 
 
-FORMS = [("defstate/linear/bf16x3_jbf16", "V_DEFSTATE", "INTERP_LINEAR", "PREC_BF16X3_JBF16", False),
-         ("image/linear/fp32", "V_IMAGE", "INTERP_LINEAR", "PREC_FP32", False),
-         ("defstate/cubic/fp32", "V_DEFSTATE", "INTERP_CUBIC", "PREC_FP32", False),
-         ("image/cubic/fp32", "V_IMAGE", "INTERP_CUBIC", "PREC_FP32", False),
-         ("defstate/linear/fp32/nonstationary", "V_DEFSTATE", "INTERP_LINEAR", "PREC_FP32", True),
-         ("state/linear/fp32", "V_STATE", "INTERP_LINEAR", "PREC_FP32", False)]
+# name, variant, interpolation, precision, non-stationary, spatial domain
+FORMS = [("defstate/linear/bf16x3_jbf16", "V_DEFSTATE", "INTERP_LINEAR", "PREC_BF16X3_JBF16", False, False),
+         ("image/linear/fp32", "V_IMAGE", "INTERP_LINEAR", "PREC_FP32", False, False),
+         ("defstate/cubic/fp32", "V_DEFSTATE", "INTERP_CUBIC", "PREC_FP32", False, False),
+         ("image/cubic/fp32", "V_IMAGE", "INTERP_CUBIC", "PREC_FP32", False, False),
+         ("defstate/linear/fp32/nonstationary", "V_DEFSTATE", "INTERP_LINEAR", "PREC_FP32", True, False),
+         ("state/linear/fp32", "V_STATE", "INTERP_LINEAR", "PREC_FP32", False, False),
+         ("defstate/linear/fp32/spatial", "V_DEFSTATE", "INTERP_LINEAR", "PREC_FP32", False, True),
+         ("image/linear/fp32/spatial", "V_IMAGE", "INTERP_LINEAR", "PREC_FP32", False, True)]
 
 
 def measure_forms(L, torch, I0d, I1d, stream, flush):
     """The bench pair in the other forms of the workload (variant x interpolation, the
-    mixed-precision form, the non-stationary velocity): one untimed and one event-timed
-    registration each."""
+    mixed-precision form, the non-stationary velocity, the spatial domain): one untimed and
+    one event-timed registration each."""
     nz, ny, nx = SHAPE
     res = {}
-    for name, var, interp, prec, nonst in FORMS:
+    for name, var, interp, prec, nonst, spatial in FORMS:
         ctx = L.Context(nx, ny, nz, K, nt=NT, variant=getattr(L, var), interp=getattr(L, interp),
                         alpha=ALPHA, s=S_EXP, sigma2=SIGMA2, max_gn=MAX_GN, max_pcg=MAX_PCG,
-                        gtol=GTOL, precision=getattr(L, prec), nonstationary=nonst)
+                        gtol=GTOL, precision=getattr(L, prec), nonstationary=nonst, spatial=spatial)
         ctx.set_images(I0d, I1d)
         ctx.register()
         flush.fill_(1.0)

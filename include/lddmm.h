@@ -85,6 +85,13 @@ typedef struct {
                           norms and inner products of such stacks weight node j by the
                           trapezoid weight w_j (R11), and the gradient / Hessian at node j is
                           the integrand of Eq. 32 / 33 at t_j. */
+    int spatial;       /* 0: band-limited (the default; Sec. 2.2-2.3). 1: spatial domain (Sec. 2.1
+                          with SL-RK in Omega, the paper's "PDE-LDDMM ... SL" methods): every
+                          velocity argument is a field float[3][nz][ny][nx] (physical
+                          units); K is ignored, pi and iota are the identity, and L, L^{-1}
+                          and the derivatives grad m,
+                          D u, div v are spectral on the full grid (cuFFT). Inner products and
+                          E_reg use the voxel mean. nx must be even; stationary only. */
 } lddmm_params;
 
 /* Outcome of lddmm_register. */

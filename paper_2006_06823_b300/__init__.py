@@ -41,7 +41,8 @@ class Params(ctypes.Structure):
                 ("interp", ctypes.c_int), ("alpha", ctypes.c_double), ("s", ctypes.c_int),
                 ("sigma2", ctypes.c_double), ("max_gn", ctypes.c_int),
                 ("max_pcg", ctypes.c_int), ("gtol", ctypes.c_double),
-                ("precision", ctypes.c_int), ("nonstationary", ctypes.c_int)]
+                ("precision", ctypes.c_int), ("nonstationary", ctypes.c_int),
+                ("spatial", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -239,13 +240,17 @@ class Context:
 
     def __init__(self, nx, ny, nz, K, nt=10, variant=V_DEFSTATE, interp=INTERP_LINEAR,
                  alpha=0.0025, s=2, sigma2=0.01, max_gn=10, max_pcg=20, gtol=1e-3,
-                 precision=PREC_FP32, nonstationary=False):
+                 precision=PREC_FP32, nonstationary=False, spatial=False):
         self.params = Params(nx, ny, nz, K, nt, variant, interp, alpha, s, sigma2, max_gn,
-                             max_pcg, gtol, precision, 1 if nonstationary else 0)
+                             max_pcg, gtol, precision, 1 if nonstationary else 0,
+                             1 if spatial else 0)
         self.shape = (nz, ny, nx)
         self.K = K
         self.nt = nt
         self.nonstationary = bool(nonstationary)
+        self.spatial = bool(spatial)
+        # velocity-shaped arguments: complex64 cubes, or float32 fields in the spatial form
+        self._vec = _f32 if spatial else _c64
         self._h = ctypes.c_void_p()
         _check(load().lddmm_create(ctypes.byref(self.params), _stream(), ctypes.byref(self._h)))
 
@@ -267,9 +272,12 @@ class Context:
         self.close()
 
     def zeros_cube(self):
-        """A zero velocity: [3, K, K, K], or [nt + 1, 3, K, K, K] for a non-stationary context."""
+        """A zero velocity: [3, K, K, K] complex64 ([3, nz, ny, nx] float32 in the spatial
+        form), with a leading nt + 1 for a non-stationary context."""
         import torch
         lead = (self.nt + 1, 3) if self.nonstationary else (3,)
+        if self.spatial:
+            return torch.zeros(lead + self.shape, dtype=torch.float32, device="cuda")
         return torch.zeros(lead + (self.K, self.K, self.K), dtype=torch.complex64, device="cuda")
 
     def set_images(self, I0, I1):
@@ -284,7 +292,7 @@ class Context:
 
     def objective(self, v):
         E, Er, Ed = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
-        _check(load().lddmm_objective(self._h, _c64(v), ctypes.byref(E), ctypes.byref(Er),
+        _check(load().lddmm_objective(self._h, self._vec(v), ctypes.byref(E), ctypes.byref(Er),
                                       ctypes.byref(Ed)))
         return E.value, Er.value, Ed.value
 
@@ -292,14 +300,14 @@ class Context:
         import torch
         g = torch.empty_like(v) if out is None else out
         E, Er, Ed = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
-        _check(load().lddmm_gradient(self._h, _c64(v), _c64(g), ctypes.byref(E),
+        _check(load().lddmm_gradient(self._h, self._vec(v), self._vec(g), ctypes.byref(E),
                                      ctypes.byref(Er), ctypes.byref(Ed)))
         return (E.value, Er.value, Ed.value), g
 
     def hessian_matvec(self, v, dv, out=None):
         import torch
         h = torch.empty_like(dv) if out is None else out
-        _check(load().lddmm_hessian_matvec(self._h, _c64(v), _c64(dv), _c64(h)))
+        _check(load().lddmm_hessian_matvec(self._h, self._vec(v), self._vec(dv), self._vec(h)))
         return h
 
     def register(self, v=None, g_ref_norms=None):
@@ -309,7 +317,7 @@ class Context:
         ref = None
         if g_ref_norms is not None:
             ref = (ctypes.c_double * 2)(*g_ref_norms)
-        _check(load().lddmm_register(self._h, _c64(v), ref, ctypes.byref(rep)))
+        _check(load().lddmm_register(self._h, self._vec(v), ref, ctypes.byref(rep)))
         return v, rep.as_dict()
 
     def set_option(self, option, value):
@@ -330,7 +338,7 @@ class Context:
         if field:
             J = torch.empty(self.shape, dtype=torch.float32, device="cuda") if out is None else out
         rng = (ctypes.c_double * 2)()
-        _check(load().lddmm_jacobian_det(self._h, _c64(v), _f32(J) if J is not None else None, rng))
+        _check(load().lddmm_jacobian_det(self._h, self._vec(v), _f32(J) if J is not None else None, rng))
         return (rng[0], rng[1]), J
 
     def get_warped(self, out=None):
@@ -455,7 +463,7 @@ def register_batch(contexts, velocities, g_ref_norms=None, max_threads=8):
     [3, K, K, K] device cubes updated in place. Returns the list of report dicts."""
     n = len(contexts)
     hs = (_P * n)(*[c._h for c in contexts])
-    vs = (_P * n)(*[ctypes.c_void_p(_c64(v).value) for v in velocities])
+    vs = (_P * n)(*[ctypes.c_void_p(c._vec(v).value) for c, v in zip(contexts, velocities)])
     reps = (Report * n)()
     ref = None
     if g_ref_norms is not None:

@@ -66,6 +66,8 @@ struct lddmm_ctx {
     float* Gm = nullptr;    // IMAGE, STATE: iota(grad~ pi(m_j)), (nt+1) x 3 planes
     float* Wb = nullptr;    // STATE: source of the nu~ step, -dt/2 (v(X+) + v(x)), 3 planes
     float* PJ = nullptr;    // STATE: per node iota(nu~_j) (3 planes, physical) and J_j (1 plane)
+    // spatial form: full-grid FFT plans (the "cubes" of this context are fields on the grid)
+    SpatialFFT* fft = nullptr;
     float *G = nullptr, *m1 = nullptr;
     // work fields
     float *fa = nullptr, *fb = nullptr, *fc = nullptr, *fd = nullptr, *acc = nullptr,
@@ -122,7 +124,20 @@ static int validate(const lddmm_params* p) {
         set_error("grid too large: nx*ny*nz must stay below 2^31/3 voxels");
         return LDDMM_EINVAL;
     }
-    if (p->K < 4 || (p->K & 1) || p->K > 64 || p->K > p->nx || p->K > p->ny || p->K > p->nz) {
+    if (p->spatial != 0 && p->spatial != 1) {
+        set_error("spatial must be 0 or 1");
+        return LDDMM_EINVAL;
+    }
+    if (p->spatial && (p->nx & 1)) {
+        set_error("the spatial form needs an even nx");
+        return LDDMM_EINVAL;
+    }
+    if (p->spatial && p->nonstationary) {
+        set_error("the non-stationary form is implemented for band-limited velocities");
+        return LDDMM_EINVAL;
+    }
+    if (!p->spatial &&
+        (p->K < 4 || (p->K & 1) || p->K > 64 || p->K > p->nx || p->K > p->ny || p->K > p->nz)) {
         set_error("band K must be even, 4 <= K <= min(64, nx, ny, nz)");
         return LDDMM_EINVAL;
     }
@@ -167,14 +182,65 @@ static int spec_prec(const lddmm_ctx* c) {
     return c->p.precision == LDDMM_PREC_BF16X3_JBF16 ? LDDMM_PREC_BF16X3 : c->p.precision;
 }
 static bool jac_bf16(const lddmm_ctx* c) { return c->p.precision == LDDMM_PREC_BF16X3_JBF16; }
+// Spatial form (Sec. 2.1 with SL in Omega): velocity-shaped vectors are fields on the grid,
+// pi and iota are the identity, derivatives and L go through full-grid FFTs.
+static bool spatial(const lddmm_ctx* c) { return c->p.spatial != 0; }
+// factor of the device dot products: l2 over cube coefficients (band-limited) or the voxel
+// mean (spatial)
+static double dscale(const lddmm_ctx* c) { return spatial(c) ? 1.0 / (double)c->n : 1.0; }
+
 static int project(lddmm_ctx* c, const float* f, int ncomp, float2* out) {
+    if (spatial(c)) {
+        if (reinterpret_cast<const void*>(f) != out)
+            LDDMM_CUDA(cudaMemcpyAsync(out, f, (size_t)ncomp * c->n * sizeof(float),
+                                       cudaMemcpyDeviceToDevice, c->st));
+        return LDDMM_OK;
+    }
     return bl_project(c->g, c->tw, f, c->n, ncomp, out, c->s1, c->s2, spec_prec(c), c->st);
 }
 static int include(lddmm_ctx* c, const float2* cube, int ncomp, float* f, long fstride,
                    int deriv, int bspline) {
+    if (spatial(c)) {
+        const float* src = reinterpret_cast<const float*>(cube);
+        const long n = c->n;
+        if (deriv < 0 && bspline) {
+            if (fstride != n) { set_error("internal: strided spline coefficients"); return LDDMM_EINVAL; }
+            return bspline_prefilter(c->g, src, ncomp, f, c->st);
+        }
+        if (deriv < 0) {
+            for (int k = 0; k < ncomp; ++k)
+                if (src + k * n != f + k * fstride)
+                    LDDMM_CUDA(cudaMemcpyAsync(f + k * fstride, src + k * n, n * sizeof(float),
+                                               cudaMemcpyDeviceToDevice, c->st));
+            return LDDMM_OK;
+        }
+        if (deriv == 3) {
+            TRY(spatial_deriv(c->fft, src, 3, 3, f, fstride, c->st));
+            return bspline ? bspline_prefilter(c->g, f, 1, f, c->st) : LDDMM_OK;
+        }
+        if (bspline) { set_error("internal: spline coefficients of a derivative"); return LDDMM_EINVAL; }
+        return spatial_deriv(c->fft, src, ncomp, deriv, f, fstride, c->st);
+    }
     return bl_include(c->g, c->tw, cube, ncomp, f, fstride, deriv, bspline, c->s1, c->s2,
                       spec_prec(c), c->st);
 }
+// out = wL L~ x + a y (mode 1) or L~^{-1} x (mode -1) over ncube cubes (fields when spatial)
+static int op_L(lddmm_ctx* c, float2* out, const float2* x, float wL, float a, const float2* y,
+                int ncube, int mode) {
+    if (spatial(c))
+        return spatial_apply_L(c->fft, reinterpret_cast<float*>(out), reinterpret_cast<const float*>(x),
+                               wL, a, reinterpret_cast<const float*>(y), ncube, c->p.alpha, c->p.s, mode,
+                               c->st);
+    return cube_apply_L(out, x, wL, a, y, c->K, ncube, c->p.alpha, c->p.s, mode, c->st);
+}
+// max |.| of a velocity-shaped vector of nf2 float2 (complex modulus per coefficient; per value
+// when spatial)
+static int max_abs(lddmm_ctx* c, const float2* v, long nf2, double* out) {
+    if (spatial(c))
+        return max_abs_f32(reinterpret_cast<const float*>(v), 2 * nf2, c->partials, out, c->st);
+    return max_abs_f2(v, nf2, c->partials, out, c->st);
+}
+
 // the Jacobian planes of node j, as the Hessian (hess) or the gradient reads them
 static const void* jac(const lddmm_ctx* c, int j, bool hess) {
     if (hess && jac_bf16(c)) return static_cast<const uint16_t*>(c->Du16) + (long)j * 9 * c->n;
@@ -310,7 +376,7 @@ static int data_term(lddmm_ctx* c, float* rho) {
 // E_reg = 1/2 <L~ v~, v~> into dsc[1] (non-stationary: sum_j w_j <L~ v~_j, v~_j>)
 static int reg_term(lddmm_ctx* c, const float2* vt) {
     float2* t = c->cv[lddmm_ctx::C_T0];
-    TRY(cube_apply_L(t, vt, 1.f, 0.f, nullptr, c->K, 3 * nodes(c), c->p.alpha, c->p.s, 1, c->st));
+    TRY(op_L(c, t, vt, 1.f, 0.f, nullptr, 3 * nodes(c), 1));
     TRY(dot_f2_nodes(t, vt, 3 * c->kc, nodes(c), c->dt, c->partials, c->dsc + 1, c->st));
     return LDDMM_OK;
 }
@@ -430,7 +496,7 @@ static int adjoint_defstate(lddmm_ctx* c, const float* rho1, const float2* base,
     float2* pacc = c->cv[lddmm_ctx::C_T0];
     TRY(project(c, c->acc, 3, pacc));
     TRY(cube_axpby(rsum, 1.f, rsum, -1.f, pacc, kc3, c->st));
-    TRY(cube_apply_L(out, base, 1.f, 1.f, rsum, c->K, 3, c->p.alpha, c->p.s, 1, c->st));
+    TRY(op_L(c, out, base, 1.f, 1.f, rsum, 3, 1));
     return LDDMM_OK;
 }
 
@@ -458,8 +524,7 @@ static int adjoint_defstate_ns(lddmm_ctx* c, const float* rho1, const float2* ba
         TRY(accum_JT(c->g, jac(c, j, hess), jac_bf16(c) && hess, c->fc, 1.f, c->acc, 1, c->st));
         TRY(project(c, c->acc, 3, pj));
         TRY(cube_axpby(pj, 1.f, rt, -1.f, pj, kc3, c->st));
-        TRY(cube_apply_L(vcube(c, out, j), vcube(c, base, j), 1.f, 1.f, pj, c->K, 3, c->p.alpha,
-                         c->p.s, 1, c->st));
+        TRY(op_L(c, vcube(c, out, j), vcube(c, base, j), 1.f, 1.f, pj, 3, 1));
     }
     c->solves++;
     return LDDMM_OK;
@@ -488,7 +553,7 @@ static int pullback_assemble(lddmm_ctx* c, const float* f1, const float2* base, 
     c->solves++;
     float2* pacc = c->cv[lddmm_ctx::C_T0];
     TRY(project(c, c->acc, 3, pacc));
-    TRY(cube_apply_L(out, base, 1.f, 1.f, pacc, c->K, 3, c->p.alpha, c->p.s, 1, c->st));
+    TRY(op_L(c, out, base, 1.f, 1.f, pacc, 3, 1));
     return LDDMM_OK;
 }
 
@@ -518,7 +583,7 @@ static int gradient_image_adjoint(lddmm_ctx* c, const float2* vt, float2* g) {
     c->solves++;
     float2* pacc = c->cv[lddmm_ctx::C_T0];
     TRY(project(c, c->acc, 3, pacc));
-    TRY(cube_apply_L(g, vt, 1.f, 1.f, pacc, c->K, 3, c->p.alpha, c->p.s, 1, c->st));
+    TRY(op_L(c, g, vt, 1.f, 1.f, pacc, 3, 1));
     return LDDMM_OK;
 }
 
@@ -529,7 +594,7 @@ static int objective_impl(lddmm_ctx* c, const float2* vt, bool known_same, doubl
     TRY(data_term(c, nullptr));
     TRY(reg_term(c, vt));
     TRY(read_scalars(c, 2));
-    double ed = c->hsc[0] / (double)c->n / c->p.sigma2, er = 0.5 * c->hsc[1];
+    double ed = c->hsc[0] / (double)c->n / c->p.sigma2, er = 0.5 * c->hsc[1] * dscale(c);
     if (E) *E = er + ed;
     if (Er) *Er = er;
     if (Ed) *Ed = ed;
@@ -555,7 +620,7 @@ static int gradient_impl(lddmm_ctx* c, const float2* vt, bool known_same, float2
     }
     TRY(reg_term(c, cur));
     TRY(read_scalars(c, 2));
-    double ed = c->hsc[0] / (double)c->n / c->p.sigma2, er = 0.5 * c->hsc[1];
+    double ed = c->hsc[0] / (double)c->n / c->p.sigma2, er = 0.5 * c->hsc[1] * dscale(c);
     if (E) *E = er + ed;
     if (Er) *Er = er;
     if (Ed) *Ed = ed;
@@ -641,7 +706,7 @@ static int hessian_impl(lddmm_ctx* c, const float2* dvt, float2* out) {
     c->solves++;
     float2* pacc = c->cv[lddmm_ctx::C_T0];
     TRY(project(c, c->acc, 3, pacc));
-    TRY(cube_apply_L(out, dvt, 1.f, 1.f, pacc, c->K, 3, c->p.alpha, c->p.s, 1, c->st));
+    TRY(op_L(c, out, dvt, 1.f, 1.f, pacc, 3, 1));
     return LDDMM_OK;
 }
 
@@ -726,7 +791,7 @@ static double dot_host(lddmm_ctx* c, const float2* a, const float2* b, int* rc) 
     *rc = dot_f2_nodes(a, b, 3 * c->kc, nodes(c), c->dt, c->partials, c->dsc, c->st);
     if (*rc) return 0;
     *rc = read_scalars(c, 1);
-    return c->hsc[0];
+    return c->hsc[0] * dscale(c);
 }
 
 static int register_impl(lddmm_ctx* c, float2* v_io, const double* gref_in, lddmm_report* rep) {
@@ -743,7 +808,7 @@ static int register_impl(lddmm_ctx* c, float2* v_io, const double* gref_in, lddm
     float2 *r = c->cv[lddmm_ctx::C_R], *z = c->cv[lddmm_ctx::C_Z], *pp = c->cv[lddmm_ctx::C_P];
     float2 *Hp = c->cv[lddmm_ctx::C_HP], *x = c->cv[lddmm_ctx::C_X];
     LDDMM_CUDA(cudaMemcpyAsync(v, v_io, kc3 * sizeof(float2), cudaMemcpyDeviceToDevice, c->st));
-    TRY(cube_hermitian(v, K, ncube, c->st));
+    if (!spatial(c)) TRY(cube_hermitian(v, K, ncube, c->st));
 
     double gref2, grefi;
     double E, Er, Ed;
@@ -752,14 +817,14 @@ static int register_impl(lddmm_ctx* c, float2* v_io, const double* gref_in, lddm
         grefi = gref_in[1];
     } else {
         // reference: the gradient at v~ = 0 (cold start)
-        TRY(max_abs_f2(v, kc3, c->partials, c->dsc, c->st));
+        TRY(max_abs(c, v, kc3, c->dsc));
         TRY(read_scalars(c, 1));
         if (c->hsc[0] != 0.0) {
             LDDMM_CUDA(cudaMemsetAsync(vtr, 0, kc3 * sizeof(float2), c->st));
             TRY(gradient_impl(c, vtr, false, g, nullptr, nullptr, nullptr));
             gref2 = std::sqrt(dot_host(c, g, g, &rc));
             TRY(rc);
-            TRY(max_abs_f2(g, kc3, c->partials, c->dsc, c->st));
+            TRY(max_abs(c, g, kc3, c->dsc));
             TRY(read_scalars(c, 1));
             grefi = c->hsc[0];
         } else {
@@ -771,7 +836,7 @@ static int register_impl(lddmm_ctx* c, float2* v_io, const double* gref_in, lddm
     TRY(rc);
     if (gref2 < 0) {
         gref2 = gn;
-        TRY(max_abs_f2(g, kc3, c->partials, c->dsc, c->st));
+        TRY(max_abs(c, g, kc3, c->dsc));
         TRY(read_scalars(c, 1));
         grefi = c->hsc[0];
     }
@@ -789,7 +854,7 @@ static int register_impl(lddmm_ctx* c, float2* v_io, const double* gref_in, lddm
         // PCG on H x = -g with preconditioner L~^{-1}, x0 = 0
         LDDMM_CUDA(cudaMemsetAsync(x, 0, kc3 * sizeof(float2), c->st));
         TRY(cube_axpby(r, -1.f, g, 0.f, nullptr, kc3, c->st));
-        TRY(cube_apply_L(z, r, 1.f, 0.f, nullptr, K, ncube, c->p.alpha, c->p.s, -1, c->st));
+        TRY(op_L(c, z, r, 1.f, 0.f, nullptr, ncube, -1));
         TRY(cube_axpby(pp, 1.f, z, 0.f, nullptr, kc3, c->st));
         double rz = dot_host(c, r, z, &rc);
         TRY(rc);
@@ -800,7 +865,7 @@ static int register_impl(lddmm_ctx* c, float2* v_io, const double* gref_in, lddm
             TRY(rc);
             if (pHp <= 0.0) {
                 if (i == 0)  // preconditioned steepest descent
-                    TRY(cube_apply_L(x, r, 1.f, 0.f, nullptr, K, ncube, c->p.alpha, c->p.s, -1, c->st));
+                    TRY(op_L(c, x, r, 1.f, 0.f, nullptr, ncube, -1));
                 break;
             }
             const double a = rz / pHp;
@@ -809,7 +874,7 @@ static int register_impl(lddmm_ctx* c, float2* v_io, const double* gref_in, lddm
             double rn = std::sqrt(dot_host(c, r, r, &rc));
             TRY(rc);
             if (rn <= eta * gn) break;
-            TRY(cube_apply_L(z, r, 1.f, 0.f, nullptr, K, ncube, c->p.alpha, c->p.s, -1, c->st));
+            TRY(op_L(c, z, r, 1.f, 0.f, nullptr, ncube, -1));
             double rz2 = dot_host(c, r, z, &rc);
             TRY(rc);
             TRY(cube_axpby(pp, 1.f, z, (float)(rz2 / rz), pp, kc3, c->st));
@@ -847,7 +912,7 @@ static int register_impl(lddmm_ctx* c, float2* v_io, const double* gref_in, lddm
     const float* m1 = has_u(c) ? c->m1 : c->ms + (long)c->p.nt * c->n;
     TRY(sum_sq_diff(m1, c->I1, c->n, c->partials, c->dsc, c->st));
     TRY(sum_sq_diff(c->I0, c->I1, c->n, c->partials, c->dsc + 1, c->st));
-    TRY(max_abs_f2(g, kc3, c->partials, c->dsc + 2, c->st));
+    TRY(max_abs(c, g, kc3, c->dsc + 2));
     TRY(read_scalars(c, 3));
     rep->mse_rel = c->hsc[1] > 0 ? c->hsc[0] / c->hsc[1] : 0.0;
     rep->grad_rel_inf = c->hsc[2] / grefi;
@@ -869,9 +934,13 @@ static int ctx_alloc(lddmm_ctx* c) {
     const long n = c->n, kc3 = 3 * c->kc;
     const int nt = c->p.nt;
     const bool def = has_u(c), cub = cubic(c);
-    float* twm = nullptr;
-    TRY(dalloc_t(c, &twm, twiddle_floats(c->g, c->K)));
-    TRY(twiddle_init(c->g, c->K, twm, c->tw, c->st));
+    if (spatial(c)) {
+        TRY(spatial_fft_create(c->g, c->st, &c->fft));
+    } else {
+        float* twm = nullptr;
+        TRY(dalloc_t(c, &twm, twiddle_floats(c->g, c->K)));
+        TRY(twiddle_init(c->g, c->K, twm, c->tw, c->st));
+    }
     TRY(dalloc_t(c, &c->I0, n));
     TRY(dalloc_t(c, &c->I1, n));
     if (cub) TRY(dalloc_t(c, &c->I0c, n));
@@ -901,9 +970,11 @@ static int ctx_alloc(lddmm_ctx* c) {
         TRY(dalloc_t(c, &c->PJ, (size_t)(nt + 1) * 4 * n));
     }
     for (float** f : {&c->fa, &c->fb, &c->fc, &c->fd, &c->acc, &c->dvsp}) TRY(dalloc_t(c, f, 3 * n));
-    long se = spectral_scratch_elems(c->g, c->K, 3);
-    TRY(dalloc_t(c, &c->s1, se));
-    TRY(dalloc_t(c, &c->s2, se));
+    if (!spatial(c)) {
+        long se = spectral_scratch_elems(c->g, c->K, 3);
+        TRY(dalloc_t(c, &c->s1, se));
+        TRY(dalloc_t(c, &c->s2, se));
+    }
     for (int i = 0; i < lddmm_ctx::C_NUM; ++i) {
         TRY(dalloc_t(c, &c->cv[i], nvec(c)));
         LDDMM_CUDA(cudaMemsetAsync(c->cv[i], 0, nvec(c) * sizeof(float2), c->st));
@@ -958,8 +1029,10 @@ int lddmm_create(const lddmm_params* params, void* stream, lddmm_ctx** out) {
     c->p = *params;
     c->g = Grid{params->nx, params->ny, params->nz};
     c->n = c->g.ntot();
-    c->K = params->K;
-    c->kc = (long)c->K * c->K * c->K;
+    c->K = params->spatial ? 0 : params->K;
+    // float2 per component of a velocity-shaped vector: K^3 coefficients, or a field of n
+    // floats (n even: nx is) viewed as n/2 float2 in the spatial form
+    c->kc = params->spatial ? c->n / 2 : (long)c->K * c->K * c->K;
     c->st = static_cast<cudaStream_t>(stream);
     c->dt = 1.0 / params->nt;
     c->to_vox[0] = (float)(params->nx / (2.0 * M_PI));
@@ -981,6 +1054,7 @@ int lddmm_destroy(lddmm_ctx* c) {
     if (!c) return LDDMM_OK;
     if (c->st || true) cudaStreamSynchronize(c->st);
     if (c->hv_exec) cudaGraphExecDestroy(c->hv_exec);
+    spatial_fft_destroy(c->fft);
     for (void* p : c->allocs) cudaFree(p);
     if (c->hsc) cudaFreeHost(c->hsc);
     delete c;

@@ -116,6 +116,22 @@ int dot_f2_nodes(const float2* a, const float2* b, long npn, int nodes, double d
                  double* partials, double* out, cudaStream_t st);
 constexpr int kReduceBlocks = 296;  // 2 x 148 SMs
 
+// ---------------------------------------------------------------- spatial form (spatial.cu)
+// Full-grid FFT plans and buffers of one context (cuFFT R2C / C2R on its stream).
+struct SpatialFFT;
+int spatial_fft_create(const Grid& g, cudaStream_t st, SpatialFFT** out);
+void spatial_fft_destroy(SpatialFFT* f);
+// out_c = wL L x_c + a y_c (mode 1; y may be null) or L^{-1} x_c (mode -1), ncomp fields of
+// ntot floats; L = (Id - alpha Laplacian)^s on [0, 2 pi)^3. out may alias x.
+int spatial_apply_L(SpatialFFT* f, float* out, const float* x, float wL, float a, const float* y,
+                    int ncomp, double alpha, int s, int mode, cudaStream_t st);
+// spectral d/dx_axis of ncomp fields (component c to out + c fstride), axis 0..2; axis 3:
+// divergence of three fields into one. The Nyquist wavenumber of a derivative axis is zero.
+int spatial_deriv(SpatialFFT* f, const float* in, int ncomp, int axis, float* out, long fstride,
+                  cudaStream_t st);
+// max |a_i| over n floats
+int max_abs_f32(const float* a, long n, double* partials, double* out, cudaStream_t st);
+
 // ---------------------------------------------------------------- SL kernels (sl.cu)
 struct SLArgs {
     Grid g;

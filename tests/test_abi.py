@@ -95,3 +95,13 @@ def test_nonstationary_flag_is_validated_before_any_device_work():
         h = ctypes.c_void_p(123)
         assert lib.lddmm_create(ctypes.byref(p), None, ctypes.byref(h)) == L.EINVAL
         assert b"nonstationary" in lib.lddmm_last_error() or b"non-stationary" in lib.lddmm_last_error()
+
+
+def test_spatial_flag_is_validated_before_any_device_work():
+    lib = L.load()
+    for nx, spatial, nonst in ((32, 2, 0), (33, 1, 0), (32, 1, 1)):
+        p = L.Params(nx, 32, 32, 16, 10, L.V_DEFSTATE, L.INTERP_LINEAR, 0.0025, 2, 0.01, 5, 10,
+                     1e-3, L.PREC_FP32, nonst, spatial)
+        h = ctypes.c_void_p(123)
+        assert lib.lddmm_create(ctypes.byref(p), None, ctypes.byref(h)) == L.EINVAL
+        assert h.value is None
