@@ -59,9 +59,8 @@ def is_hbm_kernel(name):
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
 # the kernel, scaled by voxels to the 192x224x192 launch where the capture ran a smaller grid
-# (profiles/k_inc_defstate_128x160x128.md: 268.2 MB at 128x160x128 -> 844.8 MB); kernels
-# without a capture of their current code are absent (reported as null).
-NCU_TRAFFIC_PER_LAUNCH = {"sl_inc_defstate": 844.8e6}
+# kernels without a capture of their current code are absent (reported as null).
+NCU_TRAFFIC_PER_LAUNCH = {}
 
 
 def _peaks():

@@ -163,11 +163,16 @@ int lddmm_register(lddmm_ctx* ctx, float* v_inout, const double* g_ref_norms,
 int lddmm_register_batch(lddmm_ctx* const* ctxs, float* const* v_inout, int n,
                          const double* g_ref_norms, lddmm_report* reports, int max_threads);
 
-enum { LDDMM_OPT_GRAPHS = 1, LDDMM_OPT_BLOCK_X = 2 };
+enum { LDDMM_OPT_GRAPHS = 1, LDDMM_OPT_BLOCK_X = 2, LDDMM_OPT_GATHER_ZT = 3 };
 
 /* Context options: LDDMM_OPT_GRAPHS (0/1) captures the PCG Hessian-vector product into a
  * CUDA graph on its second use and replays it (lddmm_register); LDDMM_OPT_BLOCK_X sets the
- * x extent of the 256-thread blocks of the SL voxel kernels (must divide 256). */
+ * x extent of the 256-thread blocks of the SL voxel kernels (must divide 256);
+ * LDDMM_OPT_GATHER_ZT (0..16) the number of consecutive z planes one thread of the
+ * 3-component trilinear gathers and incremental deformation-state steps handles (1: one voxel
+ * per thread; more: the next plane's offsets are loaded while the current taps are in
+ * flight; 0, the default: 4 or 2 when the grid still fills the GPU, else 1). Results do not
+ * depend on it. EINVAL for other values. */
 int lddmm_set_option(lddmm_ctx* ctx, int option, long value);
 
 /* Autotuner: times the SL voxel kernels of the context's grid for block shapes

@@ -31,7 +31,7 @@ INTERP_LINEAR, INTERP_CUBIC = 1, 3
 PREC_FP32, PREC_BF16X3, PREC_FP32_SIMT, PREC_BF16X3_JBF16 = 0, 1, 2, 3
 FORWARD, BACKWARD = 1, -1
 STOP_GTOL, STOP_MAXIT, STOP_LINESEARCH = 1, 2, 3
-OPT_GRAPHS, OPT_BLOCK_X = 1, 2
+OPT_GRAPHS, OPT_BLOCK_X, OPT_GATHER_ZT = 1, 2, 3
 NET_BF16, NET_FP32 = 0, 1
 
 

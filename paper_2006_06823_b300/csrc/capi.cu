@@ -1313,6 +1313,14 @@ int lddmm_set_option(lddmm_ctx* c, int option, long value) {
             c->sl.by = 256 / (int)value;
             return LDDMM_OK;
         }
+        case LDDMM_OPT_GATHER_ZT: {
+            if (value < 0 || value > 16) {
+                set_error("gather z planes per thread must be 0 (by grid size) .. 16");
+                return LDDMM_EINVAL;
+            }
+            c->sl.zt = (int)value;
+            return LDDMM_OK;
+        }
         default:
             set_error("unknown option");
             return LDDMM_EINVAL;

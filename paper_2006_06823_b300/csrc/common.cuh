@@ -138,6 +138,7 @@ struct SLArgs {
     int interp;      // 1 or 3
     int bx = 32;     // block shape of the one-voxel-per-thread kernels (bx * by = 256)
     int by = 8;
+    int zt = 0;      // z planes per thread of the pipelined trilinear kernels (0: by grid size)
 };
 // D = offsets of departure points; vsrc = samples (linear) or spline coefficients (cubic)
 // of the velocity, vval its samples; scale[a] converts component a to voxels.

@@ -267,6 +267,65 @@ k_sl_gather(Grid g, const float* __restrict__ src, const float* __restrict__ D,
     }
 }
 
+// Trilinear 3-component gather, zt consecutive z planes per thread: the offsets (and aux) of
+// plane z + 1 are loaded while the taps of plane z are in flight, so a thread keeps the two
+// levels of its load chain (offsets -> taps) overlapped instead of serialised.
+template <int MODE>
+__global__ void __launch_bounds__(256, 5)
+k_sl_gather_zt(Grid g, const float* __restrict__ src, const float* __restrict__ D,
+               const float* __restrict__ aux, float* __restrict__ out, int zt) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= g.nx || y >= g.ny) return;
+    const int n = (int)g.ntot();             // 3 n < 2^31 (checked at context creation)
+    const int plane = g.nx * g.ny;
+    int z = blockIdx.z * zt;
+    const int zend = min(z + zt, g.nz);
+    if (z >= zend) return;
+    int i = (z * g.ny + y) * g.nx + x;
+    float d0 = __ldcs(D + i), d1 = __ldcs(D + n + i), d2 = __ldcs(D + 2 * n + i);
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f;
+    if (MODE == 1) a0 = __ldcs(aux + i);
+    if (MODE == 2) {
+        a0 = __ldcs(aux + i);
+        a1 = __ldcs(aux + n + i);
+        a2 = __ldcs(aux + 2 * n + i);
+    }
+    for (;;) {
+        const bool more = z + 1 < zend;
+        const int ip = more ? i + plane : i;
+        // next plane's streams, issued before this plane's taps are consumed
+        const float e0 = __ldcs(D + ip), e1 = __ldcs(D + n + ip), e2 = __ldcs(D + 2 * n + ip);
+        float b0 = 0.f, b1 = 0.f, b2 = 0.f;
+        if (MODE == 1) b0 = __ldcs(aux + ip);
+        if (MODE == 2) {
+            b0 = __ldcs(aux + ip);
+            b1 = __ldcs(aux + n + ip);
+            b2 = __ldcs(aux + 2 * n + ip);
+        }
+        const LinCell c = lin_cell(g, x, y, z, d0, d1, d2);
+        float v0 = lin_eval(src, c), v1 = lin_eval(src + n, c), v2 = lin_eval(src + 2 * n, c);
+        if (MODE == 1) {
+            v0 *= a0;
+            v1 *= a0;
+            v2 *= a0;
+        }
+        if (MODE == 2) {
+            v0 += a0;
+            v1 += a1;
+            v2 += a2;
+        }
+        __stcs(out + i, v0);
+        __stcs(out + n + i, v1);
+        __stcs(out + 2 * n + i, v2);
+        if (!more) break;
+        ++z;
+        i = ip;
+        d0 = e0; d1 = e1; d2 = e2;
+        a0 = b0; a1 = b1; a2 = b2;
+    }
+}
+
 // Trilinear gather, four consecutive x voxels per thread (nx % 4 == 0): float4 offset loads
 // and stores, 4 x 8 independent gathers per component in flight.
 template <int MODE, int NC>
@@ -307,6 +366,16 @@ k_sl_gather4(Grid g, const float* __restrict__ src, const float* __restrict__ D,
 
 static inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
+// z planes per thread of the pipelined 3-component kernels: the set value, or (0) the largest
+// of 4, 2 that still leaves about two waves of 256-thread blocks on 148 SMs at five per SM.
+static int zt_of(const SLArgs& a) {
+    if (a.zt > 0) return a.zt;
+    const long tiles = (long)cdiv(a.g.nx, a.bx) * cdiv(a.g.ny, a.by);
+    for (int zt : {4, 2})
+        if (tiles * cdiv(a.g.nz, zt) >= 2L * 148 * 5) return zt;
+    return 1;
+}
+
 template <int IP, int MODE>
 static void launch_gather_nc(const SLArgs& a, const float* src, const float* D, const float* aux,
                              int ncomp, float* out, cudaStream_t st) {
@@ -325,7 +394,12 @@ static void launch_gather_nc(const SLArgs& a, const float* src, const float* D, 
             k_sl_gather4<MODE, 1><<<g4, b4, 0, st>>>(a.g, s, D, x, o);
             c0 += 1;
         } else if (left >= 3) {
-            k_sl_gather<IP, MODE, 3><<<VOX_LAUNCH(a), 0, st>>>(a.g, s, D, x, o);
+            const int zt = zt_of(a);
+            if (IP == 1 && zt > 1)
+                k_sl_gather_zt<MODE><<<dim3(cdiv(a.g.nx, a.bx), cdiv(a.g.ny, a.by), cdiv(a.g.nz, zt)),
+                                       dim3(a.bx, a.by, 1), 0, st>>>(a.g, s, D, x, o, zt);
+            else
+                k_sl_gather<IP, MODE, 3><<<VOX_LAUNCH(a), 0, st>>>(a.g, s, D, x, o);
             c0 += 3;
         } else {
             k_sl_gather<IP, MODE, 1><<<VOX_LAUNCH(a), 0, st>>>(a.g, s, D, x, o);
@@ -560,6 +634,46 @@ k_inc_defstate(Grid g, const float* __restrict__ U, const float* __restrict__ D,
     }
 }
 
+// The same step over zt consecutive z planes per thread (trilinear), the offsets of plane
+// z + 1 loaded while the taps of plane z are in flight.
+template <typename TJ>
+__global__ void __launch_bounds__(256, 4)
+k_inc_defstate_zt(Grid g, const float* __restrict__ U, const float* __restrict__ D,
+                  const float* __restrict__ Fold, const TJ* __restrict__ Du,
+                  const float* __restrict__ dv, float dt, float* __restrict__ out,
+                  float* __restrict__ Fnew, int zt) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= g.nx || y >= g.ny) return;
+    const int n = (int)g.ntot();             // 3 n < 2^31 (checked at context creation)
+    const int plane = g.nx * g.ny;
+    int z = blockIdx.z * zt;
+    const int zend = min(z + zt, g.nz);
+    if (z >= zend) return;
+    int i = (z * g.ny + y) * g.nx + x;
+    float d0 = __ldcs(D + i), d1 = __ldcs(D + n + i), d2 = __ldcs(D + 2 * n + i);
+    const float h = 0.5f * dt;
+    for (;;) {
+        const bool more = z + 1 < zend;
+        const int ip = more ? i + plane : i;
+        const float e0 = __ldcs(D + ip), e1 = __ldcs(D + n + ip), e2 = __ldcs(D + 2 * n + ip);
+        const LinCell c = lin_cell(g, x, y, z, d0, d1, d2);
+        const float w0 = __ldcs(dv + i), w1 = __ldcs(dv + n + i), w2 = __ldcs(dv + 2 * n + i);
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            const float j0 = ldj(Du + (3 * a + 0) * n + i), j1 = ldj(Du + (3 * a + 1) * n + i),
+                        j2 = ldj(Du + (3 * a + 2) * n + i);
+            const float F = (a == 0 ? w0 : a == 1 ? w1 : w2) - (j0 * w0 + j1 * w1 + j2 * w2);
+            __stcs(out + a * n + i, lin_eval(U + a * n, c) + h * (lin_eval(Fold + a * n, c) + F));
+            __stcs(Fnew + a * n + i, F);
+        }
+        if (!more) break;
+        ++z;
+        i = ip;
+        d0 = e0; d1 = e1; d2 = e2;
+    }
+}
+
 int sl_inc_defstate(const SLArgs& a, const float* U, const float* D, const float* Fold,
                     const void* Du, bool du_bf16, const float* dv, double dt, float* out,
                     float* Fnew, cudaStream_t st) {
@@ -574,6 +688,13 @@ int sl_inc_defstate(const SLArgs& a, const float* U, const float* D, const float
             k_inc_defstate<3, __nv_bfloat16><<<VOX_LAUNCH(a), 0, st>>>(a.g, U, D, Fold, j16, dv, (float)dt, out, Fnew);
         else
             k_inc_defstate<3, float><<<VOX_LAUNCH(a), 0, st>>>(a.g, U, D, Fold, j32, dv, (float)dt, out, Fnew);
+    } else if (zt_of(a) > 1) {
+        const int zt = zt_of(a);
+        const dim3 grid(cdiv(a.g.nx, a.bx), cdiv(a.g.ny, a.by), cdiv(a.g.nz, zt)), block(a.bx, a.by, 1);
+        if (du_bf16)
+            k_inc_defstate_zt<__nv_bfloat16><<<grid, block, 0, st>>>(a.g, U, D, Fold, j16, dv, (float)dt, out, Fnew, zt);
+        else
+            k_inc_defstate_zt<float><<<grid, block, 0, st>>>(a.g, U, D, Fold, j32, dv, (float)dt, out, Fnew, zt);
     } else {
         if (du_bf16)
             k_inc_defstate<1, __nv_bfloat16><<<VOX_LAUNCH(a), 0, st>>>(a.g, U, D, Fold, j16, dv, (float)dt, out, Fnew);

@@ -216,3 +216,23 @@ def test_jacobian_determinant_needs_the_deformation_state():
     with gpu_context(prob) as ctx:
         with pytest.raises(L.LddmmError):
             ctx.jacobian_det(ctx.zeros_cube())
+
+
+@pytest.mark.parametrize("variant", [Vn.DEFSTATE, Vn.IMAGE])
+def test_z_pipelined_kernels_give_identical_results(variant):
+    """LDDMM_OPT_GATHER_ZT only changes how many z planes a thread walks (ragged last block
+    here: nz = 37): gradients and Hessian-vector products are bitwise equal for every depth."""
+    prob = oracle_problem((37, 20, 32), 16, variant, 1, nt=4)
+    vt = devc(synth.random_velocity_coeffs(16, 16, seed=3) * 0.5)
+    dv = devc(synth.random_coeffs(16, seed=4) * 0.1)
+    out = []
+    for zt in (1, 2, 4, 16, 0):
+        with gpu_context(prob) as ctx:          # a fresh context: the state sweep runs too
+            ctx.set_option(L.OPT_GATHER_ZT, zt)
+            g = ctx.gradient(vt)[1].clone()
+            h = ctx.hessian_matvec(vt, dv).clone()
+            out.append((g, h))
+            with pytest.raises(L.LddmmError):
+                ctx.set_option(L.OPT_GATHER_ZT, 17)
+    for g, h in out[1:]:
+        assert torch.equal(g, out[0][0]) and torch.equal(h, out[0][1])
