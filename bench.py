@@ -59,8 +59,9 @@ def is_hbm_kernel(name):
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
 # the kernel, scaled by voxels to the 192x224x192 launch where the capture ran a smaller grid
-# kernels without a capture of their current code are absent (reported as null).
-NCU_TRAFFIC_PER_LAUNCH = {}
+# (profiles/k_inc_defstate_128x160x128.md: 263.7 MB at 128x160x128 -> 830.6 MB); kernels
+# without a capture of their current code are absent (reported as null).
+NCU_TRAFFIC_PER_LAUNCH = {"sl_inc_defstate": 830.6e6}
 
 
 def _peaks():

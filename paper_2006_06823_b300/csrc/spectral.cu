@@ -513,14 +513,18 @@ int bl_project(const Grid& g, const Twiddles& tw, const float* f, long fstride, 
 // ------------------------------------------------- iota stage Z (GEMM over all planes)
 // T1[comp][z][j] = sum_{jz>=1} Ez[z][jz] * m(k) c[comp][jz][jy][K/2+kx],  j = jy*KH + kx,
 // with m(k) the derivative / divergence multiplier and 1/B^(k) for B-spline coefficients.
-// CTA tile: 32 planes x 32 columns (128 threads, so that 192-plane grids still fill the SMs);
-// thread: 4 planes x 2 columns (8 complex accumulators).
-constexpr int Z2_ZT = 32, Z2_JT = 32, Z2_THREADS = (Z2_JT / 2) * (Z2_ZT / 4);
+// CTA tile: 32 planes x 32 columns; thread: ZPT planes x 2 columns (2 ZPT complex
+// accumulators), 16 x 32 / ZPT threads. The stage is small and latency-bound, so fewer planes
+// per thread (more resident warps) is faster.
+constexpr int Z2_ZT = 32, Z2_JT = 32;
+constexpr int IOTA_Z_ZPT = 1;
 
-__global__ void __launch_bounds__(Z2_THREADS)
+template <int ZPT>
+__global__ void __launch_bounds__((Z2_JT / 2) * (Z2_ZT / ZPT))
 k_iota_z2(const float2* __restrict__ c, int nz, int ny, int nx, int K, int KH, int deriv_axis,
           int bspline, const float* __restrict__ cxT, const float* __restrict__ cyT,
           const float* __restrict__ czT, const float* __restrict__ szT, float2* __restrict__ T1) {
+    constexpr int NTH = (Z2_JT / 2) * (Z2_ZT / ZPT);
     __shared__ float4 cs4[32 * Z2_JT / 2];   // [jz][Z2_JT] float2 (K <= 64 -> 2 passes if K > 32)
     __shared__ float4 es4[32 * Z2_ZT / 2];   // [jz][Z2_ZT] float2
     float2* cs = reinterpret_cast<float2*>(cs4);
@@ -529,16 +533,16 @@ k_iota_z2(const float2* __restrict__ c, int nz, int ny, int nx, int K, int KH, i
     const int z0 = blockIdx.x * Z2_ZT, j0 = blockIdx.y * Z2_JT;
     const int KK = K * KH, h = K / 2;
     const int tid = threadIdx.x, jq = tid % (Z2_JT / 2), zq = tid / (Z2_JT / 2);
-    float ar[4][2], ai[4][2];
+    float ar[ZPT][2], ai[ZPT][2];
 #pragma unroll
-    for (int a = 0; a < 4; ++a)
+    for (int a = 0; a < ZPT; ++a)
 #pragma unroll
         for (int b = 0; b < 2; ++b) ar[a][b] = ai[a][b] = 0.f;
     const long kk3 = (long)K * K * K;
     for (int jzb = 0; jzb < K; jzb += 32) {
         const int nj = min(32, K - jzb);
         __syncthreads();
-        for (int e = tid; e < 32 * Z2_JT; e += Z2_THREADS) {
+        for (int e = tid; e < 32 * Z2_JT; e += NTH) {
             const int jzl = e / Z2_JT, jj = e - jzl * Z2_JT;
             const int jz = jzb + jzl, j = j0 + jj;
             float2 v = make_float2(0.f, 0.f);
@@ -575,7 +579,7 @@ k_iota_z2(const float2* __restrict__ c, int nz, int ny, int nx, int K, int KH, i
             }
             cs[e] = v;
         }
-        for (int e = tid; e < 32 * Z2_ZT; e += Z2_THREADS) {
+        for (int e = tid; e < 32 * Z2_ZT; e += NTH) {
             const int jzl = e / Z2_ZT, zz = e - jzl * Z2_ZT;
             const int jz = jzb + jzl, z = z0 + zz;
             es[e] = (jzl < nj && z < nz) ? make_float2(czT[(long)jz * nz + z], szT[(long)jz * nz + z])
@@ -584,13 +588,12 @@ k_iota_z2(const float2* __restrict__ c, int nz, int ny, int nx, int K, int KH, i
         __syncthreads();
         for (int jzl = 0; jzl < nj; ++jzl) {
             const float4 cv = *reinterpret_cast<const float4*>(&cs[jzl * Z2_JT + 2 * jq]);
-            const float4 e01 = *reinterpret_cast<const float4*>(&es[jzl * Z2_ZT + 4 * zq]);
-            const float4 e23 = *reinterpret_cast<const float4*>(&es[jzl * Z2_ZT + 4 * zq + 2]);
-            const float2 ev[4] = {make_float2(e01.x, e01.y), make_float2(e01.z, e01.w),
-                                  make_float2(e23.x, e23.y), make_float2(e23.z, e23.w)};
+            float2 ev[ZPT];
+#pragma unroll
+            for (int a = 0; a < ZPT; ++a) ev[a] = es[jzl * Z2_ZT + ZPT * zq + a];
             const float2 cw[2] = {make_float2(cv.x, cv.y), make_float2(cv.z, cv.w)};
 #pragma unroll
-            for (int a = 0; a < 4; ++a)
+            for (int a = 0; a < ZPT; ++a)
 #pragma unroll
                 for (int b = 0; b < 2; ++b) {
                     // (e.x + i e.y)(c.x + i c.y)
@@ -600,8 +603,8 @@ k_iota_z2(const float2* __restrict__ c, int nz, int ny, int nx, int K, int KH, i
         }
     }
 #pragma unroll
-    for (int a = 0; a < 4; ++a) {
-        const int z = z0 + 4 * zq + a;
+    for (int a = 0; a < ZPT; ++a) {
+        const int z = z0 + ZPT * zq + a;
         if (z >= nz) continue;
         float2* dst = T1 + ((long)comp * nz + z) * KK + j0 + 2 * jq;
 #pragma unroll
@@ -618,8 +621,8 @@ static int launch_iota_zy2(const Grid& g, const Twiddles& tw, const float2* c, i
         KTRACE("iota_z", st, (double)(deriv_axis == 3 ? 3 : nout) * K * K * KH * 8.0 +
                                  (double)nout * g.nz * KK * 8.0,
                (double)nout * g.nz * KK * K * 8.0);
-        k_iota_z2<<<grid, Z2_THREADS, 0, st>>>(c, g.nz, g.ny, g.nx, K, KH, deriv_axis, bspline, tw.cx,
-                                        tw.cy, tw.cz, tw.sz, T1);
+        k_iota_z2<IOTA_Z_ZPT><<<grid, (Z2_JT / 2) * (Z2_ZT / IOTA_Z_ZPT), 0, st>>>(
+            c, g.nz, g.ny, g.nx, K, KH, deriv_axis, bspline, tw.cx, tw.cy, tw.cz, tw.sz, T1);
     }
     LDDMM_CHECK_LAUNCH();
     // stage Y: T2[plane][y][kx] = sum_{jy >= 1} e^{+i ky y} T1[plane][jy][kx]
