@@ -915,24 +915,32 @@ __device__ __forceinline__ void prefilter_line(float* f, long stride, int L) {
     }
 }
 
-// x lines through shared memory: the CTA stages `rows` rows, one thread filters one row.
-__global__ void k_prefilter_x(const float* __restrict__ in, float* __restrict__ out, long nrows,
-                              int nx, int rows) {
+// x lines through shared memory: the CTA stages `rows` rows with all of its threads (a flat,
+// unrolled copy, so that many loads are in flight), one thread filters one row, and all
+// threads write the rows back. Rows are padded to nx + 1 floats (no bank conflicts).
+constexpr int PFX_THREADS = 256;
+
+__global__ void __launch_bounds__(PFX_THREADS)
+k_prefilter_x(const float* __restrict__ in, float* __restrict__ out, long nrows, int nx, int rows) {
     extern __shared__ float sm[];
     const int ld = nx + 1;
     const long row0 = (long)blockIdx.x * rows;
-    for (int r = 0; r < rows; ++r) {
-        long row = row0 + r;
-        if (row >= nrows) break;
-        for (int x = threadIdx.x; x < nx; x += blockDim.x) sm[r * ld + x] = in[row * nx + x];
+    const int nr = (int)min((long)rows, nrows - row0);
+    const int tot = nr * nx;
+    const float* src = in + row0 * nx;
+#pragma unroll 4
+    for (int e = threadIdx.x; e < tot; e += PFX_THREADS) {
+        const int r = e / nx;
+        sm[r * ld + (e - r * nx)] = __ldcs(src + e);
     }
     __syncthreads();
-    if (threadIdx.x < rows && row0 + threadIdx.x < nrows) prefilter_line(sm + threadIdx.x * ld, 1, nx);
+    if ((int)threadIdx.x < nr) prefilter_line(sm + threadIdx.x * ld, 1, nx);
     __syncthreads();
-    for (int r = 0; r < rows; ++r) {
-        long row = row0 + r;
-        if (row >= nrows) break;
-        for (int x = threadIdx.x; x < nx; x += blockDim.x) out[row * nx + x] = sm[r * ld + x];
+    float* dst = out + row0 * nx;
+#pragma unroll 4
+    for (int e = threadIdx.x; e < tot; e += PFX_THREADS) {
+        const int r = e / nx;
+        dst[e] = sm[r * ld + (e - r * nx)];
     }
 }
 
@@ -948,8 +956,9 @@ __global__ void k_prefilter_strided(float* f, long nlines, int nx, long outer_st
 // out = B-spline coefficients of ncomp fields `in` (out may alias in).
 int bspline_prefilter(const Grid& g, const float* in, int ncomp, float* out, cudaStream_t st) {
     const long n = g.ntot();
-    int rows = 128;
-    while (rows > 32 && (long)rows * (g.nx + 1) * 4 > 200 * 1024) rows -= 32;
+    // rows per CTA: up to one per thread, fewer when the staged rows would not fit
+    int rows = PFX_THREADS;
+    while (rows > 32 && (long)rows * (g.nx + 1) * 4 > 100 * 1024) rows -= 32;
     if ((long)rows * (g.nx + 1) * 4 > 220 * 1024) {
         set_error("bspline_prefilter: nx too large");
         return LDDMM_EINVAL;
@@ -967,7 +976,7 @@ int bspline_prefilter(const Grid& g, const float* in, int ncomp, float* out, cud
         long nrows = (long)g.ny * g.nz;
         {
             KTRACE("prefilter_x", st, 8.0 * n, 8.0 * n);
-            k_prefilter_x<<<cdiv(nrows, rows), rows, smem, st>>>(src, dst, nrows, g.nx, rows);
+            k_prefilter_x<<<cdiv(nrows, rows), PFX_THREADS, smem, st>>>(src, dst, nrows, g.nx, rows);
         }
         LDDMM_CHECK_LAUNCH();
         // y lines: for each z, x -> start z*nx*ny + x, stride nx
