@@ -1054,11 +1054,40 @@ __global__ void k_accum_sv(long n, const float* __restrict__ s, const float* __r
         acc[b * n + i] = init ? v * Gm[b * n + i] : fmaf(v, Gm[b * n + i], acc[b * n + i]);
 }
 
+// four voxels per thread (n % 4 == 0, 16-byte aligned planes): 16-byte loads and stores
+__global__ void k_accum_sv4(long n4, long n, const float4* __restrict__ s, const float* __restrict__ Gm,
+                            float w, float* __restrict__ acc, int init) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n4) return;
+    const float4 sv = __ldcs(s + i);
+    const float4 v = make_float4(w * sv.x, w * sv.y, w * sv.z, w * sv.w);
+#pragma unroll
+    for (int b = 0; b < 3; ++b) {
+        const float4 gm = __ldcs(reinterpret_cast<const float4*>(Gm + b * n) + i);
+        float4* a = reinterpret_cast<float4*>(acc + b * n) + i;
+        float4 r;
+        if (init) {
+            r = make_float4(v.x * gm.x, v.y * gm.y, v.z * gm.z, v.w * gm.w);
+        } else {
+            const float4 o = *a;
+            r = make_float4(fmaf(v.x, gm.x, o.x), fmaf(v.y, gm.y, o.y), fmaf(v.z, gm.z, o.z),
+                            fmaf(v.w, gm.w, o.w));
+        }
+        *a = r;
+    }
+}
+
 int accum_sv(const Grid& g, const float* s, const float* Gm, float w, float* acc, int init,
              cudaStream_t st) {
     long n = g.ntot();
     KTRACE("accum_sv", st, n * (28.0 + (init ? 0.0 : 12.0)), 7.0 * n);
-    k_accum_sv<<<cdiv(n, 256), 256, 0, st>>>(n, s, Gm, w, acc, init);
+    const bool al = ((reinterpret_cast<uintptr_t>(s) | reinterpret_cast<uintptr_t>(Gm) |
+                      reinterpret_cast<uintptr_t>(acc)) & 15) == 0;
+    if ((n & 3) == 0 && al)
+        k_accum_sv4<<<cdiv(n / 4, 256), 256, 0, st>>>(n / 4, n, reinterpret_cast<const float4*>(s), Gm,
+                                                      w, acc, init);
+    else
+        k_accum_sv<<<cdiv(n, 256), 256, 0, st>>>(n, s, Gm, w, acc, init);
     LDDMM_CHECK_LAUNCH();
     return LDDMM_OK;
 }
