@@ -97,6 +97,15 @@ def heun_jacobian_step(U, Dplus, d, dt, order):
     return a + 0.5 * dt * (f_old + d * (u_star - 1.0))
 
 
+def heun_jacobian_step_ns(U, Dplus, d_next, d_here, dt, order):
+    """heun_jacobian_step between nodes t_j and t_{j+1} (non-stationary v): d(X+) from d_{j+1},
+    d(x) from d_j."""
+    a = I.interpolate(U, Dplus, order)
+    f_old = I.interpolate(d_next, Dplus, order) * (a - 1.0)
+    u_star = a + dt * f_old
+    return a + 0.5 * dt * (f_old + d_here * (u_star - 1.0))
+
+
 def heun_divergence_step_ns(u, Dplus, d_next, d_here, dt, order):
     """-D_t u = u div v_t between nodes t_j and t_{j+1} (non-stationary v): as
     heun_divergence_step with d(X+) taken from d_{j+1} and d(x) from d_j."""
@@ -129,6 +138,11 @@ def bl_transport_step(c, D, order, shape, K):
 def bl_heun_source_step(c, D, F_old, F_new, dt, order, shape, K):
     """One BL step of D~_t u~ = F with spatial right-hand sides F_j, F_{j+1} on the grid."""
     return S.project(heun_source_step(S.include(c, shape), D, F_old, F_new, dt, order), K)
+
+
+def bl_heun_jacobian_step_ns(c, Dplus, d_next, d_here, dt, order, shape, K):
+    """One backward BL step of the U~ equation with node-dependent divergence."""
+    return S.project(heun_jacobian_step_ns(S.include(c, shape), Dplus, d_next, d_here, dt, order), K)
 
 
 def bl_heun_divergence_step_ns(c, Dplus, d_next, d_here, dt, order, shape, K):

@@ -332,9 +332,10 @@ class Problem:
 
 
 class ProblemNS(Problem):
-    """Non-stationary deformation-state variant (Sec. 2.3.3 with a time-dependent v~_t; the
+    """Non-stationary forms of the three variants (Sec. 2.3 with a time-dependent v~_t; the
     paper's NSt rows): the unknown is v~ = [v~_0 .. v~_nt], one cube per node t_j = j/nt
-    ([nt+1][3][K][K][K]). Equations as in Problem with v~ replaced by v~(t_j) at node j:
+    ([nt+1][3][K][K][K]). Equations as in Problem with v~ replaced by v~(t_j) at node j.
+    Deformation state:
       state   u~_{j+1} = pi[iota(u~_j) o X_j + dt/2 (v_j(X_j) + v_{j+1}(x))],
               X_j from departure_offsets_ns(V_{j+1}, V_j) (R10);
       adjoint rho~_j = pi[Heun step of -D_t rho = rho div v_t along X+_j],
@@ -345,12 +346,14 @@ class ProblemNS(Problem):
               g_j = L~v~_j + rho~_j - pi((D iota u~_j)^T iota rho~_j);
       Gauss-Newton Hessian likewise with drho~ and the incremental state
               D~_t du~ = dv~_t - D~u~ * dv~_t.
-    With all nodes equal it reduces to Problem (the weighted sum of g_j is the stationary
+    Image variant: m_{j+1} = m_j o X_j; lambda_j = Heun step of -D_t lambda = lambda div v_t
+    along X+_j; g_j = L~v~_j + pi(iota(pi lambda_j) iota(grad~ m~_j)); the incremental state
+    dm~ with right-hand sides -grad~ m~_j * dv~_j, dlambda~ along X+_j, H_j likewise.
+    State-equation variant: u~ as above, nu~_j = pi[iota(nu~_{j+1}) o X+_j - dt/2 (v_{j+1}(X+_j)
+    + v_j(x))], U~ with d_{j+1}(X+_j) and d_j(x), lambda_j = J_j lambda(1) o psi_j, g_j and H_j
+    as for the image variant with these m_j and lambda_j.
+    With all nodes equal each reduces to Problem (the weighted sum of g_j is the stationary
     gradient)."""
-
-    def __init__(self, I0, I1, params: Params):
-        assert params.variant == DEFSTATE
-        super().__init__(I0, I1, params)
 
     def inner(self, a, b):
         return float(sum(w * S.inner(x, y) for w, x, y in zip(self.tw, a, b)))
@@ -406,9 +409,52 @@ class ProblemNS(Problem):
             out.append(S.apply_L(bj, self.p.alpha, self.p.s) + rho - S.project(JT, self.p.K))
         return np.stack(out)
 
+    def state_image(self, vts):
+        Df, _ = self._offsets(self.velocities(vts))
+        ms = [self.I0.copy()]
+        for j in range(self.p.nt):
+            ms.append(SL.transport_step(ms[-1], Df[j], self.p.order))
+        return ms
+
+    def inverse_maps(self, vts):
+        p = self.p
+        vel = self.velocities(vts)
+        _, Db = self._offsets(vel)
+        nu = np.zeros((3, p.K, p.K, p.K), dtype=np.complex128)
+        U = np.zeros((p.K, p.K, p.K), dtype=np.complex128)
+        nus, Us = [None] * (p.nt + 1), [None] * (p.nt + 1)
+        nus[p.nt], Us[p.nt] = nu, U
+        for j in range(p.nt - 1, -1, -1):
+            nu = SL.bl_heun_source_step(nu, Db[j], -vel[j + 1][0], -vel[j][0], self.dt, p.order,
+                                        self.shape, p.K)
+            U = SL.bl_heun_jacobian_step_ns(U, Db[j], vel[j + 1][2], vel[j][2], self.dt, p.order,
+                                            self.shape, p.K)
+            nus[j], Us[j] = nu, U
+        return nus, Us
+
+    def _assemble_image_ns(self, base, lams, gms, project_lam=True):
+        out = []
+        for bj, lam, gm in zip(base, lams, gms):
+            lt = S.project(lam, self.p.K) if project_lam else lam
+            out.append(S.apply_L(bj, self.p.alpha, self.p.s)
+                       + S.project(S.include(lt, self.shape)[None] * gm, self.p.K))
+        return np.stack(out)
+
+    def _inc_defstate_ns(self, vts, dvts, us, Df):
+        p = self.p
+        Jus = self._jacobians(us)
+        dvs = [S.include(dv, self.shape) for dv in dvts]
+        F = [dv - np.einsum("abzyx,bzyx->azyx", Ju, dv) for Ju, dv in zip(Jus, dvs)]
+        du = np.zeros((3, p.K, p.K, p.K), dtype=np.complex128)
+        for j in range(p.nt):
+            du = SL.bl_heun_source_step(du, Df[j], F[j], F[j + 1], self.dt, p.order, self.shape, p.K)
+        return du
+
     def objective(self, vts):
-        us = self.state_defstate(vts)
-        m1, _ = self._warp_I0(us[-1])
+        if self.p.variant == IMAGE:
+            m1 = self.state_image(vts)[-1]
+        else:
+            m1, _ = self._warp_I0(self.state_defstate(vts)[-1])
         er, ed = self.energy_reg(vts), self.energy_data(m1)
         return er + ed, er, ed, m1
 
@@ -416,6 +462,25 @@ class ProblemNS(Problem):
         p = self.p
         vel = self.velocities(vts)
         _, Db = self._offsets(vel)
+        if p.variant == IMAGE:
+            ms = self.state_image(vts)
+            m1 = ms[-1]
+            lams = [None] * (p.nt + 1)
+            lams[p.nt] = lam = -(2.0 / p.sigma2) * (m1 - self.I1)
+            for j in range(p.nt - 1, -1, -1):
+                lam = SL.heun_divergence_step_ns(lam, Db[j], vel[j + 1][2], vel[j][2], self.dt, p.order)
+                lams[j] = lam
+            g = self._assemble_image_ns(vts, lams, self._grad_mtilde(ms))
+            er, ed = self.energy_reg(vts), self.energy_data(m1)
+            return er + ed, er, ed, g
+        if p.variant == STATE:
+            us = self.state_defstate(vts)
+            m1, _ = self._warp_I0(us[-1])
+            nus, Us = self.inverse_maps(vts)
+            lams = self._pull_back(-(2.0 / p.sigma2) * (m1 - self.I1), nus, Us)
+            g = self._assemble_image_ns(vts, lams, self._grad_mtilde(self._compose_I0(us)))
+            er, ed = self.energy_reg(vts), self.energy_data(m1)
+            return er + ed, er, ed, g
         us = self.state_defstate(vts)
         m1, G = self._warp_I0(us[-1])
         rho1 = S.project(-(2.0 / p.sigma2) * (m1 - self.I1)[None] * G, p.K)
@@ -428,15 +493,28 @@ class ProblemNS(Problem):
         p = self.p
         vel = self.velocities(vts)
         Df, Db = self._offsets(vel)
+        if p.variant == IMAGE:
+            ms = self.state_image(vts)
+            gms = self._grad_mtilde(ms)
+            F = [-np.sum(gm * S.include(dv, self.shape), axis=0) for gm, dv in zip(gms, dvts)]
+            dm = np.zeros((p.K, p.K, p.K), dtype=np.complex128)
+            for j in range(p.nt):
+                dm = SL.bl_heun_source_step(dm, Df[j], F[j], F[j + 1], self.dt, p.order, self.shape, p.K)
+            dlams = [None] * (p.nt + 1)
+            dlams[p.nt] = dlam = -(2.0 / p.sigma2) * dm
+            for j in range(p.nt - 1, -1, -1):
+                dlam = SL.bl_heun_divergence_step_ns(dlam, Db[j], vel[j + 1][2], vel[j][2], self.dt,
+                                                     p.order, self.shape, p.K)
+                dlams[j] = dlam
+            return self._assemble_image_ns(dvts, dlams, gms, project_lam=False)
         us = self.state_defstate(vts)
-        Jus = self._jacobians(us)
         _, G = self._warp_I0(us[-1])
-        dvs = [S.include(dv, self.shape) for dv in dvts]
-        F = [dv - np.einsum("abzyx,bzyx->azyx", Ju, dv) for Ju, dv in zip(Jus, dvs)]
-        du = np.zeros((3, p.K, p.K, p.K), dtype=np.complex128)
-        for j in range(p.nt):
-            du = SL.bl_heun_source_step(du, Df[j], F[j], F[j + 1], self.dt, p.order, self.shape, p.K)
-        dm1 = -np.sum(G * S.include(du, self.shape), axis=0)
+        dm1 = -np.sum(G * S.include(self._inc_defstate_ns(vts, dvts, us, Df), self.shape), axis=0)
+        if p.variant == STATE:
+            nus, Us = self.inverse_maps(vts)
+            dlams = self._pull_back(-(2.0 / p.sigma2) * dm1, nus, Us)
+            return self._assemble_image_ns(dvts, dlams, self._grad_mtilde(self._compose_I0(us)))
+        Jus = self._jacobians(us)
         drho1 = S.project(-(2.0 / p.sigma2) * dm1[None] * G, p.K)
         drhos = self._adjoint_ns(drho1, vel, Db)
         return self._assemble_ns(dvts, drhos, Jus)

@@ -1,4 +1,4 @@
-"""Pins of the non-stationary deformation-state oracle (ProblemNS): reduction to the
+"""Pins of the non-stationary oracle (ProblemNS) for the three variants: reduction to the
 stationary problem, exact two-field characteristics, central differences of the energy,
 symmetry and positivity of the Gauss-Newton Hessian, and a descending registration."""
 import numpy as np
@@ -12,9 +12,12 @@ from paper_2006_06823_b300 import synth
 from _problems import blob_pair, voxel_velocity
 
 
-def problems(shape=(16, 16, 16), K=8, nt=4, order=1):
+VARIANTS = [Vn.DEFSTATE, Vn.IMAGE, Vn.STATE]
+
+
+def problems(shape=(16, 16, 16), K=8, nt=4, order=1, variant=Vn.DEFSTATE):
     I0, I1 = blob_pair(shape, K, seed=0, order=order)
-    p = Vn.Params(K=K, nt=nt, order=order, variant=Vn.DEFSTATE)
+    p = Vn.Params(K=K, nt=nt, order=order, variant=variant)
     return Vn.Problem(I0, I1, p), Vn.ProblemNS(I0, I1, p)
 
 
@@ -31,9 +34,10 @@ def test_two_field_offsets_reduce_to_the_stationary_ones():
         assert np.array_equal(a, b)
 
 
+@pytest.mark.parametrize("variant", VARIANTS)
 @pytest.mark.parametrize("order", [1, 3])
-def test_equal_nodes_reduce_to_the_stationary_problem(order):
-    st, ns = problems(order=order)
+def test_equal_nodes_reduce_to_the_stationary_problem(order, variant):
+    st, ns = problems(order=order, variant=variant)
     K, nt = st.p.K, st.p.nt
     vt = synth.random_velocity_coeffs(K, K, seed=3) * 0.5
     vts = np.stack([vt] * (nt + 1))
@@ -49,32 +53,43 @@ def test_equal_nodes_reduce_to_the_stationary_problem(order):
     np.testing.assert_allclose(Hsum, H, atol=1e-12 * np.abs(H).max())
 
 
-def test_gradient_matches_central_differences():
-    _, ns = problems()
+# |fd - <g, e>_w| against |g|_w |e|_w, cubic interpolation: measured 5.7e-4 (deformation
+# state), 2.2e-3 (image), 1.4e-3 (state equation); Hessian asymmetry 3.9e-4, 4.6e-4, 2.9e-3
+FD_TOL = {Vn.DEFSTATE: 2e-3, Vn.IMAGE: 4e-3, Vn.STATE: 3e-3}
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_gradient_matches_central_differences(variant):
+    _, ns = problems(order=3, variant=variant)
     K, nt = ns.p.K, ns.p.nt
     vts = stack(K, nt, 10, 0.4)
-    e = stack(K, nt, 30, 0.05)
     g = ns.gradient(vts)[3]
     h = 1e-3
-    fd = (ns.objective(vts + h * e)[0] - ns.objective(vts - h * e)[0]) / (2 * h)
-    an = ns.inner(g, e)
-    assert abs(fd - an) <= 2e-2 * abs(fd), (fd, an)
+    for seed in (30, 40):
+        e = stack(K, nt, seed, 0.05)
+        fd = (ns.objective(vts + h * e)[0] - ns.objective(vts - h * e)[0]) / (2 * h)
+        an = ns.inner(g, e)
+        scale = np.sqrt(ns.inner(g, g) * ns.inner(e, e))
+        assert abs(fd - an) <= FD_TOL[variant] * scale, (fd, an, scale)
 
 
-def test_hessian_is_nearly_symmetric_and_positive():
-    _, ns = problems()
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_hessian_is_nearly_symmetric_and_positive(variant):
+    _, ns = problems(order=3, variant=variant)
     K, nt = ns.p.K, ns.p.nt
     vts = stack(K, nt, 50, 0.3)
     a = stack(K, nt, 70, 0.1)
     b = stack(K, nt, 90, 0.1)
     Ha, Hb = ns.hessian_matvec(vts, a), ns.hessian_matvec(vts, b)
     x, y = ns.inner(b, Ha), ns.inner(Hb, a)
-    assert abs(x - y) <= 2e-2 * max(abs(x), abs(y)), (x, y)
-    assert ns.inner(a, Ha) > 0 and ns.inner(b, Hb) > 0
+    aHa, bHb = ns.inner(a, Ha), ns.inner(b, Hb)
+    assert aHa > 0 and bHb > 0
+    assert abs(x - y) <= 2e-2 * np.sqrt(aHa * bHb), (x, y)
 
 
-def test_registration_descends():
-    _, ns = problems()
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_registration_descends(variant):
+    _, ns = problems(variant=variant)
     v, rep = gnk.register(ns, max_gn=3, max_pcg=5)
     Es = [h[0] for h in rep.history]
     assert all(b < a for a, b in zip(Es, Es[1:]))
