@@ -338,6 +338,8 @@ FORMS = [("defstate/linear/bf16x3_jbf16", "V_DEFSTATE", "INTERP_LINEAR", "PREC_B
          ("image/cubic/fp32", "V_IMAGE", "INTERP_CUBIC", "PREC_FP32", False, False),
          ("defstate/linear/fp32/nonstationary", "V_DEFSTATE", "INTERP_LINEAR", "PREC_FP32", True, False),
          ("state/linear/fp32", "V_STATE", "INTERP_LINEAR", "PREC_FP32", False, False),
+         ("image/linear/fp32/nonstationary", "V_IMAGE", "INTERP_LINEAR", "PREC_FP32", True, False),
+         ("state/linear/fp32/nonstationary", "V_STATE", "INTERP_LINEAR", "PREC_FP32", True, False),
          ("defstate/linear/fp32/spatial", "V_DEFSTATE", "INTERP_LINEAR", "PREC_FP32", False, True),
          ("image/linear/fp32/spatial", "V_IMAGE", "INTERP_LINEAR", "PREC_FP32", False, True)]
 

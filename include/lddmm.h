@@ -80,18 +80,19 @@ typedef struct {
     double gtol;       /* stop when ||g|| / ||g(v=0)|| <= gtol */
     int precision;     /* LDDMM_PREC_* form */
     int nonstationary; /* 0: one cube v~ for all t (the default); 1: v~_j at every node t_j =
-                          j/nt (deformation state only). Every velocity argument of a
+                          j/nt (any variant, either domain). Every velocity argument of a
                           non-stationary context is then the stack float[nt+1][3][K][K][K][2];
                           norms and inner products of such stacks weight node j by the
                           trapezoid weight w_j (R11), and the gradient / Hessian at node j is
-                          the integrand of Eq. 32 / 33 at t_j. */
+                          the integrand of Eq. 32 / 33 (15 / 16 for IMAGE and STATE) at t_j. */
     int spatial;       /* 0: band-limited (the default; Sec. 2.2-2.3). 1: spatial domain (Sec. 2.1
                           with SL-RK in Omega, the paper's "PDE-LDDMM ... SL" methods): every
                           velocity argument is a field float[3][nz][ny][nx] (physical
                           units); K is ignored, pi and iota are the identity, and L, L^{-1}
                           and the derivatives grad m,
                           D u, div v are spectral on the full grid (cuFFT). Inner products and
-                          E_reg use the voxel mean. nx must be even; stationary only. */
+                          E_reg use the voxel mean. nx must be even. A non-stationary
+                          spatial velocity is float[nt+1][3][nz][ny][nx]. */
 } lddmm_params;
 
 /* Outcome of lddmm_register. */

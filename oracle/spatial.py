@@ -20,7 +20,7 @@ Readings fixed here:
   * Every other reading (Heun step, trapezoid integrals, G = grad(I0 interpolant) o phi(1),
     dm(1) = -G . du(1), the Gauss-Newton terms of each variant, the nu and U equations of the
     state variant) is the band-limited one (``oracle/variants.py``).
-  * Stationary velocity.
+  * SpatialProblem: stationary velocity; SpatialProblemNS: one field per time node.
 """
 from __future__ import annotations
 
@@ -248,3 +248,122 @@ class SpatialProblem:
             return self._assemble_image(dv, dlams, [grad(m) for m in ms])
         drhos = self._backward(-(2.0 / p.sigma2) * dm1[None] * G, v)
         return self._assemble_defstate(dv, drhos, us)
+
+
+class SpatialProblemNS(SpatialProblem):
+    """Non-stationary spatial forms (the paper's "NSt. PDE-LDDMM ... SL" rows): the unknown is
+    [v_0 .. v_nt], one field per node t_j = j / nt ([nt+1][3][nz][ny][nx]); every step uses the
+    two-field characteristics of its end nodes (SL.departure_offsets_ns), the divergence of
+    the node it reads, the gradient and Hessian at node j are the integrands at t_j, and the
+    product is the trapezoid-weighted sum of the voxel-mean products of the nodes. With all
+    nodes equal it reduces to SpatialProblem (the weighted sum of the g_j is its gradient)."""
+
+    def zeros(self):
+        return np.zeros((self.p.nt + 1, 3) + self.shape)
+
+    def inner(self, a, b):
+        return float(sum(w * inner(x, y) for w, x, y in zip(self.tw, a, b)))
+
+    def precond(self, r):
+        return np.stack([apply_L(x, self.p.alpha, self.p.s, inverse=True) for x in r])
+
+    def energy_reg(self, vs):
+        return float(sum(w * 0.5 * inner(apply_L(v, self.p.alpha, self.p.s), v)
+                         for w, v in zip(self.tw, vs)))
+
+    def _offsets_ns(self, vs):
+        p = self.p
+        Vs = [v * self.tv for v in vs]
+        Df = [SL.departure_offsets_ns(Vs[j + 1], Vs[j], self.dt, +1, p.order) for j in range(p.nt)]
+        Db = [SL.departure_offsets_ns(Vs[j], Vs[j + 1], self.dt, -1, p.order) for j in range(p.nt)]
+        return Df, Db
+
+    def state_defstate(self, vs):
+        Df, _ = self._offsets_ns(vs)
+        us = [np.zeros_like(vs[0])]
+        for j in range(self.p.nt):
+            us.append(SL.heun_source_step(us[-1], Df[j], vs[j], vs[j + 1], self.dt, self.p.order))
+        return us
+
+    def state_image(self, vs):
+        Df, _ = self._offsets_ns(vs)
+        ms = [self.I0.copy()]
+        for j in range(self.p.nt):
+            ms.append(SL.transport_step(ms[-1], Df[j], self.p.order))
+        return ms
+
+    def inverse_maps(self, vs):
+        _, Db = self._offsets_ns(vs)
+        ds = [div(v) for v in vs]
+        nus, Us = [None] * (self.p.nt + 1), [None] * (self.p.nt + 1)
+        nus[-1], Us[-1] = np.zeros_like(vs[0]), np.zeros(self.shape)
+        for j in range(self.p.nt - 1, -1, -1):
+            nus[j] = SL.heun_source_step(nus[j + 1], Db[j], -vs[j + 1], -vs[j], self.dt, self.p.order)
+            Us[j] = SL.heun_jacobian_step_ns(Us[j + 1], Db[j], ds[j + 1], ds[j], self.dt, self.p.order)
+        return nus, Us
+
+    def _backward_ns(self, f_end, vs):
+        _, Db = self._offsets_ns(vs)
+        ds = [div(v) for v in vs]
+        fs = [None] * (self.p.nt + 1)
+        fs[-1] = f_end
+        for j in range(self.p.nt - 1, -1, -1):
+            fs[j] = SL.heun_divergence_step_ns(fs[j + 1], Db[j], ds[j + 1], ds[j], self.dt, self.p.order)
+        return fs
+
+    def _node_image(self, base, lams, gms):
+        return np.stack([apply_L(b, self.p.alpha, self.p.s) + lam[None] * gm
+                         for b, lam, gm in zip(base, lams, gms)])
+
+    def _node_defstate(self, base, rhos, us):
+        return np.stack([apply_L(b, self.p.alpha, self.p.s) + rho
+                         - np.einsum("abzyx,azyx->bzyx", jacobian(u), rho)
+                         for b, rho, u in zip(base, rhos, us)])
+
+    def gradient(self, vs):
+        p = self.p
+        if p.variant == IMAGE:
+            ms = self.state_image(vs)
+            m1 = ms[-1]
+            lams = self._backward_ns(-(2.0 / p.sigma2) * (m1 - self.I1), vs)
+            g = self._node_image(vs, lams, [grad(m) for m in ms])
+        elif p.variant == STATE:
+            us = self.state_defstate(vs)
+            m1, _ = self._warp_I0(us[-1])
+            ms = [I.interpolate(self.I0, -u * self.tv, p.order) for u in us]
+            nus, Us = self.inverse_maps(vs)
+            lams = self._pull_back(-(2.0 / p.sigma2) * (m1 - self.I1), nus, Us)
+            g = self._node_image(vs, lams, [grad(m) for m in ms])
+        else:
+            us = self.state_defstate(vs)
+            m1, G = self._warp_I0(us[-1])
+            rhos = self._backward_ns(-(2.0 / p.sigma2) * (m1 - self.I1)[None] * G, vs)
+            g = self._node_defstate(vs, rhos, us)
+        er, ed = self.energy_reg(vs), self.energy_data(m1)
+        return er + ed, er, ed, g
+
+    def hessian_matvec(self, vs, dvs):
+        p = self.p
+        Df, _ = self._offsets_ns(vs)
+        if p.variant == IMAGE:
+            ms = self.state_image(vs)
+            gms = [grad(m) for m in ms]
+            F = [-np.sum(gm * dv, axis=0) for gm, dv in zip(gms, dvs)]
+            dm = np.zeros(self.shape)
+            for j in range(p.nt):
+                dm = SL.heun_source_step(dm, Df[j], F[j], F[j + 1], self.dt, p.order)
+            return self._node_image(dvs, self._backward_ns(-(2.0 / p.sigma2) * dm, vs), gms)
+        us = self.state_defstate(vs)
+        _, G = self._warp_I0(us[-1])
+        F = [dv - np.einsum("abzyx,bzyx->azyx", jacobian(u), dv) for u, dv in zip(us, dvs)]
+        du = np.zeros_like(vs[0])
+        for j in range(p.nt):
+            du = SL.heun_source_step(du, Df[j], F[j], F[j + 1], self.dt, p.order)
+        dm1 = -np.sum(G * du, axis=0)
+        if p.variant == STATE:
+            ms = [I.interpolate(self.I0, -u * self.tv, p.order) for u in us]
+            nus, Us = self.inverse_maps(vs)
+            dlams = self._pull_back(-(2.0 / p.sigma2) * dm1, nus, Us)
+            return self._node_image(dvs, dlams, [grad(m) for m in ms])
+        drhos = self._backward_ns(-(2.0 / p.sigma2) * dm1[None] * G, vs)
+        return self._node_defstate(dvs, drhos, us)

@@ -64,7 +64,7 @@ struct lddmm_ctx {
     void* Du16 = nullptr;   // the same, LDDMM_PREC_BF16X3_JBF16: BF16 copy read by the Hessian
     float* ms = nullptr;    // IMAGE: m_j, (nt+1) planes
     float* Gm = nullptr;    // IMAGE, STATE: iota(grad~ pi(m_j)), (nt+1) x 3 planes
-    float* Wb = nullptr;    // STATE: source of the nu~ step, -dt/2 (v(X+) + v(x)), 3 planes
+    float* Wb = nullptr;    // STATE: source of the nu~ step, -dt/2 (v(X+) + v(x)), 3 planes per step
     float* PJ = nullptr;    // STATE: per node iota(nu~_j) (3 planes, physical) and J_j (1 plane)
     // spatial form: full-grid FFT plans (the "cubes" of this context are fields on the grid)
     SpatialFFT* fft = nullptr;
@@ -132,10 +132,6 @@ static int validate(const lddmm_params* p) {
         set_error("the spatial form needs an even nx");
         return LDDMM_EINVAL;
     }
-    if (p->spatial && p->nonstationary) {
-        set_error("the non-stationary form is implemented for band-limited velocities");
-        return LDDMM_EINVAL;
-    }
     if (!p->spatial &&
         (p->K < 4 || (p->K & 1) || p->K > 64 || p->K > p->nx || p->K > p->ny || p->K > p->nz)) {
         set_error("band K must be even, 4 <= K <= min(64, nx, ny, nz)");
@@ -151,10 +147,7 @@ static int validate(const lddmm_params* p) {
         set_error("nonstationary must be 0 or 1");
         return LDDMM_EINVAL;
     }
-    if (p->nonstationary && p->variant != LDDMM_V_DEFSTATE) {
-        set_error("the non-stationary form is implemented for the deformation-state variant");
-        return LDDMM_EINVAL;
-    }
+
     if (p->interp != LDDMM_INTERP_LINEAR && p->interp != LDDMM_INTERP_CUBIC) {
         set_error("interp must be LDDMM_INTERP_LINEAR or LDDMM_INTERP_CUBIC");
         return LDDMM_EINVAL;
@@ -264,6 +257,7 @@ static float* dcnode(lddmm_ctx* c, int j) { return c->dc + node_off(c, j, 1); }
 static float* Dfstep(lddmm_ctx* c, int j) { return c->Df + node_off(c, j, 3); }
 static float* Dbstep(lddmm_ctx* c, int j) { return c->Db + node_off(c, j, 3); }
 static float* Wstep(lddmm_ctx* c, int j) { return c->W + node_off(c, j, 3); }
+static float* Wbstep(lddmm_ctx* c, int j) { return c->Wb + node_off(c, j, 3); }
 static float* gamstep(lddmm_ctx* c, int j) { return c->gam + node_off(c, j, 1); }
 // cube j of a velocity-shaped vector (node j; the one cube when stationary)
 static const float2* vcube(const lddmm_ctx* c, const float2* vt, int j) {
@@ -319,9 +313,9 @@ static int prepare_velocity(lddmm_ctx* c, const float2* vt) {
         // W = dt/2 (v_a(X) + v_b(x))
         if (has_u(c))
             TRY(sl_prep_source(c->sl, vsrc_a, vnode(c, b), Dfstep(c, j), c->dt, Wstep(c, j), c->st));
-        // STATE (stationary): Wb = -dt/2 (v(X+) + v(x)), the source of the nu~ step
+        // STATE: Wb = -dt/2 (v_b(X+) + v_a(x)), the source of the nu~ step
         if (state_eq(c))
-            TRY(sl_prep_source(c->sl, vsrc_b, vnode(c, a), Dbstep(c, j), -c->dt, c->Wb, c->st));
+            TRY(sl_prep_source(c->sl, vsrc_b, vnode(c, a), Dbstep(c, j), -c->dt, Wbstep(c, j), c->st));
     }
     return LDDMM_OK;
 }
@@ -350,7 +344,7 @@ static int state_image(lddmm_ctx* c) {
             TRY(bspline_prefilter(c->g, src, 1, c->fa, c->st));
             src = c->fa;
         }
-        TRY(sl_gather(c->sl, src, c->Df, 1, c->ms + (j + 1) * n, c->st));
+        TRY(sl_gather(c->sl, src, Dfstep(c, j), 1, c->ms + (j + 1) * n, c->st));
     }
     c->solves++;
     return LDDMM_OK;
@@ -430,8 +424,8 @@ static int state_traj(lddmm_ctx* c) {
             src_nu = c->fa;
             src_J = c->fd;
         }
-        TRY(sl_gather_add(c->sl, src_nu, c->Db, c->Wb, 3, c->fb, c->st));
-        TRY(sl_gather_scale(c->sl, src_J, c->Db, c->gam, 1, c->fc, c->st));
+        TRY(sl_gather_add(c->sl, src_nu, Dbstep(c, j), Wbstep(c, j), 3, c->fb, c->st));
+        TRY(sl_gather_scale(c->sl, src_J, Dbstep(c, j), gamstep(c, j), 1, c->fc, c->st));
         TRY(project(c, c->fb, 3, nut));
         TRY(project(c, c->fc, 1, Jt));
         pj = c->PJ + (long)j * 4 * n;
@@ -530,6 +524,25 @@ static int adjoint_defstate_ns(lddmm_ctx* c, const float* rho1, const float2* ba
     return LDDMM_OK;
 }
 
+// Image-type assembly (IMAGE and STATE, Eqs. 15-16): node j contributes pi(s_j Gm_j), s_j the
+// values of a projected scalar. Stationary: acc (+)= w_j s_j Gm_j over the nodes and, at the end,
+// out = L~ base + pi(acc). Non-stationary: out_j = L~ base_j + pi(s_j Gm_j) at every node.
+static int image_term(lddmm_ctx* c, int j, const float* vals, const float2* base, float2* out,
+                      bool first) {
+    const float* gm = c->Gm + (long)j * 3 * c->n;
+    if (!ns(c)) return accum_sv(c->g, vals, gm, (float)trap_w(c, j), c->acc, first, c->st);
+    TRY(accum_sv(c->g, vals, gm, 1.f, c->acc, 1, c->st));
+    float2* pacc = c->cv[lddmm_ctx::C_T0];
+    TRY(project(c, c->acc, 3, pacc));
+    return op_L(c, vcube(c, out, j), vcube(c, base, j), 1.f, 1.f, pacc, 3, 1);
+}
+static int image_finish(lddmm_ctx* c, const float2* base, float2* out) {
+    if (ns(c)) return LDDMM_OK;
+    float2* pacc = c->cv[lddmm_ctx::C_T0];
+    TRY(project(c, c->acc, 3, pacc));
+    return op_L(c, out, base, 1.f, 1.f, pacc, 3, 1);
+}
+
 // STATE, gradient and Hessian (Eqs. 15-16 with lambda(t) = J(t) lambda(1) o psi(t)):
 // out = L~ base + sum_j w_j pi(iota(pi(f_j)) Gm_j), f_j = J_j f1 o psi_j, with f1 = lambda(1) for the
 // gradient and dlambda(1) for the Gauss-Newton Hessian. No recurrence: every node reads f1.
@@ -547,14 +560,10 @@ static int pullback_assemble(lddmm_ctx* c, const float* f1, const float2* base, 
         TRY(sl_compose(c->sl, src, pj, c->to_vox, pj + 3 * n, c->fd, c->st));
         TRY(project(c, c->fd, 1, lt));
         TRY(include(c, lt, 1, c->fc, n, -1, 0));
-        TRY(accum_sv(c->g, c->fc, c->Gm + (long)j * 3 * n, (float)trap_w(c, j), c->acc, j == nt,
-                     c->st));
+        TRY(image_term(c, j, c->fc, base, out, j == nt));
     }
     c->solves++;
-    float2* pacc = c->cv[lddmm_ctx::C_T0];
-    TRY(project(c, c->acc, 3, pacc));
-    TRY(op_L(c, out, base, 1.f, 1.f, pacc, 3, 1));
-    return LDDMM_OK;
+    return image_finish(c, base, out);
 }
 
 // IMAGE, gradient (Eqs. 15, 18; Table 1 row 2): spatial adjoint lambda from
@@ -568,23 +577,20 @@ static int gradient_image_adjoint(lddmm_ctx* c, const float2* vt, float2* g) {
         // fb holds lambda_j (spatial)
         TRY(project(c, c->fb, 1, lt));
         TRY(include(c, lt, 1, c->fc, n, -1, 0));
-        TRY(accum_sv(c->g, c->fc, c->Gm + (long)j * 3 * n, (float)trap_w(c, j), c->acc, j == nt,
-                     c->st));
+        TRY(image_term(c, j, c->fc, vt, g, j == nt));
         if (j > 0) {
             const float* src = c->fb;
             if (cubic(c)) {
                 TRY(bspline_prefilter(c->g, c->fb, 1, c->fa, c->st));
                 src = c->fa;
             }
-            TRY(sl_gather_scale(c->sl, src, c->Db, c->gam, 1, c->fd, c->st));
+            // step j - 1 runs between nodes j - 1 and j
+            TRY(sl_gather_scale(c->sl, src, Dbstep(c, j - 1), gamstep(c, j - 1), 1, c->fd, c->st));
             std::swap(c->fb, c->fd);
         }
     }
     c->solves++;
-    float2* pacc = c->cv[lddmm_ctx::C_T0];
-    TRY(project(c, c->acc, 3, pacc));
-    TRY(op_L(c, g, vt, 1.f, 1.f, pacc, 3, 1));
-    return LDDMM_OK;
+    return image_finish(c, vt, g);
 }
 
 // ------------------------------------------------------------------ objective / gradient
@@ -681,8 +687,10 @@ static int hessian_impl(lddmm_ctx* c, const float2* dvt, float2* out) {
             TRY(bspline_prefilter(c->g, Fold, 1, c->acc, c->st));
             Fsrc = c->acc;
         }
-        TRY(sl_inc_image(c->sl, c->fb, c->Df, Fsrc, c->Gm + (long)(j + 1) * 3 * n, c->dvsp, c->dt,
-                         c->fc, Fnew, c->st));
+        // non-stationary: the right-hand side at node j + 1 uses dv~_{j+1}
+        if (ns(c)) TRY(include(c, vcube(c, dvt, j + 1), 3, c->dvsp, n, -1, 0));
+        TRY(sl_inc_image(c->sl, c->fb, Dfstep(c, j), Fsrc, c->Gm + (long)(j + 1) * 3 * n, c->dvsp,
+                         c->dt, c->fc, Fnew, c->st));
         TRY(project(c, c->fc, 1, dmt));
         std::swap(Fold, Fnew);
     }
@@ -691,23 +699,19 @@ static int hessian_impl(lddmm_ctx* c, const float2* dvt, float2* out) {
     TRY(cube_axpby(dmt, (float)(-2.0 / c->p.sigma2), dmt, 0.f, nullptr, c->kc, c->st));
     for (int j = nt; j >= 0; --j) {
         TRY(include(c, dmt, 1, c->fc, n, -1, 0));
-        TRY(accum_sv(c->g, c->fc, c->Gm + (long)j * 3 * n, (float)trap_w(c, j), c->acc, j == nt,
-                     c->st));
+        TRY(image_term(c, j, c->fc, dvt, out, j == nt));
         if (j > 0) {
             const float* src = c->fc;
             if (cubic(c)) {
                 TRY(include(c, dmt, 1, c->fa, n, -1, 1));
                 src = c->fa;
             }
-            TRY(sl_gather_scale(c->sl, src, c->Db, c->gam, 1, c->fd, c->st));
+            TRY(sl_gather_scale(c->sl, src, Dbstep(c, j - 1), gamstep(c, j - 1), 1, c->fd, c->st));
             TRY(project(c, c->fd, 1, dmt));
         }
     }
     c->solves++;
-    float2* pacc = c->cv[lddmm_ctx::C_T0];
-    TRY(project(c, c->acc, 3, pacc));
-    TRY(op_L(c, out, dvt, 1.f, 1.f, pacc, 3, 1));
-    return LDDMM_OK;
+    return image_finish(c, dvt, out);
 }
 
 // device comparison of vt against the cached velocity: true if bitwise equal
@@ -966,7 +970,7 @@ static int ctx_alloc(lddmm_ctx* c) {
     }
     if (!def || state_eq(c)) TRY(dalloc_t(c, &c->Gm, (size_t)(nt + 1) * 3 * n));
     if (state_eq(c)) {
-        TRY(dalloc_t(c, &c->Wb, 3 * n));
+        TRY(dalloc_t(c, &c->Wb, steps * 3 * n));
         TRY(dalloc_t(c, &c->PJ, (size_t)(nt + 1) * 4 * n));
     }
     for (float** f : {&c->fa, &c->fb, &c->fc, &c->fd, &c->acc, &c->dvsp}) TRY(dalloc_t(c, f, 3 * n));

@@ -89,7 +89,7 @@ def test_net_calls_reject_null_network():
 
 def test_nonstationary_flag_is_validated_before_any_device_work():
     lib = L.load()
-    for variant, flag in ((L.V_IMAGE, 1), (L.V_STATE, 1), (L.V_DEFSTATE, 2)):
+    for variant, flag in ((L.V_IMAGE, 2), (L.V_STATE, -1), (L.V_DEFSTATE, 2)):
         p = L.Params(32, 32, 32, 16, 10, variant, L.INTERP_LINEAR, 0.0025, 2, 0.01, 5, 10,
                      1e-3, L.PREC_FP32, flag)
         h = ctypes.c_void_p(123)
@@ -99,7 +99,7 @@ def test_nonstationary_flag_is_validated_before_any_device_work():
 
 def test_spatial_flag_is_validated_before_any_device_work():
     lib = L.load()
-    for nx, spatial, nonst in ((32, 2, 0), (33, 1, 0), (32, 1, 1)):
+    for nx, spatial, nonst in ((32, 2, 0), (33, 1, 0), (32, -1, 1)):
         p = L.Params(nx, 32, 32, 16, 10, L.V_DEFSTATE, L.INTERP_LINEAR, 0.0025, 2, 0.01, 5, 10,
                      1e-3, L.PREC_FP32, nonst, spatial)
         h = ctypes.c_void_p(123)

@@ -123,3 +123,29 @@ def test_full_size_zero_velocity_gradient_sampled():
         ref = np.array([r * gx, r * gy, r * gz])
         assert np.abs(g[:, z, y, x] - ref).max() <= 1e-4 * (np.abs(ref).max() + 1.0)
     assert rep["gn_iters"] == 2 and rep["E"] < 0.9 * rep["E0"]
+
+
+@pytest.mark.parametrize("variant,order", [(Vn.DEFSTATE, 1), (Vn.IMAGE, 3), (Vn.STATE, 1)])
+def test_nonstationary_spatial_form_matches_oracle(variant, order):
+    """One field per node (lddmm_params.spatial = nonstationary = 1) against SpatialProblemNS:
+    energy, node gradients and Hessian-vector products, then a short registration."""
+    shape, nt = (16, 16, 16), 4
+    I0, I1 = blob_pair(shape, 8, seed=0, order=order)
+    p = Vn.Params(K=0, nt=nt, order=order, variant=variant, sigma2=0.01)
+    prob = Sp.SpatialProblemNS(I0, I1, p)
+    base = field(shape, 3, 1.0)
+    base *= 2.0 / np.abs(base * prob.tv).max()
+    vs = np.stack([base * (0.5 + 0.1 * j) for j in range(nt + 1)])
+    dvs = np.stack([field(shape, 20 + j, 0.1) for j in range(nt + 1)])
+    E, Er, Ed, g = prob.gradient(vs)
+    H = prob.hessian_matvec(vs, dvs)
+    with gpu_context(prob, nonstationary=True, max_gn=3, max_pcg=5) as ctx:
+        (Eg, Erg, _), gg = ctx.gradient(dev(vs))
+        assert Eg == pytest.approx(E, rel=1e-5) and Erg == pytest.approx(Er, rel=1e-5)
+        assert rel_l2(host(gg), g) < 1e-4
+        assert rel_l2(host(ctx.hessian_matvec(dev(vs), dev(dvs))), H) < 1e-4
+        v, rep = ctx.register()
+    v_o, rep_o = gnk.register(prob, max_gn=3, max_pcg=5)
+    assert v.shape == (nt + 1, 3) + shape
+    assert rep["gn_iters"] == rep_o.gn_iters and rep["pcg_iters_total"] == rep_o.pcg_iters_total
+    assert rep["E"] == pytest.approx(rep_o.E, rel=1e-3)

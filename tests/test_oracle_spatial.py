@@ -176,3 +176,36 @@ def test_pulled_back_adjoint_matches_the_transported_adjoint(order, tol):
     for j in range(prob.p.nt + 1):
         err = np.linalg.norm(pulled[j] - ref[j]) / np.linalg.norm(lam1)
         assert err < tol, (j, err)
+
+
+def _ns_problems(variant, order, nt=4):
+    prob, v = _problem(variant, order, nt=nt)
+    return prob, Sp.SpatialProblemNS(prob.I0, prob.I1, prob.p), v
+
+
+@pytest.mark.parametrize("variant", [Vn.IMAGE, Vn.STATE, Vn.DEFSTATE])
+def test_nonstationary_equal_nodes_reduce_to_the_stationary_problem(variant):
+    st, ns, v = _ns_problems(variant, 3)
+    v = v * 0.3
+    vs = np.stack([v] * (ns.p.nt + 1))
+    E, Er, Ed, g = st.gradient(v)
+    En, Ern, Edn, gn = ns.gradient(vs)
+    assert En == pytest.approx(E, rel=1e-12) and Ern == pytest.approx(Er, rel=1e-12)
+    np.testing.assert_allclose(sum(w * gj for w, gj in zip(ns.tw, gn)), g, atol=1e-12 * np.abs(g).max())
+    dv = _rand_field(4)
+    H = st.hessian_matvec(v, dv)
+    Hn = ns.hessian_matvec(vs, np.stack([dv] * (ns.p.nt + 1)))
+    np.testing.assert_allclose(sum(w * hj for w, hj in zip(ns.tw, Hn)), H, atol=1e-12 * np.abs(H).max())
+
+
+@pytest.mark.parametrize("variant", [Vn.IMAGE, Vn.STATE, Vn.DEFSTATE])
+def test_nonstationary_gradient_matches_central_differences(variant):
+    _, ns, v = _ns_problems(variant, 3)
+    vs = np.stack([v * (0.2 + 0.05 * j) for j in range(ns.p.nt + 1)])
+    g = ns.gradient(vs)[3]
+    h = 1e-3
+    for seed in (5, 6):
+        e = np.stack([_rand_field(seed + 10 * j) for j in range(ns.p.nt + 1)])
+        fd = (ns.objective(vs + h * e)[0] - ns.objective(vs - h * e)[0]) / (2 * h)
+        scale = np.sqrt(ns.inner(g, g) * ns.inner(e, e))
+        assert abs(fd - ns.inner(g, e)) <= 3e-3 * scale, (fd, ns.inner(g, e), scale)
