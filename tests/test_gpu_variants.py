@@ -218,11 +218,12 @@ def test_jacobian_determinant_needs_the_deformation_state():
             ctx.jacobian_det(ctx.zeros_cube())
 
 
-@pytest.mark.parametrize("variant", [Vn.DEFSTATE, Vn.IMAGE])
-def test_z_pipelined_kernels_give_identical_results(variant):
+@pytest.mark.parametrize("variant,order", [(Vn.DEFSTATE, 1), (Vn.IMAGE, 1), (Vn.DEFSTATE, 3),
+                                           (Vn.STATE, 3)])
+def test_z_pipelined_kernels_give_identical_results(variant, order):
     """LDDMM_OPT_GATHER_ZT only changes how many z planes a thread walks (ragged last block
     here: nz = 37): gradients and Hessian-vector products are bitwise equal for every depth."""
-    prob = oracle_problem((37, 20, 32), 16, variant, 1, nt=4)
+    prob = oracle_problem((37, 20, 32), 16, variant, order, nt=4)
     vt = devc(synth.random_velocity_coeffs(16, 16, seed=3) * 0.5)
     dv = devc(synth.random_coeffs(16, seed=4) * 0.1)
     out = []
