@@ -214,8 +214,6 @@ struct Interp<3> {
     const long n = g.ntot();                                    \
     const int i = (z * g.ny + y) * g.nx + x;
 
-static inline dim3 vox_grid(const Grid& g) { return dim3(cdiv(g.nx, 32), cdiv(g.ny, 8), g.nz); }
-static const dim3 kVoxBlock(32, 8, 1);
 // launch shape of a voxel kernel for SLArgs (autotuned block, 256 threads)
 #define VOX_LAUNCH(a) dim3(cdiv((a).g.nx, (a).bx), cdiv((a).g.ny, (a).by), (a).g.nz), dim3((a).bx, (a).by, 1)
 
