@@ -324,6 +324,55 @@ k_sl_gather_zt(Grid g, const float* __restrict__ src, const float* __restrict__ 
     }
 }
 
+// The same for NC single fields (NC = 1: the cubic scalar gathers).
+template <int IP, int MODE, int NC>
+__global__ void __launch_bounds__(256, IP == 3 ? 2 : 5)
+k_sl_gather_zt1(Grid g, const float* __restrict__ src, const float* __restrict__ D,
+               const float* __restrict__ aux, float* __restrict__ out, int zt) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= g.nx || y >= g.ny) return;
+    const int n = (int)g.ntot();             // 3 n < 2^31 (checked at context creation)
+    const int plane = g.nx * g.ny;
+    int z = blockIdx.z * zt;
+    const int zend = min(z + zt, g.nz);
+    if (z >= zend) return;
+    int i = (z * g.ny + y) * g.nx + x;
+    float d0 = __ldcs(D + i), d1 = __ldcs(D + n + i), d2 = __ldcs(D + 2 * n + i);
+    float a[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+        a[c] = MODE == 1 ? (c == 0 ? __ldcs(aux + i) : 0.f) : MODE == 2 ? __ldcs(aux + c * n + i) : 0.f;
+    for (;;) {
+        const bool more = z + 1 < zend;
+        const int ip = more ? i + plane : i;
+        // next plane's streams, issued before this plane's taps are consumed
+        const float e0 = __ldcs(D + ip), e1 = __ldcs(D + n + ip), e2 = __ldcs(D + 2 * n + ip);
+        float b[NC];
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+            b[c] = MODE == 1 ? (c == 0 ? __ldcs(aux + ip) : 0.f) : MODE == 2 ? __ldcs(aux + c * n + ip) : 0.f;
+        float v[NC];
+        {
+            const Interp<IP> it(g, x, y, z, d0, d1, d2);
+#pragma unroll
+            for (int c = 0; c < NC; ++c) v[c] = it(src + c * n);
+        }
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            if (MODE == 1) v[c] *= a[0];
+            if (MODE == 2) v[c] += a[c];
+            __stcs(out + c * n + i, v[c]);
+        }
+        if (!more) break;
+        ++z;
+        i = ip;
+        d0 = e0; d1 = e1; d2 = e2;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) a[c] = b[c];
+    }
+}
+
 // Trilinear gather, four consecutive x voxels per thread (nx % 4 == 0): float4 offset loads
 // and stores, 4 x 8 independent gathers per component in flight.
 template <int MODE, int NC>
@@ -395,12 +444,17 @@ static void launch_gather_nc(const SLArgs& a, const float* src, const float* D, 
             const int zt = zt_of(a);
             if (zt > 1)
                 k_sl_gather_zt<IP, MODE><<<dim3(cdiv(a.g.nx, a.bx), cdiv(a.g.ny, a.by), cdiv(a.g.nz, zt)),
-                                           dim3(a.bx, a.by, 1), 0, st>>>(a.g, s, D, x, o, zt);
+                                            dim3(a.bx, a.by, 1), 0, st>>>(a.g, s, D, x, o, zt);
             else
                 k_sl_gather<IP, MODE, 3><<<VOX_LAUNCH(a), 0, st>>>(a.g, s, D, x, o);
             c0 += 3;
         } else {
-            k_sl_gather<IP, MODE, 1><<<VOX_LAUNCH(a), 0, st>>>(a.g, s, D, x, o);
+            const int zt = zt_of(a);
+            if (IP == 3 && zt > 1)   // (trilinear single fields take the four-voxel kernel)
+                k_sl_gather_zt1<IP, MODE, 1><<<dim3(cdiv(a.g.nx, a.bx), cdiv(a.g.ny, a.by), cdiv(a.g.nz, zt)),
+                                               dim3(a.bx, a.by, 1), 0, st>>>(a.g, s, D, x, o, zt);
+            else
+                k_sl_gather<IP, MODE, 1><<<VOX_LAUNCH(a), 0, st>>>(a.g, s, D, x, o);
             c0 += 1;
         }
     }

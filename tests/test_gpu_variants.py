@@ -219,7 +219,7 @@ def test_jacobian_determinant_needs_the_deformation_state():
 
 
 @pytest.mark.parametrize("variant,order", [(Vn.DEFSTATE, 1), (Vn.IMAGE, 1), (Vn.DEFSTATE, 3),
-                                           (Vn.STATE, 3)])
+                                           (Vn.STATE, 3), (Vn.IMAGE, 3)])
 def test_z_pipelined_kernels_give_identical_results(variant, order):
     """LDDMM_OPT_GATHER_ZT only changes how many z planes a thread walks (ragged last block
     here: nz = 37): gradients and Hessian-vector products are bitwise equal for every depth."""
