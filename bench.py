@@ -25,6 +25,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import threading
 import time
 
@@ -524,8 +525,8 @@ def run_batch(args):
     torch.cuda.synchronize()
     streams = [torch.cuda.Stream() for _ in pairs]
     ctxs = []
-    tune = os.path.join(ROOT, "gpurun_out", "autotune.json") if os.path.isdir(
-        os.path.join(ROOT, "gpurun_out")) else None
+    # the autotuner's cache of block shapes per grid (a scratch file outside the repository)
+    tune = os.path.join(tempfile.gettempdir(), "lddmm_autotune.json")
     for (shape, K, I0, I1), st in zip(pairs, streams):
         nz, ny, nx = shape
         with torch.cuda.stream(st):

@@ -149,7 +149,7 @@ int lddmm_hessian_matvec(lddmm_ctx* ctx, const float* v, const float* dv, float*
  * initial velocity (zeros for a cold start) and receives the result; PCG with
  * preconditioner L~^{-1}, Armijo update length, stop on grad ratio or max_gn.
  * g_ref_norms (host, may be NULL): {||g(0)||_2, ||g(0)||_inf} of the cold start, so that a
- * warm start is judged against the cold-start reference; NULL computes them here.
+ * warm start is measured against the cold-start reference; NULL computes them here.
  * *report (host) receives the outcome. Synchronises. */
 int lddmm_register(lddmm_ctx* ctx, float* v_inout, const double* g_ref_norms,
                    lddmm_report* report);
@@ -251,7 +251,7 @@ int lddmm_sl_transport(int nx, int ny, int nz, int nt, int interp, const float* 
 /* No counterpart in the paper (its solver always starts from v = 0). A 3-D convolutional
  * encoder-decoder maps the image pair, band-limited and resampled to D^3, to a velocity on
  * the (D/2)^3 grid; its band-limited projection is an initial velocity for lddmm_register,
- * which then finishes the registration and judges the prediction by its own residual.
+ * which then finishes the registration and measures the prediction by its own residual.
  * Architecture (base c channels): D^3: conv 2->c, c->c; pool; (D/2)^3: c->2c, 2c->2c;
  * pool; (D/4)^3: 2c->4c, 4c->4c; pool; (D/8)^3: 4c->8c, 8c->8c; upsample; (D/4)^3:
  * [8c up | 4c skip] -> 4c, 4c->4c; upsample; (D/2)^3: [4c up | 2c skip] -> 2c, 2c->2c,

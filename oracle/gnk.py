@@ -14,7 +14,7 @@ Readings (the stopping rules of the cited work are not written out in the paper)
   * Update length eps: Armijo backtracking from eps = 1, halving up to 10 times, accepting
     E(v + eps dv) <= E(v) + 1e-4 eps <g, dv>; no acceptable eps stops with LINESEARCH.
   * Stop when ||g_n||_2 / ||g_ref||_2 <= gtol, g_ref the gradient at v~ = 0 (the cold-start
-    gradient, so warm starts are judged against the same reference), or after max_gn
+    gradient, so warm starts are measured against the same reference), or after max_gn
     updates.
 """
 from __future__ import annotations

@@ -2,7 +2,7 @@
 // (template, reference) pair, band-limited and resampled to D^3 (D = 64), to a velocity on
 // the (D/2)^3 grid, whose exact band-limited projection is the solver's initial velocity.
 // The paper has no learned component; the Gauss-Newton-Krylov solver always finishes the
-// registration and judges the prediction by its own residual.
+// registration and measures the prediction by its own residual.
 //
 // Layers (base c channels): D^3: conv 2->c, c->c; pool; (D/2)^3: c->2c, 2c->2c; pool;
 // (D/4)^3: 2c->4c, 4c->4c; pool; (D/8)^3: 4c->8c, 8c->8c; up; (D/4)^3: [8c up | 4c skip]
