@@ -217,6 +217,16 @@ struct Interp<3> {
 // launch shape of a voxel kernel for SLArgs (autotuned block, 256 threads)
 #define VOX_LAUNCH(a) dim3(cdiv((a).g.nx, (a).bx), cdiv((a).g.ny, (a).by), (a).g.nz), dim3((a).bx, (a).by, 1)
 
+// z planes per thread of the pipelined 3-component kernels: the set value, or (0) the largest
+// of 4, 2 that still leaves about two waves of 256-thread blocks on 148 SMs at five per SM.
+static int zt_of(const SLArgs& a) {
+    if (a.zt > 0) return a.zt;
+    const long tiles = (long)cdiv(a.g.nx, a.bx) * cdiv(a.g.ny, a.by);
+    for (int zt : {4, 2})
+        if (tiles * cdiv(a.g.nz, zt) >= 2L * 148 * 5) return zt;
+    return 1;
+}
+
 // ---------------------------------------------------------------- characteristics
 template <int IP>
 __global__ void __launch_bounds__(256, IP == 3 ? 2 : 3)
@@ -232,12 +242,49 @@ k_sl_char(Grid g, const float* __restrict__ vsrc, const float* __restrict__ vval
     D[2 * n + i] = h * (W2 + V2);
 }
 
+// The same over zt consecutive z planes per thread (trilinear): the velocity of plane z + 1
+// is loaded while the taps of plane z are in flight.
+__global__ void __launch_bounds__(256, 5)
+k_sl_char_zt(Grid g, const float* __restrict__ vsrc, const float* __restrict__ vval, float s0,
+             float s1, float s2, float dts, float* __restrict__ D, int zt) {
+    const int x = blockIdx.x * blockDim.x + threadIdx.x;
+    const int y = blockIdx.y * blockDim.y + threadIdx.y;
+    if (x >= g.nx || y >= g.ny) return;
+    const int n = (int)g.ntot();             // 3 n < 2^31 (checked at context creation)
+    const int plane = g.nx * g.ny;
+    int z = blockIdx.z * zt;
+    const int zend = min(z + zt, g.nz);
+    if (z >= zend) return;
+    int i = (z * g.ny + y) * g.nx + x;
+    float V0 = __ldcs(vval + i) * s0, V1 = __ldcs(vval + n + i) * s1, V2 = __ldcs(vval + 2 * n + i) * s2;
+    const float h = 0.5f * dts;
+    for (;;) {
+        const bool more = z + 1 < zend;
+        const int ip = more ? i + plane : i;
+        const float U0 = __ldcs(vval + ip) * s0, U1 = __ldcs(vval + n + ip) * s1,
+                    U2 = __ldcs(vval + 2 * n + ip) * s2;
+        const Interp<1> it(g, x, y, z, dts * V0, dts * V1, dts * V2);   // X* = x + dts V
+        const float W0 = it(vsrc) * s0, W1 = it(vsrc + n) * s1, W2 = it(vsrc + 2 * n) * s2;
+        __stcs(D + i, h * (W0 + V0));
+        __stcs(D + n + i, h * (W1 + V1));
+        __stcs(D + 2 * n + i, h * (W2 + V2));
+        if (!more) break;
+        ++z;
+        i = ip;
+        V0 = U0; V1 = U1; V2 = U2;
+    }
+}
+
 int sl_characteristics(const SLArgs& a, const float* vsrc, const float* vval, const float scale[3],
                        double dt_signed, float* D, cudaStream_t st) {
     KTRACE(a.interp == 3 ? "sl_char_cubic" : "sl_char", st, 36.0 * a.g.ntot(), 0);
     if (a.interp == 3)
         k_sl_char<3><<<VOX_LAUNCH(a), 0, st>>>(a.g, vsrc, vval, scale[0], scale[1],
                                                           scale[2], (float)dt_signed, D);
+    else if (zt_of(a) > 1)
+        k_sl_char_zt<<<dim3(cdiv(a.g.nx, a.bx), cdiv(a.g.ny, a.by), cdiv(a.g.nz, zt_of(a))),
+                       dim3(a.bx, a.by, 1), 0, st>>>(a.g, vsrc, vval, scale[0], scale[1], scale[2],
+                                                     (float)dt_signed, D, zt_of(a));
     else
         k_sl_char<1><<<VOX_LAUNCH(a), 0, st>>>(a.g, vsrc, vval, scale[0], scale[1],
                                                           scale[2], (float)dt_signed, D);
@@ -413,15 +460,6 @@ k_sl_gather4(Grid g, const float* __restrict__ src, const float* __restrict__ D,
 
 static inline bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
 
-// z planes per thread of the pipelined 3-component kernels: the set value, or (0) the largest
-// of 4, 2 that still leaves about two waves of 256-thread blocks on 148 SMs at five per SM.
-static int zt_of(const SLArgs& a) {
-    if (a.zt > 0) return a.zt;
-    const long tiles = (long)cdiv(a.g.nx, a.bx) * cdiv(a.g.ny, a.by);
-    for (int zt : {4, 2})
-        if (tiles * cdiv(a.g.nz, zt) >= 2L * 148 * 5) return zt;
-    return 1;
-}
 
 template <int IP, int MODE>
 static void launch_gather_nc(const SLArgs& a, const float* src, const float* D, const float* aux,
@@ -435,7 +473,13 @@ static void launch_gather_nc(const SLArgs& a, const float* src, const float* D, 
         const float* s = src + c0 * n;
         const float* x = MODE == 2 ? aux + c0 * n : aux;
         float* o = out + c0 * n;
-        if (vec4 && left < 3) {
+        if (IP == 1 && left < 3 && zt_of(a) > 1) {
+            // single fields on grids that fill the GPU: one voxel per thread, z-pipelined
+            const int zt = zt_of(a);
+            k_sl_gather_zt1<IP, MODE, 1><<<dim3(cdiv(a.g.nx, a.bx), cdiv(a.g.ny, a.by), cdiv(a.g.nz, zt)),
+                                           dim3(a.bx, a.by, 1), 0, st>>>(a.g, s, D, x, o, zt);
+            c0 += 1;
+        } else if (vec4 && left < 3) {
             // single fields: four voxels per thread (the 3-component form keeps one voxel per
             // thread, which holds more gathers in flight per register)
             k_sl_gather4<MODE, 1><<<g4, b4, 0, st>>>(a.g, s, D, x, o);
