@@ -19,7 +19,8 @@ torch = pytest.importorskip("torch")
 import paper_2006_06823_b300 as L  # noqa: E402
 
 CASES = [((16, 16, 16), 8), ((20, 24, 36), 10), ((18, 22, 37), 12), ((33, 40, 64), 32),
-         ((8, 8, 8), 4)]
+         ((8, 8, 8), 4),
+         ((64, 66, 64), 64)]   # the largest band the library accepts (K = 64)
 
 
 def dev(a):

@@ -47,11 +47,18 @@ CASES = [((16, 16, 16), 8, Vn.DEFSTATE, 1), ((16, 16, 16), 8, Vn.DEFSTATE, 3),
          ((20, 24, 28), 10, Vn.DEFSTATE, 1), ((20, 24, 28), 10, Vn.IMAGE, 1),
          # K = 16 with nx = 32: the x stages of pi and iota run on the tensor cores
          ((24, 20, 32), 16, Vn.DEFSTATE, 1), ((24, 20, 32), 16, Vn.DEFSTATE, 3),
-         ((24, 20, 32), 16, Vn.IMAGE, 3)]
+         ((24, 20, 32), 16, Vn.IMAGE, 3),
+         # the largest band a context accepts
+         ((64, 64, 64), 64, Vn.DEFSTATE, 1)]
 
 
 @pytest.mark.parametrize("shape,K,variant,order", CASES)
 def test_objective_gradient_hessian_match_oracle(shape, K, variant, order):
+    # K = 64 on a 64^3 grid keeps every mode below the Nyquist frequency: the FP32 rounding of
+    # the departure offsets then moves near-Nyquist content measurably (gradient error measured
+    # 1.1e-4 with the split-TF32 stages, 2.1e-5 with FP32 SIMT; 1.2e-5 at K = 32 on the same
+    # grid), so the full-band case gets a 3e-4 bound
+    tol = 3e-4 if K == min(shape) else 1e-4
     prob = oracle_problem(shape, K, variant, order, nt=5)
     vt = synth.random_velocity_coeffs(K, K, seed=3) * 0.5
     E, Er, Ed, g = prob.gradient(vt)
@@ -63,9 +70,9 @@ def test_objective_gradient_hessian_match_oracle(shape, K, variant, order):
         assert Erg == pytest.approx(Er, rel=1e-6)
         (E2, _, _), gg = ctx.gradient(devc(vt))
         assert E2 == pytest.approx(E, rel=1e-5)
-        assert rel_l2(host(gg), g) < 1e-4
+        assert rel_l2(host(gg), g) < tol
         Hg = ctx.hessian_matvec(devc(vt), devc(dv))
-        assert rel_l2(host(Hg), Hdv) < 1e-4
+        assert rel_l2(host(Hg), Hdv) < tol
 
 
 @pytest.mark.parametrize("shape,K,order", [((16, 16, 16), 8, 1), ((20, 24, 28), 10, 1),
