@@ -14,6 +14,8 @@ Modules
   spatial   the three variants in the spatial domain (Sec. 2.1, SL-RK in Omega): velocity on
             the grid, spectral derivatives and L by numpy's FFT, voxel-mean L2 product
   gnk       PCG with preconditioner L~^-1, Gauss-Newton update, line search (Sec. 2.1-2.2)
+  multilevel  two-level preconditioner (coarse half-grid Gauss-Newton solve on the low
+            modes, L~^-1 on the rest) and flexible PCG (Secs. 6-7 name it as future work)
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test against a closed
 form, an invariant, a library routine or brute force, except the full registration

@@ -16,6 +16,9 @@ Readings (the stopping rules of the cited work are not written out in the paper)
   * Stop when ||g_n||_2 / ||g_ref||_2 <= gtol, g_ref the gradient at v~ = 0 (the cold-start
     gradient, so warm starts are measured against the same reference), or after max_gn
     updates.
+  * ``two_level = m > 0`` replaces L~^{-1} by the two-level preconditioner of
+    ``oracle/multilevel.py`` (at most m coarse PCG iterations per application) and PCG by
+    flexible PCG; the coarse Hessian is re-taken at every Gauss-Newton iterate.
 """
 from __future__ import annotations
 
@@ -71,10 +74,11 @@ class Report:
     grad_rel_l2: float = 0.0
     grad_rel_inf: float = 0.0
     mse_rel: float = 0.0
+    pcg_inner_total: int = 0
     history: list = field(default_factory=list)
 
 
-def register(problem, v0=None, max_gn=5, max_pcg=10, gtol=1e-3, g_ref=None):
+def register(problem, v0=None, max_gn=5, max_pcg=10, gtol=1e-3, g_ref=None, two_level=0):
     """Gauss-Newton-Krylov registration from v0 (zero by default). Returns (v~, Report)."""
     p = problem.p
     K = p.K
@@ -86,6 +90,13 @@ def register(problem, v0=None, max_gn=5, max_pcg=10, gtol=1e-3, g_ref=None):
     else:
         v = np.zeros((3, K, K, K), dtype=np.complex128) if v0 is None else np.array(v0, np.complex128)
         prec = lambda c: S.apply_Linv(c, p.alpha, p.s)
+    solver = pcg
+    tl = None
+    if two_level > 0:
+        from . import multilevel as ML
+
+        tl = ML.TwoLevel(problem, ML.coarse_problem(problem), two_level)
+        prec, solver = tl, ML.fpcg
     if g_ref is None:
         g_ref = problem.gradient(np.zeros_like(v))[3] if v0 is not None else None
     rep = Report()
@@ -102,7 +113,9 @@ def register(problem, v0=None, max_gn=5, max_pcg=10, gtol=1e-3, g_ref=None):
             rep.stop_reason = STOP_GTOL
             break
         eta = min(0.5, np.sqrt(gn / gref_l2))
-        dv, its, _ = pcg(lambda c: problem.hessian_matvec(v, c), -g, prec, eta, max_pcg, inner)
+        if tl is not None:
+            tl.set_velocity(v)
+        dv, its, _ = solver(lambda c: problem.hessian_matvec(v, c), -g, prec, eta, max_pcg, inner)
         rep.pcg_iters_total += its
         slope = inner(g, dv)
         eps, accepted = 1.0, False
@@ -128,4 +141,6 @@ def register(problem, v0=None, max_gn=5, max_pcg=10, gtol=1e-3, g_ref=None):
     rep.grad_rel_l2 = gn / gref_l2
     rep.grad_rel_inf = np.abs(g).max() / gref_inf
     rep.mse_rel = problem.mse_rel(m1)
+    if tl is not None:
+        rep.pcg_inner_total = tl.inner_its
     return v, rep
