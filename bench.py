@@ -333,28 +333,32 @@ def run_b300(args):
 
 
 # name, variant, interpolation, precision, non-stationary, spatial domain
-FORMS = [("defstate/linear/bf16x3_jbf16", "V_DEFSTATE", "INTERP_LINEAR", "PREC_BF16X3_JBF16", False, False),
-         ("image/linear/fp32", "V_IMAGE", "INTERP_LINEAR", "PREC_FP32", False, False),
-         ("defstate/cubic/fp32", "V_DEFSTATE", "INTERP_CUBIC", "PREC_FP32", False, False),
-         ("image/cubic/fp32", "V_IMAGE", "INTERP_CUBIC", "PREC_FP32", False, False),
-         ("defstate/linear/fp32/nonstationary", "V_DEFSTATE", "INTERP_LINEAR", "PREC_FP32", True, False),
-         ("state/linear/fp32", "V_STATE", "INTERP_LINEAR", "PREC_FP32", False, False),
-         ("image/linear/fp32/nonstationary", "V_IMAGE", "INTERP_LINEAR", "PREC_FP32", True, False),
-         ("state/linear/fp32/nonstationary", "V_STATE", "INTERP_LINEAR", "PREC_FP32", True, False),
-         ("defstate/linear/fp32/spatial", "V_DEFSTATE", "INTERP_LINEAR", "PREC_FP32", False, True),
-         ("image/linear/fp32/spatial", "V_IMAGE", "INTERP_LINEAR", "PREC_FP32", False, True)]
+FORMS = [("defstate/linear/bf16x3_jbf16", "V_DEFSTATE", "INTERP_LINEAR", "PREC_BF16X3_JBF16", False, False, 0),
+         ("image/linear/fp32", "V_IMAGE", "INTERP_LINEAR", "PREC_FP32", False, False, 0),
+         ("defstate/cubic/fp32", "V_DEFSTATE", "INTERP_CUBIC", "PREC_FP32", False, False, 0),
+         ("image/cubic/fp32", "V_IMAGE", "INTERP_CUBIC", "PREC_FP32", False, False, 0),
+         ("defstate/linear/fp32/nonstationary", "V_DEFSTATE", "INTERP_LINEAR", "PREC_FP32", True, False, 0),
+         ("state/linear/fp32", "V_STATE", "INTERP_LINEAR", "PREC_FP32", False, False, 0),
+         ("image/linear/fp32/nonstationary", "V_IMAGE", "INTERP_LINEAR", "PREC_FP32", True, False, 0),
+         ("state/linear/fp32/nonstationary", "V_STATE", "INTERP_LINEAR", "PREC_FP32", True, False, 0),
+         ("defstate/linear/fp32/spatial", "V_DEFSTATE", "INTERP_LINEAR", "PREC_FP32", False, True, 0),
+         ("image/linear/fp32/spatial", "V_IMAGE", "INTERP_LINEAR", "PREC_FP32", False, True, 0),
+         # two-level preconditioner, at most 5 coarse PCG iterations per application
+         ("defstate/linear/fp32/two_level", "V_DEFSTATE", "INTERP_LINEAR", "PREC_FP32", False, False, 5)]
 
 
 def measure_forms(L, torch, I0d, I1d, stream, flush):
     """The bench pair in the other forms of the workload (variant x interpolation, the
-    mixed-precision form, the non-stationary velocity, the spatial domain): one untimed and
-    one event-timed registration each."""
+    mixed-precision form, the non-stationary velocity, the spatial domain, the two-level
+    preconditioner): one untimed and one event-timed registration each."""
     nz, ny, nx = SHAPE
     res = {}
-    for name, var, interp, prec, nonst, spatial in FORMS:
+    for name, var, interp, prec, nonst, spatial, two_level in FORMS:
         ctx = L.Context(nx, ny, nz, K, nt=NT, variant=getattr(L, var), interp=getattr(L, interp),
                         alpha=ALPHA, s=S_EXP, sigma2=SIGMA2, max_gn=MAX_GN, max_pcg=MAX_PCG,
                         gtol=GTOL, precision=getattr(L, prec), nonstationary=nonst, spatial=spatial)
+        if two_level:
+            ctx.set_option(L.OPT_TWO_LEVEL, two_level)
         ctx.set_images(I0d, I1d)
         ctx.register()
         flush.fill_(1.0)
@@ -367,6 +371,7 @@ def measure_forms(L, torch, I0d, I1d, stream, flush):
         ctx.close()
         res[name] = {"s_per_pair": e0.elapsed_time(e1) / 1e3, "gn_iters": rep["gn_iters"],
                      "pcg_iters": rep["pcg_iters_total"], "E": rep["E"],
+                     "coarse_pcg_iters": rep["pcg_inner_total"],
                      "grad_rel_l2": rep["grad_rel_l2"],
                      "residual_reached": rep["grad_rel_l2"] <= GTOL}
     return res

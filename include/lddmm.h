@@ -106,6 +106,8 @@ typedef struct {
     double grad_rel_inf;  /* ||g(v)||_inf / ||g(0)||_inf (Sec. 5.1.1) */
     double mse_rel;       /* ||m(1) - I1||^2 / ||I0 - I1||^2 (Sec. 5.1.1) */
     double seconds;       /* wall time inside the call */
+    int pcg_inner_total;  /* coarse-level Hessian-vector products of the two-level
+                             preconditioner (LDDMM_OPT_TWO_LEVEL; 0 without it) */
 } lddmm_report;
 
 typedef struct lddmm_ctx lddmm_ctx;
@@ -164,7 +166,8 @@ int lddmm_register(lddmm_ctx* ctx, float* v_inout, const double* g_ref_norms,
 int lddmm_register_batch(lddmm_ctx* const* ctxs, float* const* v_inout, int n,
                          const double* g_ref_norms, lddmm_report* reports, int max_threads);
 
-enum { LDDMM_OPT_GRAPHS = 1, LDDMM_OPT_BLOCK_X = 2, LDDMM_OPT_GATHER_ZT = 3 };
+enum { LDDMM_OPT_GRAPHS = 1, LDDMM_OPT_BLOCK_X = 2, LDDMM_OPT_GATHER_ZT = 3,
+       LDDMM_OPT_TWO_LEVEL = 4 };
 
 /* Context options: LDDMM_OPT_GRAPHS (0/1) captures the PCG Hessian-vector product into a
  * CUDA graph on its second use and replays it (lddmm_register); LDDMM_OPT_BLOCK_X sets the
@@ -173,7 +176,17 @@ enum { LDDMM_OPT_GRAPHS = 1, LDDMM_OPT_BLOCK_X = 2, LDDMM_OPT_GATHER_ZT = 3 };
  * 3-component trilinear gathers and incremental deformation-state steps handles (1: one voxel
  * per thread; more: the next plane's offsets are loaded while the current taps are in
  * flight; 0, the default: 4 or 2 when the grid still fills the GPU, else 1). Results do not
- * depend on it. EINVAL for other values. */
+ * depend on it. LDDMM_OPT_TWO_LEVEL (0..1000) replaces the preconditioner L~^{-1} of
+ * lddmm_register's PCG by a two-level one (the multi-level preconditioner Secs. 6-7 name as
+ * future work; value = the cap on its coarse PCG iterations per application, 0 = off): a
+ * coarse context on the half grid with band Kc = 2 floor(K/4) and the images restricted
+ * spectrally (modes with 2|k_a| < N_a/2 kept) solves H_c y = R r to relative tolerance 0.1
+ * (R: the coefficients of the coarse band, H_c: its Gauss-Newton Hessian at R v~), and
+ * P^{-1} r = E y + theta L~^{-1}(r - E R r), theta = <R r, y> / <R r, L~_c^{-1} R r>; the
+ * outer PCG becomes flexible PCG. Needs a band-limited stationary context, K >= 8 and even
+ * nx, ny, nz; the coarse context is allocated by this call (freed by value 0 or
+ * lddmm_destroy) and its images follow lddmm_set_images. EINVAL for other values or
+ * contexts; ENOMEM, ECUDA. */
 int lddmm_set_option(lddmm_ctx* ctx, int option, long value);
 
 /* Autotuner: times the SL voxel kernels of the context's grid for block shapes

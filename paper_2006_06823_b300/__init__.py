@@ -31,7 +31,7 @@ INTERP_LINEAR, INTERP_CUBIC = 1, 3
 PREC_FP32, PREC_BF16X3, PREC_FP32_SIMT, PREC_BF16X3_JBF16 = 0, 1, 2, 3
 FORWARD, BACKWARD = 1, -1
 STOP_GTOL, STOP_MAXIT, STOP_LINESEARCH = 1, 2, 3
-OPT_GRAPHS, OPT_BLOCK_X, OPT_GATHER_ZT = 1, 2, 3
+OPT_GRAPHS, OPT_BLOCK_X, OPT_GATHER_ZT, OPT_TWO_LEVEL = 1, 2, 3, 4
 NET_BF16, NET_FP32 = 0, 1
 
 
@@ -51,7 +51,7 @@ class Report(ctypes.Structure):
                 ("E0", ctypes.c_double), ("E", ctypes.c_double), ("E_reg", ctypes.c_double),
                 ("E_data", ctypes.c_double), ("grad_rel_l2", ctypes.c_double),
                 ("grad_rel_inf", ctypes.c_double), ("mse_rel", ctypes.c_double),
-                ("seconds", ctypes.c_double)]
+                ("seconds", ctypes.c_double), ("pcg_inner_total", ctypes.c_int)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

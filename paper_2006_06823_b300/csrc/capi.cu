@@ -75,7 +75,7 @@ struct lddmm_ctx {
     // spectral scratch
     float2 *s1 = nullptr, *s2 = nullptr;
     // cube vectors (3 x K^3 each, x (nt + 1) nodes in a non-stationary context)
-    enum { C_V, C_VT, C_G, C_R, C_Z, C_P, C_HP, C_X, C_T0, C_T1, C_T2, C_CUR, C_DV, C_NUM };
+    enum { C_V, C_VT, C_G, C_R, C_Z, C_P, C_HP, C_X, C_T0, C_T1, C_T2, C_CUR, C_DV, C_RP, C_NUM };
     float2* cv[C_NUM];
     // reductions
     double* partials = nullptr;
@@ -92,6 +92,11 @@ struct lddmm_ctx {
     int hv_eager_runs = 0;
     cudaGraphExec_t hv_exec = nullptr;
     long hv_graph_launches = 0;
+    // two-level preconditioner: the half-grid context of the coarse level (owned) and the cap
+    // on its PCG iterations per application (0: the spectral preconditioner L~^{-1} alone)
+    lddmm_ctx* coarse = nullptr;
+    int tl_inner = 0;
+    bool have_images = false;
 };
 
 static int fail(lddmm_ctx* c, int rc) {
@@ -798,6 +803,103 @@ static double dot_host(lddmm_ctx* c, const float2* a, const float2* b, int* rc) 
     return c->hsc[0] * dscale(c);
 }
 
+// ------------------------------------------------------------------ two-level preconditioner
+// The multi-level preconditioner named in Secs. 6-7 (that of the CLAIRE solver), read as: the
+// same problem on the half grid with band Kc = 2 floor(K/4) and spectrally restricted images
+// (the coarse context); P^{-1} r = E y + theta L~^{-1}(r - E R r), y from at most tl_inner PCG
+// iterations (relative tolerance 0.1, preconditioner L~_c^{-1}) on H_c y = R r, H_c the coarse
+// Gauss-Newton Hessian at R v~, theta = <R r, y> / <R r, L~_c^{-1} R r> (1 if R r = 0), which
+// puts the modes above the coarse band on the scale of the coarse solve: with alpha = 0.0025 the
+// data term, not L~, dominates H there. The outer Krylov method is then flexible PCG.
+static const double kInnerTol = 0.1;
+static bool two_level(const lddmm_ctx* c) { return c->coarse && c->tl_inner > 0; }
+
+static int pcg_solve(lddmm_ctx* c, double bnorm, double eta, int maxit, int* its, int* inner_its);
+
+// z = P^{-1} r (velocity-shaped vectors of c)
+static int apply_precond(lddmm_ctx* c, const float2* r, float2* z, int* inner_its) {
+    TRY(op_L(c, z, r, 1.f, 0.f, nullptr, 3 * nodes(c), -1));
+    if (!two_level(c)) return LDDMM_OK;
+    lddmm_ctx* q = c->coarse;
+    float2* b = q->cv[lddmm_ctx::C_G];   // R r
+    float2* y = q->cv[lddmm_ctx::C_X];
+    float2* lb = q->cv[lddmm_ctx::C_Z];
+    int rc = 0;
+    TRY(cube_restrict(r, c->K, b, q->K, 3, c->st));
+    LDDMM_CUDA(cudaMemcpyAsync(q->cv[lddmm_ctx::C_R], b, nvec(q) * sizeof(float2),
+                               cudaMemcpyDeviceToDevice, c->st));
+    const double bb = dot_host(q, b, b, &rc);
+    TRY(rc);
+    int its = 0;
+    TRY(pcg_solve(q, std::sqrt(bb), kInnerTol, c->tl_inner, &its, nullptr));
+    if (inner_its) *inner_its += its;
+    TRY(op_L(q, lb, b, 1.f, 0.f, nullptr, 3, -1));
+    const double by = dot_host(q, b, y, &rc);
+    TRY(rc);
+    const double bl = dot_host(q, b, lb, &rc);
+    TRY(rc);
+    const double theta = bl > 0.0 ? by / bl : 1.0;
+    return cube_two_level(z, c->K, y, q->K, (float)theta, 3, c->st);
+}
+
+// PCG on H x = b from x = 0, b in cv[C_R] on entry (overwritten by the residual), x left in
+// cv[C_X]; flexible (beta = <z', r' - r> / <z, r>) with the two-level preconditioner. Stops on
+// ||r|| <= eta bnorm, after maxit products, or on non-positive curvature (at the first
+// iteration x = P^{-1} b, the preconditioned steepest-descent direction).
+static int pcg_solve(lddmm_ctx* c, double bnorm, double eta, int maxit, int* its, int* inner_its) {
+    const long kc3 = nvec(c);
+    float2 *r = c->cv[lddmm_ctx::C_R], *z = c->cv[lddmm_ctx::C_Z], *pp = c->cv[lddmm_ctx::C_P];
+    float2 *Hp = c->cv[lddmm_ctx::C_HP], *x = c->cv[lddmm_ctx::C_X], *rp = c->cv[lddmm_ctx::C_RP];
+    const bool flex = two_level(c);
+    int rc = 0;
+    *its = 0;
+    LDDMM_CUDA(cudaMemsetAsync(x, 0, kc3 * sizeof(float2), c->st));
+    TRY(apply_precond(c, r, z, inner_its));
+    TRY(cube_axpby(pp, 1.f, z, 0.f, nullptr, kc3, c->st));
+    double rz = dot_host(c, r, z, &rc);
+    TRY(rc);
+    for (int i = 0; i < maxit; ++i) {
+        TRY(hessian_pcg(c));
+        ++*its;
+        const double pHp = dot_host(c, pp, Hp, &rc);
+        TRY(rc);
+        if (pHp <= 0.0) {
+            if (i == 0)
+                LDDMM_CUDA(cudaMemcpyAsync(x, z, kc3 * sizeof(float2), cudaMemcpyDeviceToDevice, c->st));
+            break;
+        }
+        const double a = rz / pHp;
+        TRY(cube_axpby(x, 1.f, x, (float)a, pp, kc3, c->st));
+        if (flex)
+            LDDMM_CUDA(cudaMemcpyAsync(rp, r, kc3 * sizeof(float2), cudaMemcpyDeviceToDevice, c->st));
+        TRY(cube_axpby(r, 1.f, r, (float)-a, Hp, kc3, c->st));
+        const double rn = std::sqrt(dot_host(c, r, r, &rc));
+        TRY(rc);
+        if (rn <= eta * bnorm) break;
+        TRY(apply_precond(c, r, z, inner_its));
+        const double rz2 = dot_host(c, r, z, &rc);
+        TRY(rc);
+        double num = rz2;
+        if (flex) {
+            num -= dot_host(c, rp, z, &rc);
+            TRY(rc);
+        }
+        TRY(cube_axpby(pp, 1.f, z, (float)(num / rz), pp, kc3, c->st));
+        rz = rz2;
+    }
+    return LDDMM_OK;
+}
+
+// The coarse Hessian of the next solve is taken at R v~ (v the current iterate).
+static int coarse_prepare(lddmm_ctx* c, const float2* v) {
+    lddmm_ctx* q = c->coarse;
+    q->use_graphs = c->use_graphs;
+    float2* vq = q->cv[lddmm_ctx::C_VT];
+    TRY(cube_restrict(v, c->K, vq, q->K, 3, c->st));
+    TRY(ensure_state(q, vq, false));
+    return ensure_traj(q);
+}
+
 static int register_impl(lddmm_ctx* c, float2* v_io, const double* gref_in, lddmm_report* rep) {
     auto t0 = std::chrono::steady_clock::now();
     const long kc3 = nvec(c);             // float2 per velocity-shaped vector
@@ -809,8 +911,7 @@ static int register_impl(lddmm_ctx* c, float2* v_io, const double* gref_in, lddm
     float2* v = c->cv[lddmm_ctx::C_V];
     float2* vtr = c->cv[lddmm_ctx::C_VT];
     float2* g = c->cv[lddmm_ctx::C_G];
-    float2 *r = c->cv[lddmm_ctx::C_R], *z = c->cv[lddmm_ctx::C_Z], *pp = c->cv[lddmm_ctx::C_P];
-    float2 *Hp = c->cv[lddmm_ctx::C_HP], *x = c->cv[lddmm_ctx::C_X];
+    float2 *r = c->cv[lddmm_ctx::C_R], *x = c->cv[lddmm_ctx::C_X];
     LDDMM_CUDA(cudaMemcpyAsync(v, v_io, kc3 * sizeof(float2), cudaMemcpyDeviceToDevice, c->st));
     if (!spatial(c)) TRY(cube_hermitian(v, K, ncube, c->st));
 
@@ -855,35 +956,14 @@ static int register_impl(lddmm_ctx* c, float2* v_io, const double* gref_in, lddm
             break;
         }
         const double eta = std::min(0.5, std::sqrt(gn / gref2));
-        // PCG on H x = -g with preconditioner L~^{-1}, x0 = 0
-        LDDMM_CUDA(cudaMemsetAsync(x, 0, kc3 * sizeof(float2), c->st));
+        // PCG on H x = -g from x0 = 0 (flexible PCG with the two-level preconditioner, whose
+        // coarse Hessian is taken at the current iterate)
+        if (two_level(c)) TRY(coarse_prepare(c, v));
         TRY(cube_axpby(r, -1.f, g, 0.f, nullptr, kc3, c->st));
-        TRY(op_L(c, z, r, 1.f, 0.f, nullptr, ncube, -1));
-        TRY(cube_axpby(pp, 1.f, z, 0.f, nullptr, kc3, c->st));
-        double rz = dot_host(c, r, z, &rc);
-        TRY(rc);
-        for (int i = 0; i < c->p.max_pcg; ++i) {
-            TRY(hessian_pcg(c));
-            rep->pcg_iters_total++;
-            double pHp = dot_host(c, pp, Hp, &rc);
-            TRY(rc);
-            if (pHp <= 0.0) {
-                if (i == 0)  // preconditioned steepest descent
-                    TRY(op_L(c, x, r, 1.f, 0.f, nullptr, ncube, -1));
-                break;
-            }
-            const double a = rz / pHp;
-            TRY(cube_axpby(x, 1.f, x, (float)a, pp, kc3, c->st));
-            TRY(cube_axpby(r, 1.f, r, (float)-a, Hp, kc3, c->st));
-            double rn = std::sqrt(dot_host(c, r, r, &rc));
-            TRY(rc);
-            if (rn <= eta * gn) break;
-            TRY(op_L(c, z, r, 1.f, 0.f, nullptr, ncube, -1));
-            double rz2 = dot_host(c, r, z, &rc);
-            TRY(rc);
-            TRY(cube_axpby(pp, 1.f, z, (float)(rz2 / rz), pp, kc3, c->st));
-            rz = rz2;
-        }
+        int its = 0, inner = 0;
+        TRY(pcg_solve(c, gn, eta, c->p.max_pcg, &its, &inner));
+        rep->pcg_iters_total += its;
+        rep->pcg_inner_total += inner;
         // Armijo backtracking on eps
         const double slope = dot_host(c, g, x, &rc);
         TRY(rc);
@@ -1007,9 +1087,54 @@ static int check_ctx(lddmm_ctx* c) {
         return LDDMM_OK;                  \
     } while (0)
 
+static int after_images(lddmm_ctx* c);
+
+// The coarse level's images: the spectral restriction of the context's images to the half grid.
+static int coarse_images(lddmm_ctx* c) {
+    lddmm_ctx* q = c->coarse;
+    const float* in[2] = {c->I0, c->I1};
+    float* out[2] = {q->I0, q->I1};
+    TRY(spectral_restrict_half(c->g, in, q->g, out, 2, c->st));
+    return after_images(q);
+}
+
 static int after_images(lddmm_ctx* c) {
     c->vel_valid = c->traj_valid = c->warp_valid = false;
+    c->have_images = true;
     if (cubic(c)) TRY(bspline_prefilter(c->g, c->I0, 1, c->I0c, c->st));
+    if (c->coarse) TRY(coarse_images(c));
+    return LDDMM_OK;
+}
+
+// Creates the coarse level of the two-level preconditioner (half grid, band 2 floor(K/4), same
+// variant, interpolation, nt, alpha, s, sigma^2 and precision form; stream shared).
+static int make_coarse(lddmm_ctx* c) {
+    if (spatial(c) || ns(c)) {
+        set_error("the two-level preconditioner needs a band-limited stationary context");
+        return LDDMM_EINVAL;
+    }
+    if (c->K < 8 || (c->g.nx & 1) || (c->g.ny & 1) || (c->g.nz & 1)) {
+        set_error("the two-level preconditioner needs K >= 8 and even nx, ny, nz");
+        return LDDMM_EINVAL;
+    }
+    lddmm_params cp = c->p;
+    cp.nx /= 2;
+    cp.ny /= 2;
+    cp.nz /= 2;
+    cp.K = 2 * (c->K / 4);
+    lddmm_ctx* q = nullptr;
+    TRY(lddmm_create(&cp, c->st, &q));
+    c->coarse = q;
+    if (c->have_images) {
+        int rc = coarse_images(c);
+        if (rc) {
+            std::string msg = g_last_error;
+            lddmm_destroy(q);
+            c->coarse = nullptr;
+            set_error(msg);
+            return rc;
+        }
+    }
     return LDDMM_OK;
 }
 
@@ -1058,6 +1183,7 @@ int lddmm_destroy(lddmm_ctx* c) {
     if (!c) return LDDMM_OK;
     if (c->st || true) cudaStreamSynchronize(c->st);
     if (c->hv_exec) cudaGraphExecDestroy(c->hv_exec);
+    lddmm_destroy(c->coarse);
     spatial_fft_destroy(c->fft);
     for (void* p : c->allocs) cudaFree(p);
     if (c->hsc) cudaFreeHost(c->hsc);
@@ -1323,6 +1449,24 @@ int lddmm_set_option(lddmm_ctx* c, int option, long value) {
                 return LDDMM_EINVAL;
             }
             c->sl.zt = (int)value;
+            return LDDMM_OK;
+        }
+        case LDDMM_OPT_TWO_LEVEL: {
+            if (value < 0 || value > 1000) {
+                set_error("two-level inner iterations must be 0 (off) .. 1000");
+                return LDDMM_EINVAL;
+            }
+            if (value == 0) {
+                lddmm_destroy(c->coarse);
+                c->coarse = nullptr;
+                c->tl_inner = 0;
+                return LDDMM_OK;
+            }
+            if (!c->coarse) {
+                rc = make_coarse(c);
+                if (rc) return rc;
+            }
+            c->tl_inner = (int)value;
             return LDDMM_OK;
         }
         default:

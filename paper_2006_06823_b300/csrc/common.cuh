@@ -105,6 +105,10 @@ int cube_apply_L(float2* out, const float2* x, float wL, float a, const float2* 
 // Hermitian symmetrisation of ncomp cubes in place: c <- (c + conj c_{-k}) / 2, slot-0
 // planes zeroed.
 int cube_hermitian(float2* c, int K, int ncomp, cudaStream_t st);
+// Two-level preconditioner on band-limited cubes: R (the coarse band S_c of edge Kc, slot 0
+// zero) and z <- E y on S_c, theta z on the other modes.
+int cube_restrict(const float2* fine, int K, float2* coarse, int Kc, int ncomp, cudaStream_t st);
+int cube_two_level(float2* z, int K, const float2* y, int Kc, float theta, int ncomp, cudaStream_t st);
 
 // FP64 reductions into device doubles (deterministic two-pass).
 int dot_f2(const float2* a, const float2* b, long n, double* partials, double* out,
@@ -131,6 +135,11 @@ int spatial_deriv(SpatialFFT* f, const float* in, int ncomp, int axis, float* ou
                   cudaStream_t st);
 // max |a_i| over n floats
 int max_abs_f32(const float* a, long n, double* partials, double* out, cudaStream_t st);
+// Spectral restriction of nimg periodic images from grid gf to the half grid gc (gc = gf / 2 per
+// axis): Fourier modes with 2|k_a| < gc_a kept, synthesised on gc (full-grid cuFFT plans made
+// and released inside the call; synchronises the stream).
+int spectral_restrict_half(const Grid& gf, const float* const* in, const Grid& gc, float* const* out,
+                           int nimg, cudaStream_t st);
 
 // ---------------------------------------------------------------- SL kernels (sl.cu)
 struct SLArgs {

@@ -4,6 +4,8 @@
 // (the PCG preconditioner, Eqs. 13-14) and the spectral derivatives of the fields (grad m,
 // D u, div v) go through full-grid FFTs (cuFFT, the plain library transform). Everything
 // else -- characteristics, gathers, incremental steps, accumulations -- is the same kernels.
+// The same transforms restrict the images of a band-limited context to the half grid for the
+// coarse level of the two-level preconditioner.
 #include <cufft.h>
 
 #include <algorithm>
@@ -105,6 +107,28 @@ __global__ void k_finalize_max(const double* partials, int n, double* out) {
         __syncthreads();
     }
     if (threadIdx.x == 0) *out = sm[0];
+}
+
+// Coarse half spectrum [nzc][nyc][nxc/2 + 1] from the fine one: modes with 2|k_a| < n_a (the
+// half grid's n) copied with the factor scale (1/n_fine: mean-normalised coefficients, which
+// the unnormalised C2R then synthesises), every other mode zero.
+__global__ void k_spec_restrict(const cufftComplex* __restrict__ fs, int nxf, int nyf, int nzf,
+                                cufftComplex* __restrict__ cs, int nxc, int nyc, int nzc, float scale) {
+    const int nxhc = nxc / 2 + 1, nxhf = nxf / 2 + 1;
+    const long tot = (long)nzc * nyc * nxhc;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < tot; i += (long)gridDim.x * blockDim.x) {
+        const int ix = (int)(i % nxhc);
+        const int iy = (int)((i / nxhc) % nyc);
+        const int iz = (int)(i / ((long)nxhc * nyc));
+        const int kx = ix, ky = wavenum(iy, nyc), kz = wavenum(iz, nzc);
+        cufftComplex v = make_float2(0.f, 0.f);
+        if (2 * kx < nxc && 2 * abs(ky) < nyc && 2 * abs(kz) < nzc) {
+            const int fy = ky < 0 ? ky + nyf : ky, fz = kz < 0 ? kz + nzf : kz;
+            const cufftComplex f = fs[((long)fz * nyf + fy) * nxhf + kx];
+            v = make_float2(f.x * scale, f.y * scale);
+        }
+        cs[i] = v;
+    }
 }
 
 inline int spec_grid(const Grid& g) {
@@ -213,6 +237,48 @@ int spatial_deriv(SpatialFFT* f, const float* in, int ncomp, int axis, float* ou
         LDDMM_CUFFT(cufftExecC2R(f->c2r, f->acc, out + c * fstride));
     }
     return LDDMM_OK;
+}
+
+int spectral_restrict_half(const Grid& gf, const float* const* in, const Grid& gc, float* const* out,
+                           int nimg, cudaStream_t st) {
+    if (gf.nx != 2 * gc.nx || gf.ny != 2 * gc.ny || gf.nz != 2 * gc.nz) {
+        set_error("spectral_restrict_half: the coarse grid must be half the fine grid");
+        return LDDMM_EINVAL;
+    }
+    SpatialFFT *ff = nullptr, *fc = nullptr;
+    int rc = spatial_fft_create(gf, st, &ff);
+    if (rc == LDDMM_OK) rc = spatial_fft_create(gc, st, &fc);
+    for (int i = 0; rc == LDDMM_OK && i < nimg; ++i) {
+        cufftResult r = cufftExecR2C(ff->r2c, const_cast<float*>(in[i]), ff->spec);
+        if (r != CUFFT_SUCCESS) {
+            set_error("cufftExecR2C (restriction): cuFFT error " + std::to_string((int)r));
+            rc = LDDMM_ECUDA;
+            break;
+        }
+        {
+            KTRACE("spec_restrict", st, 16.0 * gc.ntot(), 2.0 * gc.ntot());
+            k_spec_restrict<<<spec_grid(gc), 256, 0, st>>>(ff->spec, gf.nx, gf.ny, gf.nz, fc->spec, gc.nx,
+                                                          gc.ny, gc.nz, (float)(1.0 / (double)gf.ntot()));
+        }
+        if (cudaGetLastError() != cudaSuccess) {
+            set_error("k_spec_restrict launch failed");
+            rc = LDDMM_ECUDA;
+            break;
+        }
+        r = cufftExecC2R(fc->c2r, fc->spec, out[i]);
+        if (r != CUFFT_SUCCESS) {
+            set_error("cufftExecC2R (restriction): cuFFT error " + std::to_string((int)r));
+            rc = LDDMM_ECUDA;
+        }
+    }
+    // the plans and spectra are released only after the work queued on them has finished
+    if (cudaStreamSynchronize(st) != cudaSuccess && rc == LDDMM_OK) {
+        set_error("spectral_restrict_half: stream synchronisation failed");
+        rc = LDDMM_ECUDA;
+    }
+    spatial_fft_destroy(ff);
+    spatial_fft_destroy(fc);
+    return rc;
 }
 
 int max_abs_f32(const float* a, long n, double* partials, double* out, cudaStream_t st) {

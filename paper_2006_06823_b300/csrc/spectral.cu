@@ -844,6 +844,67 @@ int cube_hermitian(float2* c, int K, int ncomp, cudaStream_t st) {
     return LDDMM_OK;
 }
 
+// --------------------------------------------------------- coarse band (two-level PCG)
+// Coarse band S_c = {|k|_inf <= Kc/2 - 1} of a band-K cube: fine slot j holds k = j - K/2,
+// coarse slot jc holds k = jc - Kc/2, so jc = j - (K - Kc)/2; coarse slot 0 is never filled.
+
+// R: coarse[c][jz][jy][jx] = fine[c][jz + o][jy + o][jx + o] (o = (K - Kc)/2), 0 on slot 0
+__global__ void k_cube_restrict(const float2* __restrict__ fine, int K, float2* __restrict__ coarse,
+                                int Kc, long n) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const long kk = (long)Kc * Kc * Kc;
+    const long comp = i / kk, r = i - comp * kk;
+    const int jx = (int)(r % Kc), jy = (int)((r / Kc) % Kc), jz = (int)(r / ((long)Kc * Kc));
+    float2 v = make_float2(0.f, 0.f);
+    if (jx >= 1 && jy >= 1 && jz >= 1) {
+        const int o = (K - Kc) / 2;
+        v = fine[comp * K * K * K + ((long)(jz + o) * K + (jy + o)) * K + (jx + o)];
+    }
+    coarse[i] = v;
+}
+
+// z <- E y on the coarse band, theta z elsewhere (z holds L~^{-1} r on entry)
+__global__ void k_cube_two_level(float2* __restrict__ z, int K, const float2* __restrict__ y, int Kc,
+                                 float theta, long n) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const long kk = (long)K * K * K;
+    const long comp = i / kk, r = i - comp * kk;
+    const int o = (K - Kc) / 2;
+    const int jx = (int)(r % K) - o, jy = (int)((r / K) % K) - o, jz = (int)(r / ((long)K * K)) - o;
+    if (jx >= 1 && jy >= 1 && jz >= 1 && jx < Kc && jy < Kc && jz < Kc) {
+        z[i] = y[comp * Kc * Kc * Kc + ((long)jz * Kc + jy) * Kc + jx];
+    } else {
+        const float2 v = z[i];
+        z[i] = make_float2(theta * v.x, theta * v.y);
+    }
+}
+
+int cube_restrict(const float2* fine, int K, float2* coarse, int Kc, int ncomp, cudaStream_t st) {
+    if (Kc < 2 || Kc > K || (Kc & 1) || (K & 1)) {
+        set_error("cube_restrict: need even 2 <= Kc <= K");
+        return LDDMM_EINVAL;
+    }
+    const long n = (long)ncomp * Kc * Kc * Kc;
+    KTRACE("cube_restrict", st, 16.0 * n, 0);
+    k_cube_restrict<<<cdiv(n, 256), 256, 0, st>>>(fine, K, coarse, Kc, n);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+int cube_two_level(float2* z, int K, const float2* y, int Kc, float theta, int ncomp, cudaStream_t st) {
+    if (Kc < 2 || Kc > K || (Kc & 1) || (K & 1)) {
+        set_error("cube_two_level: need even 2 <= Kc <= K");
+        return LDDMM_EINVAL;
+    }
+    const long n = (long)ncomp * K * K * K;
+    KTRACE("cube_two_level", st, 16.0 * n, 2.0 * n);
+    k_cube_two_level<<<cdiv(n, 256), 256, 0, st>>>(z, K, y, Kc, theta, n);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
 // ------------------------------------------------------------------- FP64 reductions
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll

@@ -105,3 +105,34 @@ def test_spatial_flag_is_validated_before_any_device_work():
         h = ctypes.c_void_p(123)
         assert lib.lddmm_create(ctypes.byref(p), None, ctypes.byref(h)) == L.EINVAL
         assert h.value is None
+
+
+def _header_text():
+    import os
+    return open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "..", "include",
+                             "lddmm.h")).read()
+
+
+def test_report_struct_of_the_binding_follows_the_header():
+    """lddmm_report is filled by the library through the binding's ctypes mirror: same fields,
+    same order (the two-level preconditioner's pcg_inner_total last)."""
+    import re
+    text = _header_text()
+    body = text[text.index("/* Outcome of lddmm_register. */"):text.index("} lddmm_report;")]
+    body = re.sub(r"/\*.*?\*/", "", body, flags=re.S)
+    names = []
+    for decl in body.split("{", 1)[1].split(";"):
+        decl = decl.strip()
+        if decl:
+            names += [n.strip() for n in decl.split(None, 1)[1].split(",")]
+    assert names == [n for n, _ in L.Report._fields_]
+    assert names[-1] == "pcg_inner_total"
+
+
+def test_option_codes_of_the_binding_follow_the_header():
+    import re
+    text = _header_text()
+    codes = dict(re.findall(r"LDDMM_OPT_(\w+) = (\d+)", text))
+    assert {k: int(v) for k, v in codes.items()} == {
+        "GRAPHS": L.OPT_GRAPHS, "BLOCK_X": L.OPT_BLOCK_X, "GATHER_ZT": L.OPT_GATHER_ZT,
+        "TWO_LEVEL": L.OPT_TWO_LEVEL}
