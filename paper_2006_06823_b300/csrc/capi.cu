@@ -1181,7 +1181,7 @@ int lddmm_create(const lddmm_params* params, void* stream, lddmm_ctx** out) {
 
 int lddmm_destroy(lddmm_ctx* c) {
     if (!c) return LDDMM_OK;
-    if (c->st || true) cudaStreamSynchronize(c->st);
+    cudaStreamSynchronize(c->st);   // also for the legacy default stream (st == NULL)
     if (c->hv_exec) cudaGraphExecDestroy(c->hv_exec);
     lddmm_destroy(c->coarse);
     spatial_fft_destroy(c->fft);
