@@ -94,3 +94,35 @@ def test_odd_grid_is_refused():
         ctx.set_option(L.OPT_TWO_LEVEL, 2)
     assert e.value.code == L.EINVAL
     ctx.close()
+
+
+def test_batch_with_two_level_matches_sequential_registrations():
+    """lddmm_register_batch runs each pair's coarse level on that pair's stream: results equal
+    the sequential two-level registrations bit for bit."""
+    probs = [oracle_problem((16, 16, 16), 8, Vn.DEFSTATE, 1, nt=4, seed=0),
+             oracle_problem((16, 24, 20), 8, Vn.IMAGE, 1, nt=4, seed=1)]
+    kw = dict(max_gn=2, max_pcg=4)
+    seq = []
+    for prob in probs:
+        with context(prob, **kw) as ctx:
+            ctx.set_option(L.OPT_TWO_LEVEL, 3)
+            v, rep = ctx.register()
+            seq.append((v.cpu().numpy(), rep))
+    streams = [torch.cuda.Stream() for _ in probs]
+    ctxs = []
+    for prob, st in zip(probs, streams):
+        with torch.cuda.stream(st):
+            ctx = context(prob, **kw)
+            ctx.set_option(L.OPT_TWO_LEVEL, 3)
+        ctxs.append(ctx)
+    vs = [c.zeros_cube() for c in ctxs]
+    torch.cuda.synchronize()
+    reps = L.register_batch(ctxs, vs, max_threads=2)
+    torch.cuda.synchronize()
+    for (v0, r0), v1, r1 in zip(seq, vs, reps):
+        assert (r1["pcg_iters_total"], r1["pcg_inner_total"]) == (r0["pcg_iters_total"],
+                                                                   r0["pcg_inner_total"])
+        np.testing.assert_array_equal(v1.cpu().numpy(), v0)
+    for c in ctxs:
+        c.close()
+    assert L.device_error() == 0
