@@ -136,3 +136,43 @@ def test_option_codes_of_the_binding_follow_the_header():
     assert {k: int(v) for k, v in codes.items()} == {
         "GRAPHS": L.OPT_GRAPHS, "BLOCK_X": L.OPT_BLOCK_X, "GATHER_ZT": L.OPT_GATHER_ZT,
         "TWO_LEVEL": L.OPT_TWO_LEVEL}
+
+
+C_CONSUMER = r"""
+#include <stdio.h>
+#include "lddmm.h"
+int main(void) {
+    lddmm_params p = {0};
+    p.nx = p.ny = p.nz = 32; p.K = 7; p.nt = 10; p.variant = LDDMM_V_DEFSTATE;
+    p.interp = LDDMM_INTERP_LINEAR; p.alpha = 0.0025; p.s = 2; p.sigma2 = 0.01;
+    p.max_gn = 5; p.max_pcg = 10; p.gtol = 1e-3;
+    lddmm_ctx* c = (lddmm_ctx*)0x1;
+    int rc = lddmm_create(&p, NULL, &c);
+    printf("%s|%d|%d|%s\n", lddmm_version(), rc, c == NULL, lddmm_last_error());
+    return rc == LDDMM_EINVAL && c == NULL ? 0 : 1;
+}
+"""
+
+
+def test_header_is_plain_c_and_the_library_links_from_c(tmp_path):
+    """The boundary needs no C++ or Python: a C99 program (-pedantic, warnings as errors)
+    includes include/lddmm.h, links liblddmm.so and gets EINVAL for an odd band before any
+    device work."""
+    import os
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    root = os.path.join(os.path.dirname(os.path.abspath(__file__)), "..")
+    libdir = os.path.dirname(os.path.abspath(L.LIB_PATH))
+    src = tmp_path / "consumer.c"
+    src.write_text(C_CONSUMER)
+    exe = tmp_path / "consumer"
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                    "-I", os.path.join(root, "include"), str(src), "-L", libdir, "-llddmm",
+                    f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, out.stdout + out.stderr
+    version, rc, null, msg = out.stdout.strip().split("|", 3)
+    assert "sm_103a" in version and int(rc) == L.EINVAL and null == "1" and "band" in msg
