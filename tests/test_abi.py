@@ -176,3 +176,29 @@ def test_header_is_plain_c_and_the_library_links_from_c(tmp_path):
     assert out.returncode == 0, out.stdout + out.stderr
     version, rc, null, msg = out.stdout.strip().split("|", 3)
     assert "sm_103a" in version and int(rc) == L.EINVAL and null == "1" and "band" in msg
+
+
+def test_every_context_call_rejects_a_null_context_before_any_device_work():
+    lib = L.load()
+    p = ctypes.c_void_p(256)                 # never dereferenced: the context check comes first
+    d = ctypes.c_double(0)
+    rep = L.Report()
+    calls = [
+        lambda: lib.lddmm_set_images(None, p, p),
+        lambda: lib.lddmm_set_images_host(None, p, p),
+        lambda: lib.lddmm_objective(None, p, ctypes.byref(d), None, None),
+        lambda: lib.lddmm_gradient(None, p, p, None, None, None),
+        lambda: lib.lddmm_hessian_matvec(None, p, p, p),
+        lambda: lib.lddmm_register(None, p, None, ctypes.byref(rep)),
+        lambda: lib.lddmm_jacobian_det(None, p, None, ctypes.byref(d)),
+        lambda: lib.lddmm_get_warped(None, p),
+        lambda: lib.lddmm_set_option(None, L.OPT_TWO_LEVEL, 2),
+        lambda: lib.lddmm_autotune(None, None, None),
+    ]
+    for call in calls:
+        assert call() == L.EINVAL
+        assert b"NULL" in lib.lddmm_last_error()
+    ctxs = (ctypes.c_void_p * 1)(None)
+    vs = (ctypes.c_void_p * 1)(p)
+    reps = (L.Report * 1)()
+    assert lib.lddmm_register_batch(ctxs, vs, 1, None, reps, 1) == L.EINVAL
