@@ -340,6 +340,25 @@ const char* lddmm_last_error(void);
  * device-side wait gives up (*code = LDDMM_ETIMEOUT; 0 if none). Synchronises the device. */
 int lddmm_device_error(int* code);
 
+/* Self-test of the device-side wait bound: a one-thread kernel waits, through the routine the
+ * tensor-core kernels use, on an mbarrier phase that nothing completes, with the bound set to
+ * `seconds`; it gives up, records LDDMM_ETIMEOUT in the device error word (see
+ * lddmm_device_error) and returns, and *status receives LDDMM_ETIMEOUT. The wait is bounded by
+ * %globaltimer and by an iteration count: no fault, trap or hang, and the CUDA context stays
+ * usable. Synchronises. EINVAL unless 0 < seconds <= 1 and status != NULL. */
+int lddmm_selftest_wait(double seconds, int* status);
+
+/* Caps the device memory that each context may allocate for its workspace (bytes, process-
+ * wide, applies to contexts created afterwards and to later allocations of existing ones,
+ * e.g. the coarse context of LDDMM_OPT_TWO_LEVEL, which counts on its own; 0 = no cap, the
+ * default). An allocation beyond the cap fails with LDDMM_ENOMEM before calling cudaMalloc
+ * (lddmm_create then frees what it holds). cuFFT's plan work areas are not counted. EINVAL for
+ * a negative value. */
+int lddmm_set_workspace_limit(long long bytes);
+
+/* *bytes = the device bytes the context's workspace holds (its own allocations). */
+int lddmm_workspace_bytes(lddmm_ctx* ctx, long long* bytes);
+
 /* Library version string, e.g. "lddmm-b300 0.1 sm_103a". */
 const char* lddmm_version(void);
 

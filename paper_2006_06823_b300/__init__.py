@@ -104,6 +104,9 @@ def _declare(lib):
         "lddmm_trace_reset": (_I, []),
         "lddmm_trace_read": (_I, [ctypes.c_char_p, _I]),
         "lddmm_device_error": (_I, [ctypes.POINTER(_I)]),
+        "lddmm_selftest_wait": (_I, [_D, ctypes.POINTER(_I)]),
+        "lddmm_set_workspace_limit": (_I, [ctypes.c_longlong]),
+        "lddmm_workspace_bytes": (_I, [_P, ctypes.POINTER(ctypes.c_longlong)]),
         "lddmm_last_error": (ctypes.c_char_p, []),
         "lddmm_version": (ctypes.c_char_p, []),
     }
@@ -323,6 +326,12 @@ class Context:
     def set_option(self, option, value):
         _check(load().lddmm_set_option(self._h, option, int(value)))
 
+    def workspace_bytes(self):
+        """Device bytes of the context's own workspace (lddmm_workspace_bytes)."""
+        b = ctypes.c_longlong(0)
+        _check(load().lddmm_workspace_bytes(self._h, ctypes.byref(b)))
+        return b.value
+
     def autotune(self, cache_path=None):
         """Picks the fastest SL voxel-kernel block shape for this grid (lddmm_autotune)."""
         bx = ctypes.c_int(0)
@@ -455,6 +464,19 @@ def device_error():
     code = ctypes.c_int(0)
     _check(load().lddmm_device_error(ctypes.byref(code)))
     return code.value
+
+
+def selftest_wait(seconds):
+    """Runs the bounded-wait self-test (lddmm_selftest_wait): a device wait that nothing
+    completes gives up after `seconds`; returns the status it reported (ETIMEOUT)."""
+    status = ctypes.c_int(0)
+    _check(load().lddmm_selftest_wait(float(seconds), ctypes.byref(status)))
+    return status.value
+
+
+def set_workspace_limit(nbytes):
+    """Caps the device bytes each context may allocate (0: no cap; lddmm_set_workspace_limit)."""
+    _check(load().lddmm_set_workspace_limit(int(nbytes)))
 
 
 def register_batch(contexts, velocities, g_ref_norms=None, max_threads=8):

@@ -97,7 +97,12 @@ struct lddmm_ctx {
     lddmm_ctx* coarse = nullptr;
     int tl_inner = 0;
     bool have_images = false;
+    // device bytes of the context's own allocations (checked against the workspace limit)
+    long long ws_bytes = 0;
 };
+
+// Process-wide cap on the device bytes one context may allocate (0: none).
+static std::atomic<long long> g_ws_limit{0};
 
 static int fail(lddmm_ctx* c, int rc) {
     if (c && c->sticky == LDDMM_OK) c->sticky = rc;
@@ -105,6 +110,13 @@ static int fail(lddmm_ctx* c, int rc) {
 }
 
 static int dalloc(lddmm_ctx* c, void** p, size_t bytes) {
+    const long long lim = g_ws_limit.load();
+    if (lim > 0 && c->ws_bytes + (long long)bytes > lim) {
+        set_error("workspace limit: the context needs more than the " + std::to_string(lim) +
+                  " bytes allowed (lddmm_set_workspace_limit)");
+        *p = nullptr;
+        return LDDMM_ENOMEM;
+    }
     cudaError_t e = cudaMalloc(p, bytes);
     if (e != cudaSuccess) {
         set_error(std::string("cudaMalloc(") + std::to_string(bytes) + "): " + cudaGetErrorString(e));
@@ -112,6 +124,7 @@ static int dalloc(lddmm_ctx* c, void** p, size_t bytes) {
         return LDDMM_ENOMEM;
     }
     c->allocs.push_back(*p);
+    c->ws_bytes += (long long)bytes;
     return LDDMM_OK;
 }
 template <class T>
@@ -1148,6 +1161,22 @@ int lddmm_device_error(int* code) {
     if (!code) { set_error("code is NULL"); return LDDMM_EINVAL; }
     LDDMM_CUDA(cudaDeviceSynchronize());
     return tc_take_error(code);
+}
+
+int lddmm_selftest_wait(double seconds, int* status) { return wait_selftest(seconds, status); }
+
+int lddmm_set_workspace_limit(long long bytes) {
+    if (bytes < 0) { set_error("workspace limit must be >= 0 (0: none)"); return LDDMM_EINVAL; }
+    g_ws_limit.store(bytes);
+    return LDDMM_OK;
+}
+
+int lddmm_workspace_bytes(lddmm_ctx* c, long long* bytes) {
+    if (!bytes) { set_error("bytes is NULL"); return LDDMM_EINVAL; }
+    int rc = check_ctx(c);
+    if (rc) return rc;
+    *bytes = c->ws_bytes;
+    return LDDMM_OK;
 }
 
 int lddmm_create(const lddmm_params* params, void* stream, lddmm_ctx** out) {

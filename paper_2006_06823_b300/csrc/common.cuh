@@ -84,6 +84,9 @@ long tc_wimage_bytes(int N, int kdim);
 int tc_build_wimage(const float* W, int N, int kdim, int prec, unsigned char* img,
                     cudaStream_t st);
 int tc_take_error(int* code);
+// Bounded-wait self-test (a wait nothing completes, limited to `seconds`): *status =
+// LDDMM_ETIMEOUT, and the device error word records it. Synchronous.
+int wait_selftest(double seconds, int* status);
 
 // pi: ncomp fields (component stride fstride floats) -> ncomp cubes (stride K^3 float2).
 int bl_project(const Grid& g, const Twiddles& tw, const float* f, long fstride, int ncomp,

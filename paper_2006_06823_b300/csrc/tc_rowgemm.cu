@@ -66,17 +66,19 @@ __device__ __forceinline__ bool mbar_try(unsigned a, unsigned parity) {
     return ok != 0;
 }
 
-// Parity wait bounded by wall-clock time; returns false on timeout. The clock is read only
-// once the phase has been found incomplete (a %globaltimer read is slow next to a
-// completed try_wait).
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity) {
+// Parity wait bounded by wall-clock time (and, as a backstop, by an iteration count);
+// returns false on timeout. The clock is read only once the phase has been found incomplete
+// (a %globaltimer read is slow next to a completed try_wait).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, unsigned parity,
+                                          unsigned long long limit_ns = kWaitLimitNs) {
     const unsigned a = smem_u32(bar);
     if (mbar_try(a, parity)) return true;
     const unsigned long long t0 = now_ns();
-    for (unsigned it = 0;; ++it) {
+    for (unsigned it = 0; it != 0xFFFFFFFFu; ++it) {
         if (mbar_try(a, parity)) return true;
-        if ((it & 255u) == 255u && now_ns() - t0 > kWaitLimitNs) return false;
+        if ((it & 255u) == 255u && now_ns() - t0 > limit_ns) return false;
     }
+    return false;
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
@@ -725,6 +727,37 @@ int tc_rowgemm(const float* in, long rows, int kdim, long in_row_floats, const u
                                                                comp_stride, n_out, cols);
     }
     LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+// Self-test of the bounded waits: one thread waits, through the same routine as the
+// tensor-core kernel, on an mbarrier phase that nothing completes; when the bound runs out it
+// records LDDMM_ETIMEOUT in the device error word as a production kernel would, and returns.
+__global__ void k_wait_selftest(unsigned long long limit_ns, int* status) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x != 0) return;
+    mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    const bool done = mbar_wait(&bar, 0, limit_ns);
+    if (!done) atomicExch(&g_tc_error, LDDMM_ETIMEOUT);
+    *status = done ? LDDMM_OK : LDDMM_ETIMEOUT;
+}
+
+int wait_selftest(double seconds, int* status) {
+    if (!status || !(seconds > 0.0) || seconds > 1.0) {
+        set_error("selftest_wait: need status != NULL and 0 < seconds <= 1");
+        return LDDMM_EINVAL;
+    }
+    int* d = nullptr;
+    LDDMM_CUDA(cudaMalloc(&d, sizeof(int)));
+    k_wait_selftest<<<1, 32>>>((unsigned long long)(seconds * 1e9), d);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpy(status, d, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d);
+    if (e != cudaSuccess) {
+        set_error(std::string("selftest_wait: ") + cudaGetErrorString(e));
+        return LDDMM_ECUDA;
+    }
     return LDDMM_OK;
 }
 

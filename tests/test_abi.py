@@ -202,3 +202,27 @@ def test_every_context_call_rejects_a_null_context_before_any_device_work():
     vs = (ctypes.c_void_p * 1)(p)
     reps = (L.Report * 1)()
     assert lib.lddmm_register_batch(ctxs, vs, 1, None, reps, 1) == L.EINVAL
+
+
+def test_workspace_limit_gives_enomem_before_any_device_work():
+    lib = L.load()
+    p = L.Params(32, 32, 32, 16, 10, L.V_DEFSTATE, L.INTERP_LINEAR, 0.0025, 2, 0.01, 5, 10,
+                 1e-3, L.PREC_FP32)
+    h = ctypes.c_void_p(123)
+    try:
+        assert lib.lddmm_set_workspace_limit(1) == L.OK
+        assert lib.lddmm_create(ctypes.byref(p), None, ctypes.byref(h)) == L.ENOMEM
+        assert h.value is None
+        assert b"workspace limit" in lib.lddmm_last_error()
+    finally:
+        lib.lddmm_set_workspace_limit(0)
+    assert lib.lddmm_set_workspace_limit(-1) == L.EINVAL
+
+
+@pytest.mark.parametrize("seconds", [0.0, -1.0, 1.5])
+def test_wait_selftest_validates_its_bound_before_any_device_work(seconds):
+    lib = L.load()
+    st = ctypes.c_int(7)
+    assert lib.lddmm_selftest_wait(seconds, ctypes.byref(st)) == L.EINVAL
+    assert st.value == 7
+    assert lib.lddmm_selftest_wait(0.01, None) == L.EINVAL
