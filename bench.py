@@ -263,6 +263,7 @@ def run_b300(args):
     # ---- e2e: the public API with host buffers, copies inside the timing
     # diagnostics of the solution (Sec. 5.1.1): range of det D phi(1)
     jac_range, _ = ctx.jacobian_det(v_sol)
+    max_disp = ctx.max_displacement(v_sol)
 
     e2e_s = []
     v_host = torch.empty((3, K, K, K), dtype=torch.complex64).pin_memory()
@@ -312,7 +313,8 @@ def run_b300(args):
         "residual_reached": last["grad_rel_l2"] <= GTOL,
         "report": dict({k: last[k] for k in ("gn_iters", "pcg_iters_total", "stop_reason", "solves",
                                              "E0", "E", "grad_rel_l2", "grad_rel_inf", "mse_rel")},
-                       jacobian_det_min=jac_range[0], jacobian_det_max=jac_range[1]),
+                       jacobian_det_min=jac_range[0], jacobian_det_max=jac_range[1],
+                       max_displacement_vox=max_disp),
         "sl_voxel_steps_per_s": sl_vps,
         "e2e": {"value": e2e_total / (args.steps * world), "unit": "s/pair",
                 "h2d_bytes_per_step": 2 * ntot * 4, "d2h_bytes_per_step": 3 * K ** 3 * 8},

@@ -203,6 +203,12 @@ int lddmm_autotune(lddmm_ctx* ctx, const char* cache_path, int* block_x_out);
  * DEFSTATE and STATE contexts only (EINVAL for IMAGE). Synchronises. */
 int lddmm_jacobian_det(lddmm_ctx* ctx, const float* v, float* J, double* range);
 
+/* *vox = max over voxels of |phi(1)(x) - x| = |iota(u~(1))(x)| in voxels (per-axis voxel
+ * units, FP64 reduction): the largest displacement of the deformation for the velocity v
+ * (device, the context's velocity layout). Solves the state for v unless it is the context's
+ * current one. DEFSTATE and STATE contexts only (EINVAL for IMAGE). Synchronises. */
+int lddmm_max_displacement(lddmm_ctx* ctx, const float* v, double* vox);
+
 /* Warp m(1) = I0 o phi(1) of the last state solved in the context into m1 (device,
  * float[nz][ny][nx]). DEFSTATE, STATE: phi(1) = id - iota(u~(1)); IMAGE: m(nt). */
 int lddmm_get_warped(lddmm_ctx* ctx, float* m1);

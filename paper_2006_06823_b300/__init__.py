@@ -79,6 +79,7 @@ def _declare(lib):
         "lddmm_register": (_I, [_P, _P, _P, ctypes.POINTER(Report)]),
         "lddmm_get_warped": (_I, [_P, _P]),
         "lddmm_jacobian_det": (_I, [_P, _P, _P, ctypes.POINTER(_D)]),
+        "lddmm_max_displacement": (_I, [_P, _P, ctypes.POINTER(_D)]),
         "lddmm_bl_project": (_I, [_I, _I, _I, _I, _P, _I, _P, _I, _P]),
         "lddmm_bl_project_noalloc": (_I, [_I, _I, _I, _I, _P, _I, _P, _I, _P]),
         "lddmm_bl_include": (_I, [_I, _I, _I, _I, _P, _I, _P, _I, _I, _I, _P]),
@@ -349,6 +350,12 @@ class Context:
         rng = (ctypes.c_double * 2)()
         _check(load().lddmm_jacobian_det(self._h, self._vec(v), _f32(J) if J is not None else None, rng))
         return (rng[0], rng[1]), J
+
+    def max_displacement(self, v):
+        """max |phi(1)(x) - x| in voxels for velocity v (lddmm_max_displacement)."""
+        d = ctypes.c_double(0)
+        _check(load().lddmm_max_displacement(self._h, self._vec(v), ctypes.byref(d)))
+        return d.value
 
     def get_warped(self, out=None):
         import torch

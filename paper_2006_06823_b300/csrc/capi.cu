@@ -1290,6 +1290,26 @@ int lddmm_jacobian_det(lddmm_ctx* c, const float* v, float* J, double* range) {
     })());
 }
 
+int lddmm_max_displacement(lddmm_ctx* c, const float* v, double* vox) {
+    if (!v || !vox) { set_error("max_displacement: v or vox is NULL"); return LDDMM_EINVAL; }
+    CTX_CALL(c, ([&]() -> int {
+        if (!has_u(c)) {
+            set_error("max_displacement: deformation-state or state-equation contexts only");
+            return LDDMM_EINVAL;
+        }
+        const float2* vt = reinterpret_cast<const float2*>(v);
+        bool same = false;
+        TRY(same_as_current(c, vt, &same));
+        TRY(ensure_state(c, vt, same));
+        // |phi(1)(x) - x| = |iota(u~(1))(x)|, in voxels per axis
+        TRY(include(c, c->ut + (long)c->p.nt * 3 * c->kc, 3, c->fa, c->n, -1, 0));
+        TRY(max_norm3(c->fa, c->n, c->to_vox, c->partials, c->dsc, c->st));
+        TRY(read_scalars(c, 1));
+        *vox = c->hsc[0];
+        return LDDMM_OK;
+    })());
+}
+
 int lddmm_get_warped(lddmm_ctx* c, float* m1) {
     if (!m1) { set_error("m1 is NULL"); return LDDMM_EINVAL; }
     CTX_CALL(c, ([&]() -> int {

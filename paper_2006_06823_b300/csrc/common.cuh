@@ -117,6 +117,8 @@ int cube_two_level(float2* z, int K, const float2* y, int Kc, float theta, int n
 int dot_f2(const float2* a, const float2* b, long n, double* partials, double* out,
            cudaStream_t st);
 int max_abs_f2(const float2* a, long n, double* partials, double* out, cudaStream_t st);
+// max over voxels of the length of the 3-plane field u scaled per component by s (FP64)
+int max_norm3(const float* u, long n, const float s[3], double* partials, double* out, cudaStream_t st);
 // sum_j w_j <a_j, b_j> over `nodes` blocks of npn elements, w_j trapezoid weights of step dt
 // (nodes == 1: plain dot)
 int dot_f2_nodes(const float2* a, const float2* b, long npn, int nodes, double dt,

@@ -1011,6 +1011,29 @@ int max_abs_f2(const float2* a, long n, double* partials, double* out, cudaStrea
     return LDDMM_OK;
 }
 
+// max over voxels of |(s0 u0, s1 u1, s2 u2)| for a 3-plane field u (a displacement in voxels)
+__global__ void k_max_norm3(const float* __restrict__ u, long n, float s0, float s1, float s2,
+                            double* partials) {
+    double m = 0.0;
+    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x) {
+        const double a = (double)u[i] * s0, b = (double)u[n + i] * s1, c = (double)u[2 * n + i] * s2;
+        m = fmax(m, sqrt(a * a + b * b + c * c));
+    }
+    block_reduce_store<true>(m, partials + blockIdx.x);
+}
+
+int max_norm3(const float* u, long n, const float s[3], double* partials, double* out, cudaStream_t st) {
+    {
+        KTRACE("max_norm3", st, 12.0 * n, 8.0 * n);
+        k_max_norm3<<<kReduceBlocks, 256, 0, st>>>(u, n, s[0], s[1], s[2], partials);
+    }
+    LDDMM_CHECK_LAUNCH();
+    KTRACE("finalize", st, 8.0 * kReduceBlocks, kReduceBlocks);
+    k_finalize<<<1, 256, 0, st>>>(partials, kReduceBlocks, out, 1);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
 int finalize_sum(const double* partials, int n, double* out, cudaStream_t st) {
     KTRACE("finalize", st, 8.0 * n, n);
     k_finalize<<<1, 256, 0, st>>>(partials, n, out, 0);

@@ -218,6 +218,23 @@ def test_jacobian_determinant_matches_oracle(shape, K, order):
     assert zmin == 1.0 and zmax == 1.0                 # identity map
 
 
+@pytest.mark.parametrize("variant,order", [(Vn.DEFSTATE, 1), (Vn.DEFSTATE, 3), (Vn.STATE, 1)])
+def test_max_displacement_matches_oracle(variant, order):
+    """max |phi(1)(x) - x| in voxels (a Sec. 5.1.1-style diagnostic) against the oracle, on a
+    non-cubic grid (per-axis voxel units)."""
+    prob = oracle_problem((20, 24, 28), 10, variant, order, nt=5)
+    vt = synth.random_velocity_coeffs(10, 10, seed=9) * 2.0
+    ref = prob.max_displacement_vox(vt)
+    with gpu_context(prob) as ctx:
+        d = ctx.max_displacement(devc(vt))
+        d0 = ctx.max_displacement(ctx.zeros_cube())
+    assert ref > 0.5 and d == pytest.approx(ref, rel=1e-4)
+    assert d0 == 0.0
+    with gpu_context(oracle_problem((16, 16, 16), 8, Vn.IMAGE, 1, nt=3)) as ctx:
+        with pytest.raises(L.LddmmError):
+            ctx.max_displacement(ctx.zeros_cube())
+
+
 def test_jacobian_determinant_needs_the_deformation_state():
     prob = oracle_problem((16, 16, 16), 8, Vn.IMAGE, 1, nt=3)
     with gpu_context(prob) as ctx:
