@@ -47,15 +47,15 @@ WORKLOAD = ("192x224x192 brain-like ellipsoid phantom pair (moving = phantom war
 # oracle's sample in the reference arm.
 REF_STEPS_PER_PAIR = 740
 
-# Kernels whose roofline is HBM bandwidth (every kernel of the registration path: the SL
-# sweeps and the spectral stages, whose tensor-core contractions move far more bytes than
-# their flops need). The network's convolutions are arithmetic-bound.
-HBM_PREFIXES = ("sl_", "pi_", "iota_", "prefilter", "warp_image", "defstate_", "sum_sq_diff",
-                "scale", "accum_", "image_rhs", "cube_", "dot_f2", "maxabs", "finalize")
+# Kernels bound by FP32 arithmetic: the Y/Z contractions of pi and iota (SIMT complex
+# multiply-adds with L2-resident operands) and the network's convolutions. Every other kernel
+# streams fields through HBM: the SL sweeps, the element-wise and reduction kernels, and the x
+# stages of pi / iota, whose tensor-core contractions move far more bytes than their flops need.
+ALU_KERNELS = ("pi_y", "pi_z", "iota_y", "iota_z")
 
 
 def is_hbm_kernel(name):
-    return name.startswith(HBM_PREFIXES)
+    return not (name in ALU_KERNELS or name.startswith("cnn_"))
 
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of

@@ -1,0 +1,76 @@
+"""Host-side logic of the benchmark (no GPU): the clock sampler's parsing of nvidia-smi lines,
+the roofline peaks and their fallback, the kernel classification."""
+import importlib.util
+import os
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+class _Done:
+    def terminate(self):
+        pass
+
+    def wait(self, timeout=None):
+        return 0
+
+
+def test_clock_sampler_takes_the_median_and_collects_active_reasons(bench):
+    s = bench.ClockSampler(0)
+    s.proc = _Done()
+    s.lines = [
+        "0, 2032, 2032, 812.4, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2032, 1099.1, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+        "0, 2010, 2032, 1050.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+        "0, [N/A], 2032, 10.0, 0x0, Not Active, Not Active, Not Active, Not Active",   # skipped
+        "truncated, line",                                                                 # skipped
+    ]
+    out = s.stop()
+    assert out["samples"] == 3
+    assert out["sm_mhz"] == 2010.0 and out["sm_max_mhz"] == 2032.0
+    assert out["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_sampler_flags_thermal_and_hardware_slowdown(bench):
+    s = bench.ClockSampler(0)
+    s.proc = _Done()
+    s.lines = ["0, 1500, 2032, 700, 0x48, Active, Not Active, Active, Not Active"]
+    assert s.stop()["reasons"] == ["hw_slowdown", "sw_thermal_slowdown"]
+
+
+def test_clock_sampler_without_nvidia_smi_says_so(bench):
+    out = bench.ClockSampler(0).stop()
+    assert out["sm_mhz"] is None and out["reasons"] == ["nvidia-smi unavailable"]
+
+
+def test_peaks_come_from_the_measured_file_or_the_stated_fallback(bench, tmp_path, monkeypatch):
+    peaks, source = bench._peaks()
+    if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
+        assert source == "measured" and peaks["hbm_gbs"] > 1000
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    peaks, source = bench._peaks()
+    assert source == "fallback"
+    assert peaks["hbm_gbs"] == 6400.0 and peaks["bf16_tflops"] == 1800.0
+
+
+def test_fp32_simt_peak_follows_the_unit_count_and_clock(bench):
+    assert bench._fp32_simt_peak_tflops(2032.0) == pytest.approx(76.99, abs=0.01)
+    assert bench._fp32_simt_peak_tflops(1016.0) == pytest.approx(76.99 / 2, abs=0.01)
+
+
+def test_kernels_are_classified_by_their_roofline(bench):
+    for name in ("sl_inc_defstate", "sl_gather3_scale", "pi_x_tc", "iota_x_tc", "pi_z_fin",
+                 "accum_JT", "cube_two_level", "dot_f2", "finalize", "spatial_L", "spec_restrict",
+                 "max_norm3", "state_dlam1"):
+        assert bench.is_hbm_kernel(name), name
+    for name in ("pi_y", "pi_z", "iota_y", "iota_z", "cnn_conv", "cnn_wgrad"):
+        assert not bench.is_hbm_kernel(name), name
