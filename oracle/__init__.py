@@ -18,7 +18,9 @@ Modules
             modes, L~^-1 on the rest) and flexible PCG (Secs. 6-7 name it as future work)
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test against a closed
-form, an invariant, a library routine or brute force, except the full registration
-(``gnk.register``), for which no exact answer exists: parity unpinned beyond the pins on
-its parts (objective, gradient-vs-finite-difference, Hessian symmetry, PCG closed form).
+form, an invariant, a library routine or brute force. ``gnk.register`` is pinned as a driver
+on quadratic model problems (each Gauss-Newton step meets its forcing term, the Armijo
+halving lands on the closed-form step, the stop rules), but the registration it produces on
+the LDDMM problem has no exact answer: parity unpinned beyond the pins on its parts
+(objective, gradient-vs-finite-difference, Hessian symmetry, PCG closed form).
 """
