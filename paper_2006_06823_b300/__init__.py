@@ -7,9 +7,11 @@ all arithmetic runs in the library's CUDA kernels. There is no CPU fallback: if 
 library is missing, the first call raises.
 
 Names follow the C entry points without their ``lddmm_`` prefix:
-``bl_project``, ``bl_include``, ``sl_characteristics``, ``sl_transport`` and the context
-methods ``set_images``, ``objective``, ``gradient``, ``hessian_matvec``, ``register``,
-``get_warped``.
+``bl_project``, ``bl_include``, ``sl_characteristics``, ``sl_transport``, ``register_batch``,
+``device_error``, ``selftest_wait``, ``set_workspace_limit``, the context methods
+``set_images``, ``objective``, ``gradient``, ``hessian_matvec``, ``register``,
+``get_warped``, ``jacobian_det``, ``max_displacement``, ``set_option``, ``autotune``,
+``workspace_bytes``, and the warm-start network ``Net``.
 
 Conventions (see the header): images float32 ``[nz, ny, nx]``; vector fields float32
 ``[3, nz, ny, nx]`` (component 0 = x); band-limited cubes complex64 ``[C, K, K, K]``
