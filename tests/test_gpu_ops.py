@@ -81,6 +81,21 @@ def test_characteristics_match_oracle(shape, order, direction):
     assert rel_l2(D, ref) < 2e-6
 
 
+@pytest.mark.parametrize("direction", [1, -1])
+def test_interpolation_cells_of_the_departure_points_are_bit_exact(direction):
+    """Index-valued result: the cell j + floor(D) each departure point falls in equals the
+    oracle's wherever the fraction of D is not within 1e-4 of a cell boundary (the FP32 and
+    FP64 offsets differ by ~1e-5 voxels, so only points that close to a boundary may differ)."""
+    shape = (20, 24, 37)
+    V = synth.random_displacement(shape, seed=15, max_vox=12.0, smooth=3.0)
+    D = L.sl_characteristics(dev(V), 0.2, direction, 1).cpu().numpy().astype(np.float64)
+    ref = SL.departure_offsets(V, 0.2, direction, 1)
+    frac = ref - np.floor(ref)
+    clear = (frac > 1e-4) & (frac < 1 - 1e-4)
+    assert clear.mean() > 0.99
+    assert np.array_equal(np.floor(D)[clear].astype(np.int64), np.floor(ref)[clear].astype(np.int64))
+
+
 @pytest.mark.parametrize("shape", [(16, 16, 16), (20, 24, 37), (33, 40, 64)])
 @pytest.mark.parametrize("order", [1, 3])
 @pytest.mark.parametrize("direction", [1, -1])
