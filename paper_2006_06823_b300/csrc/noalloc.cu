@@ -64,6 +64,11 @@ extern "C" int lddmm_bl_project_noalloc(int nx, int ny, int nz, int K, const flo
         set_error("bl_project_noalloc: grid must be 2..1024 (x, y) and 2..4096 (z) voxels");
         return LDDMM_EINVAL;
     }
+    // the same voxel-count limit as lddmm_bl_project, so both accept the same grids
+    if ((long)nx * ny * nz > 0x7fffffffL / 3) {
+        set_error("bl_project_noalloc: grid too large: nx*ny*nz must stay below 2^31/3 voxels");
+        return LDDMM_EINVAL;
+    }
     if (!f || !c || ncomp < 1) {
         set_error("bl_project_noalloc: null pointer or ncomp < 1");
         return LDDMM_EINVAL;

@@ -47,6 +47,17 @@ def test_standalone_calls_reject_bad_shapes_before_any_device_work():
     assert lib.lddmm_destroy(None) == L.OK
 
 
+@pytest.mark.parametrize("fn", ["lddmm_bl_project", "lddmm_bl_project_noalloc"])
+def test_projections_reject_the_same_oversized_grid(fn):
+    """1024^3 voxels exceed the 2^31/3 voxel limit of the projection; the allocation-free
+    form would otherwise fit its scratch at K = 4, so both must return EINVAL before any
+    device work (on a machine without a GPU any device call would give ECUDA instead)."""
+    lib = L.load()
+    p = ctypes.c_void_p(256)
+    assert getattr(lib, fn)(1024, 1024, 1024, 4, p, 1, p, 0, None) == L.EINVAL
+    assert b"too large" in lib.lddmm_last_error()
+
+
 @pytest.mark.parametrize("prec", [3, 7, -1])
 def test_standalone_spectral_calls_reject_unknown_precision(prec):
     """The stand-alone operators take FP32, BF16X3 or FP32_SIMT (BF16X3_JBF16 is a context
