@@ -149,6 +149,77 @@ def test_option_codes_of_the_binding_follow_the_header():
         "TWO_LEVEL": L.OPT_TWO_LEVEL}
 
 
+_SCALARS = {"int": ctypes.c_int, "long": ctypes.c_long, "long long": ctypes.c_longlong,
+            "unsigned long long": ctypes.c_ulonglong, "double": ctypes.c_double,
+            "float": ctypes.c_float, "char": ctypes.c_char}
+_STRUCTS = {"lddmm_params": L.Params, "lddmm_report": L.Report}
+
+
+def _header_prototypes():
+    """(return type, name, [parameter types]) of every function declared in the header."""
+    import re
+    text = re.sub(r"/\*.*?\*/", "", _header_text(), flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    out = []
+    for m in re.finditer(r"([A-Za-z_][\w\s\*]*?)\b(lddmm_[a-z_]+)\s*\(([^)]*)\)\s*;", text):
+        params = [] if m.group(3).strip() == "void" else [
+            re.sub(r"\b[A-Za-z_]\w*\s*$", "", p).strip() for p in m.group(3).split(",")]
+        out.append((" ".join(m.group(1).split()), m.group(2), params))
+    return out
+
+
+def _type_matches(ctype_decl, t):
+    """Whether the ctypes type t passes a C parameter of type ctype_decl without conversion
+    loss: scalars exactly, pointers as c_void_p, c_char_p (char only) or a POINTER to the
+    pointee's own type (c_void_p for a pointer to a pointer)."""
+    stars = ctype_decl.count("*")
+    base = " ".join(ctype_decl.replace("*", " ").replace("const", " ").split())
+    if stars == 0:
+        return t is _SCALARS[base]
+    if t is ctypes.c_void_p:
+        return True
+    if t is ctypes.c_char_p:
+        return base == "char" and stars == 1
+    pointee = getattr(t, "_type_", None)
+    if not isinstance(pointee, type):
+        return False
+    if stars >= 2:
+        return pointee is ctypes.c_void_p
+    return pointee is _SCALARS.get(base, _STRUCTS.get(base))
+
+
+def test_binding_signatures_follow_the_header_prototypes():
+    """Every declared function has a ctypes signature in the binding whose arity and argument
+    types match the C prototype: an undeclared or mistyped argument would pass a truncated
+    pointer or a misread scalar without any error."""
+    lib = L.load()
+    protos = _header_prototypes()
+    assert sorted(n for _, n, _ in protos) == L.header_functions()
+    bad = []
+    for ret, name, params in protos:
+        fn = getattr(lib, name)
+        args = fn.argtypes
+        if args is None or len(args) != len(params):
+            bad.append((name, "arity", params, args))
+            continue
+        bad += [(name, i, p, a) for i, (p, a) in enumerate(zip(params, args))
+                if not _type_matches(p, a)]
+        if not _type_matches(ret, fn.restype):
+            bad.append((name, "return", ret, fn.restype))
+    assert bad == []
+
+
+def test_signature_check_catches_a_mistyped_argument():
+    """The comparison above is not vacuous: a double where the header has int, an int where
+    it has a pointer and a pointer to the wrong struct are each rejected."""
+    assert _type_matches("int", ctypes.c_int) and not _type_matches("int", ctypes.c_double)
+    assert not _type_matches("const float*", ctypes.c_int)
+    assert _type_matches("lddmm_report*", ctypes.POINTER(L.Report))
+    assert not _type_matches("lddmm_report*", ctypes.POINTER(L.Params))
+    assert _type_matches("lddmm_ctx**", ctypes.POINTER(ctypes.c_void_p))
+    assert not _type_matches("double*", ctypes.POINTER(ctypes.c_int))
+
+
 C_CONSUMER = r"""
 #include <stdio.h>
 #include "lddmm.h"
