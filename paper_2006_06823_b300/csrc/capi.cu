@@ -1357,6 +1357,16 @@ static int check_grid(int nx, int ny, int nz) {
     return LDDMM_OK;
 }
 
+// band accepted by the stand-alone spectral operators (the rule the partial-DFT stages
+// apply), checked before any scratch is taken or any twiddle table is built
+static int check_band(int nx, int ny, int nz, int K) {
+    if (K < 4 || (K & 1) || K > 64 || K > nx || K > ny || K > nz) {
+        set_error("spectral: need even 4 <= K <= min(64, nx, ny, nz)");
+        return LDDMM_EINVAL;
+    }
+    return LDDMM_OK;
+}
+
 // precision forms accepted by the stand-alone spectral operators
 static int check_spectral_precision(int precision) {
     if (precision != LDDMM_PREC_FP32 && precision != LDDMM_PREC_BF16X3 &&
@@ -1372,6 +1382,7 @@ extern "C" {
 int lddmm_bl_project(int nx, int ny, int nz, int K, const float* f, int ncomp, float* c,
                      int precision, void* stream) {
     TRY(check_grid(nx, ny, nz));
+    TRY(check_band(nx, ny, nz, K));
     TRY(check_spectral_precision(precision));
     if (!f || !c || ncomp < 1) { set_error("bl_project: null pointer or ncomp < 1"); return LDDMM_EINVAL; }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -1391,6 +1402,7 @@ int lddmm_bl_project(int nx, int ny, int nz, int K, const float* f, int ncomp, f
 int lddmm_bl_include(int nx, int ny, int nz, int K, const float* c, int ncomp, float* f,
                      int deriv_axis, int bspline, int precision, void* stream) {
     TRY(check_grid(nx, ny, nz));
+    TRY(check_band(nx, ny, nz, K));
     TRY(check_spectral_precision(precision));
     if (!f || !c || ncomp < 1) { set_error("bl_include: null pointer or ncomp < 1"); return LDDMM_EINVAL; }
     if (deriv_axis < -1 || deriv_axis > 2) { set_error("bl_include: deriv_axis must be -1..2"); return LDDMM_EINVAL; }

@@ -58,6 +58,20 @@ def test_projections_reject_the_same_oversized_grid(fn):
     assert b"too large" in lib.lddmm_last_error()
 
 
+@pytest.mark.parametrize("K", [-2, 0, 2, 5, 66, 18])
+def test_spectral_calls_reject_a_bad_band_before_any_device_work(K):
+    """The band must be even with 4 <= K <= min(64, nx, ny, nz) (18 > 16 here): EINVAL from
+    the projection, its allocation-free form and the inclusion before any scratch is taken
+    (on a machine without a GPU any device call would give ECUDA or ENOMEM instead)."""
+    lib = L.load()
+    p = ctypes.c_void_p(256)
+    assert lib.lddmm_bl_project(16, 16, 16, K, p, 1, p, 0, None) == L.EINVAL
+    assert b"K" in lib.lddmm_last_error()
+    assert lib.lddmm_bl_project_noalloc(16, 16, 16, K, p, 1, p, 0, None) == L.EINVAL
+    assert lib.lddmm_bl_include(16, 16, 16, K, p, 1, p, -1, 0, 0, None) == L.EINVAL
+    assert b"K" in lib.lddmm_last_error()
+
+
 @pytest.mark.parametrize("prec", [3, 7, -1])
 def test_standalone_spectral_calls_reject_unknown_precision(prec):
     """The stand-alone operators take FP32, BF16X3 or FP32_SIMT (BF16X3_JBF16 is a context
