@@ -1660,6 +1660,7 @@ int lddmm_register_batch(lddmm_ctx* const* ctxs, float* const* v_inout, int n,
             return LDDMM_EINVAL;
         }
     }
+    if (n == 0) return LDDMM_OK;  // an empty batch: nothing to register, no device work
     int dev = 0;
     LDDMM_CUDA(cudaGetDevice(&dev));
     const int nthreads = std::max(1, std::min(n, max_threads > 0 ? max_threads : 8));

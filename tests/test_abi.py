@@ -84,6 +84,20 @@ def test_standalone_spectral_calls_reject_unknown_precision(prec):
     assert b"precision" in lib.lddmm_last_error()
 
 
+def test_register_batch_validates_its_arrays_and_accepts_an_empty_batch():
+    """An empty batch is OK with no device work; a negative count, NULL arrays for a
+    non-empty batch or a NULL context among them are EINVAL, all before any device call."""
+    lib = L.load()
+    P = ctypes.c_void_p
+    assert lib.lddmm_register_batch(None, None, 0, None, None, 1) == L.OK
+    assert lib.lddmm_register_batch(None, None, -1, None, None, 1) == L.EINVAL
+    assert lib.lddmm_register_batch(None, None, 2, None, None, 1) == L.EINVAL
+    arr = (P * 2)(None, None)
+    reps = (L.Report * 2)()
+    assert lib.lddmm_register_batch(arr, arr, 2, None, reps, 1) == L.EINVAL
+    assert b"NULL" in lib.lddmm_last_error()
+
+
 def test_null_context_is_rejected():
     lib = L.load()
     rep = L.Report()
