@@ -165,6 +165,15 @@ def _f32(t):
     return _ptr(t, torch.float32)
 
 
+def _sized(t, numel, name):
+    """t after checking that it holds exactly ``numel`` elements: the C call reads or writes
+    that many through its pointer, so a smaller tensor would be overrun on the device."""
+    if t.numel() != numel:
+        raise ValueError(f"{name}: expected {numel} elements, got {t.numel()} "
+                         f"(shape {tuple(t.shape)})")
+    return t
+
+
 def _c64(t):
     import torch
     return _ptr(t, torch.complex64)
@@ -180,6 +189,7 @@ def bl_project(f, K, precision=PREC_FP32, out=None):
     C, nz, ny, nx = f.shape
     if out is None:
         out = torch.empty((C, K, K, K), dtype=torch.complex64, device=f.device)
+    _sized(out, C * K ** 3, "bl_project: out")
     _check(load().lddmm_bl_project(nx, ny, nz, K, _f32(f), C, _c64(out), precision, _stream()))
     return out
 
@@ -191,6 +201,7 @@ def bl_project_noalloc(f, K, out, precision=PREC_FP32):
     if f.dim() == 3:
         f = f.unsqueeze(0)
     C, nz, ny, nx = f.shape
+    _sized(out, C * K ** 3, "bl_project_noalloc: out")
     _check(load().lddmm_bl_project_noalloc(nx, ny, nz, K, _f32(f), C, _c64(out), precision,
                                            _stream()))
     return out
@@ -209,6 +220,8 @@ def bl_include(c, shape, deriv_axis=-1, bspline=False, precision=PREC_FP32, out=
     nz, ny, nx = shape
     if out is None:
         out = torch.empty((C, nz, ny, nx), dtype=torch.float32, device=c.device)
+    _sized(c, C * K ** 3, "bl_include: c")
+    _sized(out, C * nz * ny * nx, "bl_include: out")
     _check(load().lddmm_bl_include(nx, ny, nz, K, _c64(c), C, _f32(out), deriv_axis,
                                    1 if bspline else 0, precision, _stream()))
     return out
@@ -220,6 +233,8 @@ def sl_characteristics(vel, dt, direction=FORWARD, interp=INTERP_LINEAR, out=Non
     _, nz, ny, nx = vel.shape
     if out is None:
         out = torch.empty_like(vel)
+    _sized(vel, 3 * nz * ny * nx, "sl_characteristics: vel")
+    _sized(out, 3 * nz * ny * nx, "sl_characteristics: out")
     _check(load().lddmm_sl_characteristics(nx, ny, nz, _f32(vel), float(dt), direction, interp,
                                            _f32(out), _stream()))
     return out
@@ -234,6 +249,8 @@ def sl_transport(vel, field, nt, direction=FORWARD, interp=INTERP_LINEAR, out=No
     C, nz, ny, nx = field.shape
     if out is None:
         out = torch.empty_like(field)
+    _sized(vel, 3 * nz * ny * nx, "sl_transport: vel")
+    _sized(out, C * nz * ny * nx, "sl_transport: out")
     _check(load().lddmm_sl_transport(nx, ny, nz, nt, interp, _f32(vel), _f32(field), C,
                                      direction, _f32(out), _stream()))
     return out[0] if squeeze else out
@@ -255,8 +272,11 @@ class Context:
         self.nt = nt
         self.nonstationary = bool(nonstationary)
         self.spatial = bool(spatial)
-        # velocity-shaped arguments: complex64 cubes, or float32 fields in the spatial form
-        self._vec = _f32 if spatial else _c64
+        # velocity-shaped arguments: complex64 cubes, or float32 fields in the spatial form,
+        # (nt + 1) of them in the non-stationary form
+        self._vec_ptr = _f32 if spatial else _c64
+        self._vec_len = ((nt + 1) if nonstationary else 1) * 3 * (
+            nx * ny * nz if spatial else K ** 3)
         self._h = ctypes.c_void_p()
         _check(load().lddmm_create(ctypes.byref(self.params), _stream(), ctypes.byref(self._h)))
 
@@ -276,6 +296,13 @@ class Context:
 
     def __exit__(self, *exc):
         self.close()
+
+    def _vec(self, t):
+        return self._vec_ptr(_sized(t, self._vec_len, "velocity-shaped argument"))
+
+    def _field(self, t, name):
+        nz, ny, nx = self.shape
+        return _f32(_sized(t, nx * ny * nz, name))
 
     def zeros_cube(self):
         """A zero velocity: [3, K, K, K] complex64 ([3, nz, ny, nx] float32 in the spatial
@@ -350,7 +377,9 @@ class Context:
         if field:
             J = torch.empty(self.shape, dtype=torch.float32, device="cuda") if out is None else out
         rng = (ctypes.c_double * 2)()
-        _check(load().lddmm_jacobian_det(self._h, self._vec(v), _f32(J) if J is not None else None, rng))
+        _check(load().lddmm_jacobian_det(self._h, self._vec(v),
+                                         self._field(J, "jacobian_det: out") if J is not None else None,
+                                         rng))
         return (rng[0], rng[1]), J
 
     def max_displacement(self, v):
@@ -362,7 +391,7 @@ class Context:
     def get_warped(self, out=None):
         import torch
         m = torch.empty(self.shape, dtype=torch.float32, device="cuda") if out is None else out
-        _check(load().lddmm_get_warped(self._h, _f32(m)))
+        _check(load().lddmm_get_warped(self._h, self._field(m, "get_warped: out")))
         return m
 
 
@@ -411,17 +440,26 @@ class Net:
         import torch
         B, d = x.shape[0], self.D // 2
         y = torch.empty((B, 3, d, d, d), dtype=torch.float32, device=x.device) if out is None else out
+        _sized(x, B * 2 * self.D ** 3, "net forward: x")
+        _sized(y, B * 3 * d ** 3, "net forward: out")
         _check(load().lddmm_net_forward(self._h, _f32(x), B, _f32(y)))
         return y
 
     def gradients(self, x, dy, out=None):
         import torch
         g = torch.empty(self.num_params, dtype=torch.float32, device=x.device) if out is None else out
+        B, d = x.shape[0], self.D // 2
+        _sized(x, B * 2 * self.D ** 3, "net gradients: x")
+        _sized(dy, B * 3 * d ** 3, "net gradients: dy")
+        _sized(g, self.num_params, "net gradients: out")
         _check(load().lddmm_net_gradients(self._h, _f32(x), _f32(dy), x.shape[0], _f32(g)))
         return g
 
     def train_step(self, x, target, lr, want_loss=True):
         loss = ctypes.c_double(0.0)
+        B, d = x.shape[0], self.D // 2
+        _sized(x, B * 2 * self.D ** 3, "net train_step: x")
+        _sized(target, B * 3 * d ** 3, "net train_step: target")
         _check(load().lddmm_net_train_step(self._h, _f32(x), _f32(target), x.shape[0],
                                            float(lr), ctypes.byref(loss) if want_loss else None))
         return loss.value if want_loss else None
@@ -431,6 +469,8 @@ class Net:
         nz, ny, nx = I0.shape
         x = torch.empty((2, self.D, self.D, self.D), dtype=torch.float32, device=I0.device) \
             if out is None else out
+        _sized(I1, nx * ny * nz, "net input: I1")
+        _sized(x, 2 * self.D ** 3, "net input: out")
         _check(load().lddmm_net_input(self._h, nx, ny, nz, _f32(I0), _f32(I1), _f32(x)))
         return x
 
@@ -439,6 +479,8 @@ class Net:
         nz, ny, nx = I0.shape
         v = torch.empty((3, K, K, K), dtype=torch.complex64, device=I0.device) \
             if out is None else out
+        _sized(I1, nx * ny * nz, "net warm_start: I1")
+        _sized(v, 3 * K ** 3, "net warm_start: out")
         _check(load().lddmm_net_warm_start(self._h, nx, ny, nz, _f32(I0), _f32(I1), K, _c64(v)))
         return v
 

@@ -337,3 +337,38 @@ def test_wait_selftest_validates_its_bound_before_any_device_work(seconds):
     assert lib.lddmm_selftest_wait(seconds, ctypes.byref(st)) == L.EINVAL
     assert st.value == 7
     assert lib.lddmm_selftest_wait(0.01, None) == L.EINVAL
+
+
+def test_binding_rejects_undersized_and_mismatched_tensors_before_calling_the_library():
+    """The wrappers check every tensor's element count against what the C call reads or
+    writes through its pointer (an undersized ``out`` would be overrun on the device). The
+    check runs before the device check, so CPU tensors exercise it without a GPU."""
+    import torch
+    f = torch.zeros((1, 8, 8, 8))
+    with pytest.raises(ValueError, match="bl_project: out"):
+        L.bl_project(f, 4, out=torch.empty((1, 4, 4, 3), dtype=torch.complex64))
+    with pytest.raises(ValueError, match="bl_project_noalloc: out"):
+        L.bl_project_noalloc(f, 4, out=torch.empty((2, 4, 4), dtype=torch.complex64))
+    with pytest.raises(ValueError, match="bl_include: c"):
+        L.bl_include(torch.zeros((3, 4, 4, 2), dtype=torch.complex64), (8, 8, 8))
+    with pytest.raises(ValueError, match="bl_include: out"):
+        L.bl_include(torch.zeros((3, 4, 4, 4), dtype=torch.complex64), (8, 8, 8),
+                     out=torch.empty((3, 8, 8, 7)))
+    vel = torch.zeros((3, 8, 8, 8))
+    with pytest.raises(ValueError, match="sl_characteristics: vel"):
+        L.sl_characteristics(torch.zeros((2, 8, 8, 8)), 0.1)
+    with pytest.raises(ValueError, match="sl_characteristics: out"):
+        L.sl_characteristics(vel, 0.1, out=torch.empty((3, 8, 8)))
+    with pytest.raises(ValueError, match="sl_transport: vel"):
+        L.sl_transport(torch.zeros((3, 8, 8, 4)), f, 2)
+    with pytest.raises(ValueError, match="sl_transport: out"):
+        L.sl_transport(vel, torch.zeros((2, 8, 8, 8)), 2, out=torch.empty((1, 8, 8, 8)))
+    # a context's velocity-shaped arguments: (nt + 1) cubes in the non-stationary form
+    ctx = object.__new__(L.Context)
+    ctx._vec_ptr, ctx._vec_len = L._c64, 5 * 3 * 4 ** 3
+    with pytest.raises(ValueError, match="velocity-shaped"):
+        ctx._vec(torch.zeros((3, 4, 4, 4), dtype=torch.complex64))
+    # the right count reaches the device check (no GPU here)
+    with pytest.raises(ValueError, match="CUDA tensor"):
+        ctx._vec(torch.zeros((5, 3, 4, 4, 4), dtype=torch.complex64))
+    ctx._h = None
