@@ -315,11 +315,13 @@ class Context:
 
     def set_images(self, I0, I1):
         if I0.is_cuda:
-            _check(load().lddmm_set_images(self._h, _f32(I0), _f32(I1)))
+            _check(load().lddmm_set_images(self._h, self._field(I0, "set_images: I0"),
+                                           self._field(I1, "set_images: I1")))
         else:
             import torch
-            a = I0.to(torch.float32).contiguous()
-            b = I1.to(torch.float32).contiguous()
+            nz, ny, nx = self.shape
+            a = _sized(I0.to(torch.float32).contiguous(), nx * ny * nz, "set_images: I0")
+            b = _sized(I1.to(torch.float32).contiguous(), nx * ny * nz, "set_images: I1")
             _check(load().lddmm_set_images_host(self._h, ctypes.c_void_p(a.data_ptr()),
                                                 ctypes.c_void_p(b.data_ptr())))
 

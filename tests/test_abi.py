@@ -372,3 +372,19 @@ def test_binding_rejects_undersized_and_mismatched_tensors_before_calling_the_li
     with pytest.raises(ValueError, match="CUDA tensor"):
         ctx._vec(torch.zeros((5, 3, 4, 4, 4), dtype=torch.complex64))
     ctx._h = None
+
+
+def test_set_images_checks_both_images_against_the_grid():
+    """Host images are copied by the library for nx*ny*nz floats each: a smaller array would
+    be over-read on the host, so the binding refuses it; the right size reaches the library
+    (here a NULL context, so EINVAL)."""
+    import torch
+    ctx = object.__new__(L.Context)
+    ctx.shape, ctx._h = (4, 5, 6), None
+    with pytest.raises(ValueError, match="set_images: I1"):
+        ctx.set_images(torch.zeros((4, 5, 6)), torch.zeros((4, 5, 5)))
+    with pytest.raises(ValueError, match="set_images: I0"):
+        ctx.set_images(torch.zeros(100, dtype=torch.float64), torch.zeros((4, 5, 6)))
+    with pytest.raises(L.LddmmError) as e:
+        ctx.set_images(torch.zeros((4, 5, 6)), torch.zeros((4, 5, 6), dtype=torch.float64))
+    assert e.value.code == L.EINVAL
