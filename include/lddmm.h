@@ -163,6 +163,8 @@ int lddmm_register(lddmm_ctx* ctx, float* v_inout, const double* g_ref_norms,
  * once into a CUDA graph and replayed for every PCG iteration. g_ref_norms: NULL or n pairs
  * of {||g(0)||_2, ||g(0)||_inf}. reports[i] receives pair i's outcome. Returns the first
  * failure (message names the pair); the other pairs still complete. Synchronises.
+ * The n contexts must be distinct (each is driven by one thread at a time): a context that
+ * appears twice is EINVAL before any device work.
  * n = 0 returns OK without touching the device; n < 0, or NULL arrays with n > 0, EINVAL. */
 int lddmm_register_batch(lddmm_ctx* const* ctxs, float* const* v_inout, int n,
                          const double* g_ref_norms, lddmm_report* reports, int max_threads);

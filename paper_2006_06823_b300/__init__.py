@@ -153,6 +153,11 @@ def _ptr(t, dtype):
     import torch
     if not t.is_cuda:
         raise ValueError("expected a CUDA tensor")
+    # the library launches on the current device's stream (and the projection's scratch and
+    # tensor maps belong to that device): a tensor of another device would be a peer pointer
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"tensor on {t.device}, but the current device is "
+                         f"cuda:{torch.cuda.current_device()}")
     if t.dtype != dtype:
         raise TypeError(f"expected {dtype}, got {t.dtype}")
     if not t.is_contiguous():

@@ -1345,7 +1345,9 @@ struct PoolScratch {
     }
 };
 
-static int check_grid(int nx, int ny, int nz) {
+namespace lddmm {
+
+int check_grid(int nx, int ny, int nz) {
     if (nx < 2 || ny < 2 || nz < 2 || nx > 1024 || ny > 1024 || nz > 4096) {
         set_error("grid must be 2..1024 (x, y) and 2..4096 (z) voxels per axis");
         return LDDMM_EINVAL;
@@ -1359,7 +1361,7 @@ static int check_grid(int nx, int ny, int nz) {
 
 // band accepted by the stand-alone spectral operators (the rule the partial-DFT stages
 // apply), checked before any scratch is taken or any twiddle table is built
-static int check_band(int nx, int ny, int nz, int K) {
+int check_band(int nx, int ny, int nz, int K) {
     if (K < 4 || (K & 1) || K > 64 || K > nx || K > ny || K > nz) {
         set_error("spectral: need even 4 <= K <= min(64, nx, ny, nz)");
         return LDDMM_EINVAL;
@@ -1368,7 +1370,7 @@ static int check_band(int nx, int ny, int nz, int K) {
 }
 
 // precision forms accepted by the stand-alone spectral operators
-static int check_spectral_precision(int precision) {
+int check_spectral_precision(int precision) {
     if (precision != LDDMM_PREC_FP32 && precision != LDDMM_PREC_BF16X3 &&
         precision != LDDMM_PREC_FP32_SIMT) {
         set_error("spectral precision must be LDDMM_PREC_FP32, LDDMM_PREC_BF16X3 or LDDMM_PREC_FP32_SIMT");
@@ -1376,6 +1378,8 @@ static int check_spectral_precision(int precision) {
     }
     return LDDMM_OK;
 }
+
+}  // namespace lddmm
 
 extern "C" {
 
@@ -1651,6 +1655,19 @@ int lddmm_register_batch(lddmm_ctx* const* ctxs, float* const* v_inout, int n,
     if (n < 0 || (n > 0 && (!ctxs || !v_inout || !reports))) {
         set_error("register_batch: null arrays or n < 0");
         return LDDMM_EINVAL;
+    }
+    // one worker thread per pair owns its context (host fields, buffers, graph, stream): the
+    // same context twice would be driven by two threads at once. Compared as pointers, before
+    // any context is read (NULL entries are left to the context check below).
+    if (n > 1) {
+        std::vector<const lddmm_ctx*> sorted;
+        for (int i = 0; i < n; ++i)
+            if (ctxs[i]) sorted.push_back(ctxs[i]);
+        std::sort(sorted.begin(), sorted.end());
+        if (std::adjacent_find(sorted.begin(), sorted.end()) != sorted.end()) {
+            set_error("register_batch: the same context appears more than once");
+            return LDDMM_EINVAL;
+        }
     }
     for (int i = 0; i < n; ++i) {
         int rc = check_ctx(ctxs[i]);

@@ -71,6 +71,13 @@ long twiddle_floats(const Grid& g, int K);
 // Fills `mem` (twiddle_floats floats, device) and points `tw` into it.
 int twiddle_init(const Grid& g, int K, float* mem, Twiddles& tw, cudaStream_t st);
 
+// Argument checks of the stand-alone spectral operators (capi.cu), shared by every entry
+// point that runs bl_project / bl_include so that all accept the same grids, bands and
+// precision forms. Each returns LDDMM_OK or LDDMM_EINVAL with the message set.
+int check_grid(int nx, int ny, int nz);
+int check_band(int nx, int ny, int nz, int K);
+int check_spectral_precision(int precision);
+
 // float2 elements of each of the two scratch buffers that bl_project / bl_include need
 // for `ncomp` components.
 long spectral_scratch_elems(const Grid& g, int K, int ncomp);

@@ -60,27 +60,15 @@ using namespace lddmm;
 
 extern "C" int lddmm_bl_project_noalloc(int nx, int ny, int nz, int K, const float* f, int ncomp,
                                         float* c, int precision, void* stream) {
-    if (nx < 2 || ny < 2 || nz < 2 || nx > 1024 || ny > 1024 || nz > 4096) {
-        set_error("bl_project_noalloc: grid must be 2..1024 (x, y) and 2..4096 (z) voxels");
-        return LDDMM_EINVAL;
-    }
-    // the same voxel-count limit as lddmm_bl_project, so both accept the same grids
-    if ((long)nx * ny * nz > 0x7fffffffL / 3) {
-        set_error("bl_project_noalloc: grid too large: nx*ny*nz must stay below 2^31/3 voxels");
-        return LDDMM_EINVAL;
-    }
+    // the checks of lddmm_bl_project itself, so that both accept the same arguments
+    int rc = check_grid(nx, ny, nz);
+    if (rc) return rc;
+    rc = check_band(nx, ny, nz, K);
+    if (rc) return rc;
+    rc = check_spectral_precision(precision);
+    if (rc) return rc;
     if (!f || !c || ncomp < 1) {
         set_error("bl_project_noalloc: null pointer or ncomp < 1");
-        return LDDMM_EINVAL;
-    }
-    if (K < 4 || (K & 1) || K > 64 || K > nx || K > ny || K > nz) {
-        set_error("bl_project_noalloc: need even 4 <= K <= min(64, nx, ny, nz)");
-        return LDDMM_EINVAL;
-    }
-    if (precision != LDDMM_PREC_FP32 && precision != LDDMM_PREC_BF16X3 &&
-        precision != LDDMM_PREC_FP32_SIMT) {
-        set_error("bl_project_noalloc: precision must be LDDMM_PREC_FP32, LDDMM_PREC_BF16X3 or "
-                  "LDDMM_PREC_FP32_SIMT");
         return LDDMM_EINVAL;
     }
     const Grid g{nx, ny, nz};
@@ -97,7 +85,7 @@ extern "C" int lddmm_bl_project_noalloc(int nx, int ny, int nz, int K, const flo
         return LDDMM_EINVAL;
     }
     void* base = nullptr;
-    int rc = scratch_address(&base);
+    rc = scratch_address(&base);
     if (rc) return rc;
     unsigned char* p = static_cast<unsigned char*>(base);
     float* twm = reinterpret_cast<float*>(p);

@@ -98,6 +98,20 @@ def test_register_batch_validates_its_arrays_and_accepts_an_empty_batch():
     assert b"NULL" in lib.lddmm_last_error()
 
 
+def test_register_batch_rejects_a_context_given_twice():
+    """Each pair's context is driven by one worker thread; the same handle twice in one batch
+    is EINVAL, decided on the pointers alone before any context is read or device call made
+    (the fake handles here are never dereferenced)."""
+    lib = L.load()
+    P = ctypes.c_void_p
+    a, b = P(0x1000), P(0x2000)
+    ctxs = (P * 3)(a, b, a)
+    vs = (P * 3)(P(256), P(512), P(768))
+    reps = (L.Report * 3)()
+    assert lib.lddmm_register_batch(ctxs, vs, 3, None, reps, 2) == L.EINVAL
+    assert b"more than once" in lib.lddmm_last_error()
+
+
 def test_null_context_is_rejected():
     lib = L.load()
     rep = L.Report()
