@@ -58,6 +58,14 @@ def is_hbm_kernel(name):
     return not (name in ALU_KERNELS or name.startswith("cnn_"))
 
 
+# Bytes per voxel of the SL kernels as the hot-path table of the survey counts them (state a3
+# 20 B; adjoint and BL vector steps 36 B; incremental deformation state a7 84 B), beside the
+# library's own algorithmic count (KTRACE): the Heun step of the incremental deformation state
+# also gathers the previous right-hand side F_j at the departure point and writes F_{j+1}
+# (+12 B each), which the survey's 84 B omit, so the library counts 108 B there.
+SURVEY_BYTES_PER_VOXEL = {"sl_gather": 20.0, "sl_gather3_scale": 36.0, "sl_gather3_add": 36.0,
+                          "sl_inc_defstate": 84.0}
+
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) from one ncu capture of
 # the kernel, scaled by voxels to the 192x224x192 launch where the capture ran a smaller grid
 # (profiles/k_inc_defstate_128x160x128.md: 263.7 MB at 128x160x128 -> 830.6 MB); kernels
@@ -214,6 +222,7 @@ def run_b300(args):
         sampler.start()
     launches0 = L.launch_count()
     step_ms = []
+    histories = []
     barrier(world)
     torch.cuda.synchronize()
     for _ in range(args.steps):
@@ -228,6 +237,7 @@ def run_b300(args):
         torch.cuda.nvtx.range_pop()
         step_ms.append(e0.elapsed_time(e1))
         reports.append(rep)
+        histories.append(ctx.history())       # host-only read of the per-iterate record
     torch.cuda.synchronize()
     barrier(world)
     launches = L.launch_count() - launches0
@@ -278,6 +288,9 @@ def run_b300(args):
         e2e_s.append(time.perf_counter() - t0)
     e2e_total = max_over_ranks(sum(e2e_s), world)
     ctx.close()
+    # ---- the same pair with the Gauss-Newton cap raised to LONG_GN: where the residual
+    # plateaus and when (if ever) it reaches 1e-3 (outside the timed region)
+    long_run = measure_long_run(L, torch, I0d, I1d, flush) if args.forms and rank == 0 else None
     forms = measure_forms(L, torch, I0d, I1d, stream, flush) if args.forms and rank == 0 else None
     warm = measure_warm_start(L, torch) if args.forms and rank == 0 else None
 
@@ -298,7 +311,17 @@ def run_b300(args):
         pk = _fp32_simt_peak_tflops(peaks.get("sm_max_mhz", 2032.0))
         roof = {"bound": "alu", "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
                 "frac": achieved / pk}
-    roof.update({"kernel": name, "traffic": NCU_TRAFFIC_PER_LAUNCH.get(name), "peak_source": peak_src,
+    traffic = NCU_TRAFFIC_PER_LAUNCH.get(name)
+    if roof["bound"] == "hbm":
+        avg_s = avg_ms * 1e-3
+        if name in SURVEY_BYTES_PER_VOXEL:
+            ach_s = SURVEY_BYTES_PER_VOXEL[name] * nx * ny * nz / avg_s / 1e9
+            roof["frac_survey"] = ach_s / hbm
+            roof["bytes_per_voxel"] = {"library": kt["bytes"] / kt["launches"] / (nx * ny * nz),
+                                       "survey": SURVEY_BYTES_PER_VOXEL[name]}
+        if traffic:
+            roof["dram_frac"] = traffic / avg_s / 1e9 / hbm
+    roof.update({"kernel": name, "traffic": traffic, "peak_source": peak_src,
                  "avg_launch_us": avg_ms * 1e3, "launches": kt["launches"],
                  "share": kt["ms"] / sum(v["ms"] for v in trace.values())})
     out = {
@@ -311,6 +334,12 @@ def run_b300(args):
                    "pairs_per_step": world,
                    "l2": "flushed (256 MB write) between timed steps; working set ~5 GB"},
         "residual_reached": last["grad_rel_l2"] <= GTOL,
+        "value_is": (f"time to the relative residual {GTOL:g}" if last["grad_rel_l2"] <= GTOL else
+                     f"time to the {MAX_GN}-GN cap of the workload (relative residual "
+                     f"{last['grad_rel_l2']:.3g} there; {GTOL:g} not reached)"),
+        "time_to_residual_s": time_to_residual(histories),
+        "residual_trajectory": [[round(h["t"], 5), h["residual"], int(h["pcg"])]
+                                for h in histories[-1]],
         "report": dict({k: last[k] for k in ("gn_iters", "pcg_iters_total", "stop_reason", "solves",
                                              "E0", "E", "grad_rel_l2", "grad_rel_inf", "mse_rel")},
                        jacobian_det_min=jac_range[0], jacobian_det_max=jac_range[1],
@@ -327,11 +356,57 @@ def run_b300(args):
     }
     if forms is not None:
         out["forms"] = forms
+    if long_run is not None:
+        out["long_run"] = long_run
     if warm is not None:
         out["chosen_form"] = warm
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(steps_per_pair=last["solves"] * NT, samples=1)
     return out
+
+
+RESIDUAL_LEVELS = (1e-1, 1e-2, 1e-3)
+LONG_GN = 40
+
+
+def first_time_at(hist, level):
+    """Seconds from the start of the registration to the first Gauss-Newton iterate whose
+    relative residual ||g||/||g_ref|| is at or below `level` (None if none is)."""
+    for h in hist:
+        if h["residual"] <= level:
+            return h["t"]
+    return None
+
+
+def time_to_residual(histories):
+    """Mean over the timed registrations of the time to each residual level (None where a
+    registration never reached it), with the smallest residual reached."""
+    out = {}
+    for lv in RESIDUAL_LEVELS:
+        ts = [first_time_at(h, lv) for h in histories]
+        out[f"{lv:g}"] = statistics.mean(ts) if all(t is not None for t in ts) else None
+    out["min_residual"] = min(min(x["residual"] for x in h) for h in histories)
+    return out
+
+
+def measure_long_run(L, torch, I0d, I1d, flush):
+    """The bench pair registered once more with the Gauss-Newton cap raised to LONG_GN (all
+    else as the workload): the residual trajectory shows whether and when 1e-3 is reached."""
+    nz, ny, nx = SHAPE
+    ctx = L.Context(nx, ny, nz, K, nt=NT, variant=L.V_DEFSTATE, interp=L.INTERP_LINEAR,
+                    alpha=ALPHA, s=S_EXP, sigma2=SIGMA2, max_gn=LONG_GN, max_pcg=MAX_PCG,
+                    gtol=GTOL)
+    ctx.set_images(I0d, I1d)
+    flush.fill_(1.0)
+    torch.cuda.synchronize()
+    _, rep = ctx.register()
+    hist = ctx.history()
+    ctx.close()
+    return {"max_gn": LONG_GN, "gn_iters": rep["gn_iters"], "pcg_iters": rep["pcg_iters_total"],
+            "stop_reason": rep["stop_reason"], "E": rep["E"], "seconds": rep["seconds"],
+            "time_to_residual_s": time_to_residual([hist]),
+            "trajectory": [[round(h["t"], 5), h["residual"], int(h["pcg"]), h["E"]]
+                           for h in hist]}
 
 
 # name, variant, interpolation, precision, non-stationary, spatial domain
@@ -370,8 +445,10 @@ def measure_forms(L, torch, I0d, I1d, stream, flush):
         _, rep = ctx.register()
         e1.record(stream)
         e1.synchronize()
+        hist = ctx.history()
         ctx.close()
         res[name] = {"s_per_pair": e0.elapsed_time(e1) / 1e3, "gn_iters": rep["gn_iters"],
+                     "time_to_residual_s": time_to_residual([hist]),
                      "pcg_iters": rep["pcg_iters_total"], "E": rep["E"],
                      "coarse_pcg_iters": rep["pcg_inner_total"],
                      "grad_rel_l2": rep["grad_rel_l2"],
@@ -448,48 +525,138 @@ def measure_warm_start(L, torch):
             "chosen": "network warm start + LDDMM_PREC_BF16X3_JBF16 + lddmm_register_batch"}
 
 
-def cpu_baseline(steps_per_pair, samples=1):
-    """The FP64 oracle timed on one BL SL-RK step of the deformation state at full size
-    (iota of 3 components, trilinear gather, pi), extrapolated to a registration."""
-    import numpy as np
-    from oracle import sl as SL
-    from oracle import spectral as S
+ORACLE_GB_PER_REPLICA = 3.0     # peak host memory of one oracle step at 192x224x192 (~1.9 GB)
+
+
+def _oracle_step_inputs():
+    """Seeded inputs of the oracle's one-step sample (a BL SL-RK step of the deformation
+    state at the workload's grid)."""
     from paper_2006_06823_b300 import synth
-    nz, ny, nx = SHAPE
-    rng = synth.rng(7)
+    r = synth.rng(7)
     u = synth.random_velocity_coeffs(K, K, seed=8) * 0.05
     D = synth.random_displacement(SHAPE, seed=9, max_vox=4.0, smooth=2.0)
-    W = rng.standard_normal((3,) + SHAPE) * 1e-3
+    W = r.standard_normal((3,) + SHAPE) * 1e-3
+    return u, D, W
+
+
+def _oracle_step(inputs):
+    """One BL SL-RK step by the FP64 oracle: iota of 3 components, trilinear Heun gather, pi."""
+    from oracle import sl as SL
+    u, D, W = inputs
+    SL.bl_heun_source_step(u, D, W, W, 0.1, 1, SHAPE, K)
+
+
+def _oracle_replica(shape, n_warm, n_timed, barriers, queue):
+    """One replica of the sample in a spawned process: inputs built, n_warm untimed steps,
+    then (all replicas together) n_timed timed steps; reports (start, end) of the timed ones
+    in wall-clock time."""
+    global SHAPE
+    SHAPE = tuple(shape)
+    inputs = _oracle_step_inputs()
+    barriers[0].wait()
+    for _ in range(n_warm):
+        _oracle_step(inputs)
+    barriers[1].wait()
+    t0 = time.time()
+    for _ in range(n_timed):
+        _oracle_step(inputs)
+    queue.put((t0, time.time()))
+
+
+def _oracle_parallel(nproc, warm=0, timed=None):
+    """Wall time of `timed` oracle steps (default: one per replica) spread over nproc
+    concurrent replica processes (started with spawn), after `warm` untimed steps spread
+    the same way. Returns (wall seconds, replicas used)."""
+    import multiprocessing as mp
+    timed = nproc if timed is None else timed
+    nproc = max(1, min(nproc, max(timed, 1)))
+    share = lambda n, i: n // nproc + (1 if i < n % nproc else 0)
+    ctx = mp.get_context("spawn")
+    barriers = (ctx.Barrier(nproc), ctx.Barrier(nproc))
+    queue = ctx.Queue()
+    procs = [ctx.Process(target=_oracle_replica,
+                         args=(SHAPE, share(warm, i), share(timed, i), barriers, queue))
+             for i in range(nproc)]
+    for pr in procs:
+        pr.start()
+    spans = [queue.get(timeout=3600) for _ in procs]
+    for pr in procs:
+        pr.join(timeout=60)
+    return max(t1 for _, t1 in spans) - min(t0 for t0, _ in spans), nproc
+
+
+def _host_replicas():
+    """Replicas the host can run at once: one per core, bounded by the available memory."""
+    ncpu = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else os.cpu_count()
+    try:
+        import psutil
+        mem_gb = psutil.virtual_memory().available / 1e9
+        return max(1, min(ncpu, int(mem_gb * 0.8 / ORACLE_GB_PER_REPLICA))), ncpu
+    except Exception:
+        return max(1, min(ncpu, 4)), ncpu
+
+
+def cpu_baseline(steps_per_pair, samples=1, parallel=True):
+    """The FP64 oracle timed on one BL SL-RK step of the deformation state at full size
+    (iota of 3 components, trilinear gather, pi), extrapolated to a registration: on one
+    core, and as P concurrent replicas on the host's cores (independent pairs, one per core,
+    the way a CPU machine would serve many registrations; P bounded by the memory)."""
+    nz, ny, nx = SHAPE
+    inputs = _oracle_step_inputs()
     ts = []
     for _ in range(samples):
         t0 = time.perf_counter()
-        SL.bl_heun_source_step(u, D, W, W, 0.1, 1, SHAPE, K)
+        _oracle_step(inputs)
         ts.append(time.perf_counter() - t0)
     step_s = min(ts)
-    return {"value": step_s * steps_per_pair, "unit": "s/pair", "cores": 1, "kind": "oracle",
-            "sample": (f"one BL SL-RK step (iota x3, trilinear gather, pi x3) at 192x224x192 "
-                       f"in FP64 numpy = {step_s:.2f} s, x {steps_per_pair} steps per "
-                       f"registration (the GPU path's count on this workload)"),
-            "voxel_steps_per_s": nx * ny * nz / step_s}
+    single = {"value": step_s * steps_per_pair, "unit": "s/pair", "cores": 1,
+              "step_s": step_s, "voxel_steps_per_s": nx * ny * nz / step_s}
+    P, ncpu = _host_replicas() if parallel else (1, 1)
+    if P > 1:
+        wall, P = _oracle_parallel(P)
+        per_step = wall / P
+        value, cores = per_step * steps_per_pair, P
+        sample = (f"one BL SL-RK step (iota x3, trilinear gather, pi x3) at {nx}x{ny}x{nz} in "
+                  f"FP64 numpy, {P} concurrent replicas on {ncpu} host cores: {wall:.2f} s wall "
+                  f"= {per_step:.2f} s per step per pair; single core {step_s:.2f} s; x "
+                  f"{steps_per_pair} steps per registration (the GPU path's count)")
+    else:
+        per_step, value, cores = step_s, single["value"], 1
+        sample = (f"one BL SL-RK step (iota x3, trilinear gather, pi x3) at {nx}x{ny}x{nz} "
+                  f"in FP64 numpy = {step_s:.2f} s on one core, x {steps_per_pair} steps per "
+                  f"registration (the GPU path's count on this workload)")
+    return {"value": value, "unit": "s/pair", "cores": cores, "host_cores": ncpu,
+            "kind": "oracle", "sample": sample, "voxel_steps_per_s": nx * ny * nz / per_step,
+            "single_core": single}
 
 
 def run_reference(args):
+    """The FP64 oracle on the host cores: the one-step sample of the workload (a BL SL-RK step
+    of the deformation state at 192x224x192), `warmup` untimed and `steps` timed samples spread
+    over concurrent replica processes (one per core, bounded by memory), extrapolated to a
+    registration by the GPU path's step count."""
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return None
     steps_per_pair = REF_STEPS_PER_PAIR
-    t0 = time.perf_counter()
-    vals = []
-    for i in range(args.warmup + args.steps):
-        cb = cpu_baseline(steps_per_pair, samples=1)
-        if i >= args.warmup:
-            vals.append(cb["value"])
-    value = statistics.mean(vals)
-    cb["value"] = value
+    nz, ny, nx = SHAPE
+    P, ncpu = _host_replicas()
+    t_start = time.perf_counter()
+    wall, used = _oracle_parallel(P, warm=args.warmup, timed=args.steps)
+    per_step = wall / args.steps
+    value = per_step * steps_per_pair
+    cb = {"value": value, "unit": "s/pair", "cores": used, "host_cores": ncpu, "kind": "oracle",
+          "sample": (f"{args.steps} timed (+{args.warmup} untimed) one-step samples (BL SL-RK step "
+                     f"of the deformation state: iota x3, trilinear gather, pi x3, FP64 numpy, "
+                     f"{nx}x{ny}x{nz}) over {used} concurrent replica processes on {ncpu} host "
+                     f"cores: {wall:.2f} s wall = {per_step:.2f} s per pair-step, x "
+                     f"{steps_per_pair} steps per registration"),
+          "voxel_steps_per_s": nx * ny * nz / per_step}
     return {"metric": METRIC, "value": value, "unit": "s/pair", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": (time.perf_counter() - t0) * 1e3 / (args.steps + args.warmup),
+            "ms_per_step": wall * 1e3 / args.steps,
+            "wall_s": time.perf_counter() - t_start,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference", "config": {"workload": WORKLOAD},
             "cpu_baseline": cb,

@@ -156,6 +156,17 @@ int lddmm_hessian_matvec(lddmm_ctx* ctx, const float* v, const float* dv, float*
 int lddmm_register(lddmm_ctx* ctx, float* v_inout, const double* g_ref_norms,
                    lddmm_report* report);
 
+/* Convergence history of the last lddmm_register (or of this context's pair in
+ * lddmm_register_batch): one record per Gauss-Newton iterate n = 0 .. gn_iters, five
+ * doubles each: {seconds since the call began (host clock, read once the iterate's gradient
+ * norm is on the host, i.e. after its device work finished), ||g_n||_2 / ||g_ref||_2 (the
+ * residual of the stopping test, Sec. 4.3), E(v~_n), PCG iterations so far, PDE solves so
+ * far}. The time-to-residual of a threshold is the first record at or below it. Writes
+ * min(cap, available) records to out (host, 5 * cap doubles) and the number available to
+ * *count (0 before the first registration). NULL ctx or count, cap < 0, or NULL out with
+ * cap > 0: EINVAL. Host-only; never touches the device. */
+int lddmm_get_history(lddmm_ctx* ctx, double* out, int cap, int* count);
+
 /* Batched form (no counterpart in the paper's text; it serves many independent pairs).
  * Registers n pairs, each with its own context (created on the current device, ideally each
  * bound to its own stream so that their kernels overlap), from up to max_threads host

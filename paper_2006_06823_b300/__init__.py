@@ -10,7 +10,7 @@ Names follow the C entry points without their ``lddmm_`` prefix:
 ``bl_project``, ``bl_include``, ``sl_characteristics``, ``sl_transport``, ``register_batch``,
 ``device_error``, ``selftest_wait``, ``set_workspace_limit``, the context methods
 ``set_images``, ``objective``, ``gradient``, ``hessian_matvec``, ``register``,
-``get_warped``, ``jacobian_det``, ``max_displacement``, ``set_option``, ``autotune``,
+``get_warped``, ``history``, ``jacobian_det``, ``max_displacement``, ``set_option``, ``autotune``,
 ``workspace_bytes``, and the warm-start network ``Net``.
 
 Conventions (see the header): images float32 ``[nz, ny, nx]``; vector fields float32
@@ -81,6 +81,7 @@ def _declare(lib):
         "lddmm_register": (_I, [_P, _P, _P, ctypes.POINTER(Report)]),
         "lddmm_get_warped": (_I, [_P, _P]),
         "lddmm_jacobian_det": (_I, [_P, _P, _P, ctypes.POINTER(_D)]),
+        "lddmm_get_history": (_I, [_P, ctypes.POINTER(_D), _I, ctypes.POINTER(_I)]),
         "lddmm_max_displacement": (_I, [_P, _P, ctypes.POINTER(_D)]),
         "lddmm_bl_project": (_I, [_I, _I, _I, _I, _P, _I, _P, _I, _P]),
         "lddmm_bl_project_noalloc": (_I, [_I, _I, _I, _I, _P, _I, _P, _I, _P]),
@@ -359,6 +360,17 @@ class Context:
             ref = (ctypes.c_double * 2)(*g_ref_norms)
         _check(load().lddmm_register(self._h, self._vec(v), ref, ctypes.byref(rep)))
         return v, rep.as_dict()
+
+    def history(self):
+        """Convergence history of the last registration (lddmm_get_history): a list of dicts
+        per Gauss-Newton iterate with ``t`` (seconds since the call began), ``residual``
+        (||g||_2 / ||g_ref||_2), ``E``, ``pcg`` and ``solves`` (cumulative)."""
+        n = ctypes.c_int(0)
+        _check(load().lddmm_get_history(self._h, None, 0, ctypes.byref(n)))
+        buf = (ctypes.c_double * (5 * max(n.value, 1)))()
+        _check(load().lddmm_get_history(self._h, buf, n.value, ctypes.byref(n)))
+        keys = ("t", "residual", "E", "pcg", "solves")
+        return [{k: buf[5 * i + j] for j, k in enumerate(keys)} for i in range(n.value)]
 
     def set_option(self, option, value):
         _check(load().lddmm_set_option(self._h, option, int(value)))

@@ -13,6 +13,7 @@
 #include "lddmm.h"
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <chrono>
 #include <mutex>
@@ -99,6 +100,9 @@ struct lddmm_ctx {
     bool have_images = false;
     // device bytes of the context's own allocations (checked against the workspace limit)
     long long ws_bytes = 0;
+    // convergence history of the last registration: per Gauss-Newton iterate {seconds since
+    // the call began, ||g||_2 / ||g_ref||_2, E, PCG iterations so far, solves so far}
+    std::vector<std::array<double, 5>> hist;
 };
 
 // Process-wide cap on the device bytes one context may allocate (0: none).
@@ -961,6 +965,13 @@ static int register_impl(lddmm_ctx* c, float2* v_io, const double* gref_in, lddm
     if (!(gref2 > 0)) gref2 = 1.0;
     if (!(grefi > 0)) grefi = 1.0;
     rep->E0 = E;
+    c->hist.clear();
+    auto record = [&](double Ecur) {
+        // taken after the iterate's gradient norm reached the host, so the device is done
+        const double t = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+        c->hist.push_back({t, gn / gref2, Ecur, (double)rep->pcg_iters_total, (double)c->solves});
+    };
+    record(E);
     int stop = LDDMM_STOP_MAXIT;
     int gn_iters = 0;
     for (int it = 0; it < c->p.max_gn; ++it) {
@@ -1001,6 +1012,7 @@ static int register_impl(lddmm_ctx* c, float2* v_io, const double* gref_in, lddm
         TRY(gradient_impl(c, vtr, true, g, &E, &Er, &Ed));
         gn = std::sqrt(dot_host(c, g, g, &rc));
         TRY(rc);
+        record(E);
     }
     if (stop == LDDMM_STOP_MAXIT && gn / gref2 <= c->p.gtol) stop = LDDMM_STOP_GTOL;
     // if the line search failed, the state in the buffers belongs to a rejected trial
@@ -1263,6 +1275,19 @@ int lddmm_hessian_matvec(lddmm_ctx* c, const float* v, const float* dv, float* H
 int lddmm_register(lddmm_ctx* c, float* v_inout, const double* g_ref_norms, lddmm_report* rep) {
     if (!v_inout || !rep) { set_error("v_inout or report is NULL"); return LDDMM_EINVAL; }
     CTX_CALL(c, register_impl(c, reinterpret_cast<float2*>(v_inout), g_ref_norms, rep));
+}
+
+int lddmm_get_history(lddmm_ctx* c, double* out, int cap, int* count) {
+    if (!c) { set_error("context is NULL"); return LDDMM_EINVAL; }
+    if (!count || cap < 0 || (cap > 0 && !out)) {
+        set_error("get_history: null count, cap < 0, or null out with cap > 0");
+        return LDDMM_EINVAL;
+    }
+    const int n = (int)c->hist.size();
+    for (int i = 0; i < std::min(n, cap); ++i)
+        for (int k = 0; k < 5; ++k) out[5 * i + k] = c->hist[i][k];
+    *count = n;
+    return LDDMM_OK;
 }
 
 int lddmm_jacobian_det(lddmm_ctx* c, const float* v, float* J, double* range) {

@@ -317,6 +317,7 @@ def test_every_context_call_rejects_a_null_context_before_any_device_work():
         lambda: lib.lddmm_jacobian_det(None, p, None, ctypes.byref(d)),
         lambda: lib.lddmm_max_displacement(None, p, ctypes.byref(d)),
         lambda: lib.lddmm_get_warped(None, p),
+        lambda: lib.lddmm_get_history(None, None, 0, ctypes.byref(ctypes.c_int(0))),
         lambda: lib.lddmm_set_option(None, L.OPT_TWO_LEVEL, 2),
         lambda: lib.lddmm_autotune(None, None, None),
     ]

@@ -74,3 +74,21 @@ def test_kernels_are_classified_by_their_roofline(bench):
         assert bench.is_hbm_kernel(name), name
     for name in ("pi_y", "pi_z", "iota_y", "iota_z", "cnn_conv", "cnn_wgrad"):
         assert not bench.is_hbm_kernel(name), name
+
+
+def test_time_to_residual_takes_the_first_iterate_at_or_below_each_level(bench):
+    h1 = [{"t": 0.0, "residual": 1.0}, {"t": 0.5, "residual": 0.08},
+          {"t": 1.0, "residual": 0.009}, {"t": 1.5, "residual": 0.004}]
+    h2 = [{"t": 0.0, "residual": 1.0}, {"t": 0.7, "residual": 0.1},
+          {"t": 1.2, "residual": 0.01}, {"t": 1.9, "residual": 0.0009}]
+    out = bench.time_to_residual([h1, h2])
+    assert out["0.1"] == pytest.approx((0.5 + 0.7) / 2)
+    assert out["0.01"] == pytest.approx((1.0 + 1.2) / 2)
+    assert out["0.001"] is None               # h1 never reaches it: no mean over a subset
+    assert out["min_residual"] == 0.0009
+    assert bench.first_time_at(h2, 1e-3) == 1.9
+
+
+def test_host_replicas_are_bounded_by_cores_and_memory(bench):
+    P, ncpu = bench._host_replicas()
+    assert 1 <= P <= ncpu
