@@ -52,6 +52,8 @@ struct Grid {
     __host__ __device__ long ntot() const { return (long)nx * ny * nz; }
 };
 
+constexpr int kMaxIotaYBlocks = 8;   // 2 ny / 256 rounded up, ny <= 1024
+
 // Twiddle tables [K][n] per axis: cos/sin(2 pi k j / n) for k = slot - K/2, FP64-evaluated,
 // stored FP32. All six tables sit in one allocation of table_floats(grid, K) floats.
 struct Twiddles {
@@ -66,6 +68,13 @@ struct Twiddles {
     // Y/Z-stage contraction matrices, complex [q][p] (p fastest): mpy[y][jy] = e^{-i ky y},
     // miy[jy][y] = e^{+i ky y} (0 for jy = 0), mpz[z][jz] = e^{-i kz z}
     const float2 *mpy, *miy, *mpz;
+    // Y stages on the tensor cores (tc_y): real W matrices with (cos, sin) row pairs as operand
+    // images per precision form: pi, W[2 jy + {0, 1}][y] = {cos, sin}(ky y 2pi/ny) (N = 2K,
+    // kdim = ny); iota in iy_blocks blocks of iy_nyb positions, W[2 y + {0, 1}][jy] = the same
+    // (0 for jy = 0; N = 2 iy_nyb, kdim = K)
+    bool tc_y;
+    int iy_blocks, iy_nyb;
+    const unsigned char *wpy_img[2], *wiy_img[2][kMaxIotaYBlocks];
 };
 long twiddle_floats(const Grid& g, int K);
 // Fills `mem` (twiddle_floats floats, device) and points `tw` into it.
@@ -82,11 +91,22 @@ int check_spectral_precision(int precision);
 // for `ncomp` components.
 long spectral_scratch_elems(const Grid& g, int K, int ncomp);
 
-// Tensor-core row GEMM OUT[row][n] = sum_k IN[row][k] W[n][k] (tc_rowgemm.cu).
-bool tc_rowgemm_supported(int N, int kdim, long rows, const void* in, long in_row_floats);
+// Tensor-core row GEMM OUT[row][n] = sum_k IN[row][k] W[n][k] (tc_rowgemm.cu). epi selects
+// the store: 0 row-major OUT[comp][row in comp][n] (rpc rows per component, component stride
+// comp_stride); 1 transposed per slab of rpc rows, OUT[slab][n][row in slab]; 2 / 3 complex
+// completion of a real-GEMM complex contraction (rows: (Re, Im) pairs of `lines` complex lines
+// per slab of rpc = 2 lines rows; W rows: (cos, sin) pairs), writing interleaved complex
+// OUT[slab][p0 + p][line] (ptot positions per slab) with e^{-i} (2) or e^{+i} (3) phases.
+// prec < 0 in the support test asks for both precision forms.
+bool tc_rowgemm_supported(int N, int kdim, long rows, const void* in, long in_row_floats,
+                          int epi = 0, int prec = -1);
 int tc_rowgemm(const float* in, long rows, int kdim, long in_row_floats, const unsigned char* W,
                int N, int prec, float* out, long rpc, long comp_stride, int n_out,
                const char* trace_name, double trace_bytes, cudaStream_t st);
+int tc_rowgemm_ex(const float* in, long rows, int kdim, long in_row_floats, const unsigned char* W,
+                  int N, int prec, int epi, float* out, long rpc, long comp_stride, int n_out,
+                  int ptot, int p0, int lines, const char* trace_name, double trace_bytes,
+                  cudaStream_t st);
 long tc_wimage_bytes(int N, int kdim);
 int tc_build_wimage(const float* W, int N, int kdim, int prec, unsigned char* img,
                     cudaStream_t st);

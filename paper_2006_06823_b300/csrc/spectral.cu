@@ -21,6 +21,39 @@ namespace lddmm {
 
 static inline int cdiv(long a, long b) { return (int)((a + b - 1) / b); }
 
+// Split of iota's Y stage into blocks of nyb positions (2 nyb <= 256 columns, nyb a multiple of
+// 8 so that N = 2 nyb is a multiple of 16); false if ny has no such split.
+static bool iota_y_blocks(int ny, int* nblk, int* nyb) {
+    for (int b = (2 * ny + 255) / 256; b <= kMaxIotaYBlocks; ++b)
+        if (ny % (8 * b) == 0) {
+            *nblk = b;
+            *nyb = ny / b;
+            return true;
+        }
+    return false;
+}
+
+// The Y stages run on the tensor cores when both precision forms fit: W rows 2K (pi) and the
+// (cos, sin) pairs of iota's positions, K-major operand rows of ny and K floats (16-B
+// aligned rows), even row counts for the complex completion.
+static bool tc_y_possible(const Grid& g, int K) {
+    int nb, nyb;
+    if ((K % 8) != 0 || (g.ny % 4) != 0 || !iota_y_blocks(g.ny, &nb, &nyb)) return false;
+    const void* aligned = reinterpret_cast<const void*>(uintptr_t(256));
+    return tc_rowgemm_supported(2 * K, g.ny, 2, aligned, g.ny, 2) &&
+           tc_rowgemm_supported(2 * nyb, K, 2, aligned, K, 3) &&
+           tc_rowgemm_supported(K, g.nx, 2, aligned, g.nx, 1);
+}
+
+static long ytables_floats(const Grid& g, int K) {
+    if (!tc_y_possible(g, K)) return 0;
+    int nb, nyb;
+    iota_y_blocks(g.ny, &nb, &nyb);
+    long f = 2L * K * g.ny * 2;   // W matrices of pi Y and iota Y
+    f += 2 * ((tc_wimage_bytes(2 * K, g.ny) + 255) / 4 + nb * ((tc_wimage_bytes(2 * nyb, K) + 255) / 4));
+    return f + 64 * (2 + 2 * nb);
+}
+
 long twiddle_floats(const Grid& g, int K) {
     // tables, W_pi and W_io, then the two tensor-core operand images (64-float aligned)
     long f = 2L * K * ((long)g.nx + g.ny + g.nz) + 2L * K * g.nx;
@@ -28,6 +61,8 @@ long twiddle_floats(const Grid& g, int K) {
     f += 2 * ((tc_wimage_bytes(K, g.nx) + 255) / 4 + (tc_wimage_bytes(g.nx, K) + 255) / 4);
     f = (f + 63) & ~63L;
     f += 2L * K * (2L * g.ny + g.nz);  // mpy, miy, mpz (float2)
+    f = (f + 63) & ~63L;
+    f += ytables_floats(g, K);
     return f + 64;
 }
 
@@ -41,6 +76,23 @@ __global__ void k_build_cmat(const float* cosT, const float* sinT, int len, int 
     const int m = mode_is_p ? pp : q, x = mode_is_p ? q : pp;
     const long o = (long)m * len + x;
     M[i] = (zero_mode0 && m == 0) ? make_float2(0.f, 0.f) : make_float2(cosT[o], sgn * sinT[o]);
+}
+
+// Y-stage matrices of the tensor-core path from the y twiddle table (slot jy: wavenumber
+// jy - K/2): wpy[2 jy + {0, 1}][y] = {cos, sin}, wiy[2 y + {0, 1}][jy] = {cos, sin} (0 at jy = 0)
+__global__ void k_build_wy(const float* cyT, const float* syT, int K, int ny, float* wpy, float* wiy) {
+    int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= 2 * K * ny) return;
+    {
+        const int n = i / ny, y = i - n * ny, jy = n >> 1;
+        const long o = (long)jy * ny + y;
+        wpy[i] = (n & 1) ? syT[o] : cyT[o];
+    }
+    {
+        const int n = i / K, jy = i - n * K, y = n >> 1;
+        const long o = (long)jy * ny + y;
+        wiy[i] = jy == 0 ? 0.f : ((n & 1) ? syT[o] : cyT[o]);
+    }
 }
 
 // x-stage matrices of the tensor-core path from the x twiddle table (slot h + kx = wavenumber kx)
@@ -136,6 +188,41 @@ int twiddle_init(const Grid& g, int K, float* mem, Twiddles& tw, cudaStream_t st
         tw.mpy = mpy;
         tw.miy = miy;
         tw.mpz = mpz;
+        moff += 2L * K * (2L * g.ny + g.nz);
+        moff = (moff + 63) & ~63L;
+        // Y stages on the tensor cores: W matrices, then their operand images
+        tw.tc_y = tc_y_possible(g, K);
+        tw.iy_blocks = tw.iy_nyb = 0;
+        if (tw.tc_y) {
+            int nb, nyb;
+            iota_y_blocks(g.ny, &nb, &nyb);
+            tw.iy_blocks = nb;
+            tw.iy_nyb = nyb;
+            float* wpy = mem + moff;
+            float* wiy = wpy + 2L * K * g.ny;
+            {
+                KTRACE("twiddle", st, 32.0 * K * g.ny, 0);
+                k_build_wy<<<cdiv(2L * K * g.ny, 256), 256, 0, st>>>(tw.cy, tw.sy, K, g.ny, wpy, wiy);
+            }
+            LDDMM_CHECK_LAUNCH();
+            long boff = moff + 4L * K * g.ny;
+            boff = (boff + 63) & ~63L;
+            unsigned char* b = reinterpret_cast<unsigned char*>(mem + boff);
+            const long bpy = (tc_wimage_bytes(2 * K, g.ny) + 255) & ~255L;
+            const long biy = (tc_wimage_bytes(2 * nyb, K) + 255) & ~255L;
+            for (int prec = 0; prec < 2; ++prec) {
+                int rc = tc_build_wimage(wpy, 2 * K, g.ny, prec, b, st);
+                if (rc) return rc;
+                tw.wpy_img[prec] = b;
+                b += bpy;
+                for (int blk = 0; blk < nb; ++blk) {
+                    rc = tc_build_wimage(wiy + 2L * blk * nyb * K, 2 * nyb, K, prec, b, st);
+                    if (rc) return rc;
+                    tw.wiy_img[prec][blk] = b;
+                    b += biy;
+                }
+            }
+        }
     }
     return LDDMM_OK;
 }
@@ -474,10 +561,18 @@ int bl_project(const Grid& g, const Twiddles& tw, const float* f, long fstride, 
     if (rc) return rc;
     const int K = tw.K, KH = K / 2;
     const long rows = (long)ncomp * g.nz * g.ny;
-    if (precision != LDDMM_PREC_FP32_SIMT && fstride == (long)g.nz * g.ny * g.nx &&
-        tc_rowgemm_supported(K, g.nx, rows, f, g.nx)) {
+    const long nslab = (long)ncomp * g.nz;
+    const int tp = precision == LDDMM_PREC_BF16X3 ? 1 : 0;
+    const bool tcx = precision != LDDMM_PREC_FP32_SIMT && fstride == (long)g.nz * g.ny * g.nx &&
+                     tc_rowgemm_supported(K, g.nx, rows, f, g.nx);
+    const bool tcy = tcx && tw.tc_y && (reinterpret_cast<uintptr_t>(s1) & 15) == 0;
+    if (tcy) {
+        // stage X on the tensor cores, stored transposed per (comp, z) slab:
+        // A[comp, z][2 kx + re/im][y], the K-major rows of the tensor-core Y stage
+        rc = tc_rowgemm_ex(f, rows, g.nx, g.nx, tw.wpi_img[tp], K, tp, 1, reinterpret_cast<float*>(s1),
+                           g.ny, 0, K, 0, 0, 0, "pi_x_tc", rows * g.nx * 4.0 + rows * K * 4.0, st);
+    } else if (tcx) {
         // stage X on the tensor cores: A[row][0..K) = (Re, Im) pairs of kx = 0..K/2-1
-        const int tp = precision == LDDMM_PREC_BF16X3 ? 1 : 0;
         rc = tc_rowgemm(f, rows, g.nx, g.nx, tw.wpi_img[tp], K, tp, reinterpret_cast<float*>(s1), rows, 0, K,
                         "pi_x_tc", rows * g.nx * 4.0 + rows * K * 4.0, st);
     } else {
@@ -485,8 +580,13 @@ int bl_project(const Grid& g, const Twiddles& tw, const float* f, long fstride, 
     }
     if (rc) return rc;
     // stage Y: B[comp, z][jy][kx] = sum_y e^{-i ky y} A[comp, z][y][kx]
-    {
-        const long nslab = (long)ncomp * g.nz;
+    if (tcy) {
+        // rows (comp, z, kx, re/im) of ny floats against W[2 jy + {cos, sin}][y]
+        rc = tc_rowgemm_ex(reinterpret_cast<const float*>(s1), nslab * K, g.ny, g.ny, tw.wpy_img[tp],
+                           2 * K, tp, 2, reinterpret_cast<float*>(s2), K, 0, 2 * K, K, 0, KH, "pi_y_tc",
+                           (double)nslab * K * g.ny * 4.0 + (double)nslab * K * KH * 8.0, st);
+        if (rc) return rc;
+    } else {
         rc = cgemm_tw(tw.mpy, K, g.ny, KH, nslab, s1, (long)g.ny * KH, KH, s2, (long)K * KH, KH, 1, 0,
                       "pi_y", (double)nslab * (g.ny + K) * KH * 8.0, st);
         if (rc) return rc;
@@ -523,7 +623,8 @@ template <int ZPT>
 __global__ void __launch_bounds__((Z2_JT / 2) * (Z2_ZT / ZPT))
 k_iota_z2(const float2* __restrict__ c, int nz, int ny, int nx, int K, int KH, int deriv_axis,
           int bspline, const float* __restrict__ cxT, const float* __restrict__ cyT,
-          const float* __restrict__ czT, const float* __restrict__ szT, float2* __restrict__ T1) {
+          const float* __restrict__ czT, const float* __restrict__ szT, float2* __restrict__ T1,
+          int kmajor) {
     constexpr int NTH = (Z2_JT / 2) * (Z2_ZT / ZPT);
     __shared__ float4 cs4[32 * Z2_JT / 2];   // [jz][Z2_JT] float2 (K <= 64 -> 2 passes if K > 32)
     __shared__ float4 es4[32 * Z2_ZT / 2];   // [jz][Z2_ZT] float2
@@ -606,15 +707,30 @@ k_iota_z2(const float2* __restrict__ c, int nz, int ny, int nx, int K, int KH, i
     for (int a = 0; a < ZPT; ++a) {
         const int z = z0 + ZPT * zq + a;
         if (z >= nz) continue;
-        float2* dst = T1 + ((long)comp * nz + z) * KK + j0 + 2 * jq;
+        if (kmajor) {
+            // T1[comp][z][kx][re, im][jy] (floats): the K-major rows the tensor-core Y stage reads
+            float* dst = reinterpret_cast<float*>(T1) + ((long)comp * nz + z) * 2 * KK;
 #pragma unroll
-        for (int b = 0; b < 2; ++b)
-            if (j0 + 2 * jq + b < KK) dst[b] = make_float2(ar[a][b], ai[a][b]);
+            for (int b = 0; b < 2; ++b) {
+                const int j = j0 + 2 * jq + b;
+                if (j < KK) {
+                    const int jy = j / KH, kx = j - jy * KH;
+                    dst[(2 * kx) * K + jy] = ar[a][b];
+                    dst[(2 * kx + 1) * K + jy] = ai[a][b];
+                }
+            }
+        } else {
+            float2* dst = T1 + ((long)comp * nz + z) * KK + j0 + 2 * jq;
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+                if (j0 + 2 * jq + b < KK) dst[b] = make_float2(ar[a][b], ai[a][b]);
+        }
     }
 }
 
 static int launch_iota_zy2(const Grid& g, const Twiddles& tw, const float2* c, int nout,
-                           int deriv_axis, int bspline, float2* T1, float2* T2, cudaStream_t st) {
+                           int deriv_axis, int bspline, float2* T1, float2* T2, int tp,
+                           bool tc_y, cudaStream_t st) {
     const int K = tw.K, KH = K / 2, KK = K * KH;
     {
         dim3 grid(cdiv(g.nz, Z2_ZT), cdiv(KK, Z2_JT), nout);
@@ -622,11 +738,25 @@ static int launch_iota_zy2(const Grid& g, const Twiddles& tw, const float2* c, i
                                  (double)nout * g.nz * KK * 8.0,
                (double)nout * g.nz * KK * K * 8.0);
         k_iota_z2<IOTA_Z_ZPT><<<grid, (Z2_JT / 2) * (Z2_ZT / IOTA_Z_ZPT), 0, st>>>(
-            c, g.nz, g.ny, g.nx, K, KH, deriv_axis, bspline, tw.cx, tw.cy, tw.cz, tw.sz, T1);
+            c, g.nz, g.ny, g.nx, K, KH, deriv_axis, bspline, tw.cx, tw.cy, tw.cz, tw.sz, T1,
+            tc_y ? 1 : 0);
     }
     LDDMM_CHECK_LAUNCH();
     // stage Y: T2[plane][y][kx] = sum_{jy >= 1} e^{+i ky y} T1[plane][jy][kx]
     const long nplanes = (long)nout * g.nz;
+    if (tc_y) {
+        // on the tensor cores: rows (plane, kx, re/im) of K floats against W[2y + {cos, sin}][jy],
+        // in blocks of iy_nyb positions y
+        const int nyb = tw.iy_nyb;
+        for (int b = 0; b < tw.iy_blocks; ++b) {
+            int rc = tc_rowgemm_ex(reinterpret_cast<const float*>(T1), nplanes * K, K, K,
+                                   tw.wiy_img[tp][b], 2 * nyb, tp, 3, reinterpret_cast<float*>(T2),
+                                   K, 0, 2 * nyb, g.ny, b * nyb, KH, "iota_y_tc",
+                                   (double)nplanes * K * K * 4.0 + (double)nplanes * nyb * KH * 8.0, st);
+            if (rc) return rc;
+        }
+        return LDDMM_OK;
+    }
     return cgemm_tw(tw.miy, g.ny, K, KH, nplanes, T1, (long)K * KH, KH, T2, (long)g.ny * KH, KH, 1, 0,
                     "iota_y", (double)nplanes * (K + g.ny) * KH * 8.0, st);
 }
@@ -753,14 +883,15 @@ int bl_include(const Grid& g, const Twiddles& tw, const float2* c, int ncomp, fl
     }
     const int K = tw.K, KH = K / 2;
     const int nout = deriv_axis == 3 ? 1 : ncomp;
-    (void)s2;
-    // stage Z into s2, stage Y into s1
-    int rc2 = launch_iota_zy2(g, tw, c, nout, deriv_axis, bspline ? 1 : 0, s2, s1, st);
-    if (rc2) return rc2;
     const long rows = (long)nout * g.nz * g.ny;
-    if (precision != LDDMM_PREC_FP32_SIMT && tc_rowgemm_supported(g.nx, K, rows, s1, K)) {
+    const bool tcx = precision != LDDMM_PREC_FP32_SIMT && tc_rowgemm_supported(g.nx, K, rows, s1, K);
+    const bool tcy = tcx && tw.tc_y && (reinterpret_cast<uintptr_t>(s2) & 15) == 0;
+    const int tp = precision == LDDMM_PREC_BF16X3 ? 1 : 0;
+    // stage Z into s2, stage Y into s1
+    int rc2 = launch_iota_zy2(g, tw, c, nout, deriv_axis, bspline ? 1 : 0, s2, s1, tp, tcy, st);
+    if (rc2) return rc2;
+    if (tcx) {
         // stage X on the tensor cores: f[row][x] = sum_j T[row][j] W_io[x][j]
-        const int tp = precision == LDDMM_PREC_BF16X3 ? 1 : 0;
         return tc_rowgemm(reinterpret_cast<const float*>(s1), rows, K, K, tw.wio_img[tp], g.nx, tp, f,
                           (long)g.nz * g.ny, fstride, g.nx, "iota_x_tc",
                           rows * K * 4.0 + rows * g.nx * 4.0, st);

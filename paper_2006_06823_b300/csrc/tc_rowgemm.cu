@@ -18,6 +18,16 @@
 // the result matches FP32 arithmetic to within its rounding. (BF16 hi + lo with kind::f16
 // is the lower-precision variant of the same scheme.)
 //
+// Epilogue forms (EPI): 0 stores OUT row-major through TMA; 1 stores it transposed per slab of
+// `rps` rows (OUT[slab][n][row in slab], so that the next stage reads it K-major: the x stage
+// of pi feeding the Y stage); 2 and 3 finish a complex contraction written as a real GEMM
+// over (Re, Im) input rows: rows come in (Re, Im) pairs of one complex line (adjacent lanes),
+// the W rows in (cos, sin) pairs of one output position p, and each lane combines its own
+// cos-sum with its partner's sin-sum (exchanged by a warp shuffle):
+//   2 (pi, e^{-i theta}):  Re = C_re + S_im,  Im = C_im - S_re
+//   3 (iota, e^{+i theta}): Re = C_re - S_im,  Im = C_im + S_re
+// and stores OUT[slab][p0 + p][line].{re, im} (interleaved complex, line = kx fastest).
+//
 // Every mbarrier wait is bounded; on timeout the kernel records an error code in a device
 // word (read by lddmm_device_error), stops issuing work, waits (bounded) for its own copies
 // and MMAs, frees its TMEM and returns.
@@ -243,11 +253,12 @@ __host__ __device__ constexpr int nop_planes(int prec) { return prec == 0 ? 1 : 
 // OUT is the 3-D tensor [ncomp][rpc][n_out] behind tmap_out (rows r = comp * rpc + local).
 // PREC 0: TF32 hi + lo (4 k-steps of 8 per 32-column chunk). PREC 1: BF16 hi + lo, the 32
 // elements of a chunk in the first 64 bytes of each 128-byte operand row (2 k-steps of 16).
-template <int PREC, int DEPTH>
+template <int PREC, int DEPTH, int EPI>
 __global__ void __launch_bounds__(NTHREADS_WS, 1)
 k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant__ CUtensorMap tmap_out,
              const unsigned char* __restrict__ w_image, int N, int kdim, long rows,
-             float* __restrict__ out, long rpc, long comp_stride, int n_out, unsigned tmem_cols) {
+             float* __restrict__ out, long rpc, long comp_stride, int n_out, unsigned tmem_cols,
+             int ptot, int p0, int lines) {
     extern __shared__ unsigned char smem_raw[];
     constexpr int NRAW = nraw(PREC, DEPTH);
     constexpr int NOP = nop(PREC, DEPTH);
@@ -414,6 +425,60 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
                     ++t;
                 }
             }
+        }
+    } else if (warp >= NWORK && EPI != 0) {
+        // ------------------------------------------- epilogue warps, direct-store forms
+        const int et = tid - 32 * NWORK;
+        const int quarter = (warp - NWORK) & 3;
+        for (long t = 0; t < my_tiles; ++t) {
+            // warp-uniform decisions: the completion step below exchanges values between lanes
+            if (__any_sync(0xffffffffu, abort_flag != 0)) break;
+            const int b = (int)(t & 1);
+            const bool ok = mbar_wait(&accfull_bar[b], (unsigned)((t >> 1) & 1));
+            if (!__all_sync(0xffffffffu, ok)) {
+                abort_flag = 1;
+                break;
+            }
+            fence_after();
+            const long row = (blockIdx.x + t * gridDim.x) * TM + et;
+            const bool live = row < rows;
+            const long slab = row / rpc;
+            const long r = row - slab * rpc;        // row within its slab
+            for (int c0 = 0; c0 < N; c0 += 32) {
+                float v[32];
+                const unsigned trow = tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)(b * accw + c0);
+                tmem_ld32(trow, v);
+                if (cat) {
+                    float v2[32];
+                    tmem_ld32(trow + (unsigned)N, v2);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) v[i] += v2[i];
+                }
+                if (EPI == 1) {
+                    // OUT[slab][n][r]: for each n the warp's 32 rows are 32 consecutive floats
+                    if (live) {
+                        float* dst = out + (slab * N + c0) * rpc + r;
+#pragma unroll
+                        for (int i = 0; i < 32; ++i)
+                            if (c0 + i < n_out) dst[(long)i * rpc] = v[i];
+                    }
+                } else {
+                    // rows r = 2 line + c (c = 0: Re, 1: Im); columns 2 p + {0: cos, 1: sin}
+                    const int c = (int)(r & 1);
+                    const long line = r >> 1;
+                    const float sg = ((EPI == 2) == (c == 0)) ? 1.f : -1.f;
+                    float* dst = out + ((slab * ptot + p0 + (c0 >> 1)) * lines + line) * 2 + c;
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) {
+                        const float sp = __shfl_xor_sync(0xffffffffu, v[2 * i + 1], 1);
+                        if (live && (c0 >> 1) + i < (n_out >> 1))
+                            dst[(long)i * lines * 2] = v[2 * i] + sg * sp;
+                    }
+                }
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&accempty_bar[b]);
         }
     } else if (warp >= NWORK) {
         // ---------------------------------------------------------------- epilogue warps
@@ -610,37 +675,88 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// W hi + lo, the raw ring, the split operands and two staging tiles (+ alignment slack);
-// both precisions come to 10 tiles besides W
-int tc_smem_bytes(int N, int kdim, int prec, int depth) {
+// W hi + lo, the raw ring, the split operands and (TMA-store epilogue only) two staging
+// tiles, + alignment slack
+int tc_smem_bytes(int N, int kdim, int prec, int depth, int epi) {
     const int nchunk = (kdim + CHUNK - 1) / CHUNK;
-    return 2 * nchunk * N * 128 + (nraw(prec, depth) + nop_planes(prec) * nop(prec, depth) + 2) * TILE_B + 1024;
+    return 2 * nchunk * N * 128 +
+           (nraw(prec, depth) + nop_planes(prec) * nop(prec, depth) + (epi == 0 ? 2 : 0)) * TILE_B + 1024;
 }
 
 constexpr int kTcSmemLimit = 220 * 1024;
 
-// the deepest ring that fits (4, else 3); 0 if none
-int tc_depth(int N, int kdim, int prec) {
-    if (tc_smem_bytes(N, kdim, prec, 4) <= kTcSmemLimit) return 4;
-    if (tc_smem_bytes(N, kdim, prec, 3) <= kTcSmemLimit) return 3;
+// the deepest ring that fits (4, else 3, else 2 for the direct-store epilogues); 0 if none
+int tc_depth(int N, int kdim, int prec, int epi) {
+    if (tc_smem_bytes(N, kdim, prec, 4, epi) <= kTcSmemLimit) return 4;
+    if (tc_smem_bytes(N, kdim, prec, 3, epi) <= kTcSmemLimit) return 3;
+    if (epi != 0 && tc_smem_bytes(N, kdim, prec, 2, epi) <= kTcSmemLimit) return 2;
     return 0;
+}
+
+template <int PREC, int DEPTH, int EPI>
+cudaError_t tc_launch(int grid, int smem, cudaStream_t st, const CUtensorMap& map, const CUtensorMap& omap,
+                      const unsigned char* W, int N, int kdim, long rows, float* out, long rpc,
+                      long comp_stride, int n_out, unsigned cols, int ptot, int p0, int lines) {
+    static int attr = 0;   // largest dynamic size requested so far (under the caller's lock)
+    if (smem > attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_tc_rowgemm<PREC, DEPTH, EPI>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr = smem;
+    }
+    k_tc_rowgemm<PREC, DEPTH, EPI><<<grid, NTHREADS_WS, smem, st>>>(
+        map, omap, W, N, kdim, rows, out, rpc, comp_stride, n_out, cols, ptot, p0, lines);
+    return cudaGetLastError();
+}
+
+template <int PREC, int EPI>
+cudaError_t tc_launch_depth(int depth, int grid, int smem, cudaStream_t st, const CUtensorMap& map,
+                            const CUtensorMap& omap, const unsigned char* W, int N, int kdim,
+                            long rows, float* out, long rpc, long comp_stride, int n_out,
+                            unsigned cols, int ptot, int p0, int lines) {
+    if (depth == 4)
+        return tc_launch<PREC, 4, EPI>(grid, smem, st, map, omap, W, N, kdim, rows, out, rpc,
+                                       comp_stride, n_out, cols, ptot, p0, lines);
+    if (depth == 3)
+        return tc_launch<PREC, 3, EPI>(grid, smem, st, map, omap, W, N, kdim, rows, out, rpc,
+                                       comp_stride, n_out, cols, ptot, p0, lines);
+    if constexpr (EPI != 0) {
+        if (depth == 2)
+            return tc_launch<PREC, 2, EPI>(grid, smem, st, map, omap, W, N, kdim, rows, out, rpc,
+                                           comp_stride, n_out, cols, ptot, p0, lines);
+    }
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace
 
-bool tc_rowgemm_supported(int N, int kdim, long rows, const void* in, long in_row_floats) {
+bool tc_rowgemm_supported(int N, int kdim, long rows, const void* in, long in_row_floats,
+                          int epi, int prec) {
     if (N < 16 || N > 256 || (N % 16) != 0) return false;
     if (kdim < 1 || (in_row_floats % 4) != 0) return false;
     if ((reinterpret_cast<uintptr_t>(in) & 15) != 0) return false;
     if (rows < 1 || rows > 0x7fffffffL) return false;
-    if (tc_depth(N, kdim, 0) == 0 || tc_depth(N, kdim, 1) == 0) return false;
+    if (epi < 0 || epi > 3 || (epi >= 2 && (rows & 1))) return false;
+    if (prec < 0) {
+        if (tc_depth(N, kdim, 0, epi) == 0 || tc_depth(N, kdim, 1, epi) == 0) return false;
+    } else if (tc_depth(N, kdim, prec, epi) == 0) {
+        return false;
+    }
     return encode_fn() != nullptr;
 }
 
-// in: rows x in_row_floats FP32 (the first kdim columns are used), W: N x kdim FP32.
 int tc_rowgemm(const float* in, long rows, int kdim, long in_row_floats, const unsigned char* W,
                int N, int prec, float* out, long rpc, long comp_stride, int n_out,
                const char* trace_name, double trace_bytes, cudaStream_t st) {
+    return tc_rowgemm_ex(in, rows, kdim, in_row_floats, W, N, prec, 0, out, rpc, comp_stride,
+                         n_out, 0, 0, 0, trace_name, trace_bytes, st);
+}
+
+// in: rows x in_row_floats FP32 (the first kdim columns are used), W: N x kdim FP32.
+int tc_rowgemm_ex(const float* in, long rows, int kdim, long in_row_floats, const unsigned char* W,
+                  int N, int prec, int epi, float* out, long rpc, long comp_stride, int n_out,
+                  int ptot, int p0, int lines, const char* trace_name, double trace_bytes,
+                  cudaStream_t st) {
     CUtensorMap map;
     cuuint64_t dims[2] = {(cuuint64_t)in_row_floats, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)in_row_floats * 4};
@@ -654,44 +770,33 @@ int tc_rowgemm(const float* in, long rows, int kdim, long in_row_floats, const u
         set_error("tc_rowgemm: cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
         return LDDMM_ECUDA;
     }
-    // output: [ncomp][rpc][n_out] with component stride comp_stride floats
-    CUtensorMap omap;
-    const long ncomp_out = (rows + rpc - 1) / rpc;
-    cuuint64_t odims[3] = {(cuuint64_t)n_out, (cuuint64_t)rpc, (cuuint64_t)ncomp_out};
-    cuuint64_t ostr[2] = {(cuuint64_t)n_out * 4, (cuuint64_t)(ncomp_out > 1 ? comp_stride : rpc * n_out) * 4};
-    cuuint32_t obox[3] = {32, TM, 1};
-    cuuint32_t oestr[3] = {1, 1, 1};
-    r = encode_fn()(&omap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, out, odims, ostr, obox, oestr,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
-                    CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) {
-        set_error("tc_rowgemm: cuTensorMapEncodeTiled (output) failed (" + std::to_string((int)r) + ")");
-        return LDDMM_ECUDA;
+    if (epi < 0 || epi > 3 || rpc < 1 || (epi >= 2 && (rows & 1))) {
+        set_error("tc_rowgemm: bad epilogue arguments");
+        return LDDMM_EINVAL;
     }
-    const int depth = tc_depth(N, kdim, prec);
+    // output of the TMA-store epilogue: [ncomp][rpc][n_out] with component stride comp_stride
+    // floats (the direct-store epilogues address OUT themselves; the map is then unused)
+    CUtensorMap omap = map;
+    if (epi == 0) {
+        const long ncomp_out = (rows + rpc - 1) / rpc;
+        cuuint64_t odims[3] = {(cuuint64_t)n_out, (cuuint64_t)rpc, (cuuint64_t)ncomp_out};
+        cuuint64_t ostr[2] = {(cuuint64_t)n_out * 4, (cuuint64_t)(ncomp_out > 1 ? comp_stride : rpc * n_out) * 4};
+        cuuint32_t obox[3] = {32, TM, 1};
+        cuuint32_t oestr[3] = {1, 1, 1};
+        r = encode_fn()(&omap, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, out, odims, ostr, obox, oestr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                        CU_TENSOR_MAP_L2_PROMOTION_NONE, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (r != CUDA_SUCCESS) {
+            set_error("tc_rowgemm: cuTensorMapEncodeTiled (output) failed (" + std::to_string((int)r) + ")");
+            return LDDMM_ECUDA;
+        }
+    }
+    const int depth = tc_depth(N, kdim, prec, epi);
     if (depth == 0) {
         set_error("tc_rowgemm: W too large for shared memory");
         return LDDMM_EINVAL;
     }
-    const int smem = tc_smem_bytes(N, kdim, prec, depth);
-    {
-        // largest dynamic size requested so far per instantiation
-        static std::mutex mu;
-        static int attr_smem[2][2] = {{0, 0}, {0, 0}};
-        std::lock_guard<std::mutex> lock(mu);
-        int& cur = attr_smem[prec][depth == 4];
-        if (smem > cur) {
-            cudaError_t e;
-            if (prec == 0)
-                e = depth == 4 ? cudaFuncSetAttribute(k_tc_rowgemm<0, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
-                               : cudaFuncSetAttribute(k_tc_rowgemm<0, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            else
-                e = depth == 4 ? cudaFuncSetAttribute(k_tc_rowgemm<1, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
-                               : cudaFuncSetAttribute(k_tc_rowgemm<1, 3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-            LDDMM_CUDA(e);
-            cur = smem;
-        }
-    }
+    const int smem = tc_smem_bytes(N, kdim, prec, depth, epi);
     // two accumulators at columns 0 and N; the epilogue reads 32-column blocks, so the
     // second buffer's last block ends at N + roundup(N, 32)
     const int accw = wcat(N) ? 2 * N : N;
@@ -713,20 +818,22 @@ int tc_rowgemm(const float* in, long rows, int kdim, long in_row_floats, const u
     const int grid = (int)std::min<long>(ntiles, nsm);
     {
         KTRACE(trace_name, st, trace_bytes, 2.0 * rows * (double)N * kdim);
-        if (prec == 0 && depth == 4)
-            k_tc_rowgemm<0, 4><<<grid, NTHREADS_WS, smem, st>>>(map, omap, W, N, kdim, rows, out, rpc,
-                                                               comp_stride, n_out, cols);
-        else if (prec == 0)
-            k_tc_rowgemm<0, 3><<<grid, NTHREADS_WS, smem, st>>>(map, omap, W, N, kdim, rows, out, rpc,
-                                                               comp_stride, n_out, cols);
-        else if (depth == 4)
-            k_tc_rowgemm<1, 4><<<grid, NTHREADS_WS, smem, st>>>(map, omap, W, N, kdim, rows, out, rpc,
-                                                               comp_stride, n_out, cols);
-        else
-            k_tc_rowgemm<1, 3><<<grid, NTHREADS_WS, smem, st>>>(map, omap, W, N, kdim, rows, out, rpc,
-                                                               comp_stride, n_out, cols);
+        static std::mutex mu;   // serialises the per-instantiation shared-memory attribute
+        std::lock_guard<std::mutex> lock(mu);
+        cudaError_t e = cudaErrorInvalidValue;
+        switch (prec * 4 + epi) {
+            case 0: e = tc_launch_depth<0, 0>(depth, grid, smem, st, map, omap, W, N, kdim, rows, out, rpc, comp_stride, n_out, cols, ptot, p0, lines); break;
+            case 1: e = tc_launch_depth<0, 1>(depth, grid, smem, st, map, omap, W, N, kdim, rows, out, rpc, comp_stride, n_out, cols, ptot, p0, lines); break;
+            case 2: e = tc_launch_depth<0, 2>(depth, grid, smem, st, map, omap, W, N, kdim, rows, out, rpc, comp_stride, n_out, cols, ptot, p0, lines); break;
+            case 3: e = tc_launch_depth<0, 3>(depth, grid, smem, st, map, omap, W, N, kdim, rows, out, rpc, comp_stride, n_out, cols, ptot, p0, lines); break;
+            case 4: e = tc_launch_depth<1, 0>(depth, grid, smem, st, map, omap, W, N, kdim, rows, out, rpc, comp_stride, n_out, cols, ptot, p0, lines); break;
+            case 5: e = tc_launch_depth<1, 1>(depth, grid, smem, st, map, omap, W, N, kdim, rows, out, rpc, comp_stride, n_out, cols, ptot, p0, lines); break;
+            case 6: e = tc_launch_depth<1, 2>(depth, grid, smem, st, map, omap, W, N, kdim, rows, out, rpc, comp_stride, n_out, cols, ptot, p0, lines); break;
+            case 7: e = tc_launch_depth<1, 3>(depth, grid, smem, st, map, omap, W, N, kdim, rows, out, rpc, comp_stride, n_out, cols, ptot, p0, lines); break;
+            default: break;
+        }
+        LDDMM_CUDA(e);
     }
-    LDDMM_CHECK_LAUNCH();
     return LDDMM_OK;
 }
 

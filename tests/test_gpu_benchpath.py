@@ -25,13 +25,13 @@ SHAPE = (96, 112, 96)   # nz, ny, nx
 K = 32
 
 
-def phantom_problem(order, nt):
+def phantom_problem(order, nt, noisy=True):
     nz, ny, nx = SHAPE
     fixed = synth.ellipsoid_phantom(SHAPE)
     vt = scaled_velocity(K, K, 1, SHAPE, 8.0 * nx / 192)
     moving = SL.sl_transport(fixed, voxel_velocity(vt, SHAPE), 10, +1, 1)
-    I0 = synth.add_noise(moving, seed=2)
-    I1 = synth.add_noise(fixed, seed=3)
+    I0 = synth.add_noise(moving, seed=2) if noisy else moving
+    I1 = synth.add_noise(fixed, seed=3) if noisy else fixed
     return Vn.Problem(I0, I1, Vn.Params(K=K, nt=nt, order=order, variant=Vn.DEFSTATE, sigma2=0.01))
 
 
@@ -43,9 +43,17 @@ def _devc(c):
     return torch.as_tensor(np.ascontiguousarray(c).astype(np.complex64), device="cuda")
 
 
-@pytest.mark.parametrize("order,nt", [(1, 3), (3, 2)])
-def test_gradient_and_hessian_on_the_bench_launch_path(order, nt):
-    prob = phantom_problem(order, nt)
+# Tolerances (relative L2). Trilinear interpolation of a noisy image has a gradient that jumps
+# across cell faces, and the gradient and Gauss-Newton product use it at the deformed points
+# (G = grad I0 o phi(1)): FP32 rounding of a departure point moves some points across a face.
+# The oracle's own FP64 gradient on the noisy trilinear case moves by 5.7e-4 when the velocity
+# cube is perturbed by 6e-8 relative (FP32 rounding size), and by 8.5e-8 on the same phantom
+# without noise, so the FP32 path is held to 1e-4 where the data are smooth (noise-free
+# trilinear; cubic B-splines, whose gradient is continuous) and to 5e-3 on noisy trilinear.
+@pytest.mark.parametrize("order,nt,noisy,tol", [(1, 3, False, 1e-4), (1, 3, True, 5e-3),
+                                                (3, 2, True, 1e-4)])
+def test_gradient_and_hessian_on_the_bench_launch_path(order, nt, noisy, tol):
+    prob = phantom_problem(order, nt, noisy)
     vt = scaled_velocity(K, K, 5, SHAPE, 2.0)
     E, Er, Ed, g = prob.gradient(vt)
     # the first PCG direction of a Gauss-Newton step, L~^{-1}(-g), as the product's argument
@@ -61,10 +69,10 @@ def test_gradient_and_hessian_on_the_bench_launch_path(order, nt):
         gg = gg.cpu().numpy().astype(np.complex128)
         Hg = Hg.cpu().numpy().astype(np.complex128)
     assert Eg == pytest.approx(E, rel=1e-5)
-    assert rel_l2(gg, g) < 1e-4
-    assert rel_l2(Hg, Hp) < 1e-4
+    assert rel_l2(gg, g) < tol
+    assert rel_l2(Hg, Hp) < tol
     # the curvature PCG tests first (its sign decides a negative-curvature stop)
-    assert S.inner(p, Hg) == pytest.approx(S.inner(p, Hp), rel=1e-4)
+    assert S.inner(p, Hg) == pytest.approx(S.inner(p, Hp), rel=tol)
     assert S.inner(p, Hp) > 0
 
 

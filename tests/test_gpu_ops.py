@@ -20,7 +20,9 @@ import paper_2006_06823_b300 as L  # noqa: E402
 
 CASES = [((16, 16, 16), 8), ((20, 24, 36), 10), ((18, 22, 37), 12), ((33, 40, 64), 32),
          ((8, 8, 8), 4),
-         ((64, 66, 64), 64)]   # the largest band the library accepts (K = 64)
+         ((64, 66, 64), 64),   # the largest band the library accepts (K = 64)
+         # Y stages on the tensor cores: iota's in two blocks of 72 positions; K = 48
+         ((20, 144, 32), 16), ((48, 112, 48), 48)]
 
 
 def dev(a):
