@@ -156,6 +156,29 @@ int lddmm_hessian_matvec(lddmm_ctx* ctx, const float* v, const float* dv, float*
 int lddmm_register(lddmm_ctx* ctx, float* v_inout, const double* g_ref_norms,
                    lddmm_report* report);
 
+/* Persistent batched transport (the batched form; no counterpart in the paper's text): the
+ * state sweep D_t m = 0 (Table 1 row 1; SL-RK characteristics Eqs. 40-42 with trilinear
+ * interpolation, Sec. 3.1) of n independent pairs with their own grids, all in ONE cooperative
+ * kernel launch: blocks take 256-voxel tiles from one work list spanning every active pair,
+ * first the departure points of every pair, then nt steps, with a grid-wide barrier between
+ * steps. Per pair p: dims[3p..3p+2] = (nx, ny, nz) (host array), vel[p] a device [3][nz][ny][nx]
+ * velocity in voxels per unit time, field[p] the device [nz][ny][nx] field transported, out[p]
+ * the device result (must not be field[p]); vel, field and out are host arrays of device
+ * pointers. active: NULL (all pairs) or a device int[n], nonzero = transport this pair (the
+ * others' out is left untouched; read once, synchronously, before the launch). direction +1
+ * forward, -1 backward. Each pair's result equals lddmm_sl_transport(..., interp = 1, ...)
+ * bit for bit. wait_seconds bounds every barrier wait (0: 1 s; at most 10 s); on expiry the
+ * kernel records LDDMM_ETIMEOUT and returns, and so does this call (the outputs are then
+ * incomplete; the device stays usable). A negative value -s is a self-test: the barrier
+ * expects one block more than the launch has, so every wait runs out after s seconds.
+ * Scratch (4 floats per voxel) comes from the stream-ordered pool. Synchronises. n = 0: OK
+ * without device work; n < 0 or > 256, NULL arrays, bad grids (the stand-alone operators'
+ * limits), nt < 1, a bad direction or field[p] == out[p]: EINVAL before any device work. */
+int lddmm_sl_transport_batch(int n, const int* dims, int nt, int direction,
+                             const float* const* vel, const float* const* field,
+                             float* const* out, const int* active, double wait_seconds,
+                             void* stream);
+
 /* Convergence history of the last lddmm_register (or of this context's pair in
  * lddmm_register_batch): one record per Gauss-Newton iterate n = 0 .. gn_iters, five
  * doubles each: {seconds since the call began (host clock, read once the iterate's gradient

@@ -7,7 +7,8 @@ all arithmetic runs in the library's CUDA kernels. There is no CPU fallback: if 
 library is missing, the first call raises.
 
 Names follow the C entry points without their ``lddmm_`` prefix:
-``bl_project``, ``bl_include``, ``sl_characteristics``, ``sl_transport``, ``register_batch``,
+``bl_project``, ``bl_include``, ``sl_characteristics``, ``sl_transport``,
+``sl_transport_batch``, ``register_batch``,
 ``device_error``, ``selftest_wait``, ``set_workspace_limit``, the context methods
 ``set_images``, ``objective``, ``gradient``, ``hessian_matvec``, ``register``,
 ``get_warped``, ``history``, ``jacobian_det``, ``max_displacement``, ``set_option``, ``autotune``,
@@ -88,6 +89,8 @@ def _declare(lib):
         "lddmm_bl_include": (_I, [_I, _I, _I, _I, _P, _I, _P, _I, _I, _I, _P]),
         "lddmm_sl_characteristics": (_I, [_I, _I, _I, _P, _D, _I, _I, _P, _P]),
         "lddmm_sl_transport": (_I, [_I, _I, _I, _I, _I, _P, _P, _I, _I, _P, _P]),
+        "lddmm_sl_transport_batch": (_I, [_I, ctypes.POINTER(_I), _I, _I, ctypes.POINTER(_P),
+                                          ctypes.POINTER(_P), ctypes.POINTER(_P), _P, _D, _P]),
         "lddmm_register_batch": (_I, [ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _P,
                                       ctypes.POINTER(Report), _I]),
         "lddmm_set_option": (_I, [_P, _I, ctypes.c_long]),
@@ -412,6 +415,34 @@ class Context:
         m = torch.empty(self.shape, dtype=torch.float32, device="cuda") if out is None else out
         _check(load().lddmm_get_warped(self._h, self._field(m, "get_warped: out")))
         return m
+
+
+def sl_transport_batch(vels, fields, nt, direction=FORWARD, outs=None, active=None,
+                       wait_seconds=0.0):
+    """Scalar SL transport of many pairs of different grids in one persistent launch
+    (lddmm_sl_transport_batch): vels[p] float32 [3, nz, ny, nx] (voxel units), fields[p]
+    float32 [nz, ny, nx]; returns the transported fields. ``active`` (int32 device tensor
+    [n], optional) selects the pairs to transport."""
+    import torch
+    n = len(vels)
+    if len(fields) != n:
+        raise ValueError("sl_transport_batch: one field per velocity")
+    if outs is None:
+        outs = [torch.empty_like(f) for f in fields]
+    dims = (ctypes.c_int * (3 * max(n, 1)))()
+    vp, fp, op = ((_P * max(n, 1))() for _ in range(3))
+    for p, (v, f, o) in enumerate(zip(vels, fields, outs)):
+        nz, ny, nx = f.shape
+        dims[3 * p], dims[3 * p + 1], dims[3 * p + 2] = nx, ny, nz
+        vp[p] = _f32(_sized(v, 3 * f.numel(), "sl_transport_batch: velocity")).value
+        fp[p] = _f32(f).value
+        op[p] = _f32(_sized(o, f.numel(), "sl_transport_batch: out")).value
+    act = None
+    if active is not None:
+        act = _ptr(_sized(active, n, "sl_transport_batch: active"), torch.int32)
+    _check(load().lddmm_sl_transport_batch(n, dims, nt, direction, vp, fp, op, act,
+                                           float(wait_seconds), _stream()))
+    return outs
 
 
 # ------------------------------------------------------------------ learned warm start

@@ -7,6 +7,11 @@ initial velocity. The solver always finishes the job; its stopping test keeps th
 cold-start reference ||g(0)|| (the library computes it when the initial velocity is not
 zero), so a warm start has to reach the same relative residual as a cold one.
 
+Two workloads. ``phantom``: the paper-scale recipe itself (the noisy ellipsoid phantom of
+the benchmark, moving = phantom transported along a random 32^3-mode band-limited velocity of
+8 voxels maximum displacement, N(0, 0.01) noise on both images; velocity seed s, noise seeds
+s + 1, s + 2). ``blobs`` (the default, noise-free):
+
 Workload (the small workload's recipe scaled to the paper-scale grid): the fixed image is
 the Gaussian-blob phantom (``synth.gaussian_blobs`` scaled to the grid), the moving image
 is the fixed one transported by the library for nt steps along a random stationary
@@ -45,6 +50,9 @@ EVAL_MAX_GN = 30       # GN cap of the evaluation (both arms), so both can reach
 TRAIN_SEED0, EVAL_SEED0 = 100_000, 900_000
 WEIGHTS = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights",
                        "warmstart_d64_c16.npz")
+# the same network trained on the paper-scale (noisy ellipsoid-phantom) recipe
+WEIGHTS_PHANTOM = os.path.join(os.path.dirname(os.path.abspath(__file__)), "weights",
+                               "warmstart_phantom_d64_c16.npz")
 
 
 def make_pair(seed, shape=SHAPE, K=K, nt=NT, max_vox=None):
@@ -64,6 +72,58 @@ def make_pair(seed, shape=SHAPE, K=K, nt=NT, max_vox=None):
     V *= max_vox / V.pow(2).sum(0).sqrt().max()
     I0 = L.sl_transport(V, I1, nt, L.FORWARD, L.INTERP_LINEAR)
     return I0.contiguous(), I1
+
+
+_PHANTOM = {}
+
+
+def phantom_fixed(shape=SHAPE):
+    """The paper-scale workload's fixed image (ellipsoid phantom, no noise) on the device,
+    built once per grid."""
+    import torch
+    if shape not in _PHANTOM:
+        _PHANTOM[shape] = torch.as_tensor(synth.ellipsoid_phantom(shape), dtype=torch.float32,
+                                          device="cuda")
+    return _PHANTOM[shape]
+
+
+def make_phantom_pair(vel_seed, noise_seeds, shape=SHAPE, K=K, nt=NT, max_vox=None,
+                      host_noise=False):
+    """(I0, I1) of the paper-scale workload's recipe: I1 = phantom + noise, I0 = phantom
+    transported (library kernels) along the seed's random band-limited velocity (K^3 generated
+    modes, (1 + |k|^2)^-2, max_vox voxels max) + noise, N(0, 0.01) on both. host_noise draws
+    the noise with ``synth.add_noise`` (the benchmark's pair), else with a seeded device
+    generator (training pairs)."""
+    import torch
+    nz, ny, nx = shape
+    if max_vox is None:
+        max_vox = MAX_VOX
+    fixed = phantom_fixed(shape)
+    vt = synth.random_velocity_coeffs(K, K, vel_seed)
+    v = L.bl_include(torch.as_tensor(vt.astype(np.complex64), device="cuda"), shape)
+    to_vox = torch.tensor([nx, ny, nz], dtype=torch.float32, device="cuda").view(3, 1, 1, 1) / (2 * math.pi)
+    V = v * to_vox
+    V *= max_vox / V.pow(2).sum(0).sqrt().max()
+    moving = L.sl_transport(V, fixed, nt, L.FORWARD, L.INTERP_LINEAR)
+    if host_noise:
+        I0 = synth.add_noise(moving.cpu().numpy().astype(np.float64), seed=noise_seeds[0])
+        I1 = synth.add_noise(fixed.cpu().numpy().astype(np.float64), seed=noise_seeds[1])
+        return (torch.as_tensor(I0, dtype=torch.float32, device="cuda"),
+                torch.as_tensor(I1, dtype=torch.float32, device="cuda"))
+    out = []
+    for img, sd in zip((moving, fixed), noise_seeds):
+        g = torch.Generator(device="cuda")
+        g.manual_seed(int(sd))
+        out.append((img + 0.1 * torch.randn(img.shape, generator=g, device="cuda")).contiguous())
+    return out[0], out[1]
+
+
+def make_workload_pair(workload, seed, max_vox=None):
+    """One pair of the named workload from one seed: 'blobs' (the warm-start workload) or
+    'phantom' (the paper-scale recipe; velocity seed = seed, noise seeds seed + 1, seed + 2)."""
+    if workload == "phantom":
+        return make_phantom_pair(seed, (seed + 1, seed + 2), max_vox=max_vox)
+    return make_pair(seed, max_vox=max_vox)
 
 
 def save_params(net, path):
@@ -100,7 +160,7 @@ def _bias_mask(net):
     return m
 
 
-def generate(seeds, net, max_vox=None, contexts=4, log=print):
+def generate(seeds, net, max_vox=None, contexts=4, log=print, workload="blobs"):
     """Registers every seed's pair from a cold start (``contexts`` pairs at a time through
     lddmm_register_batch, one stream each); returns (X, T, reports) with X the network
     inputs [N, 2, D^3] and T the targets [N, 3, (D/2)^3] on the device."""
@@ -118,7 +178,7 @@ def generate(seeds, net, max_vox=None, contexts=4, log=print):
     t0 = time.time()
     for a in range(0, len(seeds), contexts):
         chunk = seeds[a:a + contexts]
-        pairs = [make_pair(s, max_vox=max_vox) for s in chunk]
+        pairs = [make_workload_pair(workload, s, max_vox=max_vox) for s in chunk]
         torch.cuda.synchronize()
         for c, (I0, I1) in zip(ctxs, pairs):
             c.set_images(I0, I1)
@@ -195,20 +255,20 @@ def prediction_error(net, X, T, batch=8):
     return errs
 
 
-def evaluate(net, seeds, max_vox=None, max_gn=None, log=print):
+def evaluate(net, seeds, max_vox=None, max_gn=None, log=print, workload="blobs"):
     """Cold vs warm registrations of the seeds' pairs (wall time with device sync); both
     arms stop at the same relative residual gtol or after max_gn GN iterations."""
     import torch
     nz, ny, nx = SHAPE
     ctx = L.Context(nx, ny, nz, K, **dict(SOLVER, max_gn=max_gn or SOLVER["max_gn"]))
     # one untimed warm-up of both paths
-    I0, I1 = make_pair(seeds[0], max_vox=max_vox)
+    I0, I1 = make_workload_pair(workload, seeds[0], max_vox=max_vox)
     ctx.set_images(I0, I1)
     ctx.register()
     ctx.register(net.warm_start(I0, I1, K))
     rows = []
     for i, s in enumerate(seeds):
-        I0, I1 = make_pair(s, max_vox=max_vox)
+        I0, I1 = make_workload_pair(workload, s, max_vox=max_vox)
         ctx.set_images(I0, I1)
         torch.cuda.synchronize()
         t = time.perf_counter()
@@ -272,6 +332,9 @@ def main(argv=None):
                     help="maximum displacement of the generating velocity (voxels)")
     ap.add_argument("--eval-max-gn", type=int, default=EVAL_MAX_GN)
     ap.add_argument("--contexts", type=int, default=4)
+    ap.add_argument("--workload", default="blobs", choices=["blobs", "phantom"],
+                    help="training and evaluation pairs: Gaussian blobs (no noise) or the "
+                         "paper-scale ellipsoid-phantom recipe (noisy)")
     args = ap.parse_args(argv)
     import torch
     torch.cuda.set_device(0)
@@ -281,10 +344,12 @@ def main(argv=None):
     if args.init:
         load_params(net, args.init)
     log(f"network: {net.num_params} parameters")
-    train_seeds = [TRAIN_SEED0 + 2 * i for i in range(args.train_pairs)]
-    eval_seeds = [EVAL_SEED0 + 2 * i for i in range(args.eval_pairs)]
+    stride = 3 if args.workload == "phantom" else 2    # seeds consumed per pair
+    train_seeds = [TRAIN_SEED0 + stride * i for i in range(args.train_pairs)]
+    eval_seeds = [EVAL_SEED0 + stride * i for i in range(args.eval_pairs)]
     t = time.time()
-    X, T, reps = generate(train_seeds, net, max_vox=args.max_vox, contexts=args.contexts, log=log)
+    X, T, reps = generate(train_seeds, net, max_vox=args.max_vox, contexts=args.contexts, log=log,
+                          workload=args.workload)
     t_gen = time.time() - t
     n_val = max(1, len(train_seeds) // 20)
     t = time.time()
@@ -300,8 +365,9 @@ def main(argv=None):
                    "train_reached_gtol": float(np.mean([r["grad_rel_l2"] <= SOLVER["gtol"] for r in reps]))},
                   f, indent=1)
     del X, T
-    rows, summary = evaluate(net, eval_seeds, max_vox=args.max_vox, max_gn=args.eval_max_gn, log=log)
-    summary.update({"max_vox": args.max_vox, "eval_max_gn": args.eval_max_gn,
+    rows, summary = evaluate(net, eval_seeds, max_vox=args.max_vox, max_gn=args.eval_max_gn, log=log,
+                             workload=args.workload)
+    summary.update({"max_vox": args.max_vox, "eval_max_gn": args.eval_max_gn, "workload": args.workload,
                     "train_pairs": len(train_seeds) - n_val, "epochs": args.epochs})
     with open(os.path.join(args.out, "warmstart_eval.json"), "w") as f:
         json.dump({"summary": summary, "pairs": rows}, f, indent=1)

@@ -403,3 +403,31 @@ def test_set_images_checks_both_images_against_the_grid():
     with pytest.raises(L.LddmmError) as e:
         ctx.set_images(torch.zeros((4, 5, 6)), torch.zeros((4, 5, 6), dtype=torch.float64))
     assert e.value.code == L.EINVAL
+
+
+def test_batched_transport_rejects_bad_arguments_before_any_device_work():
+    lib = L.load()
+    P = ctypes.c_void_p
+    dims = (ctypes.c_int * 6)(16, 16, 16, 8, 8, 8)
+    a, b, c = P(256), P(512), P(768)
+    vel = (P * 2)(a, a)
+    fld = (P * 2)(b, b)
+    out = (P * 2)(c, P(1024))
+    ok_args = dict(n=2, dims=dims, nt=4, direction=1, vel=vel, field=fld, out=out)
+
+    def call(**kw):
+        k = dict(ok_args, **kw)
+        return lib.lddmm_sl_transport_batch(k["n"], k["dims"], k["nt"], k["direction"], k["vel"],
+                                            k["field"], k["out"], None, kw.get("wait", 0.0), None)
+
+    assert lib.lddmm_sl_transport_batch(0, None, 1, 1, None, None, None, None, 0.0, None) == L.OK
+    assert call(n=-1) == L.EINVAL
+    assert call(n=257) == L.EINVAL
+    assert call(dims=None) == L.EINVAL
+    assert call(nt=0) == L.EINVAL
+    assert call(direction=0) == L.EINVAL
+    assert call(wait=11.0) == L.EINVAL
+    assert call(dims=(ctypes.c_int * 6)(16, 16, 16, 1, 8, 8)) == L.EINVAL     # a grid below 2
+    assert call(out=(P * 2)(c, b)) == L.EINVAL                                # out = field
+    assert b"same buffer" in lib.lddmm_last_error()
+    assert call(vel=(P * 2)(a, None)) == L.EINVAL
