@@ -99,14 +99,17 @@ long spectral_scratch_elems(const Grid& g, int K, int ncomp);
 // OUT[slab][p0 + p][line] (ptot positions per slab) with e^{-i} (2) or e^{+i} (3) phases.
 // prec < 0 in the support test asks for both precision forms.
 bool tc_rowgemm_supported(int N, int kdim, long rows, const void* in, long in_row_floats,
-                          int epi = 0, int prec = -1);
+                          int epi = 0, int prec = -1, int nblk = 1);
 int tc_rowgemm(const float* in, long rows, int kdim, long in_row_floats, const unsigned char* W,
                int N, int prec, float* out, long rpc, long comp_stride, int n_out,
                const char* trace_name, double trace_bytes, cudaStream_t st);
+// nblk > 1 (complex completion forms only): W holds nblk consecutive operand images of N
+// rows each, block b covering positions p0 + b N / 2 ...; the work items are (row tile, block)
+// pairs in one launch.
 int tc_rowgemm_ex(const float* in, long rows, int kdim, long in_row_floats, const unsigned char* W,
                   int N, int prec, int epi, float* out, long rpc, long comp_stride, int n_out,
-                  int ptot, int p0, int lines, const char* trace_name, double trace_bytes,
-                  cudaStream_t st);
+                  int ptot, int p0, int lines, int nblk, const char* trace_name,
+                  double trace_bytes, cudaStream_t st);
 long tc_wimage_bytes(int N, int kdim);
 int tc_build_wimage(const float* W, int N, int kdim, int prec, unsigned char* img,
                     cudaStream_t st);

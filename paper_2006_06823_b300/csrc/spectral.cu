@@ -41,7 +41,7 @@ static bool tc_y_possible(const Grid& g, int K) {
     if ((K % 8) != 0 || (g.ny % 4) != 0 || !iota_y_blocks(g.ny, &nb, &nyb)) return false;
     const void* aligned = reinterpret_cast<const void*>(uintptr_t(256));
     return tc_rowgemm_supported(2 * K, g.ny, 2, aligned, g.ny, 2) &&
-           tc_rowgemm_supported(2 * nyb, K, 2, aligned, K, 3) &&
+           tc_rowgemm_supported(2 * nyb, K, 2, aligned, K, 3, -1, nb) &&
            tc_rowgemm_supported(K, g.nx, 2, aligned, g.nx, 1);
 }
 
@@ -570,7 +570,7 @@ int bl_project(const Grid& g, const Twiddles& tw, const float* f, long fstride, 
         // stage X on the tensor cores, stored transposed per (comp, z) slab:
         // A[comp, z][2 kx + re/im][y], the K-major rows of the tensor-core Y stage
         rc = tc_rowgemm_ex(f, rows, g.nx, g.nx, tw.wpi_img[tp], K, tp, 1, reinterpret_cast<float*>(s1),
-                           g.ny, 0, K, 0, 0, 0, "pi_x_tc", rows * g.nx * 4.0 + rows * K * 4.0, st);
+                           g.ny, 0, K, 0, 0, 0, 1, "pi_x_tc", rows * g.nx * 4.0 + rows * K * 4.0, st);
     } else if (tcx) {
         // stage X on the tensor cores: A[row][0..K) = (Re, Im) pairs of kx = 0..K/2-1
         rc = tc_rowgemm(f, rows, g.nx, g.nx, tw.wpi_img[tp], K, tp, reinterpret_cast<float*>(s1), rows, 0, K,
@@ -583,7 +583,7 @@ int bl_project(const Grid& g, const Twiddles& tw, const float* f, long fstride, 
     if (tcy) {
         // rows (comp, z, kx, re/im) of ny floats against W[2 jy + {cos, sin}][y]
         rc = tc_rowgemm_ex(reinterpret_cast<const float*>(s1), nslab * K, g.ny, g.ny, tw.wpy_img[tp],
-                           2 * K, tp, 2, reinterpret_cast<float*>(s2), K, 0, 2 * K, K, 0, KH, "pi_y_tc",
+                           2 * K, tp, 2, reinterpret_cast<float*>(s2), K, 0, 2 * K, K, 0, KH, 1, "pi_y_tc",
                            (double)nslab * K * g.ny * 4.0 + (double)nslab * K * KH * 8.0, st);
         if (rc) return rc;
     } else {
@@ -648,7 +648,10 @@ k_iota_z2(const float2* __restrict__ c, int nz, int ny, int nx, int K, int KH, i
             const int jz = jzb + jzl, j = j0 + jj;
             float2 v = make_float2(0.f, 0.f);
             if (jzl < nj && jz >= 1 && j < KK) {
-                const int jy = j / KH, kx = j - jy * KH;
+                // column j: (jy, kx) = (j / KH, j % KH), or kx-major (kx, jy) = (j / K, j % K)
+                // for the K-major store, so that a tile's columns are consecutive jy
+                const int jy = kmajor ? j % K : j / KH;
+                const int kx = kmajor ? j / K : j - jy * KH;
                 if (jy >= 1) {
                     const long o = ((long)jz * K + jy) * K + h + kx;
                     const float kxf = (float)kx, kyf = (float)(jy - h), kzf = (float)(jz - h);
@@ -708,13 +711,14 @@ k_iota_z2(const float2* __restrict__ c, int nz, int ny, int nx, int K, int KH, i
         const int z = z0 + ZPT * zq + a;
         if (z >= nz) continue;
         if (kmajor) {
-            // T1[comp][z][kx][re, im][jy] (floats): the K-major rows the tensor-core Y stage reads
+            // T1[comp][z][kx][re, im][jy] (floats): the K-major rows the tensor-core Y stage
+            // reads; the warp's columns are consecutive jy of one kx (128-byte stores)
             float* dst = reinterpret_cast<float*>(T1) + ((long)comp * nz + z) * 2 * KK;
 #pragma unroll
             for (int b = 0; b < 2; ++b) {
                 const int j = j0 + 2 * jq + b;
                 if (j < KK) {
-                    const int jy = j / KH, kx = j - jy * KH;
+                    const int kx = j / K, jy = j - kx * K;
                     dst[(2 * kx) * K + jy] = ar[a][b];
                     dst[(2 * kx + 1) * K + jy] = ai[a][b];
                 }
@@ -746,16 +750,12 @@ static int launch_iota_zy2(const Grid& g, const Twiddles& tw, const float2* c, i
     const long nplanes = (long)nout * g.nz;
     if (tc_y) {
         // on the tensor cores: rows (plane, kx, re/im) of K floats against W[2y + {cos, sin}][jy],
-        // in blocks of iy_nyb positions y
+        // the positions y in iy_blocks column blocks of one launch
         const int nyb = tw.iy_nyb;
-        for (int b = 0; b < tw.iy_blocks; ++b) {
-            int rc = tc_rowgemm_ex(reinterpret_cast<const float*>(T1), nplanes * K, K, K,
-                                   tw.wiy_img[tp][b], 2 * nyb, tp, 3, reinterpret_cast<float*>(T2),
-                                   K, 0, 2 * nyb, g.ny, b * nyb, KH, "iota_y_tc",
-                                   (double)nplanes * K * K * 4.0 + (double)nplanes * nyb * KH * 8.0, st);
-            if (rc) return rc;
-        }
-        return LDDMM_OK;
+        return tc_rowgemm_ex(reinterpret_cast<const float*>(T1), nplanes * K, K, K, tw.wiy_img[tp][0],
+                             2 * nyb, tp, 3, reinterpret_cast<float*>(T2), K, 0, 2 * nyb, g.ny, 0, KH,
+                             tw.iy_blocks, "iota_y_tc",
+                             (double)nplanes * K * K * 4.0 + (double)nplanes * g.ny * KH * 8.0, st);
     }
     return cgemm_tw(tw.miy, g.ny, K, KH, nplanes, T1, (long)K * KH, KH, T2, (long)g.ny * KH, KH, 1, 0,
                     "iota_y", (double)nplanes * (K + g.ny) * KH * 8.0, st);

@@ -258,7 +258,7 @@ __global__ void __launch_bounds__(NTHREADS_WS, 1)
 k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant__ CUtensorMap tmap_out,
              const unsigned char* __restrict__ w_image, int N, int kdim, long rows,
              float* __restrict__ out, long rpc, long comp_stride, int n_out, unsigned tmem_cols,
-             int ptot, int p0, int lines) {
+             int ptot, int p0, int lines, int nblk) {
     extern __shared__ unsigned char smem_raw[];
     constexpr int NRAW = nraw(PREC, DEPTH);
     constexpr int NOP = nop(PREC, DEPTH);
@@ -272,10 +272,11 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
     const int nchunk = (kdim + CHUNK - 1) / CHUNK;
     unsigned char* base = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    // W: nblk column blocks of N rows, each an image of hi and lo parts (2 wbytes)
     const size_t wbytes = (size_t)nchunk * N * 128;
     unsigned char* w_hi = base;
     unsigned char* w_lo = base + wbytes;
-    unsigned char* raw = base + 2 * wbytes;          // NRAW x 16 KB
+    unsigned char* raw = base + 2 * wbytes * nblk;   // NRAW x 16 KB
     unsigned char* op_lo = raw + NRAW * TILE_B;      // NOP x 16 KB
     unsigned char* op_hi = op_lo + NOP * TILE_B;     // NOP x 16 KB (BF16 only)
     unsigned char* stg = op_lo + nop_planes(PREC) * NOP * TILE_B;  // 2 x 16 KB epilogue staging
@@ -300,7 +301,7 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
         // W (hi | lo, already in the swizzled operand layout) arrives by bulk copies; only
         // the MMA warp waits for it
-        const unsigned wtot = (unsigned)(2 * wbytes);
+        const unsigned wtot = (unsigned)(2 * wbytes * nblk);
         asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(&w_bar)),
                      "r"(wtot)
                      : "memory");
@@ -325,7 +326,8 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
     fence_after();
     const unsigned tmem = tmem_holder;
 
-    const long ntiles = (rows + TM - 1) / TM;
+    // work items: (row tile, column block) pairs, item = tile * nblk + block
+    const long ntiles = (rows + TM - 1) / TM * nblk;
     const long my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
     const long total = my_tiles * nchunk;
     const uint32_t idesc = PREC == 0 ? idesc_tf32(N) : idesc_bf16(N);
@@ -349,8 +351,8 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
                     break;
                 }
                 if (abort_flag) break;
-                tma_load_2d(raw + (size_t)s * TILE_B, &tmap_in, c * CHUNK, (int)(t * TM), &raw_full[s],
-                            TILE_B);
+                tma_load_2d(raw + (size_t)s * TILE_B, &tmap_in, c * CHUNK, (int)(t / nblk * TM),
+                            &raw_full[s], TILE_B);
                 issued_sh = q + 1;
                 if (++s == NRAW) {
                     s = 0;
@@ -384,8 +386,10 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
                 const unsigned ah = PREC == 0 ? smem_u32(raw + (size_t)s * TILE_B)
                                               : smem_u32(op_hi + (size_t)o * TILE_B);
                 const unsigned al = smem_u32(op_lo + (size_t)o * TILE_B);
-                const unsigned wh = smem_u32(w_hi + (size_t)c * (cat ? 2 * N : N) * 128);
-                const unsigned wl = cat ? wh + (unsigned)(N * 128) : smem_u32(w_lo + (size_t)c * N * 128);
+                const size_t wblk = 2 * wbytes * (size_t)((blockIdx.x + t * gridDim.x) % nblk);
+                const unsigned wh = smem_u32(w_hi + wblk + (size_t)c * (cat ? 2 * N : N) * 128);
+                const unsigned wl = cat ? wh + (unsigned)(N * 128)
+                                        : smem_u32(w_lo + wblk + (size_t)c * N * 128);
                 if (PREC == 0) {
 #pragma unroll
                     for (int kk = 0; kk < CHUNK / 8; ++kk) {
@@ -440,7 +444,9 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
                 break;
             }
             fence_after();
-            const long row = (blockIdx.x + t * gridDim.x) * TM + et;
+            const long item = blockIdx.x + t * gridDim.x;
+            const long row = item / nblk * TM + et;
+            const int pblk = p0 + (int)(item % nblk) * (N >> 1);   // first position of the block
             const bool live = row < rows;
             const long slab = row / rpc;
             const long r = row - slab * rpc;        // row within its slab
@@ -467,7 +473,7 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
                     const int c = (int)(r & 1);
                     const long line = r >> 1;
                     const float sg = ((EPI == 2) == (c == 0)) ? 1.f : -1.f;
-                    float* dst = out + ((slab * ptot + p0 + (c0 >> 1)) * lines + line) * 2 + c;
+                    float* dst = out + ((slab * ptot + pblk + (c0 >> 1)) * lines + line) * 2 + c;
 #pragma unroll
                     for (int i = 0; i < 16; ++i) {
                         const float sp = __shfl_xor_sync(0xffffffffu, v[2 * i + 1], 1);
@@ -677,26 +683,27 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
 
 // W hi + lo, the raw ring, the split operands and (TMA-store epilogue only) two staging
 // tiles, + alignment slack
-int tc_smem_bytes(int N, int kdim, int prec, int depth, int epi) {
+int tc_smem_bytes(int N, int kdim, int prec, int depth, int epi, int nblk = 1) {
     const int nchunk = (kdim + CHUNK - 1) / CHUNK;
-    return 2 * nchunk * N * 128 +
+    return 2 * nchunk * N * 128 * nblk +
            (nraw(prec, depth) + nop_planes(prec) * nop(prec, depth) + (epi == 0 ? 2 : 0)) * TILE_B + 1024;
 }
 
 constexpr int kTcSmemLimit = 220 * 1024;
 
 // the deepest ring that fits (4, else 3, else 2 for the direct-store epilogues); 0 if none
-int tc_depth(int N, int kdim, int prec, int epi) {
-    if (tc_smem_bytes(N, kdim, prec, 4, epi) <= kTcSmemLimit) return 4;
-    if (tc_smem_bytes(N, kdim, prec, 3, epi) <= kTcSmemLimit) return 3;
-    if (epi != 0 && tc_smem_bytes(N, kdim, prec, 2, epi) <= kTcSmemLimit) return 2;
+int tc_depth(int N, int kdim, int prec, int epi, int nblk = 1) {
+    if (tc_smem_bytes(N, kdim, prec, 4, epi, nblk) <= kTcSmemLimit) return 4;
+    if (tc_smem_bytes(N, kdim, prec, 3, epi, nblk) <= kTcSmemLimit) return 3;
+    if (epi != 0 && tc_smem_bytes(N, kdim, prec, 2, epi, nblk) <= kTcSmemLimit) return 2;
     return 0;
 }
 
 template <int PREC, int DEPTH, int EPI>
 cudaError_t tc_launch(int grid, int smem, cudaStream_t st, const CUtensorMap& map, const CUtensorMap& omap,
                       const unsigned char* W, int N, int kdim, long rows, float* out, long rpc,
-                      long comp_stride, int n_out, unsigned cols, int ptot, int p0, int lines) {
+                      long comp_stride, int n_out, unsigned cols, int ptot, int p0, int lines,
+                      int nblk) {
     static int attr = 0;   // largest dynamic size requested so far (under the caller's lock)
     if (smem > attr) {
         cudaError_t e = cudaFuncSetAttribute(k_tc_rowgemm<PREC, DEPTH, EPI>,
@@ -705,7 +712,7 @@ cudaError_t tc_launch(int grid, int smem, cudaStream_t st, const CUtensorMap& ma
         attr = smem;
     }
     k_tc_rowgemm<PREC, DEPTH, EPI><<<grid, NTHREADS_WS, smem, st>>>(
-        map, omap, W, N, kdim, rows, out, rpc, comp_stride, n_out, cols, ptot, p0, lines);
+        map, omap, W, N, kdim, rows, out, rpc, comp_stride, n_out, cols, ptot, p0, lines, nblk);
     return cudaGetLastError();
 }
 
@@ -713,17 +720,17 @@ template <int PREC, int EPI>
 cudaError_t tc_launch_depth(int depth, int grid, int smem, cudaStream_t st, const CUtensorMap& map,
                             const CUtensorMap& omap, const unsigned char* W, int N, int kdim,
                             long rows, float* out, long rpc, long comp_stride, int n_out,
-                            unsigned cols, int ptot, int p0, int lines) {
+                            unsigned cols, int ptot, int p0, int lines, int nblk) {
     if (depth == 4)
         return tc_launch<PREC, 4, EPI>(grid, smem, st, map, omap, W, N, kdim, rows, out, rpc,
-                                       comp_stride, n_out, cols, ptot, p0, lines);
+                                       comp_stride, n_out, cols, ptot, p0, lines, nblk);
     if (depth == 3)
         return tc_launch<PREC, 3, EPI>(grid, smem, st, map, omap, W, N, kdim, rows, out, rpc,
-                                       comp_stride, n_out, cols, ptot, p0, lines);
+                                       comp_stride, n_out, cols, ptot, p0, lines, nblk);
     if constexpr (EPI != 0) {
         if (depth == 2)
             return tc_launch<PREC, 2, EPI>(grid, smem, st, map, omap, W, N, kdim, rows, out, rpc,
-                                           comp_stride, n_out, cols, ptot, p0, lines);
+                                           comp_stride, n_out, cols, ptot, p0, lines, nblk);
     }
     return cudaErrorInvalidValue;
 }
@@ -731,15 +738,16 @@ cudaError_t tc_launch_depth(int depth, int grid, int smem, cudaStream_t st, cons
 }  // namespace
 
 bool tc_rowgemm_supported(int N, int kdim, long rows, const void* in, long in_row_floats,
-                          int epi, int prec) {
+                          int epi, int prec, int nblk) {
     if (N < 16 || N > 256 || (N % 16) != 0) return false;
     if (kdim < 1 || (in_row_floats % 4) != 0) return false;
     if ((reinterpret_cast<uintptr_t>(in) & 15) != 0) return false;
     if (rows < 1 || rows > 0x7fffffffL) return false;
     if (epi < 0 || epi > 3 || (epi >= 2 && (rows & 1))) return false;
+    if (nblk < 1 || (nblk > 1 && epi < 2)) return false;
     if (prec < 0) {
-        if (tc_depth(N, kdim, 0, epi) == 0 || tc_depth(N, kdim, 1, epi) == 0) return false;
-    } else if (tc_depth(N, kdim, prec, epi) == 0) {
+        if (tc_depth(N, kdim, 0, epi, nblk) == 0 || tc_depth(N, kdim, 1, epi, nblk) == 0) return false;
+    } else if (tc_depth(N, kdim, prec, epi, nblk) == 0) {
         return false;
     }
     return encode_fn() != nullptr;
@@ -749,14 +757,15 @@ int tc_rowgemm(const float* in, long rows, int kdim, long in_row_floats, const u
                int N, int prec, float* out, long rpc, long comp_stride, int n_out,
                const char* trace_name, double trace_bytes, cudaStream_t st) {
     return tc_rowgemm_ex(in, rows, kdim, in_row_floats, W, N, prec, 0, out, rpc, comp_stride,
-                         n_out, 0, 0, 0, trace_name, trace_bytes, st);
+                         n_out, 0, 0, 0, 1, trace_name, trace_bytes, st);
 }
 
-// in: rows x in_row_floats FP32 (the first kdim columns are used), W: N x kdim FP32.
+// in: rows x in_row_floats FP32 (the first kdim columns are used), W: nblk blocks of N x kdim
+// FP32 as consecutive operand images (tc_wimage_bytes(N, kdim) each).
 int tc_rowgemm_ex(const float* in, long rows, int kdim, long in_row_floats, const unsigned char* W,
                   int N, int prec, int epi, float* out, long rpc, long comp_stride, int n_out,
-                  int ptot, int p0, int lines, const char* trace_name, double trace_bytes,
-                  cudaStream_t st) {
+                  int ptot, int p0, int lines, int nblk, const char* trace_name,
+                  double trace_bytes, cudaStream_t st) {
     CUtensorMap map;
     cuuint64_t dims[2] = {(cuuint64_t)in_row_floats, (cuuint64_t)rows};
     cuuint64_t strides[1] = {(cuuint64_t)in_row_floats * 4};
@@ -770,7 +779,8 @@ int tc_rowgemm_ex(const float* in, long rows, int kdim, long in_row_floats, cons
         set_error("tc_rowgemm: cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
         return LDDMM_ECUDA;
     }
-    if (epi < 0 || epi > 3 || rpc < 1 || (epi >= 2 && (rows & 1))) {
+    if (epi < 0 || epi > 3 || rpc < 1 || (epi >= 2 && (rows & 1)) || nblk < 1 ||
+        (nblk > 1 && epi < 2)) {
         set_error("tc_rowgemm: bad epilogue arguments");
         return LDDMM_EINVAL;
     }
@@ -791,12 +801,12 @@ int tc_rowgemm_ex(const float* in, long rows, int kdim, long in_row_floats, cons
             return LDDMM_ECUDA;
         }
     }
-    const int depth = tc_depth(N, kdim, prec, epi);
+    const int depth = tc_depth(N, kdim, prec, epi, nblk);
     if (depth == 0) {
         set_error("tc_rowgemm: W too large for shared memory");
         return LDDMM_EINVAL;
     }
-    const int smem = tc_smem_bytes(N, kdim, prec, depth, epi);
+    const int smem = tc_smem_bytes(N, kdim, prec, depth, epi, nblk);
     // two accumulators at columns 0 and N; the epilogue reads 32-column blocks, so the
     // second buffer's last block ends at N + roundup(N, 32)
     const int accw = wcat(N) ? 2 * N : N;
@@ -814,7 +824,7 @@ int tc_rowgemm_ex(const float* in, long rows, int kdim, long in_row_floats, cons
         cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
         nsm = v;
     }
-    const long ntiles = (rows + TM - 1) / TM;
+    const long ntiles = (rows + TM - 1) / TM * nblk;
     const int grid = (int)std::min<long>(ntiles, nsm);
     {
         KTRACE(trace_name, st, trace_bytes, 2.0 * rows * (double)N * kdim);
@@ -822,14 +832,14 @@ int tc_rowgemm_ex(const float* in, long rows, int kdim, long in_row_floats, cons
         std::lock_guard<std::mutex> lock(mu);
         cudaError_t e = cudaErrorInvalidValue;
         switch (prec * 4 + epi) {
-            case 0: e = tc_launch_depth<0, 0>(depth, grid, smem, st, map, omap, W, N, kdim, rows, out, rpc, comp_stride, n_out, cols, ptot, p0, lines); break;
-            case 1: e = tc_launch_depth<0, 1>(depth, grid, smem, st, map, omap, W, N, kdim, rows, out, rpc, comp_stride, n_out, cols, ptot, p0, lines); break;
-            case 2: e = tc_launch_depth<0, 2>(depth, grid, smem, st, map, omap, W, N, kdim, rows, out, rpc, comp_stride, n_out, cols, ptot, p0, lines); break;
-            case 3: e = tc_launch_depth<0, 3>(depth, grid, smem, st, map, omap, W, N, kdim, rows, out, rpc, comp_stride, n_out, cols, ptot, p0, lines); break;
-            case 4: e = tc_launch_depth<1, 0>(depth, grid, smem, st, map, omap, W, N, kdim, rows, out, rpc, comp_stride, n_out, cols, ptot, p0, lines); break;
-            case 5: e = tc_launch_depth<1, 1>(depth, grid, smem, st, map, omap, W, N, kdim, rows, out, rpc, comp_stride, n_out, cols, ptot, p0, lines); break;
-            case 6: e = tc_launch_depth<1, 2>(depth, grid, smem, st, map, omap, W, N, kdim, rows, out, rpc, comp_stride, n_out, cols, ptot, p0, lines); break;
-            case 7: e = tc_launch_depth<1, 3>(depth, grid, smem, st, map, omap, W, N, kdim, rows, out, rpc, comp_stride, n_out, cols, ptot, p0, lines); break;
+            case 0: e = tc_launch_depth<0, 0>(depth, grid, smem, st, map, omap, W, N, kdim, rows, out, rpc, comp_stride, n_out, cols, ptot, p0, lines, nblk); break;
+            case 1: e = tc_launch_depth<0, 1>(depth, grid, smem, st, map, omap, W, N, kdim, rows, out, rpc, comp_stride, n_out, cols, ptot, p0, lines, nblk); break;
+            case 2: e = tc_launch_depth<0, 2>(depth, grid, smem, st, map, omap, W, N, kdim, rows, out, rpc, comp_stride, n_out, cols, ptot, p0, lines, nblk); break;
+            case 3: e = tc_launch_depth<0, 3>(depth, grid, smem, st, map, omap, W, N, kdim, rows, out, rpc, comp_stride, n_out, cols, ptot, p0, lines, nblk); break;
+            case 4: e = tc_launch_depth<1, 0>(depth, grid, smem, st, map, omap, W, N, kdim, rows, out, rpc, comp_stride, n_out, cols, ptot, p0, lines, nblk); break;
+            case 5: e = tc_launch_depth<1, 1>(depth, grid, smem, st, map, omap, W, N, kdim, rows, out, rpc, comp_stride, n_out, cols, ptot, p0, lines, nblk); break;
+            case 6: e = tc_launch_depth<1, 2>(depth, grid, smem, st, map, omap, W, N, kdim, rows, out, rpc, comp_stride, n_out, cols, ptot, p0, lines, nblk); break;
+            case 7: e = tc_launch_depth<1, 3>(depth, grid, smem, st, map, omap, W, N, kdim, rows, out, rpc, comp_stride, n_out, cols, ptot, p0, lines, nblk); break;
             default: break;
         }
         LDDMM_CUDA(e);

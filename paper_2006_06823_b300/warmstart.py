@@ -160,7 +160,23 @@ def _bias_mask(net):
     return m
 
 
-def generate(seeds, net, max_vox=None, contexts=4, log=print, workload="blobs"):
+def low_band(v, kb):
+    """The coefficient cube v [3, K, K, K] with every mode of |k_a| > kb on some axis set to
+    zero (kb = None: v itself): the smooth part of a solution as a training target."""
+    if kb is None:
+        return v
+    K = v.shape[-1]
+    out = v.clone()
+    k = (np.arange(K) - K // 2)
+    drop = np.abs(k) > kb
+    idx = np.nonzero(drop)[0].tolist()
+    out[:, idx, :, :] = 0
+    out[:, :, idx, :] = 0
+    out[:, :, :, idx] = 0
+    return out
+
+
+def generate(seeds, net, max_vox=None, contexts=4, log=print, workload="blobs", target_band=None):
     """Registers every seed's pair from a cold start (``contexts`` pairs at a time through
     lddmm_register_batch, one stream each); returns (X, T, reports) with X the network
     inputs [N, 2, D^3] and T the targets [N, 3, (D/2)^3] on the device."""
@@ -187,7 +203,7 @@ def generate(seeds, net, max_vox=None, contexts=4, log=print, workload="blobs"):
         reps += L.register_batch(ctxs[:len(chunk)], vs, max_threads=contexts)
         for j, ((I0, I1), v) in enumerate(zip(pairs, vs)):
             net.input(I0, I1, out=X[a + j])
-            L.bl_include(v, (d, d, d), out=T[a + j])
+            L.bl_include(low_band(v, target_band), (d, d, d), out=T[a + j])
         done = a + len(chunk)
         if done % 100 < contexts or done == len(seeds):
             log(f"  generated {done}/{len(seeds)} pairs, {time.time() - t0:.0f} s, "
@@ -332,6 +348,9 @@ def main(argv=None):
                     help="maximum displacement of the generating velocity (voxels)")
     ap.add_argument("--eval-max-gn", type=int, default=EVAL_MAX_GN)
     ap.add_argument("--contexts", type=int, default=4)
+    ap.add_argument("--target-band", type=int, default=None,
+                    help="train on the solution's modes with |k_a| <= this only (its smooth part)")
+    ap.add_argument("--weights-out", default=None, help="also save the weights here")
     ap.add_argument("--workload", default="blobs", choices=["blobs", "phantom"],
                     help="training and evaluation pairs: Gaussian blobs (no noise) or the "
                          "paper-scale ellipsoid-phantom recipe (noisy)")
@@ -349,7 +368,7 @@ def main(argv=None):
     eval_seeds = [EVAL_SEED0 + stride * i for i in range(args.eval_pairs)]
     t = time.time()
     X, T, reps = generate(train_seeds, net, max_vox=args.max_vox, contexts=args.contexts, log=log,
-                          workload=args.workload)
+                          workload=args.workload, target_band=args.target_band)
     t_gen = time.time() - t
     n_val = max(1, len(train_seeds) // 20)
     t = time.time()
@@ -357,6 +376,8 @@ def main(argv=None):
     t_train = time.time() - t
     val_err = prediction_error(net, X[:n_val], T[:n_val])
     save_params(net, os.path.join(args.out, "warmstart_params.npz"))
+    if args.weights_out:
+        save_params(net, args.weights_out)
     with open(os.path.join(args.out, "warmstart_train.json"), "w") as f:
         json.dump({"train_pairs": len(train_seeds) - n_val, "val_pairs": n_val,
                    "generate_s": t_gen, "train_s": t_train, "loss_per_epoch": curve,
