@@ -255,20 +255,43 @@ def run_b300(args):
     trace = L.trace_read()
     L.trace_enable(False)
 
-    # ---- SL voxel-steps/s: nt-step scalar transport of the phantom (Table 1 row 1)
+    # ---- SL voxel-steps/s: nt-step scalar transport of the phantom (Table 1 row 1). Device
+    # rate: REPS transports back to back between two events (the host enqueues ahead; the
+    # working set, ~300 MB, exceeds L2); single call: one flushed call, host latency included
+    ntot = nx * ny * nz
+    sl_out = torch.empty_like(fixed_d)
+
+    def sl_rate(fn, reps=10):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return reps * NT * ntot / (e0.elapsed_time(e1) / 1e3)
+
+    sl_vps = sl_rate(lambda: L.sl_transport(V, fixed_d, NT, L.FORWARD, L.INTERP_LINEAR, out=sl_out))
     sl_ms = []
     for i in range(args.warmup + args.steps):
         flush.fill_(1.0)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        L.sl_transport(V, fixed_d, NT, L.FORWARD, L.INTERP_LINEAR)
+        L.sl_transport(V, fixed_d, NT, L.FORWARD, L.INTERP_LINEAR, out=sl_out)
         e1.record(stream)
         e1.synchronize()
         if i >= args.warmup:
             sl_ms.append(e0.elapsed_time(e1))
-    ntot = nx * ny * nz
-    sl_vps = NT * ntot / (statistics.mean(sl_ms) / 1e3)
+    sl_vps_call = NT * ntot / (statistics.mean(sl_ms) / 1e3)
+    # the BF16-storage forms (separately reported mixed-precision variant of the same sweep)
+    sl_bf16 = {"fields_bf16": sl_rate(lambda: L.sl_transport_bf16(V, fixed_d, NT, L.FORWARD, False,
+                                                                  out=sl_out)),
+               "fields_and_offsets_bf16": sl_rate(lambda: L.sl_transport_bf16(V, fixed_d, NT, L.FORWARD,
+                                                                              True, out=sl_out))}
 
     # ---- e2e: the public API with host buffers, copies inside the timing
     # diagnostics of the solution (Sec. 5.1.1): range of det D phi(1)
@@ -299,6 +322,7 @@ def run_b300(args):
         return None
     last = reports[-1]
     per_pair = total_s / (args.steps * world)
+    hbm_peak = peaks["hbm_gbs"]
     # dominant kernel by total device time in the timed region
     name, kt = max(trace.items(), key=lambda kv: kv[1]["ms"])
     avg_ms = kt["ms"] / kt["launches"]
@@ -346,6 +370,10 @@ def run_b300(args):
                        jacobian_det_min=jac_range[0], jacobian_det_max=jac_range[1],
                        max_displacement_vox=max_disp),
         "sl_voxel_steps_per_s": sl_vps,
+        "sl_voxel_steps_per_s_single_call": sl_vps_call,
+        "sl_roofline": {"bytes_per_voxel_step": 20, "achieved_GB_s": sl_vps * 20 / 1e9,
+                        "frac": sl_vps * 20 / 1e9 / hbm_peak},
+        "sl_voxel_steps_per_s_bf16_storage": sl_bf16,
         "e2e": {"value": e2e_total / (args.steps * world), "unit": "s/pair",
                 "h2d_bytes_per_step": 2 * ntot * 4, "d2h_bytes_per_step": 3 * K ** 3 * 8},
         "gpu_launches": launches,

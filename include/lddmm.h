@@ -156,6 +156,19 @@ int lddmm_hessian_matvec(lddmm_ctx* ctx, const float* v, const float* dv, float*
 int lddmm_register(lddmm_ctx* ctx, float* v_inout, const double* g_ref_norms,
                    lddmm_report* report);
 
+/* BF16-storage form of the scalar transport (the mixed-precision variant of the state sweep
+ * D_t m = 0, Table 1 row 1; trilinear SL-RK, Sec. 3.1): the departure offsets are computed in
+ * FP32 exactly as lddmm_sl_transport does, then stored in BF16 (offsets_bf16 = 1) or kept FP32
+ * (0); the field is stored in BF16 between steps (rounded to nearest even after each step);
+ * every interpolation is evaluated in FP32. vel: device [3][nz][ny][nx] in voxels per unit
+ * time; field, out: device [nz][ny][nx] FP32 (out must not be field). Bytes per voxel-step 10
+ * (BF16 offsets) or 16, against 20 for FP32 storage; the error against FP32 storage is that of
+ * the BF16 roundings (about 2^-9 relative per step). Scratch from the stream-ordered pool;
+ * asynchronous on stream. EINVAL before any device work for bad grids, NULL pointers, nt < 1,
+ * a bad direction or flag, or field == out. */
+int lddmm_sl_transport_bf16(int nx, int ny, int nz, int nt, const float* vel, const float* field,
+                            int direction, int offsets_bf16, float* out, void* stream);
+
 /* Persistent batched transport (the batched form; no counterpart in the paper's text): the
  * state sweep D_t m = 0 (Table 1 row 1; SL-RK characteristics Eqs. 40-42 with trilinear
  * interpolation, Sec. 3.1) of n independent pairs with their own grids, all in ONE cooperative

@@ -8,7 +8,7 @@ library is missing, the first call raises.
 
 Names follow the C entry points without their ``lddmm_`` prefix:
 ``bl_project``, ``bl_include``, ``sl_characteristics``, ``sl_transport``,
-``sl_transport_batch``, ``register_batch``,
+``sl_transport_bf16``, ``sl_transport_batch``, ``register_batch``,
 ``device_error``, ``selftest_wait``, ``set_workspace_limit``, the context methods
 ``set_images``, ``objective``, ``gradient``, ``hessian_matvec``, ``register``,
 ``get_warped``, ``history``, ``jacobian_det``, ``max_displacement``, ``set_option``, ``autotune``,
@@ -89,6 +89,7 @@ def _declare(lib):
         "lddmm_bl_include": (_I, [_I, _I, _I, _I, _P, _I, _P, _I, _I, _I, _P]),
         "lddmm_sl_characteristics": (_I, [_I, _I, _I, _P, _D, _I, _I, _P, _P]),
         "lddmm_sl_transport": (_I, [_I, _I, _I, _I, _I, _P, _P, _I, _I, _P, _P]),
+        "lddmm_sl_transport_bf16": (_I, [_I, _I, _I, _I, _P, _P, _I, _I, _P, _P]),
         "lddmm_sl_transport_batch": (_I, [_I, ctypes.POINTER(_I), _I, _I, ctypes.POINTER(_P),
                                           ctypes.POINTER(_P), ctypes.POINTER(_P), _P, _D, _P]),
         "lddmm_register_batch": (_I, [ctypes.POINTER(_P), ctypes.POINTER(_P), _I, _P,
@@ -415,6 +416,20 @@ class Context:
         m = torch.empty(self.shape, dtype=torch.float32, device="cuda") if out is None else out
         _check(load().lddmm_get_warped(self._h, self._field(m, "get_warped: out")))
         return m
+
+
+def sl_transport_bf16(vel, field, nt, direction=FORWARD, offsets_bf16=True, out=None):
+    """Scalar SL transport with BF16 storage of the field between steps (and of the departure
+    offsets with ``offsets_bf16``), FP32 arithmetic (lddmm_sl_transport_bf16)."""
+    import torch
+    nz, ny, nx = field.shape
+    if out is None:
+        out = torch.empty_like(field)
+    _sized(vel, 3 * field.numel(), "sl_transport_bf16: velocity")
+    _sized(out, field.numel(), "sl_transport_bf16: out")
+    _check(load().lddmm_sl_transport_bf16(nx, ny, nz, nt, _f32(vel), _f32(field), direction,
+                                          1 if offsets_bf16 else 0, _f32(out), _stream()))
+    return out
 
 
 def sl_transport_batch(vels, fields, nt, direction=FORWARD, outs=None, active=None,

@@ -431,3 +431,14 @@ def test_batched_transport_rejects_bad_arguments_before_any_device_work():
     assert call(out=(P * 2)(c, b)) == L.EINVAL                                # out = field
     assert b"same buffer" in lib.lddmm_last_error()
     assert call(vel=(P * 2)(a, None)) == L.EINVAL
+
+
+def test_bf16_transport_rejects_bad_arguments_before_any_device_work():
+    lib = L.load()
+    p, q, r = ctypes.c_void_p(256), ctypes.c_void_p(512), ctypes.c_void_p(768)
+    ok = (16, 16, 16, 4, p, q, 1, 1, r, None)
+    for bad in [(1, 16, 16, 4, p, q, 1, 1, r, None), (16, 16, 16, 0, p, q, 1, 1, r, None),
+                (16, 16, 16, 4, p, q, 0, 1, r, None), (16, 16, 16, 4, p, q, 1, 2, r, None),
+                (16, 16, 16, 4, None, q, 1, 1, r, None), (16, 16, 16, 4, p, q, 1, 1, q, None)]:
+        assert lib.lddmm_sl_transport_bf16(*bad) == L.EINVAL
+    assert ok[5] != ok[8]
