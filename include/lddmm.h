@@ -337,11 +337,17 @@ int lddmm_sl_transport(int nx, int ny, int nz, int nt, int interp, const float* 
 typedef struct lddmm_net lddmm_net;
 
 /* Storage of the network's weights and activations: BF16 (the default form) or FP32 (the
- * same kernels with FP32 storage; the reference form for checking the BF16 one). */
-enum { LDDMM_NET_BF16 = 0, LDDMM_NET_FP32 = 1 };
+ * reference form for checking the BF16 one). In both, the 3x3x3 convolutions (forward, input
+ * gradient, weight gradient) run on the tensor cores as implicit GEMMs (tcgen05 kind::tf32,
+ * FP32 accumulation; BF16 operands enter exactly, FP32 operands split hi + lo so that the
+ * products keep FP32 accuracy); the weight gradient of layers narrower than 32 voxels per axis
+ * runs on the FP32 SIMT kernel. LDDMM_NET_BF16_SIMT and LDDMM_NET_FP32_SIMT are the same
+ * networks with every convolution on the FP32 SIMT kernels (the reference for the
+ * tensor-core ones, which sum in another order). */
+enum { LDDMM_NET_BF16 = 0, LDDMM_NET_FP32 = 1, LDDMM_NET_BF16_SIMT = 2, LDDMM_NET_FP32_SIMT = 3 };
 
 /* D a power of two in 8..128, base_channels 1..64, batch_max 1..64 (largest B of later
- * calls), storage LDDMM_NET_BF16 or LDDMM_NET_FP32. Weights He-initialised (normal, std
+ * calls), storage one of the four LDDMM_NET_* forms. Weights He-initialised (normal, std
  * sqrt(2 / (27 cin))) from `seed`, biases 0. Synchronises. Errors: EINVAL, ENOMEM, ECUDA. */
 int lddmm_net_create(int D, int base_channels, int batch_max, int storage,
                      unsigned long long seed, void* stream, lddmm_net** out);

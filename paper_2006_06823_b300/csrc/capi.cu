@@ -1172,7 +1172,11 @@ const char* lddmm_version(void) { return "lddmm-b300 0.1 sm_103a"; }
 int lddmm_device_error(int* code) {
     if (!code) { set_error("code is NULL"); return LDDMM_EINVAL; }
     LDDMM_CUDA(cudaDeviceSynchronize());
-    return tc_take_error(code);
+    int conv = 0;
+    TRY(tc_take_error(code));
+    TRY(tc_conv_take_error(&conv));
+    if (*code == LDDMM_OK) *code = conv;
+    return LDDMM_OK;
 }
 
 int lddmm_selftest_wait(double seconds, int* status) { return wait_selftest(seconds, status); }

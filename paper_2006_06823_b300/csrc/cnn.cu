@@ -25,6 +25,7 @@
 #include <cmath>
 #include <random>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 namespace lddmm {
@@ -411,6 +412,12 @@ struct Net {
     float* gw(int i) const { return n->G + n->L[i].woff; }
     float* gb(int i) const { return n->G + n->L[i].boff; }
 
+    // the convolutions run on the tensor cores (BF16 and FP32 storage); the *_SIMT storage
+    // forms keep the FP32 SIMT kernels as the reference for them
+    bool use_tc() const {
+        return n->storage == LDDMM_NET_BF16 || n->storage == LDDMM_NET_FP32;
+    }
+
     template <typename TI, typename TO>
     int conv(const TI* in, int cin, int D, long in_bs, const TA* Wm, const float* b, int cout, TO* out,
              long out_bs, int out_coff, bool relu, int B, const char* name) const {
@@ -418,6 +425,8 @@ struct Net {
         KTRACE(name, n->st,
                (double)B * vol(D) * (cin * sizeof(TI) + cout * sizeof(TO)) + cout * cin * 27.0 * sizeof(TA),
                2.0 * B * vol(D) * cin * 27.0 * cout);
+        if (use_tc() && tc_conv_supported(cout, D, false))
+            return tc_conv<TI, TA, TO>(in, cin, D, in_bs, Wm, b, cout, out, out_bs, out_coff, relu, B, n->st);
         if (relu)
             k_conv<TI, TA, TO, true><<<grid, 256, 0, n->st>>>(in, cin, lg2(D), in_bs, Wm, b, cout, out, out_bs, out_coff);
         else
@@ -436,8 +445,14 @@ struct Net {
         {
             KTRACE("cnn_wgrad", n->st, (double)B * vol(D) * (cin * sizeof(TA) + cout * 4.0) + cout * Kdim * 8.0,
                    2.0 * total * Kdim * cout);
-            k_conv_wgrad<TA><<<dim3(cdiv_i(Kdim, CV_N), cdiv_i(cout, CV_M), splits), 256, 0, n->st>>>(
-                dout, cout, dout_bs, in, cin, in_bs, lg2(D), B, dW);
+            bool done = false;
+            if (use_tc() && tc_conv_supported(cout, D, true)) {
+                NTRY(tc_conv_wgrad<TA>(dout, cout, dout_bs, in, cin, in_bs, D, B, dW, n->st));
+                done = true;
+            }
+            if (!done)
+                k_conv_wgrad<TA><<<dim3(cdiv_i(Kdim, CV_N), cdiv_i(cout, CV_M), splits), 256, 0, n->st>>>(
+                    dout, cout, dout_bs, in, cin, in_bs, lg2(D), B, dW);
         }
         LDDMM_CHECK_LAUNCH();
         {
@@ -615,16 +630,20 @@ int Net<TA>::backward(const float* dy, int B) const {
     return LDDMM_OK;
 }
 
+bool fp32_storage(const lddmm_net* n) {
+    return n->storage == LDDMM_NET_FP32 || n->storage == LDDMM_NET_FP32_SIMT;
+}
+
 int refresh_weights(lddmm_net* n) {
-    return n->storage == LDDMM_NET_FP32 ? Net<float>{n}.refresh_weights()
+    return fp32_storage(n) ? Net<float>{n}.refresh_weights()
                                         : Net<__nv_bfloat16>{n}.refresh_weights();
 }
 int forward_impl(lddmm_net* n, const float* xin, int B) {
-    return n->storage == LDDMM_NET_FP32 ? Net<float>{n}.forward(xin, B)
+    return fp32_storage(n) ? Net<float>{n}.forward(xin, B)
                                         : Net<__nv_bfloat16>{n}.forward(xin, B);
 }
 int backward_impl(lddmm_net* n, const float* dy, int B) {
-    return n->storage == LDDMM_NET_FP32 ? Net<float>{n}.backward(dy, B)
+    return fp32_storage(n) ? Net<float>{n}.backward(dy, B)
                                         : Net<__nv_bfloat16>{n}.backward(dy, B);
 }
 
@@ -718,9 +737,10 @@ int lddmm_net_create(int D, int base_channels, int batch_max, int storage, unsig
     }
     *out = nullptr;
     if (D < 8 || D > 128 || (D & (D - 1)) || base_channels < 1 || base_channels > 64 ||
-        batch_max < 1 || batch_max > 64 || (storage != LDDMM_NET_BF16 && storage != LDDMM_NET_FP32)) {
+        batch_max < 1 || batch_max > 64 ||
+        storage < LDDMM_NET_BF16 || storage > LDDMM_NET_FP32_SIMT) {
         set_error("net_create: D must be a power of two in 8..128, base_channels 1..64, batch_max "
-                  "1..64, storage LDDMM_NET_BF16 or LDDMM_NET_FP32");
+                  "1..64, storage LDDMM_NET_BF16, LDDMM_NET_FP32, LDDMM_NET_BF16_SIMT or LDDMM_NET_FP32_SIMT");
         return LDDMM_EINVAL;
     }
     lddmm_net* n = new lddmm_net();
@@ -728,7 +748,7 @@ int lddmm_net_create(int D, int base_channels, int batch_max, int storage, unsig
     n->c = base_channels;
     n->bmax = batch_max;
     n->storage = storage;
-    n->esz = storage == LDDMM_NET_FP32 ? sizeof(float) : sizeof(__nv_bfloat16);
+    n->esz = fp32_storage(n) ? sizeof(float) : sizeof(__nv_bfloat16);
     n->st = static_cast<cudaStream_t>(stream);
     int rc = net_alloc(n, seed);
     if (rc == LDDMM_OK) rc = refresh_weights(n);

@@ -155,6 +155,20 @@ int dot_f2_nodes(const float2* a, const float2* b, long npn, int nodes, double d
                  double* partials, double* out, cudaStream_t st);
 constexpr int kReduceBlocks = 296;  // 2 x 148 SMs
 
+// ---------------------------------------------------------------- tensor-core convolutions
+// 3x3x3 convolutions of the warm-start network on tcgen05 (tc_conv.cu). W: stored weights
+// [cout][cin * 27] (the forward weights, or the transposed tap-flipped ones for the input
+// gradient), BF16 or FP32; TI / TO: the stored activation type or FP32 (gradients, output).
+bool tc_conv_supported(int cout, int D, bool wgrad);
+template <typename TI, typename TW, typename TO>
+int tc_conv(const TI* in, int cin, int D, long in_bstride, const TW* W, const float* bias,
+            int cout, TO* out, long out_bstride, int out_coff, bool relu, int B, cudaStream_t st);
+// dW[co][ci * 27 + t] += sum over the B samples of dout[b][co][v] in[b][ci][v + o(t)]
+template <typename TA>
+int tc_conv_wgrad(const float* dout, int cout, long dout_bstride, const TA* in, int cin,
+                  long in_bstride, int D, int B, float* dW, cudaStream_t st);
+int tc_conv_take_error(int* code);
+
 // ---------------------------------------------------------------- spatial form (spatial.cu)
 // Full-grid FFT plans and buffers of one context (cuFFT R2C / C2R on its stream).
 struct SpatialFFT;

@@ -121,7 +121,7 @@ def test_null_context_is_rejected():
 
 @pytest.mark.parametrize("D,c,B,st", [(48, 4, 1, 0), (4, 4, 1, 0), (256, 4, 1, 0), (64, 0, 1, 0),
                                       (64, 65, 1, 0), (64, 16, 0, 0), (64, 16, 65, 0),
-                                      (64, 16, 8, 2), (64, 16, 8, -1)])
+                                      (64, 16, 8, 4), (64, 16, 8, -1)])
 def test_net_create_rejects_bad_shapes_before_any_device_work(D, c, B, st):
     lib = L.load()
     h = ctypes.c_void_p(123)
@@ -180,6 +180,14 @@ def test_report_struct_of_the_binding_follows_the_header():
             names += [n.strip() for n in decl.split(None, 1)[1].split(",")]
     assert names == [n for n, _ in L.Report._fields_]
     assert names[-1] == "pcg_inner_total"
+
+
+def test_network_storage_codes_of_the_binding_follow_the_header():
+    import re
+    codes = dict(re.findall(r"LDDMM_NET_(\w+) = (\d+)", _header_text()))
+    assert {k: int(v) for k, v in codes.items()} == {
+        "BF16": L.NET_BF16, "FP32": L.NET_FP32, "BF16_SIMT": L.NET_BF16_SIMT,
+        "FP32_SIMT": L.NET_FP32_SIMT}
 
 
 def test_option_codes_of_the_binding_follow_the_header():

@@ -63,10 +63,14 @@ def rel(a, b):
 CASES = [(16, 4, 2, 0), (16, 3, 1, 1), (32, 2, 3, 2), (32, 8, 2, 3)]   # (D, c, batch, seed)
 
 
+def is_bf16(L, storage):
+    return storage in (L.NET_BF16, L.NET_BF16_SIMT)
+
+
 def run_case(L, D, c, B, seed, storage, sample=None):
     net = L.Net(D, c, batch_max=B, seed=seed, storage=storage)
     p = net.get_params().cpu().numpy().astype(np.float64)
-    P = unpack(p, c, round_weights=storage == L.NET_BF16)
+    P = unpack(p, c, round_weights=is_bf16(L, storage))
     x = synth.random_field((D, D, D), seed + 11, ncomp=2 * B, smooth=1.5).reshape(B, 2, D, D, D)
     dy = synth.rng(seed + 10).standard_normal((B, 3, D // 2, D // 2, D // 2))
     if sample is not None:          # gradient of one sample of the batch alone
@@ -76,7 +80,7 @@ def run_case(L, D, c, B, seed, storage, sample=None):
     grads = net.gradients(xd, torch.as_tensor(dy, dtype=torch.float32, device="cuda").contiguous())
     grads = grads.cpu().double().numpy()
     net.close()
-    mode = "bf16" if storage == L.NET_BF16 else None
+    mode = "bf16" if is_bf16(L, storage) else None
     ys, gref = [], None
     for b in range(B) if sample is None else [sample]:
         yr, cache = ON.forward(P, x[b], storage=mode)
@@ -96,28 +100,33 @@ def layer_errors(g_gpu, g_ref, c):
     return out
 
 
+# the tensor-core convolutions (the default) and the FP32 SIMT ones (the *_SIMT forms); with
+# FP32 storage both must reach the FP64 network's values to FP32 accuracy, which checks the
+# tensor-core kernels (operand split, swizzled layouts, zero padding, every layer's shape) tightly
+@pytest.mark.parametrize("storage", ["FP32", "FP32_SIMT"])
 @pytest.mark.parametrize("D,c,B,seed", CASES)
-def test_fp32_storage_matches_fp64_network(L, D, c, B, seed):
-    ey, layers = run_case(L, D, c, B, seed, L.NET_FP32)
+def test_fp32_storage_matches_fp64_network(L, D, c, B, seed, storage):
+    ey, layers = run_case(L, D, c, B, seed, getattr(L, "NET_" + storage))
     assert ey <= 1e-5, ey
     for name, r, cos in layers:
         assert r <= 1e-4, (name, r)
 
 
+@pytest.mark.parametrize("storage", ["BF16", "BF16_SIMT"])
 @pytest.mark.parametrize("D,c,B,seed", CASES)
-def test_bf16_storage_matches_bf16_model(L, D, c, B, seed):
-    ey, layers = run_case(L, D, c, B, seed, L.NET_BF16)
+def test_bf16_storage_matches_bf16_model(L, D, c, B, seed, storage):
+    ey, layers = run_case(L, D, c, B, seed, getattr(L, "NET_" + storage))
     assert ey <= 1e-2, ey
     for name, r, cos in layers:
         assert cos >= 0.95 and r <= 0.35, (name, r, cos)
 
 
-@pytest.mark.parametrize("storage", [0, 1])
+@pytest.mark.parametrize("storage", [0, 1, 2, 3])
 def test_full_size_sample(L, storage):
     """The configuration the warm start trains (D = 64, 16 base channels, batch 8): sample
     5 of a batch of 8 against the reference, forward and weight gradients."""
     ey, layers = run_case(L, 64, 16, 8, 3, storage, sample=5)
-    if storage == L.NET_FP32:
+    if not is_bf16(L, storage):
         assert ey <= 1e-5, ey
         assert all(r <= 1e-4 for _, r, _ in layers), layers
     else:
