@@ -336,15 +336,17 @@ int lddmm_sl_transport(int nx, int ny, int nz, int nt, int interp, const float* 
  * stream, are not thread-safe on one object, and are asynchronous unless stated. */
 typedef struct lddmm_net lddmm_net;
 
-/* Storage of the network's weights and activations: BF16 (the default form) or FP32 (the
- * reference form for checking the BF16 one). In both, the 3x3x3 convolutions (forward, input
+/* Storage of the network's weights and activations and the kernels of its convolutions.
+ * LDDMM_NET_BF16 (the default form): BF16 storage; the 3x3x3 convolutions (forward, input
  * gradient, weight gradient) run on the tensor cores as implicit GEMMs (tcgen05 kind::tf32,
- * FP32 accumulation; BF16 operands enter exactly, FP32 operands split hi + lo so that the
- * products keep FP32 accuracy); the weight gradient of layers narrower than 32 voxels per axis
- * runs on the FP32 SIMT kernel. LDDMM_NET_BF16_SIMT and LDDMM_NET_FP32_SIMT are the same
- * networks with every convolution on the FP32 SIMT kernels (the reference for the
- * tensor-core ones, which sum in another order). */
-enum { LDDMM_NET_BF16 = 0, LDDMM_NET_FP32 = 1, LDDMM_NET_BF16_SIMT = 2, LDDMM_NET_FP32_SIMT = 3 };
+ * FP32 accumulation; BF16 operands enter exactly, FP32 gradients split hi + lo), except the
+ * weight gradient of layers narrower than 32 voxels per axis (FP32 SIMT kernel).
+ * LDDMM_NET_FP32: FP32 storage with the FP32 SIMT convolutions, the reference form for
+ * checking the BF16 one. LDDMM_NET_BF16_SIMT: BF16 storage with the FP32 SIMT convolutions
+ * (the reference for the tensor-core ones, which sum in another order). LDDMM_NET_FP32_TC:
+ * FP32 storage with the tensor-core convolutions, every FP32 operand split hi + lo (products
+ * within about 2^-21 relative of FP32's), to check those kernels against FP32 arithmetic. */
+enum { LDDMM_NET_BF16 = 0, LDDMM_NET_FP32 = 1, LDDMM_NET_BF16_SIMT = 2, LDDMM_NET_FP32_TC = 3 };
 
 /* D a power of two in 8..128, base_channels 1..64, batch_max 1..64 (largest B of later
  * calls), storage one of the four LDDMM_NET_* forms. Weights He-initialised (normal, std

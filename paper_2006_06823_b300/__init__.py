@@ -35,7 +35,7 @@ PREC_FP32, PREC_BF16X3, PREC_FP32_SIMT, PREC_BF16X3_JBF16 = 0, 1, 2, 3
 FORWARD, BACKWARD = 1, -1
 STOP_GTOL, STOP_MAXIT, STOP_LINESEARCH = 1, 2, 3
 OPT_GRAPHS, OPT_BLOCK_X, OPT_GATHER_ZT, OPT_TWO_LEVEL = 1, 2, 3, 4
-NET_BF16, NET_FP32, NET_BF16_SIMT, NET_FP32_SIMT = 0, 1, 2, 3
+NET_BF16, NET_FP32, NET_BF16_SIMT, NET_FP32_TC = 0, 1, 2, 3
 
 
 class Params(ctypes.Structure):

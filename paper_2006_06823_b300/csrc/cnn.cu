@@ -412,10 +412,10 @@ struct Net {
     float* gw(int i) const { return n->G + n->L[i].woff; }
     float* gb(int i) const { return n->G + n->L[i].boff; }
 
-    // the convolutions run on the tensor cores (BF16 and FP32 storage); the *_SIMT storage
-    // forms keep the FP32 SIMT kernels as the reference for them
+    // the convolutions run on the tensor cores for BF16 storage (the default) and the FP32
+    // tensor-core check form; FP32 storage and LDDMM_NET_BF16_SIMT keep the FP32 SIMT kernels
     bool use_tc() const {
-        return n->storage == LDDMM_NET_BF16 || n->storage == LDDMM_NET_FP32;
+        return n->storage == LDDMM_NET_BF16 || n->storage == LDDMM_NET_FP32_TC;
     }
 
     template <typename TI, typename TO>
@@ -631,7 +631,7 @@ int Net<TA>::backward(const float* dy, int B) const {
 }
 
 bool fp32_storage(const lddmm_net* n) {
-    return n->storage == LDDMM_NET_FP32 || n->storage == LDDMM_NET_FP32_SIMT;
+    return n->storage == LDDMM_NET_FP32 || n->storage == LDDMM_NET_FP32_TC;
 }
 
 int refresh_weights(lddmm_net* n) {
@@ -738,9 +738,9 @@ int lddmm_net_create(int D, int base_channels, int batch_max, int storage, unsig
     *out = nullptr;
     if (D < 8 || D > 128 || (D & (D - 1)) || base_channels < 1 || base_channels > 64 ||
         batch_max < 1 || batch_max > 64 ||
-        storage < LDDMM_NET_BF16 || storage > LDDMM_NET_FP32_SIMT) {
+        storage < LDDMM_NET_BF16 || storage > LDDMM_NET_FP32_TC) {
         set_error("net_create: D must be a power of two in 8..128, base_channels 1..64, batch_max "
-                  "1..64, storage LDDMM_NET_BF16, LDDMM_NET_FP32, LDDMM_NET_BF16_SIMT or LDDMM_NET_FP32_SIMT");
+                  "1..64, storage LDDMM_NET_BF16, LDDMM_NET_FP32, LDDMM_NET_BF16_SIMT or LDDMM_NET_FP32_TC");
         return LDDMM_EINVAL;
     }
     lddmm_net* n = new lddmm_net();

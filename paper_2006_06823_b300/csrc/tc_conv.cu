@@ -13,11 +13,11 @@
 //
 // Operands are FP32 words in the 128-byte-swizzled K-major layout (32 per row). BF16 values
 // (the stored weights and activations of the BF16 network) are exact in TF32, so they enter
-// the MMA unchanged; FP32 operands (the gradients, and everything of the FP32-storage network)
-// are split hi + lo (hi = TF32 truncation, lo = x - hi, exact) and the products
-// A_hi B_hi + A_lo B_hi + A_hi B_lo are accumulated, so every product is the FP32 product up
-// to about 2^-21 relative (the dropped A_lo B_lo and the TF32 truncation of lo), as in the
-// FP32 SIMT kernels these replace; the sums are FP32.
+// the MMA unchanged; FP32 operands (the gradients, and every operand of the FP32 tensor-core
+// check form) are split hi + lo, hi = x rounded to TF32, lo = (x - hi) rounded to TF32
+// (|x - hi - lo| <= 2^-22 |x|), and the products A_hi B_hi + A_lo B_hi + A_hi B_lo are
+// accumulated, so every product is the FP32 product up to about 2^-21 relative (the dropped
+// A_lo B_lo and the rounding of lo), against 2^-24 for the FP32 SIMT kernels; sums are FP32.
 //
 // One CTA of 128 threads per output tile: for each 32-wide K chunk all threads build the
 // next chunk's operands into the free one of two smem stages while the MMAs of the previous
@@ -112,8 +112,12 @@ __device__ __forceinline__ void tmem_ld32(unsigned taddr, float (&v)[32]) {
 #pragma unroll
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
-__device__ __forceinline__ float tf32_hi(float x) {
-    return __uint_as_float(__float_as_uint(x) & 0xFFFFE000u);
+// x rounded to TF32 (nearest, ties away), as an FP32 bit pattern with the low 13 bits zero, so
+// that the tensor core's reading of the upper 19 bits is exact
+__device__ __forceinline__ float tf32_rna(float x) {
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;\n" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
 }
 __device__ __forceinline__ float ldv(const float* p) { return *p; }
 __device__ __forceinline__ float ldv(const __nv_bfloat16* p) { return __bfloat162float(*p); }
@@ -278,8 +282,8 @@ k_conv_tc(const TI* __restrict__ in, int cin, int lgD, long in_bstride,
                 if (k0 + kk < Kdim && ((mask >> t) & 1u))
                     val = ldv(inb + (long)ci * nv + v + tap_off(t, lgD));
                 if (SPLIT_A) {
-                    hi[kk] = tf32_hi(val);
-                    lo[kk] = val - hi[kk];
+                    hi[kk] = tf32_rna(val);
+                    lo[kk] = tf32_rna(val - hi[kk]);
                 } else {
                     hi[kk] = val;
                 }
@@ -299,8 +303,8 @@ k_conv_tc(const TI* __restrict__ in, int cin, int lgD, long in_bstride,
             for (int kk = 0; kk < KC; ++kk) {
                 const float val = (co < cout && k0 + kk < Kdim) ? ldv(W + (long)co * Kdim + k0 + kk) : 0.f;
                 if (SPLIT_B) {
-                    w[kk] = tf32_hi(val);
-                    wl[kk] = val - w[kk];
+                    w[kk] = tf32_rna(val);
+                    wl[kk] = tf32_rna(val - w[kk]);
                 } else {
                     w[kk] = val;
                 }
@@ -376,8 +380,8 @@ k_conv_wgrad_tc(const float* __restrict__ dout, int cout, long dout_bstride,
                 const int xx = x0 + i + dx;
                 const float val = (rowok && (unsigned)xx < (unsigned)D) ? ldv(src + xx) : 0.f;
                 if (SPLIT_A) {
-                    a[i] = tf32_hi(val);
-                    al[i] = val - a[i];
+                    a[i] = tf32_rna(val);
+                    al[i] = tf32_rna(val - a[i]);
                 } else {
                     a[i] = val;
                 }
@@ -395,8 +399,8 @@ k_conv_wgrad_tc(const float* __restrict__ dout, int cout, long dout_bstride,
                 const float f[4] = {f4.x, f4.y, f4.z, f4.w};
 #pragma unroll
                 for (int e = 0; e < 4; ++e) {
-                    hi[4 * j + e] = tf32_hi(f[e]);
-                    lo[4 * j + e] = f[e] - hi[4 * j + e];
+                    hi[4 * j + e] = tf32_rna(f[e]);
+                    lo[4 * j + e] = tf32_rna(f[e] - hi[4 * j + e]);
                 }
             }
             put_row(bhi, co, hi);

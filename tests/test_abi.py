@@ -187,7 +187,7 @@ def test_network_storage_codes_of_the_binding_follow_the_header():
     codes = dict(re.findall(r"LDDMM_NET_(\w+) = (\d+)", _header_text()))
     assert {k: int(v) for k, v in codes.items()} == {
         "BF16": L.NET_BF16, "FP32": L.NET_FP32, "BF16_SIMT": L.NET_BF16_SIMT,
-        "FP32_SIMT": L.NET_FP32_SIMT}
+        "FP32_TC": L.NET_FP32_TC}
 
 
 def test_option_codes_of_the_binding_follow_the_header():
