@@ -258,7 +258,7 @@ static int max_abs(lddmm_ctx* c, const float2* v, long nf2, double* out) {
 
 // the Jacobian planes of node j, as the Hessian (hess) or the gradient reads them
 static const void* jac(const lddmm_ctx* c, int j, bool hess) {
-    if (hess && jac_bf16(c)) return static_cast<const uint16_t*>(c->Du16) + (long)j * 9 * c->n;
+    if (hess && jac_bf16(c)) return static_cast<const uint16_t*>(c->Du16) + (long)j * jac_bf16_stride(c->n);
     return c->Du + (long)j * 9 * c->n;
 }
 static bool cubic(const lddmm_ctx* c) { return c->p.interp == LDDMM_INTERP_CUBIC; }
@@ -467,7 +467,7 @@ static int ensure_traj(lddmm_ctx* c) {
             for (int b = 0; b < 3; ++b)
                 TRY(include(c, c->ut + (long)j * 3 * c->kc, 3, c->Du + (long)j * 9 * n + b * n,
                             3 * n, b, 0));
-        if (jac_bf16(c)) TRY(to_bf16(c->Du, c->Du16, (long)(c->p.nt + 1) * 9 * n, c->st));
+        if (jac_bf16(c)) TRY(pack_jac_bf16(c->Du, c->Du16, n, c->p.nt + 1, c->st));
         if (state_eq(c)) TRY(state_traj(c));
     } else {
         float2* mt = c->cv[lddmm_ctx::C_T1];
@@ -1067,7 +1067,8 @@ static int ctx_alloc(lddmm_ctx* c) {
         TRY(dalloc_t(c, &c->W, steps * 3 * n));
         TRY(dalloc_t(c, &c->ut, (size_t)(nt + 1) * kc3));
         TRY(dalloc_t(c, &c->Du, (size_t)(nt + 1) * 9 * n));
-        if (jac_bf16(c)) TRY(dalloc_t(c, reinterpret_cast<uint16_t**>(&c->Du16), (size_t)(nt + 1) * 9 * n));
+        if (jac_bf16(c))
+            TRY(dalloc_t(c, reinterpret_cast<uint16_t**>(&c->Du16), (size_t)(nt + 1) * jac_bf16_stride(n)));
         TRY(dalloc_t(c, &c->G, 3 * n));
         TRY(dalloc_t(c, &c->m1, n));
     } else {

@@ -244,8 +244,11 @@ int accum_JT(const Grid& g, const void* Du, bool du_bf16, const float* R, float 
              int init, cudaStream_t st);
 // J = det(I - Du) per voxel (J may be NULL) and kReduceBlocks per-block minima / maxima
 int jacobian_det(const Grid& g, const float* Du, float* J, double* pmin, double* pmax, cudaStream_t st);
-// out[i] = bf16(in[i]), i < n (round to nearest even)
-int to_bf16(const float* in, void* out, long n, cudaStream_t st);
+// Jacobian planes in the packed BF16 form the Hessian kernels read: per node, the 8 entries
+// Du[0..7] of each voxel as one 16-byte word ([n] words), then the plane of Du[8]; node stride
+// jac_bf16_stride(n) BF16 elements (16-byte aligned); round to nearest even
+long jac_bf16_stride(long n);
+int pack_jac_bf16(const float* in, void* out, long n, int nodes, cudaStream_t st);
 // out[i] = v, i < n
 int fill_field(float* out, float v, long n, cudaStream_t st);
 // x_out = a * x (n floats)

@@ -754,8 +754,22 @@ int state_dlam1(const Grid& g, const float* G, const float* du1, double sigma2, 
 }
 
 // ---------------------------------------------------------------- incremental state
-__device__ __forceinline__ float ldj(const float* p) { return *p; }
-__device__ __forceinline__ float ldj(const __nv_bfloat16* p) { return __bfloat162float(*p); }
+// The nine Jacobian entries Du[3a + b] = d u_a / d x_b of voxel i: FP32 planes [9][n], or the
+// packed BF16 form [n] x 8 entries (one 16-byte load) followed by the plane of entry 8.
+__device__ __forceinline__ void load_jac9(const float* __restrict__ Du, int n, int i, float j[9]) {
+#pragma unroll
+    for (int k = 0; k < 9; ++k) j[k] = __ldcs(Du + k * n + i);
+}
+__device__ __forceinline__ void load_jac9(const __nv_bfloat16* __restrict__ Du, int n, int i, float j[9]) {
+    const uint4 p = __ldcs(reinterpret_cast<const uint4*>(Du) + i);
+    const unsigned w[4] = {p.x, p.y, p.z, p.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        j[2 * k] = __uint_as_float(w[k] << 16);
+        j[2 * k + 1] = __uint_as_float(w[k] & 0xFFFF0000u);
+    }
+    j[8] = __bfloat162float(Du[8 * n + i]);
+}
 
 // D~_t du~ = dv~ - D~u~ * dv~ (Table 1 row 7): F = dv - (Du) dv, Heun along X.
 template <int IP, typename TJ>
@@ -766,11 +780,11 @@ k_inc_defstate(Grid g, const float* __restrict__ U, const float* __restrict__ D,
                                float* __restrict__ Fnew) {
     VOXEL_PROLOGUE
     float w0 = dv[i], w1 = dv[n + i], w2 = dv[2 * n + i];
-    float F[3];
+    float F[3], J[9];
+    load_jac9(Du, (int)n, i, J);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        float j0 = ldj(Du + (3 * c + 0) * n + i), j1 = ldj(Du + (3 * c + 1) * n + i),
-              j2 = ldj(Du + (3 * c + 2) * n + i);
+        const float j0 = J[3 * c], j1 = J[3 * c + 1], j2 = J[3 * c + 2];
         F[c] = (c == 0 ? w0 : c == 1 ? w1 : w2) - (j0 * w0 + j1 * w1 + j2 * w2);
     }
     Interp<IP> it(g, x, y, z, D[i], D[n + i], D[2 * n + i]);
@@ -806,10 +820,11 @@ k_inc_defstate_zt(Grid g, const float* __restrict__ U, const float* __restrict__
         const float e0 = __ldcs(D + ip), e1 = __ldcs(D + n + ip), e2 = __ldcs(D + 2 * n + ip);
         const Interp<IP> it(g, x, y, z, d0, d1, d2);
         const float w0 = __ldcs(dv + i), w1 = __ldcs(dv + n + i), w2 = __ldcs(dv + 2 * n + i);
+        float J[9];
+        load_jac9(Du, n, i, J);
 #pragma unroll
         for (int a = 0; a < 3; ++a) {
-            const float j0 = ldj(Du + (3 * a + 0) * n + i), j1 = ldj(Du + (3 * a + 1) * n + i),
-                        j2 = ldj(Du + (3 * a + 2) * n + i);
+            const float j0 = J[3 * a], j1 = J[3 * a + 1], j2 = J[3 * a + 2];
             const float F = (a == 0 ? w0 : a == 1 ? w1 : w2) - (j0 * w0 + j1 * w1 + j2 * w2);
             __stcs(out + a * n + i, it(U + a * n) + h * (it(Fold + a * n) + F));
             __stcs(Fnew + a * n + i, F);
@@ -860,10 +875,11 @@ __global__ void k_defstate_rhs(long n, const TJ* __restrict__ Du, const float* _
     long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float w0 = dv[i], w1 = dv[n + i], w2 = dv[2 * n + i];
+    float J[9];
+    load_jac9(Du, (int)n, (int)i, J);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        float j0 = ldj(Du + (3 * c + 0) * n + i), j1 = ldj(Du + (3 * c + 1) * n + i),
-              j2 = ldj(Du + (3 * c + 2) * n + i);
+        const float j0 = J[3 * c], j1 = J[3 * c + 1], j2 = J[3 * c + 2];
         F[c * n + i] = (c == 0 ? w0 : c == 1 ? w1 : w2) - (j0 * w0 + j1 * w1 + j2 * w2);
     }
 }
@@ -880,14 +896,35 @@ int defstate_rhs(const Grid& g, const void* Du, bool du_bf16, const float* dv, f
     return LDDMM_OK;
 }
 
-__global__ void k_to_bf16(const float* __restrict__ in, __nv_bfloat16* __restrict__ out, long n) {
-    for (long i = (long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
-        out[i] = __float2bfloat16_rn(in[i]);
+// FP32 Jacobian planes of `nodes` nodes ([node][9][n]) -> the packed BF16 form read by
+// load_jac9 (per node: [n] x entries 0..7 as one 16-byte word, then the plane of entry 8;
+// node stride jac_bf16_stride(n) elements), each entry rounded to nearest even.
+__global__ void k_pack_jac_bf16(const float* __restrict__ in, __nv_bfloat16* __restrict__ out,
+                                long n, int nodes, long stride) {
+    const long total = n * nodes;
+    for (long t = (long)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (long)gridDim.x * blockDim.x) {
+        const long node = t / n, i = t - node * n;
+        const float* src = in + node * 9 * n + i;
+        __nv_bfloat16* dst = out + node * stride;
+        unsigned w[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            const unsigned lo = __bfloat16_as_ushort(__float2bfloat16_rn(__ldcs(src + (2 * k) * n)));
+            const unsigned hi = __bfloat16_as_ushort(__float2bfloat16_rn(__ldcs(src + (2 * k + 1) * n)));
+            w[k] = lo | (hi << 16);
+        }
+        reinterpret_cast<uint4*>(dst)[i] = make_uint4(w[0], w[1], w[2], w[3]);
+        dst[8 * n + i] = __float2bfloat16_rn(__ldcs(src + 8 * n));
+    }
 }
 
-int to_bf16(const float* in, void* out, long n, cudaStream_t st) {
-    KTRACE("to_bf16", st, 6.0 * n, 0);
-    k_to_bf16<<<(int)std::min<long>(cdiv(n, 256), 16 * 148), 256, 0, st>>>(in, static_cast<__nv_bfloat16*>(out), n);
+long jac_bf16_stride(long n) { return (9 * n + 7) & ~7L; }
+
+int pack_jac_bf16(const float* in, void* out, long n, int nodes, cudaStream_t st) {
+    KTRACE("to_bf16", st, 54.0 * n * nodes, 0);
+    const long total = n * nodes;
+    k_pack_jac_bf16<<<(int)std::min<long>(cdiv(total, 256), 16 * 148), 256, 0, st>>>(
+        in, static_cast<__nv_bfloat16*>(out), n, nodes, jac_bf16_stride(n));
     LDDMM_CHECK_LAUNCH();
     return LDDMM_OK;
 }
@@ -920,10 +957,11 @@ __global__ void k_accum_JT(long n, const TJ* __restrict__ Du, const float* __res
     long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float r0 = R[i], r1 = R[n + i], r2 = R[2 * n + i];
+    float J[9];
+    load_jac9(Du, (int)n, (int)i, J);
 #pragma unroll
     for (int b = 0; b < 3; ++b) {
-        float s = ldj(Du + (0 + b) * n + i) * r0 + ldj(Du + (3 + b) * n + i) * r1 +
-                  ldj(Du + (6 + b) * n + i) * r2;
+        float s = J[b] * r0 + J[3 + b] * r1 + J[6 + b] * r2;
         acc[b * n + i] = init ? w * s : fmaf(w, s, acc[b * n + i]);
     }
 }
