@@ -420,51 +420,6 @@ k_sl_gather_zt1(Grid g, const float* __restrict__ src, const float* __restrict__
     }
 }
 
-// Plain trilinear gather of one field, zt consecutive z planes per thread taken two at a time:
-// the 16 taps of planes z and z + 1 are in flight together while the offsets of planes z + 2
-// and z + 3 load (twice the independent loads per thread of k_sl_gather_zt1; the same
-// arithmetic per voxel, so the results are bitwise those of the one-plane kernels).
-__global__ void __launch_bounds__(256, 4)
-k_sl_gather_zt2p(Grid g, const float* __restrict__ src, const float* __restrict__ D,
-                 float* __restrict__ out, int zt) {
-    const int x = blockIdx.x * blockDim.x + threadIdx.x;
-    const int y = blockIdx.y * blockDim.y + threadIdx.y;
-    if (x >= g.nx || y >= g.ny) return;
-    const int n = (int)g.ntot();             // 3 n < 2^31 (checked at context creation)
-    const int plane = g.nx * g.ny;
-    int z = blockIdx.z * zt;
-    const int zend = min(z + zt, g.nz);
-    if (z >= zend) return;
-    int i = (z * g.ny + y) * g.nx + x;
-    // offsets of the current pair of planes (the second one only if it exists)
-    bool two = z + 1 < zend;
-    int i1 = two ? i + plane : i;
-    float d0 = __ldcs(D + i), d1 = __ldcs(D + n + i), d2 = __ldcs(D + 2 * n + i);
-    float e0 = __ldcs(D + i1), e1 = __ldcs(D + n + i1), e2 = __ldcs(D + 2 * n + i1);
-    for (;;) {
-        const bool more = z + 2 < zend;
-        const bool two_next = z + 3 < zend;
-        const int j0 = more ? i + 2 * plane : i;
-        const int j1 = two_next ? i + 3 * plane : j0;
-        // next pair's offsets, issued before this pair's taps are consumed
-        const float f0 = __ldcs(D + j0), f1 = __ldcs(D + n + j0), f2 = __ldcs(D + 2 * n + j0);
-        const float h0 = __ldcs(D + j1), h1 = __ldcs(D + n + j1), h2 = __ldcs(D + 2 * n + j1);
-        const LinCell ca = lin_cell(g, x, y, z, d0, d1, d2);
-        const LinCell cb = lin_cell(g, x, y, two ? z + 1 : z, e0, e1, e2);
-        const float va = lin_eval(src, ca);
-        const float vb = lin_eval(src, cb);
-        __stcs(out + i, va);
-        if (two) __stcs(out + i1, vb);
-        if (!more) break;
-        z += 2;
-        i = j0;
-        i1 = j1;
-        two = two_next;
-        d0 = f0; d1 = f1; d2 = f2;
-        e0 = h0; e1 = h1; e2 = h2;
-    }
-}
-
 // Trilinear gather, four consecutive x voxels per thread (nx % 4 == 0): float4 offset loads
 // and stores, 4 x 8 independent gathers per component in flight.
 template <int MODE, int NC>
@@ -518,13 +473,7 @@ static void launch_gather_nc(const SLArgs& a, const float* src, const float* D, 
         const float* s = src + c0 * n;
         const float* x = MODE == 2 ? aux + c0 * n : aux;
         float* o = out + c0 * n;
-        if (IP == 1 && MODE == 0 && left < 3 && zt_of(a) > 2) {
-            // plain single fields on grids that fill the GPU: planes taken two at a time
-            const int zt = zt_of(a);
-            k_sl_gather_zt2p<<<dim3(cdiv(a.g.nx, a.bx), cdiv(a.g.ny, a.by), cdiv(a.g.nz, zt)),
-                               dim3(a.bx, a.by, 1), 0, st>>>(a.g, s, D, o, zt);
-            c0 += 1;
-        } else if (IP == 1 && left < 3 && zt_of(a) > 1) {
+        if (IP == 1 && left < 3 && zt_of(a) > 1) {
             // single fields on grids that fill the GPU: one voxel per thread, z-pipelined
             const int zt = zt_of(a);
             k_sl_gather_zt1<IP, MODE, 1><<<dim3(cdiv(a.g.nx, a.bx), cdiv(a.g.ny, a.by), cdiv(a.g.nz, zt)),
