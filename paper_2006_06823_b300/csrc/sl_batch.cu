@@ -1,7 +1,8 @@
 // Persistent batched SL transport: the state sweep D_t m = 0 (Table 1 row 1; Sec. 3.1,
 // Eqs. 40-43) of many independent image pairs of different grid sizes in ONE cooperative
-// launch. Every block takes tiles of 256 consecutive voxels from one work list that spans all
-// active pairs; the characteristics (trilinear, RK2) are computed for every pair first, then
+// launch. Every block takes tiles (32 x 8 voxels in x, y, four consecutive z planes per thread)
+// from one work list that spans all active pairs; the characteristics (trilinear, RK2) are
+// computed for every pair first, then
 // the nt gather steps follow, separated by a grid-wide barrier (step j + 1 reads what step j
 // wrote, anywhere in the same pair's grid).
 //
@@ -26,11 +27,13 @@ namespace lddmm {
 namespace {
 
 constexpr int kBatchMaxPairs = 256;
-constexpr int kTile = 256;   // voxels per tile (one thread each)
+constexpr int kTile = 256;   // threads per block: 32 x 8 (x, y), each over kZt consecutive z planes
+constexpr int kTx = 32, kTy = 8, kZt = 4;
 
 struct BatchPair {
     int nx, ny, nz;
     int active;
+    int tx, txy;             // tiles along x, and per z block (tx * ty)
     long tile0;              // first tile of this pair in the work list
     const float* vel;        // 3 planes, voxels per unit time
     const float* field;
@@ -141,45 +144,66 @@ __device__ __forceinline__ int pair_of(const BatchTable& tb, int npairs, long t)
     return lo;
 }
 
-__global__ void __launch_bounds__(kTile)
+// tile t of pair P: this thread's (x, y) and first z plane; false if outside the grid
+__device__ __forceinline__ bool tile_voxel(const BatchPair& P, long t, int& x, int& y, int& z, int& zend) {
+    const int tl = (int)(t - P.tile0);
+    const int bz = tl / P.txy, r = tl - bz * P.txy;
+    const int by = r / P.tx, bx = r - by * P.tx;
+    x = bx * kTx + (int)(threadIdx.x & (kTx - 1));
+    y = by * kTy + (int)(threadIdx.x / kTx);
+    z = bz * kZt;
+    zend = min(z + kZt, P.nz);
+    return x < P.nx && y < P.ny && z < zend;
+}
+
+__global__ void __launch_bounds__(kTile, 5)
 k_sl_transport_batch(const __grid_constant__ BatchTable tb, int npairs, long ntiles, int nt,
                      float dts, unsigned* bar, unsigned extra_arrivals,
                      unsigned long long limit_ns, int* status) {
     const unsigned expected = gridDim.x + extra_arrivals;
+    const float h = 0.5f * dts;
     // ---- characteristics: D = dt/2 (v(X*) + v(x)), X* = x + dts v(x)  (dts = -dt forward)
     for (long t = blockIdx.x; t < ntiles; t += gridDim.x) {
         const BatchPair& P = tb.p[pair_of(tb, npairs, t)];
-        if (!P.active) continue;
-        const int n = P.nx * P.ny * P.nz;
-        const int i = (int)((t - P.tile0) * kTile) + (int)threadIdx.x;
-        if (i >= n) continue;
-        const int x = i % P.nx, yz = i / P.nx, y = yz % P.ny, z = yz / P.ny;
-        const float V0 = __ldcs(P.vel + i), V1 = __ldcs(P.vel + n + i), V2 = __ldcs(P.vel + 2 * n + i);
-        const float W0 = lin_at<true>(P.vel, P.nx, P.ny, P.nz, x, y, z, dts * V0, dts * V1, dts * V2);
-        const float W1 = lin_at<true>(P.vel + n, P.nx, P.ny, P.nz, x, y, z, dts * V0, dts * V1, dts * V2);
-        const float W2 = lin_at<true>(P.vel + 2 * n, P.nx, P.ny, P.nz, x, y, z, dts * V0, dts * V1, dts * V2);
-        const float h = 0.5f * dts;
-        P.D[i] = h * (W0 + V0);
-        P.D[n + i] = h * (W1 + V1);
-        P.D[2 * n + i] = h * (W2 + V2);
+        int x, y, z, zend;
+        if (!P.active || !tile_voxel(P, t, x, y, z, zend)) continue;
+        const int n = P.nx * P.ny * P.nz, plane = P.nx * P.ny;
+        for (int i = (z * P.ny + y) * P.nx + x; z < zend; ++z, i += plane) {
+            const float V0 = __ldcs(P.vel + i), V1 = __ldcs(P.vel + n + i), V2 = __ldcs(P.vel + 2 * n + i);
+            const float W0 = lin_at<true>(P.vel, P.nx, P.ny, P.nz, x, y, z, dts * V0, dts * V1, dts * V2);
+            const float W1 = lin_at<true>(P.vel + n, P.nx, P.ny, P.nz, x, y, z, dts * V0, dts * V1, dts * V2);
+            const float W2 = lin_at<true>(P.vel + 2 * n, P.nx, P.ny, P.nz, x, y, z, dts * V0, dts * V1, dts * V2);
+            P.D[i] = h * (W0 + V0);
+            P.D[n + i] = h * (W1 + V1);
+            P.D[2 * n + i] = h * (W2 + V2);
+        }
     }
-    // ---- nt steps m^{j+1} = m^j o X, ping-pong so that the last one lands in out
+    // ---- nt steps m^{j+1} = m^j o X, ping-pong so that the last one lands in out; the offsets
+    // of plane z + 1 are loaded while the taps of plane z are in flight
     for (int j = 0; j < nt; ++j) {
         if (!grid_barrier(bar, expected, limit_ns, status)) return;
         const bool to_out = ((nt - 1 - j) % 2) == 0;
         for (long t = blockIdx.x; t < ntiles; t += gridDim.x) {
             const BatchPair& P = tb.p[pair_of(tb, npairs, t)];
-            if (!P.active) continue;
-            const int n = P.nx * P.ny * P.nz;
-            const int i = (int)((t - P.tile0) * kTile) + (int)threadIdx.x;
-            if (i >= n) continue;
+            int x, y, z, zend;
+            if (!P.active || !tile_voxel(P, t, x, y, z, zend)) continue;
+            const int n = P.nx * P.ny * P.nz, plane = P.nx * P.ny;
             const float* src = j == 0 ? P.field : (to_out ? P.tmp : P.out);
             float* dst = to_out ? P.out : P.tmp;
-            const int x = i % P.nx, yz = i / P.nx, y = yz % P.ny, z = yz / P.ny;
-            const float d0 = __ldcs(P.D + i), d1 = __ldcs(P.D + n + i), d2 = __ldcs(P.D + 2 * n + i);
-            const float v = j == 0 ? lin_at<true>(src, P.nx, P.ny, P.nz, x, y, z, d0, d1, d2)
-                                   : lin_at<false>(src, P.nx, P.ny, P.nz, x, y, z, d0, d1, d2);
-            __stcs(dst + i, v);
+            int i = (z * P.ny + y) * P.nx + x;
+            float d0 = __ldcs(P.D + i), d1 = __ldcs(P.D + n + i), d2 = __ldcs(P.D + 2 * n + i);
+            for (;;) {
+                const bool more = z + 1 < zend;
+                const int ip = more ? i + plane : i;
+                const float e0 = __ldcs(P.D + ip), e1 = __ldcs(P.D + n + ip), e2 = __ldcs(P.D + 2 * n + ip);
+                const float v = j == 0 ? lin_at<true>(src, P.nx, P.ny, P.nz, x, y, z, d0, d1, d2)
+                                       : lin_at<false>(src, P.nx, P.ny, P.nz, x, y, z, d0, d1, d2);
+                __stcs(dst + i, v);
+                if (!more) break;
+                ++z;
+                i = ip;
+                d0 = e0; d1 = e1; d2 = e2;
+            }
         }
     }
 }
@@ -232,11 +256,13 @@ extern "C" int lddmm_sl_transport_batch(int n, const int* dims, int nt, int dire
         P.ny = ny;
         P.nz = nz;
         P.active = 1;
+        P.tx = (nx + kTx - 1) / kTx;
+        P.txy = P.tx * ((ny + kTy - 1) / kTy);
         P.tile0 = ntiles;
         P.vel = vel[p];
         P.field = field[p];
         P.out = out[p];
-        ntiles += (nv + kTile - 1) / kTile;
+        ntiles += (long)P.txy * ((nz + kZt - 1) / kZt);
         scratch += 4 * nv;   // D (3 planes) + the ping-pong field
     }
     cudaStream_t st = static_cast<cudaStream_t>(stream);
