@@ -941,6 +941,114 @@ def run_spectral(args):
             "kernels": res}
 
 
+NET_FORMS = (("bf16_tensor_cores", "NET_BF16"), ("bf16_simt", "NET_BF16_SIMT"),
+             ("fp32_simt", "NET_FP32"), ("fp32_tensor_cores", "NET_FP32_TC"))
+
+
+def run_net(args):
+    """The warm-start network (64^3 input, 16 base channels, batch 8) in each storage form:
+    forward pass and training step (forward, backward, Adam), event-timed, and the per-kernel
+    throughput of its convolutions from the library's trace; not a bench line of the headline
+    metric."""
+    import torch
+    import paper_2006_06823_b300 as L
+    from paper_2006_06823_b300 import synth
+    torch.cuda.set_device(0)
+    D, c, B = 64, 16, 8
+    x = torch.as_tensor(synth.random_field((D, D, D), 5, ncomp=2 * B, smooth=1.5),
+                        dtype=torch.float32, device="cuda").reshape(B, 2, D, D, D).contiguous()
+    t = torch.as_tensor(synth.rng(6).standard_normal((B, 3, D // 2, D // 2, D // 2)),
+                        dtype=torch.float32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    res = {}
+    for name, form in NET_FORMS:
+        net = L.Net(D, c, batch_max=B, seed=0, storage=getattr(L, form))
+        fwd = timed(lambda: net.forward(x))
+        step = timed(lambda: net.train_step(x, t, 1e-4, want_loss=False))
+        L.trace_reset()
+        L.trace_enable(True)
+        net.train_step(x, t, 1e-4, want_loss=False)
+        tr = L.trace_read()
+        L.trace_enable(False)
+        net.close()
+        res[name] = {"forward_ms": fwd, "train_step_ms": step,
+                     "conv_TFLOP_s": {k: v["flops"] / (v["ms"] * 1e-3) / 1e12 for k, v in tr.items()
+                                      if k in ("cnn_conv", "cnn_dgrad", "cnn_wgrad")}}
+    return {"metric": "warm-start network forward / training step (ms)", "unit": "ms",
+            "impl": "b300", "steps": args.steps, "warmup": args.warmup,
+            "config": {"workload": f"encoder-decoder, {D}^3 input, {c} base channels, batch {B}"},
+            "forms": res,
+            "speedup_train_step_bf16": res["bf16_simt"]["train_step_ms"] / res["bf16_tensor_cores"]["train_step_ms"]}
+
+
+TRANSPORT_SHAPES = [(64, 64, 64), (96, 96, 96), (128, 128, 128), (160, 160, 160), (96, 128, 96),
+                    (64, 64, 64), (128, 128, 128), (96, 96, 96)]
+
+
+def run_transport(args):
+    """The SL state sweep alone (nt = 10 steps, trilinear): the scalar transport at the paper
+    grid in FP32 and the BF16-storage forms, and a batch of eight pairs of the batched
+    workload's grids in one persistent launch against one call per pair; device rates with the
+    transports issued back to back (the working sets exceed L2)."""
+    import torch
+    import paper_2006_06823_b300 as L
+    from paper_2006_06823_b300 import synth
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+
+    def rate(fn, voxels):
+        for _ in range(args.warmup):
+            fn()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        return args.steps * NT * voxels / (e0.elapsed_time(e1) / 1e3)
+
+    nz, ny, nx = SHAPE
+    V = torch.as_tensor(synth.random_displacement(SHAPE, seed=1, max_vox=8.0, smooth=6.0),
+                        dtype=torch.float32, device="cuda")
+    f = torch.as_tensor(synth.ellipsoid_phantom(SHAPE), dtype=torch.float32, device="cuda")
+    o = torch.empty_like(f)
+    n = f.numel()
+    single = {"fp32": rate(lambda: L.sl_transport(V, f, NT, L.FORWARD, L.INTERP_LINEAR, out=o), n),
+              "fields_bf16": rate(lambda: L.sl_transport_bf16(V, f, NT, L.FORWARD, False, out=o), n),
+              "fields_and_offsets_bf16": rate(lambda: L.sl_transport_bf16(V, f, NT, L.FORWARD, True, out=o), n)}
+    vels, fields = [], []
+    for i, sh in enumerate(TRANSPORT_SHAPES):
+        vels.append(torch.as_tensor(synth.random_displacement(sh, seed=10 + i, max_vox=8.0 * sh[2] / 192,
+                                                              smooth=4.0), dtype=torch.float32, device="cuda"))
+        fields.append(torch.as_tensor(synth.ellipsoid_phantom(sh), dtype=torch.float32, device="cuda"))
+    outs_b = [torch.empty_like(x) for x in fields]
+    outs_s = [torch.empty_like(x) for x in fields]
+    nb = sum(x.numel() for x in fields)
+    batch = {"persistent": rate(lambda: L.sl_transport_batch(vels, fields, NT, outs=outs_b), nb),
+             "per_pair_calls": rate(lambda: [L.sl_transport(v, x, NT, L.FORWARD, L.INTERP_LINEAR, out=y)
+                                             for v, x, y in zip(vels, fields, outs_s)], nb)}
+    batch["bit_identical"] = all(torch.equal(a, b) for a, b in zip(outs_b, outs_s))
+    return {"metric": "SL voxel-steps/s (state sweep, nt = 10, trilinear)", "unit": "voxel-steps/s",
+            "impl": "b300", "steps": args.steps, "warmup": args.warmup,
+            "config": {"workload": f"scalar transport of the phantom at {nx}x{ny}x{nz}; batch of "
+                                   f"{len(TRANSPORT_SHAPES)} pairs of the batched workload's grids"},
+            "single_pair": single, "batch": batch}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -950,7 +1058,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", dest="forms", action="store_false",
                     help="skip the other forms of the workload and the warm-start comparison")
-    ap.add_argument("--config", default="paper", choices=["paper", "batch", "spectral"])
+    ap.add_argument("--config", default="paper", choices=["paper", "batch", "spectral", "net", "transport"])
     ap.add_argument("--pairs", type=int, default=64)
     ap.add_argument("--batch-threads", type=int, default=16)
     ap.add_argument("--grid", type=int, nargs=3, metavar=("NZ", "NY", "NX"), default=None,
@@ -963,6 +1071,10 @@ def main():
         out = run_batch(args)
     elif args.config == "spectral" and args.impl == "b300":
         out = run_spectral(args)
+    elif args.config == "net" and args.impl == "b300":
+        out = run_net(args)
+    elif args.config == "transport" and args.impl == "b300":
+        out = run_transport(args)
     else:
         out = run_reference(args) if args.impl == "reference" else run_b300(args)
     if out is not None:
