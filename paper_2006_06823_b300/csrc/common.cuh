@@ -110,6 +110,14 @@ int tc_rowgemm_ex(const float* in, long rows, int kdim, long in_row_floats, cons
                   int N, int prec, int epi, float* out, long rpc, long comp_stride, int n_out,
                   int ptot, int p0, int lines, int nblk, const char* trace_name,
                   double trace_bytes, cudaStream_t st);
+// Transposed tensor-core form for narrow outputs (16 <= N <= 64, N % 16 == 0; the x stage of
+// pi): the same OUT as tc_rowgemm_ex with epi = 1 (OUT[slab][n][row in slab], slabs of rpc
+// rows), from the same W operand image, with W as the MMA's A operand and 128 input rows per
+// instruction (tc_rowgemm.cu).
+bool tc_rowgemm_t_supported(int N, int kdim, long rows, const void* in, long in_row_floats);
+int tc_rowgemm_t(const float* in, long rows, int kdim, long in_row_floats, const unsigned char* W,
+                 int N, int prec, float* out, long rpc, int n_out, const char* trace_name,
+                 double trace_bytes, cudaStream_t st);
 long tc_wimage_bytes(int N, int kdim);
 int tc_build_wimage(const float* W, int N, int kdim, int prec, unsigned char* img,
                     cudaStream_t st);

@@ -568,9 +568,14 @@ int bl_project(const Grid& g, const Twiddles& tw, const float* f, long fstride, 
     const bool tcy = tcx && tw.tc_y && (reinterpret_cast<uintptr_t>(s1) & 15) == 0;
     if (tcy) {
         // stage X on the tensor cores, stored transposed per (comp, z) slab:
-        // A[comp, z][2 kx + re/im][y], the K-major rows of the tensor-core Y stage
-        rc = tc_rowgemm_ex(f, rows, g.nx, g.nx, tw.wpi_img[tp], K, tp, 1, reinterpret_cast<float*>(s1),
-                           g.ny, 0, K, 0, 0, 0, 1, "pi_x_tc", rows * g.nx * 4.0 + rows * K * 4.0, st);
+        // A[comp, z][2 kx + re/im][y], the K-major rows of the tensor-core Y stage; W as the
+        // MMA's A operand (128 input rows per instruction) where it fits
+        if (tc_rowgemm_t_supported(K, g.nx, rows, f, g.nx))
+            rc = tc_rowgemm_t(f, rows, g.nx, g.nx, tw.wpi_img[tp], K, tp, reinterpret_cast<float*>(s1), g.ny,
+                              K, "pi_x_tc", rows * g.nx * 4.0 + rows * K * 4.0, st);
+        else
+            rc = tc_rowgemm_ex(f, rows, g.nx, g.nx, tw.wpi_img[tp], K, tp, 1, reinterpret_cast<float*>(s1),
+                               g.ny, 0, K, 0, 0, 0, 1, "pi_x_tc", rows * g.nx * 4.0 + rows * K * 4.0, st);
     } else if (tcx) {
         // stage X on the tensor cores: A[row][0..K) = (Re, Im) pairs of kx = 0..K/2-1
         rc = tc_rowgemm(f, rows, g.nx, g.nx, tw.wpi_img[tp], K, tp, reinterpret_cast<float*>(s1), rows, 0, K,

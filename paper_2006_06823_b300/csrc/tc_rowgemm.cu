@@ -610,6 +610,300 @@ k_tc_rowgemm(const __grid_constant__ CUtensorMap tmap_in, const __grid_constant_
                      "r"(tmem_cols));
 }
 
+template <int PREC>
+__device__ __forceinline__ void mma_kind(unsigned tmem_d, uint64_t a, uint64_t b, uint32_t idesc,
+                                         unsigned accumulate) {
+    if (PREC == 0) mma_tf32(tmem_d, a, b, idesc, accumulate);
+    else mma_bf16(tmem_d, a, b, idesc, accumulate);
+}
+
+// Transposed form for narrow outputs (16 <= N <= 64: the x stage of pi), OUT^T = W IN^T.
+// One tcgen05.mma instruction takes about the same time for every N up to 256 at M = 128, so
+// the row GEMM above (input rows as A, N = 2 N_out and N_out per k-step) leaves most of each
+// instruction's array idle when N is small. Here W is the A operand and the input rows are B,
+// and one instruction per k-step covers 128 input rows and all four split products:
+//   A (128 rows) = W rows interleaved: row 2n + h = W_h[n] (h = 0 hi, 1 lo; n < N), zero rows
+//                  from 2N on
+//   B (256 rows) = [IN_hi (128 rows); IN_lo (128 rows)] of one 32-column chunk
+//   D[2n + h][j]: j < 128 the input row j times W_h, j >= 128 the lo part of row j - 128
+//   OUT[row j][n] = D[2n][j] + D[2n][128 + j] + D[2n + 1][j] + D[2n + 1][128 + j]
+//                 = (W_hi + W_lo)(IN_hi + IN_lo) (all four products)
+// The epilogue adds the two column halves in each lane and the lane pair (2n, 2n + 1) by a
+// shuffle, and stores OUT transposed per slab of rpc rows, OUT[slab][n][row in slab] (the form
+// the Y stage reads). Warp roles as in k_tc_rowgemm: 0-7 split the landed tile into hi and lo
+// (both materialised, so the raw slot is released right after the split), 8-11 epilogue (the
+// lane quarters holding rows < 2N), 12 TMA producer, 13 MMA issuer. W's operand image is
+// rebuilt in shared memory from the row GEMM's image (per chunk [hi N rows | lo N rows],
+// 128-byte swizzle) by warps 0-11 while the first tiles load.
+constexpr int TR_OP_B = 2 * TILE_B;   // one B operand: hi and lo tiles, 32 KB
+constexpr int TR_NOP = 2;             // B operand ring
+
+template <int PREC, int NRAW>
+__global__ void __launch_bounds__(NTHREADS_WS, 1)
+k_tc_rowgemm_t(const __grid_constant__ CUtensorMap tmap_in, const unsigned char* __restrict__ w_image,
+               int N, int kdim, long rows, float* __restrict__ out, long rpc, int n_out) {
+    extern __shared__ unsigned char smem_raw[];
+    __shared__ uint64_t raw_full[NRAW], raw_empty[NRAW], op_full[TR_NOP], op_empty[TR_NOP], w_bar;
+    __shared__ uint64_t accfull_bar[2], accempty_bar[2];
+    __shared__ unsigned tmem_holder;
+    __shared__ volatile int abort_flag;
+    __shared__ long consumed_sh, issued_sh;
+    constexpr unsigned TMEM_COLS = 2 * 2 * TM;   // two accumulators of 256 columns
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int nchunk = (kdim + CHUNK - 1) / CHUNK;
+    unsigned char* base = reinterpret_cast<unsigned char*>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    unsigned char* wT = base;                                // nchunk x 16 KB
+    unsigned char* raw = wT + (size_t)nchunk * TILE_B;       // NRAW x 16 KB
+    unsigned char* ops = raw + (size_t)NRAW * TILE_B;        // TR_NOP x 32 KB
+
+    if (tid == 0) {
+        mbar_init(&w_bar, 1);
+        for (int i = 0; i < NRAW; ++i) {
+            mbar_init(&raw_full[i], 1);
+            mbar_init(&raw_empty[i], NWORK);
+        }
+        for (int i = 0; i < TR_NOP; ++i) {
+            mbar_init(&op_full[i], NWORK);
+            mbar_init(&op_empty[i], 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(&accfull_bar[b], 1);
+            mbar_init(&accempty_bar[b], NEPI);
+        }
+        abort_flag = 0;
+        consumed_sh = 0;
+        issued_sh = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    }
+    if (warp == WARP_MMA) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;\n" ::"r"(
+                         smem_u32(&tmem_holder)),
+                     "r"(TMEM_COLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;\n");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const unsigned tmem = tmem_holder;
+
+    const long ntiles = (rows + TM - 1) / TM;
+    const long my_tiles = blockIdx.x < ntiles ? (ntiles - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+    const long total = my_tiles * nchunk;
+
+    if (warp < WARP_TMA) {
+        // A image: row r = 2n + h of chunk c from source row c 2N + h N + n; each 16-byte piece
+        // j moves from its source position j ^ (n & 7) to j ^ (r & 7) (rows of 128 bytes,
+        // 8-row swizzle groups; 2N is a multiple of 32, so chunk bases keep phase 0)
+        const int npieces = nchunk * TM * 8;
+        for (int idx = tid; idx < npieces; idx += 32 * WARP_TMA) {
+            const int c = idx >> 10, rem = idx & 1023, r = rem >> 3, j = rem & 7;
+            const int n = r >> 1, h = r & 1;
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (n < N) {
+                const int sr = c * 2 * N + h * N + n;
+                v = __ldg(reinterpret_cast<const uint4*>(w_image + (size_t)sr * 128 + ((j ^ (sr & 7)) << 4)));
+            }
+            *reinterpret_cast<uint4*>(wT + (size_t)(c * TM + r) * 128 + ((j ^ (r & 7)) << 4)) = v;
+        }
+        asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+        asm volatile("bar.sync 2, %0;\n" ::"r"(32 * WARP_TMA) : "memory");
+        if (tid == 0) mbar_arrive(&w_bar);
+    }
+
+    if (warp == WARP_TMA) {
+        if (lane == 0) {
+            int s = 0, c = 0;
+            unsigned u = 0;
+            long t = blockIdx.x;
+            for (long q = 0; q < total; ++q) {
+                if (u > 0 && !mbar_wait(&raw_empty[s], (u - 1) & 1)) {
+                    abort_flag = 1;
+                    break;
+                }
+                if (abort_flag) break;
+                tma_load_2d(raw + (size_t)s * TILE_B, &tmap_in, c * CHUNK, (int)(t * TM), &raw_full[s], TILE_B);
+                issued_sh = q + 1;
+                if (++s == NRAW) {
+                    s = 0;
+                    ++u;
+                }
+                if (++c == nchunk) {
+                    c = 0;
+                    t += gridDim.x;
+                }
+            }
+        }
+    } else if (warp == WARP_MMA) {
+        if (lane == 0) {
+            if (total > 0 && !mbar_wait(&w_bar, 0)) abort_flag = 1;
+            const uint32_t idesc = PREC == 0 ? idesc_tf32(2 * TM) : idesc_bf16(2 * TM);
+            constexpr int KSTEP = PREC == 0 ? 8 : 16;   // elements per MMA k-step
+            int o = 0, c = 0;
+            unsigned uo = 0;
+            long t = 0;
+            for (long q = 0; q < total && !abort_flag; ++q) {
+                const int b = (int)(t & 1);
+                if (c == 0 && t >= 2 && !mbar_wait(&accempty_bar[b], (unsigned)(((t >> 1) - 1) & 1))) {
+                    abort_flag = 1;
+                    break;
+                }
+                if (!mbar_wait(&op_full[o], uo & 1)) {
+                    abort_flag = 1;
+                    break;
+                }
+                if (abort_flag) break;
+                fence_after();
+                const unsigned d = tmem + (unsigned)(b * 2 * TM);
+                const unsigned a = smem_u32(wT + (size_t)c * TILE_B);
+                const unsigned bo = smem_u32(ops + (size_t)o * TR_OP_B);
+#pragma unroll
+                for (int kk = 0; kk < CHUNK / KSTEP; ++kk) {
+                    const unsigned ko = kk * 32;
+                    mma_kind<PREC>(d, sw128_desc(a + ko), sw128_desc(bo + ko), idesc,
+                                   (c > 0 || kk > 0) ? 1u : 0u);
+                }
+                mma_commit(&op_empty[o]);
+                if (c == nchunk - 1) mma_commit(&accfull_bar[b]);
+                if (++o == TR_NOP) {
+                    o = 0;
+                    ++uo;
+                }
+                if (++c == nchunk) {
+                    c = 0;
+                    ++t;
+                }
+            }
+        }
+    } else if (warp >= NWORK) {
+        // ---------------------------------------------------------------- epilogue warps
+        const int quarter = (warp - NWORK) & 3;        // TMEM lanes 32 quarter .. + 31
+        const bool active = quarter * 16 < N;          // lane l holds row 2n + h, n = 16 quarter + l / 2
+        const int n = quarter * 16 + (lane >> 1), h = lane & 1;
+        const bool vec = (rpc % 16) == 0;              // 16-row groups never straddle a slab
+        for (long t = 0; t < my_tiles; ++t) {
+            if (__any_sync(0xffffffffu, abort_flag != 0)) break;
+            const int b = (int)(t & 1);
+            const bool ok = mbar_wait(&accfull_bar[b], (unsigned)((t >> 1) & 1));
+            if (!__all_sync(0xffffffffu, ok)) {
+                abort_flag = 1;
+                break;
+            }
+            fence_after();
+            const long row0 = (blockIdx.x + t * gridDim.x) * TM;
+            if (active) {
+                for (int cb = 0; cb < TM / 32; ++cb) {
+                    float v[32], w[32];
+                    const unsigned ta = tmem + ((unsigned)(quarter * 32) << 16) + (unsigned)(b * 2 * TM + cb * 32);
+                    tmem_ld32(ta, v);
+                    tmem_ld32(ta + TM, w);
+#pragma unroll
+                    for (int i = 0; i < 32; ++i) {
+                        const float sum = v[i] + w[i];
+                        v[i] = sum + __shfl_xor_sync(0xffffffffu, sum, 1);
+                    }
+                    // the lane pair both hold rows cb 32 .. cb 32 + 31 of output n: lane h
+                    // stores the 16 rows from 16 h
+                    float o16[16];
+#pragma unroll
+                    for (int i = 0; i < 16; ++i) o16[i] = h ? v[16 + i] : v[i];
+                    const long r0 = row0 + cb * 32 + 16 * h;
+                    if (n < n_out) {
+                        if (vec) {
+                            if (r0 < rows) {
+                                const long slab = r0 / rpc, rr = r0 - slab * rpc;
+                                float4* dst = reinterpret_cast<float4*>(out + (slab * N + n) * rpc + rr);
+#pragma unroll
+                                for (int k = 0; k < 4; ++k)
+                                    dst[k] = make_float4(o16[4 * k], o16[4 * k + 1], o16[4 * k + 2], o16[4 * k + 3]);
+                            }
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < 16; ++i) {
+                                const long r = r0 + i;
+                                if (r < rows) {
+                                    const long slab = r / rpc;
+                                    out[(slab * N + n) * rpc + (r - slab * rpc)] = o16[i];
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+            fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&accempty_bar[b]);
+        }
+    } else {
+        // ---------------------------------------------------------------- split warps
+        int s = 0, o = 0;
+        unsigned us = 0, uo = 0;
+        for (long q = 0; q < total; ++q) {
+            if (!mbar_wait(&raw_full[s], us & 1) || (uo > 0 && !mbar_wait(&op_empty[o], (uo - 1) & 1)) ||
+                abort_flag) {
+                abort_flag = 1;
+                break;
+            }
+            const float4* src = reinterpret_cast<const float4*>(raw + (size_t)s * TILE_B);
+            unsigned char* hi = ops + (size_t)o * TR_OP_B;
+            unsigned char* lo = hi + TILE_B;
+#pragma unroll
+            for (int i = 0; i < TILE_B / 16 / (32 * NWORK); ++i) {
+                const int e = tid + i * 32 * NWORK;
+                const float4 v = src[e];
+                if (PREC == 0) {
+                    const float4 hv = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
+                    reinterpret_cast<float4*>(hi)[e] = hv;
+                    reinterpret_cast<float4*>(lo)[e] = make_float4(v.x - hv.x, v.y - hv.y, v.z - hv.z, v.w - hv.w);
+                } else {
+                    // raw 16-byte chunk e = (row r, physical chunk p) holds logical chunk
+                    // j = p ^ (r & 7): elements 4j .. 4j + 3 -> BF16 bytes 8j .. 8j + 7
+                    const int r = e >> 3, pch = e & 7, j = pch ^ (r & 7);
+                    const unsigned off = sw128_off(r, 8 * j);
+                    uint2 h2, l2;
+                    bf16_split4(v, h2, l2);
+                    *reinterpret_cast<uint2*>(hi + off) = h2;
+                    *reinterpret_cast<uint2*>(lo + off) = l2;
+                }
+            }
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(&raw_empty[s]);
+                mbar_arrive(&op_full[o]);
+            }
+            if (tid == 0) consumed_sh = q + 1;
+            if (++s == NRAW) {
+                s = 0;
+                ++us;
+            }
+            if (++o == TR_NOP) {
+                o = 0;
+                ++uo;
+            }
+        }
+    }
+
+    __syncthreads();
+    if (abort_flag && tid == 0) {
+        atomicExch(&g_tc_error, LDDMM_ETIMEOUT);
+        for (long qq = consumed_sh; qq < issued_sh; ++qq)
+            mbar_wait(&raw_full[qq % NRAW], (unsigned)((qq / NRAW) & 1));
+    }
+    if (abort_flag && warp == WARP_MMA && lane == 0) {
+        mma_commit(&accfull_bar[0]);
+        mbar_wait(&accfull_bar[0], 0);
+        mbar_wait(&accfull_bar[0], 1);
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == WARP_MMA)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;\n" ::"r"(tmem),
+                     "r"(TMEM_COLS));
+}
+
 // W (N x kdim FP32) -> its shared-memory operand image: hi and lo parts, each nchunk x N rows
 // of 128 bytes in the 128-byte-swizzled K-major layout (zero past kdim); per chunk [hi | lo]
 // when wcat(N), else all hi chunks then all lo chunks.
@@ -840,6 +1134,98 @@ int tc_rowgemm_ex(const float* in, long rows, int kdim, long in_row_floats, cons
             case 5: e = tc_launch_depth<1, 1>(depth, grid, smem, st, map, omap, W, N, kdim, rows, out, rpc, comp_stride, n_out, cols, ptot, p0, lines, nblk); break;
             case 6: e = tc_launch_depth<1, 2>(depth, grid, smem, st, map, omap, W, N, kdim, rows, out, rpc, comp_stride, n_out, cols, ptot, p0, lines, nblk); break;
             case 7: e = tc_launch_depth<1, 3>(depth, grid, smem, st, map, omap, W, N, kdim, rows, out, rpc, comp_stride, n_out, cols, ptot, p0, lines, nblk); break;
+            default: break;
+        }
+        LDDMM_CUDA(e);
+    }
+    return LDDMM_OK;
+}
+
+// ------------------------------------------------- transposed form (narrow outputs)
+namespace {
+
+int tc_t_smem_bytes(int kdim, int nraw) {
+    const int nchunk = (kdim + CHUNK - 1) / CHUNK;
+    return (nchunk + nraw) * TILE_B + TR_NOP * TR_OP_B + 1024;
+}
+
+// the deepest raw ring (4, 3 or 2 slots) that fits with W's 128-row image; 0 if none
+int tc_t_depth(int kdim) {
+    for (int d : {4, 3, 2})
+        if (tc_t_smem_bytes(kdim, d) <= kTcSmemLimit) return d;
+    return 0;
+}
+
+template <int PREC, int NRAW>
+cudaError_t tc_t_launch(int grid, int smem, cudaStream_t st, const CUtensorMap& map,
+                        const unsigned char* W, int N, int kdim, long rows, float* out, long rpc,
+                        int n_out) {
+    static int attr = 0;   // largest dynamic size requested so far (under the caller's lock)
+    if (smem > attr) {
+        cudaError_t e = cudaFuncSetAttribute(k_tc_rowgemm_t<PREC, NRAW>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        if (e != cudaSuccess) return e;
+        attr = smem;
+    }
+    k_tc_rowgemm_t<PREC, NRAW><<<grid, NTHREADS_WS, smem, st>>>(map, W, N, kdim, rows, out, rpc, n_out);
+    return cudaGetLastError();
+}
+
+}  // namespace
+
+bool tc_rowgemm_t_supported(int N, int kdim, long rows, const void* in, long in_row_floats) {
+    if (N < 16 || N > 64 || (N % 16) != 0) return false;
+    if (kdim < 1 || kdim > in_row_floats || (in_row_floats % 4) != 0) return false;
+    if ((reinterpret_cast<uintptr_t>(in) & 15) != 0) return false;
+    if (rows < 1 || rows > 0x7fffffffL) return false;
+    if (tc_t_depth(kdim) == 0) return false;
+    return encode_fn() != nullptr;
+}
+
+int tc_rowgemm_t(const float* in, long rows, int kdim, long in_row_floats, const unsigned char* W,
+                 int N, int prec, float* out, long rpc, int n_out, const char* trace_name,
+                 double trace_bytes, cudaStream_t st) {
+    if (!tc_rowgemm_t_supported(N, kdim, rows, in, in_row_floats) || rpc < 1 || n_out < 1 ||
+        n_out > N || (prec != 0 && prec != 1) || (reinterpret_cast<uintptr_t>(out) & 15) != 0) {
+        set_error("tc_rowgemm_t: unsupported arguments");
+        return LDDMM_EINVAL;
+    }
+    CUtensorMap map;
+    cuuint64_t dims[2] = {(cuuint64_t)in_row_floats, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)in_row_floats * 4};
+    cuuint32_t box[2] = {CHUNK, TM};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = encode_fn()(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(in), dims,
+                             strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                             CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        set_error("tc_rowgemm_t: cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
+        return LDDMM_ECUDA;
+    }
+    const int depth = tc_t_depth(kdim);
+    const int smem = tc_t_smem_bytes(kdim, depth);
+    static int nsm = 0;
+    if (nsm == 0) {
+        int dev = 0, v = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+        nsm = v;
+    }
+    const long ntiles = (rows + TM - 1) / TM;
+    const int grid = (int)std::min<long>(ntiles, nsm);
+    {
+        KTRACE(trace_name, st, trace_bytes, 2.0 * rows * (double)N * kdim);
+        static std::mutex mu;   // serialises the per-instantiation shared-memory attribute
+        std::lock_guard<std::mutex> lock(mu);
+        cudaError_t e = cudaErrorInvalidValue;
+        switch (prec * 8 + depth) {
+            case 2: e = tc_t_launch<0, 2>(grid, smem, st, map, W, N, kdim, rows, out, rpc, n_out); break;
+            case 3: e = tc_t_launch<0, 3>(grid, smem, st, map, W, N, kdim, rows, out, rpc, n_out); break;
+            case 4: e = tc_t_launch<0, 4>(grid, smem, st, map, W, N, kdim, rows, out, rpc, n_out); break;
+            case 10: e = tc_t_launch<1, 2>(grid, smem, st, map, W, N, kdim, rows, out, rpc, n_out); break;
+            case 11: e = tc_t_launch<1, 3>(grid, smem, st, map, W, N, kdim, rows, out, rpc, n_out); break;
+            case 12: e = tc_t_launch<1, 4>(grid, smem, st, map, W, N, kdim, rows, out, rpc, n_out); break;
             default: break;
         }
         LDDMM_CUDA(e);
