@@ -622,17 +622,20 @@ __device__ __forceinline__ void mma_kind(unsigned tmem_d, uint64_t a, uint64_t b
 // the row GEMM above (input rows as A, N = 2 N_out and N_out per k-step) leaves most of each
 // instruction's array idle when N is small. Here W is the A operand and the input rows are B,
 // and one instruction per k-step covers 128 input rows and all four split products:
-//   A (128 rows) = W rows interleaved: row 2n + h = W_h[n] (h = 0 hi, 1 lo; n < N), zero rows
-//                  from 2N on
+//   A (MA rows)  = W rows interleaved: row 2n + h = W_h[n] (h = 0 hi, 1 lo; n < N), zero rows
+//                  from 2N on; MA = 64 for N <= 32, else 128
 //   B (256 rows) = [IN_hi (128 rows); IN_lo (128 rows)] of one 32-column chunk
 //   D[2n + h][j]: j < 128 the input row j times W_h, j >= 128 the lo part of row j - 128
 //   OUT[row j][n] = D[2n][j] + D[2n][128 + j] + D[2n + 1][j] + D[2n + 1][128 + j]
 //                 = (W_hi + W_lo)(IN_hi + IN_lo) (all four products)
 // The epilogue adds the two column halves in each lane and the lane pair (2n, 2n + 1) by a
 // shuffle, and stores OUT transposed per slab of rpc rows, OUT[slab][n][row in slab] (the form
-// the Y stage reads). Warp roles as in k_tc_rowgemm: 0-7 split the landed tile into hi and lo
-// (both materialised, so the raw slot is released right after the split), 8-11 epilogue (the
-// lane quarters holding rows < 2N), 12 TMA producer, 13 MMA issuer. W's operand image is
+// the Y stage reads). D row r of an M = 128 MMA is TMEM lane r; of an M = 64 MMA, lane
+// 32 (r / 16) + r % 16 (the first 16 lanes of each quarter). Warp roles as in k_tc_rowgemm:
+// 0-7 split the landed tile into hi and lo (both materialised, so the raw slot is released
+// right after the split), 8-11 epilogue (the lane quarters holding rows < 2N), 12 TMA
+// producer, 13 MMA issuer. The smaller A image of MA = 64 leaves room for a deeper raw ring.
+// W's operand image is
 // rebuilt in shared memory from the row GEMM's image (per chunk [hi N rows | lo N rows],
 // 128-byte swizzle) by warps 0-11 while the first tiles load.
 constexpr int TR_OP_B = 2 * TILE_B;   // one B operand: hi and lo tiles, 32 KB
@@ -641,7 +644,7 @@ constexpr int TR_NOP = 2;             // B operand ring
 template <int PREC, int NRAW>
 __global__ void __launch_bounds__(NTHREADS_WS, 1)
 k_tc_rowgemm_t(const __grid_constant__ CUtensorMap tmap_in, const unsigned char* __restrict__ w_image,
-               int N, int kdim, long rows, float* __restrict__ out, long rpc, int n_out) {
+               int N, int kdim, long rows, float* __restrict__ out, long rpc, int n_out, int ma) {
     extern __shared__ unsigned char smem_raw[];
     __shared__ uint64_t raw_full[NRAW], raw_empty[NRAW], op_full[TR_NOP], op_empty[TR_NOP], w_bar;
     __shared__ uint64_t accfull_bar[2], accempty_bar[2];
@@ -654,8 +657,9 @@ k_tc_rowgemm_t(const __grid_constant__ CUtensorMap tmap_in, const unsigned char*
     const int nchunk = (kdim + CHUNK - 1) / CHUNK;
     unsigned char* base = reinterpret_cast<unsigned char*>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-    unsigned char* wT = base;                                // nchunk x 16 KB
-    unsigned char* raw = wT + (size_t)nchunk * TILE_B;       // NRAW x 16 KB
+    const int abytes = ma * 128;                             // one chunk of the A image
+    unsigned char* wT = base;                                // nchunk x abytes
+    unsigned char* raw = wT + (size_t)nchunk * abytes;       // NRAW x 16 KB
     unsigned char* ops = raw + (size_t)NRAW * TILE_B;        // TR_NOP x 32 KB
 
     if (tid == 0) {
@@ -696,16 +700,28 @@ k_tc_rowgemm_t(const __grid_constant__ CUtensorMap tmap_in, const unsigned char*
         // A image: row r = 2n + h of chunk c from source row c 2N + h N + n; each 16-byte piece
         // j moves from its source position j ^ (n & 7) to j ^ (r & 7) (rows of 128 bytes,
         // 8-row swizzle groups; 2N is a multiple of 32, so chunk bases keep phase 0)
-        const int npieces = nchunk * TM * 8;
-        for (int idx = tid; idx < npieces; idx += 32 * WARP_TMA) {
-            const int c = idx >> 10, rem = idx & 1023, r = rem >> 3, j = rem & 7;
-            const int n = r >> 1, h = r & 1;
-            uint4 v = make_uint4(0u, 0u, 0u, 0u);
-            if (n < N) {
-                const int sr = c * 2 * N + h * N + n;
-                v = __ldg(reinterpret_cast<const uint4*>(w_image + (size_t)sr * 128 + ((j ^ (sr & 7)) << 4)));
+        // (eight loads in flight per thread before their stores)
+        constexpr int TPB = 32 * WARP_TMA, BATCH = 8;
+        const int cshift = ma == 64 ? 9 : 10;                // log2(ma * 8 pieces)
+        const int npieces = nchunk * ma * 8;
+        for (int b0 = 0; b0 < npieces; b0 += BATCH * TPB) {
+            uint4 v[BATCH];
+            int dst[BATCH];
+#pragma unroll
+            for (int u = 0; u < BATCH; ++u) {
+                const int idx = b0 + u * TPB + tid;
+                const int c = idx >> cshift, rem = idx & ((1 << cshift) - 1), r = rem >> 3, j = rem & 7;
+                const int n = r >> 1, h = r & 1;
+                v[u] = make_uint4(0u, 0u, 0u, 0u);
+                dst[u] = idx < npieces ? (c * ma + r) * 128 + ((j ^ (r & 7)) << 4) : -1;
+                if (idx < npieces && n < N) {
+                    const int sr = c * 2 * N + h * N + n;
+                    v[u] = __ldg(reinterpret_cast<const uint4*>(w_image + (size_t)sr * 128 + ((j ^ (sr & 7)) << 4)));
+                }
             }
-            *reinterpret_cast<uint4*>(wT + (size_t)(c * TM + r) * 128 + ((j ^ (r & 7)) << 4)) = v;
+#pragma unroll
+            for (int u = 0; u < BATCH; ++u)
+                if (dst[u] >= 0) *reinterpret_cast<uint4*>(wT + dst[u]) = v[u];
         }
         asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
         asm volatile("bar.sync 2, %0;\n" ::"r"(32 * WARP_TMA) : "memory");
@@ -738,7 +754,8 @@ k_tc_rowgemm_t(const __grid_constant__ CUtensorMap tmap_in, const unsigned char*
     } else if (warp == WARP_MMA) {
         if (lane == 0) {
             if (total > 0 && !mbar_wait(&w_bar, 0)) abort_flag = 1;
-            const uint32_t idesc = PREC == 0 ? idesc_tf32(2 * TM) : idesc_bf16(2 * TM);
+            const uint32_t idesc = (PREC == 0 ? idesc_tf32(2 * TM) : idesc_bf16(2 * TM)) & ~(31u << 24) |
+                                   ((uint32_t)(ma >> 4) << 24);   // M = ma
             constexpr int KSTEP = PREC == 0 ? 8 : 16;   // elements per MMA k-step
             int o = 0, c = 0;
             unsigned uo = 0;
@@ -756,7 +773,7 @@ k_tc_rowgemm_t(const __grid_constant__ CUtensorMap tmap_in, const unsigned char*
                 if (abort_flag) break;
                 fence_after();
                 const unsigned d = tmem + (unsigned)(b * 2 * TM);
-                const unsigned a = smem_u32(wT + (size_t)c * TILE_B);
+                const unsigned a = smem_u32(wT + (size_t)c * abytes);
                 const unsigned bo = smem_u32(ops + (size_t)o * TR_OP_B);
 #pragma unroll
                 for (int kk = 0; kk < CHUNK / KSTEP; ++kk) {
@@ -779,8 +796,10 @@ k_tc_rowgemm_t(const __grid_constant__ CUtensorMap tmap_in, const unsigned char*
     } else if (warp >= NWORK) {
         // ---------------------------------------------------------------- epilogue warps
         const int quarter = (warp - NWORK) & 3;        // TMEM lanes 32 quarter .. + 31
-        const bool active = quarter * 16 < N;          // lane l holds row 2n + h, n = 16 quarter + l / 2
-        const int n = quarter * 16 + (lane >> 1), h = lane & 1;
+        const int qrows = ma / 4;                      // D rows per lane quarter (lanes 0 .. qrows-1)
+        const bool active = quarter * (qrows / 2) < N; // lane l holds row 2n + h, n = quarter qrows / 2 + l / 2
+        const int n = quarter * (qrows / 2) + (lane >> 1), h = lane & 1;
+        const bool lane_ok = lane < qrows;
         const bool vec = (rpc % 16) == 0;              // 16-row groups never straddle a slab
         for (long t = 0; t < my_tiles; ++t) {
             if (__any_sync(0xffffffffu, abort_flag != 0)) break;
@@ -809,7 +828,7 @@ k_tc_rowgemm_t(const __grid_constant__ CUtensorMap tmap_in, const unsigned char*
 #pragma unroll
                     for (int i = 0; i < 16; ++i) o16[i] = h ? v[16 + i] : v[i];
                     const long r0 = row0 + cb * 32 + 16 * h;
-                    if (n < n_out) {
+                    if (lane_ok && n < n_out) {
                         if (vec) {
                             if (r0 < rows) {
                                 const long slab = r0 / rpc, rr = r0 - slab * rpc;
@@ -1144,22 +1163,25 @@ int tc_rowgemm_ex(const float* in, long rows, int kdim, long in_row_floats, cons
 // ------------------------------------------------- transposed form (narrow outputs)
 namespace {
 
-int tc_t_smem_bytes(int kdim, int nraw) {
+// rows of the A image: 64 (the M = 64 MMA) when the 2N interleaved W rows fit, else 128
+int tc_t_ma(int N) { return 2 * N <= 64 ? 64 : 128; }
+
+int tc_t_smem_bytes(int kdim, int nraw, int ma) {
     const int nchunk = (kdim + CHUNK - 1) / CHUNK;
-    return (nchunk + nraw) * TILE_B + TR_NOP * TR_OP_B + 1024;
+    return nchunk * ma * 128 + nraw * TILE_B + TR_NOP * TR_OP_B + 1024;
 }
 
-// the deepest raw ring (4, 3 or 2 slots) that fits with W's 128-row image; 0 if none
-int tc_t_depth(int kdim) {
-    for (int d : {4, 3, 2})
-        if (tc_t_smem_bytes(kdim, d) <= kTcSmemLimit) return d;
+// the deepest raw ring (6, 4, 3 or 2 slots) that fits with W's image; 0 if none
+int tc_t_depth(int kdim, int ma) {
+    for (int d : {6, 4, 3, 2})
+        if (tc_t_smem_bytes(kdim, d, ma) <= kTcSmemLimit) return d;
     return 0;
 }
 
 template <int PREC, int NRAW>
 cudaError_t tc_t_launch(int grid, int smem, cudaStream_t st, const CUtensorMap& map,
                         const unsigned char* W, int N, int kdim, long rows, float* out, long rpc,
-                        int n_out) {
+                        int n_out, int ma) {
     static int attr = 0;   // largest dynamic size requested so far (under the caller's lock)
     if (smem > attr) {
         cudaError_t e = cudaFuncSetAttribute(k_tc_rowgemm_t<PREC, NRAW>,
@@ -1167,7 +1189,7 @@ cudaError_t tc_t_launch(int grid, int smem, cudaStream_t st, const CUtensorMap& 
         if (e != cudaSuccess) return e;
         attr = smem;
     }
-    k_tc_rowgemm_t<PREC, NRAW><<<grid, NTHREADS_WS, smem, st>>>(map, W, N, kdim, rows, out, rpc, n_out);
+    k_tc_rowgemm_t<PREC, NRAW><<<grid, NTHREADS_WS, smem, st>>>(map, W, N, kdim, rows, out, rpc, n_out, ma);
     return cudaGetLastError();
 }
 
@@ -1178,7 +1200,7 @@ bool tc_rowgemm_t_supported(int N, int kdim, long rows, const void* in, long in_
     if (kdim < 1 || kdim > in_row_floats || (in_row_floats % 4) != 0) return false;
     if ((reinterpret_cast<uintptr_t>(in) & 15) != 0) return false;
     if (rows < 1 || rows > 0x7fffffffL) return false;
-    if (tc_t_depth(kdim) == 0) return false;
+    if (tc_t_depth(kdim, tc_t_ma(N)) == 0) return false;
     return encode_fn() != nullptr;
 }
 
@@ -1203,8 +1225,9 @@ int tc_rowgemm_t(const float* in, long rows, int kdim, long in_row_floats, const
         set_error("tc_rowgemm_t: cuTensorMapEncodeTiled failed (" + std::to_string((int)r) + ")");
         return LDDMM_ECUDA;
     }
-    const int depth = tc_t_depth(kdim);
-    const int smem = tc_t_smem_bytes(kdim, depth);
+    const int ma = tc_t_ma(N);
+    const int depth = tc_t_depth(kdim, ma);
+    const int smem = tc_t_smem_bytes(kdim, depth, ma);
     static int nsm = 0;
     if (nsm == 0) {
         int dev = 0, v = 148;
@@ -1220,12 +1243,14 @@ int tc_rowgemm_t(const float* in, long rows, int kdim, long in_row_floats, const
         std::lock_guard<std::mutex> lock(mu);
         cudaError_t e = cudaErrorInvalidValue;
         switch (prec * 8 + depth) {
-            case 2: e = tc_t_launch<0, 2>(grid, smem, st, map, W, N, kdim, rows, out, rpc, n_out); break;
-            case 3: e = tc_t_launch<0, 3>(grid, smem, st, map, W, N, kdim, rows, out, rpc, n_out); break;
-            case 4: e = tc_t_launch<0, 4>(grid, smem, st, map, W, N, kdim, rows, out, rpc, n_out); break;
-            case 10: e = tc_t_launch<1, 2>(grid, smem, st, map, W, N, kdim, rows, out, rpc, n_out); break;
-            case 11: e = tc_t_launch<1, 3>(grid, smem, st, map, W, N, kdim, rows, out, rpc, n_out); break;
-            case 12: e = tc_t_launch<1, 4>(grid, smem, st, map, W, N, kdim, rows, out, rpc, n_out); break;
+            case 2: e = tc_t_launch<0, 2>(grid, smem, st, map, W, N, kdim, rows, out, rpc, n_out, ma); break;
+            case 3: e = tc_t_launch<0, 3>(grid, smem, st, map, W, N, kdim, rows, out, rpc, n_out, ma); break;
+            case 4: e = tc_t_launch<0, 4>(grid, smem, st, map, W, N, kdim, rows, out, rpc, n_out, ma); break;
+            case 6: e = tc_t_launch<0, 6>(grid, smem, st, map, W, N, kdim, rows, out, rpc, n_out, ma); break;
+            case 10: e = tc_t_launch<1, 2>(grid, smem, st, map, W, N, kdim, rows, out, rpc, n_out, ma); break;
+            case 11: e = tc_t_launch<1, 3>(grid, smem, st, map, W, N, kdim, rows, out, rpc, n_out, ma); break;
+            case 12: e = tc_t_launch<1, 4>(grid, smem, st, map, W, N, kdim, rows, out, rpc, n_out, ma); break;
+            case 14: e = tc_t_launch<1, 6>(grid, smem, st, map, W, N, kdim, rows, out, rpc, n_out, ma); break;
             default: break;
         }
         LDDMM_CUDA(e);
