@@ -867,23 +867,32 @@ k_tc_rowgemm_t(const __grid_constant__ CUtensorMap tmap_in, const unsigned char*
             const float4* src = reinterpret_cast<const float4*>(raw + (size_t)s * TILE_B);
             unsigned char* hi = ops + (size_t)o * TR_OP_B;
             unsigned char* lo = hi + TILE_B;
+            if (PREC == 0) {
 #pragma unroll
-            for (int i = 0; i < TILE_B / 16 / (32 * NWORK); ++i) {
-                const int e = tid + i * 32 * NWORK;
-                const float4 v = src[e];
-                if (PREC == 0) {
+                for (int i = 0; i < TILE_B / 16 / (32 * NWORK); ++i) {
+                    const int e = tid + i * 32 * NWORK;
+                    const float4 v = src[e];
                     const float4 hv = make_float4(tf32_hi(v.x), tf32_hi(v.y), tf32_hi(v.z), tf32_hi(v.w));
                     reinterpret_cast<float4*>(hi)[e] = hv;
                     reinterpret_cast<float4*>(lo)[e] = make_float4(v.x - hv.x, v.y - hv.y, v.z - hv.z, v.w - hv.w);
-                } else {
-                    // raw 16-byte chunk e = (row r, physical chunk p) holds logical chunk
-                    // j = p ^ (r & 7): elements 4j .. 4j + 3 -> BF16 bytes 8j .. 8j + 7
-                    const int r = e >> 3, pch = e & 7, j = pch ^ (r & 7);
-                    const unsigned off = sw128_off(r, 8 * j);
-                    uint2 h2, l2;
-                    bf16_split4(v, h2, l2);
-                    *reinterpret_cast<uint2*>(hi + off) = h2;
-                    *reinterpret_cast<uint2*>(lo + off) = l2;
+                }
+            } else {
+                // raw 16-byte chunk e = (row r, physical chunk p) holds logical chunk
+                // j = p ^ (r & 7), elements 4j .. 4j + 3 -> BF16 bytes 8j .. 8j + 7. The
+                // physical pair (2m', 2m' + 1) holds the logical pair (2m, 2m + 1),
+                // m = (2m' ^ (r & 7)) / 2, i.e. one 16-byte BF16 piece of hi and of lo
+#pragma unroll
+                for (int i = 0; i < TILE_B / 32 / (32 * NWORK); ++i) {
+                    const int e0 = 2 * (tid + i * 32 * NWORK);
+                    const int r = e0 >> 3, j0 = (e0 & 7) ^ (r & 7);
+                    const float4 va = src[e0], vb = src[e0 + 1];
+                    const bool swap = (j0 & 1) != 0;        // e0 holds the odd logical chunk
+                    uint2 ha, la, hb, lb;
+                    bf16_split4(swap ? vb : va, ha, la);
+                    bf16_split4(swap ? va : vb, hb, lb);
+                    const unsigned off = sw128_off(r, 16 * (j0 >> 1));
+                    *reinterpret_cast<uint4*>(hi + off) = make_uint4(ha.x, ha.y, hb.x, hb.y);
+                    *reinterpret_cast<uint4*>(lo + off) = make_uint4(la.x, la.y, lb.x, lb.y);
                 }
             }
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");

@@ -149,7 +149,8 @@ def test_invalid_arguments_raise():
 # shapes that take the tensor-core x stages (K a multiple of 16, nx a multiple of 4; iota also
 # needs nx a multiple of 16): ragged row counts, a partial last K chunk, K = 16 and 32
 TC_CASES = [((33, 40, 64), 32), ((20, 24, 48), 16), ((40, 36, 100), 32), ((18, 20, 80), 16),
-            ((34, 36, 256), 32)]   # nx = 256: the shallower (3-deep) tensor-core rings
+            ((34, 36, 256), 32),   # nx = 256: the shallower tensor-core rings
+            ((64, 64, 64), 64)]    # pi's x stage with all 128 rows of the M = 128 A operand
 
 
 @pytest.mark.parametrize("shape,K", TC_CASES)
@@ -176,7 +177,8 @@ def test_bl_include_tensor_core_and_simt_paths_match_oracle(shape, K, precision,
 def test_bf16x3_projection_and_inclusion_error_is_bounded(shape, K):
     """Mixed-precision spectral path: BF16 hi + lo split products with FP32 accumulation.
     hi and lo each carry 8 mantissa bits, so the represented operands are exact to ~2^-17
-    and the dropped lo*lo product is ~2^-18 relative: results stay within ~1e-5 of FP64."""
+    and the lo*lo product that the row-GEMM stages drop is ~2^-18 relative (pi's transposed x
+    stage keeps it): results stay within ~1e-5 of FP64."""
     f = synth.random_field(shape, seed=53, ncomp=3)
     c = host(L.bl_project(dev(f), K, precision=L.PREC_BF16X3))
     e_pi = rel_l2(c, S.project(f, K))
