@@ -67,6 +67,8 @@ struct lddmm_ctx {
     float* Gm = nullptr;    // IMAGE, STATE: iota(grad~ pi(m_j)), (nt+1) x 3 planes
     float* Wb = nullptr;    // STATE: source of the nu~ step, -dt/2 (v(X+) + v(x)), 3 planes per step
     float* PJ = nullptr;    // STATE: per node iota(nu~_j) (3 planes, physical) and J_j (1 plane)
+    float* Rn = nullptr;    // DEFSTATE, stationary: per node iota(rho~_j) of the adjoint sweep, 3 planes
+    float* Sn = nullptr;    // IMAGE, STATE, stationary: per node the projected adjoint scalar, 1 plane
     // spatial form: full-grid FFT plans (the "cubes" of this context are fields on the grid)
     SpatialFFT* fft = nullptr;
     float *G = nullptr, *m1 = nullptr;
@@ -483,20 +485,21 @@ static int ensure_traj(lddmm_ctx* c) {
 
 // ------------------------------------------------------------------ adjoint sweeps
 // DEFSTATE (Eqs. 35, 37; Table 1 rows 4, 8), backward from rho(1) given spatially in `rho1`:
-// out = wL L~ base + sum_j w_j (rho~_j - pi((D iota u~_j)^T iota(rho~_j))).
+// out = wL L~ base + sum_j w_j (rho~_j - pi((D iota u~_j)^T iota(rho~_j))). The sweep keeps
+// iota(rho~_j) of every node (Rn) and the trapezoid sum of (D iota u~_j)^T iota(rho~_j) runs
+// in one pass over all nodes at the end, which writes the accumulator once.
 static int adjoint_defstate(lddmm_ctx* c, const float* rho1, const float2* base, float2* out,
                             bool hess) {
     const long n = c->n, kc3 = 3 * c->kc;
     const int nt = c->p.nt;
     float2* rt = c->cv[lddmm_ctx::C_T1];     // rho~_j
     float2* rsum = c->cv[lddmm_ctx::C_T2];   // sum_j w_j rho~_j
+    auto rnode = [&](int j) { return c->Rn + (long)j * 3 * n; };
     TRY(project(c, rho1, 3, rt));
     TRY(cube_axpby(rsum, (float)trap_w(c, nt), rt, 0.f, nullptr, kc3, c->st));
-    TRY(include(c, rt, 3, c->fc, n, -1, 0));  // iota(rho~_nt) values
-    TRY(accum_JT(c->g, jac(c, nt, hess), jac_bf16(c) && hess, c->fc, (float)trap_w(c, nt), c->acc, 1,
-                 c->st));
+    TRY(include(c, rt, 3, rnode(nt), n, -1, 0));  // iota(rho~_nt) values
     for (int j = nt - 1; j >= 0; --j) {
-        const float* src = c->fc;
+        const float* src = rnode(j + 1);
         if (cubic(c)) {
             TRY(include(c, rt, 3, c->fa, n, -1, 1));
             src = c->fa;
@@ -504,10 +507,10 @@ static int adjoint_defstate(lddmm_ctx* c, const float* rho1, const float2* base,
         TRY(sl_gather_scale(c->sl, src, c->Db, c->gam, 3, c->fd, c->st));
         TRY(project(c, c->fd, 3, rt));
         TRY(cube_axpby(rsum, 1.f, rsum, (float)trap_w(c, j), rt, kc3, c->st));
-        TRY(include(c, rt, 3, c->fc, n, -1, 0));
-        TRY(accum_JT(c->g, jac(c, j, hess), jac_bf16(c) && hess, c->fc, (float)trap_w(c, j), c->acc, 0,
-                     c->st));
+        TRY(include(c, rt, 3, rnode(j), n, -1, 0));
     }
+    TRY(accum_JT_nodes(c->g, jac(c, 0, hess), jac_bf16(c) && hess, c->Rn, nt, (float)trap_w(c, 0),
+                       (float)c->dt, c->acc, c->st));
     c->solves++;
     float2* pacc = c->cv[lddmm_ctx::C_T0];
     TRY(project(c, c->acc, 3, pacc));
@@ -547,12 +550,14 @@ static int adjoint_defstate_ns(lddmm_ctx* c, const float* rho1, const float2* ba
 }
 
 // Image-type assembly (IMAGE and STATE, Eqs. 15-16): node j contributes pi(s_j Gm_j), s_j the
-// values of a projected scalar. Stationary: acc (+)= w_j s_j Gm_j over the nodes and, at the end,
-// out = L~ base + pi(acc). Non-stationary: out_j = L~ base_j + pi(s_j Gm_j) at every node.
-static int image_term(lddmm_ctx* c, int j, const float* vals, const float2* base, float2* out,
-                      bool first) {
+// values of a projected scalar, which the sweeps write to image_vals(c, j). Stationary: the
+// sweep keeps s_j of every node, and at the end one pass over all nodes forms
+// acc = sum_j w_j s_j Gm_j, then out = L~ base + pi(acc). Non-stationary: out_j = L~ base_j +
+// pi(s_j Gm_j) at every node.
+static float* image_vals(lddmm_ctx* c, int j) { return ns(c) ? c->fc : c->Sn + (long)j * c->n; }
+static int image_term(lddmm_ctx* c, int j, const float* vals, const float2* base, float2* out) {
+    if (!ns(c)) return LDDMM_OK;
     const float* gm = c->Gm + (long)j * 3 * c->n;
-    if (!ns(c)) return accum_sv(c->g, vals, gm, (float)trap_w(c, j), c->acc, first, c->st);
     TRY(accum_sv(c->g, vals, gm, 1.f, c->acc, 1, c->st));
     float2* pacc = c->cv[lddmm_ctx::C_T0];
     TRY(project(c, c->acc, 3, pacc));
@@ -560,6 +565,7 @@ static int image_term(lddmm_ctx* c, int j, const float* vals, const float2* base
 }
 static int image_finish(lddmm_ctx* c, const float2* base, float2* out) {
     if (ns(c)) return LDDMM_OK;
+    TRY(accum_sv_nodes(c->g, c->Sn, c->Gm, c->p.nt, (float)trap_w(c, 0), (float)c->dt, c->acc, c->st));
     float2* pacc = c->cv[lddmm_ctx::C_T0];
     TRY(project(c, c->acc, 3, pacc));
     return op_L(c, out, base, 1.f, 1.f, pacc, 3, 1);
@@ -581,8 +587,8 @@ static int pullback_assemble(lddmm_ctx* c, const float* f1, const float2* base, 
         const float* pj = c->PJ + (long)j * 4 * n;
         TRY(sl_compose(c->sl, src, pj, c->to_vox, pj + 3 * n, c->fd, c->st));
         TRY(project(c, c->fd, 1, lt));
-        TRY(include(c, lt, 1, c->fc, n, -1, 0));
-        TRY(image_term(c, j, c->fc, base, out, j == nt));
+        TRY(include(c, lt, 1, image_vals(c, j), n, -1, 0));
+        TRY(image_term(c, j, image_vals(c, j), base, out));
     }
     c->solves++;
     return image_finish(c, base, out);
@@ -598,8 +604,8 @@ static int gradient_image_adjoint(lddmm_ctx* c, const float2* vt, float2* g) {
     for (int j = nt; j >= 0; --j) {
         // fb holds lambda_j (spatial)
         TRY(project(c, c->fb, 1, lt));
-        TRY(include(c, lt, 1, c->fc, n, -1, 0));
-        TRY(image_term(c, j, c->fc, vt, g, j == nt));
+        TRY(include(c, lt, 1, image_vals(c, j), n, -1, 0));
+        TRY(image_term(c, j, image_vals(c, j), vt, g));
         if (j > 0) {
             const float* src = c->fb;
             if (cubic(c)) {
@@ -720,10 +726,10 @@ static int hessian_impl(lddmm_ctx* c, const float2* dvt, float2* out) {
     // incremental adjoint -D~_t dlambda~ = dlambda~ * div~ v~ (Eq. 20), dlambda~(1) = -(2/s2) dm~(1)
     TRY(cube_axpby(dmt, (float)(-2.0 / c->p.sigma2), dmt, 0.f, nullptr, c->kc, c->st));
     for (int j = nt; j >= 0; --j) {
-        TRY(include(c, dmt, 1, c->fc, n, -1, 0));
-        TRY(image_term(c, j, c->fc, dvt, out, j == nt));
+        TRY(include(c, dmt, 1, image_vals(c, j), n, -1, 0));
+        TRY(image_term(c, j, image_vals(c, j), dvt, out));
         if (j > 0) {
-            const float* src = c->fc;
+            const float* src = image_vals(c, j);
             if (cubic(c)) {
                 TRY(include(c, dmt, 1, c->fa, n, -1, 1));
                 src = c->fa;
@@ -1079,6 +1085,8 @@ static int ctx_alloc(lddmm_ctx* c) {
         TRY(dalloc_t(c, &c->Wb, steps * 3 * n));
         TRY(dalloc_t(c, &c->PJ, (size_t)(nt + 1) * 4 * n));
     }
+    if (c->p.variant == LDDMM_V_DEFSTATE && !ns(c)) TRY(dalloc_t(c, &c->Rn, (size_t)(nt + 1) * 3 * n));
+    if (c->p.variant != LDDMM_V_DEFSTATE && !ns(c)) TRY(dalloc_t(c, &c->Sn, (size_t)(nt + 1) * n));
     for (float** f : {&c->fa, &c->fb, &c->fc, &c->fd, &c->acc, &c->dvsp}) TRY(dalloc_t(c, f, 3 * n));
     if (!spatial(c)) {
         long se = spectral_scratch_elems(c->g, c->K, 3);

@@ -250,6 +250,11 @@ int defstate_drho1(const Grid& g, const float* G, const float* du1, double sigma
 // acc_b (+)= w sum_a Du[a*3+b] R_a   (init != 0 overwrites)
 int accum_JT(const Grid& g, const void* Du, bool du_bf16, const float* R, float w, float* acc,
              int init, cudaStream_t st);
+// acc_b = sum_{j=nt..0} w_j sum_a Du_j[a*3+b] R_j[a] in one pass over nt + 1 nodes (R_j at
+// R + 3 n j; Du_j at node stride 9 n floats or jac_bf16_stride(n) BF16 elements; w_j = w_end
+// at j = 0 and nt, w_mid between): the same bits as accum_JT node by node from j = nt down
+int accum_JT_nodes(const Grid& g, const void* Du, bool du_bf16, const float* R, int nt,
+                   float w_end, float w_mid, float* acc, cudaStream_t st);
 // J = det(I - Du) per voxel (J may be NULL) and kReduceBlocks per-block minima / maxima
 int jacobian_det(const Grid& g, const float* Du, float* J, double* pmin, double* pmax, cudaStream_t st);
 // Jacobian planes in the packed BF16 form the Hessian kernels read: per node, the 8 entries
@@ -274,6 +279,11 @@ int sl_inc_image(const SLArgs& a, const float* U, const float* D, const float* F
 int image_rhs(const Grid& g, const float* Gm, const float* dv, float* F, cudaStream_t st);
 int accum_sv(const Grid& g, const float* s, const float* Gm, float w, float* acc, int init,
              cudaStream_t st);
+// acc_b = sum_{j=nt..0} w_j s_j Gm_{j,b} in one pass over nt + 1 nodes (s_j at S + n j, Gm_j at
+// Gm + 3 n j; w_j = w_end at j = 0 and nt, w_mid between): the same bits as accum_sv node by
+// node from j = nt down
+int accum_sv_nodes(const Grid& g, const float* S, const float* Gm, int nt, float w_end, float w_mid,
+                   float* acc, cudaStream_t st);
 int scaled_diff(const Grid& g, const float* a, const float* b, float coef, float* out,
                 cudaStream_t st);
 

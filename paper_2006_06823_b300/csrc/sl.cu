@@ -929,6 +929,50 @@ int accum_JT(const Grid& g, const void* Du, bool du_bf16, const float* R, float 
     return LDDMM_OK;
 }
 
+// acc_b = sum_j w_j sum_a Du_j[a*3+b] R_j[a] over the nodes j = nt .. 0 in one pass (the
+// trapezoid weights: w_end at j = 0 and j = nt, w_mid between). The sum runs in the order of
+// the node-by-node form above (node nt first, then one fmaf per node downwards), so both give
+// the same bits, while the accumulator is written once instead of read and written per node.
+template <typename TJ>
+__global__ void __launch_bounds__(256)
+k_accum_JT_nodes(long n, int nt, const TJ* __restrict__ Du, long du_stride,
+                 const float* __restrict__ R, float w_end, float w_mid, float* __restrict__ acc) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float a[3];
+#pragma unroll 2
+    for (int j = nt; j >= 0; --j) {
+        const float* Rj = R + (long)j * 3 * n;
+        const float r0 = __ldcs(Rj + i), r1 = __ldcs(Rj + n + i), r2 = __ldcs(Rj + 2 * n + i);
+        float J[9];
+        load_jac9(Du + (long)j * du_stride, (int)n, (int)i, J);
+        const float w = (j == 0 || j == nt) ? w_end : w_mid;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            float s = J[b] * r0 + J[3 + b] * r1 + J[6 + b] * r2;
+            a[b] = j == nt ? w * s : fmaf(w, s, a[b]);
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < 3; ++b) acc[b * n + i] = a[b];
+}
+
+int accum_JT_nodes(const Grid& g, const void* Du, bool du_bf16, const float* R, int nt,
+                   float w_end, float w_mid, float* acc, cudaStream_t st) {
+    long n = g.ntot();
+    if (nt < 1) { set_error("accum_JT_nodes: nt must be >= 1"); return LDDMM_EINVAL; }
+    KTRACE("accum_JT_nodes", st, n * ((nt + 1) * (du_bf16 ? 30.0 : 48.0) + 12.0),
+           21.0 * n * (nt + 1));
+    if (du_bf16)
+        k_accum_JT_nodes<<<cdiv(n, 256), 256, 0, st>>>(n, nt, static_cast<const __nv_bfloat16*>(Du),
+                                                       jac_bf16_stride(n), R, w_end, w_mid, acc);
+    else
+        k_accum_JT_nodes<<<cdiv(n, 256), 256, 0, st>>>(n, nt, static_cast<const float*>(Du), 9 * n, R,
+                                                       w_end, w_mid, acc);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
 // J = det(I - Du) per voxel from the nine planes Du[3a + b] = d u_a / d x_b (physical), with
 // per-block minimum and maximum (FP64) into pmin / pmax (kReduceBlocks each).
 __global__ void __launch_bounds__(256)
@@ -1226,6 +1270,72 @@ int accum_sv(const Grid& g, const float* s, const float* Gm, float w, float* acc
                                                       w, acc, init);
     else
         k_accum_sv<<<cdiv(n, 256), 256, 0, st>>>(n, s, Gm, w, acc, init);
+    LDDMM_CHECK_LAUNCH();
+    return LDDMM_OK;
+}
+
+// acc_b = sum_{j=nt..0} w_j s_j(x) Gm_{j,b}(x) in one pass over the nodes (s_j at S + n j, Gm_j at
+// Gm + 3 n j; w_j = w_end at j = 0 and nt, w_mid between), in the order and with the roundings
+// of accum_sv node by node from j = nt down, so both give the same bits.
+__global__ void __launch_bounds__(256)
+k_accum_sv_nodes(long n, int nt, const float* __restrict__ S, const float* __restrict__ Gm,
+                 float w_end, float w_mid, float* __restrict__ acc) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float a[3];
+#pragma unroll 2
+    for (int j = nt; j >= 0; --j) {
+        const float w = (j == 0 || j == nt) ? w_end : w_mid;
+        const float v = w * __ldcs(S + (long)j * n + i);
+        const float* G = Gm + (long)j * 3 * n;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const float gm = __ldcs(G + b * n + i);
+            a[b] = j == nt ? v * gm : fmaf(v, gm, a[b]);
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < 3; ++b) acc[b * n + i] = a[b];
+}
+
+// four voxels per thread (n % 4 == 0, 16-byte aligned planes)
+__global__ void __launch_bounds__(256)
+k_accum_sv4_nodes(long n4, long n, int nt, const float* __restrict__ S, const float* __restrict__ Gm,
+                  float w_end, float w_mid, float* __restrict__ acc) {
+    long i = (long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n4) return;
+    float4 a[3];
+#pragma unroll 2
+    for (int j = nt; j >= 0; --j) {
+        const float w = (j == 0 || j == nt) ? w_end : w_mid;
+        const float4 sv = __ldcs(reinterpret_cast<const float4*>(S + (long)j * n) + i);
+        const float4 v = make_float4(w * sv.x, w * sv.y, w * sv.z, w * sv.w);
+        const float* G = Gm + (long)j * 3 * n;
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            const float4 gm = __ldcs(reinterpret_cast<const float4*>(G + b * n) + i);
+            if (j == nt)
+                a[b] = make_float4(v.x * gm.x, v.y * gm.y, v.z * gm.z, v.w * gm.w);
+            else
+                a[b] = make_float4(fmaf(v.x, gm.x, a[b].x), fmaf(v.y, gm.y, a[b].y),
+                                   fmaf(v.z, gm.z, a[b].z), fmaf(v.w, gm.w, a[b].w));
+        }
+    }
+#pragma unroll
+    for (int b = 0; b < 3; ++b) reinterpret_cast<float4*>(acc + b * n)[i] = a[b];
+}
+
+int accum_sv_nodes(const Grid& g, const float* S, const float* Gm, int nt, float w_end, float w_mid,
+                   float* acc, cudaStream_t st) {
+    long n = g.ntot();
+    if (nt < 1) { set_error("accum_sv_nodes: nt must be >= 1"); return LDDMM_EINVAL; }
+    KTRACE("accum_sv_nodes", st, n * ((nt + 1) * 16.0 + 12.0), 7.0 * n * (nt + 1));
+    const bool al = ((reinterpret_cast<uintptr_t>(S) | reinterpret_cast<uintptr_t>(Gm) |
+                      reinterpret_cast<uintptr_t>(acc)) & 15) == 0;
+    if ((n & 3) == 0 && al)
+        k_accum_sv4_nodes<<<cdiv(n / 4, 256), 256, 0, st>>>(n / 4, n, nt, S, Gm, w_end, w_mid, acc);
+    else
+        k_accum_sv_nodes<<<cdiv(n, 256), 256, 0, st>>>(n, nt, S, Gm, w_end, w_mid, acc);
     LDDMM_CHECK_LAUNCH();
     return LDDMM_OK;
 }
