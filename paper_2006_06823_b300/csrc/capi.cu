@@ -350,7 +350,9 @@ static int state_defstate(lddmm_ctx* c) {
     const long kc3 = 3 * c->kc;
     LDDMM_CUDA(cudaMemsetAsync(c->ut, 0, kc3 * sizeof(float2), c->st));
     for (int j = 0; j < c->p.nt; ++j) {
-        TRY(include(c, c->ut + j * kc3, 3, c->fa, c->n, -1, cubic(c)));
+        // iota(u~_0) = 0 (and so are its B-spline coefficients): cleared, not synthesised
+        if (j == 0) LDDMM_CUDA(cudaMemsetAsync(c->fa, 0, 3 * c->n * sizeof(float), c->st));
+        else TRY(include(c, c->ut + j * kc3, 3, c->fa, c->n, -1, cubic(c)));
         TRY(sl_gather_add(c->sl, c->fa, Dfstep(c, j), Wstep(c, j), 3, c->fb, c->st));
         TRY(project(c, c->fb, 3, c->ut + (j + 1) * kc3));
     }
@@ -465,7 +467,9 @@ static int ensure_traj(lddmm_ctx* c) {
     if (c->traj_valid) return LDDMM_OK;
     const long n = c->n;
     if (has_u(c)) {
-        for (int j = 0; j <= c->p.nt; ++j)
+        // the Jacobian of u~_0 = 0 vanishes
+        LDDMM_CUDA(cudaMemsetAsync(c->Du, 0, 9 * n * sizeof(float), c->st));
+        for (int j = 1; j <= c->p.nt; ++j)
             for (int b = 0; b < 3; ++b)
                 TRY(include(c, c->ut + (long)j * 3 * c->kc, 3, c->Du + (long)j * 9 * n + b * n,
                             3 * n, b, 0));
@@ -676,7 +680,9 @@ static int hessian_impl(lddmm_ctx* c, const float2* dvt, float2* out) {
         TRY(defstate_rhs(c->g, jac(c, 0, true), jac_bf16(c), c->dvsp, Fold, c->st));
         LDDMM_CUDA(cudaMemsetAsync(dut, 0, kc3 * sizeof(float2), c->st));
         for (int j = 0; j < nt; ++j) {
-            TRY(include(c, dut, 3, c->fb, n, -1, cubic(c)));
+            // du~_0 = 0: its values (or B-spline coefficients) are cleared, not synthesised
+            if (j == 0) LDDMM_CUDA(cudaMemsetAsync(c->fb, 0, 3 * n * sizeof(float), c->st));
+            else TRY(include(c, dut, 3, c->fb, n, -1, cubic(c)));
             const float* Fsrc = Fold;
             if (cubic(c)) {
                 TRY(bspline_prefilter(c->g, Fold, 3, c->acc, c->st));
@@ -709,7 +715,9 @@ static int hessian_impl(lddmm_ctx* c, const float2* dvt, float2* out) {
     TRY(image_rhs(c->g, c->Gm, c->dvsp, Fold, c->st));
     LDDMM_CUDA(cudaMemsetAsync(dmt, 0, c->kc * sizeof(float2), c->st));
     for (int j = 0; j < nt; ++j) {
-        TRY(include(c, dmt, 1, c->fb, n, -1, cubic(c)));
+        // dm~_0 = 0: cleared, not synthesised
+        if (j == 0) LDDMM_CUDA(cudaMemsetAsync(c->fb, 0, n * sizeof(float), c->st));
+        else TRY(include(c, dmt, 1, c->fb, n, -1, cubic(c)));
         const float* Fsrc = Fold;
         if (cubic(c)) {
             TRY(bspline_prefilter(c->g, Fold, 1, c->acc, c->st));
