@@ -115,7 +115,10 @@ typedef struct lddmm_ctx lddmm_ctx;
 /* ---------------------------------------------------------------- context lifecycle */
 
 /* Validates *params, allocates the context's device workspace on the current device and
- * binds the context to `stream`. *out receives the handle (NULL on failure).
+ * binds the context to `stream`. *out receives the handle (NULL on failure). The workspace
+ * grows with nt: the stationary deformation-state form keeps, per voxel, 36 (nt + 1) bytes of
+ * trajectory Jacobians and 12 (nt + 1) bytes of per-node adjoint values besides about 150
+ * bytes of fields; lddmm_workspace_bytes reports a context's total.
  * Errors: EINVAL (shape, band, variant, interp, nt, sigma2 <= 0), ENOMEM, ECUDA. */
 int lddmm_create(const lddmm_params* params, void* stream, lddmm_ctx** out);
 
