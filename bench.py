@@ -317,6 +317,7 @@ def run_b300(args):
     forms = measure_forms(L, torch, I0d, I1d, stream, flush) if args.forms and rank == 0 else None
     warm = measure_warm_start(L, torch) if args.forms and rank == 0 else None
     chosen = measure_chosen_form(L, torch) if args.forms and rank == 0 else None
+    batched = measure_batched_form(args) if args.forms and rank == 0 else None
 
     if rank != 0:
         return None
@@ -391,6 +392,8 @@ def run_b300(args):
         out["chosen_form"] = chosen
     if warm is not None:
         out["warm_start_blobs"] = warm
+    if batched is not None:
+        out["batched_form"] = batched
     if not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(steps_per_pair=last["solves"] * NT, samples=1)
     return out
@@ -398,6 +401,24 @@ def run_b300(args):
 
 RESIDUAL_LEVELS = (1e-1, 1e-2, 1e-3)
 LONG_GN = 40
+BATCH_PAIRS_IN_LINE = 16
+
+
+def measure_batched_form(args):
+    """The batched form on the first BATCH_PAIRS_IN_LINE pairs of the batched workload (the
+    `--config batch` run with fewer pairs), reported beside the headline: pairs/s through
+    lddmm_register_batch against the sequential loop, and the persistent batched transport.
+    Outside the timed region; a failure is reported in place of the numbers."""
+    sub = argparse.Namespace(**vars(args))
+    sub.pairs = min(args.pairs, BATCH_PAIRS_IN_LINE)
+    try:
+        r = run_batch(sub)
+    except Exception as e:   # noqa: BLE001 - reported, the headline stands
+        return {"error": f"{type(e).__name__}: {e}"}
+    keep = ("value", "unit", "config", "sequential_pairs_per_s", "speedup_vs_sequential",
+            "per_pair_time_to_residual_s", "residual_reached", "identical_to_sequential",
+            "gpu_launches", "transport")
+    return {k: r[k] for k in keep if k in r}
 
 
 def first_time_at(hist, level):
@@ -782,9 +803,10 @@ def run_reference(args):
 
 
 BATCH_SHAPES = [(64, 64, 64), (96, 96, 96), (128, 128, 128), (160, 160, 160), (96, 128, 96)]
-BATCH_WORKLOAD = ("64 seeded ellipsoid-phantom pairs (seeds 100-163), grids drawn from "
-                  "{64^3, 96^3, 128^3, 160^3, 96x128x96}, K drawn from even 16..32, "
-                  "deformation-state, nt=10, trilinear, <=10 GN x <=20 PCG, gtol=1e-3")
+def batch_workload(npairs):
+    return (f"{npairs} seeded ellipsoid-phantom pairs (seeds 100-{99 + npairs}), grids drawn "
+            "from {64^3, 96^3, 128^3, 160^3, 96x128x96}, K drawn from even 16..32, "
+            "deformation-state, nt=10, trilinear, <=10 GN x <=20 PCG, gtol=1e-3")
 
 
 def measure_batch_transport(L, torch, warps, reps=5):
@@ -895,7 +917,7 @@ def run_batch(args):
             "unit": "pairs/s", "n_gpus": 1, "steps": 1, "warmup": 1,
             "ms_per_step": t_bat * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "b300",
-            "config": {"workload": BATCH_WORKLOAD, "pairs": npairs,
+            "config": {"workload": batch_workload(npairs), "pairs": npairs,
                        "threads": args.batch_threads},
             "sequential_pairs_per_s": npairs / t_seq,
             "speedup_vs_sequential": t_seq / t_bat,

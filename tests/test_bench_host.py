@@ -92,3 +92,24 @@ def test_time_to_residual_takes_the_first_iterate_at_or_below_each_level(bench):
 def test_host_replicas_are_bounded_by_cores_and_memory(bench):
     P, ncpu = bench._host_replicas()
     assert 1 <= P <= ncpu
+
+
+def test_batched_form_in_the_line_reports_a_failure_instead_of_raising(bench, monkeypatch):
+    def broken(args):
+        assert args.pairs == bench.BATCH_PAIRS_IN_LINE   # the reduced pair count is passed on
+        raise RuntimeError("no device")
+    monkeypatch.setattr(bench, "run_batch", broken)
+    import argparse
+    out = bench.measure_batched_form(argparse.Namespace(pairs=64, batch_threads=16))
+    assert out == {"error": "RuntimeError: no device"}
+
+
+def test_batched_form_keeps_the_throughput_fields(bench, monkeypatch):
+    full = {"value": 14.0, "unit": "pairs/s", "config": {"pairs": 16}, "sequential_pairs_per_s": 9.0,
+            "speedup_vs_sequential": 1.5, "metric": "dropped", "ms_per_step": 1.0}
+    monkeypatch.setattr(bench, "run_batch", lambda args: full)
+    import argparse
+    out = bench.measure_batched_form(argparse.Namespace(pairs=64, batch_threads=16))
+    assert out == {k: full[k] for k in ("value", "unit", "config", "sequential_pairs_per_s",
+                                        "speedup_vs_sequential")}
+    assert "16 seeded" in bench.batch_workload(16) and "seeds 100-115" in bench.batch_workload(16)
