@@ -444,14 +444,17 @@ def sl_transport_batch(vels, fields, nt, direction=FORWARD, outs=None, active=No
         raise ValueError("sl_transport_batch: one field per velocity")
     if outs is None:
         outs = [torch.empty_like(f) for f in fields]
+    if len(outs) != n:
+        raise ValueError("sl_transport_batch: one output per velocity")
     dims = (ctypes.c_int * (3 * max(n, 1)))()
     vp, fp, op = ((_P * max(n, 1))() for _ in range(3))
+    for v, f, o in zip(vels, fields, outs):   # every size before any device check
+        _sized(v, 3 * f.numel(), "sl_transport_batch: velocity")
+        _sized(o, f.numel(), "sl_transport_batch: out")
     for p, (v, f, o) in enumerate(zip(vels, fields, outs)):
         nz, ny, nx = f.shape
         dims[3 * p], dims[3 * p + 1], dims[3 * p + 2] = nx, ny, nz
-        vp[p] = _f32(_sized(v, 3 * f.numel(), "sl_transport_batch: velocity")).value
-        fp[p] = _f32(f).value
-        op[p] = _f32(_sized(o, f.numel(), "sl_transport_batch: out")).value
+        vp[p], fp[p], op[p] = _f32(v).value, _f32(f).value, _f32(o).value
     act = None
     if active is not None:
         act = _ptr(_sized(active, n, "sl_transport_batch: active"), torch.int32)

@@ -386,6 +386,17 @@ def test_binding_rejects_undersized_and_mismatched_tensors_before_calling_the_li
         L.sl_transport(torch.zeros((3, 8, 8, 4)), f, 2)
     with pytest.raises(ValueError, match="sl_transport: out"):
         L.sl_transport(vel, torch.zeros((2, 8, 8, 8)), 2, out=torch.empty((1, 8, 8, 8)))
+    field = torch.zeros((8, 8, 8))
+    with pytest.raises(ValueError, match="one field per velocity"):
+        L.sl_transport_batch([vel, vel], [field], 2)
+    with pytest.raises(ValueError, match="one output per velocity"):
+        L.sl_transport_batch([vel, vel], [field, field], 2, outs=[field])
+    with pytest.raises(ValueError, match="sl_transport_batch: velocity"):
+        L.sl_transport_batch([torch.zeros((2, 8, 8, 8))], [field], 2)
+    with pytest.raises(ValueError, match="sl_transport_batch: out"):
+        L.sl_transport_batch([vel], [field], 2, outs=[torch.empty((8, 8, 7))])
+    with pytest.raises(ValueError, match="sl_transport_bf16: out"):
+        L.sl_transport_bf16(vel, field, 2, out=torch.empty((8, 8, 7)))
     # a context's velocity-shaped arguments: (nt + 1) cubes in the non-stationary form
     ctx = object.__new__(L.Context)
     ctx._vec_ptr, ctx._vec_len = L._c64, 5 * 3 * 4 ** 3
