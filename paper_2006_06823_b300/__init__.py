@@ -603,6 +603,10 @@ def register_batch(contexts, velocities, g_ref_norms=None, max_threads=8):
     (each best created under its own torch CUDA stream); ``velocities``: complex64
     [3, K, K, K] device cubes updated in place. Returns the list of report dicts."""
     n = len(contexts)
+    if len(velocities) != n:
+        raise ValueError("register_batch: one velocity per context")
+    if g_ref_norms is not None and (len(g_ref_norms) != n or any(len(p) != 2 for p in g_ref_norms)):
+        raise ValueError("register_batch: g_ref_norms needs one (l2, inf) norm pair per context")
     hs = (_P * n)(*[c._h for c in contexts])
     vs = (_P * n)(*[ctypes.c_void_p(c._vec(v).value) for c, v in zip(contexts, velocities)])
     reps = (Report * n)()

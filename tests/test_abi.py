@@ -386,6 +386,10 @@ def test_binding_rejects_undersized_and_mismatched_tensors_before_calling_the_li
         L.sl_transport(torch.zeros((3, 8, 8, 4)), f, 2)
     with pytest.raises(ValueError, match="sl_transport: out"):
         L.sl_transport(vel, torch.zeros((2, 8, 8, 8)), 2, out=torch.empty((1, 8, 8, 8)))
+    with pytest.raises(ValueError, match="one velocity per context"):
+        L.register_batch([object(), object()], [None])
+    with pytest.raises(ValueError, match="norm pair per context"):
+        L.register_batch([object()], [None], g_ref_norms=[(1.0,)])
     field = torch.zeros((8, 8, 8))
     with pytest.raises(ValueError, match="one field per velocity"):
         L.sl_transport_batch([vel, vel], [field], 2)
