@@ -5,34 +5,27 @@ pipelined SL kernels (the depth the paper-scale grid gets by default), and the p
 input recipe scaled to this grid: the ellipsoid phantom warped by a random band-limited
 velocity (4 voxels max displacement, the oracle's transport) with N(0, 0.01) noise on both
 images. Trilinear and cubic B-spline interpolation (Sec. 4.2), deformation-state variant
-(Sec. 2.3.3). The oracle's time steps are kept few (nt = 3 / 2) so that its FP64 sweeps
-over the million voxels finish in about a minute."""
+(Sec. 2.3.3). The oracle's time steps are kept few (nt = 3 / 2). The inputs are rebuilt here
+from the seeded generator and the oracle's transport; the oracle's gradient, Gauss-Newton
+product and registration reports, which take minutes of host time at this size, are read
+from ``tests/golden/`` as written by ``tests/golden/make_benchpath.py`` (oracle calls only;
+``tests/test_golden_benchpath.py`` checks them against the live oracle where that is cheap)."""
+import json
+import os
+
 import numpy as np
 import pytest
 
-from oracle import sl as SL
+from _problems import BENCH_K, BENCH_SHAPE, bench_phantom_problem, bench_velocity, \
+    first_direction, rel_l2, small_phantom_problem
 from oracle import spectral as S
-from oracle import variants as Vn
-from paper_2006_06823_b300 import synth
-from _problems import rel_l2, scaled_velocity, voxel_velocity
 
 pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 import paper_2006_06823_b300 as L  # noqa: E402
 
-SHAPE = (96, 112, 96)   # nz, ny, nx
-K = 32
-
-
-def phantom_problem(order, nt, noisy=True):
-    nz, ny, nx = SHAPE
-    fixed = synth.ellipsoid_phantom(SHAPE)
-    vt = scaled_velocity(K, K, 1, SHAPE, 8.0 * nx / 192)
-    moving = SL.sl_transport(fixed, voxel_velocity(vt, SHAPE), 10, +1, 1)
-    I0 = synth.add_noise(moving, seed=2) if noisy else moving
-    I1 = synth.add_noise(fixed, seed=3) if noisy else fixed
-    return Vn.Problem(I0, I1, Vn.Params(K=K, nt=nt, order=order, variant=Vn.DEFSTATE, sigma2=0.01))
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
 
 
 def _dev(a):
@@ -41,6 +34,11 @@ def _dev(a):
 
 def _devc(c):
     return torch.as_tensor(np.ascontiguousarray(c).astype(np.complex64), device="cuda")
+
+
+def _stored(order, nt, noisy):
+    kind = "noisy" if noisy else "clean"
+    return np.load(os.path.join(GOLDEN, f"benchpath_o{order}_nt{nt}_{kind}.npz"))
 
 
 # Tolerances (relative L2). Trilinear interpolation of a noisy image has a gradient that jumps
@@ -53,15 +51,15 @@ def _devc(c):
 @pytest.mark.parametrize("order,nt,noisy,tol", [(1, 3, False, 1e-4), (1, 3, True, 5e-3),
                                                 (3, 2, True, 1e-4)])
 def test_gradient_and_hessian_on_the_bench_launch_path(order, nt, noisy, tol):
-    prob = phantom_problem(order, nt, noisy)
-    vt = scaled_velocity(K, K, 5, SHAPE, 2.0)
-    E, Er, Ed, g = prob.gradient(vt)
+    prob = bench_phantom_problem(order, nt, noisy)
+    ref = _stored(order, nt, noisy)
+    E, g, Hp, pHp = float(ref["E"]), ref["g"], ref["Hp"], float(ref["pHp"])
     # the first PCG direction of a Gauss-Newton step, L~^{-1}(-g), as the product's argument
-    p = S.apply_Linv(-g, prob.p.alpha, prob.p.s)
-    Hp = prob.hessian_matvec(vt, p)
-    nz, ny, nx = SHAPE
-    with L.Context(nx, ny, nz, K, nt=nt, variant=L.V_DEFSTATE, interp=order, alpha=prob.p.alpha,
-                   s=prob.p.s, sigma2=prob.p.sigma2) as ctx:
+    p = first_direction(g, prob.p.alpha, prob.p.s)
+    vt = bench_velocity()
+    nz, ny, nx = BENCH_SHAPE
+    with L.Context(nx, ny, nz, BENCH_K, nt=nt, variant=L.V_DEFSTATE, interp=order,
+                   alpha=prob.p.alpha, s=prob.p.s, sigma2=prob.p.sigma2) as ctx:
         ctx.set_option(L.OPT_GATHER_ZT, 4)
         ctx.set_images(_dev(prob.I0), _dev(prob.I1))
         (Eg, _, _), gg = ctx.gradient(_devc(vt))
@@ -72,18 +70,8 @@ def test_gradient_and_hessian_on_the_bench_launch_path(order, nt, noisy, tol):
     assert rel_l2(gg, g) < tol
     assert rel_l2(Hg, Hp) < tol
     # the curvature PCG tests first (its sign decides a negative-curvature stop)
-    assert S.inner(p, Hg) == pytest.approx(S.inner(p, Hp), rel=tol)
-    assert S.inner(p, Hp) > 0
-
-
-def small_phantom_problem(order, nt, shape=(32, 32, 32), K_=16):
-    nz, ny, nx = shape
-    fixed = synth.ellipsoid_phantom(shape)
-    vt = scaled_velocity(K_, K_, 1, shape, 8.0 * nx / 192)
-    moving = SL.sl_transport(fixed, voxel_velocity(vt, shape), 10, +1, 1)
-    I0 = synth.add_noise(moving, seed=2)
-    I1 = synth.add_noise(fixed, seed=3)
-    return Vn.Problem(I0, I1, Vn.Params(K=K_, nt=nt, order=order, variant=Vn.DEFSTATE, sigma2=0.01))
+    assert S.inner(p, Hg) == pytest.approx(pHp, rel=tol)
+    assert pHp > 0
 
 
 @pytest.mark.parametrize("order", [1, 3])
@@ -93,24 +81,25 @@ def test_noisy_phantom_registration_follows_the_oracle_iterate_by_iterate(order)
     oracle's. With cubic interpolation both take only one to three PCG iterations per
     Gauss-Newton step (a single conjugate-gradient step already meets the forcing term 0.5)
     and the residual falls slowly, as the cubic form does at the paper grid."""
-    from oracle import gnk
-    prob = small_phantom_problem(order, nt=4)
-    v_o, rep_o = gnk.register(prob, max_gn=3, max_pcg=20)
+    with open(os.path.join(GOLDEN, f"benchpath_registration_o{order}.json")) as f:
+        rep_o = json.load(f)
+    cfg = rep_o["config"]
+    prob = small_phantom_problem(order, nt=cfg["nt"])
     nz, ny, nx = prob.I0.shape
     with L.Context(nx, ny, nz, prob.p.K, nt=prob.p.nt, variant=L.V_DEFSTATE, interp=order,
-                   alpha=prob.p.alpha, s=prob.p.s, sigma2=prob.p.sigma2, max_gn=3,
-                   max_pcg=20) as ctx:
+                   alpha=prob.p.alpha, s=prob.p.s, sigma2=prob.p.sigma2, max_gn=cfg["max_gn"],
+                   max_pcg=cfg["max_pcg"]) as ctx:
         ctx.set_images(_dev(prob.I0), _dev(prob.I1))
         _, rep = ctx.register()
         hist = ctx.history()
-    assert rep["gn_iters"] == rep_o.gn_iters
-    assert rep["pcg_iters_total"] == rep_o.pcg_iters_total
-    assert rep["stop_reason"] == rep_o.stop_reason
-    assert rep["E"] == pytest.approx(rep_o.E, rel=1e-3)
-    assert rep["grad_rel_l2"] == pytest.approx(rep_o.grad_rel_l2, rel=1e-2)
+    assert rep["gn_iters"] == rep_o["gn_iters"]
+    assert rep["pcg_iters_total"] == rep_o["pcg_iters_total"]
+    assert rep["stop_reason"] == rep_o["stop_reason"]
+    assert rep["E"] == pytest.approx(rep_o["E"], rel=1e-3)
+    assert rep["grad_rel_l2"] == pytest.approx(rep_o["grad_rel_l2"], rel=1e-2)
     # the history: one record per iterate, the oracle's (E, residual) before each update
     assert len(hist) == rep["gn_iters"] + 1
-    for h, (E_o, res_o) in zip(hist, rep_o.history):
+    for h, (E_o, res_o) in zip(hist, rep_o["history"]):
         assert h["E"] == pytest.approx(E_o, rel=1e-3)
         assert h["residual"] == pytest.approx(res_o, rel=1e-2)
     assert hist[-1]["residual"] == pytest.approx(rep["grad_rel_l2"], rel=1e-12)
