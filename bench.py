@@ -358,7 +358,7 @@ def run_b300(args):
         "config": {"workload": WORKLOAD if SHAPE == (192, 224, 192) else
                    f"profiling case: {WORKLOAD} on a {SHAPE[2]}x{SHAPE[1]}x{SHAPE[0]} grid",
                    "pairs_per_step": world,
-                   "l2": "flushed (256 MB write) between timed steps; working set ~5 GB"},
+                   "l2": "flushed (256 MB write) between timed steps; working set ~6 GB"},
         "residual_reached": last["grad_rel_l2"] <= GTOL,
         "value_is": (f"time to the relative residual {GTOL:g}" if last["grad_rel_l2"] <= GTOL else
                      f"time to the {MAX_GN}-GN cap of the workload (relative residual "
